@@ -1,0 +1,199 @@
+"""Seeded synthetic inputs: cell-type maps of distributor trees and test domains.
+
+This module only draws geometry (integer cell maps) and workload recipes; it
+holds none of the lattice Boltzmann arithmetic, so both the CUDA path and the
+CPU oracle can be fed from it.  Cell maps are uint8 arrays of shape (ny, nx),
+row-major, 1 = solid, 0 = fluid; x runs along the flow, y across.
+
+The paper's own geometry figures are not available, so the distributor is
+drawn from its description (Sec. 3.2): a binary tree of T-bifurcations fed by
+one inlet channel, 2^G parallel outlets, segment lengths in the 2:2:1:1
+proportion of Eq. 7 (the inlet trunk counted as 2), widths shrinking by a
+ratio r per generation.
+"""
+import math
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, counter: int) -> int:
+    """SplitMix64 output for state seed + (counter+1)*golden (Steele, Lea & Flood 2014)."""
+    z = (seed + (counter + 1) * 0x9E3779B97F4A7C15) & MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return z ^ (z >> 31)
+
+
+def uniform01(seed: int, counter: int) -> float:
+    return (splitmix64(seed, counter) >> 11) * (1.0 / (1 << 53))
+
+
+def _fill(cells, x0, x1, y0, y1):
+    ny, nx = cells.shape
+    cells[max(y0, 1):min(y1, ny - 1), max(x0, 0):min(x1, nx)] = 0
+
+
+def tree_widths(w0: int, ratio: float, generations: int, min_width: int = 3):
+    return [max(min_width, int(round(w0 * ratio ** k))) for k in range(generations + 1)]
+
+
+def tree(nx: int, ny: int, generations: int, w0: int, ratio: float = 0.5, jitter: int = 2,
+         seed: int = 0, widths=None, lengths=(2, 2, 2, 1, 1)) -> np.ndarray:
+    """Arborescent distributor: one inlet on x = 0, 2^G outlets on x = nx-1.
+
+    Generation 0 is the trunk of width W0 centred on y = ny/2.  A node of
+    generation k (k = 1..G) sits at x = X_k (+ jitter) and is a vertical bar of
+    width W_k spanning its parent's centre +- s_k, s_k = ny / 2^(k+1); two
+    horizontal children of width W_k leave the bar ends towards the next
+    generation (or the outlet column for k = G).  X_k follows the segment
+    lengths `lengths` (Eq. 7 proportions), unit = nx / sum(lengths[:G+1]).
+    Each node is shifted by an integer in [-jitter, jitter] drawn from
+    splitmix64(seed, node id), node id = 2^(k-1) + j in heap order.
+    """
+    G = int(generations)
+    if widths is None:
+        widths = tree_widths(w0, ratio, G)
+    widths = [int(w) for w in widths]
+    lens = list(lengths[:G + 1])
+    unit = nx / float(sum(lens))
+    xs_nominal = [int(round(unit * sum(lens[:k]))) for k in range(G + 1)]  # X_0 = 0 .. X_G
+    cells = np.ones((ny, nx), np.uint8)
+
+    def node_x(k, j):
+        if jitter <= 0:
+            return xs_nominal[k]
+        node_id = (1 << (k - 1)) + j
+        shift = int(splitmix64(seed, node_id) % (2 * jitter + 1)) - jitter
+        return xs_nominal[k] + shift
+
+    def hchannel(yc, w, x0, x1):
+        _fill(cells, x0, x1, yc - w // 2, yc - w // 2 + w)
+
+    yc0 = ny // 2
+    if G == 0:
+        hchannel(yc0, widths[0], 0, nx)
+        return cells
+    # trunk: from the inlet to the far side of the first bar
+    x1 = node_x(1, 0)
+    hchannel(yc0, widths[0], 0, x1 + widths[1])
+    # level by level: (centre y, x of the node) of every node of generation k
+    level = [(yc0, x1)]
+    for k in range(1, G + 1):
+        s = ny >> (k + 1)
+        wk = widths[k]
+        nxt = []
+        for j, (yc, xk) in enumerate(level):
+            # vertical bar of the T
+            _fill(cells, xk, xk + wk, yc - s - wk // 2, yc + s - wk // 2 + wk)
+            for side, yc_child in enumerate((yc - s, yc + s)):
+                if k < G:
+                    jj = 2 * j + side
+                    x_next = node_x(k + 1, jj)
+                    hchannel(yc_child, wk, xk, x_next + widths[k + 1])
+                    nxt.append((yc_child, x_next))
+                else:
+                    hchannel(yc_child, wk, xk, nx)
+        level = nxt
+    return cells
+
+
+def channel(nx: int, height: int) -> np.ndarray:
+    """Straight channel of `height` fluid rows between two walls, open at both ends."""
+    cells = np.ones((height + 2, nx), np.uint8)
+    cells[1:height + 1, :] = 0
+    return cells
+
+
+def box(nx: int, ny: int) -> np.ndarray:
+    """Closed box: fluid inside a one-cell solid frame on all four sides."""
+    cells = np.ones((ny, nx), np.uint8)
+    cells[1:ny - 1, 1:nx - 1] = 0
+    return cells
+
+
+def channel_array(nx: int, ny: int, n_channels: int, fill: float = 0.5) -> np.ndarray:
+    """n straight parallel channels across the whole length (fluid fraction ~fill)."""
+    cells = np.ones((ny, nx), np.uint8)
+    pitch = ny // n_channels
+    h = max(1, int(round(pitch * fill)))
+    for c in range(n_channels):
+        y0 = c * pitch + (pitch - h) // 2
+        _fill(cells, 0, nx, y0, y0 + h)
+    return cells
+
+
+def random_blobs(nx: int, ny: int, seed: int, density: float = 0.15) -> np.ndarray:
+    """Channel with random solid obstacles (interior only), for parity of irregular walls."""
+    cells = channel(nx, ny - 2)
+    for y in range(1, ny - 1):
+        for x in range(3, nx - 3):
+            if uniform01(seed, y * nx + x) < density:
+                cells[y, x] = 1
+    return cells
+
+
+# ---------------------------------------------------------------------------
+# Workload recipes.  Lattice units: dx = dt = 1, rho0 = 1.
+# ---------------------------------------------------------------------------
+
+def config_t_junction(seed: int = 0):
+    """128 x 64, one T: inlet 8 wide, two outlets 4 wide; tau 0.8, u_max 0.05, 10 x 2000 steps."""
+    cells = tree(128, 64, 1, 8, widths=[8, 4], jitter=2, seed=seed)
+    return dict(name="t_junction_128x64", cells=cells, nx=128, ny=64, tau=0.8, u_max=0.05,
+                n_iter=10, steps=2000)
+
+
+def config_tree_2048(seed: int = 0):
+    """2048 x 1024, four generations, widths 64/32/16/8/4, jitter +-2; Re = 50 on the
+    64-wide inlet at nu = 0.01 (tau 0.53): mean inlet speed 0.0078125, u_max = 1.5x that."""
+    cells = tree(2048, 1024, 4, 64, widths=[64, 32, 16, 8, 4], jitter=2, seed=seed)
+    return dict(name="tree_2048x1024_g4", cells=cells, nx=2048, ny=1024, tau=0.53,
+                u_max=0.01171875, n_iter=50, steps=5000)
+
+
+def config_candidates(n: int = 256, base_seed: int = 0):
+    """Uneven candidate distributors: nx log-uniform in [256, 1024] (multiple of 32),
+    ny = nx/2, G in {2,3,4}, width ratio in [0.6, 0.8], W0 = ny/16; tau 0.53 and
+    Re = 50 on the inlet (u_max = 1.5 * 50 * 0.01 / W0)."""
+    out = []
+    for c in range(n):
+        s = base_seed + c
+        u = uniform01(s, 1)
+        nx = int(round(math.exp(math.log(256) + u * (math.log(1024) - math.log(256))) / 32.0)) * 32
+        ny = nx // 2
+        G = 2 + int(splitmix64(s, 2) % 3)
+        r = 0.6 + 0.2 * uniform01(s, 3)
+        w0 = max(8, ny // 16)
+        cells = tree(nx, ny, G, w0, ratio=r, jitter=2, seed=s)
+        out.append(dict(name=f"cand{c}", cells=cells, nx=nx, ny=ny, tau=0.53,
+                        u_max=1.5 * 50 * 0.01 / w0, generations=G, ratio=r, seed=s))
+    return out
+
+
+def config_served_request(seed: int):
+    """One served request: nx log-uniform in [128, 2048], ny = nx/2,
+    G = clamp(floor(log2(nx/128)) + 1, 1, 4), W0 = max(8, ny/16), r = 0.5."""
+    u = uniform01(seed, 11)
+    nx = int(round(math.exp(math.log(128) + u * (math.log(2048) - math.log(128))) / 32.0)) * 32
+    ny = nx // 2
+    G = min(4, max(1, int(math.floor(math.log2(nx / 128.0))) + 1))
+    w0 = max(8, ny // 16)
+    cells = tree(nx, ny, G, w0, ratio=0.5, jitter=2, seed=seed)
+    optimize = uniform01(seed, 12) < 0.2
+    return dict(name=f"req{seed}", cells=cells, nx=nx, ny=ny, tau=0.53,
+                u_max=min(0.05, 1.5 * 50 * 0.01 / w0), optimize=optimize, steps=1000,
+                n_iter=20 if optimize else 0, seed=seed)
+
+
+def poisson_arrivals(rate_hz: float, duration_s: float, seed: int):
+    """Arrival times (s) of a Poisson process: exponential gaps from splitmix64 uniforms."""
+    t, k, out = 0.0, 0, []
+    while True:
+        u = uniform01(seed, 1000003 + k)
+        t += -math.log(1.0 - u) / rate_hz
+        if t >= duration_s:
+            return out
+        out.append(t)
+        k += 1
