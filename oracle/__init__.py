@@ -15,13 +15,15 @@ from . import build as _build
 from .scaling import eq8_widths, reynolds, viscosity  # noqa: F401
 
 OUT_CONST_RHO, OUT_NEUMANN = 0, 1
+PORTS_REGULARIZED, PORTS_ZOU_HE = 0, 1
 REINIT_WARM, REINIT_COLD = 0, 1
 
 
 class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("tau", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("u_max", ctypes.c_double),
-                ("outlet_rule", ctypes.c_int32), ("periodic", ctypes.c_int32)]
+                ("outlet_rule", ctypes.c_int32), ("periodic", ctypes.c_int32),
+                ("port_scheme", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _LIB = None
@@ -77,9 +79,10 @@ def _u8(a):
     return np.ascontiguousarray(a, dtype=np.uint8)
 
 
-def make_params(nx, ny, tau, rho0=1.0, u_max=0.0, outlet_rule=OUT_CONST_RHO, periodic=False):
+def make_params(nx, ny, tau, rho0=1.0, u_max=0.0, outlet_rule=OUT_CONST_RHO, periodic=False,
+                port_scheme=PORTS_REGULARIZED):
     return Params(int(nx), int(ny), float(tau), float(rho0), float(u_max), int(outlet_rule),
-                  int(bool(periodic)))
+                  int(bool(periodic)), int(port_scheme), 0)
 
 
 def lattice():

@@ -53,6 +53,7 @@ static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 /
 static const double CS2 = 1.0 / 3.0;
 
 enum { ORA_OUT_CONST_RHO = 0, ORA_OUT_NEUMANN = 1 };
+enum { ORA_PORTS_REGULARIZED = 0, ORA_PORTS_ZOU_HE = 1 };
 enum { ORA_REINIT_WARM = 0, ORA_REINIT_COLD = 1 };
 enum { ORA_OK = 0, ORA_ERR_ARG = 1, ORA_ERR_GEOMETRY = 2, ORA_ERR_DIVERGED = 5 };
 
@@ -64,6 +65,10 @@ typedef struct {
   int32_t outlet_rule; /* ORA_OUT_CONST_RHO or ORA_OUT_NEUMANN                */
   int32_t periodic;    /* 1: wrap streaming in x and y, no ports (a check of
                           the bulk scheme only; never used for distributors)  */
+  int32_t port_scheme; /* ORA_PORTS_REGULARIZED or ORA_PORTS_ZOU_HE: how the
+                          velocity inlet and the constant-density outlet are
+                          imposed                                            */
+  int32_t reserved;
 } ora_params;
 
 /* Export the lattice tables so that tests can check them against the
@@ -187,6 +192,23 @@ static int pull(const ora_params* p, const uint8_t* solid, const double* fp, int
   return 1;
 }
 
+/* Regularised populations of a port cell with moments (rho, ux, uy):
+ * f_i = f_i^eq + w_i / (2 c_s^4) * (Q_i,xx Pi_xx + Q_i,yy Pi_yy + 2 Q_i,xy Pi_xy),
+ * Pi^neq = sum_i c_i c_i (f_i - f_i^eq), Q_i = c_i c_i - c_s^2 I.           */
+static void regularize(double* f, double rho, double ux, double uy) {
+  double pxx = 0.0, pyy = 0.0, pxy = 0.0;
+  for (int i = 0; i < 9; ++i) {
+    double fneq = f[i] - ora_feq(i, rho, ux, uy);
+    pxx += CX[i] * CX[i] * fneq;
+    pyy += CY[i] * CY[i] * fneq;
+    pxy += CX[i] * CY[i] * fneq;
+  }
+  for (int i = 0; i < 9; ++i) {
+    double qxx = CX[i] * CX[i] - CS2, qyy = CY[i] * CY[i] - CS2, qxy = CX[i] * CY[i];
+    f[i] = ora_feq(i, rho, ux, uy) + W[i] / (2.0 * CS2 * CS2) * (qxx * pxx + qyy * pyy + 2.0 * qxy * pxy);
+  }
+}
+
 /* One time step of Eq. 1 over columns [x_begin, x_end) (the whole lattice when
  * x_begin = 0, x_end = nx): stream (pull, bounce-back), apply the port rules,
  * take the moments (Eq. 2), relax towards f^eq with 1/tau.  fp is the
@@ -194,11 +216,26 @@ static int pull(const ora_params* p, const uint8_t* solid, const double* fp, int
  * uy (optional, may be NULL) receive the moments used in this collision; solid
  * cells get zeros there.
  *
- * Port rules (Sec. 3.3; the schemes are not named there):
- *   inlet  (x = 0): velocity (u_in(y), 0) imposed by Zou-He reconstruction of
- *                   the unknown f1, f5, f8;
- *   outlet (x = nx-1), constant density: density rho0 imposed by Zou-He
- *                   reconstruction of the unknown f3, f6, f7, u_y = 0;
+ * Port rules (Sec. 3.3 imposes a parabolic velocity at the inlet and a Neumann
+ * condition at the outlet without naming the schemes):
+ *   inlet (x = 0): velocity (u_in(y), 0).  Zou-He: the density follows from
+ *                   mass and x-momentum of the known populations,
+ *                   rho = (f0 + f2 + f4 + 2 (f3 + f6 + f7)) / (1 - u), and the
+ *                   unknown f1, f5, f8 are rebuilt so that the cell carries
+ *                   exactly (rho, rho u);
+ *   outlet (x = nx-1), constant density: rho0 imposed, the velocity
+ *                   u = -1 + (f0 + f2 + f4 + 2 (f1 + f5 + f8)) / rho0, u_y = 0,
+ *                   and f3, f6, f7 rebuilt the same way;
+ *   port scheme "regularized" (default): after that, every population of the
+ *                   port cell is replaced by f^eq(rho, u) plus the projection
+ *                   of its non-equilibrium part onto the second-order Hermite
+ *                   tensor: f_i = f_i^eq + w_i/(2 c_s^4) Q_i : Pi^neq,
+ *                   Q_i = c_i c_i - c_s^2 I, Pi^neq = sum_i c_i c_i (f_i - f_i^eq),
+ *                   with the unknown non-equilibrium parts first taken from the
+ *                   opposite directions (Latt & Chopard 2008).  Same (rho, u);
+ *                   stable down to tau close to 1/2, where plain Zou-He on wide
+ *                   ports is not;
+ *   port scheme "Zou-He": the Zou-He populations as they are (Zou & He 1997);
  *   outlet, Neumann (zero gradient, the paper's rule): the unknown f3, f6, f7
  *                   are the streamed f3, f6, f7 of the cell (nx-2, y).
  * A population of a port cell whose upstream cell is a wall was already set by
@@ -222,12 +259,20 @@ void ora_step_columns(const ora_params* p, const uint8_t* solid, const double* u
         if (!pull(p, solid, fp, i, x, y, &f[i])) f[i] = 0.0; /* set by a port rule below */
 
       if (!p->periodic && x == 0) {
-        /* inlet, Zou-He velocity rule with u = (u_in(y), 0) */
         double ux = u_in[y];
         double rho = (f[0] + f[2] + f[4] + 2.0 * (f[3] + f[6] + f[7])) / (1.0 - ux);
-        f[1] = f[3] + (2.0 / 3.0) * rho * ux;
-        f[5] = f[7] - 0.5 * (f[2] - f[4]) + (1.0 / 6.0) * rho * ux;
-        f[8] = f[6] + 0.5 * (f[2] - f[4]) + (1.0 / 6.0) * rho * ux;
+        if (p->port_scheme == ORA_PORTS_ZOU_HE) {
+          f[1] = f[3] + (2.0 / 3.0) * rho * ux;
+          f[5] = f[7] - 0.5 * (f[2] - f[4]) + (1.0 / 6.0) * rho * ux;
+          f[8] = f[6] + 0.5 * (f[2] - f[4]) + (1.0 / 6.0) * rho * ux;
+        } else {
+          for (int k = 0; k < 3; ++k) {
+            static const int UNK[3] = {1, 5, 8};
+            int i = UNK[k];
+            f[i] = ora_feq(i, rho, ux, 0.0) + (f[OPP[i]] - ora_feq(OPP[i], rho, ux, 0.0));
+          }
+          regularize(f, rho, ux, 0.0);
+        }
       } else if (!p->periodic && x == nx - 1) {
         if (p->outlet_rule == ORA_OUT_NEUMANN) {
           double g;
@@ -237,9 +282,18 @@ void ora_step_columns(const ora_params* p, const uint8_t* solid, const double* u
         } else {
           double rho = p->rho0;
           double ux = -1.0 + (f[0] + f[2] + f[4] + 2.0 * (f[1] + f[5] + f[8])) / rho;
-          f[3] = f[1] - (2.0 / 3.0) * rho * ux;
-          f[7] = f[5] + 0.5 * (f[2] - f[4]) - (1.0 / 6.0) * rho * ux;
-          f[6] = f[8] - 0.5 * (f[2] - f[4]) - (1.0 / 6.0) * rho * ux;
+          if (p->port_scheme == ORA_PORTS_ZOU_HE) {
+            f[3] = f[1] - (2.0 / 3.0) * rho * ux;
+            f[7] = f[5] + 0.5 * (f[2] - f[4]) - (1.0 / 6.0) * rho * ux;
+            f[6] = f[8] - 0.5 * (f[2] - f[4]) - (1.0 / 6.0) * rho * ux;
+          } else {
+            for (int k = 0; k < 3; ++k) {
+              static const int UNK[3] = {3, 6, 7};
+              int i = UNK[k];
+              f[i] = ora_feq(i, rho, ux, 0.0) + (f[OPP[i]] - ora_feq(OPP[i], rho, ux, 0.0));
+            }
+            regularize(f, rho, ux, 0.0);
+          }
         }
       }
 

@@ -17,9 +17,9 @@ import pytest
 from paper_1303_0107_gb300 import inputs as I
 
 
-def _poiseuille(ora, H, nx, tau, u_max, steps, rule=0):
+def _poiseuille(ora, H, nx, tau, u_max, steps, rule=0, scheme=0):
     cells = I.channel(nx, H)
-    p = ora.make_params(nx, H + 2, tau, 1.0, u_max, rule)
+    p = ora.make_params(nx, H + 2, tau, 1.0, u_max, rule, port_scheme=scheme)
     u_in = ora.inlet_profile(p, cells)
     f = ora.init(p, cells)
     f, rho, ux, uy, st = ora.run(p, cells, u_in, f, steps)
@@ -83,21 +83,24 @@ def test_poiseuille_profile_and_pressure_gradient(ora):
 
 @pytest.mark.slow
 def test_poiseuille_second_order_convergence(ora):
+    # Zou-He inlet: the profile is imposed on the inlet cells themselves, so the
+    # mid-channel error is the bulk scheme's and the walls' alone
     errs = []
     for H, steps in [(8, 4000), (16, 10000), (32, 30000)]:
-        p, cells, f, rho, ux, uy = _poiseuille(ora, H, 128, 0.8, 0.01, steps)
+        p, cells, f, rho, ux, uy = _poiseuille(ora, H, 128, 0.8, 0.01, steps, scheme=ora.PORTS_ZOU_HE)
         s = (np.arange(H) + 0.5) / H
         errs.append(np.abs(ux[1:H + 1, 64] - 0.04 * s * (1 - s)).max())
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(1.7 < o < 2.3 for o in orders), orders
 
 
-def test_port_rules_impose_their_moments(ora):
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_port_rules_impose_their_moments(ora, scheme):
     H, nx = 16, 64
-    p, cells, f, rho, ux, uy = _poiseuille(ora, H, nx, 0.8, 0.02, 500)
+    p, cells, f, rho, ux, uy = _poiseuille(ora, H, nx, 0.8, 0.02, 500, scheme=scheme)
     u_in = ora.inlet_profile(p, cells)
     fl = slice(1, H + 1)
-    # inlet: the reconstructed populations carry exactly u = (u_in(y), 0)
+    # inlet: the rebuilt populations carry exactly u = (u_in(y), 0)
     assert np.abs(ux[fl, 0] - u_in[fl]).max() <= 1e-15
     assert np.abs(uy[fl, 0]).max() <= 1e-16
     # constant-density outlet: rho = rho0, u_y = 0
@@ -111,6 +114,54 @@ def test_port_rules_impose_their_moments(ora):
     assert np.abs(ff.sum(axis=0)[fluid] - rho.reshape(-1)[fluid]).max() <= 1e-14
     jx = (cx[:, None] * ff).sum(axis=0)
     assert np.abs(jx[fluid] - (rho * ux).reshape(-1)[fluid]).max() <= 1e-15
+
+
+def test_regularized_inlet_keeps_the_nonequilibrium_stress(ora):
+    """Regularised port: the inlet cell's populations are rebuilt as
+    f^eq + w_i/(2 c_s^4) Q_i : Pi, Pi the non-equilibrium stress of the
+    populations streamed in with the unknown ones taken by non-equilibrium
+    bounce-back.  After the BGK collision the stored populations must therefore
+    be f^eq + (1 - 1/tau) * 4.5 w_i Q_i : Pi, with Pi rebuilt here by hand."""
+    H, nx, tau = 10, 32, 0.7
+    cells = I.channel(nx, H)
+    p = ora.make_params(nx, H + 2, tau, 1.0, 0.03)
+    u_in = ora.inlet_profile(p, cells)
+    f1, *_ = ora.run(p, cells, u_in, ora.init(p, cells), 40)
+    f2, (rho, ux, uy) = ora.step_columns(p, cells, u_in, f1, 0, nx)
+    cx, cy, opp, w, cs2 = ora.lattice()
+    for y in (1, 4, H):  # wall-adjacent and interior inlet cells
+        fin = np.zeros(9)
+        for i in range(9):
+            sx, sy = 0 - cx[i], y - cy[i]
+            if sx < 0:
+                continue
+            fin[i] = f1[opp[i], y, 0] if cells[sy, sx] else f1[i, sy, sx]
+        u = u_in[y]
+        r = (fin[0] + fin[2] + fin[4] + 2 * (fin[3] + fin[6] + fin[7])) / (1 - u)
+        feq = np.array([ora.feq(i, r, u, 0.0) for i in range(9)])
+        for i in (1, 5, 8):
+            fin[i] = feq[i] + fin[opp[i]] - feq[opp[i]]
+        fneq = fin - feq
+        pxx, pyy, pxy = (cx * cx * fneq).sum(), (cy * cy * fneq).sum(), (cx * cy * fneq).sum()
+        q = (cx * cx - 1 / 3) * pxx + (cy * cy - 1 / 3) * pyy + 2 * cx * cy * pxy
+        expect = feq + (1 - 1 / tau) * 4.5 * w * q
+        assert rho[y, 0] == pytest.approx(r, rel=1e-14) and ux[y, 0] == pytest.approx(u, rel=1e-13)
+        assert np.abs(f2[:, y, 0] - expect).max() <= 1e-15
+
+
+def test_regularized_ports_stable_where_zou_he_is_not(ora):
+    """Reason for the default port scheme: at tau = 0.53 (nu = 0.01) a 64-wide
+    channel with a parabolic inlet diverges within a few hundred steps with
+    plain Zou-He ports and stays bounded with regularised ones."""
+    cells = I.channel(256, 64)
+    out = {}
+    for scheme in (ora.PORTS_REGULARIZED, ora.PORTS_ZOU_HE):
+        p = ora.make_params(256, 66, 0.53, 1.0, 0.0117, port_scheme=scheme)
+        f, rho, ux, uy, st = ora.run(p, cells, ora.inlet_profile(p, cells), ora.init(p, cells), 1200)
+        m = np.abs(rho - 1)[cells == 0].max()
+        out[scheme] = m if np.isfinite(m) else np.inf
+    assert out[ora.PORTS_REGULARIZED] < 0.05
+    assert out[ora.PORTS_ZOU_HE] > 1.0
 
 
 def test_inlet_profile_is_parabola_at_cell_centres(ora):
@@ -135,7 +186,7 @@ def test_steady_flux_constant_along_channel(ora):
     column but the last two (the constant-density outlet column pair carries a
     local O(1e-3) disturbance of the reconstruction), and equals the inlet flux."""
     H, nx = 16, 64
-    p, cells, f, rho, ux, uy = _poiseuille(ora, H, nx, 1.0, 0.01, 40000)
+    p, cells, f, rho, ux, uy = _poiseuille(ora, H, nx, 1.0, 0.01, 40000, scheme=ora.PORTS_ZOU_HE)
     m = (rho * ux).sum(axis=0)
     interior = m[:nx - 2]
     assert np.abs(interior - m[0]).max() <= 1e-4 * m[0]
@@ -173,7 +224,7 @@ def test_neumann_outlet_is_zero_gradient(ora):
     pulled from the same state."""
     H, nx = 8, 32
     cells = I.channel(nx, H)
-    p = ora.make_params(nx, H + 2, 0.8, 1.0, 0.03, ora.OUT_NEUMANN)
+    p = ora.make_params(nx, H + 2, 0.8, 1.0, 0.03, ora.OUT_NEUMANN, port_scheme=ora.PORTS_ZOU_HE)
     u_in = ora.inlet_profile(p, cells)
     f0 = ora.init(p, cells)
     f1, *_ = ora.run(p, cells, u_in, f0, 50)
