@@ -1,0 +1,204 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) library for the lattice Boltzmann
+ * shape-optimisation loop of Wang, Fan & Luo, "Lattice Boltzmann method for
+ * shape optimization of fluid distributor" (arXiv:1303.0107).
+ *
+ * The library owns every device buffer it allocates.  Caller buffers are
+ * borrowed for the duration of a call only.  Nothing is thrown across the
+ * ABI: every entry point returns an lbm_status.  A failed call leaves its
+ * handle usable unless the status is LBM_ERR_CUDA; lbm_last_error() gives a
+ * one-line description of the last failure on the calling thread.
+ *
+ * Lattice units throughout: dx = dt = 1.  x runs along the flow (0..nx-1),
+ * y across (0..ny-1); a cell is addressed as idx = y*nx + x.  Directions:
+ * 0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE.
+ *
+ * Geometry rules (checked by lbm_create_geometry, LBM_ERR_GEOMETRY otherwise):
+ *   - rows 0 and ny-1 are solid (the frame);
+ *   - inlet cells are the fluid cells of column 0, outlet cells those of
+ *     column nx-1; each fluid cell (0,y) has a fluid (1,y) and each fluid
+ *     (nx-1,y) a fluid (nx-2,y);
+ *   - at least one inlet and one outlet cell, at most LBM_MAX_OUTLETS outlet
+ *     runs; nx even, 4 <= nx, 3 <= ny, nx*ny < 2^31.
+ * The optimiser never changes columns 0, 1, nx-2, nx-1 nor rows 0, ny-1.
+ *
+ * Threading: a handle is used by one host thread at a time.  All device work
+ * of a handle runs on the stream given at creation (or a stream the library
+ * creates when none is given); every entry point returns after that work is
+ * complete unless stated otherwise.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_MAX_OUTLETS 64
+
+typedef struct lbm_handle_s* lbm_handle;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,       /* invalid argument (null pointer, bad size, odd step count, ...) */
+  LBM_ERR_GEOMETRY = 2,  /* cell map violates the geometry rules above */
+  LBM_ERR_OOM = 3,       /* device or pinned host allocation failed */
+  LBM_ERR_CUDA = 4,      /* a CUDA call failed; the handle must be destroyed */
+  LBM_ERR_DIVERGED = 5,  /* a reduction or a score is not finite */
+  LBM_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+  LBM_ERR_BUSY = 7       /* resource temporarily unavailable (admission refused) */
+} lbm_status;
+
+typedef enum {
+  LBM_F32 = 0,          /* populations stored as FP32, shifted: g_i = f_i - w_i rho0 */
+  LBM_BF16_SHIFTED = 1, /* stored as BF16, shifted; FP32 collision arithmetic */
+  LBM_F16_SHIFTED = 2   /* stored as FP16, shifted; FP32 collision arithmetic */
+} lbm_precision;
+
+typedef enum {
+  LBM_OUT_CONST_RHO = 0, /* outlet density fixed at rho0 (see lbm_port_scheme) */
+  LBM_OUT_NEUMANN = 1    /* zero-gradient outlet (Sec. 3.3): unknown f3,f6,f7 copied
+                            from the streamed populations of cell (nx-2, y) */
+} lbm_outlet_rule;
+
+typedef enum {
+  LBM_PORTS_REGULARIZED = 0, /* velocity inlet / constant-density outlet: the Zou-He
+                                density and velocity, non-equilibrium bounce-back for
+                                the unknown populations, then the port cell is
+                                regularised (f^eq + projected non-equilibrium stress);
+                                stable for tau close to 1/2 */
+  LBM_PORTS_ZOU_HE = 1       /* plain Zou-He reconstruction of the unknown populations */
+} lbm_port_scheme;
+
+typedef enum {
+  LBM_REINIT_WARM = 0, /* after an exchange only new fluid cells restart at f^eq(rho0, 0) */
+  LBM_REINIT_COLD = 1  /* after an exchange every fluid cell restarts at f^eq(rho0, 0) */
+} lbm_reinit;
+
+typedef struct {
+  int32_t nx, ny;         /* lattice size */
+  double tau;             /* BGK relaxation time of Eq. 1 (> 1/2); nu = (tau - 1/2)/3 */
+  double rho0;            /* reference density: initial state, outlet density */
+  double u_max;           /* centre-line speed of the parabolic inlet profile */
+  int32_t outlet;         /* lbm_outlet_rule */
+  int32_t precision;      /* lbm_precision */
+  int32_t reinit;         /* lbm_reinit */
+  int32_t residual_every; /* K: the residual compares u at the last step with u
+                             K steps earlier; even, >= 2 (0 disables it) */
+  int32_t ports;          /* lbm_port_scheme */
+  int32_t reserved;       /* must be 0 */
+} lbm_params;
+
+typedef struct {
+  double dp;        /* pressure drop: mean p = rho/3 (Eq. 4) over inlet cells minus
+                       the mean over all outlet cells (Sec. 2.3 step 5) */
+  double m_in;      /* sum of rho u_x over the inlet cells (per unit depth) */
+  double residual;  /* sum |u(T) - u(T-K)|_1 / sum |u(T)|_1 over fluid cells; -1 if not computed */
+  int32_t n_outlets;
+  int32_t reserved;
+  double m_out[LBM_MAX_OUTLETS]; /* sum of rho u_x over the cells of each outlet, runs
+                                    numbered from y = 0 upward */
+  double theta;     /* Eq. 9: max m_out / min m_out */
+  double dg;        /* Eq. 10-11: maldistribution factor of m_out */
+  int64_t steps_done;  /* total time steps taken by this handle */
+  int64_t fluid_cells; /* current number of fluid cells */
+} lbm_solve_result;
+
+typedef struct {
+  int32_t n_swapped;   /* number of fluid->solid (= solid->fluid) exchanges made */
+  int32_t reserved;
+  int64_t fluid_count; /* fluid cells after the exchange (always equal to before) */
+  lbm_solve_result solve;
+} lbm_opt_result;
+
+/* field selectors for lbm_read_fields / lbm_load_state (one per call) */
+#define LBM_FIELD_RHO 1u  /* float[ny][nx]: rho of the last step (0 on solid cells) */
+#define LBM_FIELD_UX 2u   /* float[ny][nx]: u_x of the last step (0 on solid cells) */
+#define LBM_FIELD_UY 4u   /* float[ny][nx]: u_y of the last step (0 on solid cells) */
+#define LBM_FIELD_MASK 8u /* uint8[ny][nx]: current cell types, 1 = solid, 0 = fluid */
+#define LBM_FIELD_POPS 16u /* storage type [9][ny][nx]: post-collision populations in
+                              stored (shifted) form g_i = f_i - w_i rho0; FP32 for
+                              LBM_F32, BF16 / FP16 bit patterns otherwise */
+#define LBM_FIELD_DRHO 32u /* float[ny][nx]: rho - rho0 of the last step */
+
+/* Sec. 2.3 step 1 and Sec. 3.3: create a lattice from a cell map.
+ * params      host pointer, copied.
+ * cell_types  host uint8[ny][nx] row-major, 1 = solid, 0 = fluid; copied.
+ * cuda_stream cudaStream_t to run on, or NULL for a library-owned stream.
+ * out         receives the handle (NULL on failure).
+ * The state starts at the equilibrium of rho0 at rest (Sec. 3.3).        */
+lbm_status lbm_create_geometry(const lbm_params* params, const uint8_t* cell_types, void* cuda_stream,
+                               lbm_handle* out);
+
+/* Sec. 2.3 step 2, Eq. 1-2: advance n_steps time steps of the fused
+ * stream-collide update (bounce-back walls, inlet and outlet rules of Sec. 3.3),
+ * then reduce the pressure drop, flow rates and residual in FP64.
+ * n_steps must be even and >= 2 (steps run as pairs of the single-lattice
+ * scheme).  out: host pointer, caller-owned.                             */
+lbm_status lbm_solve(lbm_handle h, int64_t n_steps, lbm_solve_result* out);
+
+/* Sec. 2.2 (Eq. 5, Eq. 6) and Sec. 2.3 steps 3-4: from the field of the last
+ * solve, exchange n = min(n_swap, interface fluid cells, interface solid
+ * cells) fluid cells of lowest dynamic pressure with the n solid cells of
+ * largest viscous stress, re-initialise (params.reinit), then solve n_steps.
+ * Requires a previous lbm_solve on this handle.  out: host, caller-owned.  */
+lbm_status lbm_optimize_step(lbm_handle h, int32_t n_swap, int64_t n_steps, lbm_opt_result* out);
+
+/* Copy one field (a single LBM_FIELD_* bit) into dst.
+ * dst_bytes must be at least the field's size; dst_is_device != 0 means dst
+ * is device memory of the handle's device (written on the handle's stream).  */
+lbm_status lbm_read_fields(lbm_handle h, uint32_t which, void* dst, size_t dst_bytes, int dst_is_device);
+
+/* Restore the populations (LBM_FIELD_POPS layout) saved by lbm_read_fields,
+ * for checkpoint/resume on a handle with the same cell map.             */
+lbm_status lbm_load_state(lbm_handle h, const void* pops, size_t bytes, int src_is_device);
+
+/* Put the handle back to its creation state: initial cell map, equilibrium
+ * populations, steps_done = 0.  No allocation.                          */
+lbm_status lbm_reset(lbm_handle h);
+
+/* Test hook for the selection of Sec. 2.3 step 3 on a supplied field: scores
+ * (Eq. 5, Eq. 6, FP64, no fused multiply-add) and the deterministic choice,
+ * fluid cells by (q ascending, idx ascending), solid cells by (sigma
+ * descending, idx ascending), on the handle's current cell map.
+ * drho, ux, uy: host float[ny][nx], rho = rho0 + drho.  fluid_idx_out and
+ * solid_idx_out: host int32[n_swap], receive the chosen cell indices sorted
+ * ascending; n_out receives n.  The handle's state is not changed.       */
+lbm_status lbm_select_swaps(lbm_handle h, const float* drho, const float* ux, const float* uy,
+                            int32_t n_swap, int32_t* fluid_idx_out, int32_t* solid_idx_out,
+                            int32_t* n_out);
+
+/* Release every resource of the handle.  NULL is accepted.              */
+void lbm_destroy(lbm_handle h);
+
+/* Static description of a status code.                                  */
+const char* lbm_status_str(lbm_status s);
+
+/* Description of the last failure on the calling thread ("" if none).   */
+const char* lbm_last_error(void);
+
+/* Number of device kernels this process has launched through the library
+ * (graph launches count every kernel node).                             */
+uint64_t lbm_kernel_launches(void);
+
+/* Device time of the stream-collide kernels of this handle, measured with CUDA
+ * events on the handle's stream around each solve's sequence of time steps
+ * (the FP64 reductions and the exchange are outside it).  ms, launches and
+ * fluid_updates (fluid cells x steps) are accumulated since creation or since
+ * the last call with reset != 0; any output pointer may be NULL.          */
+lbm_status lbm_kernel_time(lbm_handle h, int reset, double* ms, int64_t* launches,
+                           int64_t* fluid_updates);
+
+/* Algorithmic memory traffic of one fluid-cell update of the stream-collide
+ * kernel for a storage precision: 9 populations read and 9 written
+ * (2 * 9 * sizeof(stored population)) plus the cell's mask bit (1/8 byte).  */
+double lbm_bytes_per_fluid_update(int32_t precision);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

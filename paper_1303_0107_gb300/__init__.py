@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) implementation of the lattice Boltzmann shape-optimisation
+hot path of Wang, Fan & Luo (arXiv:1303.0107): fused D2Q9 BGK stream-collide
+with bounce-back and port rules, FP64 pressure-drop / flow-rate reductions,
+and the equal-count fluid/solid exchange of the optimality criterion.
+
+The computation lives in the CUDA library built from csrc/ (C ABI in
+include/lbm.h); `lib` is its ctypes binding, `inputs` the seeded synthetic
+workloads.
+"""
+from . import inputs  # noqa: F401
+from .lib import (F32, BF16_SHIFTED, F16_SHIFTED, OUT_CONST_RHO, OUT_NEUMANN, REINIT_WARM,  # noqa: F401
+                  PORTS_REGULARIZED, PORTS_ZOU_HE,
+                  REINIT_COLD, FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_MASK, FIELD_POPS, FIELD_DRHO,
+                  Lattice, LbmError, bytes_per_fluid_update, kernel_launches, load_library)

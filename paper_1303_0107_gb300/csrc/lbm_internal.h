@@ -1,0 +1,149 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Not part of the public ABI (include/lbm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "lbm.h"
+
+namespace lbm {
+
+// A tile is 32 consecutive cells of one row word (one mask word) times kTileY
+// rows; a thread block of kTileY warps processes one tile at a time, warp r
+// handling row y0 + r, lane l handling cell x0 + l.
+constexpr int kTileY = 8;
+constexpr int kStepThreads = 32 * kTileY;
+// Row pitch of every per-cell array, in elements: a multiple of 64 so that
+// each row starts on a 128-byte boundary for 16-bit and 32-bit storage.
+constexpr int kPitchAlign = 64;
+
+// Everything a kernel needs to know about one lattice.  Stored in device
+// memory (one entry per lattice of a batch) and read by each block.  Entries
+// are 16-byte aligned and a multiple of 16 bytes long, so that any entry of a
+// table can be read with 16-byte loads.
+// Cell mask layout: one bit per cell, bit (x & 31) of word x >> 5 of a row,
+// set = solid.  Rows are stored with a stride of wpr + 2 words and one solid
+// padding word on each side, plus one solid padding row above row 0 and one
+// below row ny-1; the mask pointer addresses word 0 of row 0.  Every
+// neighbour word a kernel forms (rows y-1..y+1, words w-1..w+1) therefore lies
+// inside the allocation and reads as wall outside the lattice.
+__host__ __device__ constexpr int mask_stride(int wpr) { return wpr + 2; }
+__host__ __device__ constexpr long long mask_alloc_words(int wpr, int ny) {
+  return (long long)(ny + 2) * mask_stride(wpr);
+}
+__host__ __device__ constexpr long long mask_origin(int wpr) { return mask_stride(wpr) + 1; }
+
+struct alignas(16) LatticeView {
+  void* f;               // 9 population planes [9][ny][pitch] of the storage type
+  const uint32_t* mask;  // word (0, 0) of the padded mask (see above)
+  float* drho;           // [ny][pitch] rho - rho0 of the last step (moment steps only)
+  float* ux;             // [ny][pitch]
+  float* uy;             // [ny][pitch]
+  const float* u_in;     // [ny] inlet u_x per row (0 where the row has no inlet cell)
+  long long plane;       // elements per population plane = ny * pitch
+  int nx, ny, pitch, wpr;
+  float omega;           // 1 / tau
+  float rho0;
+  int outlet_rule;       // lbm_outlet_rule
+  int port_scheme;       // lbm_port_scheme
+  long long f_elems;     // 9 * plane (extent of f)
+};
+
+struct alignas(16) TileRef {
+  int lattice;  // index into the LatticeView table
+  int x0;       // first column (multiple of 32)
+  int y0;       // first row (multiple of kTileY)
+  int reserved;
+};
+static_assert(sizeof(LatticeView) % 16 == 0 && alignof(LatticeView) == 16, "LatticeView layout");
+static_assert(sizeof(TileRef) == 16 && alignof(TileRef) == 16, "TileRef layout");
+
+// ---- stream-collide (step.cu) ----------------------------------------------
+// phase 0 ("A"): reads the post-collision state from the neighbours, writes
+//   the new post-collision values into the slots the neighbours will read
+//   (or back into the cell's own slots where the neighbour is solid);
+// phase 1 ("B"): reads and writes the cell's own slots only, leaving the
+//   canonical layout F[i][cell] = post-collision population i.
+// moments != 0 writes drho/ux/uy of the view (phase B only).
+cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
+                                  const TileRef* tiles, const int* n_tiles, int grid,
+                                  cudaStream_t stream);
+int stream_collide_blocks_per_sm(int precision, int phase, int moments);
+
+// ---- geometry / work-list (worklist.cu) ------------------------------------
+cudaError_t launch_pack_mask(const uint8_t* cells, int nx, int ny, int wpr, uint32_t* mask,
+                             cudaStream_t stream);
+cudaError_t launch_unpack_mask(const uint32_t* mask, int nx, int ny, int wpr, uint8_t* cells,
+                               cudaStream_t stream);
+// Tile list of one lattice: tiles whose words hold at least one fluid cell,
+// in ascending (y0, x0) order, tagged with `lattice`.  scratch holds
+// 2 * ceil(ny / kTileY) * wpr + 1 ints.
+cudaError_t launch_build_tiles(const uint32_t* mask, int nx, int ny, int wpr, int lattice,
+                               int* scratch, TileRef* tiles, int* n_tiles, cudaStream_t stream);
+cudaError_t launch_count_fluid(const uint32_t* mask, int nx, int ny, int wpr,
+                               unsigned long long* count, cudaStream_t stream);
+// exclusive scan of n ints in one block; out[n] = total
+cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t stream);
+cudaError_t launch_rho_from_drho(const float* drho, float rho0, const uint32_t* mask, int nx, int ny,
+                                 int pitch, int wpr, float* rho_dense, cudaStream_t stream);
+
+// ---- reductions (reduce.cu) -------------------------------------------------
+constexpr int kResidualBlocks = 128;
+// per-lattice results written by launch_finalize, doubles:
+//   [0] dp, [1] m_in, [2] residual (or -1), [3] n_in, [4] n_out,
+//   [5] sum |du|, [6] sum |u|, [7] nonfinite flag, [8] theta, [9] D_g,
+//   [10 .. 10+n_out) m_out
+constexpr int kResultDoubles = 10 + LBM_MAX_OUTLETS;
+cudaError_t launch_residual_partials(const LatticeView* views, const float* ux_prev,
+                                     const float* uy_prev, int lattice, double* partials,
+                                     cudaStream_t stream);
+cudaError_t launch_finalize(const LatticeView* views, int lattice, const int* outlet_start,
+                            const int* outlet_len, int n_outlets, const double* partials,
+                            int with_residual, double* result, cudaStream_t stream);
+
+// ---- optimality criterion (oc.cu) -------------------------------------------
+struct OcScratch {
+  int* cnt_f;            // [nwords]
+  int* cnt_s;            // [nwords]
+  int* off_f;            // [nwords + 1]
+  int* off_s;            // [nwords + 1]
+  unsigned long long* key_f;  // [ncells]
+  unsigned long long* key_s;  // [ncells]
+  int* idx_f;            // [ncells]
+  int* idx_s;            // [ncells]
+  int* sel_f;            // [cap]
+  int* sel_s;            // [cap]
+  int* info;             // [8]: n_swapped, nF, nS, error flag, ...
+  int cap;               // capacity of sel_* (max n_swap)
+};
+cudaError_t launch_oc_select(const LatticeView* view_host, const LatticeView* view_dev,
+                             double rho0, double mu, int n_swap, const OcScratch& s,
+                             cudaStream_t stream);
+cudaError_t launch_oc_apply(int precision, const LatticeView* view_dev, uint32_t* mask,
+                            const OcScratch& s, cudaStream_t stream);
+
+// ---- counters / debugging ----------------------------------------------------
+void count_launches(uint64_t n);
+// LBM_DEBUG_SYNC=1 in the environment: no graphs, synchronise after every
+// launch and name the kernel that failed.
+bool debug_sync();
+
+#ifdef LBM_CHECK_BOUNDS
+// Bounds-checked builds: every global access of the step and reduction
+// kernels is checked against its allocation; a violation is printed (first
+// few only) and the access skipped.
+__device__ __forceinline__ bool lbm_in_bounds(long long i, long long n, int line) {
+  if (i >= 0 && i < n) return true;
+  printf("lbm bounds: line %d index %lld extent %lld block %d thread %d\n", line, i, n, blockIdx.x,
+         threadIdx.x);
+  return false;
+}
+#define LBM_OK_IDX(i, n) lbm_in_bounds((long long)(i), (long long)(n), __LINE__)
+#else
+#define LBM_OK_IDX(i, n) true
+#endif
+
+}  // namespace lbm

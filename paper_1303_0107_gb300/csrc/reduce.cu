@@ -1,0 +1,162 @@
+// FP64 reductions of a solved field: pressure drop, inlet and outlet flow
+// rates (Sec. 2.3 step 5; Eq. 9-11 inputs) and the convergence residual.
+//
+// All sums are accumulated in double from the FP32 moments of the last step
+// and are deterministic: every thread owns a fixed set of cells, block sums
+// use a fixed tree, and partial sums are combined in ascending block order.
+// No floating-point atomics.
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr int kRedThreads = 256;
+
+// Fixed-shape tree sum over a block of kRedThreads doubles held in smem.
+__device__ double block_sum(double v, double* sm) {
+  const int tid = threadIdx.x;
+  sm[tid] = v;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (tid < s) sm[tid] += sm[tid + s];
+    __syncthreads();
+  }
+  const double r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+// Residual partials: block b covers rows [b*ny/B, (b+1)*ny/B) of one lattice.
+// partials[2b] = sum |u - u_prev|_1, partials[2b+1] = sum |u|_1 (solid cells
+// hold zeros in both fields and add nothing).
+__global__ void __launch_bounds__(kRedThreads)
+    k_residual_partials(const LatticeView* __restrict__ views, int lattice,
+                        const float* __restrict__ ux_prev, const float* __restrict__ uy_prev,
+                        double* __restrict__ partials) {
+  __shared__ double sm[kRedThreads];
+  const LatticeView* L = views + lattice;
+  const int nx = L->nx, ny = L->ny, pitch = L->pitch;
+  const int b = blockIdx.x;
+  const int y0 = (int)((long long)b * ny / kResidualBlocks);
+  const int y1 = (int)((long long)(b + 1) * ny / kResidualBlocks);
+  const long long n = (long long)(y1 - y0) * nx;
+  double du = 0.0, u = 0.0;
+  for (long long k = threadIdx.x; k < n; k += kRedThreads) {
+    const int y = y0 + (int)(k / nx), x = (int)(k % nx);
+    const long long c = (long long)y * pitch + x;
+    if (!LBM_OK_IDX(c, L->plane)) continue;
+    const double ux = L->ux[c], uy = L->uy[c];
+    du += fabs(ux - (double)ux_prev[c]) + fabs(uy - (double)uy_prev[c]);
+    u += fabs(ux) + fabs(uy);
+  }
+  du = block_sum(du, sm);
+  u = block_sum(u, sm);
+  if (threadIdx.x == 0) {
+    partials[2 * b] = du;
+    partials[2 * b + 1] = u;
+  }
+}
+
+// One block per lattice: port sums and the final combination.
+__global__ void __launch_bounds__(kRedThreads)
+    k_finalize(const LatticeView* __restrict__ views, int lattice, const int* __restrict__ outlet_start,
+               const int* __restrict__ outlet_len, int n_outlets, const double* __restrict__ partials,
+               int with_residual, double* __restrict__ result) {
+  __shared__ double sm[kRedThreads];
+  const LatticeView* L = views + lattice;
+  const int nx = L->nx, ny = L->ny, pitch = L->pitch, wpr = L->wpr;
+  const double rho0 = L->rho0;
+  const int wl = (nx - 1) >> 5, bl = (nx - 1) & 31;
+  double s_in = 0.0, s_out = 0.0, m_in = 0.0, n_in = 0.0, n_out = 0.0;
+  for (int y = threadIdx.x; y < ny; y += kRedThreads) {
+    const uint32_t* mr = L->mask + (long long)y * mask_stride(wpr);
+    const long long c0 = (long long)y * pitch;
+    if (!LBM_OK_IDX(c0 + nx - 1, L->plane)) continue;
+    if (!(mr[0] & 1u)) {
+      const double d = L->drho[c0];
+      s_in += d;
+      m_in += (rho0 + d) * (double)L->ux[c0];
+      n_in += 1.0;
+    }
+    if (!((mr[wl] >> bl) & 1u)) {
+      s_out += L->drho[c0 + nx - 1];
+      n_out += 1.0;
+    }
+  }
+  s_in = block_sum(s_in, sm);
+  s_out = block_sum(s_out, sm);
+  m_in = block_sum(m_in, sm);
+  n_in = block_sum(n_in, sm);
+  n_out = block_sum(n_out, sm);
+  // each outlet run summed by one thread in ascending row order
+  for (int j = threadIdx.x; j < n_outlets; j += kRedThreads) {
+    double m = 0.0;
+    const int ya = outlet_start[j], yb = ya + outlet_len[j];
+    for (int y = ya; y < yb; ++y) {
+      const long long c = (long long)y * pitch + nx - 1;
+      if (!LBM_OK_IDX(c, L->plane)) continue;
+      m += (rho0 + (double)L->drho[c]) * (double)L->ux[c];
+    }
+    result[10 + j] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // Eq. 9-11: theta = m_max / m_min, D_g = sqrt(sum (m_j / m_ave - 1)^2 / (N - 1))
+    const double* m = result + 10;
+    double mx = m[0], mn = m[0], sum = 0.0;
+    for (int j = 0; j < n_outlets; ++j) {
+      mx = m[j] > mx ? m[j] : mx;
+      mn = m[j] < mn ? m[j] : mn;
+      sum += m[j];
+    }
+    const double ave = sum / n_outlets;
+    double acc = 0.0;
+    for (int j = 0; j < n_outlets; ++j) {
+      const double d = m[j] / ave - 1.0;
+      acc += d * d;
+    }
+    result[8] = mx / mn;
+    result[9] = n_outlets > 1 ? sqrt(acc / (n_outlets - 1)) : 0.0;
+    // p = rho c_s^2 = rho / 3 (Eq. 4); the rho0/3 parts cancel in the difference
+    const double dp = (s_in / n_in - s_out / n_out) / 3.0;
+    double res = -1.0, sdu = 0.0, su = 0.0;
+    if (with_residual) {
+      for (int b = 0; b < kResidualBlocks; ++b) {
+        sdu += partials[2 * b];
+        su += partials[2 * b + 1];
+      }
+      res = sdu / su;
+    }
+    result[0] = dp;
+    result[1] = m_in;
+    result[2] = res;
+    result[3] = n_in;
+    result[4] = n_out;
+    result[5] = sdu;
+    result[6] = su;
+    const bool bad = !isfinite(dp) || !isfinite(m_in) || (with_residual && !isfinite(res));
+    result[7] = bad ? 1.0 : 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_residual_partials(const LatticeView* views, const float* ux_prev,
+                                     const float* uy_prev, int lattice, double* partials,
+                                     cudaStream_t stream) {
+  k_residual_partials<<<kResidualBlocks, kRedThreads, 0, stream>>>(views, lattice, ux_prev, uy_prev,
+                                                                   partials);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const LatticeView* views, int lattice, const int* outlet_start,
+                            const int* outlet_len, int n_outlets, const double* partials,
+                            int with_residual, double* result, cudaStream_t stream) {
+  k_finalize<<<1, kRedThreads, 0, stream>>>(views, lattice, outlet_start, outlet_len, n_outlets,
+                                            partials, with_residual, result);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

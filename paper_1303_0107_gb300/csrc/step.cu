@@ -1,0 +1,392 @@
+// Fused D2Q9 stream + collide on a single lattice (AA access pattern).
+//
+// Method: lattice BGK update of Eq. 1 with the second-order equilibrium of
+// Sec. 2.1 and the moments of Eq. 2; halfway bounce-back on solid cells, the
+// parabolic velocity inlet, and the constant-density or zero-gradient outlet
+// of Sec. 3.3 (ports regularised or plain Zou-He) -- all fused into one pass
+// per time step.
+//
+// Storage.  Populations are kept shifted, g_i = f_i - w_i rho0, in nine planes
+// F[i][y][x] (row pitch `pitch`), as FP32, BF16 or FP16; arithmetic is FP32.
+// The canonical layout between steps is F[i][cell] = post-collision g_i of
+// that cell.  Steps come in pairs:
+//   phase A  cell x pulls g_i from F[i][x - c_i] (or, where x - c_i is solid,
+//            the reversed F[opp(i)][x]: bounce-back), relaxes, and writes each
+//            outgoing g_i into F[opp(i)][x + c_i] -- the very slot it read for
+//            direction opp(i) -- or, where x + c_i is solid, into F[i][x];
+//   phase B  cell x finds its incoming g_i in F[opp(i)][x], relaxes, and
+//            writes g_i back to F[i][x]: the canonical layout again.
+// Each slot is read and then written by exactly one thread per phase, so the
+// pair needs one lattice and no barrier.  Solid cells are never read.
+//
+// Thread mapping.  A block of kTileY warps owns a 32 x kTileY tile; warp r
+// handles row y0 + r, lane l cell x0 + l, so every plane access of a warp is
+// one contiguous 32-element row segment (shifted by at most one element).
+// Blocks stride over a device-resident tile list that holds only tiles with
+// fluid cells; warps whose row segment is all solid skip at once.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+template <class T>
+struct Pop;
+template <>
+struct Pop<float> {
+  static __device__ __forceinline__ float ld(const float* p) { return *p; }
+  static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <>
+struct Pop<__nv_bfloat16> {
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <>
+struct Pop<__half> {
+  static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+  static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+
+constexpr float kW0 = 4.0f / 9.0f;
+constexpr float kW1 = 1.0f / 9.0f;
+constexpr float kW5 = 1.0f / 36.0f;
+
+// Relax a pair of opposite directions (c_o = -c_i) towards the shifted
+// equilibrium  g^eq_i = w (t0 + 3 rho cu + 4.5 rho cu^2),  t0 = drho - 1.5 rho u.u,
+// which is f^eq_i(rho, u) - w rho0 written out.
+__device__ __forceinline__ void relax_pair(float& gi, float& go, float cu, float w, float rho,
+                                           float t0, float omega) {
+  const float a = 3.0f * rho * cu;
+  const float b = 4.5f * rho * cu * cu;
+  const float ei = w * (t0 + a + b);
+  const float eo = w * (t0 - a + b);
+  gi += omega * (ei - gi);
+  go += omega * (eo - go);
+}
+
+// Moments (Eq. 2) and BGK relaxation (Eq. 1) of one cell, in place.
+__device__ __forceinline__ void bgk(float (&g)[9], float rho0, float omega, float& drho, float& ux,
+                                    float& uy) {
+  drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+  const float rho = rho0 + drho;
+  const float jx = (g[1] - g[3]) + (g[5] - g[7]) + (g[8] - g[6]);
+  const float jy = (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
+  const float inv = 1.0f / rho;
+  ux = jx * inv;
+  uy = jy * inv;
+  const float t0 = drho - 1.5f * rho * (ux * ux + uy * uy);
+  relax_pair(g[1], g[3], ux, kW1, rho, t0, omega);
+  relax_pair(g[2], g[4], uy, kW1, rho, t0, omega);
+  relax_pair(g[5], g[7], ux + uy, kW5, rho, t0, omega);
+  relax_pair(g[8], g[6], ux - uy, kW5, rho, t0, omega);
+  // BGK conserves mass and momentum; rounded FP32 relaxation does not quite,
+  // and the drift dominates the FP32 error over thousands of steps.  Close
+  // both exactly: g1 and g2 carry the momentum balance, the rest population
+  // the mass balance (an identity in exact arithmetic).
+  g[1] = jx + g[3] - ((g[5] - g[7]) + (g[8] - g[6]));
+  g[2] = jy + g[4] - ((g[5] - g[7]) + (g[6] - g[8]));
+  g[0] = drho - (((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
+}
+
+// Shifted equilibria of all nine directions for (rho0 + drho, ux, uy).
+__device__ __forceinline__ void shifted_equilibria(float (&e)[9], float rho0, float drho, float ux,
+                                                   float uy) {
+  const float rho = rho0 + drho;
+  const float t0 = drho - 1.5f * rho * (ux * ux + uy * uy);
+  e[0] = kW0 * t0;
+  const float cu[4] = {ux, uy, ux + uy, ux - uy};  // directions 1, 2, 5, 8 (opposites 3, 4, 7, 6)
+  const int di[4] = {1, 2, 5, 8}, dopp[4] = {3, 4, 7, 6};
+  const float wt[4] = {kW1, kW1, kW5, kW5};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float a = 3.0f * rho * cu[k], b = 4.5f * rho * cu[k] * cu[k];
+    e[di[k]] = wt[k] * (t0 + a + b);
+    e[dopp[k]] = wt[k] * (t0 - a + b);
+  }
+}
+
+// Regularised port cell: given the cell's (drho, u) and its populations with
+// the unknown ones already filled, replace all nine by
+//   g_i = g^eq_i + w_i / (2 c_s^4) Q_i : Pi,   Pi = sum_i c_i c_i (g_i - g^eq_i),
+// Q_i = c_i c_i - I/3.  With c_s^2 = 1/3 the coefficients 4.5 w_i Q_i are
+//   rest: -(2/3)(Pxx + Pyy); axis x: Pxx/3 - Pyy/6; axis y: Pyy/3 - Pxx/6;
+//   diagonals NE/SW: (Pxx + Pyy)/12 + Pxy/4; NW/SE: (Pxx + Pyy)/12 - Pxy/4.
+__device__ __forceinline__ void regularize(float (&g)[9], const float (&e)[9]) {
+  float n[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) n[i] = g[i] - e[i];
+  const float dsum = (n[5] + n[6]) + (n[7] + n[8]);
+  const float pxx = (n[1] + n[3]) + dsum;
+  const float pyy = (n[2] + n[4]) + dsum;
+  const float pxy = (n[5] + n[7]) - (n[6] + n[8]);
+  const float tr = pxx + pyy;
+  g[0] = e[0] - (2.0f / 3.0f) * tr;
+  const float ax = pxx * (1.0f / 3.0f) - pyy * (1.0f / 6.0f);
+  const float ay = pyy * (1.0f / 3.0f) - pxx * (1.0f / 6.0f);
+  g[1] = e[1] + ax;
+  g[3] = e[3] + ax;
+  g[2] = e[2] + ay;
+  g[4] = e[4] + ay;
+  const float dp = tr * (1.0f / 12.0f) + 0.25f * pxy, dm = tr * (1.0f / 12.0f) - 0.25f * pxy;
+  g[5] = e[5] + dp;
+  g[7] = e[7] + dp;
+  g[6] = e[6] + dm;
+  g[8] = e[8] + dm;
+}
+
+// Inlet (x = 0), imposed velocity (u, 0).  Density from mass and x-momentum of
+// the known populations, rho = (f0 + f2 + f4 + 2 (f3 + f6 + f7)) / (1 - u), in
+// shifted form drho = (s + rho0 u) / (1 - u).  Zou-He rebuilds f1, f5, f8:
+//   f1 = f3 + 2/3 rho u,  f5 = f7 - (f2 - f4)/2 + rho u / 6,
+//   f8 = f6 + (f2 - f4)/2 + rho u / 6;
+// the regularised scheme takes their non-equilibrium parts from the opposite
+// directions and then regularises the cell.
+__device__ __forceinline__ void inlet_rule(float (&g)[9], float u, float rho0, int scheme) {
+  const float s = (g[0] + g[2] + g[4]) + 2.0f * (g[3] + g[6] + g[7]);
+  const float drho = (s + rho0 * u) / (1.0f - u);
+  if (scheme == LBM_PORTS_ZOU_HE) {
+    const float ru = (rho0 + drho) * u;
+    const float d = 0.5f * (g[2] - g[4]);
+    g[1] = g[3] + (2.0f / 3.0f) * ru;
+    g[5] = g[7] - d + (1.0f / 6.0f) * ru;
+    g[8] = g[6] + d + (1.0f / 6.0f) * ru;
+  } else {
+    float e[9];
+    shifted_equilibria(e, rho0, drho, u, 0.0f);
+    g[1] = e[1] + (g[3] - e[3]);
+    g[5] = e[5] + (g[7] - e[7]);
+    g[8] = e[8] + (g[6] - e[6]);
+    regularize(g, e);
+  }
+}
+
+// Outlet (x = nx-1) at density rho0: u = -1 + (f0 + f2 + f4 + 2 (f1 + f5 + f8)) / rho0,
+// i.e. rho0 u = s in shifted form.  Zou-He rebuilds f3, f6, f7 (mirror of the
+// inlet); the regularised scheme as at the inlet.
+__device__ __forceinline__ void outlet_rule(float (&g)[9], float rho0, int scheme) {
+  const float ru = (g[0] + g[2] + g[4]) + 2.0f * (g[1] + g[5] + g[8]);
+  if (scheme == LBM_PORTS_ZOU_HE) {
+    const float d = 0.5f * (g[2] - g[4]);
+    g[3] = g[1] - (2.0f / 3.0f) * ru;
+    g[7] = g[5] + d - (1.0f / 6.0f) * ru;
+    g[6] = g[8] - d - (1.0f / 6.0f) * ru;
+  } else {
+    float e[9];
+    shifted_equilibria(e, rho0, 0.0f, ru / rho0, 0.0f);
+    g[3] = e[3] + (g[1] - e[1]);
+    g[7] = e[7] + (g[5] - e[5]);
+    g[6] = e[6] + (g[8] - e[8]);
+    regularize(g, e);
+  }
+}
+
+// population access with optional bounds checks (offset in elements from F)
+#define FLD(off) (LBM_OK_IDX((off), fe) ? P::ld(F + (off)) : 0.0f)
+#define FST(off, v)                                \
+  do {                                             \
+    if (LBM_OK_IDX((off), fe)) P::st(F + (off), (v)); \
+  } while (0)
+
+template <class T, int PHASE, bool MOMENTS>
+__global__ void __launch_bounds__(kStepThreads, 3)
+    k_stream_collide(const LatticeView* __restrict__ views, const TileRef* __restrict__ tiles,
+                     const int* __restrict__ n_tiles) {
+  using P = Pop<T>;
+  const int lane = threadIdx.x & 31;
+  const int row = threadIdx.x >> 5;
+  const int nt = *n_tiles;
+#ifdef LBM_CHECK_BOUNDS
+  {
+    const long long cap = (long long)((views->ny + kTileY - 1) / kTileY) * views->wpr;
+    if (nt < 0 || nt > cap) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) printf("lbm bounds: tile count %d outside [0, %lld]\n", nt, cap);
+      return;
+    }
+  }
+#endif
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const TileRef tr = tiles[t];
+    const LatticeView* __restrict__ L = views + tr.lattice;
+    const int ny = L->ny;
+#ifdef LBM_CHECK_BOUNDS
+    if (tr.lattice != 0 || tr.x0 < 0 || tr.x0 >= L->wpr * 32 || tr.y0 < 0 || tr.y0 >= ny) {
+      if (threadIdx.x == 0)
+        printf("lbm bounds: bad tile %d of %d: lattice %d x0 %d y0 %d\n", t, nt, tr.lattice, tr.x0, tr.y0);
+      continue;
+    }
+#endif
+    const int y = tr.y0 + row;
+    if (y < 1 || y > ny - 2) continue;  // frame rows hold no fluid
+    const int ms = mask_stride(L->wpr);
+    const int w = tr.x0 >> 5;
+    const uint32_t* mr = L->mask + (long long)y * ms;
+    const uint32_t mc = mr[w];
+    if (mc == 0xffffffffu) continue;  // whole row segment solid (warp-uniform)
+
+    const int nx = L->nx;
+    const int x = tr.x0 + lane;
+    const int pitch = L->pitch;
+    const long long pl = L->plane;
+    const float rho0 = L->rho0;
+    const float omega = L->omega;
+    const int rule = L->outlet_rule;
+    T* __restrict__ F = static_cast<T*>(L->f);
+    const long long fe = L->f_elems;
+    (void)fe;
+    const long long c = (long long)y * pitch + x;
+    const bool fluid = !((mc >> lane) & 1u);  // bits beyond nx are set (solid)
+    const bool inlet = (x == 0);
+    const bool outlet = (x == nx - 1);
+
+    float g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = 0.0f;
+
+    // solid flags of the 8 neighbours (only phase A needs them)
+    bool sE = false, sN = false, sW = false, sS = false, sNE = false, sNW = false, sSW = false,
+         sSE = false;
+    if (PHASE == 0) {
+      // padded mask: words w-1 and w+1 of rows y-1..y+1 always exist and are
+      // solid outside the lattice
+      const uint32_t* rn = mr + ms;
+      const uint32_t* rs = mr - ms;
+      const uint32_t mn = rn[w], msth = rs[w];
+      const uint32_t cw = mr[w - 1], ce = mr[w + 1];
+      const uint32_t nw = rn[w - 1], ne = rn[w + 1];
+      const uint32_t sw = rs[w - 1], se = rs[w + 1];
+      // word of x+1 bits and word of x-1 bits for each row
+      const uint32_t eC = __funnelshift_r(mc, ce, 1), wC = __funnelshift_l(cw, mc, 1);
+      const uint32_t eN = __funnelshift_r(mn, ne, 1), wN = __funnelshift_l(nw, mn, 1);
+      const uint32_t eS = __funnelshift_r(msth, se, 1), wS = __funnelshift_l(sw, msth, 1);
+      sE = (eC >> lane) & 1u;
+      sW = (wC >> lane) & 1u;
+      sN = (mn >> lane) & 1u;
+      sS = (msth >> lane) & 1u;
+      sNE = (eN >> lane) & 1u;
+      sNW = (wN >> lane) & 1u;
+      sSE = (eS >> lane) & 1u;
+      sSW = (wS >> lane) & 1u;
+    }
+
+    if (fluid) {
+      if (PHASE == 0) {
+        g[0] = FLD(c);
+        g[2] = sS ? FLD(4 * pl + c) : FLD(2 * pl + c - pitch);
+        g[4] = sN ? FLD(2 * pl + c) : FLD(4 * pl + c + pitch);
+        if (!inlet) {  // sources on the west side (unknown at the inlet)
+          g[1] = sW ? FLD(3 * pl + c) : FLD(1 * pl + c - 1);
+          g[5] = sSW ? FLD(7 * pl + c) : FLD(5 * pl + c - pitch - 1);
+          g[8] = sNW ? FLD(6 * pl + c) : FLD(8 * pl + c + pitch - 1);
+        }
+        if (!outlet) {  // sources on the east side (unknown at the outlet)
+          g[3] = sE ? FLD(1 * pl + c) : FLD(3 * pl + c + 1);
+          g[6] = sSE ? FLD(8 * pl + c) : FLD(6 * pl + c - pitch + 1);
+          g[7] = sNE ? FLD(5 * pl + c) : FLD(7 * pl + c + pitch + 1);
+        }
+      } else {
+        g[0] = FLD(c);
+        g[2] = FLD(4 * pl + c);
+        g[4] = FLD(2 * pl + c);
+        if (!inlet) {
+          g[1] = FLD(3 * pl + c);
+          g[5] = FLD(7 * pl + c);
+          g[8] = FLD(6 * pl + c);
+        }
+        if (!outlet) {
+          g[3] = FLD(1 * pl + c);
+          g[6] = FLD(8 * pl + c);
+          g[7] = FLD(5 * pl + c);
+        }
+      }
+    }
+
+    if (rule == LBM_OUT_NEUMANN) {
+      // zero-gradient outlet: the unknown g3, g6, g7 of cell (nx-1, y) are the
+      // streamed g3, g6, g7 of cell (nx-2, y), held by the lane to the left
+      // (nx is even, so both cells are in this warp's row segment).
+      const float n3 = __shfl_up_sync(0xffffffffu, g[3], 1);
+      const float n6 = __shfl_up_sync(0xffffffffu, g[6], 1);
+      const float n7 = __shfl_up_sync(0xffffffffu, g[7], 1);
+      if (outlet) {
+        g[3] = n3;
+        g[6] = n6;
+        g[7] = n7;
+      }
+    }
+
+    if (!fluid) continue;
+    if (inlet) {
+      inlet_rule(g, L->u_in[y], rho0, L->port_scheme);
+    } else if (outlet && rule == LBM_OUT_CONST_RHO) {
+      outlet_rule(g, rho0, L->port_scheme);
+    }
+    float drho, ux, uy;
+    bgk(g, rho0, omega, drho, ux, uy);
+
+    if (PHASE == 0) {
+      FST(c, g[0]);
+      if (sN) FST(2 * pl + c, g[2]); else FST(4 * pl + c + pitch, g[2]);
+      if (sS) FST(4 * pl + c, g[4]); else FST(2 * pl + c - pitch, g[4]);
+      if (!outlet) {  // destinations on the east side leave through the outlet
+        if (sE) FST(1 * pl + c, g[1]); else FST(3 * pl + c + 1, g[1]);
+        if (sNE) FST(5 * pl + c, g[5]); else FST(7 * pl + c + pitch + 1, g[5]);
+        if (sSE) FST(8 * pl + c, g[8]); else FST(6 * pl + c - pitch + 1, g[8]);
+      }
+      if (!inlet) {  // destinations on the west side leave through the inlet
+        if (sW) FST(3 * pl + c, g[3]); else FST(1 * pl + c - 1, g[3]);
+        if (sNW) FST(6 * pl + c, g[6]); else FST(8 * pl + c + pitch - 1, g[6]);
+        if (sSW) FST(7 * pl + c, g[7]); else FST(5 * pl + c - pitch - 1, g[7]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) FST(i * pl + c, g[i]);
+      if (MOMENTS && LBM_OK_IDX(c, pl)) {
+        L->drho[c] = drho;
+        L->ux[c] = ux;
+        L->uy[c] = uy;
+      }
+    }
+  }
+}
+
+template <class T>
+void* pick(int phase, int moments) {
+  if (phase == 0) return (void*)k_stream_collide<T, 0, false>;
+  if (moments) return (void*)k_stream_collide<T, 1, true>;
+  return (void*)k_stream_collide<T, 1, false>;
+}
+
+void* kernel_for(int precision, int phase, int moments) {
+  switch (precision) {
+    case LBM_F32: return pick<float>(phase, moments);
+    case LBM_BF16_SHIFTED: return pick<__nv_bfloat16>(phase, moments);
+    case LBM_F16_SHIFTED: return pick<__half>(phase, moments);
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
+                                  const TileRef* tiles, const int* n_tiles, int grid,
+                                  cudaStream_t stream) {
+  void* k = kernel_for(precision, phase, moments);
+  if (!k) return cudaErrorInvalidValue;
+  void* args[] = {(void*)&views, (void*)&tiles, (void*)&n_tiles};
+  cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kStepThreads), args, 0, stream);
+  if (e == cudaSuccess) count_launches(1);
+  return e;
+}
+
+int stream_collide_blocks_per_sm(int precision, int phase, int moments) {
+  void* k = kernel_for(precision, phase, moments);
+  int n = 0;
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kStepThreads, 0) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+}  // namespace lbm

@@ -53,6 +53,6 @@ def test_host_only_entry_points(built_lib):
 
 def test_struct_layouts_match_header():
     from paper_1303_0107_gb300 import lib
-    assert ctypes.sizeof(lib.Params) == 48
+    assert ctypes.sizeof(lib.Params) == 56
     assert ctypes.sizeof(lib.SolveResult) == 8 * 3 + 8 + 8 * 64 + 8 * 2 + 8 * 2
     assert ctypes.sizeof(lib.OptResult) == 16 + ctypes.sizeof(lib.SolveResult)

@@ -66,21 +66,25 @@ def test_selection_bit_exact_ragged_random_masks(ora):
 
 def test_optimisation_loop_matches_oracle_choice(ora):
     """Ten iterations of the 128 x 64 T-junction loop (exchange 2 cells, 2000
-    steps): each GPU exchange equals the oracle's pick on the GPU field, the
-    fluid count never changes, and the fields track the oracle run that
-    makes the same exchanges."""
+    steps).  Each iteration: the GPU's exchange equals the oracle's pick on the
+    GPU field; the oracle is restarted from the GPU's populations, makes the
+    same exchange and re-solves, and the two pressure drops agree to the FP32
+    bar of one solve (1e-5); the fluid count never changes."""
+    W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
     cfg = I.config_t_junction()
     cells = cfg["cells"]
     lat = L.Lattice(cells, cfg["tau"], cfg["u_max"])
     p = ora.make_params(128, 64, cfg["tau"], 1.0, cfg["u_max"])
     s = ora.Solver(p, cells)
-    g = lat.solve(cfg["steps"])
-    s.solve(cfg["steps"])
+    lat.solve(cfg["steps"])
     n0 = int((cells == 0).sum())
+    worst = 0.0
     for it in range(cfg["n_iter"]):
         drho, ux, uy = (lat.read(L.FIELD_DRHO), lat.read(L.FIELD_UX), lat.read(L.FIELD_UY))
         mask_before = lat.read(L.FIELD_MASK)
         fo, so = _oracle_pick(ora, p, mask_before, drho, ux, uy, 2)
+        s.solid = mask_before.copy()
+        s.f = lat.read(L.FIELD_POPS).astype(np.float64) + W[:, None, None]
         r = lat.optimize_step(2, cfg["steps"])
         assert r["n_swapped"] == len(fo) == 2
         assert r["fluid_count"] == n0
@@ -88,10 +92,12 @@ def test_optimisation_loop_matches_oracle_choice(ora):
         expect[fo] = 1
         expect[so] = 0
         assert np.array_equal(lat.read(L.FIELD_MASK).reshape(-1), expect)
-        # the oracle makes the same exchange and re-solves
         s.exchange(fo, so)
         o = s.solve(cfg["steps"])
-        assert abs(r["dp"] - o["dp"]) <= 2e-5 * abs(o["dp"]), it
+        rel = abs(r["dp"] - o["dp"]) / abs(o["dp"])
+        worst = max(worst, rel)
+        assert rel <= 1e-5, (it, rel)
+    print(f"worst per-solve relative dp difference over the loop: {worst:.2e}")
     assert int((lat.read(L.FIELD_MASK) == 0).sum()) == n0
 
 
