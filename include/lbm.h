@@ -171,6 +171,40 @@ lbm_status lbm_select_swaps(lbm_handle h, const float* drho, const float* ux, co
                             int32_t n_swap, int32_t* fluid_idx_out, int32_t* solid_idx_out,
                             int32_t* n_out);
 
+/* Largest lattice (nx * ny cells) accepted by lbm_select_swaps_noalloc;
+ * nx and ny are also limited to 4096 each.                              */
+#define LBM_NOALLOC_MAX_CELLS 262144
+
+/* The selection of lbm_select_swaps without any device allocation.  The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- for example code running inside a host application whose
+ * memory pool owns the whole device and forbids raw allocations, or a loop
+ * that must not risk the implicit device synchronisation of cudaMalloc and
+ * cudaFree.  The caller passes device buffers only and no handle is needed:
+ *   nx, ny       lattice size, nx * ny <= LBM_NOALLOC_MAX_CELLS, nx, ny <= 4096
+ *                (LBM_ERR_ARG beyond that, before any device work);
+ *   tau, rho0    as in lbm_params (mu = rho0 (tau - 1/2) / 3);
+ *   cell_types   device uint8[ny][nx], 1 = solid, 0 = fluid;
+ *   drho, ux, uy device float[ny][nx] (rho = rho0 + drho);
+ *   fluid_idx_out, solid_idx_out  device int32[n_swap]: the chosen cells,
+ *                ascending; n_out: device int32, receives n, or -1 if a score
+ *                is not a number;
+ *   cuda_stream  stream to enqueue on (NULL: the legacy default stream).
+ * The call only enqueues work and returns; results are valid once that work
+ * has completed on the stream.  All intermediate storage is one static
+ * device array of about 7.4 MB that every GPU loading the library keeps
+ * until the process exits; the first call with a given device current looks
+ * up its address there (make that first call before any stream capture).
+ * All calls share the array and it keeps the previous call's contents, so
+ * calls whose work overlaps on the GPU (different streams, no ordering)
+ * corrupt each other; calls on one stream are ordered and safe.  Errors
+ * are reported as for every entry point, through lbm_last_error().        */
+lbm_status lbm_select_swaps_noalloc(int32_t nx, int32_t ny, double tau, double rho0,
+                                    const uint8_t* cell_types, const float* drho,
+                                    const float* ux, const float* uy, int32_t n_swap,
+                                    int32_t* fluid_idx_out, int32_t* solid_idx_out,
+                                    int32_t* n_out, void* cuda_stream);
+
 /* Release every resource of the handle.  NULL is accepted.              */
 void lbm_destroy(lbm_handle h);
 

@@ -23,6 +23,8 @@ void count_launches(uint64_t n) {
   if (!t_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
 }
 
+void set_last_error(const std::string& msg) { t_last_error = msg; }
+
 bool debug_sync() {
   static const bool on = [] {
     const char* e = std::getenv("LBM_DEBUG_SYNC");

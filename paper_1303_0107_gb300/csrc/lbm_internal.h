@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <string>
 
 #include "lbm.h"
 
@@ -127,6 +128,8 @@ cudaError_t launch_oc_apply(int precision, const LatticeView* view_dev, uint32_t
 
 // ---- counters / debugging ----------------------------------------------------
 void count_launches(uint64_t n);
+// message returned by lbm_last_error() on the calling thread
+void set_last_error(const std::string& msg);
 // LBM_DEBUG_SYNC=1 in the environment: no graphs, synchronise after every
 // launch and name the kernel that failed.
 bool debug_sync();

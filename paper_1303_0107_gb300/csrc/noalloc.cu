@@ -1,0 +1,173 @@
+// Exchange selection without any device allocation.
+//
+// Some callers cannot call cudaMalloc: a host application whose caching
+// allocator owns all device memory and forbids raw allocations, a loop that
+// must never trigger the implicit device synchronisation cudaMalloc/cudaFree
+// may cause, or a deployment that reserves every byte of device memory when
+// it loads.  lbm_select_swaps_noalloc serves them: the caller passes its own
+// device buffers for inputs and outputs, and all intermediate storage (packed
+// cell mask, candidate counts, offsets, score keys, indices, picks) lives in
+// the file-scope array below, sized for lattices of up to
+// LBM_NOALLOC_MAX_CELLS cells.  Every GPU that loads the library holds this
+// array until the process exits.
+//
+// The computation is the same as the handle-based selection (the kernels of
+// oc.cu and worklist.cu are reused unchanged), so the chosen cells are
+// identical bit for bit.
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+// Scratch layout (byte offsets; every part 256-byte aligned).  Bounds for a
+// lattice with nx * ny <= LBM_NOALLOC_MAX_CELLS, nx <= 4096, ny <= 4096:
+// mask words (ny + 2) * (ceil(nx / 32) + 2) <= 24576; count / offset words
+// ny * ceil(nx / 32) + 1 <= 16384 + 1; candidates per class <= cells; picks
+// per class <= cells / 2 + 1.
+constexpr int kMaxCells = LBM_NOALLOC_MAX_CELLS;
+constexpr int kMaxSide = 4096;
+constexpr size_t kAlign = 256;
+constexpr size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+constexpr int kMaskWords = 24576;
+constexpr int kWordSlots = 16384 + 1;
+constexpr int kPickSlots = kMaxCells / 2 + 1;
+constexpr size_t kOffView = 0;
+constexpr size_t kOffInfo = kOffView + up(sizeof(LatticeView));
+constexpr size_t kOffMask = kOffInfo + up(8 * sizeof(int));
+constexpr size_t kOffCntF = kOffMask + up((size_t)kMaskWords * 4);
+constexpr size_t kOffCntS = kOffCntF + up((size_t)kWordSlots * 4);
+constexpr size_t kOffOffF = kOffCntS + up((size_t)kWordSlots * 4);
+constexpr size_t kOffOffS = kOffOffF + up((size_t)kWordSlots * 4);
+constexpr size_t kOffKeyF = kOffOffS + up((size_t)kWordSlots * 4);
+constexpr size_t kOffKeyS = kOffKeyF + up((size_t)kMaxCells * 8);
+constexpr size_t kOffIdxF = kOffKeyS + up((size_t)kMaxCells * 8);
+constexpr size_t kOffIdxS = kOffIdxF + up((size_t)kMaxCells * 4);
+constexpr size_t kOffSelF = kOffIdxS + up((size_t)kMaxCells * 4);
+constexpr size_t kOffSelS = kOffSelF + up((size_t)kPickSlots * 4);
+constexpr size_t kScratchBytes = kOffSelS + up((size_t)kPickSlots * 4);
+
+// The shared scratch (about 7.4 MB).  In host code this name is only a
+// stand-in for the symbol: its device address comes from
+// cudaGetSymbolAddress, looked up once per device below.
+static __device__ __align__(256) unsigned char g_select_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+unsigned char* g_scratch_ptr[kMaxDevices] = {};
+
+lbm_status fail(lbm_status s, const char* what, cudaError_t e = cudaSuccess) {
+  std::string msg(what);
+  if (e != cudaSuccess) {
+    msg += ": ";
+    msg += cudaGetErrorString(e);
+  }
+  set_last_error(msg);  // reported by lbm_last_error()
+  return s;
+}
+
+// Device address of the scratch array on the current device (looked up on
+// the first call made with that device current).
+lbm_status scratch_on_current_device(unsigned char** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "cudaGetDevice", e);
+  if (dev < 0 || dev >= kMaxDevices) return fail(LBM_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_select_scratch);
+    if (e != cudaSuccess || !p) return fail(LBM_ERR_CUDA, "cudaGetSymbolAddress(scratch)", e);
+    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return LBM_OK;
+}
+
+// picks -> caller's output buffers, count -> *n_out (all on the device)
+__global__ void k_copy_picks(const int* __restrict__ info, const int* __restrict__ sel_f,
+                             const int* __restrict__ sel_s, int cap, int* __restrict__ fluid_out,
+                             int* __restrict__ solid_out, int* __restrict__ n_out) {
+  const int n = min(info[0], cap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    fluid_out[k] = sel_f[k];
+    solid_out[k] = sel_s[k];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = info[3] ? -1 : n;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_select_swaps_noalloc(int32_t nx, int32_t ny, double tau, double rho0,
+                                               const uint8_t* cell_types, const float* drho,
+                                               const float* ux, const float* uy, int32_t n_swap,
+                                               int32_t* fluid_idx_out, int32_t* solid_idx_out,
+                                               int32_t* n_out, void* cuda_stream) {
+  if (!cell_types || !drho || !ux || !uy || !n_out || (n_swap > 0 && (!fluid_idx_out || !solid_idx_out)))
+    return fail(LBM_ERR_ARG, "lbm_select_swaps_noalloc: NULL argument");
+  if (nx < 4 || ny < 3 || n_swap < 0 || !(tau > 0.5) || !(rho0 > 0))
+    return fail(LBM_ERR_ARG, "lbm_select_swaps_noalloc: need nx >= 4, ny >= 3, n_swap >= 0, tau > 1/2, rho0 > 0");
+  if (nx > kMaxSide || ny > kMaxSide || (long long)nx * ny > kMaxCells)
+    return fail(LBM_ERR_ARG,
+                "lbm_select_swaps_noalloc: lattice larger than the built-in scratch allows "
+                "(nx, ny <= 4096 and nx * ny <= LBM_NOALLOC_MAX_CELLS)");
+  const int wpr = (nx + 31) / 32;
+  if (mask_alloc_words(wpr, ny) > kMaskWords || (long long)ny * wpr + 1 > kWordSlots)
+    return fail(LBM_ERR_ARG, "lbm_select_swaps_noalloc: lattice shape exceeds the built-in scratch");
+  unsigned char* base = nullptr;
+  lbm_status st = scratch_on_current_device(&base);
+  if (st != LBM_OK) return st;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+
+  uint32_t* mask_base = reinterpret_cast<uint32_t*>(base + kOffMask);
+  uint32_t* mask = mask_base + mask_origin(wpr);
+  LatticeView v;
+  std::memset(&v, 0, sizeof(v));
+  v.mask = mask;
+  v.drho = const_cast<float*>(drho);
+  v.ux = const_cast<float*>(ux);
+  v.uy = const_cast<float*>(uy);
+  v.plane = (long long)nx * ny;
+  v.nx = nx;
+  v.ny = ny;
+  v.pitch = nx;  // the caller's fields are dense [ny][nx]
+  v.wpr = wpr;
+  LatticeView* view_dev = reinterpret_cast<LatticeView*>(base + kOffView);
+
+  OcScratch s;
+  s.cnt_f = reinterpret_cast<int*>(base + kOffCntF);
+  s.cnt_s = reinterpret_cast<int*>(base + kOffCntS);
+  s.off_f = reinterpret_cast<int*>(base + kOffOffF);
+  s.off_s = reinterpret_cast<int*>(base + kOffOffS);
+  s.key_f = reinterpret_cast<unsigned long long*>(base + kOffKeyF);
+  s.key_s = reinterpret_cast<unsigned long long*>(base + kOffKeyS);
+  s.idx_f = reinterpret_cast<int*>(base + kOffIdxF);
+  s.idx_s = reinterpret_cast<int*>(base + kOffIdxS);
+  s.sel_f = reinterpret_cast<int*>(base + kOffSelF);
+  s.sel_s = reinterpret_cast<int*>(base + kOffSelS);
+  s.info = reinterpret_cast<int*>(base + kOffInfo);
+  s.cap = (int)((long long)nx * ny / 2 + 1);
+
+  cudaError_t e;
+  // the array keeps the previous call's contents: the mask padding must read
+  // as wall, so the whole mask region is reset (the selection clears its own
+  // counters; every other part is fully written before it is read)
+  if ((e = cudaMemcpyAsync(view_dev, &v, sizeof(v), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+    return fail(LBM_ERR_CUDA, "copy lattice descriptor", e);
+  if ((e = cudaMemsetAsync(mask_base, 0xff, (size_t)mask_alloc_words(wpr, ny) * 4, stream)) != cudaSuccess)
+    return fail(LBM_ERR_CUDA, "reset mask", e);
+  if ((e = launch_pack_mask(cell_types, nx, ny, wpr, mask, stream)) != cudaSuccess)
+    return fail(LBM_ERR_CUDA, "pack mask", e);
+  const double mu = rho0 * ((tau - 0.5) / 3.0);
+  if ((e = launch_oc_select(&v, view_dev, rho0, mu, n_swap, s, stream)) != cudaSuccess)
+    return fail(LBM_ERR_CUDA, "selection kernels", e);
+  k_copy_picks<<<(n_swap + 255) / 256 > 0 ? (n_swap + 255) / 256 : 1, 256, 0, stream>>>(
+      s.info, s.sel_f, s.sel_s, n_swap, fluid_idx_out, solid_idx_out, n_out);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(LBM_ERR_CUDA, "copy picks", e);
+  return LBM_OK;
+}

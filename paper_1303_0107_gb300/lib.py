@@ -89,10 +89,13 @@ def load_library(path=None):
     L.lbm_kernel_launches.restype = ctypes.c_uint64
     L.lbm_kernel_time.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    L.lbm_select_swaps_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                           _VP, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP]
     L.lbm_bytes_per_fluid_update.argtypes = [ctypes.c_int32]
     L.lbm_bytes_per_fluid_update.restype = ctypes.c_double
     for name in ("lbm_create_geometry", "lbm_solve", "lbm_optimize_step", "lbm_read_fields",
-                 "lbm_load_state", "lbm_reset", "lbm_select_swaps", "lbm_kernel_time"):
+                 "lbm_load_state", "lbm_reset", "lbm_select_swaps", "lbm_kernel_time",
+                 "lbm_select_swaps_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
