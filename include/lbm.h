@@ -19,7 +19,8 @@
  *     column nx-1; each fluid cell (0,y) has a fluid (1,y) and each fluid
  *     (nx-1,y) a fluid (nx-2,y);
  *   - at least one inlet and one outlet cell, at most LBM_MAX_OUTLETS outlet
- *     runs; nx even, 4 <= nx, 3 <= ny, nx*ny < 2^31.
+ *     runs; nx even, 4 <= nx <= 131072, 3 <= ny < 524288, and
+ *     9 * ny * pitch < 2^31 with pitch = nx rounded up to 64 (LBM_ERR_ARG).
  * The optimiser never changes columns 0, 1, nx-2, nx-1 nor rows 0, ny-1.
  *
  * Threading: a handle is used by one host thread at a time.  All device work

@@ -83,9 +83,9 @@ struct lbm_handle_s {
   int *d_outlet_start = nullptr, *d_outlet_len = nullptr;
   LatticeView* views = nullptr;
   LatticeView host_view{};
-  TileRef* tiles = nullptr;
-  int* n_tiles = nullptr;
-  int* tile_scratch = nullptr;
+  SegRef* segs = nullptr;   // row segments holding fluid cells
+  int* n_segs = nullptr;
+  int* seg_scratch = nullptr;
   double* partials = nullptr;
   double* result = nullptr;
   unsigned long long* fluid_dev = nullptr;
@@ -176,10 +176,10 @@ lbm_status run_plain_pairs(lbm_handle h, int64_t pairs);
 lbm_status launch_pair(lbm_handle h, int moments_view) {
   // moments_view: -1 none, 0 into the lattice fields, 1 into the *_prev fields
   const int prec = h->p.precision;
-  CU(launch_stream_collide(prec, 0, 0, h->views, h->tiles, h->n_tiles, h->grid, h->stream));
+  CU(launch_stream_collide(prec, 0, 0, h->views, h->segs, h->n_segs, h->grid, h->stream));
   DEBUG_SYNC(h, "stream-collide phase A");
   const LatticeView* v = moments_view == 1 ? h->views + 1 : h->views;
-  CU(launch_stream_collide(prec, 1, moments_view >= 0 ? 1 : 0, v, h->tiles, h->n_tiles, h->grid,
+  CU(launch_stream_collide(prec, 1, moments_view >= 0 ? 1 : 0, v, h->segs, h->n_segs, h->grid,
                            h->stream));
   DEBUG_SYNC(h, moments_view >= 0 ? "stream-collide phase B with moments" : "stream-collide phase B");
   return LBM_OK;
@@ -229,8 +229,7 @@ lbm_status run_plain_pairs(lbm_handle h, int64_t pairs) {
 }
 
 lbm_status rebuild_worklist(lbm_handle h) {
-  CU(launch_build_tiles(h->mask, h->nx, h->ny, h->wpr, 0, h->tile_scratch, h->tiles,
-                        h->n_tiles, h->stream));
+  CU(launch_build_segments(h->mask, h->ny, h->wpr, 0, h->seg_scratch, h->segs, h->n_segs, h->stream));
   CU(launch_count_fluid(h->mask, h->nx, h->ny, h->wpr, h->fluid_dev, h->stream));
   return LBM_OK;
 }
@@ -349,8 +348,9 @@ lbm_status lbm_create_geometry(const lbm_params* params, const uint8_t* cell_typ
   *out = nullptr;
   if (!params || !cell_types) return fail(LBM_ERR_ARG, "params or cell_types is NULL");
   const lbm_params& p = *params;
-  if (p.nx < 4 || p.ny < 3 || (p.nx % 2) != 0 || (int64_t)p.nx * p.ny >= (int64_t)1 << 31)
-    return fail(LBM_ERR_ARG, "nx must be even and >= 4, ny >= 3, nx*ny < 2^31");
+  if (p.nx < 4 || p.ny < 3 || (p.nx % 2) != 0 || (int64_t)p.nx * p.ny >= (int64_t)1 << 31 ||
+      p.nx > (32 << kSegWordBits) || p.ny >= (1 << (31 - kSegWordBits)))
+    return fail(LBM_ERR_ARG, "nx must be even, 4 <= nx <= 131072, 3 <= ny < 524288, nx*ny < 2^31");
   if (!(p.tau > 0.5) || !std::isfinite(p.tau) || !std::isfinite(p.rho0) || !(p.rho0 > 0) ||
       !std::isfinite(p.u_max))
     return fail(LBM_ERR_ARG, "tau must be > 1/2, rho0 > 0, u_max finite");
@@ -367,6 +367,10 @@ lbm_status lbm_create_geometry(const lbm_params* params, const uint8_t* cell_typ
   h->pitch = (p.nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
   h->wpr = (p.nx + 31) / 32;
   h->plane = (size_t)h->ny * h->pitch;
+  if (9 * h->plane >= ((size_t)1 << 31)) {
+    delete h;
+    return fail(LBM_ERR_ARG, "lattice too large: 9 * ny * pitch must stay below 2^31 elements");
+  }
   std::vector<float> u_in;
   lbm_status st = check_and_describe(h, cell_types, u_in);
   if (st != LBM_OK) {
@@ -406,10 +410,10 @@ lbm_status lbm_create_geometry(const lbm_params* params, const uint8_t* cell_typ
   CUH(dalloc(h, &h->d_outlet_start, LBM_MAX_OUTLETS * 4));
   CUH(dalloc(h, &h->d_outlet_len, LBM_MAX_OUTLETS * 4));
   CUH(dalloc(h, &h->views, kViews * sizeof(LatticeView)));
-  const size_t tiles_y = (ny + kTileY - 1) / kTileY, ntiles = tiles_y * h->wpr;
-  CUH(dalloc(h, &h->tiles, ntiles * sizeof(TileRef)));
-  CUH(dalloc(h, &h->n_tiles, sizeof(int)));
-  CUH(dalloc(h, &h->tile_scratch, (2 * ntiles + 1) * sizeof(int)));
+  const size_t nseg_cap = segment_capacity(h->ny, h->wpr);
+  CUH(dalloc(h, &h->segs, nseg_cap * sizeof(SegRef)));
+  CUH(dalloc(h, &h->n_segs, sizeof(int)));
+  CUH(dalloc(h, &h->seg_scratch, segment_scratch_ints(h->ny, h->wpr) * sizeof(int)));
   CUH(dalloc(h, &h->partials, 2 * kResidualBlocks * sizeof(double)));
   CUH(dalloc(h, &h->result, kResultDoubles * sizeof(double)));
   CUH(dalloc(h, &h->fluid_dev, sizeof(unsigned long long)));
@@ -428,6 +432,7 @@ lbm_status lbm_create_geometry(const lbm_params* params, const uint8_t* cell_typ
   CUH(dalloc(h, &oc.sel_f, (size_t)oc.cap * 4));
   CUH(dalloc(h, &oc.sel_s, (size_t)oc.cap * 4));
   CUH(dalloc(h, &oc.info, 8 * 4));
+  CUH(dalloc(h, &oc.scan_tmp, scan_tmp_ints((int)nwords) * 4));
   CUH(cudaMallocHost((void**)&h->h_result, kResultDoubles * sizeof(double)));
   CUH(cudaMallocHost((void**)&h->h_info, 8 * sizeof(int)));
   CUH(cudaMallocHost((void**)&h->h_count, sizeof(unsigned long long)));
@@ -465,9 +470,12 @@ lbm_status lbm_create_geometry(const lbm_params* params, const uint8_t* cell_typ
   CUH(cudaMemcpyAsync(h->cells_dev, cell_types, ncell, cudaMemcpyHostToDevice, h->stream));
   CUH(launch_pack_mask(h->cells_dev, h->nx, h->ny, h->wpr, h->mask0, h->stream));
 #undef CUH
+  // enough warps for one segment each where the lattice allows, never more
+  // blocks than fit on the device at once (the kernel strides over the list)
   const int bps = stream_collide_blocks_per_sm(p.precision, 0, 0);
   const long long cap = (long long)h->sm_count * bps;
-  h->grid = (int)(ntiles < (size_t)cap ? ntiles : cap);
+  const long long need = ((long long)nseg_cap + kStepWarps - 1) / kStepWarps;
+  h->grid = (int)(need < cap ? need : cap);
   if (h->grid < 1) h->grid = 1;
   st = initial_state(h);
   if (st != LBM_OK) {

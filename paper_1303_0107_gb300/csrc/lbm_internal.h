@@ -12,11 +12,12 @@
 
 namespace lbm {
 
-// A tile is 32 consecutive cells of one row word (one mask word) times kTileY
-// rows; a thread block of kTileY warps processes one tile at a time, warp r
-// handling row y0 + r, lane l handling cell x0 + l.
-constexpr int kTileY = 8;
-constexpr int kStepThreads = 32 * kTileY;
+// Work unit of the stream-collide kernel: one row segment, the 32 cells of
+// one mask word (row y, cells 32w .. 32w+31), taken by one warp (lane l ->
+// cell 32w + l).  A block holds kStepWarps warps; the segment list holds only
+// segments with at least one fluid cell.
+constexpr int kStepWarps = 8;
+constexpr int kStepThreads = 32 * kStepWarps;
 // Row pitch of every per-cell array, in elements: a multiple of 64 so that
 // each row starts on a 128-byte boundary for 16-bit and 32-bit storage.
 constexpr int kPitchAlign = 64;
@@ -53,14 +54,14 @@ struct alignas(16) LatticeView {
   long long f_elems;     // 9 * plane (extent of f)
 };
 
-struct alignas(16) TileRef {
-  int lattice;  // index into the LatticeView table
-  int x0;       // first column (multiple of 32)
-  int y0;       // first row (multiple of kTileY)
-  int reserved;
+// A row segment: lattice index and (y << 12) | w (w < 4096, so nx <= 131072).
+struct alignas(8) SegRef {
+  int lattice;
+  int yw;
 };
+constexpr int kSegWordBits = 12;
 static_assert(sizeof(LatticeView) % 16 == 0 && alignof(LatticeView) == 16, "LatticeView layout");
-static_assert(sizeof(TileRef) == 16 && alignof(TileRef) == 16, "TileRef layout");
+static_assert(sizeof(SegRef) == 8, "SegRef layout");
 
 // ---- stream-collide (step.cu) ----------------------------------------------
 // phase 0 ("A"): reads the post-collision state from the neighbours, writes
@@ -69,8 +70,11 @@ static_assert(sizeof(TileRef) == 16 && alignof(TileRef) == 16, "TileRef layout")
 // phase 1 ("B"): reads and writes the cell's own slots only, leaving the
 //   canonical layout F[i][cell] = post-collision population i.
 // moments != 0 writes drho/ux/uy of the view (phase B only).
+// Launched as a programmatic dependent of the previous kernel on the stream:
+// it reads its work item, descriptor and mask before waiting for that kernel,
+// and only then the populations.
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
-                                  const TileRef* tiles, const int* n_tiles, int grid,
+                                  const SegRef* segs, const int* n_segs, int grid,
                                   cudaStream_t stream);
 int stream_collide_blocks_per_sm(int precision, int phase, int moments);
 
@@ -79,15 +83,19 @@ cudaError_t launch_pack_mask(const uint8_t* cells, int nx, int ny, int wpr, uint
                              cudaStream_t stream);
 cudaError_t launch_unpack_mask(const uint32_t* mask, int nx, int ny, int wpr, uint8_t* cells,
                                cudaStream_t stream);
-// Tile list of one lattice: tiles whose words hold at least one fluid cell,
-// in ascending (y0, x0) order, tagged with `lattice`.  scratch holds
-// 2 * ceil(ny / kTileY) * wpr + 1 ints.
-cudaError_t launch_build_tiles(const uint32_t* mask, int nx, int ny, int wpr, int lattice,
-                               int* scratch, TileRef* tiles, int* n_tiles, cudaStream_t stream);
+// Segment list of one lattice: the row segments of rows 1..ny-2 holding at
+// least one fluid cell, in ascending (y, w) order, tagged with `lattice`.
+// scratch holds segment_scratch_ints(ny, wpr) ints.
+size_t segment_scratch_ints(int ny, int wpr);
+size_t segment_capacity(int ny, int wpr);
+cudaError_t launch_build_segments(const uint32_t* mask, int ny, int wpr, int lattice, int* scratch,
+                                  SegRef* segs, int* n_segs, cudaStream_t stream);
 cudaError_t launch_count_fluid(const uint32_t* mask, int nx, int ny, int wpr,
                                unsigned long long* count, cudaStream_t stream);
-// exclusive scan of n ints in one block; out[n] = total
-cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t stream);
+// exclusive scan of n ints; out[n] = total.  Fixed order for any input.
+// tmp holds scan_tmp_ints(n) ints.
+size_t scan_tmp_ints(int n);
+cudaError_t launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t stream);
 cudaError_t launch_rho_from_drho(const float* drho, float rho0, const uint32_t* mask, int nx, int ny,
                                  int pitch, int wpr, float* rho_dense, cudaStream_t stream);
 
@@ -118,6 +126,7 @@ struct OcScratch {
   int* sel_f;            // [cap]
   int* sel_s;            // [cap]
   int* info;             // [8]: n_swapped, nF, nS, error flag, ...
+  int* scan_tmp;         // scan_tmp_ints(nwords)
   int cap;               // capacity of sel_* (max n_swap)
 };
 cudaError_t launch_oc_select(const LatticeView* view_host, const LatticeView* view_dev,

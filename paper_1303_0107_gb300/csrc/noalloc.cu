@@ -49,7 +49,9 @@ constexpr size_t kOffIdxF = kOffKeyS + up((size_t)kMaxCells * 8);
 constexpr size_t kOffIdxS = kOffIdxF + up((size_t)kMaxCells * 4);
 constexpr size_t kOffSelF = kOffIdxS + up((size_t)kMaxCells * 4);
 constexpr size_t kOffSelS = kOffSelF + up((size_t)kPickSlots * 4);
-constexpr size_t kScratchBytes = kOffSelS + up((size_t)kPickSlots * 4);
+constexpr size_t kOffScan = kOffSelS + up((size_t)kPickSlots * 4);
+constexpr int kScanTmpInts = 256;  // >= scan_tmp_ints(kWordSlots)
+constexpr size_t kScratchBytes = kOffScan + up((size_t)kScanTmpInts * 4);
 
 // The shared scratch (about 7.4 MB).  In host code this name is only a
 // stand-in for the symbol: its device address comes from
@@ -116,7 +118,8 @@ extern "C" lbm_status lbm_select_swaps_noalloc(int32_t nx, int32_t ny, double ta
                 "lbm_select_swaps_noalloc: lattice larger than the built-in scratch allows "
                 "(nx, ny <= 4096 and nx * ny <= LBM_NOALLOC_MAX_CELLS)");
   const int wpr = (nx + 31) / 32;
-  if (mask_alloc_words(wpr, ny) > kMaskWords || (long long)ny * wpr + 1 > kWordSlots)
+  if (mask_alloc_words(wpr, ny) > kMaskWords || (long long)ny * wpr + 1 > kWordSlots ||
+      scan_tmp_ints(ny * wpr) > (size_t)kScanTmpInts)
     return fail(LBM_ERR_ARG, "lbm_select_swaps_noalloc: lattice shape exceeds the built-in scratch");
   unsigned char* base = nullptr;
   lbm_status st = scratch_on_current_device(&base);
@@ -150,6 +153,7 @@ extern "C" lbm_status lbm_select_swaps_noalloc(int32_t nx, int32_t ny, double ta
   s.sel_f = reinterpret_cast<int*>(base + kOffSelF);
   s.sel_s = reinterpret_cast<int*>(base + kOffSelS);
   s.info = reinterpret_cast<int*>(base + kOffInfo);
+  s.scan_tmp = reinterpret_cast<int*>(base + kOffScan);
   s.cap = (int)((long long)nx * ny / 2 + 1);
 
   cudaError_t e;

@@ -268,8 +268,8 @@ cudaError_t launch_oc_select(const LatticeView* view_host, const LatticeView* vi
   if (e != cudaSuccess) return e;
   k_oc_count<<<blocks_for(nwords, 256), 256, 0, stream>>>(view_host->mask, nx, ny, wpr, s.cnt_f,
                                                           s.cnt_s);
-  if ((e = launch_scan(s.cnt_f, s.off_f, nwords, stream)) != cudaSuccess) return e;
-  if ((e = launch_scan(s.cnt_s, s.off_s, nwords, stream)) != cudaSuccess) return e;
+  if ((e = launch_scan(s.cnt_f, s.off_f, nwords, s.scan_tmp, stream)) != cudaSuccess) return e;
+  if ((e = launch_scan(s.cnt_s, s.off_s, nwords, s.scan_tmp, stream)) != cudaSuccess) return e;
   k_oc_emit<<<blocks_for(nwords, 256), 256, 0, stream>>>(view_dev, view_host->mask, rho0, mu, s.off_f,
                                                          s.off_s, s.key_f, s.idx_f, s.key_s, s.idx_s,
                                                          s.info);

@@ -19,11 +19,14 @@
 // Each slot is read and then written by exactly one thread per phase, so the
 // pair needs one lattice and no barrier.  Solid cells are never read.
 //
-// Thread mapping.  A block of kTileY warps owns a 32 x kTileY tile; warp r
-// handles row y0 + r, lane l cell x0 + l, so every plane access of a warp is
-// one contiguous 32-element row segment (shifted by at most one element).
-// Blocks stride over a device-resident tile list that holds only tiles with
-// fluid cells; warps whose row segment is all solid skip at once.
+// Thread mapping.  Each warp takes one row segment (the 32 cells of one mask
+// word) from a device-resident list holding only segments with fluid cells;
+// lane l handles cell 32w + l, so every plane access of a warp is one
+// contiguous 32-element row segment (shifted by at most one element).  Warps
+// stride over the list; the list may span several lattices (batches).
+// Consecutive steps are programmatic dependent launches: a step's warps load
+// their segment, descriptor and mask words while the previous step is still
+// finishing, and wait for it only before touching populations.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -185,106 +188,95 @@ __device__ __forceinline__ void outlet_rule(float (&g)[9], float rho0, int schem
 
 // population access with optional bounds checks (offset in elements from F)
 #define FLD(off) (LBM_OK_IDX((off), fe) ? P::ld(F + (off)) : 0.0f)
-#define FST(off, v)                                \
-  do {                                             \
+#define FST(off, v)                                   \
+  do {                                                \
     if (LBM_OK_IDX((off), fe)) P::st(F + (off), (v)); \
   } while (0)
 
+// neighbour solid flags, bit i-1 = solid(x + c_i), i = 1..8 (E N W S NE NW SW SE)
+constexpr unsigned kE = 1u, kN = 2u, kW = 4u, kS = 8u, kNE = 16u, kNW = 32u, kSW = 64u, kSE = 128u;
+
 template <class T, int PHASE, bool MOMENTS>
-__global__ void __launch_bounds__(kStepThreads, 3)
-    k_stream_collide(const LatticeView* __restrict__ views, const TileRef* __restrict__ tiles,
-                     const int* __restrict__ n_tiles) {
+__global__ void __launch_bounds__(kStepThreads, 4)
+    k_stream_collide(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
+                     const int* __restrict__ n_segs) {
   using P = Pop<T>;
+  // The next time step may be scheduled now; it reads populations only after
+  // waiting for this grid to complete.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31;
-  const int row = threadIdx.x >> 5;
-  const int nt = *n_tiles;
+  // the segment list, descriptors and mask are never written by a time step,
+  // so they may be read before the previous step has finished
+  const int nseg = *n_segs;
+  const int stride = gridDim.x * kStepWarps;
+  bool waited = false;
+  for (int sidx = blockIdx.x * kStepWarps + (threadIdx.x >> 5); sidx < nseg; sidx += stride) {
+    const SegRef sr = segs[sidx];
+    const LatticeView* __restrict__ L = views + sr.lattice;
+    const int y = sr.yw >> kSegWordBits;
+    const int w = sr.yw & ((1 << kSegWordBits) - 1);
 #ifdef LBM_CHECK_BOUNDS
-  {
-    const long long cap = (long long)((views->ny + kTileY - 1) / kTileY) * views->wpr;
-    if (nt < 0 || nt > cap) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) printf("lbm bounds: tile count %d outside [0, %lld]\n", nt, cap);
-      return;
-    }
-  }
-#endif
-  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-    const TileRef tr = tiles[t];
-    const LatticeView* __restrict__ L = views + tr.lattice;
-    const int ny = L->ny;
-#ifdef LBM_CHECK_BOUNDS
-    if (tr.lattice != 0 || tr.x0 < 0 || tr.x0 >= L->wpr * 32 || tr.y0 < 0 || tr.y0 >= ny) {
-      if (threadIdx.x == 0)
-        printf("lbm bounds: bad tile %d of %d: lattice %d x0 %d y0 %d\n", t, nt, tr.lattice, tr.x0, tr.y0);
+    if (sr.lattice < 0 || y < 1 || y > L->ny - 2 || w < 0 || w >= L->wpr) {
+      if (lane == 0) printf("lbm bounds: bad segment %d of %d: lattice %d y %d w %d\n", sidx, nseg, sr.lattice, y, w);
       continue;
     }
 #endif
-    const int y = tr.y0 + row;
-    if (y < 1 || y > ny - 2) continue;  // frame rows hold no fluid
     const int ms = mask_stride(L->wpr);
-    const int w = tr.x0 >> 5;
     const uint32_t* mr = L->mask + (long long)y * ms;
     const uint32_t mc = mr[w];
-    if (mc == 0xffffffffu) continue;  // whole row segment solid (warp-uniform)
-
     const int nx = L->nx;
-    const int x = tr.x0 + lane;
-    const int pitch = L->pitch;
-    const long long pl = L->plane;
-    const float rho0 = L->rho0;
-    const float omega = L->omega;
-    const int rule = L->outlet_rule;
-    T* __restrict__ F = static_cast<T*>(L->f);
-    const long long fe = L->f_elems;
-    (void)fe;
-    const long long c = (long long)y * pitch + x;
+    const int x = (w << 5) + lane;
     const bool fluid = !((mc >> lane) & 1u);  // bits beyond nx are set (solid)
     const bool inlet = (x == 0);
     const bool outlet = (x == nx - 1);
 
-    float g[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = 0.0f;
-
-    // solid flags of the 8 neighbours (only phase A needs them)
-    bool sE = false, sN = false, sW = false, sS = false, sNE = false, sNW = false, sSW = false,
-         sSE = false;
+    unsigned nb = 0;  // solid flags of the 8 neighbours (phase A only)
     if (PHASE == 0) {
       // padded mask: words w-1 and w+1 of rows y-1..y+1 always exist and are
       // solid outside the lattice
       const uint32_t* rn = mr + ms;
       const uint32_t* rs = mr - ms;
       const uint32_t mn = rn[w], msth = rs[w];
-      const uint32_t cw = mr[w - 1], ce = mr[w + 1];
-      const uint32_t nw = rn[w - 1], ne = rn[w + 1];
-      const uint32_t sw = rs[w - 1], se = rs[w + 1];
-      // word of x+1 bits and word of x-1 bits for each row
-      const uint32_t eC = __funnelshift_r(mc, ce, 1), wC = __funnelshift_l(cw, mc, 1);
-      const uint32_t eN = __funnelshift_r(mn, ne, 1), wN = __funnelshift_l(nw, mn, 1);
-      const uint32_t eS = __funnelshift_r(msth, se, 1), wS = __funnelshift_l(sw, msth, 1);
-      sE = (eC >> lane) & 1u;
-      sW = (wC >> lane) & 1u;
-      sN = (mn >> lane) & 1u;
-      sS = (msth >> lane) & 1u;
-      sNE = (eN >> lane) & 1u;
-      sNW = (wN >> lane) & 1u;
-      sSE = (eS >> lane) & 1u;
-      sSW = (wS >> lane) & 1u;
+      const uint32_t eC = __funnelshift_r(mc, mr[w + 1], 1), wC = __funnelshift_l(mr[w - 1], mc, 1);
+      const uint32_t eN = __funnelshift_r(mn, rn[w + 1], 1), wN = __funnelshift_l(rn[w - 1], mn, 1);
+      const uint32_t eS = __funnelshift_r(msth, rs[w + 1], 1), wS = __funnelshift_l(rs[w - 1], msth, 1);
+      nb = ((eC >> lane) & 1u) | (((mn >> lane) & 1u) << 1) | (((wC >> lane) & 1u) << 2) |
+           (((msth >> lane) & 1u) << 3) | (((eN >> lane) & 1u) << 4) | (((wN >> lane) & 1u) << 5) |
+           (((wS >> lane) & 1u) << 6) | (((eS >> lane) & 1u) << 7);
+    }
+    // 32-bit element offsets: lattices are limited to 9 * plane < 2^31
+    const int pitch = L->pitch;
+    const int pl = (int)L->plane;
+    const float rho0 = L->rho0;
+    const float omega = L->omega;
+    const int rule = L->outlet_rule;
+    T* __restrict__ F = static_cast<T*>(L->f);
+    const long long fe = L->f_elems;
+    (void)fe;
+    const int c = y * pitch + x;
+
+    if (!waited) {  // warp-uniform: populations of the previous step are final from here on
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      waited = true;
     }
 
+    float g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = 0.0f;
     if (fluid) {
       if (PHASE == 0) {
         g[0] = FLD(c);
-        g[2] = sS ? FLD(4 * pl + c) : FLD(2 * pl + c - pitch);
-        g[4] = sN ? FLD(2 * pl + c) : FLD(4 * pl + c + pitch);
+        g[2] = (nb & kS) ? FLD(4 * pl + c) : FLD(2 * pl + c - pitch);
+        g[4] = (nb & kN) ? FLD(2 * pl + c) : FLD(4 * pl + c + pitch);
         if (!inlet) {  // sources on the west side (unknown at the inlet)
-          g[1] = sW ? FLD(3 * pl + c) : FLD(1 * pl + c - 1);
-          g[5] = sSW ? FLD(7 * pl + c) : FLD(5 * pl + c - pitch - 1);
-          g[8] = sNW ? FLD(6 * pl + c) : FLD(8 * pl + c + pitch - 1);
+          g[1] = (nb & kW) ? FLD(3 * pl + c) : FLD(1 * pl + c - 1);
+          g[5] = (nb & kSW) ? FLD(7 * pl + c) : FLD(5 * pl + c - pitch - 1);
+          g[8] = (nb & kNW) ? FLD(6 * pl + c) : FLD(8 * pl + c + pitch - 1);
         }
         if (!outlet) {  // sources on the east side (unknown at the outlet)
-          g[3] = sE ? FLD(1 * pl + c) : FLD(3 * pl + c + 1);
-          g[6] = sSE ? FLD(8 * pl + c) : FLD(6 * pl + c - pitch + 1);
-          g[7] = sNE ? FLD(5 * pl + c) : FLD(7 * pl + c + pitch + 1);
+          g[3] = (nb & kE) ? FLD(1 * pl + c) : FLD(3 * pl + c + 1);
+          g[6] = (nb & kSE) ? FLD(8 * pl + c) : FLD(6 * pl + c - pitch + 1);
+          g[7] = (nb & kNE) ? FLD(5 * pl + c) : FLD(7 * pl + c + pitch + 1);
         }
       } else {
         g[0] = FLD(c);
@@ -328,17 +320,17 @@ __global__ void __launch_bounds__(kStepThreads, 3)
 
     if (PHASE == 0) {
       FST(c, g[0]);
-      if (sN) FST(2 * pl + c, g[2]); else FST(4 * pl + c + pitch, g[2]);
-      if (sS) FST(4 * pl + c, g[4]); else FST(2 * pl + c - pitch, g[4]);
+      if (nb & kN) FST(2 * pl + c, g[2]); else FST(4 * pl + c + pitch, g[2]);
+      if (nb & kS) FST(4 * pl + c, g[4]); else FST(2 * pl + c - pitch, g[4]);
       if (!outlet) {  // destinations on the east side leave through the outlet
-        if (sE) FST(1 * pl + c, g[1]); else FST(3 * pl + c + 1, g[1]);
-        if (sNE) FST(5 * pl + c, g[5]); else FST(7 * pl + c + pitch + 1, g[5]);
-        if (sSE) FST(8 * pl + c, g[8]); else FST(6 * pl + c - pitch + 1, g[8]);
+        if (nb & kE) FST(1 * pl + c, g[1]); else FST(3 * pl + c + 1, g[1]);
+        if (nb & kNE) FST(5 * pl + c, g[5]); else FST(7 * pl + c + pitch + 1, g[5]);
+        if (nb & kSE) FST(8 * pl + c, g[8]); else FST(6 * pl + c - pitch + 1, g[8]);
       }
       if (!inlet) {  // destinations on the west side leave through the inlet
-        if (sW) FST(3 * pl + c, g[3]); else FST(1 * pl + c - 1, g[3]);
-        if (sNW) FST(6 * pl + c, g[6]); else FST(8 * pl + c + pitch - 1, g[6]);
-        if (sSW) FST(7 * pl + c, g[7]); else FST(5 * pl + c - pitch - 1, g[7]);
+        if (nb & kW) FST(3 * pl + c, g[3]); else FST(1 * pl + c - 1, g[3]);
+        if (nb & kNW) FST(6 * pl + c, g[6]); else FST(8 * pl + c + pitch - 1, g[6]);
+        if (nb & kSW) FST(7 * pl + c, g[7]); else FST(5 * pl + c - pitch - 1, g[7]);
       }
     } else {
 #pragma unroll
@@ -350,6 +342,7 @@ __global__ void __launch_bounds__(kStepThreads, 3)
       }
     }
   }
+  if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 template <class T>
@@ -371,12 +364,22 @@ void* kernel_for(int precision, int phase, int moments) {
 }  // namespace
 
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
-                                  const TileRef* tiles, const int* n_tiles, int grid,
+                                  const SegRef* segs, const int* n_segs, int grid,
                                   cudaStream_t stream) {
   void* k = kernel_for(precision, phase, moments);
   if (!k) return cudaErrorInvalidValue;
-  void* args[] = {(void*)&views, (void*)&tiles, (void*)&n_tiles};
-  cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kStepThreads), args, 0, stream);
+  void* args[] = {(void*)&views, (void*)&segs, (void*)&n_segs};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kStepThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, k, args);
   if (e == cudaSuccess) count_launches(1);
   return e;
 }

@@ -1,4 +1,4 @@
-// Geometry to bit mask, tile work-list, fluid count, block scan.
+// Geometry to bit mask, row-segment work-list, fluid count, scans.
 //
 // The cell map of Sec. 3.3 (fluid / solid cells; inlet and outlet cells are
 // the fluid cells of the first and last columns) is kept as one bit per cell:
@@ -31,34 +31,28 @@ __global__ void k_unpack_mask(const uint32_t* __restrict__ mask, int nx, int ny,
   cells[i] = (mask[(long long)y * mask_stride(wpr) + (x >> 5)] >> (x & 31)) & 1u;
 }
 
-// 1 for every tile (32 x kTileY) with a fluid cell in rows 1..ny-2.
-__global__ void k_tile_flags(const uint32_t* __restrict__ mask, int ny, int wpr, int tiles_y,
-                             int* __restrict__ flags) {
+// 1 for every row segment (row y in 1..ny-2, word w) holding a fluid cell;
+// index (y - 1) * wpr + w.
+__global__ void k_segment_flags(const uint32_t* __restrict__ mask, int ny, int wpr,
+                                int* __restrict__ flags) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= tiles_y * wpr) return;
-  const int ty = i / wpr, w = i - ty * wpr;
-  int any = 0;
-  for (int r = 0; r < kTileY; ++r) {
-    const int y = ty * kTileY + r;
-    if (y >= 1 && y <= ny - 2 && mask[(long long)y * mask_stride(wpr) + w] != 0xffffffffu) any = 1;
-  }
-  flags[i] = any;
+  if (i >= (ny - 2) * wpr) return;
+  const int y = 1 + i / wpr, w = i - (i / wpr) * wpr;
+  flags[i] = mask[(long long)y * mask_stride(wpr) + w] != 0xffffffffu ? 1 : 0;
 }
 
-__global__ void k_tile_scatter(const int* __restrict__ flags, const int* __restrict__ offsets,
-                               int tiles_y, int wpr, int lattice, TileRef* __restrict__ tiles,
-                               int* __restrict__ n_tiles) {
+__global__ void k_segment_scatter(const int* __restrict__ flags, const int* __restrict__ offsets,
+                                  int ny, int wpr, int lattice, SegRef* __restrict__ segs,
+                                  int* __restrict__ n_segs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = tiles_y * wpr;
-  if (i == 0) *n_tiles = offsets[n];
+  const int n = (ny - 2) * wpr;
+  if (i == 0) *n_segs = offsets[n];
   if (i >= n || !flags[i]) return;
-  const int ty = i / wpr, w = i - ty * wpr;
-  TileRef t;
-  t.lattice = lattice;
-  t.x0 = w * 32;
-  t.y0 = ty * kTileY;
-  t.reserved = 0;
-  tiles[offsets[i]] = t;
+  const int y = 1 + i / wpr, w = i - (i / wpr) * wpr;
+  SegRef r;
+  r.lattice = lattice;
+  r.yw = (y << kSegWordBits) | w;
+  segs[offsets[i]] = r;
 }
 
 __global__ void k_count_fluid(const uint32_t* __restrict__ mask, int nx, int ny, int wpr,
@@ -79,7 +73,9 @@ __global__ void k_count_fluid(const uint32_t* __restrict__ mask, int nx, int ny,
 // Exclusive scan of n ints by one block of 1024 threads; out[n] = total.
 // Each thread sums a contiguous chunk, the chunk sums are scanned in shared
 // memory, then each thread writes its chunk: a fixed order for any input.
-__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int* __restrict__ out, int n) {
+// Used for the top level of the multi-block scan.
+__global__ void __launch_bounds__(1024) k_scan_chunked(const int* __restrict__ in, int* __restrict__ out,
+                                                       int n) {
   __shared__ int sums[1024];
   const int tid = threadIdx.x;
   const int per = (n + 1023) / 1024;
@@ -101,6 +97,58 @@ __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int* 
     run += v;
   }
   if (tid == 1023) out[n] = sums[1023];
+}
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;  // elements per block
+
+// Level 1: exclusive scan inside each tile of kScanTile elements; tile sums
+// go to block_sums[b].
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int* __restrict__ in,
+                                                             int* __restrict__ out, int n,
+                                                             int* __restrict__ block_sums) {
+  __shared__ int warp_sums[kScanThreads / 32];
+  const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int t = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = base + k < n ? in[base + k] : 0;
+    t += v[k];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = t;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int ws = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, ws, o);
+      if (lane >= o) ws += u;
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = ws;  // inclusive
+  }
+  __syncthreads();
+  int run = incl - t + (warp > 0 ? warp_sums[warp - 1] : 0);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) block_sums[blockIdx.x] = warp_sums[kScanThreads / 32 - 1];
+}
+
+// Level 3: add each tile's offset; out[n] = total.
+__global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ block_offsets,
+                           int nb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += block_offsets[i / kScanTile];
+  if (i == 0) out[n] = block_offsets[nb];
 }
 
 __global__ void k_rho_from_drho(const float* __restrict__ drho, float rho0,
@@ -131,24 +179,46 @@ cudaError_t launch_unpack_mask(const uint32_t* mask, int nx, int ny, int wpr, ui
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const int* in, int* out, int n, cudaStream_t stream) {
-  k_scan<<<1, 1024, 0, stream>>>(in, out, n);
-  count_launches(1);
+size_t scan_tmp_ints(int n) {
+  const size_t nb = (size_t)(n + kScanTile - 1) / kScanTile;
+  return 2 * nb + 2;
+}
+
+cudaError_t launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t stream) {
+  if (n <= kScanTile) {  // one level is enough
+    k_scan_chunked<<<1, 1024, 0, stream>>>(in, out, n);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  const int nb = (n + kScanTile - 1) / kScanTile;
+  int* sums = tmp;
+  int* offs = tmp + nb + 1;
+  k_scan_tiles<<<nb, kScanThreads, 0, stream>>>(in, out, n, sums);
+  k_scan_chunked<<<1, 1024, 0, stream>>>(sums, offs, nb);
+  k_scan_add<<<blocks_for(n, 256), 256, 0, stream>>>(out, n, offs, nb);
+  count_launches(3);
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_tiles(const uint32_t* mask, int nx, int ny, int wpr, int lattice,
-                               int* counts, TileRef* tiles, int* n_tiles, cudaStream_t stream) {
-  (void)nx;
-  const int tiles_y = (ny + kTileY - 1) / kTileY;
-  const int n = tiles_y * wpr;
-  int* flags = counts;
-  int* offsets = counts + n;  // counts holds 2n + 1 ints
-  k_tile_flags<<<blocks_for(n, 256), 256, 0, stream>>>(mask, ny, wpr, tiles_y, flags);
-  k_scan<<<1, 1024, 0, stream>>>(flags, offsets, n);
-  k_tile_scatter<<<blocks_for(n, 256), 256, 0, stream>>>(flags, offsets, tiles_y, wpr, lattice, tiles,
-                                                         n_tiles);
-  count_launches(3);
+size_t segment_capacity(int ny, int wpr) { return (size_t)(ny > 2 ? ny - 2 : 0) * wpr; }
+
+size_t segment_scratch_ints(int ny, int wpr) {
+  const int n = (int)segment_capacity(ny, wpr);
+  return 2 * (size_t)n + 1 + scan_tmp_ints(n);
+}
+
+cudaError_t launch_build_segments(const uint32_t* mask, int ny, int wpr, int lattice, int* scratch,
+                                  SegRef* segs, int* n_segs, cudaStream_t stream) {
+  const int n = (int)segment_capacity(ny, wpr);
+  int* flags = scratch;
+  int* offsets = scratch + n;         // n + 1
+  int* tmp = scratch + 2 * n + 1;     // scan_tmp_ints(n)
+  k_segment_flags<<<blocks_for(n, 256), 256, 0, stream>>>(mask, ny, wpr, flags);
+  count_launches(1);
+  cudaError_t e = launch_scan(flags, offsets, n, tmp, stream);
+  if (e != cudaSuccess) return e;
+  k_segment_scatter<<<blocks_for(n, 256), 256, 0, stream>>>(flags, offsets, ny, wpr, lattice, segs, n_segs);
+  count_launches(1);
   return cudaGetLastError();
 }
 
