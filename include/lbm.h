@@ -227,6 +227,41 @@ uint64_t lbm_kernel_launches(void);
 lbm_status lbm_kernel_time(lbm_handle h, int reset, double* ms, int64_t* launches,
                            int64_t* fluid_updates);
 
+/* Launch shape the handle's time steps use (warps per block, blocks): tuned
+ * on the handle's own lattice at its first solve of 256 steps or more.   */
+lbm_status lbm_step_config(lbm_handle h, int32_t* warps_per_block, int32_t* grid);
+
+/* ---- batches -------------------------------------------------------------
+ * Many candidate geometries (Sec. 2.3 applied to each) stepped together: one
+ * work-list over all members, one launch per time step, per optimiser
+ * iteration and per reduction for the whole batch.  Members may differ in
+ * size, tau, u_max, outlet rule, port scheme and re-initialisation; they
+ * share precision and residual_every.  Each member evolves exactly as it
+ * would in a handle of its own (same results, bit for bit).                */
+typedef struct lbm_batch_s* lbm_batch;
+
+/* params: host lbm_params[n]; cell_types: host array of n host pointers to
+ * uint8[ny_i][nx_i]; both copied.  Same geometry rules as a handle.        */
+lbm_status lbm_batch_create(int32_t n, const lbm_params* params, const uint8_t* const* cell_types,
+                            void* cuda_stream, lbm_batch* out);
+/* As lbm_solve for every member; out: host lbm_solve_result[n].          */
+lbm_status lbm_batch_solve(lbm_batch b, int64_t n_steps, lbm_solve_result* out);
+/* As lbm_optimize_step for every member; n_swap: host int32[n] (per member);
+ * out: host lbm_opt_result[n].                                            */
+lbm_status lbm_batch_optimize_step(lbm_batch b, const int32_t* n_swap, int64_t n_steps,
+                                   lbm_opt_result* out);
+/* As lbm_read_fields for member `member` (0 <= member < n).               */
+lbm_status lbm_batch_read_fields(lbm_batch b, int32_t member, uint32_t which, void* dst,
+                                 size_t dst_bytes, int dst_is_device);
+/* Every member back to its creation state.                                */
+lbm_status lbm_batch_reset(lbm_batch b);
+/* As lbm_kernel_time, for the batch's time steps (fluid_updates over all members). */
+lbm_status lbm_batch_kernel_time(lbm_batch b, int reset, double* ms, int64_t* launches,
+                                 int64_t* fluid_updates);
+/* As lbm_step_config.                                                    */
+lbm_status lbm_batch_step_config(lbm_batch b, int32_t* warps_per_block, int32_t* grid);
+void lbm_batch_destroy(lbm_batch b);
+
 /* Algorithmic memory traffic of one fluid-cell update of the stream-collide
  * kernel for a storage precision: 9 populations read and 9 written
  * (2 * 9 * sizeof(stored population)) plus the cell's mask bit (1/8 byte).  */

@@ -1,8 +1,16 @@
-// C ABI of the library (include/lbm.h): lattice handles, the solve loop of
-// Sec. 2.3 (steps 2-5) and field access.  Host code only: it validates
-// arguments, owns device memory, and enqueues the kernels of step.cu,
-// worklist.cu, reduce.cu and oc.cu on the handle's stream.  The repeated
-// stream-collide pairs are replayed from CUDA graphs captured once per handle.
+// C ABI of the library (include/lbm.h) and the engine behind it.
+//
+// An engine steps a set of lattices together: each member owns its
+// populations, mask and fields; the engine owns one descriptor table, one
+// row-segment work-list, one reduction block and one exchange scratch for the
+// whole set, so every stage of the loop of Sec. 2.3 (steps 2-5) is one launch
+// over all members.  A handle (lbm_create_geometry) is an engine of one
+// member, a batch (lbm_batch_create) an engine of many.  Host code only: it
+// validates arguments, owns device memory and enqueues the kernels of
+// step.cu, worklist.cu, reduce.cu and oc.cu on the engine's stream.  Repeated
+// stream-collide pairs are replayed from CUDA graphs captured once per
+// engine, after the launch shape has been tuned on the engine's own lattices.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -33,6 +41,14 @@ bool debug_sync() {
   return on;
 }
 
+static bool autotune_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("LBM_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 }  // namespace lbm
 
 using namespace lbm;
@@ -40,9 +56,6 @@ using namespace lbm;
 namespace {
 
 constexpr int kGraphPairs[3] = {64, 8, 1};
-// views[0]: the lattice; views[1]: same, moments into the *_prev fields;
-// views[2]: scratch fields of the selection test hook
-constexpr int kViews = 3;
 
 lbm_status fail(lbm_status s, const std::string& msg) {
   t_last_error = msg;
@@ -59,72 +72,42 @@ lbm_status fail(lbm_status s, const std::string& msg) {
 
 size_t storage_bytes(int precision) { return precision == LBM_F32 ? 4 : 2; }
 
-}  // namespace
-
-struct lbm_handle_s {
-  lbm_params p{};
-  int nx = 0, ny = 0, pitch = 0, wpr = 0;
-  int n_outlets = 0;
-  std::vector<int> outlet_start, outlet_len;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int sm_count = 0;
-  int grid = 1;
-  size_t plane = 0;
-
-  void* f = nullptr;
-  uint32_t* mask = nullptr;   // word (0, 0) of the padded mask
-  uint32_t* mask0 = nullptr;  // initial cell map, same layout
-  uint32_t* mask_base = nullptr;
-  uint32_t* mask0_base = nullptr;
-  size_t mask_bytes = 0;      // whole padded allocation
-  float *drho = nullptr, *ux = nullptr, *uy = nullptr, *ux_prev = nullptr, *uy_prev = nullptr;
-  float* u_in = nullptr;
-  int *d_outlet_start = nullptr, *d_outlet_len = nullptr;
-  LatticeView* views = nullptr;
-  LatticeView host_view{};
-  SegRef* segs = nullptr;   // row segments holding fluid cells
-  int* n_segs = nullptr;
-  int* seg_scratch = nullptr;
-  double* partials = nullptr;
-  double* result = nullptr;
-  unsigned long long* fluid_dev = nullptr;
-  uint8_t* cells_dev = nullptr;
-  float* dense_f = nullptr;
-  OcScratch oc{};
-
-  double* h_result = nullptr;  // pinned
-  int* h_info = nullptr;       // pinned
-  unsigned long long* h_count = nullptr;
-
-  cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // around the time steps of a solve
-  double step_ms = 0.0;
-  int64_t step_launches = 0, fluid_updates = 0;
-
-  int64_t steps_done = 0;
-  int64_t fluid_cells = 0;
-  bool solved = false;
-  std::vector<void*> allocations;
-};
-
-namespace {
-
 template <class T>
-cudaError_t dalloc(lbm_handle h, T** p, size_t bytes) {
+cudaError_t dalloc(std::vector<void*>& allocs, T** p, size_t bytes) {
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
   if (e == cudaSuccess) {
-    h->allocations.push_back(q);
+    allocs.push_back(q);
     *p = static_cast<T*>(q);
   }
   return e;
 }
 
+// One lattice: its device storage and host description.
+struct Member {
+  lbm_params p{};
+  int nx = 0, ny = 0, pitch = 0, wpr = 0;
+  size_t plane = 0;
+  std::vector<int> out_start, out_len;
+  void* f = nullptr;
+  uint32_t *mask_base = nullptr, *mask0_base = nullptr, *mask = nullptr, *mask0 = nullptr;
+  size_t mask_bytes = 0;
+  float *drho = nullptr, *ux = nullptr, *uy = nullptr, *ux_prev = nullptr, *uy_prev = nullptr;
+  float* u_in = nullptr;
+  int* d_out = nullptr;  // [LBM_MAX_OUTLETS] starts, then [LBM_MAX_OUTLETS] lengths
+  int64_t fluid_cells = 0;
+  int64_t steps_done = 0;
+  LatticeView view{};
+  std::vector<void*> allocs;
+  ~Member() {
+    for (void* q : allocs) cudaFree(q);
+  }
+};
+
 // Geometry rules of include/lbm.h; also finds the inlet runs (parabolic
 // profile of Sec. 3.3 per run) and the outlet runs.
-lbm_status check_and_describe(lbm_handle h, const uint8_t* cells, std::vector<float>& u_in) {
-  const int nx = h->nx, ny = h->ny;
+lbm_status check_and_describe(Member& m, const uint8_t* cells, std::vector<float>& u_in) {
+  const int nx = m.nx, ny = m.ny;
   for (int x = 0; x < nx; ++x)
     if (!cells[x] || !cells[(size_t)(ny - 1) * nx + x])
       return fail(LBM_ERR_GEOMETRY, "rows 0 and ny-1 must be solid");
@@ -144,71 +127,230 @@ lbm_status check_and_describe(lbm_handle h, const uint8_t* cells, std::vector<fl
     const int width = y - y_lo;
     for (int yy = y_lo; yy < y; ++yy) {
       const double s = ((double)(yy - y_lo) + 0.5) / (double)width;
-      u_in[yy] = (float)(4.0 * h->p.u_max * s * (1.0 - s));
+      u_in[yy] = (float)(4.0 * m.p.u_max * s * (1.0 - s));
     }
   }
-  h->outlet_start.clear();
-  h->outlet_len.clear();
+  m.out_start.clear();
+  m.out_len.clear();
   for (int y = 0; y < ny;) {
     if (cells[(size_t)y * nx + nx - 1]) { ++y; continue; }
     const int y_lo = y;
     while (y < ny && !cells[(size_t)y * nx + nx - 1]) ++y;
-    h->outlet_start.push_back(y_lo);
-    h->outlet_len.push_back(y - y_lo);
+    m.out_start.push_back(y_lo);
+    m.out_len.push_back(y - y_lo);
   }
-  h->n_outlets = (int)h->outlet_start.size();
-  if (h->n_outlets == 0) return fail(LBM_ERR_GEOMETRY, "no outlet cell in column nx-1");
-  if (h->n_outlets > LBM_MAX_OUTLETS) return fail(LBM_ERR_GEOMETRY, "more than LBM_MAX_OUTLETS outlets");
+  if (m.out_start.empty()) return fail(LBM_ERR_GEOMETRY, "no outlet cell in column nx-1");
+  if ((int)m.out_start.size() > LBM_MAX_OUTLETS) return fail(LBM_ERR_GEOMETRY, "more than LBM_MAX_OUTLETS outlets");
   return LBM_OK;
 }
 
-lbm_status run_plain_pairs(lbm_handle h, int64_t pairs);
+lbm_status check_params(const lbm_params& p) {
+  if (p.nx < 4 || p.ny < 3 || (p.nx % 2) != 0 || (int64_t)p.nx * p.ny >= (int64_t)1 << 31 ||
+      p.nx > (32 << kSegWordBits) || p.ny >= (1 << (31 - kSegWordBits)))
+    return fail(LBM_ERR_ARG, "nx must be even, 4 <= nx <= 131072, 3 <= ny < 524288, nx*ny < 2^31");
+  const size_t pitch = (size_t)(p.nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+  if (9 * pitch * (size_t)p.ny >= ((size_t)1 << 31))
+    return fail(LBM_ERR_ARG, "lattice too large: 9 * ny * pitch must stay below 2^31 elements");
+  if (!(p.tau > 0.5) || !std::isfinite(p.tau) || !std::isfinite(p.rho0) || !(p.rho0 > 0) ||
+      !std::isfinite(p.u_max))
+    return fail(LBM_ERR_ARG, "tau must be > 1/2, rho0 > 0, u_max finite");
+  if (p.outlet != LBM_OUT_CONST_RHO && p.outlet != LBM_OUT_NEUMANN) return fail(LBM_ERR_ARG, "outlet rule");
+  if (p.precision < LBM_F32 || p.precision > LBM_F16_SHIFTED) return fail(LBM_ERR_ARG, "precision");
+  if (p.reinit != LBM_REINIT_WARM && p.reinit != LBM_REINIT_COLD) return fail(LBM_ERR_ARG, "reinit");
+  if (p.residual_every < 0 || (p.residual_every % 2) != 0) return fail(LBM_ERR_ARG, "residual_every must be even");
+  if (p.ports != LBM_PORTS_REGULARIZED && p.ports != LBM_PORTS_ZOU_HE) return fail(LBM_ERR_ARG, "ports");
+  return LBM_OK;
+}
+
+// Allocate one member's storage and upload its cell map (packed on the device).
+lbm_status member_create(const lbm_params& p, const uint8_t* cells, uint8_t* cells_dev, cudaStream_t stream,
+                         Member** out) {
+  *out = nullptr;
+  lbm_status st = check_params(p);
+  if (st != LBM_OK) return st;
+  Member* m = new Member();
+  m->p = p;
+  m->nx = p.nx;
+  m->ny = p.ny;
+  m->pitch = (p.nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+  m->wpr = (p.nx + 31) / 32;
+  m->plane = (size_t)m->ny * m->pitch;
+  std::vector<float> u_in;
+  st = check_and_describe(*m, cells, u_in);
+  if (st != LBM_OK) {
+    delete m;
+    return st;
+  }
+#define CUM(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      delete m;                                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    }                                                                                    \
+  } while (0)
+  const size_t sb = storage_bytes(p.precision);
+  CUM(dalloc(m->allocs, &m->f, 9 * m->plane * sb));
+  m->mask_bytes = (size_t)mask_alloc_words(m->wpr, m->ny) * 4;
+  CUM(dalloc(m->allocs, &m->mask_base, m->mask_bytes));
+  CUM(dalloc(m->allocs, &m->mask0_base, m->mask_bytes));
+  for (float** a : {&m->drho, &m->ux, &m->uy, &m->ux_prev, &m->uy_prev})
+    CUM(dalloc(m->allocs, a, m->plane * 4));
+  CUM(dalloc(m->allocs, &m->u_in, (size_t)m->ny * 4));
+  CUM(dalloc(m->allocs, &m->d_out, 2 * LBM_MAX_OUTLETS * 4));
+  m->mask = m->mask_base + mask_origin(m->wpr);
+  m->mask0 = m->mask0_base + mask_origin(m->wpr);
+  CUM(cudaMemsetAsync(m->mask_base, 0xff, m->mask_bytes, stream));  // padding = wall
+  CUM(cudaMemsetAsync(m->mask0_base, 0xff, m->mask_bytes, stream));
+  std::vector<int> outs(2 * LBM_MAX_OUTLETS, 0);
+  std::copy(m->out_start.begin(), m->out_start.end(), outs.begin());
+  std::copy(m->out_len.begin(), m->out_len.end(), outs.begin() + LBM_MAX_OUTLETS);
+  // pageable sources: each call returns once its source has been staged
+  CUM(cudaMemcpyAsync(m->u_in, u_in.data(), (size_t)m->ny * 4, cudaMemcpyHostToDevice, stream));
+  CUM(cudaMemcpyAsync(m->d_out, outs.data(), outs.size() * 4, cudaMemcpyHostToDevice, stream));
+  CUM(cudaMemcpyAsync(cells_dev, cells, (size_t)m->nx * m->ny, cudaMemcpyHostToDevice, stream));
+  CUM(launch_pack_mask(cells_dev, m->nx, m->ny, m->wpr, m->mask0, stream));
+  CUM(cudaStreamSynchronize(stream));  // cells_dev is reused by the next member
+#undef CUM
+  LatticeView& v = m->view;
+  std::memset(&v, 0, sizeof(v));
+  v.f = m->f;
+  v.mask = m->mask;
+  v.drho = m->drho;
+  v.ux = m->ux;
+  v.uy = m->uy;
+  v.ux_prev = m->ux_prev;
+  v.uy_prev = m->uy_prev;
+  v.u_in = m->u_in;
+  v.out_start = m->d_out;
+  v.out_len = m->d_out + LBM_MAX_OUTLETS;
+  v.plane = (long long)m->plane;
+  v.f_elems = 9 * (long long)m->plane;
+  v.rho0d = p.rho0;
+  v.mu = p.rho0 * ((p.tau - 0.5) / 3.0);
+  v.nx = m->nx;
+  v.ny = m->ny;
+  v.pitch = m->pitch;
+  v.wpr = m->wpr;
+  v.omega = (float)(1.0 / p.tau);
+  v.rho0 = (float)p.rho0;
+  v.outlet_rule = p.outlet;
+  v.port_scheme = p.ports;
+  v.n_outlets = (int)m->out_start.size();
+  *out = m;
+  return LBM_OK;
+}
+
+}  // namespace
+
+// A set of lattices stepped together.
+struct Engine {
+  int precision = LBM_F32;
+  int residual_every = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sm_count = 0;
+  std::vector<Member*> m;
+  int n = 0;
+
+  LatticeView* views = nullptr;  // [n]
+  int* word_off = nullptr;       // [n + 1] all words (rows 0..ny-1)
+  int* seg_word_off = nullptr;   // [n + 1] interior-row words
+  int total_words = 0, total_seg_words = 0;
+  long long total_cells = 0;
+  SegRef* segs = nullptr;
+  int* n_segs = nullptr;
+  int* seg_scratch = nullptr;
+  double* partials = nullptr;
+  double* result = nullptr;
+  unsigned long long* fluid_dev = nullptr;
+  int* n_swap_dev = nullptr;
+  OcScratch oc{};
+  uint8_t* cells_dev = nullptr;  // largest member's cells
+  float* dense_f = nullptr;
+
+  double* h_result = nullptr;  // pinned [n * kResultDoubles]
+  int* h_info = nullptr;       // pinned [8 n]
+  unsigned long long* h_count = nullptr;  // pinned [n]
+  int* h_nswap = nullptr;      // pinned [n]
+
+  cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};
+  StepConfig step{kStepWarps, 1};
+  bool tuned = false;
+  cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+  double step_ms = 0.0;
+  int64_t step_launches = 0, fluid_updates = 0;
+  bool solved = false;
+  std::vector<void*> allocs;
+
+  ~Engine() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto& g : graphs)
+      if (g) cudaGraphExecDestroy(g);
+    for (Member* x : m) delete x;
+    for (void* q : allocs) cudaFree(q);
+    if (h_result) cudaFreeHost(h_result);
+    if (h_info) cudaFreeHost(h_info);
+    if (h_count) cudaFreeHost(h_count);
+    if (h_nswap) cudaFreeHost(h_nswap);
+    if (ev_begin) cudaEventDestroy(ev_begin);
+    if (ev_end) cudaEventDestroy(ev_end);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+struct lbm_handle_s {
+  Engine* e;
+};
+struct lbm_batch_s {
+  Engine* e;
+};
+
+namespace {
 
 // With LBM_DEBUG_SYNC=1: wait for the work just enqueued and name it on failure.
-#define DEBUG_SYNC(h, what)                                                              \
+#define DEBUG_SYNC(E, what)                                                              \
   do {                                                                                   \
     if (debug_sync() && !t_capturing) {                                                  \
-      cudaError_t e_ = cudaStreamSynchronize((h)->stream);                               \
+      cudaError_t e_ = cudaStreamSynchronize((E)->stream);                               \
       if (e_ != cudaSuccess) return fail(LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
     }                                                                                    \
   } while (0)
 
-lbm_status launch_pair(lbm_handle h, int moments_view) {
-  // moments_view: -1 none, 0 into the lattice fields, 1 into the *_prev fields
-  const int prec = h->p.precision;
-  CU(launch_stream_collide(prec, 0, 0, h->views, h->segs, h->n_segs, h->grid, h->stream));
-  DEBUG_SYNC(h, "stream-collide phase A");
-  const LatticeView* v = moments_view == 1 ? h->views + 1 : h->views;
-  CU(launch_stream_collide(prec, 1, moments_view >= 0 ? 1 : 0, v, h->segs, h->n_segs, h->grid,
-                           h->stream));
-  DEBUG_SYNC(h, moments_view >= 0 ? "stream-collide phase B with moments" : "stream-collide phase B");
+lbm_status launch_pair(Engine* E, int moments) {
+  // moments: 0 none, 1 into drho/ux/uy, 2 into drho/ux_prev/uy_prev
+  CU(launch_stream_collide(E->precision, 0, 0, E->views, E->segs, E->n_segs, E->step, E->stream));
+  DEBUG_SYNC(E, "stream-collide phase A");
+  CU(launch_stream_collide(E->precision, 1, moments, E->views, E->segs, E->n_segs, E->step, E->stream));
+  DEBUG_SYNC(E, "stream-collide phase B");
   return LBM_OK;
 }
 
-lbm_status ensure_graph(lbm_handle h, int which) {
-  if (h->graphs[which]) return LBM_OK;
+lbm_status ensure_graph(Engine* E, int which) {
+  if (E->graphs[which]) return LBM_OK;
   cudaGraph_t g = nullptr;
-  CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  CU(cudaStreamBeginCapture(E->stream, cudaStreamCaptureModeThreadLocal));
   t_capturing = true;
   lbm_status st = LBM_OK;
-  for (int k = 0; k < kGraphPairs[which] && st == LBM_OK; ++k) st = launch_pair(h, -1);
+  for (int k = 0; k < kGraphPairs[which] && st == LBM_OK; ++k) st = launch_pair(E, 0);
   t_capturing = false;
-  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  cudaError_t e = cudaStreamEndCapture(E->stream, &g);
   if (st != LBM_OK) {
     if (g) cudaGraphDestroy(g);
     return st;
   }
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&h->graphs[which], g, 0);
+  e = cudaGraphInstantiate(&E->graphs[which], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   return LBM_OK;
 }
 
-lbm_status run_plain_pairs(lbm_handle h, int64_t pairs) {
+lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
   if (debug_sync()) {
     for (int64_t k = 0; k < pairs; ++k) {
-      lbm_status st = launch_pair(h, -1);
+      lbm_status st = launch_pair(E, 0);
       if (st != LBM_OK) return st;
     }
     return LBM_OK;
@@ -217,10 +359,10 @@ lbm_status run_plain_pairs(lbm_handle h, int64_t pairs) {
     const int64_t chunk = kGraphPairs[which];
     const int64_t reps = pairs / chunk;
     if (reps == 0) continue;
-    lbm_status st = ensure_graph(h, which);
+    lbm_status st = ensure_graph(E, which);
     if (st != LBM_OK) return st;
     for (int64_t r = 0; r < reps; ++r) {
-      CU(cudaGraphLaunch(h->graphs[which], h->stream));
+      CU(cudaGraphLaunch(E->graphs[which], E->stream));
       count_launches(2 * chunk);
     }
     pairs -= reps * chunk;
@@ -228,76 +370,389 @@ lbm_status run_plain_pairs(lbm_handle h, int64_t pairs) {
   return LBM_OK;
 }
 
-lbm_status rebuild_worklist(lbm_handle h) {
-  CU(launch_build_segments(h->mask, h->ny, h->wpr, 0, h->seg_scratch, h->segs, h->n_segs, h->stream));
-  CU(launch_count_fluid(h->mask, h->nx, h->ny, h->wpr, h->fluid_dev, h->stream));
+// Work-list and fluid counts after any change of a cell map.
+lbm_status rebuild_worklist(Engine* E) {
+  CU(launch_build_segments(E->views, E->seg_word_off, E->n, E->total_seg_words, E->seg_scratch, E->segs,
+                           E->n_segs, E->stream));
+  CU(launch_count_fluid(E->views, E->word_off, E->n, E->total_words, E->fluid_dev, E->stream));
+  DEBUG_SYNC(E, "work-list");
   return LBM_OK;
 }
 
-lbm_status initial_state(lbm_handle h) {
-  const size_t fb = 9 * h->plane * storage_bytes(h->p.precision);
-  CU(cudaMemcpyAsync(h->mask_base, h->mask0_base, h->mask_bytes, cudaMemcpyDeviceToDevice, h->stream));
-  CU(cudaMemsetAsync(h->f, 0, fb, h->stream));  // shifted equilibrium at rest: g = 0
-  const size_t fl = h->plane * sizeof(float);
-  for (float* a : {h->drho, h->ux, h->uy, h->ux_prev, h->uy_prev}) CU(cudaMemsetAsync(a, 0, fl, h->stream));
-  lbm_status st = rebuild_worklist(h);
+// Largest grid for one block shape: every segment its own warp, but never
+// more blocks than fit on the device at once.
+StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale) {
+  const int bps = stream_collide_blocks_per_sm(E->precision, 0, 0, wpb);
+  const long long cap = (long long)E->sm_count * bps * blocks_per_sm_scale;
+  const long long need = ((long long)E->total_seg_words + wpb - 1) / wpb;
+  StepConfig c;
+  c.warps_per_block = wpb;
+  c.grid = (int)std::max<long long>(1, std::min(need, cap));
+  return c;
+}
+
+// Pick the step launch shape by timing candidate shapes on the engine's own
+// lattices.  The populations are saved and restored around the trials, and
+// every shape computes the same values per cell, so tuning changes no result.
+lbm_status autotune(Engine* E) {
+  E->tuned = true;
+  E->step = shape(E, kStepWarps, 1);
+  if (!autotune_enabled() || debug_sync()) return LBM_OK;
+  const size_t sb = storage_bytes(E->precision);
+  std::vector<void*> backups(E->n, nullptr);
+  for (int i = 0; i < E->n; ++i) {
+    const size_t bytes = 9 * E->m[i]->plane * sb;
+    if (cudaMalloc(&backups[i], bytes) != cudaSuccess) {  // no room: keep the default shape
+      for (void* b : backups) cudaFree(b);
+      cudaGetLastError();
+      return LBM_OK;
+    }
+    CU(cudaMemcpyAsync(backups[i], E->m[i]->f, bytes, cudaMemcpyDeviceToDevice, E->stream));
+  }
+  std::vector<StepConfig> cand;
+  for (int wpb : {4, 8, 16})
+    for (int scale : {1, 2}) {
+      StepConfig c = shape(E, wpb, scale);
+      bool dup = false;
+      for (auto& d : cand) dup |= (d.warps_per_block == c.warps_per_block && d.grid == c.grid);
+      if (!dup) cand.push_back(c);
+    }
+  cudaEvent_t a, b;
+  CU(cudaEventCreate(&a));
+  CU(cudaEventCreate(&b));
+  float best = 1e30f;
+  StepConfig best_cfg = E->step;
+  lbm_status st = LBM_OK;
+  for (int rep = 0; rep < 2 && st == LBM_OK; ++rep) {  // first pass warms up
+    for (const StepConfig& c : cand) {
+      E->step = c;
+      cudaEventRecord(a, E->stream);
+      for (int k = 0; k < 16 && st == LBM_OK; ++k) st = launch_pair(E, 0);
+      cudaEventRecord(b, E->stream);
+      if (cudaEventSynchronize(b) != cudaSuccess) st = fail(LBM_ERR_CUDA, "autotune timing");
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep == 1 && ms < best) {
+        best = ms;
+        best_cfg = c;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  for (int i = 0; i < E->n; ++i) {
+    cudaMemcpyAsync(E->m[i]->f, backups[i], 9 * E->m[i]->plane * sb, cudaMemcpyDeviceToDevice, E->stream);
+  }
+  cudaStreamSynchronize(E->stream);
+  for (void* q : backups) cudaFree(q);
+  E->step = best_cfg;
+  for (auto& g : E->graphs)  // captured with the previous shape
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  return st;
+}
+
+lbm_status initial_state(Engine* E) {
+  const size_t sb = storage_bytes(E->precision);
+  for (Member* m : E->m) {
+    CU(cudaMemcpyAsync(m->mask_base, m->mask0_base, m->mask_bytes, cudaMemcpyDeviceToDevice, E->stream));
+    CU(cudaMemsetAsync(m->f, 0, 9 * m->plane * sb, E->stream));  // shifted equilibrium at rest: g = 0
+    for (float* a : {m->drho, m->ux, m->uy, m->ux_prev, m->uy_prev})
+      CU(cudaMemsetAsync(a, 0, m->plane * sizeof(float), E->stream));
+    m->steps_done = 0;
+  }
+  lbm_status st = rebuild_worklist(E);
   if (st != LBM_OK) return st;
-  CU(cudaMemcpyAsync(h->h_count, h->fluid_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                     h->stream));
-  CU(cudaStreamSynchronize(h->stream));
-  h->fluid_cells = (int64_t)*h->h_count;
-  h->steps_done = 0;
-  h->solved = false;
+  CU(cudaMemcpyAsync(E->h_count, E->fluid_dev, sizeof(unsigned long long) * E->n, cudaMemcpyDeviceToHost,
+                     E->stream));
+  CU(cudaStreamSynchronize(E->stream));
+  for (int i = 0; i < E->n; ++i) E->m[i]->fluid_cells = (int64_t)E->h_count[i];
+  E->solved = false;
+  return LBM_OK;
+}
+
+lbm_status engine_create(int n, const lbm_params* params, const uint8_t* const* cells, void* cuda_stream,
+                         Engine** out) {
+  *out = nullptr;
+  if (n < 1) return fail(LBM_ERR_ARG, "need at least one lattice");
+  for (int i = 1; i < n; ++i)
+    if (params[i].precision != params[0].precision || params[i].residual_every != params[0].residual_every)
+      return fail(LBM_ERR_ARG, "all lattices of a batch share precision and residual_every");
+  for (int i = 0; i < n; ++i)
+    if (!cells[i]) return fail(LBM_ERR_ARG, "cell_types is NULL");
+  Engine* E = new Engine();
+  E->precision = params[0].precision;
+  E->residual_every = params[0].residual_every;
+  E->n = n;
+#define CUE(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      delete E;                                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    }                                                                                    \
+  } while (0)
+  int dev = 0;
+  CUE(cudaGetDevice(&dev));
+  CUE(cudaDeviceGetAttribute(&E->sm_count, cudaDevAttrMultiProcessorCount, dev));
+  if (cuda_stream) {
+    E->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    CUE(cudaStreamCreateWithFlags(&E->stream, cudaStreamNonBlocking));
+    E->own_stream = true;
+  }
+  long long max_cells = 0;
+  for (int i = 0; i < n; ++i) max_cells = std::max<long long>(max_cells, (long long)params[i].nx * params[i].ny);
+  for (int i = 0; i < n; ++i)
+    if (check_params(params[i]) != LBM_OK) {
+      delete E;
+      return LBM_ERR_ARG;
+    }
+  CUE(dalloc(E->allocs, &E->cells_dev, (size_t)max_cells));
+  CUE(dalloc(E->allocs, &E->dense_f, (size_t)max_cells * 4));
+  for (int i = 0; i < n; ++i) {
+    Member* mb = nullptr;
+    lbm_status st = member_create(params[i], cells[i], E->cells_dev, E->stream, &mb);
+    if (st != LBM_OK) {
+      delete E;
+      return st;
+    }
+    E->m.push_back(mb);
+  }
+  // set-level layout
+  std::vector<int> woff(n + 1, 0), swoff(n + 1, 0);
+  long long sel = 0, words = 0, swords = 0;
+  for (int i = 0; i < n; ++i) {
+    Member* mb = E->m[i];
+    mb->view.word_off = (int)words;
+    mb->view.seg_word_off = (int)swords;
+    mb->view.sel_off = (int)sel;
+    words += (long long)mb->ny * mb->wpr;
+    swords += (long long)(mb->ny - 2) * mb->wpr;
+    sel += sel_capacity(mb->nx, mb->ny);
+    E->total_cells += (long long)mb->nx * mb->ny;
+    woff[i + 1] = (int)words;
+    swoff[i + 1] = (int)swords;
+  }
+  if (words >= (1ll << 31) || sel >= (1ll << 31) || E->total_cells >= (1ll << 31)) {
+    delete E;
+    return fail(LBM_ERR_ARG, "batch too large: total cells must stay below 2^31");
+  }
+  E->total_words = (int)words;
+  E->total_seg_words = (int)swords;
+  CUE(dalloc(E->allocs, &E->views, sizeof(LatticeView) * n));
+  CUE(dalloc(E->allocs, &E->word_off, sizeof(int) * (n + 1)));
+  CUE(dalloc(E->allocs, &E->seg_word_off, sizeof(int) * (n + 1)));
+  CUE(dalloc(E->allocs, &E->segs, sizeof(SegRef) * std::max(1, E->total_seg_words)));
+  CUE(dalloc(E->allocs, &E->n_segs, sizeof(int)));
+  CUE(dalloc(E->allocs, &E->seg_scratch, segment_scratch_ints(E->total_seg_words) * sizeof(int)));
+  CUE(dalloc(E->allocs, &E->partials, sizeof(double) * 2 * kResidualBlocks * n));
+  CUE(dalloc(E->allocs, &E->result, sizeof(double) * kResultDoubles * n));
+  CUE(dalloc(E->allocs, &E->fluid_dev, sizeof(unsigned long long) * n));
+  CUE(dalloc(E->allocs, &E->n_swap_dev, sizeof(int) * n));
+  OcScratch& oc = E->oc;
+  CUE(dalloc(E->allocs, &oc.cnt_f, (size_t)words * 4));
+  CUE(dalloc(E->allocs, &oc.cnt_s, (size_t)words * 4));
+  CUE(dalloc(E->allocs, &oc.off_f, (size_t)(words + 1) * 4));
+  CUE(dalloc(E->allocs, &oc.off_s, (size_t)(words + 1) * 4));
+  CUE(dalloc(E->allocs, &oc.key_f, (size_t)E->total_cells * 8));
+  CUE(dalloc(E->allocs, &oc.key_s, (size_t)E->total_cells * 8));
+  CUE(dalloc(E->allocs, &oc.idx_f, (size_t)E->total_cells * 4));
+  CUE(dalloc(E->allocs, &oc.idx_s, (size_t)E->total_cells * 4));
+  CUE(dalloc(E->allocs, &oc.sel_f, (size_t)sel * 4));
+  CUE(dalloc(E->allocs, &oc.sel_s, (size_t)sel * 4));
+  CUE(dalloc(E->allocs, &oc.info, (size_t)8 * n * 4));
+  CUE(dalloc(E->allocs, &oc.scan_tmp, scan_tmp_ints(words) * 4));
+  CUE(cudaMallocHost((void**)&E->h_result, sizeof(double) * kResultDoubles * n));
+  CUE(cudaMallocHost((void**)&E->h_info, sizeof(int) * 8 * n));
+  CUE(cudaMallocHost((void**)&E->h_count, sizeof(unsigned long long) * n));
+  CUE(cudaMallocHost((void**)&E->h_nswap, sizeof(int) * n));
+  CUE(cudaEventCreate(&E->ev_begin));
+  CUE(cudaEventCreate(&E->ev_end));
+  std::vector<LatticeView> vs(n);
+  for (int i = 0; i < n; ++i) vs[i] = E->m[i]->view;
+  CUE(cudaMemcpyAsync(E->views, vs.data(), sizeof(LatticeView) * n, cudaMemcpyHostToDevice, E->stream));
+  CUE(cudaMemcpyAsync(E->word_off, woff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, E->stream));
+  CUE(cudaMemcpyAsync(E->seg_word_off, swoff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, E->stream));
+#undef CUE
+  E->step = shape(E, kStepWarps, 1);
+  lbm_status st = initial_state(E);
+  if (st != LBM_OK) {
+    delete E;
+    return st;
+  }
+  *out = E;
   return LBM_OK;
 }
 
 // after the stream has been synchronised: add the steps' device time
-void account_steps(lbm_handle h, int64_t n_steps) {
+void account_steps(Engine* E, int64_t n_steps) {
   float ms = 0.0f;
-  if (cudaEventElapsedTime(&ms, h->ev_begin, h->ev_end) == cudaSuccess) h->step_ms += ms;
-  h->step_launches += n_steps;
-  h->fluid_updates += n_steps * h->fluid_cells;
+  if (cudaEventElapsedTime(&ms, E->ev_begin, E->ev_end) == cudaSuccess) E->step_ms += ms;
+  E->step_launches += n_steps;
+  for (Member* m : E->m) E->fluid_updates += n_steps * m->fluid_cells;
 }
 
-void fill_result(lbm_handle h, lbm_solve_result* out) {
-  const double* r = h->h_result;
+void fill_result(Engine* E, int i, lbm_solve_result* out) {
+  const double* r = E->h_result + (size_t)i * kResultDoubles;
+  const Member* m = E->m[i];
   std::memset(out, 0, sizeof(*out));
   out->dp = r[0];
   out->m_in = r[1];
   out->residual = r[2];
-  out->n_outlets = h->n_outlets;
+  out->n_outlets = (int)m->out_start.size();
   out->theta = r[8];
   out->dg = r[9];
-  for (int j = 0; j < h->n_outlets; ++j) out->m_out[j] = r[10 + j];
-  out->steps_done = h->steps_done;
-  out->fluid_cells = h->fluid_cells;
+  for (int j = 0; j < out->n_outlets; ++j) out->m_out[j] = r[10 + j];
+  out->steps_done = m->steps_done;
+  out->fluid_cells = m->fluid_cells;
 }
 
 // Enqueue n_steps (even) and the reductions; copy the results to pinned host
 // memory.  The caller synchronises.
-lbm_status enqueue_solve(lbm_handle h, int64_t n_steps) {
-  const int K = h->p.residual_every;
+lbm_status enqueue_solve(Engine* E, int64_t n_steps) {
+  if (!E->tuned && n_steps >= 256) {
+    lbm_status st = autotune(E);
+    if (st != LBM_OK) return st;
+  }
+  const int K = E->residual_every;
   const bool with_res = K >= 2 && (K % 2) == 0 && n_steps >= (int64_t)K + 2;
   lbm_status st;
-  CU(cudaEventRecord(h->ev_begin, h->stream));
+  CU(cudaEventRecord(E->ev_begin, E->stream));
   if (with_res) {
-    if ((st = run_plain_pairs(h, (n_steps - K) / 2 - 1)) != LBM_OK) return st;
-    if ((st = launch_pair(h, 1)) != LBM_OK) return st;
-    if ((st = run_plain_pairs(h, K / 2 - 1)) != LBM_OK) return st;
+    if ((st = run_plain_pairs(E, (n_steps - K) / 2 - 1)) != LBM_OK) return st;
+    if ((st = launch_pair(E, 2)) != LBM_OK) return st;
+    if ((st = run_plain_pairs(E, K / 2 - 1)) != LBM_OK) return st;
   } else {
-    if ((st = run_plain_pairs(h, n_steps / 2 - 1)) != LBM_OK) return st;
+    if ((st = run_plain_pairs(E, n_steps / 2 - 1)) != LBM_OK) return st;
   }
-  if ((st = launch_pair(h, 0)) != LBM_OK) return st;
-  CU(cudaEventRecord(h->ev_end, h->stream));
+  if ((st = launch_pair(E, 1)) != LBM_OK) return st;
+  CU(cudaEventRecord(E->ev_end, E->stream));
   if (with_res) {
-    CU(launch_residual_partials(h->views, h->ux_prev, h->uy_prev, 0, h->partials, h->stream));
-    DEBUG_SYNC(h, "residual partials");
+    CU(launch_residual_partials(E->views, E->n, E->partials, E->stream));
+    DEBUG_SYNC(E, "residual partials");
   }
-  CU(launch_finalize(h->views, 0, h->d_outlet_start, h->d_outlet_len, h->n_outlets, h->partials,
-                     with_res ? 1 : 0, h->result, h->stream));
-  DEBUG_SYNC(h, "finalize");
-  CU(cudaMemcpyAsync(h->h_result, h->result, kResultDoubles * sizeof(double), cudaMemcpyDeviceToHost,
-                     h->stream));
+  CU(launch_finalize(E->views, E->n, E->partials, with_res ? 1 : 0, E->result, E->stream));
+  DEBUG_SYNC(E, "finalize");
+  CU(cudaMemcpyAsync(E->h_result, E->result, sizeof(double) * kResultDoubles * E->n, cudaMemcpyDeviceToHost,
+                     E->stream));
+  return LBM_OK;
+}
+
+lbm_status engine_solve(Engine* E, int64_t n_steps, lbm_solve_result* out) {
+  if (n_steps < 2 || (n_steps % 2) != 0) return fail(LBM_ERR_ARG, "n_steps must be even and >= 2");
+  lbm_status st = enqueue_solve(E, n_steps);
+  if (st != LBM_OK) return st;
+  CU(cudaStreamSynchronize(E->stream));
+  for (Member* m : E->m) m->steps_done += n_steps;
+  E->solved = true;
+  account_steps(E, n_steps);
+  bool bad = false;
+  for (int i = 0; i < E->n; ++i) {
+    fill_result(E, i, out + i);
+    bad |= E->h_result[(size_t)i * kResultDoubles + 7] != 0.0;
+  }
+  if (bad) return fail(LBM_ERR_DIVERGED, "non-finite pressure drop, flow rate or residual");
+  return LBM_OK;
+}
+
+lbm_status engine_optimize(Engine* E, const int32_t* n_swap, int64_t n_steps, lbm_opt_result* out) {
+  if (n_steps < 2 || (n_steps % 2) != 0) return fail(LBM_ERR_ARG, "n_steps must be even and >= 2");
+  for (int i = 0; i < E->n; ++i)
+    if (n_swap[i] < 0) return fail(LBM_ERR_ARG, "n_swap must be >= 0");
+  if (!E->solved) return fail(LBM_ERR_ARG, "an exchange needs a field: solve first");
+  for (int i = 0; i < E->n; ++i) E->h_nswap[i] = n_swap[i];
+  CU(cudaMemcpyAsync(E->n_swap_dev, E->h_nswap, sizeof(int) * E->n, cudaMemcpyHostToDevice, E->stream));
+  CU(launch_oc_select(E->views, E->word_off, E->n, E->total_words, E->n_swap_dev, E->oc, E->stream));
+  DEBUG_SYNC(E, "selection");
+  CU(launch_oc_apply(E->precision, E->views, E->n, E->oc, E->stream));
+  DEBUG_SYNC(E, "exchange");
+  const size_t sb = storage_bytes(E->precision);
+  for (Member* m : E->m)
+    if (m->p.reinit == LBM_REINIT_COLD) CU(cudaMemsetAsync(m->f, 0, 9 * m->plane * sb, E->stream));
+  lbm_status st = rebuild_worklist(E);
+  if (st != LBM_OK) return st;
+  CU(cudaMemcpyAsync(E->h_info, E->oc.info, sizeof(int) * 8 * E->n, cudaMemcpyDeviceToHost, E->stream));
+  CU(cudaMemcpyAsync(E->h_count, E->fluid_dev, sizeof(unsigned long long) * E->n, cudaMemcpyDeviceToHost,
+                     E->stream));
+  st = enqueue_solve(E, n_steps);
+  if (st != LBM_OK) return st;
+  CU(cudaStreamSynchronize(E->stream));
+  bool nan = false, count_changed = false, bad = false;
+  for (int i = 0; i < E->n; ++i) {
+    Member* m = E->m[i];
+    m->steps_done += n_steps;
+    const int64_t before = m->fluid_cells;
+    m->fluid_cells = (int64_t)E->h_count[i];
+    count_changed |= m->fluid_cells != before;
+    nan |= E->h_info[8 * i + 3] != 0;
+    bad |= E->h_result[(size_t)i * kResultDoubles + 7] != 0.0;
+  }
+  account_steps(E, n_steps);
+  for (int i = 0; i < E->n; ++i) {
+    std::memset(out + i, 0, sizeof(lbm_opt_result));
+    out[i].n_swapped = E->h_info[8 * i];
+    out[i].fluid_count = E->m[i]->fluid_cells;
+    fill_result(E, i, &out[i].solve);
+  }
+  if (nan) return fail(LBM_ERR_DIVERGED, "a dynamic-pressure or stress score is NaN");
+  if (count_changed) return fail(LBM_ERR_CUDA, "fluid cell count changed by the exchange");
+  if (bad) return fail(LBM_ERR_DIVERGED, "non-finite pressure drop, flow rate or residual");
+  return LBM_OK;
+}
+
+lbm_status engine_read(Engine* E, int i, uint32_t which, void* dst, size_t dst_bytes) {
+  if (i < 0 || i >= E->n) return fail(LBM_ERR_ARG, "member out of range");
+  if (!dst) return fail(LBM_ERR_ARG, "dst is NULL");
+  Member* m = E->m[i];
+  const size_t nx = m->nx, ny = m->ny, ncell = nx * ny;
+  const size_t sb = storage_bytes(E->precision);
+  switch (which) {
+    case LBM_FIELD_MASK:
+      if (dst_bytes < ncell) return fail(LBM_ERR_ARG, "dst too small");
+      CU(launch_unpack_mask(m->mask, m->nx, m->ny, m->wpr, E->cells_dev, E->stream));
+      CU(cudaMemcpyAsync(dst, E->cells_dev, ncell, cudaMemcpyDefault, E->stream));
+      break;
+    case LBM_FIELD_RHO:
+      if (dst_bytes < ncell * 4) return fail(LBM_ERR_ARG, "dst too small");
+      CU(launch_rho_from_drho(m->drho, (float)m->p.rho0, m->mask, m->nx, m->ny, m->pitch, m->wpr, E->dense_f,
+                              E->stream));
+      CU(cudaMemcpyAsync(dst, E->dense_f, ncell * 4, cudaMemcpyDefault, E->stream));
+      break;
+    case LBM_FIELD_DRHO:
+    case LBM_FIELD_UX:
+    case LBM_FIELD_UY: {
+      if (dst_bytes < ncell * 4) return fail(LBM_ERR_ARG, "dst too small");
+      const float* src = which == LBM_FIELD_DRHO ? m->drho : which == LBM_FIELD_UX ? m->ux : m->uy;
+      CU(cudaMemcpy2DAsync(dst, nx * 4, src, (size_t)m->pitch * 4, nx * 4, ny, cudaMemcpyDefault, E->stream));
+      break;
+    }
+    case LBM_FIELD_POPS:
+      if (dst_bytes < 9 * ncell * sb) return fail(LBM_ERR_ARG, "dst too small");
+      for (int k = 0; k < 9; ++k)
+        CU(cudaMemcpy2DAsync(static_cast<char*>(dst) + k * ncell * sb, nx * sb,
+                             static_cast<const char*>(m->f) + k * m->plane * sb, (size_t)m->pitch * sb, nx * sb,
+                             ny, cudaMemcpyDefault, E->stream));
+      break;
+    default:
+      return fail(LBM_ERR_ARG, "which must be exactly one LBM_FIELD_* value");
+  }
+  CU(cudaStreamSynchronize(E->stream));
+  return LBM_OK;
+}
+
+lbm_status engine_kernel_time(Engine* E, int reset, double* ms, int64_t* launches, int64_t* fluid_updates) {
+  if (ms) *ms = E->step_ms;
+  if (launches) *launches = E->step_launches;
+  if (fluid_updates) *fluid_updates = E->fluid_updates;
+  if (reset) {
+    E->step_ms = 0.0;
+    E->step_launches = 0;
+    E->fluid_updates = 0;
+  }
   return LBM_OK;
 }
 
@@ -327,18 +782,11 @@ double lbm_bytes_per_fluid_update(int32_t precision) {
   return 2.0 * 9.0 * (double)storage_bytes(precision) + 1.0 / 8.0;
 }
 
+// ---- single lattice ----------------------------------------------------------
+
 void lbm_destroy(lbm_handle h) {
   if (!h) return;
-  if (h->stream) cudaStreamSynchronize(h->stream);
-  for (auto& g : h->graphs)
-    if (g) cudaGraphExecDestroy(g);
-  for (void* p : h->allocations) cudaFree(p);
-  if (h->h_result) cudaFreeHost(h->h_result);
-  if (h->h_info) cudaFreeHost(h->h_info);
-  if (h->h_count) cudaFreeHost(h->h_count);
-  if (h->ev_begin) cudaEventDestroy(h->ev_begin);
-  if (h->ev_end) cudaEventDestroy(h->ev_end);
-  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h->e;
   delete h;
 }
 
@@ -347,260 +795,60 @@ lbm_status lbm_create_geometry(const lbm_params* params, const uint8_t* cell_typ
   if (!out) return fail(LBM_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!params || !cell_types) return fail(LBM_ERR_ARG, "params or cell_types is NULL");
-  const lbm_params& p = *params;
-  if (p.nx < 4 || p.ny < 3 || (p.nx % 2) != 0 || (int64_t)p.nx * p.ny >= (int64_t)1 << 31 ||
-      p.nx > (32 << kSegWordBits) || p.ny >= (1 << (31 - kSegWordBits)))
-    return fail(LBM_ERR_ARG, "nx must be even, 4 <= nx <= 131072, 3 <= ny < 524288, nx*ny < 2^31");
-  if (!(p.tau > 0.5) || !std::isfinite(p.tau) || !std::isfinite(p.rho0) || !(p.rho0 > 0) ||
-      !std::isfinite(p.u_max))
-    return fail(LBM_ERR_ARG, "tau must be > 1/2, rho0 > 0, u_max finite");
-  if (p.outlet != LBM_OUT_CONST_RHO && p.outlet != LBM_OUT_NEUMANN) return fail(LBM_ERR_ARG, "outlet rule");
-  if (p.precision < LBM_F32 || p.precision > LBM_F16_SHIFTED) return fail(LBM_ERR_ARG, "precision");
-  if (p.reinit != LBM_REINIT_WARM && p.reinit != LBM_REINIT_COLD) return fail(LBM_ERR_ARG, "reinit");
-  if (p.residual_every < 0 || (p.residual_every % 2) != 0) return fail(LBM_ERR_ARG, "residual_every must be even");
-  if (p.ports != LBM_PORTS_REGULARIZED && p.ports != LBM_PORTS_ZOU_HE) return fail(LBM_ERR_ARG, "ports");
-
-  lbm_handle h = new lbm_handle_s();
-  h->p = p;
-  h->nx = p.nx;
-  h->ny = p.ny;
-  h->pitch = (p.nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
-  h->wpr = (p.nx + 31) / 32;
-  h->plane = (size_t)h->ny * h->pitch;
-  if (9 * h->plane >= ((size_t)1 << 31)) {
-    delete h;
-    return fail(LBM_ERR_ARG, "lattice too large: 9 * ny * pitch must stay below 2^31 elements");
-  }
-  std::vector<float> u_in;
-  lbm_status st = check_and_describe(h, cell_types, u_in);
-  if (st != LBM_OK) {
-    delete h;
-    return st;
-  }
-#define CUH(call)                                                                        \
-  do {                                                                                   \
-    cudaError_t e_ = (call);                                                             \
-    if (e_ != cudaSuccess) {                                                             \
-      lbm_destroy(h);                                                                    \
-      return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,         \
-                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
-    }                                                                                    \
-  } while (0)
-  int dev = 0;
-  CUH(cudaGetDevice(&dev));
-  CUH(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
-  if (cuda_stream) {
-    h->stream = static_cast<cudaStream_t>(cuda_stream);
-  } else {
-    CUH(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
-    h->own_stream = true;
-  }
-  const size_t nx = h->nx, ny = h->ny, ncell = nx * ny, nwords = ny * h->wpr;
-  const size_t sb = storage_bytes(p.precision);
-  CUH(dalloc(h, &h->f, 9 * h->plane * sb));
-  h->mask_bytes = (size_t)mask_alloc_words(h->wpr, h->ny) * 4;
-  CUH(dalloc(h, &h->mask_base, h->mask_bytes));
-  CUH(dalloc(h, &h->mask0_base, h->mask_bytes));
-  CUH(cudaMemsetAsync(h->mask_base, 0xff, h->mask_bytes, h->stream));   // padding = wall
-  CUH(cudaMemsetAsync(h->mask0_base, 0xff, h->mask_bytes, h->stream));
-  h->mask = h->mask_base + mask_origin(h->wpr);
-  h->mask0 = h->mask0_base + mask_origin(h->wpr);
-  for (float** a : {&h->drho, &h->ux, &h->uy, &h->ux_prev, &h->uy_prev}) CUH(dalloc(h, a, h->plane * 4));
-  CUH(dalloc(h, &h->u_in, ny * 4));
-  CUH(dalloc(h, &h->d_outlet_start, LBM_MAX_OUTLETS * 4));
-  CUH(dalloc(h, &h->d_outlet_len, LBM_MAX_OUTLETS * 4));
-  CUH(dalloc(h, &h->views, kViews * sizeof(LatticeView)));
-  const size_t nseg_cap = segment_capacity(h->ny, h->wpr);
-  CUH(dalloc(h, &h->segs, nseg_cap * sizeof(SegRef)));
-  CUH(dalloc(h, &h->n_segs, sizeof(int)));
-  CUH(dalloc(h, &h->seg_scratch, segment_scratch_ints(h->ny, h->wpr) * sizeof(int)));
-  CUH(dalloc(h, &h->partials, 2 * kResidualBlocks * sizeof(double)));
-  CUH(dalloc(h, &h->result, kResultDoubles * sizeof(double)));
-  CUH(dalloc(h, &h->fluid_dev, sizeof(unsigned long long)));
-  CUH(dalloc(h, &h->cells_dev, ncell));
-  CUH(dalloc(h, &h->dense_f, ncell * 4));
-  OcScratch& oc = h->oc;
-  CUH(dalloc(h, &oc.cnt_f, nwords * 4));
-  CUH(dalloc(h, &oc.cnt_s, nwords * 4));
-  CUH(dalloc(h, &oc.off_f, (nwords + 1) * 4));
-  CUH(dalloc(h, &oc.off_s, (nwords + 1) * 4));
-  CUH(dalloc(h, &oc.key_f, ncell * 8));
-  CUH(dalloc(h, &oc.key_s, ncell * 8));
-  CUH(dalloc(h, &oc.idx_f, ncell * 4));
-  CUH(dalloc(h, &oc.idx_s, ncell * 4));
-  oc.cap = (int)(ncell / 2 + 1);
-  CUH(dalloc(h, &oc.sel_f, (size_t)oc.cap * 4));
-  CUH(dalloc(h, &oc.sel_s, (size_t)oc.cap * 4));
-  CUH(dalloc(h, &oc.info, 8 * 4));
-  CUH(dalloc(h, &oc.scan_tmp, scan_tmp_ints((int)nwords) * 4));
-  CUH(cudaMallocHost((void**)&h->h_result, kResultDoubles * sizeof(double)));
-  CUH(cudaMallocHost((void**)&h->h_info, 8 * sizeof(int)));
-  CUH(cudaMallocHost((void**)&h->h_count, sizeof(unsigned long long)));
-  CUH(cudaEventCreate(&h->ev_begin));
-  CUH(cudaEventCreate(&h->ev_end));
-
-  // views: [0] lattice, [1] moments into *_prev, [2] hook scratch (filled on use)
-  LatticeView v{};
-  v.f = h->f;
-  v.mask = h->mask;
-  v.drho = h->drho;
-  v.ux = h->ux;
-  v.uy = h->uy;
-  v.u_in = h->u_in;
-  v.plane = (long long)h->plane;
-  v.nx = h->nx;
-  v.ny = h->ny;
-  v.pitch = h->pitch;
-  v.wpr = h->wpr;
-  v.omega = (float)(1.0 / p.tau);
-  v.rho0 = (float)p.rho0;
-  v.outlet_rule = p.outlet;
-  v.port_scheme = p.ports;
-  v.f_elems = 9 * (long long)h->plane;
-  h->host_view = v;
-  LatticeView vs[kViews] = {v, v, v};
-  vs[1].ux = h->ux_prev;
-  vs[1].uy = h->uy_prev;
-  CUH(cudaMemcpyAsync(h->views, vs, sizeof(vs), cudaMemcpyHostToDevice, h->stream));
-  CUH(cudaMemcpyAsync(h->u_in, u_in.data(), ny * 4, cudaMemcpyHostToDevice, h->stream));
-  CUH(cudaMemcpyAsync(h->d_outlet_start, h->outlet_start.data(), h->n_outlets * 4, cudaMemcpyHostToDevice,
-                      h->stream));
-  CUH(cudaMemcpyAsync(h->d_outlet_len, h->outlet_len.data(), h->n_outlets * 4, cudaMemcpyHostToDevice,
-                      h->stream));
-  CUH(cudaMemcpyAsync(h->cells_dev, cell_types, ncell, cudaMemcpyHostToDevice, h->stream));
-  CUH(launch_pack_mask(h->cells_dev, h->nx, h->ny, h->wpr, h->mask0, h->stream));
-#undef CUH
-  // enough warps for one segment each where the lattice allows, never more
-  // blocks than fit on the device at once (the kernel strides over the list)
-  const int bps = stream_collide_blocks_per_sm(p.precision, 0, 0);
-  const long long cap = (long long)h->sm_count * bps;
-  const long long need = ((long long)nseg_cap + kStepWarps - 1) / kStepWarps;
-  h->grid = (int)(need < cap ? need : cap);
-  if (h->grid < 1) h->grid = 1;
-  st = initial_state(h);
-  if (st != LBM_OK) {
-    lbm_destroy(h);
-    return st;
-  }
-  *out = h;
-  return LBM_OK;
-}
-
-lbm_status lbm_kernel_time(lbm_handle h, int reset, double* ms, int64_t* launches,
-                           int64_t* fluid_updates) {
-  if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
-  if (ms) *ms = h->step_ms;
-  if (launches) *launches = h->step_launches;
-  if (fluid_updates) *fluid_updates = h->fluid_updates;
-  if (reset) {
-    h->step_ms = 0.0;
-    h->step_launches = 0;
-    h->fluid_updates = 0;
-  }
+  Engine* E = nullptr;
+  lbm_status st = engine_create(1, params, &cell_types, cuda_stream, &E);
+  if (st != LBM_OK) return st;
+  *out = new lbm_handle_s{E};
   return LBM_OK;
 }
 
 lbm_status lbm_reset(lbm_handle h) {
   if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
-  return initial_state(h);
+  return initial_state(h->e);
 }
 
 lbm_status lbm_solve(lbm_handle h, int64_t n_steps, lbm_solve_result* out) {
   if (!h || !out) return fail(LBM_ERR_ARG, "handle or out is NULL");
-  if (n_steps < 2 || (n_steps % 2) != 0) return fail(LBM_ERR_ARG, "n_steps must be even and >= 2");
-  lbm_status st = enqueue_solve(h, n_steps);
-  if (st != LBM_OK) return st;
-  CU(cudaStreamSynchronize(h->stream));
-  h->steps_done += n_steps;
-  h->solved = true;
-  account_steps(h, n_steps);
-  fill_result(h, out);
-  if (h->h_result[7] != 0.0) return fail(LBM_ERR_DIVERGED, "non-finite pressure drop, flow rate or residual");
-  return LBM_OK;
+  return engine_solve(h->e, n_steps, out);
 }
 
 lbm_status lbm_optimize_step(lbm_handle h, int32_t n_swap, int64_t n_steps, lbm_opt_result* out) {
   if (!h || !out) return fail(LBM_ERR_ARG, "handle or out is NULL");
-  if (n_steps < 2 || (n_steps % 2) != 0) return fail(LBM_ERR_ARG, "n_steps must be even and >= 2");
-  if (n_swap < 0) return fail(LBM_ERR_ARG, "n_swap must be >= 0");
-  if (!h->solved) return fail(LBM_ERR_ARG, "lbm_optimize_step needs a field: call lbm_solve first");
-  const double mu = h->p.rho0 * ((h->p.tau - 0.5) / 3.0);
-  CU(launch_oc_select(&h->host_view, h->views, h->p.rho0, mu, n_swap, h->oc, h->stream));
-  CU(launch_oc_apply(h->p.precision, h->views, h->mask, h->oc, h->stream));
-  if (h->p.reinit == LBM_REINIT_COLD)
-    CU(cudaMemsetAsync(h->f, 0, 9 * h->plane * storage_bytes(h->p.precision), h->stream));
-  lbm_status st = rebuild_worklist(h);
-  if (st != LBM_OK) return st;
-  CU(cudaMemcpyAsync(h->h_info, h->oc.info, 8 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  CU(cudaMemcpyAsync(h->h_count, h->fluid_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                     h->stream));
-  st = enqueue_solve(h, n_steps);
-  if (st != LBM_OK) return st;
-  CU(cudaStreamSynchronize(h->stream));
-  h->steps_done += n_steps;
-  const int64_t before = h->fluid_cells;
-  h->fluid_cells = (int64_t)*h->h_count;
-  account_steps(h, n_steps);
-  std::memset(out, 0, sizeof(*out));
-  out->n_swapped = h->h_info[0];
-  out->fluid_count = h->fluid_cells;
-  fill_result(h, &out->solve);
-  if (h->h_info[3] != 0) return fail(LBM_ERR_DIVERGED, "a dynamic-pressure or stress score is NaN");
-  if (h->fluid_cells != before) return fail(LBM_ERR_CUDA, "fluid cell count changed by the exchange");
-  if (h->h_result[7] != 0.0) return fail(LBM_ERR_DIVERGED, "non-finite pressure drop, flow rate or residual");
-  return LBM_OK;
+  if (!h->e->solved) return fail(LBM_ERR_ARG, "lbm_optimize_step needs a field: call lbm_solve first");
+  return engine_optimize(h->e, &n_swap, n_steps, out);
 }
 
 lbm_status lbm_read_fields(lbm_handle h, uint32_t which, void* dst, size_t dst_bytes, int dst_is_device) {
-  if (!h || !dst) return fail(LBM_ERR_ARG, "handle or dst is NULL");
+  if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
   (void)dst_is_device;  // unified addressing: cudaMemcpyDefault handles both
-  const size_t nx = h->nx, ny = h->ny, ncell = nx * ny;
-  const size_t sb = storage_bytes(h->p.precision);
-  switch (which) {
-    case LBM_FIELD_MASK:
-      if (dst_bytes < ncell) return fail(LBM_ERR_ARG, "dst too small");
-      CU(launch_unpack_mask(h->mask, h->nx, h->ny, h->wpr, h->cells_dev, h->stream));
-      CU(cudaMemcpyAsync(dst, h->cells_dev, ncell, cudaMemcpyDefault, h->stream));
-      break;
-    case LBM_FIELD_RHO:
-      if (dst_bytes < ncell * 4) return fail(LBM_ERR_ARG, "dst too small");
-      CU(launch_rho_from_drho(h->drho, (float)h->p.rho0, h->mask, h->nx, h->ny, h->pitch, h->wpr,
-                              h->dense_f, h->stream));
-      CU(cudaMemcpyAsync(dst, h->dense_f, ncell * 4, cudaMemcpyDefault, h->stream));
-      break;
-    case LBM_FIELD_DRHO:
-    case LBM_FIELD_UX:
-    case LBM_FIELD_UY: {
-      if (dst_bytes < ncell * 4) return fail(LBM_ERR_ARG, "dst too small");
-      const float* src = which == LBM_FIELD_DRHO ? h->drho : which == LBM_FIELD_UX ? h->ux : h->uy;
-      CU(cudaMemcpy2DAsync(dst, nx * 4, src, (size_t)h->pitch * 4, nx * 4, ny, cudaMemcpyDefault, h->stream));
-      break;
-    }
-    case LBM_FIELD_POPS:
-      if (dst_bytes < 9 * ncell * sb) return fail(LBM_ERR_ARG, "dst too small");
-      for (int i = 0; i < 9; ++i)
-        CU(cudaMemcpy2DAsync(static_cast<char*>(dst) + i * ncell * sb, nx * sb,
-                             static_cast<const char*>(h->f) + i * h->plane * sb, (size_t)h->pitch * sb,
-                             nx * sb, ny, cudaMemcpyDefault, h->stream));
-      break;
-    default:
-      return fail(LBM_ERR_ARG, "which must be exactly one LBM_FIELD_* value");
-  }
-  CU(cudaStreamSynchronize(h->stream));
-  return LBM_OK;
+  return engine_read(h->e, 0, which, dst, dst_bytes);
 }
 
 lbm_status lbm_load_state(lbm_handle h, const void* pops, size_t bytes, int src_is_device) {
   if (!h || !pops) return fail(LBM_ERR_ARG, "handle or pops is NULL");
   (void)src_is_device;
-  const size_t nx = h->nx, ny = h->ny, ncell = nx * ny;
-  const size_t sb = storage_bytes(h->p.precision);
+  Engine* E = h->e;
+  Member* m = E->m[0];
+  const size_t nx = m->nx, ny = m->ny, ncell = nx * ny;
+  const size_t sb = storage_bytes(E->precision);
   if (bytes < 9 * ncell * sb) return fail(LBM_ERR_ARG, "pops too small");
   for (int i = 0; i < 9; ++i)
-    CU(cudaMemcpy2DAsync(static_cast<char*>(h->f) + i * h->plane * sb, (size_t)h->pitch * sb,
+    CU(cudaMemcpy2DAsync(static_cast<char*>(m->f) + i * m->plane * sb, (size_t)m->pitch * sb,
                          static_cast<const char*>(pops) + i * ncell * sb, nx * sb, nx * sb, ny,
-                         cudaMemcpyDefault, h->stream));
-  CU(cudaStreamSynchronize(h->stream));
+                         cudaMemcpyDefault, E->stream));
+  CU(cudaStreamSynchronize(E->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_kernel_time(lbm_handle h, int reset, double* ms, int64_t* launches, int64_t* fluid_updates) {
+  if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+  return engine_kernel_time(h->e, reset, ms, launches, fluid_updates);
+}
+
+lbm_status lbm_step_config(lbm_handle h, int32_t* warps_per_block, int32_t* grid) {
+  if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
+  if (warps_per_block) *warps_per_block = h->e->step.warps_per_block;
+  if (grid) *grid = h->e->step.grid;
   return LBM_OK;
 }
 
@@ -610,37 +858,104 @@ lbm_status lbm_select_swaps(lbm_handle h, const float* drho, const float* ux, co
   if (!h || !drho || !ux || !uy || !n_out || (n_swap > 0 && (!fluid_idx_out || !solid_idx_out)))
     return fail(LBM_ERR_ARG, "NULL argument");
   if (n_swap < 0) return fail(LBM_ERR_ARG, "n_swap must be >= 0");
-  const size_t nx = h->nx, ny = h->ny;
+  Engine* E = h->e;
+  Member* m = E->m[0];
+  const size_t nx = m->nx, ny = m->ny;
+  // the member's view with its fields replaced by copies of the given ones
   float* tmp = nullptr;
-  CU(cudaMalloc(&tmp, 3 * h->plane * sizeof(float)));
-  LatticeView v = h->host_view;
+  LatticeView* vdev = nullptr;
+  CU(cudaMalloc(&tmp, 3 * m->plane * sizeof(float)));
+  if (cudaMalloc(&vdev, sizeof(LatticeView)) != cudaSuccess) {
+    cudaFree(tmp);
+    return fail(LBM_ERR_OOM, "cudaMalloc(view)");
+  }
+  LatticeView v = m->view;
   v.drho = tmp;
-  v.ux = tmp + h->plane;
-  v.uy = tmp + 2 * h->plane;
+  v.ux = tmp + m->plane;
+  v.uy = tmp + 2 * m->plane;
+  v.sel_off = 0;
+  v.word_off = 0;
   lbm_status st = LBM_OK;
   auto step = [&](cudaError_t e, const char* what) {
     if (e != cudaSuccess && st == LBM_OK) st = fail(LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
-  step(cudaMemsetAsync(tmp, 0, 3 * h->plane * sizeof(float), h->stream), "memset");
+  step(cudaMemsetAsync(tmp, 0, 3 * m->plane * sizeof(float), E->stream), "memset");
   const float* srcs[3] = {drho, ux, uy};
   for (int k = 0; k < 3; ++k)
-    step(cudaMemcpy2DAsync(tmp + k * h->plane, (size_t)h->pitch * 4, srcs[k], nx * 4, nx * 4, ny,
-                           cudaMemcpyDefault, h->stream), "copy field");
-  step(cudaMemcpyAsync(h->views + 2, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream), "view");
-  const double mu = h->p.rho0 * ((h->p.tau - 0.5) / 3.0);
-  step(launch_oc_select(&v, h->views + 2, h->p.rho0, mu, n_swap, h->oc, h->stream), "select");
-  step(cudaMemcpyAsync(h->h_info, h->oc.info, 8 * sizeof(int), cudaMemcpyDeviceToHost, h->stream), "info");
-  step(cudaStreamSynchronize(h->stream), "sync");
-  int n = st == LBM_OK ? h->h_info[0] : 0;
+    step(cudaMemcpy2DAsync(tmp + k * m->plane, (size_t)m->pitch * 4, srcs[k], nx * 4, nx * 4, ny,
+                           cudaMemcpyDefault, E->stream), "copy field");
+  step(cudaMemcpyAsync(vdev, &v, sizeof(v), cudaMemcpyHostToDevice, E->stream), "view");
+  E->h_nswap[0] = n_swap;
+  step(cudaMemcpyAsync(E->n_swap_dev, E->h_nswap, sizeof(int), cudaMemcpyHostToDevice, E->stream), "n_swap");
+  // one lattice: E->word_off is {0, words}
+  step(launch_oc_select(vdev, E->word_off, 1, E->total_words, E->n_swap_dev, E->oc, E->stream), "select");
+  step(cudaMemcpyAsync(E->h_info, E->oc.info, 8 * sizeof(int), cudaMemcpyDeviceToHost, E->stream), "info");
+  step(cudaStreamSynchronize(E->stream), "sync");
+  const int n = st == LBM_OK ? E->h_info[0] : 0;
   if (st == LBM_OK && n > 0) {
-    step(cudaMemcpyAsync(fluid_idx_out, h->oc.sel_f, n * sizeof(int), cudaMemcpyDefault, h->stream), "out");
-    step(cudaMemcpyAsync(solid_idx_out, h->oc.sel_s, n * sizeof(int), cudaMemcpyDefault, h->stream), "out");
-    step(cudaStreamSynchronize(h->stream), "sync");
+    step(cudaMemcpyAsync(fluid_idx_out, E->oc.sel_f, n * sizeof(int), cudaMemcpyDefault, E->stream), "out");
+    step(cudaMemcpyAsync(solid_idx_out, E->oc.sel_s, n * sizeof(int), cudaMemcpyDefault, E->stream), "out");
+    step(cudaStreamSynchronize(E->stream), "sync");
   }
   cudaFree(tmp);
+  cudaFree(vdev);
   if (st != LBM_OK) return st;
   *n_out = n;
-  if (h->h_info[3] != 0) return fail(LBM_ERR_DIVERGED, "a score is NaN");
+  if (E->h_info[3] != 0) return fail(LBM_ERR_DIVERGED, "a score is NaN");
+  return LBM_OK;
+}
+
+// ---- batches -------------------------------------------------------------------
+
+lbm_status lbm_batch_create(int32_t n, const lbm_params* params, const uint8_t* const* cell_types,
+                            void* cuda_stream, lbm_batch* out) {
+  if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !params || !cell_types) return fail(LBM_ERR_ARG, "need n >= 1, params and cell_types");
+  Engine* E = nullptr;
+  lbm_status st = engine_create(n, params, cell_types, cuda_stream, &E);
+  if (st != LBM_OK) return st;
+  *out = new lbm_batch_s{E};
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch b) {
+  if (!b) return;
+  delete b->e;
+  delete b;
+}
+
+lbm_status lbm_batch_reset(lbm_batch b) {
+  if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+  return initial_state(b->e);
+}
+
+lbm_status lbm_batch_solve(lbm_batch b, int64_t n_steps, lbm_solve_result* out) {
+  if (!b || !out) return fail(LBM_ERR_ARG, "batch or out is NULL");
+  return engine_solve(b->e, n_steps, out);
+}
+
+lbm_status lbm_batch_optimize_step(lbm_batch b, const int32_t* n_swap, int64_t n_steps, lbm_opt_result* out) {
+  if (!b || !n_swap || !out) return fail(LBM_ERR_ARG, "batch, n_swap or out is NULL");
+  return engine_optimize(b->e, n_swap, n_steps, out);
+}
+
+lbm_status lbm_batch_read_fields(lbm_batch b, int32_t member, uint32_t which, void* dst, size_t dst_bytes,
+                                 int dst_is_device) {
+  if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+  (void)dst_is_device;
+  return engine_read(b->e, member, which, dst, dst_bytes);
+}
+
+lbm_status lbm_batch_kernel_time(lbm_batch b, int reset, double* ms, int64_t* launches, int64_t* fluid_updates) {
+  if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+  return engine_kernel_time(b->e, reset, ms, launches, fluid_updates);
+}
+
+lbm_status lbm_batch_step_config(lbm_batch b, int32_t* warps_per_block, int32_t* grid) {
+  if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
+  if (warps_per_block) *warps_per_block = b->e->step.warps_per_block;
+  if (grid) *grid = b->e->step.grid;
   return LBM_OK;
 }
 

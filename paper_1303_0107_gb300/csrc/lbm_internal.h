@@ -1,5 +1,10 @@
 // Internal declarations shared by the CUDA translation units of the library.
 // Not part of the public ABI (include/lbm.h is).
+//
+// Every kernel works on a set of lattices described by a device table of
+// LatticeView entries: a handle is a set of one, a batch a set of many, and
+// each stage of the path (work-list, time steps, reductions, exchange) is one
+// launch over the whole set.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -14,18 +19,13 @@ namespace lbm {
 
 // Work unit of the stream-collide kernel: one row segment, the 32 cells of
 // one mask word (row y, cells 32w .. 32w+31), taken by one warp (lane l ->
-// cell 32w + l).  A block holds kStepWarps warps; the segment list holds only
-// segments with at least one fluid cell.
+// cell 32w + l).  The segment list holds only segments with a fluid cell.
+// Default block shape (the engine tunes it on its own lattices).
 constexpr int kStepWarps = 8;
-constexpr int kStepThreads = 32 * kStepWarps;
 // Row pitch of every per-cell array, in elements: a multiple of 64 so that
 // each row starts on a 128-byte boundary for 16-bit and 32-bit storage.
 constexpr int kPitchAlign = 64;
 
-// Everything a kernel needs to know about one lattice.  Stored in device
-// memory (one entry per lattice of a batch) and read by each block.  Entries
-// are 16-byte aligned and a multiple of 16 bytes long, so that any entry of a
-// table can be read with 16-byte loads.
 // Cell mask layout: one bit per cell, bit (x & 31) of word x >> 5 of a row,
 // set = solid.  Rows are stored with a stride of wpr + 2 words and one solid
 // padding word on each side, plus one solid padding row above row 0 and one
@@ -38,20 +38,33 @@ __host__ __device__ constexpr long long mask_alloc_words(int wpr, int ny) {
 }
 __host__ __device__ constexpr long long mask_origin(int wpr) { return mask_stride(wpr) + 1; }
 
+// Everything a kernel needs to know about one lattice, in a device table.
+// Entries are 16-byte aligned and a multiple of 16 bytes long, so any entry
+// of a table can be read with 16-byte loads.
 struct alignas(16) LatticeView {
-  void* f;               // 9 population planes [9][ny][pitch] of the storage type
-  const uint32_t* mask;  // word (0, 0) of the padded mask (see above)
-  float* drho;           // [ny][pitch] rho - rho0 of the last step (moment steps only)
-  float* ux;             // [ny][pitch]
-  float* uy;             // [ny][pitch]
-  const float* u_in;     // [ny] inlet u_x per row (0 where the row has no inlet cell)
-  long long plane;       // elements per population plane = ny * pitch
+  void* f;                 // 9 population planes [9][ny][pitch] of the storage type
+  const uint32_t* mask;    // word (0, 0) of the padded mask (see above)
+  float* drho;             // [ny][pitch] rho - rho0 of the last step
+  float* ux;               // [ny][pitch]
+  float* uy;               // [ny][pitch]
+  float* ux_prev;          // [ny][pitch] u of the step K steps before the last (residual)
+  float* uy_prev;          // [ny][pitch]
+  const float* u_in;       // [ny] inlet u_x per row (0 where the row has no inlet cell)
+  const int* out_start;    // [n_outlets] first row of each outlet run
+  const int* out_len;      // [n_outlets] rows of each outlet run
+  long long plane;         // elements per population plane = ny * pitch
+  long long f_elems;       // 9 * plane
+  double rho0d;            // rho0 (FP64, for the scores and reductions)
+  double mu;               // rho0 (tau - 1/2) / 3 (Eq. 5)
   int nx, ny, pitch, wpr;
-  float omega;           // 1 / tau
+  float omega;             // 1 / tau
   float rho0;
-  int outlet_rule;       // lbm_outlet_rule
-  int port_scheme;       // lbm_port_scheme
-  long long f_elems;     // 9 * plane (extent of f)
+  int outlet_rule;         // lbm_outlet_rule
+  int port_scheme;         // lbm_port_scheme
+  int n_outlets;
+  int sel_off;             // start of this lattice's picks in the shared pick arrays
+  int word_off;            // start of this lattice's words in the concatenated word space
+  int seg_word_off;        // start of its interior-row words (rows 1..ny-2)
 };
 
 // A row segment: lattice index and (y << 12) | w (w < 4096, so nx <= 131072).
@@ -63,76 +76,95 @@ constexpr int kSegWordBits = 12;
 static_assert(sizeof(LatticeView) % 16 == 0 && alignof(LatticeView) == 16, "LatticeView layout");
 static_assert(sizeof(SegRef) == 8, "SegRef layout");
 
+// Index of the lattice whose range [off[l], off[l+1]) holds i (off ascending,
+// off[0] = 0, n lattices).
+__host__ __device__ inline int find_lattice(const int* off, int n, long long i) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // ---- stream-collide (step.cu) ----------------------------------------------
 // phase 0 ("A"): reads the post-collision state from the neighbours, writes
 //   the new post-collision values into the slots the neighbours will read
 //   (or back into the cell's own slots where the neighbour is solid);
 // phase 1 ("B"): reads and writes the cell's own slots only, leaving the
 //   canonical layout F[i][cell] = post-collision population i.
-// moments != 0 writes drho/ux/uy of the view (phase B only).
+// moments (phase B only): 0 none, 1 write drho/ux/uy, 2 write drho/ux_prev/uy_prev.
 // Launched as a programmatic dependent of the previous kernel on the stream:
 // it reads its work item, descriptor and mask before waiting for that kernel,
 // and only then the populations.
+struct StepConfig {
+  int warps_per_block;  // 4, 8 or 16
+  int grid;             // blocks
+};
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
-                                  const SegRef* segs, const int* n_segs, int grid,
+                                  const SegRef* segs, const int* n_segs, StepConfig cfg,
                                   cudaStream_t stream);
-int stream_collide_blocks_per_sm(int precision, int phase, int moments);
+int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block);
 
 // ---- geometry / work-list (worklist.cu) ------------------------------------
 cudaError_t launch_pack_mask(const uint8_t* cells, int nx, int ny, int wpr, uint32_t* mask,
                              cudaStream_t stream);
 cudaError_t launch_unpack_mask(const uint32_t* mask, int nx, int ny, int wpr, uint8_t* cells,
                                cudaStream_t stream);
-// Segment list of one lattice: the row segments of rows 1..ny-2 holding at
-// least one fluid cell, in ascending (y, w) order, tagged with `lattice`.
-// scratch holds segment_scratch_ints(ny, wpr) ints.
-size_t segment_scratch_ints(int ny, int wpr);
-size_t segment_capacity(int ny, int wpr);
-cudaError_t launch_build_segments(const uint32_t* mask, int ny, int wpr, int lattice, int* scratch,
-                                  SegRef* segs, int* n_segs, cudaStream_t stream);
-cudaError_t launch_count_fluid(const uint32_t* mask, int nx, int ny, int wpr,
-                               unsigned long long* count, cudaStream_t stream);
+// Segment list of a set of lattices: the row segments of rows 1..ny-2 holding
+// a fluid cell, lattice by lattice in ascending (y, w) order.  seg_word_off is
+// a device copy of the views' seg_word_off plus the total at [n]; scratch
+// holds segment_scratch_ints(total) ints, segs room for total entries.
+size_t segment_scratch_ints(long long total_words);
+cudaError_t launch_build_segments(const LatticeView* views, const int* seg_word_off, int n_lattices,
+                                  int total_words, int* scratch, SegRef* segs, int* n_segs,
+                                  cudaStream_t stream);
+// fluid cells of each lattice into count[l] (zeroed here); word_off as for
+// the exchange below
+cudaError_t launch_count_fluid(const LatticeView* views, const int* word_off, int n_lattices,
+                               int total_words, unsigned long long* count, cudaStream_t stream);
 // exclusive scan of n ints; out[n] = total.  Fixed order for any input.
 // tmp holds scan_tmp_ints(n) ints.
-size_t scan_tmp_ints(int n);
+size_t scan_tmp_ints(long long n);
 cudaError_t launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t stream);
 cudaError_t launch_rho_from_drho(const float* drho, float rho0, const uint32_t* mask, int nx, int ny,
                                  int pitch, int wpr, float* rho_dense, cudaStream_t stream);
 
 // ---- reductions (reduce.cu) -------------------------------------------------
 constexpr int kResidualBlocks = 128;
-// per-lattice results written by launch_finalize, doubles:
+// per-lattice results written by launch_finalize, doubles (kResultDoubles each):
 //   [0] dp, [1] m_in, [2] residual (or -1), [3] n_in, [4] n_out,
 //   [5] sum |du|, [6] sum |u|, [7] nonfinite flag, [8] theta, [9] D_g,
 //   [10 .. 10+n_out) m_out
 constexpr int kResultDoubles = 10 + LBM_MAX_OUTLETS;
-cudaError_t launch_residual_partials(const LatticeView* views, const float* ux_prev,
-                                     const float* uy_prev, int lattice, double* partials,
+// partials: 2 * kResidualBlocks doubles per lattice
+cudaError_t launch_residual_partials(const LatticeView* views, int n_lattices, double* partials,
                                      cudaStream_t stream);
-cudaError_t launch_finalize(const LatticeView* views, int lattice, const int* outlet_start,
-                            const int* outlet_len, int n_outlets, const double* partials,
+cudaError_t launch_finalize(const LatticeView* views, int n_lattices, const double* partials,
                             int with_residual, double* result, cudaStream_t stream);
 
 // ---- optimality criterion (oc.cu) -------------------------------------------
 struct OcScratch {
-  int* cnt_f;            // [nwords]
-  int* cnt_s;            // [nwords]
-  int* off_f;            // [nwords + 1]
-  int* off_s;            // [nwords + 1]
-  unsigned long long* key_f;  // [ncells]
-  unsigned long long* key_s;  // [ncells]
-  int* idx_f;            // [ncells]
-  int* idx_s;            // [ncells]
-  int* sel_f;            // [cap]
-  int* sel_s;            // [cap]
-  int* info;             // [8]: n_swapped, nF, nS, error flag, ...
-  int* scan_tmp;         // scan_tmp_ints(nwords)
-  int cap;               // capacity of sel_* (max n_swap)
+  int* cnt_f;                 // [total_words]
+  int* cnt_s;                 // [total_words]
+  int* off_f;                 // [total_words + 1]
+  int* off_s;                 // [total_words + 1]
+  unsigned long long* key_f;  // [total cells]
+  unsigned long long* key_s;  // [total cells]
+  int* idx_f;                 // [total cells]
+  int* idx_s;                 // [total cells]
+  int* sel_f;                 // picks of lattice l from views[l].sel_off (sel_capacity each)
+  int* sel_s;
+  int* info;                  // [8 per lattice]: n_swapped, nF, nS, NaN flag
+  int* scan_tmp;              // scan_tmp_ints(total_words)
 };
-cudaError_t launch_oc_select(const LatticeView* view_host, const LatticeView* view_dev,
-                             double rho0, double mu, int n_swap, const OcScratch& s,
+__host__ __device__ inline int sel_capacity(int nx, int ny) { return (int)((long long)nx * ny / 2 + 1); }
+// Selection for every lattice: n_swap (device int[n]) requested per lattice;
+// word_off: device copy of the views' word_off plus the total at [n].
+cudaError_t launch_oc_select(const LatticeView* views, const int* word_off, int n_lattices,
+                             int total_words, const int* n_swap, const OcScratch& s,
                              cudaStream_t stream);
-cudaError_t launch_oc_apply(int precision, const LatticeView* view_dev, uint32_t* mask,
+cudaError_t launch_oc_apply(int precision, const LatticeView* views, int n_lattices,
                             const OcScratch& s, cudaStream_t stream);
 
 // ---- counters / debugging ----------------------------------------------------
@@ -145,8 +177,8 @@ bool debug_sync();
 
 #ifdef LBM_CHECK_BOUNDS
 // Bounds-checked builds: every global access of the step and reduction
-// kernels is checked against its allocation; a violation is printed (first
-// few only) and the access skipped.
+// kernels is checked against its allocation; a violation is printed and the
+// access skipped.
 __device__ __forceinline__ bool lbm_in_bounds(long long i, long long n, int line) {
   if (i >= 0 && i < n) return true;
   printf("lbm bounds: line %d index %lld extent %lld block %d thread %d\n", line, i, n, blockIdx.x,

@@ -51,7 +51,8 @@ constexpr size_t kOffSelF = kOffIdxS + up((size_t)kMaxCells * 4);
 constexpr size_t kOffSelS = kOffSelF + up((size_t)kPickSlots * 4);
 constexpr size_t kOffScan = kOffSelS + up((size_t)kPickSlots * 4);
 constexpr int kScanTmpInts = 256;  // >= scan_tmp_ints(kWordSlots)
-constexpr size_t kScratchBytes = kOffScan + up((size_t)kScanTmpInts * 4);
+constexpr size_t kOffWords = kOffScan + up((size_t)kScanTmpInts * 4);  // {0, words}, n_swap
+constexpr size_t kScratchBytes = kOffWords + up(4 * sizeof(int));
 
 // The shared scratch (about 7.4 MB).  In host code this name is only a
 // stand-in for the symbol: its device address comes from
@@ -139,7 +140,13 @@ extern "C" lbm_status lbm_select_swaps_noalloc(int32_t nx, int32_t ny, double ta
   v.ny = ny;
   v.pitch = nx;  // the caller's fields are dense [ny][nx]
   v.wpr = wpr;
+  v.rho0d = rho0;
+  v.mu = rho0 * ((tau - 0.5) / 3.0);
+  v.sel_off = 0;
+  v.word_off = 0;
   LatticeView* view_dev = reinterpret_cast<LatticeView*>(base + kOffView);
+  int* words_dev = reinterpret_cast<int*>(base + kOffWords);  // [0] = 0, [1] = words, [2] = n_swap
+  const int host_words[3] = {0, ny * wpr, n_swap};
 
   OcScratch s;
   s.cnt_f = reinterpret_cast<int*>(base + kOffCntF);
@@ -154,7 +161,6 @@ extern "C" lbm_status lbm_select_swaps_noalloc(int32_t nx, int32_t ny, double ta
   s.sel_s = reinterpret_cast<int*>(base + kOffSelS);
   s.info = reinterpret_cast<int*>(base + kOffInfo);
   s.scan_tmp = reinterpret_cast<int*>(base + kOffScan);
-  s.cap = (int)((long long)nx * ny / 2 + 1);
 
   cudaError_t e;
   // the array keeps the previous call's contents: the mask padding must read
@@ -162,12 +168,14 @@ extern "C" lbm_status lbm_select_swaps_noalloc(int32_t nx, int32_t ny, double ta
   // counters; every other part is fully written before it is read)
   if ((e = cudaMemcpyAsync(view_dev, &v, sizeof(v), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
     return fail(LBM_ERR_CUDA, "copy lattice descriptor", e);
+  if ((e = cudaMemcpyAsync(words_dev, host_words, sizeof(host_words), cudaMemcpyHostToDevice, stream)) !=
+      cudaSuccess)
+    return fail(LBM_ERR_CUDA, "copy word offsets", e);
   if ((e = cudaMemsetAsync(mask_base, 0xff, (size_t)mask_alloc_words(wpr, ny) * 4, stream)) != cudaSuccess)
     return fail(LBM_ERR_CUDA, "reset mask", e);
   if ((e = launch_pack_mask(cell_types, nx, ny, wpr, mask, stream)) != cudaSuccess)
     return fail(LBM_ERR_CUDA, "pack mask", e);
-  const double mu = rho0 * ((tau - 0.5) / 3.0);
-  if ((e = launch_oc_select(&v, view_dev, rho0, mu, n_swap, s, stream)) != cudaSuccess)
+  if ((e = launch_oc_select(view_dev, words_dev, 1, ny * wpr, words_dev + 2, s, stream)) != cudaSuccess)
     return fail(LBM_ERR_CUDA, "selection kernels", e);
   k_copy_picks<<<(n_swap + 255) / 256 > 0 ? (n_swap + 255) / 256 : 1, 256, 0, stream>>>(
       s.info, s.sel_f, s.sel_s, n_swap, fluid_idx_out, solid_idx_out, n_out);

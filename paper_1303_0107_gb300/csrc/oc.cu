@@ -1,4 +1,5 @@
-// Heuristic optimality criterion and the equal-count exchange of Sec. 2.2-2.3.
+// Heuristic optimality criterion and the equal-count exchange of Sec. 2.2-2.3,
+// for every lattice of a set in one launch per stage.
 //
 //   scores   interface fluid cells: dynamic pressure q = 1/2 rho |u|^2 (Eq. 6);
 //            interface solid cells: sigma = sum over fluid 4-neighbours n (E, N,
@@ -10,13 +11,15 @@
 //   select   n = min(n_swap, #fluid candidates, #solid candidates); the n fluid
 //            candidates of smallest (q, idx) and the n solid candidates of
 //            largest sigma, ties to the smaller idx.  Exact 96-bit radix select
-//            (64-bit order-preserving score key, 32-bit cell index).
+//            (64-bit order-preserving score key, 32-bit cell index), one block
+//            per (class, lattice).
 //   apply    flip the 2n mask bits at once; new fluid cells start from the
 //            rest equilibrium of rho0 (shifted populations 0).
 //
 // Interface / movable cells: 4-neighbourhood; columns 0, 1, nx-2, nx-1 and
 // rows 0, ny-1 never move.  Candidate enumeration works on whole mask words
-// with bit operations; candidates are written in ascending cell index.
+// with bit operations; the words of all lattices are numbered consecutively,
+// so candidates come out lattice by lattice in ascending cell index.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -58,12 +61,25 @@ __device__ __forceinline__ WordMasks word_masks(const uint32_t* __restrict__ mas
   return r;
 }
 
-__global__ void k_oc_count(const uint32_t* __restrict__ mask, int nx, int ny, int wpr,
-                           int* __restrict__ cnt_f, int* __restrict__ cnt_s) {
+// word i of the concatenated word space -> lattice l, row y, word w
+__device__ __forceinline__ void word_of(const LatticeView* __restrict__ views,
+                                        const int* __restrict__ word_off, int n, int i, int& l,
+                                        int& y, int& w) {
+  l = find_lattice(word_off, n, i);
+  const int wpr = views[l].wpr;
+  const int local = i - word_off[l];
+  y = local / wpr;
+  w = local - y * wpr;
+}
+
+__global__ void k_oc_count(const LatticeView* __restrict__ views, const int* __restrict__ word_off, int n,
+                           int total, int* __restrict__ cnt_f, int* __restrict__ cnt_s) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ny * wpr) return;
-  const int y = i / wpr, w = i - y * wpr;
-  const WordMasks m = word_masks(mask, nx, ny, wpr, y, w);
+  if (i >= total) return;
+  int l, y, w;
+  word_of(views, word_off, n, i, l, y, w);
+  const LatticeView& L = views[l];
+  const WordMasks m = word_masks(L.mask, L.nx, L.ny, L.wpr, y, w);
   cnt_f[i] = __popc(m.fluid_cand);
   cnt_s[i] = __popc(m.solid_cand);
 }
@@ -75,17 +91,19 @@ __device__ __forceinline__ unsigned long long order_key(double v) {
   return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
 }
 
-__global__ void k_oc_emit(const LatticeView* __restrict__ view, const uint32_t* __restrict__ mask,
-                          double rho0, double mu, const int* __restrict__ off_f,
-                          const int* __restrict__ off_s, unsigned long long* __restrict__ key_f,
-                          int* __restrict__ idx_f, unsigned long long* __restrict__ key_s,
-                          int* __restrict__ idx_s, int* __restrict__ info) {
-  const LatticeView* L = view;
-  const int nx = L->nx, ny = L->ny, wpr = L->wpr, pitch = L->pitch;
+__global__ void k_oc_emit(const LatticeView* __restrict__ views, const int* __restrict__ word_off, int n,
+                          int total, const int* __restrict__ off_f, const int* __restrict__ off_s,
+                          unsigned long long* __restrict__ key_f, int* __restrict__ idx_f,
+                          unsigned long long* __restrict__ key_s, int* __restrict__ idx_s,
+                          int* __restrict__ info) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ny * wpr) return;
-  const int y = i / wpr, w = i - y * wpr;
-  const WordMasks m = word_masks(mask, nx, ny, wpr, y, w);
+  if (i >= total) return;
+  int l, y, w;
+  word_of(views, word_off, n, i, l, y, w);
+  const LatticeView* L = views + l;
+  const int nx = L->nx, pitch = L->pitch;
+  const double rho0 = L->rho0d, mu = L->mu;
+  const WordMasks m = word_masks(L->mask, nx, L->ny, L->wpr, y, w);
   int of = off_f[i], os = off_s[i];
   bool bad = false;
   uint32_t fc = m.fluid_cand;
@@ -122,36 +140,47 @@ __global__ void k_oc_emit(const LatticeView* __restrict__ view, const uint32_t* 
     idx_s[os] = y * nx + x;
     ++os;
   }
-  if (bad) atomicOr(info + 3, 1);
+  if (bad) atomicOr(info + 8 * l + 3, 1);
 }
 
 constexpr int kSelThreads = 1024;
 
-// Block 0 selects among fluid candidates, block 1 among solid candidates: the
-// n smallest (key, idx) pairs, written in candidate (= ascending idx) order.
+// Grid (2, lattices): block (0, l) selects among lattice l's fluid candidates,
+// block (1, l) among its solid candidates: the n smallest (key, idx) pairs,
+// written in candidate (= ascending idx) order to the lattice's pick range.
 __global__ void __launch_bounds__(kSelThreads)
-    k_oc_select(const unsigned long long* __restrict__ key_f, const int* __restrict__ idx_f,
+    k_oc_select(const LatticeView* __restrict__ views, const int* __restrict__ word_off,
+                const unsigned long long* __restrict__ key_f, const int* __restrict__ idx_f,
                 const unsigned long long* __restrict__ key_s, const int* __restrict__ idx_s,
-                const int* __restrict__ n_f_ptr, const int* __restrict__ n_s_ptr, int n_swap,
-                int* __restrict__ sel_f, int* __restrict__ sel_s, int* __restrict__ info) {
+                const int* __restrict__ off_f, const int* __restrict__ off_s,
+                const int* __restrict__ n_swap, int* __restrict__ sel_f, int* __restrict__ sel_s,
+                int* __restrict__ info) {
   __shared__ int hist[256];
   __shared__ unsigned long long s_key;
   __shared__ unsigned int s_idx;
   __shared__ int s_rem;
   __shared__ int scan[kSelThreads];
   const int tid = threadIdx.x;
-  const unsigned long long* key = blockIdx.x == 0 ? key_f : key_s;
-  const int* idx = blockIdx.x == 0 ? idx_f : idx_s;
-  int* sel = blockIdx.x == 0 ? sel_f : sel_s;
-  const int nf = *n_f_ptr, ns = *n_s_ptr;
-  const int ncand = blockIdx.x == 0 ? nf : ns;
-  int n = n_swap < nf ? n_swap : nf;
+  const int l = blockIdx.y;
+  const LatticeView* L = views + l;
+  const int w0 = word_off[l], w1 = word_off[l + 1];
+  const int f0 = off_f[w0], nf = off_f[w1] - f0;
+  const int s0 = off_s[w0], ns = off_s[w1] - s0;
+  const bool fluid_class = blockIdx.x == 0;
+  const unsigned long long* key = fluid_class ? key_f + f0 : key_s + s0;
+  const int* idx = fluid_class ? idx_f + f0 : idx_s + s0;
+  int* sel = (fluid_class ? sel_f : sel_s) + L->sel_off;
+  const int ncand = fluid_class ? nf : ns;
+  int n = n_swap[l];
+  const int cap = sel_capacity(L->nx, L->ny);
+  n = n < cap ? n : cap;
+  n = n < nf ? n : nf;
   n = n < ns ? n : ns;
   if (n < 0) n = 0;
-  if (blockIdx.x == 0 && tid == 0) {
-    info[0] = n;
-    info[1] = nf;
-    info[2] = ns;
+  if (fluid_class && tid == 0) {
+    info[8 * l + 0] = n;
+    info[8 * l + 1] = nf;
+    info[8 * l + 2] = ns;
   }
   if (n == 0) return;
   if (tid == 0) {
@@ -172,13 +201,11 @@ __global__ void __launch_bounds__(kSelThreads)
       int digit;
       bool match;
       if (d < 8) {
-        const int sh = 64 - 8 * d;
-        match = d == 0 || (kk >> sh) == (pk >> sh);
+        match = d == 0 || (kk >> (64 - 8 * d)) == (pk >> (64 - 8 * d));
         digit = (int)((kk >> (56 - 8 * d)) & 0xffu);
       } else {
         const int dd = d - 8;
-        const int sh = 32 - 8 * dd;
-        match = kk == pk && (dd == 0 || (ii >> sh) == (pi >> sh));
+        match = kk == pk && (dd == 0 || (ii >> (32 - 8 * dd)) == (pi >> (32 - 8 * dd)));
         digit = (int)((ii >> (24 - 8 * dd)) & 0xffu);
       }
       if (match) atomicAdd(&hist[digit], 1);
@@ -223,15 +250,19 @@ __global__ void __launch_bounds__(kSelThreads)
   }
 }
 
+// grid (blocks, lattices): exchange lattice l's picks
 template <class T>
-__global__ void k_oc_apply(const LatticeView* __restrict__ view, uint32_t* __restrict__ mask,
-                           const int* __restrict__ sel_f, const int* __restrict__ sel_s,
-                           const int* __restrict__ info) {
-  const LatticeView* L = view;
-  const int n = info[0];
+__global__ void k_oc_apply(const LatticeView* __restrict__ views, const int* __restrict__ sel_f_all,
+                           const int* __restrict__ sel_s_all, const int* __restrict__ info) {
+  const int l = blockIdx.y;
+  const LatticeView* L = views + l;
+  const int n = info[8 * l];
   const int nx = L->nx, ms = mask_stride(L->wpr), pitch = L->pitch;
   const long long pl = L->plane;
+  uint32_t* mask = const_cast<uint32_t*>(L->mask);
   T* F = static_cast<T*>(L->f);
+  const int* sel_f = sel_f_all + L->sel_off;
+  const int* sel_s = sel_s_all + L->sel_off;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     {  // fluid -> solid
       const int id = sel_f[k];
@@ -256,42 +287,44 @@ __global__ void k_oc_apply(const LatticeView* __restrict__ view, uint32_t* __res
   }
 }
 
-inline int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
+inline int blocks_for(long long n, int threads) {
+  const long long b = (n + threads - 1) / threads;
+  return (int)(b > 0 ? b : 1);
+}
 
 }  // namespace
 
-cudaError_t launch_oc_select(const LatticeView* view_host, const LatticeView* view_dev, double rho0,
-                             double mu, int n_swap, const OcScratch& s, cudaStream_t stream) {
-  const int nx = view_host->nx, ny = view_host->ny, wpr = view_host->wpr;
-  const int nwords = ny * wpr;
-  cudaError_t e = cudaMemsetAsync(s.info, 0, 8 * sizeof(int), stream);
+cudaError_t launch_oc_select(const LatticeView* views, const int* word_off, int n_lattices, int total,
+                             const int* n_swap, const OcScratch& s, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(s.info, 0, 8 * sizeof(int) * n_lattices, stream);
   if (e != cudaSuccess) return e;
-  k_oc_count<<<blocks_for(nwords, 256), 256, 0, stream>>>(view_host->mask, nx, ny, wpr, s.cnt_f,
-                                                          s.cnt_s);
-  if ((e = launch_scan(s.cnt_f, s.off_f, nwords, s.scan_tmp, stream)) != cudaSuccess) return e;
-  if ((e = launch_scan(s.cnt_s, s.off_s, nwords, s.scan_tmp, stream)) != cudaSuccess) return e;
-  k_oc_emit<<<blocks_for(nwords, 256), 256, 0, stream>>>(view_dev, view_host->mask, rho0, mu, s.off_f,
-                                                         s.off_s, s.key_f, s.idx_f, s.key_s, s.idx_s,
-                                                         s.info);
-  const int ns = n_swap < s.cap ? n_swap : s.cap;
-  k_oc_select<<<2, kSelThreads, 0, stream>>>(s.key_f, s.idx_f, s.key_s, s.idx_s, s.off_f + nwords,
-                                             s.off_s + nwords, ns, s.sel_f, s.sel_s, s.info);
-  count_launches(3);
+  k_oc_count<<<blocks_for(total, 256), 256, 0, stream>>>(views, word_off, n_lattices, total, s.cnt_f,
+                                                         s.cnt_s);
+  count_launches(1);
+  if ((e = launch_scan(s.cnt_f, s.off_f, total, s.scan_tmp, stream)) != cudaSuccess) return e;
+  if ((e = launch_scan(s.cnt_s, s.off_s, total, s.scan_tmp, stream)) != cudaSuccess) return e;
+  k_oc_emit<<<blocks_for(total, 256), 256, 0, stream>>>(views, word_off, n_lattices, total, s.off_f,
+                                                        s.off_s, s.key_f, s.idx_f, s.key_s, s.idx_s,
+                                                        s.info);
+  k_oc_select<<<dim3(2, n_lattices), kSelThreads, 0, stream>>>(views, word_off, s.key_f, s.idx_f, s.key_s,
+                                                               s.idx_s, s.off_f, s.off_s, n_swap, s.sel_f,
+                                                               s.sel_s, s.info);
+  count_launches(2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_oc_apply(int precision, const LatticeView* view_dev, uint32_t* mask,
-                            const OcScratch& s, cudaStream_t stream) {
-  const int grid = s.cap > 0 ? blocks_for(s.cap, 128) : 1;
+cudaError_t launch_oc_apply(int precision, const LatticeView* views, int n_lattices, const OcScratch& s,
+                            cudaStream_t stream) {
+  const dim3 grid(4, n_lattices);
   switch (precision) {
     case LBM_F32:
-      k_oc_apply<float><<<grid, 128, 0, stream>>>(view_dev, mask, s.sel_f, s.sel_s, s.info);
+      k_oc_apply<float><<<grid, 128, 0, stream>>>(views, s.sel_f, s.sel_s, s.info);
       break;
     case LBM_BF16_SHIFTED:
-      k_oc_apply<__nv_bfloat16><<<grid, 128, 0, stream>>>(view_dev, mask, s.sel_f, s.sel_s, s.info);
+      k_oc_apply<__nv_bfloat16><<<grid, 128, 0, stream>>>(views, s.sel_f, s.sel_s, s.info);
       break;
     case LBM_F16_SHIFTED:
-      k_oc_apply<__half><<<grid, 128, 0, stream>>>(view_dev, mask, s.sel_f, s.sel_s, s.info);
+      k_oc_apply<__half><<<grid, 128, 0, stream>>>(views, s.sel_f, s.sel_s, s.info);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -1,5 +1,6 @@
 // FP64 reductions of a solved field: pressure drop, inlet and outlet flow
-// rates (Sec. 2.3 step 5; Eq. 9-11 inputs) and the convergence residual.
+// rates (Sec. 2.3 step 5), the uniformity measures of Eq. 9-11 and the
+// convergence residual -- for every lattice of a set in one launch.
 //
 // All sums are accumulated in double from the FP32 moments of the last step
 // and are deterministic: every thread owns a fixed set of cells, block sums
@@ -26,15 +27,13 @@ __device__ double block_sum(double v, double* sm) {
   return r;
 }
 
-// Residual partials: block b covers rows [b*ny/B, (b+1)*ny/B) of one lattice.
-// partials[2b] = sum |u - u_prev|_1, partials[2b+1] = sum |u|_1 (solid cells
-// hold zeros in both fields and add nothing).
+// Residual partials, grid (kResidualBlocks, lattices): block b of lattice l
+// covers rows [b*ny/B, (b+1)*ny/B).  partials[l][2b] = sum |u - u_prev|_1,
+// partials[l][2b+1] = sum |u|_1 (solid cells hold zeros in both fields).
 __global__ void __launch_bounds__(kRedThreads)
-    k_residual_partials(const LatticeView* __restrict__ views, int lattice,
-                        const float* __restrict__ ux_prev, const float* __restrict__ uy_prev,
-                        double* __restrict__ partials) {
+    k_residual_partials(const LatticeView* __restrict__ views, double* __restrict__ partials) {
   __shared__ double sm[kRedThreads];
-  const LatticeView* L = views + lattice;
+  const LatticeView* L = views + blockIdx.y;
   const int nx = L->nx, ny = L->ny, pitch = L->pitch;
   const int b = blockIdx.x;
   const int y0 = (int)((long long)b * ny / kResidualBlocks);
@@ -46,26 +45,29 @@ __global__ void __launch_bounds__(kRedThreads)
     const long long c = (long long)y * pitch + x;
     if (!LBM_OK_IDX(c, L->plane)) continue;
     const double ux = L->ux[c], uy = L->uy[c];
-    du += fabs(ux - (double)ux_prev[c]) + fabs(uy - (double)uy_prev[c]);
+    du += fabs(ux - (double)L->ux_prev[c]) + fabs(uy - (double)L->uy_prev[c]);
     u += fabs(ux) + fabs(uy);
   }
   du = block_sum(du, sm);
   u = block_sum(u, sm);
   if (threadIdx.x == 0) {
-    partials[2 * b] = du;
-    partials[2 * b + 1] = u;
+    double* p = partials + (size_t)blockIdx.y * 2 * kResidualBlocks;
+    p[2 * b] = du;
+    p[2 * b + 1] = u;
   }
 }
 
 // One block per lattice: port sums and the final combination.
 __global__ void __launch_bounds__(kRedThreads)
-    k_finalize(const LatticeView* __restrict__ views, int lattice, const int* __restrict__ outlet_start,
-               const int* __restrict__ outlet_len, int n_outlets, const double* __restrict__ partials,
-               int with_residual, double* __restrict__ result) {
+    k_finalize(const LatticeView* __restrict__ views, const double* __restrict__ partials_all,
+               int with_residual, double* __restrict__ result_all) {
   __shared__ double sm[kRedThreads];
-  const LatticeView* L = views + lattice;
+  const LatticeView* L = views + blockIdx.x;
+  double* result = result_all + (size_t)blockIdx.x * kResultDoubles;
+  const double* partials = partials_all + (size_t)blockIdx.x * 2 * kResidualBlocks;
   const int nx = L->nx, ny = L->ny, pitch = L->pitch, wpr = L->wpr;
-  const double rho0 = L->rho0;
+  const int n_outlets = L->n_outlets;
+  const double rho0 = L->rho0d;
   const int wl = (nx - 1) >> 5, bl = (nx - 1) & 31;
   double s_in = 0.0, s_out = 0.0, m_in = 0.0, n_in = 0.0, n_out = 0.0;
   for (int y = threadIdx.x; y < ny; y += kRedThreads) {
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(kRedThreads)
   // each outlet run summed by one thread in ascending row order
   for (int j = threadIdx.x; j < n_outlets; j += kRedThreads) {
     double m = 0.0;
-    const int ya = outlet_start[j], yb = ya + outlet_len[j];
+    const int ya = L->out_start[j], yb = ya + L->out_len[j];
     for (int y = ya; y < yb; ++y) {
       const long long c = (long long)y * pitch + nx - 1;
       if (!LBM_OK_IDX(c, L->plane)) continue;
@@ -141,20 +143,16 @@ __global__ void __launch_bounds__(kRedThreads)
 
 }  // namespace
 
-cudaError_t launch_residual_partials(const LatticeView* views, const float* ux_prev,
-                                     const float* uy_prev, int lattice, double* partials,
+cudaError_t launch_residual_partials(const LatticeView* views, int n_lattices, double* partials,
                                      cudaStream_t stream) {
-  k_residual_partials<<<kResidualBlocks, kRedThreads, 0, stream>>>(views, lattice, ux_prev, uy_prev,
-                                                                   partials);
+  k_residual_partials<<<dim3(kResidualBlocks, n_lattices), kRedThreads, 0, stream>>>(views, partials);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const LatticeView* views, int lattice, const int* outlet_start,
-                            const int* outlet_len, int n_outlets, const double* partials,
+cudaError_t launch_finalize(const LatticeView* views, int n_lattices, const double* partials,
                             int with_residual, double* result, cudaStream_t stream) {
-  k_finalize<<<1, kRedThreads, 0, stream>>>(views, lattice, outlet_start, outlet_len, n_outlets,
-                                            partials, with_residual, result);
+  k_finalize<<<n_lattices, kRedThreads, 0, stream>>>(views, partials, with_residual, result);
   count_launches(1);
   return cudaGetLastError();
 }

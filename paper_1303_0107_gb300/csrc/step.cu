@@ -196,8 +196,12 @@ __device__ __forceinline__ void outlet_rule(float (&g)[9], float rho0, int schem
 // neighbour solid flags, bit i-1 = solid(x + c_i), i = 1..8 (E N W S NE NW SW SE)
 constexpr unsigned kE = 1u, kN = 2u, kW = 4u, kS = 8u, kNE = 16u, kNW = 32u, kSW = 64u, kSE = 128u;
 
-template <class T, int PHASE, bool MOMENTS>
-__global__ void __launch_bounds__(kStepThreads, 4)
+// Block size is 128, 256 or 512 threads (chosen per launch); the register
+// budget is the same (at most 64 per thread) for all of them.
+constexpr int kMaxStepThreads = 512;
+
+template <class T, int PHASE, int MOM>
+__global__ void __launch_bounds__(kMaxStepThreads, 2)
     k_stream_collide(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
                      const int* __restrict__ n_segs) {
   using P = Pop<T>;
@@ -208,9 +212,10 @@ __global__ void __launch_bounds__(kStepThreads, 4)
   // the segment list, descriptors and mask are never written by a time step,
   // so they may be read before the previous step has finished
   const int nseg = *n_segs;
-  const int stride = gridDim.x * kStepWarps;
+  const int wpb = blockDim.x >> 5;
+  const int stride = gridDim.x * wpb;
   bool waited = false;
-  for (int sidx = blockIdx.x * kStepWarps + (threadIdx.x >> 5); sidx < nseg; sidx += stride) {
+  for (int sidx = blockIdx.x * wpb + (threadIdx.x >> 5); sidx < nseg; sidx += stride) {
     const SegRef sr = segs[sidx];
     const LatticeView* __restrict__ L = views + sr.lattice;
     const int y = sr.yw >> kSegWordBits;
@@ -335,10 +340,10 @@ __global__ void __launch_bounds__(kStepThreads, 4)
     } else {
 #pragma unroll
       for (int i = 0; i < 9; ++i) FST(i * pl + c, g[i]);
-      if (MOMENTS && LBM_OK_IDX(c, pl)) {
+      if (MOM != 0 && LBM_OK_IDX(c, pl)) {
         L->drho[c] = drho;
-        L->ux[c] = ux;
-        L->uy[c] = uy;
+        (MOM == 1 ? L->ux : L->ux_prev)[c] = ux;
+        (MOM == 1 ? L->uy : L->uy_prev)[c] = uy;
       }
     }
   }
@@ -347,9 +352,10 @@ __global__ void __launch_bounds__(kStepThreads, 4)
 
 template <class T>
 void* pick(int phase, int moments) {
-  if (phase == 0) return (void*)k_stream_collide<T, 0, false>;
-  if (moments) return (void*)k_stream_collide<T, 1, true>;
-  return (void*)k_stream_collide<T, 1, false>;
+  if (phase == 0) return (void*)k_stream_collide<T, 0, 0>;
+  if (moments == 1) return (void*)k_stream_collide<T, 1, 1>;
+  if (moments == 2) return (void*)k_stream_collide<T, 1, 2>;
+  return (void*)k_stream_collide<T, 1, 0>;
 }
 
 void* kernel_for(int precision, int phase, int moments) {
@@ -364,17 +370,18 @@ void* kernel_for(int precision, int phase, int moments) {
 }  // namespace
 
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
-                                  const SegRef* segs, const int* n_segs, int grid,
+                                  const SegRef* segs, const int* n_segs, StepConfig sc,
                                   cudaStream_t stream) {
   void* k = kernel_for(precision, phase, moments);
-  if (!k) return cudaErrorInvalidValue;
+  if (!k || sc.warps_per_block < 1 || sc.warps_per_block * 32 > kMaxStepThreads || sc.grid < 1)
+    return cudaErrorInvalidValue;
   void* args[] = {(void*)&views, (void*)&segs, (void*)&n_segs};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kStepThreads);
+  cfg.gridDim = dim3(sc.grid);
+  cfg.blockDim = dim3(32 * sc.warps_per_block);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = stream;
   cfg.attrs = attr;
@@ -384,10 +391,10 @@ cudaError_t launch_stream_collide(int precision, int phase, int moments, const L
   return e;
 }
 
-int stream_collide_blocks_per_sm(int precision, int phase, int moments) {
+int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block) {
   void* k = kernel_for(precision, phase, moments);
   int n = 0;
-  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kStepThreads, 0) != cudaSuccess)
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, 0) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }

@@ -3,7 +3,9 @@
 // The cell map of Sec. 3.3 (fluid / solid cells; inlet and outlet cells are
 // the fluid cells of the first and last columns) is kept as one bit per cell:
 // word w of row y holds cells x = 32w .. 32w+31, bit set = solid.  Bits past
-// the last column are set, so padding behaves as wall.
+// the last column are set, so padding behaves as wall.  Kernels over a set of
+// lattices number the words of all lattices consecutively and find the
+// lattice of a word by binary search in the per-lattice offsets.
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -31,49 +33,63 @@ __global__ void k_unpack_mask(const uint32_t* __restrict__ mask, int nx, int ny,
   cells[i] = (mask[(long long)y * mask_stride(wpr) + (x >> 5)] >> (x & 31)) & 1u;
 }
 
-// 1 for every row segment (row y in 1..ny-2, word w) holding a fluid cell;
-// index (y - 1) * wpr + w.
-__global__ void k_segment_flags(const uint32_t* __restrict__ mask, int ny, int wpr,
-                                int* __restrict__ flags) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (ny - 2) * wpr) return;
-  const int y = 1 + i / wpr, w = i - (i / wpr) * wpr;
-  flags[i] = mask[(long long)y * mask_stride(wpr) + w] != 0xffffffffu ? 1 : 0;
+// Interior-row words of all lattices in one index space: word i belongs to
+// lattice l = find_lattice(seg_word_off, n, i), row 1 + (i - off) / wpr.
+__device__ __forceinline__ void seg_word(const LatticeView* __restrict__ views,
+                                         const int* __restrict__ seg_word_off, int n, int i, int& l,
+                                         int& y, int& w) {
+  l = find_lattice(seg_word_off, n, i);
+  const int wpr = views[l].wpr;
+  const int local = i - seg_word_off[l];
+  y = 1 + local / wpr;
+  w = local - (y - 1) * wpr;
 }
 
-__global__ void k_segment_scatter(const int* __restrict__ flags, const int* __restrict__ offsets,
-                                  int ny, int wpr, int lattice, SegRef* __restrict__ segs,
+// 1 for every row segment (row y in 1..ny-2, word w) holding a fluid cell
+__global__ void k_segment_flags(const LatticeView* __restrict__ views, const int* __restrict__ seg_word_off,
+                                int n, int total, int* __restrict__ flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int l, y, w;
+  seg_word(views, seg_word_off, n, i, l, y, w);
+  const LatticeView& L = views[l];
+  flags[i] = L.mask[(long long)y * mask_stride(L.wpr) + w] != 0xffffffffu ? 1 : 0;
+}
+
+__global__ void k_segment_scatter(const LatticeView* __restrict__ views, const int* __restrict__ seg_word_off,
+                                  int n, int total, const int* __restrict__ flags,
+                                  const int* __restrict__ offsets, SegRef* __restrict__ segs,
                                   int* __restrict__ n_segs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = (ny - 2) * wpr;
-  if (i == 0) *n_segs = offsets[n];
-  if (i >= n || !flags[i]) return;
-  const int y = 1 + i / wpr, w = i - (i / wpr) * wpr;
+  if (i == 0) *n_segs = offsets[total];
+  if (i >= total || !flags[i]) return;
+  int l, y, w;
+  seg_word(views, seg_word_off, n, i, l, y, w);
   SegRef r;
-  r.lattice = lattice;
+  r.lattice = l;
   r.yw = (y << kSegWordBits) | w;
   segs[offsets[i]] = r;
 }
 
-__global__ void k_count_fluid(const uint32_t* __restrict__ mask, int nx, int ny, int wpr,
-                              unsigned long long* __restrict__ count) {
+// fluid cells per lattice over all words (rows 0..ny-1) of all lattices
+__global__ void k_count_fluid(const LatticeView* __restrict__ views, const int* __restrict__ word_off, int n,
+                              int total, unsigned long long* __restrict__ count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int c = 0;
-  if (i < ny * wpr) {
-    const int y = i / wpr, w = i - y * wpr;
-    const int valid = min(32, nx - w * 32);
-    const uint32_t vmask = valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u);
-    c = __popc(~mask[(long long)y * mask_stride(wpr) + w] & vmask);
-  }
-  // warp sum, then one atomic per warp (integer: order does not matter)
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+  if (i >= total) return;
+  const int l = find_lattice(word_off, n, i);
+  const LatticeView& L = views[l];
+  const int local = i - word_off[l];
+  const int y = local / L.wpr, w = local - y * L.wpr;
+  const int valid = min(32, L.nx - w * 32);
+  const uint32_t vmask = valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u);
+  const int c = __popc(~L.mask[(long long)y * mask_stride(L.wpr) + w] & vmask);
+  if (c) atomicAdd(count + l, (unsigned long long)c);  // integer: order does not matter
 }
 
 // Exclusive scan of n ints by one block of 1024 threads; out[n] = total.
 // Each thread sums a contiguous chunk, the chunk sums are scanned in shared
 // memory, then each thread writes its chunk: a fixed order for any input.
-// Used for the top level of the multi-block scan.
+// Used for small inputs and for the top level of the multi-block scan.
 __global__ void __launch_bounds__(1024) k_scan_chunked(const int* __restrict__ in, int* __restrict__ out,
                                                        int n) {
   __shared__ int sums[1024];
@@ -161,7 +177,10 @@ __global__ void k_rho_from_drho(const float* __restrict__ drho, float rho0,
   rho[i] = solid ? 0.0f : rho0 + drho[(size_t)y * pitch + x];
 }
 
-inline int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
+inline int blocks_for(long long n, int threads) {
+  const long long b = (n + threads - 1) / threads;
+  return (int)(b > 0 ? b : 1);
+}
 
 }  // namespace
 
@@ -179,8 +198,8 @@ cudaError_t launch_unpack_mask(const uint32_t* mask, int nx, int ny, int wpr, ui
   return cudaGetLastError();
 }
 
-size_t scan_tmp_ints(int n) {
-  const size_t nb = (size_t)(n + kScanTile - 1) / kScanTile;
+size_t scan_tmp_ints(long long n) {
+  const size_t nb = (size_t)((n + kScanTile - 1) / kScanTile);
   return 2 * nb + 2;
 }
 
@@ -200,33 +219,31 @@ cudaError_t launch_scan(const int* in, int* out, int n, int* tmp, cudaStream_t s
   return cudaGetLastError();
 }
 
-size_t segment_capacity(int ny, int wpr) { return (size_t)(ny > 2 ? ny - 2 : 0) * wpr; }
-
-size_t segment_scratch_ints(int ny, int wpr) {
-  const int n = (int)segment_capacity(ny, wpr);
-  return 2 * (size_t)n + 1 + scan_tmp_ints(n);
+size_t segment_scratch_ints(long long total_words) {
+  return 2 * (size_t)total_words + 1 + scan_tmp_ints(total_words);
 }
 
-cudaError_t launch_build_segments(const uint32_t* mask, int ny, int wpr, int lattice, int* scratch,
-                                  SegRef* segs, int* n_segs, cudaStream_t stream) {
-  const int n = (int)segment_capacity(ny, wpr);
+cudaError_t launch_build_segments(const LatticeView* views, const int* seg_word_off, int n_lattices,
+                                  int total, int* scratch, SegRef* segs, int* n_segs,
+                                  cudaStream_t stream) {
   int* flags = scratch;
-  int* offsets = scratch + n;         // n + 1
-  int* tmp = scratch + 2 * n + 1;     // scan_tmp_ints(n)
-  k_segment_flags<<<blocks_for(n, 256), 256, 0, stream>>>(mask, ny, wpr, flags);
+  int* offsets = scratch + total;      // total + 1
+  int* tmp = scratch + 2 * total + 1;  // scan_tmp_ints(total)
+  k_segment_flags<<<blocks_for(total, 256), 256, 0, stream>>>(views, seg_word_off, n_lattices, total, flags);
   count_launches(1);
-  cudaError_t e = launch_scan(flags, offsets, n, tmp, stream);
+  cudaError_t e = launch_scan(flags, offsets, total, tmp, stream);
   if (e != cudaSuccess) return e;
-  k_segment_scatter<<<blocks_for(n, 256), 256, 0, stream>>>(flags, offsets, ny, wpr, lattice, segs, n_segs);
+  k_segment_scatter<<<blocks_for(total, 256), 256, 0, stream>>>(views, seg_word_off, n_lattices, total, flags,
+                                                                offsets, segs, n_segs);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_count_fluid(const uint32_t* mask, int nx, int ny, int wpr, unsigned long long* count,
-                               cudaStream_t stream) {
-  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream);
+cudaError_t launch_count_fluid(const LatticeView* views, const int* word_off, int n_lattices, int total,
+                               unsigned long long* count, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long) * n_lattices, stream);
   if (e != cudaSuccess) return e;
-  k_count_fluid<<<blocks_for((long long)ny * wpr, 256), 256, 0, stream>>>(mask, nx, ny, wpr, count);
+  k_count_fluid<<<blocks_for(total, 256), 256, 0, stream>>>(views, word_off, n_lattices, total, count);
   count_launches(1);
   return cudaGetLastError();
 }

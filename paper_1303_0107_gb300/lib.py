@@ -89,13 +89,29 @@ def load_library(path=None):
     L.lbm_kernel_launches.restype = ctypes.c_uint64
     L.lbm_kernel_time.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    L.lbm_step_config.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    B = _VP
+    L.lbm_batch_create.argtypes = [ctypes.c_int32, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p), _VP,
+                                   ctypes.POINTER(B)]
+    L.lbm_batch_solve.argtypes = [B, ctypes.c_int64, ctypes.POINTER(SolveResult)]
+    L.lbm_batch_optimize_step.argtypes = [B, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                          ctypes.POINTER(OptResult)]
+    L.lbm_batch_read_fields.argtypes = [B, ctypes.c_int32, ctypes.c_uint32, _VP, ctypes.c_size_t, ctypes.c_int]
+    L.lbm_batch_reset.argtypes = [B]
+    L.lbm_batch_kernel_time.argtypes = [B, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    L.lbm_batch_step_config.argtypes = [B, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.lbm_batch_destroy.argtypes = [B]
+    L.lbm_batch_destroy.restype = None
     L.lbm_select_swaps_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                            _VP, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP]
     L.lbm_bytes_per_fluid_update.argtypes = [ctypes.c_int32]
     L.lbm_bytes_per_fluid_update.restype = ctypes.c_double
     for name in ("lbm_create_geometry", "lbm_solve", "lbm_optimize_step", "lbm_read_fields",
                  "lbm_load_state", "lbm_reset", "lbm_select_swaps", "lbm_kernel_time",
-                 "lbm_select_swaps_noalloc"):
+                 "lbm_select_swaps_noalloc", "lbm_step_config", "lbm_batch_create", "lbm_batch_solve",
+                 "lbm_batch_optimize_step", "lbm_batch_read_fields", "lbm_batch_reset",
+                 "lbm_batch_kernel_time", "lbm_batch_step_config"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -211,6 +227,13 @@ class Lattice:
     def reset(self):
         _check(load_library().lbm_reset(self._h), "lbm_reset")
 
+    def step_config(self):
+        """(warps per block, blocks) of the time-step launches (autotuned)."""
+        w = ctypes.c_int32()
+        g = ctypes.c_int32()
+        _check(load_library().lbm_step_config(self._h, ctypes.byref(w), ctypes.byref(g)), "lbm_step_config")
+        return w.value, g.value
+
     def select_swaps(self, drho, ux, uy, n_swap: int):
         arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (drho, ux, uy)]
         cap = max(int(n_swap), 1)
@@ -221,3 +244,94 @@ class Lattice:
                                                fi.ctypes.data, si.ctypes.data, ctypes.byref(n)),
                "lbm_select_swaps")
         return fi[:n.value].copy(), si[:n.value].copy()
+
+
+class Batch:
+    """Many lattices stepped together (one launch per stage for all of them).
+
+    members: list of dicts with keys cells, tau, u_max and optionally rho0,
+    outlet, ports, reinit.  precision and residual_every are shared.
+    """
+
+    def __init__(self, members, precision=F32, residual_every=100, stream=None):
+        L = load_library()
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        self.n = len(members)
+        self.precision = int(precision)
+        self._cells = [np.ascontiguousarray(m["cells"], dtype=np.uint8) for m in members]
+        self.shapes = [c.shape for c in self._cells]
+        params = (Params * self.n)()
+        for i, m in enumerate(members):
+            ny, nx = self._cells[i].shape
+            params[i] = Params(nx, ny, float(m["tau"]), float(m.get("rho0", 1.0)), float(m["u_max"]),
+                               int(m.get("outlet", OUT_CONST_RHO)), int(precision),
+                               int(m.get("reinit", REINIT_WARM)), int(residual_every),
+                               int(m.get("ports", PORTS_REGULARIZED)), 0)
+        ptrs = (ctypes.c_void_p * self.n)(*[c.ctypes.data for c in self._cells])
+        self._b = _VP()
+        _check(L.lbm_batch_create(self.n, params, ptrs, _stream_ptr(stream), ctypes.byref(self._b)),
+               "lbm_batch_create")
+
+    def close(self):
+        if self._b:
+            load_library().lbm_batch_destroy(self._b)
+            self._b = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, n_steps):
+        r = (SolveResult * self.n)()
+        _check(load_library().lbm_batch_solve(self._b, int(n_steps), r), "lbm_batch_solve")
+        return [x.to_dict() for x in r]
+
+    def optimize_step(self, n_swap, n_steps):
+        if np.isscalar(n_swap):
+            n_swap = [int(n_swap)] * self.n
+        ns = (ctypes.c_int32 * self.n)(*[int(v) for v in n_swap])
+        r = (OptResult * self.n)()
+        _check(load_library().lbm_batch_optimize_step(self._b, ns, int(n_steps), r), "lbm_batch_optimize_step")
+        out = []
+        for x in r:
+            d = x.solve.to_dict()
+            d.update(n_swapped=x.n_swapped, fluid_count=x.fluid_count)
+            out.append(d)
+        return out
+
+    def read(self, member, field, out=None):
+        if not 0 <= int(member) < self.n:
+            raise LbmError(1, "lbm_batch_read_fields", f"member {member} out of range (batch of {self.n})")
+        ny, nx = self.shapes[member]
+        if out is None:
+            if field == FIELD_MASK:
+                out = np.empty((ny, nx), np.uint8)
+            elif field == FIELD_POPS:
+                out = np.empty((9, ny, nx), np.float32 if self.precision == F32 else np.uint16)
+            else:
+                out = np.empty((ny, nx), np.float32)
+        ptr, nbytes, dev = _buffer(out)
+        _check(load_library().lbm_batch_read_fields(self._b, int(member), int(field), ptr, nbytes, dev),
+               "lbm_batch_read_fields")
+        return out
+
+    def reset(self):
+        _check(load_library().lbm_batch_reset(self._b), "lbm_batch_reset")
+
+    def kernel_time(self, reset=False):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        u = ctypes.c_int64()
+        _check(load_library().lbm_batch_kernel_time(self._b, int(bool(reset)), ctypes.byref(ms), ctypes.byref(n),
+                                                    ctypes.byref(u)), "lbm_batch_kernel_time")
+        return ms.value, n.value, u.value
+
+    def step_config(self):
+        w = ctypes.c_int32()
+        g = ctypes.c_int32()
+        _check(load_library().lbm_batch_step_config(self._b, ctypes.byref(w), ctypes.byref(g)),
+               "lbm_batch_step_config")
+        return w.value, g.value
