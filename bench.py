@@ -50,7 +50,12 @@ def parse():
     ap.add_argument("--iters", type=int, default=50, help="optimiser iterations per run")
     ap.add_argument("--lattice-steps", type=int, default=5000, help="time steps per solve")
     ap.add_argument("--precision", default="f32", choices=["f32", "bf16", "f16"])
-    ap.add_argument("--no-extras", action="store_true", help="skip the large-lattice and CPU legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip every leg after the main run")
+    ap.add_argument("--legs", default="large,precision,batched,served",
+                    help="legs after the main run: large (8192 x 4096 lattice), precision (BF16/FP16 vs the "
+                         "FP64 oracle; also the CPU baseline), batched (256 candidates), served (request loop)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="served leg: Poisson arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=30.0, help="served leg: arrival window")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--kernel-case", choices=["tree", "large"], default=None,
                     help="only create one lattice and run two 4-step solves (for ncu captures): "
@@ -182,6 +187,198 @@ def oracle_rate(cells, tau, u_max, seconds):
     dt = time.perf_counter() - t0
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return fluid * n / dt, n, dt, cores
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(math.ceil(q / 100.0 * len(xs))) - 1))
+    return xs[k]
+
+
+def leg_precision(L, I, stream):
+    """BF16 / FP16 shifted storage against the FP64 oracle on the 2048 x 1024
+    tree: the first solve of the optimisation run (5000 steps from rest, same
+    mask for all).  The oracle's solve is timed and doubles as the CPU
+    baseline sample."""
+    import numpy as np
+    import oracle as ora
+    cfg = I.config_tree_2048()
+    cells, tau, u_max, S = cfg["cells"], cfg["tau"], cfg["u_max"], 5000
+    ny, nx = cells.shape
+    fluid = int((cells == 0).sum())
+    s = ora.Solver(ora.make_params(nx, ny, tau, 1.0, u_max), cells, residual_every=0)
+    t0 = time.perf_counter()
+    o = s.solve(S)
+    t_ora = time.perf_counter() - t0
+    ref_frac = np.asarray(o["m_out"]) / np.sum(o["m_out"])
+    out = {"workload": f"{cfg['name']} first solve, {S} steps from rest",
+           "oracle": {"dp": o["dp"], "theta": o["theta"], "dg": o["dg"]}}
+    glups = {}
+    for name, pv in (("f32", L.F32), ("bf16", L.BF16_SHIFTED), ("f16", L.F16_SHIFTED)):
+        h = L.Lattice(cells, tau, u_max, precision=pv, residual_every=0, stream=stream)
+        r = h.solve(S)
+        frac = np.asarray(r["m_out"]) / np.sum(r["m_out"])
+        h.reset()
+        h.kernel_time(reset=True)
+        h.solve(S)
+        ms, nl, nu = h.kernel_time()
+        glups[name] = nu / (ms / 1e3) / 1e9
+        out[name] = {"dp": r["dp"], "dp_rel_err": abs(r["dp"] - o["dp"]) / abs(o["dp"]),
+                     "outlet_fraction_max_abs_err": float(np.max(np.abs(frac - ref_frac))),
+                     "dg_abs_err": abs(r["dg"] - o["dg"]), "theta_abs_err": abs(r["theta"] - o["theta"]),
+                     "glups_steps": glups[name], "glups_vs_f32": glups[name] / glups["f32"]}
+        h.close()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cpu = {"value": fluid * S / t_ora / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{cfg['name']}: the run's first solve, {S} FP64 time steps from rest, {t_ora:.1f} s"}
+    return out, cpu
+
+
+def leg_batched(L, I, stream, prec, n=256, iters=10, S=2000, sample=32):
+    """256 uneven candidate distributors in one batch (one launch per stage
+    for all) against the same candidates one at a time through their own
+    handles (a sample of them, creation excluded)."""
+    cands = I.config_candidates(n)
+    members = [dict(cells=c["cells"], tau=c["tau"], u_max=c["u_max"]) for c in cands]
+    fluid = [int((c["cells"] == 0).sum()) for c in cands]
+    n_swap = [max(1, f // 500) for f in fluid]
+    b = L.Batch(members, precision=prec, residual_every=0, stream=stream)
+    b.solve(S)  # tunes the launch shape and captures the step graphs
+    b.reset()
+    b.kernel_time(reset=True)
+    t0 = time.perf_counter()
+    rb = b.solve(S)
+    dp_b = [[x["dp"] for x in rb]]
+    for _ in range(iters):
+        rb = b.optimize_step(n_swap, S)
+        dp_b.append([x["dp"] for x in rb])
+    t_batch = time.perf_counter() - t0
+    ms, nl, nu = b.kernel_time()
+    w, g = b.step_config()
+    b.close()
+    upd = sum(fluid) * S * (iters + 1)
+    idx = list(range(0, n, max(1, n // sample)))[:sample]
+    t_plain, upd_plain, worst = 0.0, 0, 0.0
+    for i in idx:
+        c = cands[i]
+        h = L.Lattice(c["cells"], c["tau"], c["u_max"], precision=prec, residual_every=0, stream=stream)
+        h.solve(S)
+        h.reset()
+        t0 = time.perf_counter()
+        r = h.solve(S)
+        dps = [r["dp"]]
+        for _ in range(iters):
+            dps.append(h.optimize_step(n_swap[i], S)["dp"])
+        t_plain += time.perf_counter() - t0
+        h.close()
+        upd_plain += fluid[i] * S * (iters + 1)
+        for k, d in enumerate(dps):
+            worst = max(worst, abs(d - dp_b[k][i]) / abs(d))
+    g_batch = upd / t_batch / 1e9
+    g_plain = upd_plain / t_plain / 1e9
+    return {"candidates": n, "fluid_cells": sum(fluid), "iterations": iters, "steps_per_solve": S,
+            "batched_glups": g_batch, "batched_step_glups": nu / (ms / 1e3) / 1e9,
+            "batched_s": t_batch, "step_config": [w, g],
+            "one_at_a_time_glups": g_plain, "one_at_a_time_sample": len(idx),
+            "speedup": g_batch / g_plain, "dp_rel_diff_batched_vs_alone_max": worst}
+
+
+def leg_served(L, I, prec, rate, seconds, seed=5, plain_sample=120):
+    """Poisson request stream into the server (continuous batching), and the
+    same requests served one at a time through handles (a sample, measured
+    back to back; its queueing at the same arrivals is simulated from the
+    measured service times)."""
+    import threading
+    arrivals = I.poisson_arrivals(rate, seconds, seed)
+
+    def request(k):
+        r = I.config_served_request(k)
+        fl = int((r["cells"] == 0).sum())
+        return r, fl, (max(1, fl // 500) if r["optimize"] else 0)
+
+    srv = L.Server(precision=prec, max_active=1024, max_tick_steps=1000)
+    for k in range(8):  # warm-up requests (graph capture, allocations)
+        r, fl, ns = request(10_000_000 + k)
+        srv.submit(-1 - k, r["cells"], r["tau"], r["u_max"], r["steps"], n_iter=min(r["n_iter"], 2), n_swap=ns)
+    srv.wait_idle(120)
+    srv.poll(64)
+    base = srv.stats()
+    meta = {}
+    t_start = srv.now() + 0.05
+    errors = []
+
+    def submitter():
+        try:
+            for k, t in enumerate(arrivals):
+                r, fl, ns = request(k)
+                delay = t_start + t - srv.now()
+                if delay > 0:
+                    time.sleep(delay)
+                meta[k] = (t_start + t, bool(r["optimize"]))
+                srv.submit(k, r["cells"], r["tau"], r["u_max"], r["steps"], n_iter=r["n_iter"], n_swap=ns)
+        except Exception as e:  # reported in the result
+            errors.append(repr(e))
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    done = {}
+    deadline = time.time() + 4 * seconds + 120
+    while len(done) < len(arrivals) and time.time() < deadline:
+        for d in srv.poll(1024, wait_ms=100):
+            done[d["tag"]] = d
+        if errors:
+            break
+    th.join()
+    st = srv.stats()
+    srv.close()
+    lat = [done[k]["t_done"] - meta[k][0] for k in done if k in meta]
+    lat_s = [done[k]["t_done"] - meta[k][0] for k in done if k in meta and not meta[k][1]]
+    lat_o = [done[k]["t_done"] - meta[k][0] for k in done if k in meta and meta[k][1]]
+    upd = sum(d["fluid_updates"] for d in done.values())
+    t_end = max(d["t_done"] for d in done.values()) if done else t_start
+    out = {"rate_hz": rate, "window_s": seconds, "requests": len(arrivals), "completed": len(done),
+           "failed": sum(1 for d in done.values() if d["status"] != 0), "submit_errors": errors,
+           "optimize_share": sum(1 for v in meta.values() if v[1]) / max(1, len(meta)),
+           "p50_ms": 1e3 * pct(lat, 50), "p99_ms": 1e3 * pct(lat, 99),
+           "p50_ms_solve": 1e3 * pct(lat_s, 50) if lat_s else None, "p99_ms_solve": 1e3 * pct(lat_s, 99) if lat_s else None,
+           "p50_ms_optimize": 1e3 * pct(lat_o, 50) if lat_o else None,
+           "p99_ms_optimize": 1e3 * pct(lat_o, 99) if lat_o else None,
+           "aggregate_glups": upd / (t_end - t_start) / 1e9, "offered_glups": upd / seconds / 1e9,
+           "gpu_step_glups": (st["fluid_updates"] - base["fluid_updates"]) /
+                             max(1e-9, (st["step_ms"] - base["step_ms"]) / 1e3) / 1e9,
+           "ticks": st["ticks"] - base["ticks"], "peak_active": st["peak_active"],
+           "peak_resident_gb": st["peak_resident_bytes"] / 1e9, "peak_device_gb": st["peak_device_bytes"] / 1e9,
+           "budget_gb": st["budget_bytes"] / 1e9, "scheduler_busy_s": st["busy_s"] - base["busy_s"]}
+    # one at a time through handles, back to back, on the first requests
+    service, upd_p, worst = [], 0, 0.0
+    for k in range(min(plain_sample, len(arrivals))):
+        r, fl, ns = request(k)
+        t0 = time.perf_counter()
+        h = L.Lattice(r["cells"], r["tau"], r["u_max"], precision=prec, residual_every=0)
+        x = h.solve(r["steps"])
+        for _ in range(r["n_iter"]):
+            x = h.optimize_step(ns, r["steps"])
+        h.close()
+        service.append(time.perf_counter() - t0)
+        upd_p += fl * r["steps"] * (1 + r["n_iter"])
+        if k in done and done[k]["status"] == 0:
+            worst = max(worst, abs(done[k]["last"]["dp"] - x["dp"]) / abs(x["dp"]))
+    mean_service = sum(service) / len(service)
+    # FIFO queue at the same arrival times with the measured service times (cycled)
+    free_at, sim = 0.0, []
+    for k, t in enumerate(arrivals):
+        begin = max(t, free_at)
+        free_at = begin + service[k % len(service)]
+        sim.append(free_at - t)
+    out["one_at_a_time"] = {"sample": len(service), "glups": upd_p / sum(service) / 1e9,
+                            "mean_service_ms": 1e3 * mean_service, "utilisation_at_rate": rate * mean_service,
+                            "simulated_p50_ms": 1e3 * pct(sim, 50), "simulated_p99_ms": 1e3 * pct(sim, 99),
+                            "simulated_makespan_s": free_at}
+    out["served_vs_alone_dp_rel_diff_max"] = worst
+    out["speedup_aggregate"] = out["aggregate_glups"] / out["one_at_a_time"]["glups"]
+    return out
 
 
 def run_reference(args, world, rank):
@@ -321,18 +518,20 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     sz = ctypes_sizes()
-    n_out = r["n_outlets"]
-    # host -> device: the cell map and parameters, plus the per-row inlet speeds,
-    # outlet runs and lattice descriptors the library derives from them
-    h2d = cells.nbytes + sz["params"] + 4 * cells.shape[0] + 8 * n_out + 3 * sz["view"]
+    # host -> device: the cell map, the per-row inlet speeds and the outlet
+    # table the library derives from it, the lattice descriptor and the set
+    # offsets, and n_swap of every iteration
+    h2d = cells.nbytes + 4 * cells.shape[0] + 8 * L.lib.MAX_OUTLETS + sz["view"] + 16 + 4 * iters
     # device -> host: the reduction block of every solve, the exchange counters
-    # of every iteration, the fluid counts, and the final cell map
+    # and fluid count of every iteration and of creation, and the final cell map
     d2h = cells.nbytes + (iters + 1) * sz["result_block"] + iters * (32 + 8) + 8
     e2e = {"value": updates_per_step * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
 
     extras = {}
-    if not args.no_extras and rank == 0:
+    legs = set() if args.no_extras else set(x for x in args.legs.split(",") if x)
+    cpu = None
+    if rank == 0 and "large" in legs:
         # beyond-L2 lattice: 8192 x 4096 array of 16 straight channels (~50 % fluid)
         big = I.channel_array(8192, 4096, 16, fill=0.5)
         bf = int((big == 0).sum())
@@ -346,8 +545,16 @@ def main():
             extras[f"large_8192x4096_{pname}"] = {"glups": nu / (ms / 1e3) / 1e9, "achieved_gbs": gbs,
                                                   "frac_of_measured_hbm": gbs / peak, "fluid_cells": bf}
             hb.close()
-    cpu = None
-    if not args.no_extras and rank == 0 and world == 1:
+    if rank == 0 and "precision" in legs:
+        extras["precision_tree_2048"], cpu_p = leg_precision(L, I, stream)
+        if world == 1:
+            cpu = cpu_p
+    if rank == 0 and "batched" in legs:
+        for pname, pv in (("f32", L.F32), ("bf16", L.BF16_SHIFTED)):
+            extras[f"batched_256_{pname}"] = leg_batched(L, I, stream, pv)
+    if rank == 0 and "served" in legs:
+        extras["served_f32"] = leg_served(L, I, L.F32, args.serve_rate, args.serve_seconds)
+    if cpu is None and legs and rank == 0 and world == 1:
         r, n, dt, cores = oracle_rate(cells, cfg["tau"], cfg["u_max"], args.cpu_seconds)
         cpu = {"value": r / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{cfg['name']}: {n} FP64 time steps from rest, {dt:.1f} s"}
@@ -379,7 +586,7 @@ def ctypes_sizes():
     import ctypes
     from paper_1303_0107_gb300 import lib
     return {"params": ctypes.sizeof(lib.Params), "solve_result": ctypes.sizeof(lib.SolveResult),
-            "opt_result": ctypes.sizeof(lib.OptResult), "view": 96, "result_block": 8 * (10 + lib.MAX_OUTLETS)}
+            "opt_result": ctypes.sizeof(lib.OptResult), "view": 160, "result_block": 8 * (10 + lib.MAX_OUTLETS)}
 
 
 if __name__ == "__main__":

@@ -262,6 +262,92 @@ lbm_status lbm_batch_kernel_time(lbm_batch b, int reset, double* ms, int64_t* la
 lbm_status lbm_batch_step_config(lbm_batch b, int32_t* warps_per_block, int32_t* grid);
 void lbm_batch_destroy(lbm_batch b);
 
+/* ---- serving ---------------------------------------------------------------
+ * A request loop with continuous batching.  The paper has no counterpart: it
+ * runs one design problem at a time.  Requests -- a solve of a geometry, or
+ * the optimisation loop of Sec. 2.3 on it -- arrive at any time from any
+ * host thread.  A scheduler thread inside the library admits them in arrival
+ * order while their device footprint fits the budget and a slot is free,
+ * keeps their populations, masks and fields resident on the device, and
+ * advances every resident request in the same launches (one work-list over
+ * all of them, as a batch).  Between ticks -- runs of at most max_tick_steps
+ * time steps, cut where a resident request finishes a solve -- it retires
+ * finished requests, runs the exchanges of the requests that start a new
+ * optimiser iteration, and admits new ones.  Each request evolves exactly as
+ * it would alone in a handle of its own (same results, bit for bit), whatever
+ * else is resident.                                                        */
+typedef struct lbm_server_s* lbm_server;
+
+typedef struct {
+  int32_t precision;        /* lbm_precision of every request's populations */
+  int32_t max_active;       /* most requests resident at once (>= 1) */
+  int64_t hbm_budget_bytes; /* admission limit on the summed footprints of the
+                               resident requests; 0 = 80 % of the device memory
+                               free at creation */
+  int32_t max_tick_steps;   /* longest run of time steps between two admissions
+                               (even, >= 2) */
+  int32_t reserved;         /* must be 0 */
+} lbm_server_config;
+
+typedef struct {
+  lbm_params params;         /* precision must be the server's; residual_every 0 */
+  const uint8_t* cell_types; /* host uint8[ny][nx], 1 = solid; copied at submit */
+  int64_t n_steps;           /* time steps of every solve (even, >= 2) */
+  int32_t n_iter;            /* optimiser iterations after the first solve (0: solve only) */
+  int32_t n_swap;            /* exchanges per iteration (>= 0) */
+  int64_t tag;               /* caller's identifier, returned with the result */
+  uint8_t* out_mask;         /* optional host uint8[ny][nx]: final cell map */
+  float* out_drho;           /* optional host float[ny][nx] each: rho - rho0, u_x, u_y */
+  float* out_ux;             /*   of the last step; the out_* buffers must stay valid */
+  float* out_uy;             /*   until the request's result has been polled        */
+} lbm_request;
+
+typedef struct {
+  int64_t tag;
+  int32_t status;           /* lbm_status of the request */
+  int32_t n_swapped;        /* exchanges made over all iterations */
+  double t_submit;          /* server clock (lbm_server_now), seconds */
+  double t_admit;
+  double t_done;
+  int64_t fluid_updates;    /* fluid cells x time steps of the request */
+  int64_t footprint_bytes;  /* device bytes charged against the budget */
+  double dp_first;          /* pressure drop after the first solve */
+  lbm_solve_result last;    /* reductions after the last solve */
+} lbm_served;
+
+typedef struct {
+  int64_t submitted, admitted, completed, failed;
+  int64_t ticks, exchanges;          /* scheduler ticks; ticks that ran an exchange */
+  int64_t fluid_updates;             /* over all requests */
+  int64_t resident_bytes, peak_resident_bytes; /* charged footprints */
+  int64_t device_bytes, peak_device_bytes;     /* device memory the server holds */
+  int32_t active, peak_active, queued, reserved;
+  double busy_s;                     /* wall time spent in ticks */
+  double step_ms;                    /* CUDA-event time of the time steps */
+  int64_t budget_bytes;              /* the admission limit in force */
+} lbm_server_stats;
+
+/* Start a server (and its scheduler thread) on the current device.
+ * cfg: host, copied.  cuda_stream: stream for all device work, or NULL.   */
+lbm_status lbm_server_create(const lbm_server_config* cfg, void* cuda_stream, lbm_server* out);
+/* Queue a request (thread-safe; returns at once).  LBM_ERR_ARG or
+ * LBM_ERR_GEOMETRY for a request that can never run (also when its
+ * footprint alone exceeds the budget); the request is then not queued.    */
+lbm_status lbm_server_submit(lbm_server s, const lbm_request* r);
+/* Move up to max_out finished requests into out (host lbm_served[max_out]),
+ * waiting up to wait_ms milliseconds for the first; returns how many.     */
+int32_t lbm_server_poll(lbm_server s, lbm_served* out, int32_t max_out, int32_t wait_ms);
+/* Wait until nothing is queued or resident; LBM_ERR_TIMEOUT after timeout_ms. */
+lbm_status lbm_server_wait_idle(lbm_server s, int32_t timeout_ms);
+lbm_status lbm_server_get_stats(lbm_server s, lbm_server_stats* out);
+/* Seconds since the server was created (the clock of lbm_served).         */
+double lbm_server_now(lbm_server s);
+/* Device bytes a request of these parameters is charged at admission.     */
+int64_t lbm_server_footprint(const lbm_params* params, int32_t n_iter);
+/* Stop the scheduler (resident and queued requests are dropped) and free
+ * everything.  NULL is accepted.                                          */
+void lbm_server_destroy(lbm_server s);
+
 /* Algorithmic memory traffic of one fluid-cell update of the stream-collide
  * kernel for a storage precision: 9 populations read and 9 written
  * (2 * 9 * sizeof(stored population)) plus the cell's mask bit (1/8 byte).  */

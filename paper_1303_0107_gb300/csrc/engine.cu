@@ -1,0 +1,869 @@
+// Engine: members, set layouts, time-step graphs, autotuning, solve,
+// exchange and read-back.  Host code only: it validates arguments, owns
+// device memory and enqueues the kernels of step.cu, worklist.cu, reduce.cu
+// and oc.cu on the engine's stream.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+namespace lbm {
+
+static std::atomic<uint64_t> g_launches{0};
+thread_local bool t_capturing = false;
+thread_local std::string t_last_error;
+
+void count_launches(uint64_t n) {
+  if (!t_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+uint64_t launches_total() { return g_launches.load(); }
+
+void set_last_error(const std::string& msg) { t_last_error = msg; }
+
+bool debug_sync() {
+  static const bool on = [] {
+    const char* e = std::getenv("LBM_DEBUG_SYNC");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
+bool autotune_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("LBM_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+lbm_status fail(lbm_status s, const std::string& msg) {
+  t_last_error = msg;
+  return s;
+}
+
+size_t storage_bytes(int precision) { return precision == LBM_F32 ? 4 : 2; }
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,          \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+// With LBM_DEBUG_SYNC=1: wait for the work just enqueued and name it on failure.
+#define DEBUG_SYNC(E, what)                                                              \
+  do {                                                                                   \
+    if (debug_sync() && !t_capturing) {                                                  \
+      cudaError_t e_ = cudaStreamSynchronize((E)->stream);                               \
+      if (e_ != cudaSuccess) return fail(LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+    }                                                                                    \
+  } while (0)
+
+namespace {
+
+constexpr int kGraphPairs[3] = {64, 8, 1};
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Sub-arrays of a member's allocation, as byte offsets.
+struct SlabPlan {
+  size_t f, mask, mask0, fields, u_in, d_out, cells, total;
+};
+
+SlabPlan plan_slab(const lbm_params& p) {
+  const size_t pitch = (size_t)(p.nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+  const size_t plane = pitch * (size_t)p.ny;
+  const size_t wpr = (size_t)(p.nx + 31) / 32;
+  const size_t mask_bytes = (size_t)mask_alloc_words((int)wpr, p.ny) * 4;
+  SlabPlan s{};
+  size_t o = 0;
+  s.f = o;      o += align_up(9 * plane * storage_bytes(p.precision));
+  s.mask = o;   o += align_up(mask_bytes);
+  s.mask0 = o;  o += align_up(mask_bytes);
+  s.fields = o; o += 5 * align_up(plane * 4);  // drho, ux, uy, ux_prev, uy_prev
+  s.u_in = o;   o += align_up((size_t)p.ny * 4);
+  s.d_out = o;  o += align_up(2 * LBM_MAX_OUTLETS * 4);
+  s.cells = o;  o += align_up((size_t)p.nx * p.ny);
+  s.total = o;
+  return s;
+}
+
+// Geometry rules of include/lbm.h; also finds the inlet runs (parabolic
+// profile of Sec. 3.3 per run) and the outlet runs.
+lbm_status check_and_describe(Member& m, const uint8_t* cells, std::vector<float>& u_in) {
+  const int nx = m.nx, ny = m.ny;
+  for (int x = 0; x < nx; ++x)
+    if (!cells[x] || !cells[(size_t)(ny - 1) * nx + x])
+      return fail(LBM_ERR_GEOMETRY, "rows 0 and ny-1 must be solid");
+  int n_in = 0;
+  for (int y = 0; y < ny; ++y) {
+    const uint8_t* r = cells + (size_t)y * nx;
+    if (!r[0] && r[1]) return fail(LBM_ERR_GEOMETRY, "inlet cell without a fluid cell behind it");
+    if (!r[nx - 1] && r[nx - 2]) return fail(LBM_ERR_GEOMETRY, "outlet cell without a fluid cell before it");
+    n_in += r[0] ? 0 : 1;
+  }
+  if (n_in == 0) return fail(LBM_ERR_GEOMETRY, "no inlet cell in column 0");
+  u_in.assign(ny, 0.0f);
+  for (int y = 0; y < ny;) {
+    if (cells[(size_t)y * nx]) { ++y; continue; }
+    const int y_lo = y;
+    while (y < ny && !cells[(size_t)y * nx]) ++y;
+    const int width = y - y_lo;
+    for (int yy = y_lo; yy < y; ++yy) {
+      const double s = ((double)(yy - y_lo) + 0.5) / (double)width;
+      u_in[yy] = (float)(4.0 * m.p.u_max * s * (1.0 - s));
+    }
+  }
+  m.out_start.clear();
+  m.out_len.clear();
+  for (int y = 0; y < ny;) {
+    if (cells[(size_t)y * nx + nx - 1]) { ++y; continue; }
+    const int y_lo = y;
+    while (y < ny && !cells[(size_t)y * nx + nx - 1]) ++y;
+    m.out_start.push_back(y_lo);
+    m.out_len.push_back(y - y_lo);
+  }
+  if (m.out_start.empty()) return fail(LBM_ERR_GEOMETRY, "no outlet cell in column nx-1");
+  if ((int)m.out_start.size() > LBM_MAX_OUTLETS) return fail(LBM_ERR_GEOMETRY, "more than LBM_MAX_OUTLETS outlets");
+  return LBM_OK;
+}
+
+// Offsets and views of a member list, uploaded into the layout's buffers.
+lbm_status layout_build(SetLayout& S, const std::vector<Member*>& ms, cudaStream_t stream) {
+  const int n = (int)ms.size();
+  S.n = n;
+  S.h_views.resize(std::max(1, n));
+  S.h_woff.assign(n + 1, 0);
+  S.h_swoff.assign(n + 1, 0);
+  long long words = 0, swords = 0, sel = 0, cells = 0;
+  for (int i = 0; i < n; ++i) {
+    const Member* mb = ms[i];
+    LatticeView v = mb->view;
+    v.word_off = (int)words;
+    v.seg_word_off = (int)swords;
+    v.sel_off = (int)sel;
+    S.h_views[i] = v;
+    words += (long long)mb->ny * mb->wpr;
+    swords += (long long)(mb->ny - 2) * mb->wpr;
+    sel += sel_capacity(mb->nx, mb->ny);
+    cells += (long long)mb->nx * mb->ny;
+    S.h_woff[i + 1] = (int)std::min<long long>(words, INT32_MAX);
+    S.h_swoff[i + 1] = (int)std::min<long long>(swords, INT32_MAX);
+  }
+  if (words >= (1ll << 31) || sel >= (1ll << 31) || cells >= (1ll << 31))
+    return fail(LBM_ERR_ARG, "set too large: total cells must stay below 2^31");
+  S.total_words = (int)words;
+  S.total_seg_words = (int)swords;
+  S.total_sel = sel;
+  S.total_cells = cells;
+  CU(S.views.reserve(sizeof(LatticeView) * std::max(1, n)));
+  CU(S.word_off.reserve(sizeof(int) * (n + 1)));
+  CU(S.seg_word_off.reserve(sizeof(int) * (n + 1)));
+  if (n > 0)
+    CU(cudaMemcpyAsync(S.views.p, S.h_views.data(), sizeof(LatticeView) * n, cudaMemcpyHostToDevice, stream));
+  CU(cudaMemcpyAsync(S.word_off.p, S.h_woff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, stream));
+  CU(cudaMemcpyAsync(S.seg_word_off.p, S.h_swoff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, stream));
+  return LBM_OK;
+}
+
+// Exchange scratch for a layout, carved from one growing buffer.
+lbm_status reserve_oc(Engine* E, const SetLayout& X) {
+  const size_t words = (size_t)X.total_words, cells = (size_t)X.total_cells, sel = (size_t)X.total_sel;
+  size_t o = 0;
+  size_t off[12];
+  const size_t sz[12] = {words * 4,     words * 4,     (words + 1) * 4, (words + 1) * 4,
+                         cells * 8,     cells * 8,     cells * 4,       cells * 4,
+                         sel * 4,       sel * 4,       8 * (size_t)std::max(1, X.n) * 4,
+                         scan_tmp_ints((long long)words) * 4};
+  for (int k = 0; k < 12; ++k) {
+    off[k] = o;
+    o += align_up(std::max<size_t>(sz[k], 16));
+  }
+  CU(E->oc_buf.reserve(o));
+  char* b = static_cast<char*>(E->oc_buf.p);
+  OcScratch& s = E->oc;
+  s.cnt_f = reinterpret_cast<int*>(b + off[0]);
+  s.cnt_s = reinterpret_cast<int*>(b + off[1]);
+  s.off_f = reinterpret_cast<int*>(b + off[2]);
+  s.off_s = reinterpret_cast<int*>(b + off[3]);
+  s.key_f = reinterpret_cast<unsigned long long*>(b + off[4]);
+  s.key_s = reinterpret_cast<unsigned long long*>(b + off[5]);
+  s.idx_f = reinterpret_cast<int*>(b + off[6]);
+  s.idx_s = reinterpret_cast<int*>(b + off[7]);
+  s.sel_f = reinterpret_cast<int*>(b + off[8]);
+  s.sel_s = reinterpret_cast<int*>(b + off[9]);
+  s.info = reinterpret_cast<int*>(b + off[10]);
+  s.scan_tmp = reinterpret_cast<int*>(b + off[11]);
+  return LBM_OK;
+}
+
+lbm_status launch_pair(Engine* E, int moments) {
+  // moments: 0 none, 1 into drho/ux/uy, 2 into drho/ux_prev/uy_prev
+  const LatticeView* views = static_cast<const LatticeView*>(E->L.views.p);
+  const SegRef* segs = static_cast<const SegRef*>(E->segs.p);
+  const int* n_segs = static_cast<const int*>(E->n_segs.p);
+  CU(launch_stream_collide(E->precision, 0, 0, views, segs, n_segs, E->step, E->stream));
+  DEBUG_SYNC(E, "stream-collide phase A");
+  CU(launch_stream_collide(E->precision, 1, moments, views, segs, n_segs, E->step, E->stream));
+  DEBUG_SYNC(E, "stream-collide phase B");
+  return LBM_OK;
+}
+
+void drop_graphs(Engine* E) {
+  for (auto& g : E->graphs)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// A captured graph is valid while the buffers and the launch shape it was
+// captured with are unchanged.
+lbm_status ensure_graph(Engine* E, int which) {
+  const void* key[4] = {E->L.views.p, E->segs.p, E->n_segs.p,
+                        reinterpret_cast<const void*>((intptr_t)E->step.warps_per_block << 32 |
+                                                      (intptr_t)(uint32_t)E->step.grid)};
+  if (!std::equal(key, key + 4, E->graph_key)) {
+    drop_graphs(E);
+    std::copy(key, key + 4, E->graph_key);
+  }
+  if (E->graphs[which]) return LBM_OK;
+  cudaGraph_t g = nullptr;
+  CU(cudaStreamBeginCapture(E->stream, cudaStreamCaptureModeThreadLocal));
+  t_capturing = true;
+  lbm_status st = LBM_OK;
+  for (int k = 0; k < kGraphPairs[which] && st == LBM_OK; ++k) st = launch_pair(E, 0);
+  t_capturing = false;
+  cudaError_t e = cudaStreamEndCapture(E->stream, &g);
+  if (st != LBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&E->graphs[which], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
+  if (debug_sync()) {
+    for (int64_t k = 0; k < pairs; ++k) {
+      lbm_status st = launch_pair(E, 0);
+      if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+  }
+  for (int which = 0; which < 3 && pairs > 0; ++which) {
+    const int64_t chunk = kGraphPairs[which];
+    const int64_t reps = pairs / chunk;
+    if (reps == 0) continue;
+    lbm_status st = ensure_graph(E, which);
+    if (st != LBM_OK) return st;
+    for (int64_t r = 0; r < reps; ++r) {
+      CU(cudaGraphLaunch(E->graphs[which], E->stream));
+      count_launches(2 * chunk);
+    }
+    pairs -= reps * chunk;
+  }
+  return LBM_OK;
+}
+
+// Launch shape: every segment its own warp, but never more blocks than fit
+// on the device at once; a persistent engine always takes the device-sized
+// grid, so its captured graphs outlive changes of the member list.
+StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale) {
+  const int bps = stream_collide_blocks_per_sm(E->precision, 0, 0, wpb);
+  const long long cap = (long long)E->sm_count * bps * blocks_per_sm_scale;
+  const long long need = ((long long)E->L.total_seg_words + wpb - 1) / wpb;
+  StepConfig c;
+  c.warps_per_block = wpb;
+  c.grid = (int)(E->persistent ? cap : std::max<long long>(1, std::min(need, cap)));
+  return c;
+}
+
+// Pick the step launch shape by timing candidate shapes on the engine's own
+// lattices.  The populations are saved and restored around the trials, and
+// every shape computes the same values per cell, so tuning changes no result.
+lbm_status autotune(Engine* E) {
+  E->tuned = true;
+  E->step = shape(E, kStepWarps, 1);
+  if (!autotune_enabled() || debug_sync()) return LBM_OK;
+  const size_t sb = storage_bytes(E->precision);
+  const int n = E->n();
+  std::vector<void*> backups(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    const size_t bytes = 9 * E->m[i]->plane * sb;
+    if (cudaMalloc(&backups[i], bytes) != cudaSuccess) {  // no room: keep the default shape
+      for (void* b : backups) cudaFree(b);
+      cudaGetLastError();
+      return LBM_OK;
+    }
+    CU(cudaMemcpyAsync(backups[i], E->m[i]->f, bytes, cudaMemcpyDeviceToDevice, E->stream));
+  }
+  std::vector<StepConfig> cand;
+  for (int wpb : {4, 8, 16})
+    for (int scale : {1, 2}) {
+      StepConfig c = shape(E, wpb, scale);
+      bool dup = false;
+      for (auto& d : cand) dup |= (d.warps_per_block == c.warps_per_block && d.grid == c.grid);
+      if (!dup) cand.push_back(c);
+    }
+  cudaEvent_t a, b;
+  CU(cudaEventCreate(&a));
+  CU(cudaEventCreate(&b));
+  float best = 1e30f;
+  StepConfig best_cfg = E->step;
+  lbm_status st = LBM_OK;
+  for (int rep = 0; rep < 2 && st == LBM_OK; ++rep) {  // first pass warms up
+    for (const StepConfig& c : cand) {
+      E->step = c;
+      cudaEventRecord(a, E->stream);
+      for (int k = 0; k < 16 && st == LBM_OK; ++k) st = launch_pair(E, 0);
+      cudaEventRecord(b, E->stream);
+      if (cudaEventSynchronize(b) != cudaSuccess) st = fail(LBM_ERR_CUDA, "autotune timing");
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep == 1 && ms < best) {
+        best = ms;
+        best_cfg = c;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  for (int i = 0; i < n; ++i)
+    cudaMemcpyAsync(E->m[i]->f, backups[i], 9 * E->m[i]->plane * sb, cudaMemcpyDeviceToDevice, E->stream);
+  cudaStreamSynchronize(E->stream);
+  for (void* q : backups) cudaFree(q);
+  E->step = best_cfg;
+  return st;
+}
+
+lbm_status ensure_pinned(Engine* E, size_t n) {
+  if (n <= E->pinned_n) return LBM_OK;
+  const size_t cap = std::max(n, E->pinned_n + E->pinned_n / 2);
+  if (E->h_result) cudaFreeHost(E->h_result);
+  if (E->h_info) cudaFreeHost(E->h_info);
+  if (E->h_count) cudaFreeHost(E->h_count);
+  if (E->h_nswap) cudaFreeHost(E->h_nswap);
+  E->h_result = nullptr;
+  E->h_info = nullptr;
+  E->h_count = nullptr;
+  E->h_nswap = nullptr;
+  E->pinned_n = 0;
+  CU(cudaMallocHost((void**)&E->h_result, sizeof(double) * kResultDoubles * cap));
+  CU(cudaMallocHost((void**)&E->h_info, sizeof(int) * 8 * cap));
+  CU(cudaMallocHost((void**)&E->h_count, sizeof(unsigned long long) * cap));
+  CU(cudaMallocHost((void**)&E->h_nswap, sizeof(int) * cap));
+  E->pinned_n = cap;
+  return LBM_OK;
+}
+
+}  // namespace
+
+// ---- members -------------------------------------------------------------
+
+Member::~Member() {
+  if (slab) cudaFree(slab);
+}
+
+size_t member_footprint(const lbm_params& p) { return plan_slab(p).total; }
+
+lbm_status check_params(const lbm_params& p) {
+  if (p.nx < 4 || p.ny < 3 || (p.nx % 2) != 0 || (int64_t)p.nx * p.ny >= (int64_t)1 << 31 ||
+      p.nx > (32 << kSegWordBits) || p.ny >= (1 << (31 - kSegWordBits)))
+    return fail(LBM_ERR_ARG, "nx must be even, 4 <= nx <= 131072, 3 <= ny < 524288, nx*ny < 2^31");
+  const size_t pitch = (size_t)(p.nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+  if (9 * pitch * (size_t)p.ny >= ((size_t)1 << 31))
+    return fail(LBM_ERR_ARG, "lattice too large: 9 * ny * pitch must stay below 2^31 elements");
+  if (!(p.tau > 0.5) || !std::isfinite(p.tau) || !std::isfinite(p.rho0) || !(p.rho0 > 0) ||
+      !std::isfinite(p.u_max))
+    return fail(LBM_ERR_ARG, "tau must be > 1/2, rho0 > 0, u_max finite");
+  if (p.outlet != LBM_OUT_CONST_RHO && p.outlet != LBM_OUT_NEUMANN) return fail(LBM_ERR_ARG, "outlet rule");
+  if (p.precision < LBM_F32 || p.precision > LBM_F16_SHIFTED) return fail(LBM_ERR_ARG, "precision");
+  if (p.reinit != LBM_REINIT_WARM && p.reinit != LBM_REINIT_COLD) return fail(LBM_ERR_ARG, "reinit");
+  if (p.residual_every < 0 || (p.residual_every % 2) != 0) return fail(LBM_ERR_ARG, "residual_every must be even");
+  if (p.ports != LBM_PORTS_REGULARIZED && p.ports != LBM_PORTS_ZOU_HE) return fail(LBM_ERR_ARG, "ports");
+  return LBM_OK;
+}
+
+lbm_status member_check(const lbm_params& p, const uint8_t* cells) {
+  if (!cells) return fail(LBM_ERR_ARG, "cell_types is NULL");
+  lbm_status st = check_params(p);
+  if (st != LBM_OK) return st;
+  Member m;
+  m.p = p;
+  m.nx = p.nx;
+  m.ny = p.ny;
+  std::vector<float> u_in;
+  return check_and_describe(m, cells, u_in);
+}
+
+lbm_status member_create(const lbm_params& p, const uint8_t* cells, cudaStream_t stream, Member** out) {
+  *out = nullptr;
+  if (!cells) return fail(LBM_ERR_ARG, "cell_types is NULL");
+  lbm_status st = check_params(p);
+  if (st != LBM_OK) return st;
+  Member* m = new Member();
+  m->p = p;
+  m->nx = p.nx;
+  m->ny = p.ny;
+  m->pitch = (p.nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+  m->wpr = (p.nx + 31) / 32;
+  m->plane = (size_t)m->ny * m->pitch;
+  std::vector<float> u_in;
+  st = check_and_describe(*m, cells, u_in);
+  if (st != LBM_OK) {
+    delete m;
+    return st;
+  }
+#define CUM(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      delete m;                                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    }                                                                                    \
+  } while (0)
+  const SlabPlan s = plan_slab(p);
+  CUM(cudaMalloc(&m->slab, s.total));
+  m->slab_bytes = s.total;
+  char* b = static_cast<char*>(m->slab);
+  m->f = b + s.f;
+  m->mask_bytes = (size_t)mask_alloc_words(m->wpr, m->ny) * 4;
+  m->mask_base = reinterpret_cast<uint32_t*>(b + s.mask);
+  m->mask0_base = reinterpret_cast<uint32_t*>(b + s.mask0);
+  const size_t fstride = align_up(m->plane * 4);
+  float** fields[5] = {&m->drho, &m->ux, &m->uy, &m->ux_prev, &m->uy_prev};
+  for (int k = 0; k < 5; ++k) *fields[k] = reinterpret_cast<float*>(b + s.fields + k * fstride);
+  m->u_in = reinterpret_cast<float*>(b + s.u_in);
+  m->d_out = reinterpret_cast<int*>(b + s.d_out);
+  m->cells = reinterpret_cast<uint8_t*>(b + s.cells);
+  m->mask = m->mask_base + mask_origin(m->wpr);
+  m->mask0 = m->mask0_base + mask_origin(m->wpr);
+  CUM(cudaMemsetAsync(m->mask_base, 0xff, m->mask_bytes, stream));  // padding = wall
+  CUM(cudaMemsetAsync(m->mask0_base, 0xff, m->mask_bytes, stream));
+  std::vector<int> outs(2 * LBM_MAX_OUTLETS, 0);
+  std::copy(m->out_start.begin(), m->out_start.end(), outs.begin());
+  std::copy(m->out_len.begin(), m->out_len.end(), outs.begin() + LBM_MAX_OUTLETS);
+  // pageable sources: each call returns once its source has been staged
+  CUM(cudaMemcpyAsync(m->u_in, u_in.data(), (size_t)m->ny * 4, cudaMemcpyHostToDevice, stream));
+  CUM(cudaMemcpyAsync(m->d_out, outs.data(), outs.size() * 4, cudaMemcpyHostToDevice, stream));
+  CUM(cudaMemcpyAsync(m->cells, cells, (size_t)m->nx * m->ny, cudaMemcpyHostToDevice, stream));
+  CUM(launch_pack_mask(m->cells, m->nx, m->ny, m->wpr, m->mask0, stream));
+#undef CUM
+  LatticeView& v = m->view;
+  std::memset(&v, 0, sizeof(v));
+  v.f = m->f;
+  v.mask = m->mask;
+  v.drho = m->drho;
+  v.ux = m->ux;
+  v.uy = m->uy;
+  v.ux_prev = m->ux_prev;
+  v.uy_prev = m->uy_prev;
+  v.u_in = m->u_in;
+  v.out_start = m->d_out;
+  v.out_len = m->d_out + LBM_MAX_OUTLETS;
+  v.plane = (long long)m->plane;
+  v.f_elems = 9 * (long long)m->plane;
+  v.rho0d = p.rho0;
+  v.mu = p.rho0 * ((p.tau - 0.5) / 3.0);
+  v.nx = m->nx;
+  v.ny = m->ny;
+  v.pitch = m->pitch;
+  v.wpr = m->wpr;
+  v.omega = (float)(1.0 / p.tau);
+  v.rho0 = (float)p.rho0;
+  v.outlet_rule = p.outlet;
+  v.port_scheme = p.ports;
+  v.n_outlets = (int)m->out_start.size();
+  *out = m;
+  return LBM_OK;
+}
+
+lbm_status member_reset(Member* m, cudaStream_t stream) {
+  CU(cudaMemcpyAsync(m->mask_base, m->mask0_base, m->mask_bytes, cudaMemcpyDeviceToDevice, stream));
+  CU(cudaMemsetAsync(m->f, 0, 9 * m->plane * storage_bytes(m->p.precision), stream));  // g = 0: rest at rho0
+  CU(cudaMemsetAsync(m->drho, 0, 5 * align_up(m->plane * 4), stream));                 // the five fields
+  m->steps_done = 0;
+  return LBM_OK;
+}
+
+// ---- growing buffers -------------------------------------------------------
+
+cudaError_t GrowBuf::reserve(size_t bytes, bool* moved) {
+  if (moved) *moved = false;
+  if (bytes <= cap && p) return cudaSuccess;
+  const size_t want = std::max<size_t>(std::max<size_t>(bytes, 256), cap + cap / 2);
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    return e;
+  }
+  cap = want;
+  if (moved) *moved = true;
+  return cudaSuccess;
+}
+
+void GrowBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+}
+
+// ---- engine ----------------------------------------------------------------
+
+Engine::~Engine() {
+  if (stream) cudaStreamSynchronize(stream);
+  for (auto& g : graphs)
+    if (g) cudaGraphExecDestroy(g);
+  if (own_members)
+    for (Member* x : m) delete x;
+  for (GrowBuf* b : {&L.views, &L.word_off, &L.seg_word_off, &XL.views, &XL.word_off, &XL.seg_word_off, &segs,
+                     &n_segs, &seg_scratch, &partials, &result, &fluid_dev, &n_swap_dev, &dense_f, &oc_buf})
+    b->release();
+  if (h_result) cudaFreeHost(h_result);
+  if (h_info) cudaFreeHost(h_info);
+  if (h_count) cudaFreeHost(h_count);
+  if (h_nswap) cudaFreeHost(h_nswap);
+  if (ev_begin) cudaEventDestroy(ev_begin);
+  if (ev_end) cudaEventDestroy(ev_end);
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool persistent, Engine** out) {
+  *out = nullptr;
+  Engine* E = new Engine();
+  E->precision = precision;
+  E->residual_every = residual_every;
+  E->persistent = persistent;
+#define CUE(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      delete E;                                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    }                                                                                    \
+  } while (0)
+  int dev = 0;
+  CUE(cudaGetDevice(&dev));
+  CUE(cudaDeviceGetAttribute(&E->sm_count, cudaDevAttrMultiProcessorCount, dev));
+  if (cuda_stream) {
+    E->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    CUE(cudaStreamCreateWithFlags(&E->stream, cudaStreamNonBlocking));
+    E->own_stream = true;
+  }
+  CUE(cudaEventCreate(&E->ev_begin));
+  CUE(cudaEventCreate(&E->ev_end));
+  CUE(E->n_segs.reserve(sizeof(int)));
+#undef CUE
+  E->step = shape(E, kStepWarps, 1);
+  *out = E;
+  return LBM_OK;
+}
+
+lbm_status rebuild_worklist(Engine* E) {
+  if (E->n() == 0) return LBM_OK;
+  CU(launch_build_segments(static_cast<const LatticeView*>(E->L.views.p), static_cast<const int*>(E->L.seg_word_off.p),
+                           E->n(), E->L.total_seg_words, static_cast<int*>(E->seg_scratch.p),
+                           static_cast<SegRef*>(E->segs.p), static_cast<int*>(E->n_segs.p), E->stream));
+  CU(launch_count_fluid(static_cast<const LatticeView*>(E->L.views.p), static_cast<const int*>(E->L.word_off.p),
+                        E->n(), E->L.total_words, static_cast<unsigned long long*>(E->fluid_dev.p), E->stream));
+  DEBUG_SYNC(E, "work-list");
+  return LBM_OK;
+}
+
+lbm_status engine_set_members(Engine* E, const std::vector<Member*>& members) {
+  for (Member* mb : members)
+    if (mb->p.precision != E->precision) return fail(LBM_ERR_ARG, "all lattices of a set share one precision");
+  E->m = members;
+  const size_t n = members.size();
+  lbm_status st = layout_build(E->L, E->m, E->stream);
+  if (st != LBM_OK) return st;
+  long long max_cells = 0;
+  for (Member* mb : members) max_cells = std::max<long long>(max_cells, (long long)mb->nx * mb->ny);
+  const size_t nn = std::max<size_t>(1, n);
+  CU(E->segs.reserve(sizeof(SegRef) * std::max(1, E->L.total_seg_words)));
+  CU(E->seg_scratch.reserve(segment_scratch_ints(E->L.total_seg_words) * sizeof(int)));
+  CU(E->partials.reserve(sizeof(double) * 2 * kResidualBlocks * nn));
+  CU(E->result.reserve(sizeof(double) * kResultDoubles * nn));
+  CU(E->fluid_dev.reserve(sizeof(unsigned long long) * nn));
+  CU(E->n_swap_dev.reserve(sizeof(int) * nn));
+  CU(E->dense_f.reserve((size_t)std::max<long long>(1, max_cells) * 4));
+  st = ensure_pinned(E, nn);
+  if (st != LBM_OK) return st;
+  if (!E->tuned || E->persistent) E->step = shape(E, E->step.warps_per_block, 1);
+  if (n == 0) return LBM_OK;
+  st = rebuild_worklist(E);
+  if (st != LBM_OK) return st;
+  CU(cudaMemcpyAsync(E->h_count, E->fluid_dev.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost,
+                     E->stream));
+  CU(cudaStreamSynchronize(E->stream));
+  for (size_t i = 0; i < n; ++i) E->m[i]->fluid_cells = (int64_t)E->h_count[i];
+  return LBM_OK;
+}
+
+lbm_status engine_reset(Engine* E) {
+  for (Member* mb : E->m) {
+    lbm_status st = member_reset(mb, E->stream);
+    if (st != LBM_OK) return st;
+  }
+  lbm_status st = rebuild_worklist(E);
+  if (st != LBM_OK) return st;
+  CU(cudaMemcpyAsync(E->h_count, E->fluid_dev.p, sizeof(unsigned long long) * E->n(), cudaMemcpyDeviceToHost,
+                     E->stream));
+  CU(cudaStreamSynchronize(E->stream));
+  for (int i = 0; i < E->n(); ++i) E->m[i]->fluid_cells = (int64_t)E->h_count[i];
+  E->solved = false;
+  return LBM_OK;
+}
+
+lbm_status engine_create(int n, const lbm_params* params, const uint8_t* const* cells, void* cuda_stream,
+                         Engine** out) {
+  *out = nullptr;
+  if (n < 1) return fail(LBM_ERR_ARG, "need at least one lattice");
+  for (int i = 1; i < n; ++i)
+    if (params[i].precision != params[0].precision || params[i].residual_every != params[0].residual_every)
+      return fail(LBM_ERR_ARG, "all lattices of a batch share precision and residual_every");
+  for (int i = 0; i < n; ++i) {
+    if (!cells[i]) return fail(LBM_ERR_ARG, "cell_types is NULL");
+    lbm_status st = check_params(params[i]);
+    if (st != LBM_OK) return st;
+  }
+  Engine* E = nullptr;
+  lbm_status st = engine_new(params[0].precision, params[0].residual_every, cuda_stream, false, &E);
+  if (st != LBM_OK) return st;
+  std::vector<Member*> ms;
+  for (int i = 0; i < n && st == LBM_OK; ++i) {
+    Member* mb = nullptr;
+    st = member_create(params[i], cells[i], E->stream, &mb);
+    if (st == LBM_OK) {
+      ms.push_back(mb);
+      st = member_reset(mb, E->stream);
+    }
+  }
+  E->m = ms;  // owned from here on, also on failure
+  if (st == LBM_OK) st = engine_set_members(E, ms);
+  if (st == LBM_OK) st = reserve_oc(E, E->L);
+  if (st != LBM_OK) {
+    delete E;
+    return st;
+  }
+  *out = E;
+  return LBM_OK;
+}
+
+void account_steps(Engine* E, int64_t n_steps) {
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, E->ev_begin, E->ev_end) == cudaSuccess) E->step_ms += ms;
+  E->step_launches += n_steps;
+  for (Member* m : E->m) E->fluid_updates += n_steps * m->fluid_cells;
+}
+
+void fill_result(Engine* E, int i, lbm_solve_result* out) {
+  const double* r = E->h_result + (size_t)i * kResultDoubles;
+  const Member* m = E->m[i];
+  std::memset(out, 0, sizeof(*out));
+  out->dp = r[0];
+  out->m_in = r[1];
+  out->residual = r[2];
+  out->n_outlets = (int)m->out_start.size();
+  out->theta = r[8];
+  out->dg = r[9];
+  for (int j = 0; j < out->n_outlets; ++j) out->m_out[j] = r[10 + j];
+  out->steps_done = m->steps_done;
+  out->fluid_cells = m->fluid_cells;
+}
+
+lbm_status enqueue_steps_and_reduce(Engine* E, int64_t n_steps, bool with_res) {
+  const int K = E->residual_every;
+  lbm_status st;
+  CU(cudaEventRecord(E->ev_begin, E->stream));
+  if (with_res) {
+    if ((st = run_plain_pairs(E, (n_steps - K) / 2 - 1)) != LBM_OK) return st;
+    if ((st = launch_pair(E, 2)) != LBM_OK) return st;
+    if ((st = run_plain_pairs(E, K / 2 - 1)) != LBM_OK) return st;
+  } else {
+    if ((st = run_plain_pairs(E, n_steps / 2 - 1)) != LBM_OK) return st;
+  }
+  if ((st = launch_pair(E, 1)) != LBM_OK) return st;
+  CU(cudaEventRecord(E->ev_end, E->stream));
+  const LatticeView* views = static_cast<const LatticeView*>(E->L.views.p);
+  double* partials = static_cast<double*>(E->partials.p);
+  if (with_res) {
+    CU(launch_residual_partials(views, E->n(), partials, E->stream));
+    DEBUG_SYNC(E, "residual partials");
+  }
+  CU(launch_finalize(views, E->n(), partials, with_res ? 1 : 0, static_cast<double*>(E->result.p), E->stream));
+  DEBUG_SYNC(E, "finalize");
+  CU(cudaMemcpyAsync(E->h_result, E->result.p, sizeof(double) * kResultDoubles * E->n(), cudaMemcpyDeviceToHost,
+                     E->stream));
+  return LBM_OK;
+}
+
+lbm_status enqueue_solve(Engine* E, int64_t n_steps) {
+  if (!E->tuned && n_steps >= 256) {
+    lbm_status st = autotune(E);
+    if (st != LBM_OK) return st;
+  }
+  const int K = E->residual_every;
+  const bool with_res = K >= 2 && (K % 2) == 0 && n_steps >= (int64_t)K + 2;
+  return enqueue_steps_and_reduce(E, n_steps, with_res);
+}
+
+lbm_status enqueue_exchange(Engine* E, const std::vector<int>& which, const int32_t* n_swap) {
+  const int nx_ = (int)which.size();
+  bool all = nx_ == E->n();
+  for (int k = 0; all && k < nx_; ++k) all = which[k] == k;
+  const SetLayout* X = &E->L;
+  if (!all) {
+    std::vector<Member*> xm;
+    for (int i : which) xm.push_back(E->m[i]);
+    lbm_status st = layout_build(E->XL, xm, E->stream);
+    if (st != LBM_OK) return st;
+    X = &E->XL;
+  }
+  lbm_status st = reserve_oc(E, *X);
+  if (st != LBM_OK) return st;
+  for (int k = 0; k < nx_; ++k) E->h_nswap[k] = n_swap[k];
+  CU(cudaMemcpyAsync(E->n_swap_dev.p, E->h_nswap, sizeof(int) * nx_, cudaMemcpyHostToDevice, E->stream));
+  const LatticeView* xv = static_cast<const LatticeView*>(X->views.p);
+  CU(launch_oc_select(xv, static_cast<const int*>(X->word_off.p), nx_, X->total_words,
+                      static_cast<const int*>(E->n_swap_dev.p), E->oc, E->stream));
+  DEBUG_SYNC(E, "selection");
+  CU(launch_oc_apply(E->precision, xv, nx_, E->oc, E->stream));
+  DEBUG_SYNC(E, "exchange");
+  const size_t sb = storage_bytes(E->precision);
+  for (int i : which) {
+    Member* m = E->m[i];
+    if (m->p.reinit == LBM_REINIT_COLD) CU(cudaMemsetAsync(m->f, 0, 9 * m->plane * sb, E->stream));
+  }
+  st = rebuild_worklist(E);
+  if (st != LBM_OK) return st;
+  CU(cudaMemcpyAsync(E->h_info, E->oc.info, sizeof(int) * 8 * nx_, cudaMemcpyDeviceToHost, E->stream));
+  CU(cudaMemcpyAsync(E->h_count, E->fluid_dev.p, sizeof(unsigned long long) * E->n(), cudaMemcpyDeviceToHost,
+                     E->stream));
+  return LBM_OK;
+}
+
+lbm_status engine_solve(Engine* E, int64_t n_steps, lbm_solve_result* out) {
+  if (n_steps < 2 || (n_steps % 2) != 0) return fail(LBM_ERR_ARG, "n_steps must be even and >= 2");
+  lbm_status st = enqueue_solve(E, n_steps);
+  if (st != LBM_OK) return st;
+  CU(cudaStreamSynchronize(E->stream));
+  for (Member* m : E->m) m->steps_done += n_steps;
+  E->solved = true;
+  account_steps(E, n_steps);
+  bool bad = false;
+  for (int i = 0; i < E->n(); ++i) {
+    fill_result(E, i, out + i);
+    bad |= E->h_result[(size_t)i * kResultDoubles + 7] != 0.0;
+  }
+  if (bad) return fail(LBM_ERR_DIVERGED, "non-finite pressure drop, flow rate or residual");
+  return LBM_OK;
+}
+
+lbm_status engine_optimize(Engine* E, const int32_t* n_swap, int64_t n_steps, lbm_opt_result* out) {
+  if (n_steps < 2 || (n_steps % 2) != 0) return fail(LBM_ERR_ARG, "n_steps must be even and >= 2");
+  for (int i = 0; i < E->n(); ++i)
+    if (n_swap[i] < 0) return fail(LBM_ERR_ARG, "n_swap must be >= 0");
+  if (!E->solved) return fail(LBM_ERR_ARG, "an exchange needs a field: solve first");
+  std::vector<int> all(E->n());
+  for (int i = 0; i < E->n(); ++i) all[i] = i;
+  lbm_status st = enqueue_exchange(E, all, n_swap);
+  if (st != LBM_OK) return st;
+  st = enqueue_solve(E, n_steps);
+  if (st != LBM_OK) return st;
+  CU(cudaStreamSynchronize(E->stream));
+  bool nan = false, count_changed = false, bad = false;
+  for (int i = 0; i < E->n(); ++i) {
+    Member* m = E->m[i];
+    m->steps_done += n_steps;
+    const int64_t before = m->fluid_cells;
+    m->fluid_cells = (int64_t)E->h_count[i];
+    count_changed |= m->fluid_cells != before;
+    nan |= E->h_info[8 * i + 3] != 0;
+    bad |= E->h_result[(size_t)i * kResultDoubles + 7] != 0.0;
+  }
+  account_steps(E, n_steps);
+  for (int i = 0; i < E->n(); ++i) {
+    std::memset(out + i, 0, sizeof(lbm_opt_result));
+    out[i].n_swapped = E->h_info[8 * i];
+    out[i].fluid_count = E->m[i]->fluid_cells;
+    fill_result(E, i, &out[i].solve);
+  }
+  if (nan) return fail(LBM_ERR_DIVERGED, "a dynamic-pressure or stress score is NaN");
+  if (count_changed) return fail(LBM_ERR_CUDA, "fluid cell count changed by the exchange");
+  if (bad) return fail(LBM_ERR_DIVERGED, "non-finite pressure drop, flow rate or residual");
+  return LBM_OK;
+}
+
+lbm_status engine_read(Engine* E, int i, uint32_t which, void* dst, size_t dst_bytes) {
+  if (i < 0 || i >= E->n()) return fail(LBM_ERR_ARG, "member out of range");
+  if (!dst) return fail(LBM_ERR_ARG, "dst is NULL");
+  Member* m = E->m[i];
+  const size_t nx = m->nx, ny = m->ny, ncell = nx * ny;
+  const size_t sb = storage_bytes(E->precision);
+  switch (which) {
+    case LBM_FIELD_MASK:
+      if (dst_bytes < ncell) return fail(LBM_ERR_ARG, "dst too small");
+      CU(launch_unpack_mask(m->mask, m->nx, m->ny, m->wpr, m->cells, E->stream));
+      CU(cudaMemcpyAsync(dst, m->cells, ncell, cudaMemcpyDefault, E->stream));
+      break;
+    case LBM_FIELD_RHO:
+      if (dst_bytes < ncell * 4) return fail(LBM_ERR_ARG, "dst too small");
+      CU(launch_rho_from_drho(m->drho, (float)m->p.rho0, m->mask, m->nx, m->ny, m->pitch, m->wpr,
+                              static_cast<float*>(E->dense_f.p), E->stream));
+      CU(cudaMemcpyAsync(dst, E->dense_f.p, ncell * 4, cudaMemcpyDefault, E->stream));
+      break;
+    case LBM_FIELD_DRHO:
+    case LBM_FIELD_UX:
+    case LBM_FIELD_UY: {
+      if (dst_bytes < ncell * 4) return fail(LBM_ERR_ARG, "dst too small");
+      const float* src = which == LBM_FIELD_DRHO ? m->drho : which == LBM_FIELD_UX ? m->ux : m->uy;
+      CU(cudaMemcpy2DAsync(dst, nx * 4, src, (size_t)m->pitch * 4, nx * 4, ny, cudaMemcpyDefault, E->stream));
+      break;
+    }
+    case LBM_FIELD_POPS:
+      if (dst_bytes < 9 * ncell * sb) return fail(LBM_ERR_ARG, "dst too small");
+      for (int k = 0; k < 9; ++k)
+        CU(cudaMemcpy2DAsync(static_cast<char*>(dst) + k * ncell * sb, nx * sb,
+                             static_cast<const char*>(m->f) + k * m->plane * sb, (size_t)m->pitch * sb, nx * sb,
+                             ny, cudaMemcpyDefault, E->stream));
+      break;
+    default:
+      return fail(LBM_ERR_ARG, "which must be exactly one LBM_FIELD_* value");
+  }
+  CU(cudaStreamSynchronize(E->stream));
+  return LBM_OK;
+}
+
+lbm_status engine_kernel_time(Engine* E, int reset, double* ms, int64_t* launches, int64_t* fluid_updates) {
+  if (ms) *ms = E->step_ms;
+  if (launches) *launches = E->step_launches;
+  if (fluid_updates) *fluid_updates = E->fluid_updates;
+  if (reset) {
+    E->step_ms = 0.0;
+    E->step_launches = 0;
+    E->fluid_updates = 0;
+  }
+  return LBM_OK;
+}
+
+}  // namespace lbm

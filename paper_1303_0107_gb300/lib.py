@@ -56,6 +56,36 @@ class OptResult(ctypes.Structure):
                 ("fluid_count", ctypes.c_int64), ("solve", SolveResult)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_active", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64), ("max_tick_steps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("params", Params), ("cell_types", ctypes.c_void_p), ("n_steps", ctypes.c_int64),
+                ("n_iter", ctypes.c_int32), ("n_swap", ctypes.c_int32), ("tag", ctypes.c_int64),
+                ("out_mask", ctypes.c_void_p), ("out_drho", ctypes.c_void_p), ("out_ux", ctypes.c_void_p),
+                ("out_uy", ctypes.c_void_p)]
+
+
+class Served(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_int64), ("status", ctypes.c_int32), ("n_swapped", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("fluid_updates", ctypes.c_int64), ("footprint_bytes", ctypes.c_int64),
+                ("dp_first", ctypes.c_double), ("last", SolveResult)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("ticks", ctypes.c_int64), ("exchanges", ctypes.c_int64),
+                ("fluid_updates", ctypes.c_int64), ("resident_bytes", ctypes.c_int64),
+                ("peak_resident_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("peak_device_bytes", ctypes.c_int64), ("active", ctypes.c_int32),
+                ("peak_active", ctypes.c_int32), ("queued", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("busy_s", ctypes.c_double), ("step_ms", ctypes.c_double), ("budget_bytes", ctypes.c_int64)]
+
+
 _LIB = None
 _VP = ctypes.c_void_p
 
@@ -105,13 +135,27 @@ def load_library(path=None):
     L.lbm_batch_destroy.restype = None
     L.lbm_select_swaps_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                            _VP, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP]
+    S = _VP
+    L.lbm_server_create.argtypes = [ctypes.POINTER(ServerConfig), _VP, ctypes.POINTER(S)]
+    L.lbm_server_submit.argtypes = [S, ctypes.POINTER(Request)]
+    L.lbm_server_poll.argtypes = [S, ctypes.POINTER(Served), ctypes.c_int32, ctypes.c_int32]
+    L.lbm_server_poll.restype = ctypes.c_int32
+    L.lbm_server_wait_idle.argtypes = [S, ctypes.c_int32]
+    L.lbm_server_get_stats.argtypes = [S, ctypes.POINTER(ServerStats)]
+    L.lbm_server_now.argtypes = [S]
+    L.lbm_server_now.restype = ctypes.c_double
+    L.lbm_server_footprint.argtypes = [ctypes.POINTER(Params), ctypes.c_int32]
+    L.lbm_server_footprint.restype = ctypes.c_int64
+    L.lbm_server_destroy.argtypes = [S]
+    L.lbm_server_destroy.restype = None
     L.lbm_bytes_per_fluid_update.argtypes = [ctypes.c_int32]
     L.lbm_bytes_per_fluid_update.restype = ctypes.c_double
     for name in ("lbm_create_geometry", "lbm_solve", "lbm_optimize_step", "lbm_read_fields",
                  "lbm_load_state", "lbm_reset", "lbm_select_swaps", "lbm_kernel_time",
                  "lbm_select_swaps_noalloc", "lbm_step_config", "lbm_batch_create", "lbm_batch_solve",
                  "lbm_batch_optimize_step", "lbm_batch_read_fields", "lbm_batch_reset",
-                 "lbm_batch_kernel_time", "lbm_batch_step_config"):
+                 "lbm_batch_kernel_time", "lbm_batch_step_config", "lbm_server_create", "lbm_server_submit",
+                 "lbm_server_wait_idle", "lbm_server_get_stats"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -335,3 +379,97 @@ class Batch:
         _check(load_library().lbm_batch_step_config(self._b, ctypes.byref(w), ctypes.byref(g)),
                "lbm_batch_step_config")
         return w.value, g.value
+
+
+class Server:
+    """Request loop with continuous batching (lbm_server_*).
+
+    submit() queues a solve (n_iter = 0) or an optimisation (n_iter
+    iterations after the first solve) of a geometry and returns at once; the
+    library's scheduler thread admits requests by device footprint, steps all
+    resident requests in the same launches, and poll() returns finished ones
+    as dicts.  With keep_fields=True the final mask, drho, ux and uy come back
+    in the result.
+    """
+
+    def __init__(self, precision=F32, max_active=256, hbm_budget_bytes=0, max_tick_steps=1000, stream=None):
+        L = load_library()
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        self.precision = int(precision)
+        cfg = ServerConfig(int(precision), int(max_active), int(hbm_budget_bytes), int(max_tick_steps), 0)
+        self._s = _VP()
+        self._outs = {}
+        _check(L.lbm_server_create(ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(self._s)),
+               "lbm_server_create")
+
+    @staticmethod
+    def params_for(cells, tau, u_max, precision=F32, rho0=1.0, outlet=OUT_CONST_RHO, reinit=REINIT_WARM,
+                   ports=PORTS_REGULARIZED):
+        ny, nx = np.asarray(cells).shape
+        return Params(nx, ny, float(tau), float(rho0), float(u_max), int(outlet), int(precision), int(reinit), 0,
+                      int(ports), 0)
+
+    @staticmethod
+    def footprint(nx, ny, n_iter=0, precision=F32):
+        p = Params(int(nx), int(ny), 0.6, 1.0, 0.0, 0, int(precision), 0, 0, 0, 0)
+        return int(load_library().lbm_server_footprint(ctypes.byref(p), int(n_iter)))
+
+    def submit(self, tag, cells, tau, u_max, n_steps, n_iter=0, n_swap=0, keep_fields=False, **kw):
+        cells = np.ascontiguousarray(cells, dtype=np.uint8)
+        ny, nx = cells.shape
+        r = Request()
+        r.params = self.params_for(cells, tau, u_max, precision=self.precision, **kw)
+        r.cell_types = cells.ctypes.data
+        r.n_steps, r.n_iter, r.n_swap, r.tag = int(n_steps), int(n_iter), int(n_swap), int(tag)
+        if keep_fields:
+            outs = dict(mask=np.empty((ny, nx), np.uint8), drho=np.empty((ny, nx), np.float32),
+                        ux=np.empty((ny, nx), np.float32), uy=np.empty((ny, nx), np.float32))
+            r.out_mask, r.out_drho, r.out_ux, r.out_uy = [outs[k].ctypes.data for k in ("mask", "drho", "ux", "uy")]
+            self._outs[int(tag)] = outs
+        st = load_library().lbm_server_submit(self._s, ctypes.byref(r))
+        if st != 0:
+            self._outs.pop(int(tag), None)
+        _check(st, "lbm_server_submit")
+
+    def poll(self, max_out=256, wait_ms=0):
+        buf = (Served * int(max_out))()
+        k = load_library().lbm_server_poll(self._s, buf, int(max_out), int(wait_ms))
+        out = []
+        for x in buf[:k]:
+            d = dict(tag=x.tag, status=x.status, n_swapped=x.n_swapped, t_submit=x.t_submit, t_admit=x.t_admit,
+                     t_done=x.t_done, fluid_updates=x.fluid_updates, footprint_bytes=x.footprint_bytes,
+                     dp_first=x.dp_first, last=x.last.to_dict())
+            f = self._outs.pop(int(x.tag), None)
+            if f is not None:
+                d["fields"] = f
+            out.append(d)
+        return out
+
+    def wait_idle(self, timeout_s=600.0):
+        _check(load_library().lbm_server_wait_idle(self._s, int(timeout_s * 1000)), "lbm_server_wait_idle")
+
+    def stats(self):
+        st = ServerStats()
+        _check(load_library().lbm_server_get_stats(self._s, ctypes.byref(st)), "lbm_server_get_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_ if k != "reserved"}
+
+    def now(self):
+        return float(load_library().lbm_server_now(self._s))
+
+    def close(self):
+        if self._s:
+            load_library().lbm_server_destroy(self._s)
+            self._s = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -49,6 +49,18 @@ def test_host_only_entry_points(built_lib):
     assert L.lbm_create_geometry(None, None, None, ctypes.byref(h)) == 1
     assert not h.value
     L.lbm_destroy(None)
+    # server: configuration checks and the footprint rule are host-only
+    srv = ctypes.c_void_p()
+    bad = lib.ServerConfig(lib.F32, 0, 0, 100, 0)  # no slot
+    assert L.lbm_server_create(ctypes.byref(bad), None, ctypes.byref(srv)) == 1 and not srv.value
+    odd = lib.ServerConfig(lib.F32, 4, 0, 101, 0)  # odd tick
+    assert L.lbm_server_create(ctypes.byref(odd), None, ctypes.byref(srv)) == 1
+    L.lbm_server_destroy(None)
+    small = L.lbm_server_footprint(ctypes.byref(lib.Params(128, 64, 0.8, 1.0, 0.05, 0, 0, 0, 0, 0, 0)), 0)
+    opt = L.lbm_server_footprint(ctypes.byref(lib.Params(128, 64, 0.8, 1.0, 0.05, 0, 0, 0, 0, 0, 0)), 5)
+    half = L.lbm_server_footprint(ctypes.byref(lib.Params(128, 64, 0.8, 1.0, 0.05, 0, 1, 0, 0, 0, 0)), 0)
+    # FP32 populations alone are 9 * 64 * 128 * 4 bytes; optimising adds exchange scratch
+    assert small > 9 * 64 * 128 * 4 and opt > small > half
 
 
 def test_struct_layouts_match_header():
@@ -56,3 +68,36 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(lib.Params) == 56
     assert ctypes.sizeof(lib.SolveResult) == 8 * 3 + 8 + 8 * 64 + 8 * 2 + 8 * 2
     assert ctypes.sizeof(lib.OptResult) == 16 + ctypes.sizeof(lib.SolveResult)
+
+
+def test_struct_layouts_match_a_c_compiler(tmp_path):
+    """sizeof and field offsets of the ABI structs as gcc lays them out from
+    include/lbm.h, against the ctypes mirrors of the binding."""
+    import shutil
+    import subprocess
+    from paper_1303_0107_gb300 import lib
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    checks = [("lbm_params", lib.Params, ["tau", "ports"]),
+              ("lbm_solve_result", lib.SolveResult, ["m_out", "fluid_cells"]),
+              ("lbm_opt_result", lib.OptResult, ["solve"]),
+              ("lbm_server_config", lib.ServerConfig, ["hbm_budget_bytes", "max_tick_steps"]),
+              ("lbm_request", lib.Request, ["cell_types", "n_steps", "tag", "out_uy"]),
+              ("lbm_served", lib.Served, ["t_done", "dp_first", "last"]),
+              ("lbm_server_stats", lib.ServerStats, ["active", "busy_s", "budget_bytes"])]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', "int main(void) {"]
+    for cname, _, fields in checks:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = []
+    for _, ct, fields in checks:
+        want.append(ctypes.sizeof(ct))
+        want += [getattr(ct, f).offset for f in fields]
+    assert got == want
