@@ -227,9 +227,16 @@ uint64_t lbm_kernel_launches(void);
 lbm_status lbm_kernel_time(lbm_handle h, int reset, double* ms, int64_t* launches,
                            int64_t* fluid_updates);
 
-/* Launch shape the handle's time steps use (warps per block, blocks): tuned
- * on the handle's own lattice at its first solve of 256 steps or more.   */
-lbm_status lbm_step_config(lbm_handle h, int32_t* warps_per_block, int32_t* grid);
+/* Launch shape the handle's time steps use: warps per block, blocks, and
+ * persistent = 1 when every run of time steps is one cooperative launch with
+ * grid-wide barriers between phases (0: one launch per phase).  Tuned on the
+ * handle's own lattice at its first solve of 256 steps or more, unless set
+ * with lbm_set_step_config.  Any output pointer may be NULL.               */
+lbm_status lbm_step_config(lbm_handle h, int32_t* warps_per_block, int32_t* grid, int32_t* persistent);
+/* Fix the launch shape (and skip tuning): warps_per_block 4, 8 or 16 (8 or 16
+ * when persistent); the grid is sized for the device.  Every shape computes
+ * the same values, so this changes timings only.                          */
+lbm_status lbm_set_step_config(lbm_handle h, int32_t warps_per_block, int32_t persistent);
 
 /* ---- batches -------------------------------------------------------------
  * Many candidate geometries (Sec. 2.3 applied to each) stepped together: one
@@ -258,8 +265,9 @@ lbm_status lbm_batch_reset(lbm_batch b);
 /* As lbm_kernel_time, for the batch's time steps (fluid_updates over all members). */
 lbm_status lbm_batch_kernel_time(lbm_batch b, int reset, double* ms, int64_t* launches,
                                  int64_t* fluid_updates);
-/* As lbm_step_config.                                                    */
-lbm_status lbm_batch_step_config(lbm_batch b, int32_t* warps_per_block, int32_t* grid);
+/* As lbm_step_config / lbm_set_step_config.                               */
+lbm_status lbm_batch_step_config(lbm_batch b, int32_t* warps_per_block, int32_t* grid, int32_t* persistent);
+lbm_status lbm_batch_set_step_config(lbm_batch b, int32_t warps_per_block, int32_t persistent);
 void lbm_batch_destroy(lbm_batch b);
 
 /* ---- serving ---------------------------------------------------------------

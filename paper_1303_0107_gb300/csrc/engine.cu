@@ -35,6 +35,15 @@ bool debug_sync() {
   return on;
 }
 
+// LBM_PERSISTENT=0 keeps the persistent step kernel out of the tuner's candidates.
+bool persistent_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("LBM_PERSISTENT");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 bool autotune_enabled() {
   static const bool on = [] {
     const char* e = std::getenv("LBM_AUTOTUNE");
@@ -255,7 +264,17 @@ lbm_status ensure_graph(Engine* E, int which) {
   return LBM_OK;
 }
 
+lbm_status run_persistent(Engine* E, int64_t pairs) {
+  if (pairs <= 0) return LBM_OK;
+  CU(launch_stream_collide_persistent(E->precision, static_cast<const LatticeView*>(E->L.views.p),
+                                      static_cast<const SegRef*>(E->segs.p), static_cast<const int*>(E->n_segs.p),
+                                      (int)pairs, E->step, static_cast<StepBarrier*>(E->bar.p), E->stream));
+  E->bar_used = true;
+  return LBM_OK;
+}
+
 lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
+  if (E->step.persistent && !debug_sync()) return run_persistent(E, pairs);
   if (debug_sync()) {
     for (int64_t k = 0; k < pairs; ++k) {
       lbm_status st = launch_pair(E, 0);
@@ -279,7 +298,7 @@ lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
 }
 
 // Launch shape: every segment its own warp, but never more blocks than fit
-// on the device at once; a persistent engine always takes the device-sized
+// on the device at once; a fixed-grid engine always takes the device-sized
 // grid, so its captured graphs outlive changes of the member list.
 StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale) {
   const int bps = stream_collide_blocks_per_sm(E->precision, 0, 0, wpb);
@@ -287,7 +306,18 @@ StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale) {
   const long long need = ((long long)E->L.total_seg_words + wpb - 1) / wpb;
   StepConfig c;
   c.warps_per_block = wpb;
-  c.grid = (int)(E->persistent ? cap : std::max<long long>(1, std::min(need, cap)));
+  c.grid = (int)(E->fixed_grid ? cap : std::max<long long>(1, std::min(need, cap)));
+  c.persistent = 0;
+  return c;
+}
+
+// The persistent shape: one cooperative launch per run of pairs, as many
+// blocks as are resident at once.
+StepConfig persistent_shape(Engine* E, int wpb) {
+  StepConfig c;
+  c.warps_per_block = wpb;
+  c.grid = stream_collide_persistent_grid(E->precision, wpb);
+  c.persistent = 1;
   return c;
 }
 
@@ -318,6 +348,11 @@ lbm_status autotune(Engine* E) {
       for (auto& d : cand) dup |= (d.warps_per_block == c.warps_per_block && d.grid == c.grid);
       if (!dup) cand.push_back(c);
     }
+  if (persistent_enabled())
+    for (int wpb : {8, 16}) {
+      StepConfig c = persistent_shape(E, wpb);
+      if (c.grid > 0) cand.push_back(c);
+    }
   cudaEvent_t a, b;
   CU(cudaEventCreate(&a));
   CU(cudaEventCreate(&b));
@@ -328,11 +363,22 @@ lbm_status autotune(Engine* E) {
     for (const StepConfig& c : cand) {
       E->step = c;
       cudaEventRecord(a, E->stream);
-      for (int k = 0; k < 16 && st == LBM_OK; ++k) st = launch_pair(E, 0);
+      if (c.persistent) {
+        st = run_persistent(E, 16);
+      } else {
+        for (int k = 0; k < 16 && st == LBM_OK; ++k) st = launch_pair(E, 0);
+      }
       cudaEventRecord(b, E->stream);
       if (cudaEventSynchronize(b) != cudaSuccess) st = fail(LBM_ERR_CUDA, "autotune timing");
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, a, b);
+      if (c.persistent && st == LBM_OK) {  // a barrier that gave up would look fast: never pick it
+        int err = 0;
+        if (cudaMemcpy(&err, &static_cast<StepBarrier*>(E->bar.p)->error, sizeof(int), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+          st = fail(LBM_ERR_CUDA, "autotune barrier flag");
+        if (err != 0) st = fail(LBM_ERR_TIMEOUT, "persistent step kernel: a grid barrier wait gave up");
+      }
       if (rep == 1 && ms < best) {
         best = ms;
         best_cfg = c;
@@ -341,6 +387,7 @@ lbm_status autotune(Engine* E) {
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  E->bar_used = false;
   for (int i = 0; i < n; ++i)
     cudaMemcpyAsync(E->m[i]->f, backups[i], 9 * E->m[i]->plane * sb, cudaMemcpyDeviceToDevice, E->stream);
   cudaStreamSynchronize(E->stream);
@@ -356,6 +403,8 @@ lbm_status ensure_pinned(Engine* E, size_t n) {
   if (E->h_info) cudaFreeHost(E->h_info);
   if (E->h_count) cudaFreeHost(E->h_count);
   if (E->h_nswap) cudaFreeHost(E->h_nswap);
+  if (E->h_bar_error) cudaFreeHost(E->h_bar_error);
+  E->h_bar_error = nullptr;
   E->h_result = nullptr;
   E->h_info = nullptr;
   E->h_count = nullptr;
@@ -365,6 +414,8 @@ lbm_status ensure_pinned(Engine* E, size_t n) {
   CU(cudaMallocHost((void**)&E->h_info, sizeof(int) * 8 * cap));
   CU(cudaMallocHost((void**)&E->h_count, sizeof(unsigned long long) * cap));
   CU(cudaMallocHost((void**)&E->h_nswap, sizeof(int) * cap));
+  CU(cudaMallocHost((void**)&E->h_bar_error, sizeof(int)));
+  *E->h_bar_error = 0;
   E->pinned_n = cap;
   return LBM_OK;
 }
@@ -534,8 +585,9 @@ Engine::~Engine() {
   if (own_members)
     for (Member* x : m) delete x;
   for (GrowBuf* b : {&L.views, &L.word_off, &L.seg_word_off, &XL.views, &XL.word_off, &XL.seg_word_off, &segs,
-                     &n_segs, &seg_scratch, &partials, &result, &fluid_dev, &n_swap_dev, &dense_f, &oc_buf})
+                     &n_segs, &seg_scratch, &partials, &result, &fluid_dev, &n_swap_dev, &dense_f, &oc_buf, &bar})
     b->release();
+  if (h_bar_error) cudaFreeHost(h_bar_error);
   if (h_result) cudaFreeHost(h_result);
   if (h_info) cudaFreeHost(h_info);
   if (h_count) cudaFreeHost(h_count);
@@ -545,12 +597,12 @@ Engine::~Engine() {
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
-lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool persistent, Engine** out) {
+lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool fixed_grid, Engine** out) {
   *out = nullptr;
   Engine* E = new Engine();
   E->precision = precision;
   E->residual_every = residual_every;
-  E->persistent = persistent;
+  E->fixed_grid = fixed_grid;
 #define CUE(call)                                                                        \
   do {                                                                                   \
     cudaError_t e_ = (call);                                                             \
@@ -572,6 +624,8 @@ lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool
   CUE(cudaEventCreate(&E->ev_begin));
   CUE(cudaEventCreate(&E->ev_end));
   CUE(E->n_segs.reserve(sizeof(int)));
+  CUE(E->bar.reserve(sizeof(StepBarrier)));
+  CUE(cudaMemsetAsync(E->bar.p, 0, sizeof(StepBarrier), E->stream));
 #undef CUE
   E->step = shape(E, kStepWarps, 1);
   *out = E;
@@ -608,7 +662,7 @@ lbm_status engine_set_members(Engine* E, const std::vector<Member*>& members) {
   CU(E->dense_f.reserve((size_t)std::max<long long>(1, max_cells) * 4));
   st = ensure_pinned(E, nn);
   if (st != LBM_OK) return st;
-  if (!E->tuned || E->persistent) E->step = shape(E, E->step.warps_per_block, 1);
+  if (!E->tuned || E->fixed_grid) E->step = shape(E, E->step.warps_per_block, 1);
   if (n == 0) return LBM_OK;
   st = rebuild_worklist(E);
   if (st != LBM_OK) return st;
@@ -694,6 +748,7 @@ void fill_result(Engine* E, int i, lbm_solve_result* out) {
 lbm_status enqueue_steps_and_reduce(Engine* E, int64_t n_steps, bool with_res) {
   const int K = E->residual_every;
   lbm_status st;
+  E->bar_used = false;
   CU(cudaEventRecord(E->ev_begin, E->stream));
   if (with_res) {
     if ((st = run_plain_pairs(E, (n_steps - K) / 2 - 1)) != LBM_OK) return st;
@@ -714,6 +769,11 @@ lbm_status enqueue_steps_and_reduce(Engine* E, int64_t n_steps, bool with_res) {
   DEBUG_SYNC(E, "finalize");
   CU(cudaMemcpyAsync(E->h_result, E->result.p, sizeof(double) * kResultDoubles * E->n(), cudaMemcpyDeviceToHost,
                      E->stream));
+  if (E->bar_used)
+    CU(cudaMemcpyAsync(E->h_bar_error, &static_cast<StepBarrier*>(E->bar.p)->error, sizeof(int),
+                       cudaMemcpyDeviceToHost, E->stream));
+  else
+    *E->h_bar_error = 0;
   return LBM_OK;
 }
 
@@ -770,6 +830,7 @@ lbm_status engine_solve(Engine* E, int64_t n_steps, lbm_solve_result* out) {
   for (Member* m : E->m) m->steps_done += n_steps;
   E->solved = true;
   account_steps(E, n_steps);
+  if (*E->h_bar_error != 0) return fail(LBM_ERR_TIMEOUT, "persistent step kernel: a grid barrier wait gave up");
   bool bad = false;
   for (int i = 0; i < E->n(); ++i) {
     fill_result(E, i, out + i);
@@ -802,6 +863,7 @@ lbm_status engine_optimize(Engine* E, const int32_t* n_swap, int64_t n_steps, lb
     bad |= E->h_result[(size_t)i * kResultDoubles + 7] != 0.0;
   }
   account_steps(E, n_steps);
+  if (*E->h_bar_error != 0) return fail(LBM_ERR_TIMEOUT, "persistent step kernel: a grid barrier wait gave up");
   for (int i = 0; i < E->n(); ++i) {
     std::memset(out + i, 0, sizeof(lbm_opt_result));
     out[i].n_swapped = E->h_info[8 * i];
@@ -851,6 +913,25 @@ lbm_status engine_read(Engine* E, int i, uint32_t which, void* dst, size_t dst_b
       return fail(LBM_ERR_ARG, "which must be exactly one LBM_FIELD_* value");
   }
   CU(cudaStreamSynchronize(E->stream));
+  return LBM_OK;
+}
+
+lbm_status engine_step_config(Engine* E, int32_t* warps_per_block, int32_t* grid, int32_t* persistent) {
+  if (warps_per_block) *warps_per_block = E->step.warps_per_block;
+  if (grid) *grid = E->step.grid;
+  if (persistent) *persistent = E->step.persistent;
+  return LBM_OK;
+}
+
+lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t persistent) {
+  if (warps_per_block != 4 && warps_per_block != 8 && warps_per_block != 16)
+    return fail(LBM_ERR_ARG, "warps_per_block must be 4, 8 or 16");
+  if (persistent != 0 && persistent != 1) return fail(LBM_ERR_ARG, "persistent must be 0 or 1");
+  if (persistent && warps_per_block == 4) return fail(LBM_ERR_ARG, "the persistent kernel takes 8 or 16 warps per block");
+  StepConfig c = persistent ? persistent_shape(E, warps_per_block) : shape(E, warps_per_block, 1);
+  if (c.grid < 1) return fail(LBM_ERR_CUDA, "no resident block for the persistent kernel");
+  E->step = c;
+  E->tuned = true;
   return LBM_OK;
 }
 

@@ -80,13 +80,13 @@ struct Engine {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   bool own_members = true;  // handles and batches own their members; the server does not
-  bool persistent = false;  // step grid sized for the device, not for the current list
+  bool fixed_grid = false;  // step grid sized for the device, not for the current list
   int sm_count = 0;
   std::vector<Member*> m;
 
   SetLayout L;   // every member: time steps, reductions, work-list
   SetLayout XL;  // members of the next exchange (server only)
-  GrowBuf segs, n_segs, seg_scratch, partials, result, fluid_dev, n_swap_dev, dense_f;
+  GrowBuf segs, n_segs, seg_scratch, partials, result, fluid_dev, n_swap_dev, dense_f, bar;
   GrowBuf oc_buf;  // exchange scratch, carved into `oc`
   OcScratch oc{};
   size_t pinned_n = 0;
@@ -94,10 +94,12 @@ struct Engine {
   int* h_info = nullptr;                  // pinned [8 n]
   unsigned long long* h_count = nullptr;  // pinned [n]
   int* h_nswap = nullptr;                 // pinned [n]
+  int* h_bar_error = nullptr;             // pinned: grid-barrier error flag of the last solve
+  bool bar_used = false;                  // the last enqueued solve ran the persistent kernel
 
   cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};  // views, segs, n_segs, shape
-  StepConfig step{kStepWarps, 1};
+  StepConfig step{kStepWarps, 1, 0};
   bool tuned = false;
   cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
   double step_ms = 0.0;
@@ -109,7 +111,7 @@ struct Engine {
 };
 
 // An engine with no members (add them with engine_set_members).
-lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool persistent, Engine** out);
+lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool fixed_grid, Engine** out);
 // Replace the member list; rebuilds the layout, the work-list and the fluid
 // counts (synchronises the stream).
 lbm_status engine_set_members(Engine* E, const std::vector<Member*>& members);
@@ -135,6 +137,8 @@ void account_steps(Engine* E, int64_t n_steps);
 lbm_status engine_solve(Engine* E, int64_t n_steps, lbm_solve_result* out);
 lbm_status engine_optimize(Engine* E, const int32_t* n_swap, int64_t n_steps, lbm_opt_result* out);
 lbm_status engine_read(Engine* E, int i, uint32_t which, void* dst, size_t dst_bytes);
+lbm_status engine_step_config(Engine* E, int32_t* warps_per_block, int32_t* grid, int32_t* persistent);
+lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t persistent);
 lbm_status engine_kernel_time(Engine* E, int reset, double* ms, int64_t* launches, int64_t* fluid_updates);
 
 // thread-local last error and launch counter state shared with api.cu

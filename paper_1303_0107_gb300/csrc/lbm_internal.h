@@ -100,11 +100,28 @@ __host__ __device__ inline int find_lattice(const int* off, int n, long long i) 
 struct StepConfig {
   int warps_per_block;  // 4, 8 or 16
   int grid;             // blocks
+  int persistent;       // 1: all pairs of a solve in one cooperative launch
+};
+// Grid barrier state of the persistent kernel (device memory, 16 bytes).
+struct StepBarrier {
+  unsigned count;  // arrivals in the current generation
+  unsigned gen;    // completed barriers
+  int error;       // set when a wait gave up (the launch then stops early)
+  int pad;
 };
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
                                   const SegRef* segs, const int* n_segs, StepConfig cfg,
                                   cudaStream_t stream);
 int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block);
+// n_pairs time-step pairs (phase A then B, no moments) in one cooperative
+// launch with a grid barrier between phases; sc.grid must not exceed
+// stream_collide_persistent_grid (every block resident at once).  The
+// barrier is reset on the stream first; a barrier wait that gives up sets
+// bar->error and ends the launch early.
+cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* views, const SegRef* segs,
+                                             const int* n_segs, int n_pairs, StepConfig sc, StepBarrier* bar,
+                                             cudaStream_t stream);
+int stream_collide_persistent_grid(int precision, int warps_per_block);
 
 // ---- geometry / work-list (worklist.cu) ------------------------------------
 cudaError_t launch_pack_mask(const uint8_t* cells, int nx, int ny, int wpr, uint32_t* mask,

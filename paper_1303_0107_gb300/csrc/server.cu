@@ -76,7 +76,7 @@ size_t engine_buffer_bytes(const Engine* E) {
   size_t b = 0;
   for (const GrowBuf* g : {&E->L.views, &E->L.word_off, &E->L.seg_word_off, &E->XL.views, &E->XL.word_off,
                            &E->XL.seg_word_off, &E->segs, &E->n_segs, &E->seg_scratch, &E->partials, &E->result,
-                           &E->fluid_dev, &E->n_swap_dev, &E->dense_f, &E->oc_buf})
+                           &E->fluid_dev, &E->n_swap_dev, &E->dense_f, &E->oc_buf, &E->bar})
     b += g->cap;
   return b;
 }

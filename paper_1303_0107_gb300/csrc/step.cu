@@ -37,19 +37,25 @@ namespace {
 
 template <class T>
 struct Pop;
+// ld: plain load; ldcg: load cached in L2 only.  Within one persistent launch
+// a slot written by another block must not be served from this SM's L1 (L1
+// is not coherent across SMs), so that kernel reads populations with ldcg.
 template <>
 struct Pop<float> {
   static __device__ __forceinline__ float ld(const float* p) { return *p; }
+  static __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
   static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 template <>
 struct Pop<__nv_bfloat16> {
   static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ float ldcg(const __nv_bfloat16* p) { return __bfloat162float(__ldcg(p)); }
   static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 template <>
 struct Pop<__half> {
   static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+  static __device__ __forceinline__ float ldcg(const __half* p) { return __half2float(__ldcg(p)); }
   static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
@@ -187,7 +193,7 @@ __device__ __forceinline__ void outlet_rule(float (&g)[9], float rho0, int schem
 }
 
 // population access with optional bounds checks (offset in elements from F)
-#define FLD(off) (LBM_OK_IDX((off), fe) ? P::ld(F + (off)) : 0.0f)
+#define FLD(off) (LBM_OK_IDX((off), fe) ? (PERSIST ? P::ldcg(F + (off)) : P::ld(F + (off))) : 0.0f)
 #define FST(off, v)                                   \
   do {                                                \
     if (LBM_OK_IDX((off), fe)) P::st(F + (off), (v)); \
@@ -200,30 +206,23 @@ constexpr unsigned kE = 1u, kN = 2u, kW = 4u, kS = 8u, kNE = 16u, kNW = 32u, kSW
 // budget is the same (at most 64 per thread) for all of them.
 constexpr int kMaxStepThreads = 512;
 
-template <class T, int PHASE, int MOM>
-__global__ void __launch_bounds__(kMaxStepThreads, 2)
-    k_stream_collide(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
-                     const int* __restrict__ n_segs) {
+// One phase of one time step on one row segment (lane = cell 32w + lane).
+// PERSIST: called from the persistent kernel (populations read through L2
+// only; no programmatic-launch wait); otherwise from a programmatic dependent
+// launch, which waits for the previous step once, just before its first
+// population access (`waited`).
+template <class T, int PHASE, int MOM, bool PERSIST>
+__device__ __forceinline__ void update_segment(const LatticeView* __restrict__ views, const SegRef sr,
+                                               const int lane, bool& waited) {
   using P = Pop<T>;
-  // The next time step may be scheduled now; it reads populations only after
-  // waiting for this grid to complete.
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const int lane = threadIdx.x & 31;
-  // the segment list, descriptors and mask are never written by a time step,
-  // so they may be read before the previous step has finished
-  const int nseg = *n_segs;
-  const int wpb = blockDim.x >> 5;
-  const int stride = gridDim.x * wpb;
-  bool waited = false;
-  for (int sidx = blockIdx.x * wpb + (threadIdx.x >> 5); sidx < nseg; sidx += stride) {
-    const SegRef sr = segs[sidx];
+  {
     const LatticeView* __restrict__ L = views + sr.lattice;
     const int y = sr.yw >> kSegWordBits;
     const int w = sr.yw & ((1 << kSegWordBits) - 1);
 #ifdef LBM_CHECK_BOUNDS
     if (sr.lattice < 0 || y < 1 || y > L->ny - 2 || w < 0 || w >= L->wpr) {
-      if (lane == 0) printf("lbm bounds: bad segment %d of %d: lattice %d y %d w %d\n", sidx, nseg, sr.lattice, y, w);
-      continue;
+      if (lane == 0) printf("lbm bounds: bad segment: lattice %d y %d w %d\n", sr.lattice, y, w);
+      return;
     }
 #endif
     const int ms = mask_stride(L->wpr);
@@ -260,7 +259,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, 2)
     (void)fe;
     const int c = y * pitch + x;
 
-    if (!waited) {  // warp-uniform: populations of the previous step are final from here on
+    if (!PERSIST && !waited) {  // warp-uniform: populations of the previous step are final from here on
       asm volatile("griddepcontrol.wait;" ::: "memory");
       waited = true;
     }
@@ -314,7 +313,7 @@ __global__ void __launch_bounds__(kMaxStepThreads, 2)
       }
     }
 
-    if (!fluid) continue;
+    if (!fluid) return;
     if (inlet) {
       inlet_rule(g, L->u_in[y], rho0, L->port_scheme);
     } else if (outlet && rule == LBM_OUT_CONST_RHO) {
@@ -347,8 +346,92 @@ __global__ void __launch_bounds__(kMaxStepThreads, 2)
       }
     }
   }
+}
+
+template <class T, int PHASE, int MOM>
+__global__ void __launch_bounds__(kMaxStepThreads, 2)
+    k_stream_collide(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
+                     const int* __restrict__ n_segs) {
+  // The next time step may be scheduled now; it reads populations only after
+  // waiting for this grid to complete.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  // the segment list, descriptors and mask are never written by a time step,
+  // so they may be read before the previous step has finished
+  const int nseg = *n_segs;
+  const int wpb = blockDim.x >> 5;
+  const int stride = gridDim.x * wpb;
+  bool waited = false;
+  for (int sidx = blockIdx.x * wpb + (threadIdx.x >> 5); sidx < nseg; sidx += stride)
+    update_segment<T, PHASE, MOM, false>(views, segs[sidx], lane, waited);
   if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
+
+// Grid-wide barrier of the persistent kernel (all blocks co-resident: the
+// kernel is launched cooperatively).  Sense by generation: a block reads the
+// generation, publishes its writes, arrives; the last arrival resets the
+// count and advances the generation; the others wait for the advance.  The
+// wait gives up after kSpinLimit polls, flags the failure and makes every
+// block leave the kernel at its next barrier.
+constexpr unsigned kSpinLimit = 1u << 24;
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ bool grid_barrier(StepBarrier* b) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned gen = ld_acquire(&b->gen);
+    __threadfence();  // this block's population writes before its arrival
+    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      unsigned spins = 0;
+      while (ld_acquire(&b->gen) == gen) {
+        if (++spins > kSpinLimit || ld_acquire(reinterpret_cast<const unsigned*>(&b->error)) != 0) {
+          atomicExch(&b->error, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// n_pairs (A, B) time-step pairs in one launch, a grid barrier after every
+// phase but the last.  Same per-cell arithmetic as k_stream_collide.
+template <class T>
+__global__ void __launch_bounds__(kMaxStepThreads, 2)
+    k_stream_collide_persistent(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
+                                const int* __restrict__ n_segs, int n_pairs, StepBarrier* bar) {
+  const int lane = threadIdx.x & 31;
+  const int nseg = *n_segs;
+  const int wpb = blockDim.x >> 5;
+  const int stride = gridDim.x * wpb;
+  const int first = blockIdx.x * wpb + (threadIdx.x >> 5);
+  bool waited = true;
+  for (int p = 0; p < n_pairs; ++p) {
+    for (int sidx = first; sidx < nseg; sidx += stride)
+      update_segment<T, 0, 0, true>(views, segs[sidx], lane, waited);
+    if (!grid_barrier(bar)) return;
+    for (int sidx = first; sidx < nseg; sidx += stride)
+      update_segment<T, 1, 0, true>(views, segs[sidx], lane, waited);
+    if (p + 1 < n_pairs && !grid_barrier(bar)) return;
+  }
+}
+
 
 template <class T>
 void* pick(int phase, int moments) {
@@ -387,6 +470,53 @@ cudaError_t launch_stream_collide(int precision, int phase, int moments, const L
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e = cudaLaunchKernelExC(&cfg, k, args);
+  if (e == cudaSuccess) count_launches(1);
+  return e;
+}
+
+namespace {
+void* persistent_kernel_for(int precision) {
+  switch (precision) {
+    case LBM_F32: return (void*)k_stream_collide_persistent<float>;
+    case LBM_BF16_SHIFTED: return (void*)k_stream_collide_persistent<__nv_bfloat16>;
+    case LBM_F16_SHIFTED: return (void*)k_stream_collide_persistent<__half>;
+    default: return nullptr;
+  }
+}
+}  // namespace
+
+int stream_collide_persistent_grid(int precision, int warps_per_block) {
+  void* k = persistent_kernel_for(precision);
+  int dev = 0, sms = 0, n = 0;
+  if (!k || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, 0) != cudaSuccess)
+    return 0;
+  return n * sms;
+}
+
+cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* views, const SegRef* segs,
+                                             const int* n_segs, int n_pairs, StepConfig sc, StepBarrier* bar,
+                                             cudaStream_t stream) {
+  void* k = persistent_kernel_for(precision);
+  if (!k || n_pairs < 1 || sc.warps_per_block < 1 || sc.warps_per_block * 32 > kMaxStepThreads || sc.grid < 1 ||
+      sc.grid > stream_collide_persistent_grid(precision, sc.warps_per_block))
+    return cudaErrorInvalidValue;
+  // a fresh barrier: count 0, generation 0, no error
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(StepBarrier), stream);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&views, (void*)&segs, (void*)&n_segs, (void*)&n_pairs, (void*)&bar};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all blocks co-resident: the barrier can complete
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sc.grid);
+  cfg.blockDim = dim3(32 * sc.warps_per_block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelExC(&cfg, k, args);
   if (e == cudaSuccess) count_launches(1);
   return e;
 }

@@ -119,7 +119,9 @@ def load_library(path=None):
     L.lbm_kernel_launches.restype = ctypes.c_uint64
     L.lbm_kernel_time.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
-    L.lbm_step_config.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.lbm_step_config.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int32)]
+    L.lbm_set_step_config.argtypes = [H, ctypes.c_int32, ctypes.c_int32]
     B = _VP
     L.lbm_batch_create.argtypes = [ctypes.c_int32, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p), _VP,
                                    ctypes.POINTER(B)]
@@ -130,7 +132,9 @@ def load_library(path=None):
     L.lbm_batch_reset.argtypes = [B]
     L.lbm_batch_kernel_time.argtypes = [B, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
-    L.lbm_batch_step_config.argtypes = [B, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.lbm_batch_step_config.argtypes = [B, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32)]
+    L.lbm_batch_set_step_config.argtypes = [B, ctypes.c_int32, ctypes.c_int32]
     L.lbm_batch_destroy.argtypes = [B]
     L.lbm_batch_destroy.restype = None
     L.lbm_select_swaps_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
@@ -152,9 +156,9 @@ def load_library(path=None):
     L.lbm_bytes_per_fluid_update.restype = ctypes.c_double
     for name in ("lbm_create_geometry", "lbm_solve", "lbm_optimize_step", "lbm_read_fields",
                  "lbm_load_state", "lbm_reset", "lbm_select_swaps", "lbm_kernel_time",
-                 "lbm_select_swaps_noalloc", "lbm_step_config", "lbm_batch_create", "lbm_batch_solve",
+                 "lbm_select_swaps_noalloc", "lbm_step_config", "lbm_set_step_config", "lbm_batch_create", "lbm_batch_solve",
                  "lbm_batch_optimize_step", "lbm_batch_read_fields", "lbm_batch_reset",
-                 "lbm_batch_kernel_time", "lbm_batch_step_config", "lbm_server_create", "lbm_server_submit",
+                 "lbm_batch_kernel_time", "lbm_batch_step_config", "lbm_batch_set_step_config", "lbm_server_create", "lbm_server_submit",
                  "lbm_server_wait_idle", "lbm_server_get_stats"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
@@ -272,11 +276,17 @@ class Lattice:
         _check(load_library().lbm_reset(self._h), "lbm_reset")
 
     def step_config(self):
-        """(warps per block, blocks) of the time-step launches (autotuned)."""
+        """(warps per block, blocks, persistent) of the time-step launches (autotuned)."""
         w = ctypes.c_int32()
         g = ctypes.c_int32()
-        _check(load_library().lbm_step_config(self._h, ctypes.byref(w), ctypes.byref(g)), "lbm_step_config")
-        return w.value, g.value
+        p = ctypes.c_int32()
+        _check(load_library().lbm_step_config(self._h, ctypes.byref(w), ctypes.byref(g), ctypes.byref(p)),
+               "lbm_step_config")
+        return w.value, g.value, p.value
+
+    def set_step_config(self, warps_per_block, persistent=False):
+        _check(load_library().lbm_set_step_config(self._h, int(warps_per_block), int(persistent)),
+               "lbm_set_step_config")
 
     def select_swaps(self, drho, ux, uy, n_swap: int):
         arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (drho, ux, uy)]
@@ -376,9 +386,14 @@ class Batch:
     def step_config(self):
         w = ctypes.c_int32()
         g = ctypes.c_int32()
-        _check(load_library().lbm_batch_step_config(self._b, ctypes.byref(w), ctypes.byref(g)),
+        p = ctypes.c_int32()
+        _check(load_library().lbm_batch_step_config(self._b, ctypes.byref(w), ctypes.byref(g), ctypes.byref(p)),
                "lbm_batch_step_config")
-        return w.value, g.value
+        return w.value, g.value, p.value
+
+    def set_step_config(self, warps_per_block, persistent=False):
+        _check(load_library().lbm_batch_set_step_config(self._b, int(warps_per_block), int(persistent)),
+               "lbm_batch_set_step_config")
 
 
 class Server:

@@ -1,0 +1,104 @@
+"""The persistent stream-collide kernel (all time steps of a solve in one
+cooperative launch, grid barriers between phases) against the one-launch-
+per-phase kernel and against the FP64 oracle.
+
+Both launch modes run the same per-cell code, so their populations, fields
+and reductions must agree bit for bit; the full-size tree is also checked
+against the oracle at the FP32 tolerance.
+"""
+import numpy as np
+import pytest
+
+import paper_1303_0107_gb300 as L
+from paper_1303_0107_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    L.load_library()
+
+
+def _cases():
+    t = I.config_t_junction()
+    c = I.config_candidates(1, base_seed=7)[0]
+    return [
+        dict(cells=t["cells"], tau=t["tau"], u_max=t["u_max"]),
+        dict(cells=I.random_blobs(100, 40, 9, density=0.2), tau=0.7, u_max=0.03, outlet=L.OUT_NEUMANN),
+        dict(cells=I.channel(64, 14), tau=0.9, u_max=0.04, ports=L.PORTS_ZOU_HE),
+        dict(cells=c["cells"], tau=c["tau"], u_max=c["u_max"]),
+    ]
+
+
+def _handle(case, precision, persistent, wpb=8):
+    h = L.Lattice(case["cells"], case["tau"], case["u_max"], precision=precision, outlet=case.get("outlet", 0),
+                  ports=case.get("ports", 0), residual_every=100)
+    h.set_step_config(wpb, persistent=persistent)
+    return h
+
+
+@pytest.mark.parametrize("precision", [L.F32, L.BF16_SHIFTED])
+@pytest.mark.parametrize("k", range(4))
+def test_persistent_equals_per_phase_launches(k, precision):
+    case = _cases()[k]
+    a = _handle(case, precision, False)
+    b = _handle(case, precision, True, wpb=16 if k % 2 else 8)
+    assert b.step_config()[2] == 1 and a.step_config()[2] == 0
+    ra, rb = a.solve(600), b.solve(600)
+    assert ra["dp"] == rb["dp"] and ra["residual"] == rb["residual"]
+    assert np.array_equal(a.read(L.FIELD_POPS), b.read(L.FIELD_POPS))
+    fl = int((case["cells"] == 0).sum())
+    oa, ob = a.optimize_step(max(1, fl // 200), 300), b.optimize_step(max(1, fl // 200), 300)
+    assert oa["dp"] == ob["dp"] and oa["n_swapped"] == ob["n_swapped"]
+    for f in (L.FIELD_MASK, L.FIELD_UX, L.FIELD_UY, L.FIELD_DRHO, L.FIELD_POPS):
+        assert np.array_equal(a.read(f), b.read(f)), f
+    a.close()
+    b.close()
+
+
+def test_persistent_tree_2048_matches_oracle(ora):
+    cfg = I.config_tree_2048()
+    cells = cfg["cells"]
+    ny, nx = cells.shape
+    h = L.Lattice(cells, cfg["tau"], cfg["u_max"], residual_every=0)
+    h.set_step_config(16, persistent=True)
+    g = h.solve(300)
+    s = ora.Solver(ora.make_params(nx, ny, cfg["tau"], 1.0, cfg["u_max"]), cells, residual_every=0)
+    o = s.solve(300)
+    ux = h.read(L.FIELD_UX).astype(np.float64)
+    uy = h.read(L.FIELD_UY).astype(np.float64)
+    assert np.linalg.norm(ux - s.ux) / np.linalg.norm(s.ux) <= 1e-5
+    assert np.abs(ux - s.ux).max() / np.abs(s.ux).max() <= 1e-5
+    assert np.abs(uy - s.uy).max() / np.abs(s.ux).max() <= 1e-5
+    assert abs(g["dp"] - o["dp"]) <= 1e-5 * abs(o["dp"])
+    h.close()
+
+
+def test_persistent_batch_equals_per_phase_batch():
+    members = _cases()
+    a = L.Batch(members, residual_every=0)
+    b = L.Batch(members, residual_every=0)
+    a.set_step_config(8, persistent=False)
+    b.set_step_config(16, persistent=True)
+    ra, rb = a.solve(400), b.solve(400)
+    assert [x["dp"] for x in ra] == [x["dp"] for x in rb]
+    oa, ob = a.optimize_step([3, 2, 1, 4], 200), b.optimize_step([3, 2, 1, 4], 200)
+    assert [x["dp"] for x in oa] == [x["dp"] for x in ob]
+    for i in range(len(members)):
+        assert np.array_equal(a.read(i, L.FIELD_POPS), b.read(i, L.FIELD_POPS)), i
+    a.close()
+    b.close()
+
+
+def test_set_step_config_errors():
+    t = I.config_t_junction()
+    h = L.Lattice(t["cells"], t["tau"], t["u_max"])
+    for wpb, pers in ((3, 0), (32, 0), (4, 1), (8, 2)):
+        with pytest.raises(L.LbmError) as e:
+            h.set_step_config(wpb, persistent=pers)
+        assert e.value.status == 1
+    h.close()
