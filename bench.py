@@ -58,8 +58,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="served leg: arrival window")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--kernel-case", choices=["tree", "large"], default=None,
-                    help="only create one lattice and run two 4-step solves (for ncu captures): "
-                         "tree = 2048 x 1024 distributor, large = 8192 x 4096 channel array")
+                    help="only create one lattice and run two solves of --kernel-steps steps (for ncu "
+                         "captures): tree = 2048 x 1024 distributor, large = 8192 x 4096 channel array")
+    ap.add_argument("--kernel-steps", type=int, default=4)
     return ap.parse_args()
 
 
@@ -75,12 +76,29 @@ def kernel_case(args):
     else:
         cells, tau, u_max = I.channel_array(8192, 4096, 16, fill=0.5), 0.6, 0.05
     lat = L.Lattice(cells, tau, u_max, precision=prec, residual_every=0)
-    lat.solve(4)
-    r = lat.solve(4)
+    lat.solve(args.kernel_steps)
+    r = lat.solve(args.kernel_steps)
     lat.close()
     print(json.dumps({"kernel_case": args.kernel_case, "precision": args.precision,
                       "fluid_cells": int((cells == 0).sum()), "dp": r["dp"]}))
     return 0
+
+
+def max_over_ranks(value, dist, device):
+    """The largest value over all ranks (the slowest rank's time); the value
+    itself when there is no process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(updates_per_rank, world, seconds):
+    """Whole-job GLUPS of `world` replicas that each did updates_per_rank
+    fluid updates, timed by the slowest rank."""
+    return updates_per_rank * world / seconds / 1e9
 
 
 def dist_env():
@@ -256,7 +274,7 @@ def leg_batched(L, I, stream, prec, n=256, iters=10, S=2000, sample=32):
         dp_b.append([x["dp"] for x in rb])
     t_batch = time.perf_counter() - t0
     ms, nl, nu = b.kernel_time()
-    w, g, pers = b.step_config()
+    w, g, pers, cpt = b.step_config()
     b.close()
     upd = sum(fluid) * S * (iters + 1)
     idx = list(range(0, n, max(1, n // sample)))[:sample]
@@ -280,7 +298,7 @@ def leg_batched(L, I, stream, prec, n=256, iters=10, S=2000, sample=32):
     g_plain = upd_plain / t_plain / 1e9
     return {"candidates": n, "fluid_cells": sum(fluid), "iterations": iters, "steps_per_solve": S,
             "batched_glups": g_batch, "batched_step_glups": nu / (ms / 1e3) / 1e9,
-            "batched_s": t_batch, "step_config": [w, g, pers],
+            "batched_s": t_batch, "step_config": [w, g, pers, cpt],
             "one_at_a_time_glups": g_plain, "one_at_a_time_sample": len(idx),
             "speedup": g_batch / g_plain, "dp_rel_diff_batched_vs_alone_max": worst}
 
@@ -482,11 +500,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
     updates_per_step = fluid * S * (iters + 1)
-    if dist is not None:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = updates_per_step * args.steps * world / total_s / 1e9
+    total_s = max_over_ranks(total_s, dist, "cuda")
+    value = replica_value(updates_per_step * args.steps, world, total_s)
 
     # roofline of the stream-collide kernel, from the timed region
     bpu = L.bytes_per_fluid_update(prec)
@@ -516,10 +531,7 @@ def main():
         h.close()
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_times) / len(e2e_times)
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     sz = ctypes_sizes()
     # host -> device: the cell map, the per-row inlet speeds and the outlet
     # table the library derives from it, the lattice descriptor and the set
@@ -528,7 +540,7 @@ def main():
     # device -> host: the reduction block of every solve, the exchange counters
     # and fluid count of every iteration and of creation, and the final cell map
     d2h = cells.nbytes + (iters + 1) * sz["result_block"] + iters * (32 + 8) + 8
-    e2e = {"value": updates_per_step * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    e2e = {"value": replica_value(updates_per_step, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
 
     extras = {}

@@ -265,11 +265,17 @@ lbm_status ensure_graph(Engine* E, int which) {
 }
 
 lbm_status run_persistent(Engine* E, int64_t pairs) {
-  if (pairs <= 0) return LBM_OK;
-  CU(launch_stream_collide_persistent(E->precision, static_cast<const LatticeView*>(E->L.views.p),
-                                      static_cast<const SegRef*>(E->segs.p), static_cast<const int*>(E->n_segs.p),
-                                      (int)pairs, E->step, static_cast<StepBarrier*>(E->bar.p), E->stream));
-  E->bar_used = true;
+  // the barrier counter counts 2 * pairs * grid arrivals per launch: keep it below 2^32
+  const int64_t max_pairs = std::max<int64_t>(1, ((int64_t)1 << 31) / std::max(1, E->step.grid) - 1);
+  while (pairs > 0) {
+    const int64_t k = std::min(pairs, max_pairs);
+    CU(launch_stream_collide_persistent(E->precision, static_cast<const LatticeView*>(E->L.views.p),
+                                        static_cast<const SegRef*>(E->segs.p),
+                                        static_cast<const int*>(E->n_segs.p), (int)k, E->step,
+                                        static_cast<StepBarrier*>(E->bar.p), E->stream));
+    E->bar_used = true;
+    pairs -= k;
+  }
   return LBM_OK;
 }
 
@@ -300,24 +306,27 @@ lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
 // Launch shape: every segment its own warp, but never more blocks than fit
 // on the device at once; a fixed-grid engine always takes the device-sized
 // grid, so its captured graphs outlive changes of the member list.
-StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale) {
-  const int bps = stream_collide_blocks_per_sm(E->precision, 0, 0, wpb);
+StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale, int cpt = 1) {
+  const int bps = stream_collide_blocks_per_sm(E->precision, 0, 0, wpb, cpt);
   const long long cap = (long long)E->sm_count * bps * blocks_per_sm_scale;
-  const long long need = ((long long)E->L.total_seg_words + wpb - 1) / wpb;
+  const long long tasks = ((long long)E->L.total_seg_words + cpt - 1) / cpt;
+  const long long need = (tasks + wpb - 1) / wpb;
   StepConfig c;
   c.warps_per_block = wpb;
   c.grid = (int)(E->fixed_grid ? cap : std::max<long long>(1, std::min(need, cap)));
   c.persistent = 0;
+  c.cells_per_thread = cpt;
   return c;
 }
 
 // The persistent shape: one cooperative launch per run of pairs, as many
 // blocks as are resident at once.
-StepConfig persistent_shape(Engine* E, int wpb) {
+StepConfig persistent_shape(Engine* E, int wpb, int cpt = 1) {
   StepConfig c;
   c.warps_per_block = wpb;
-  c.grid = stream_collide_persistent_grid(E->precision, wpb);
+  c.grid = stream_collide_persistent_grid(E->precision, wpb, cpt);
   c.persistent = 1;
+  c.cells_per_thread = cpt;
   return c;
 }
 
@@ -341,16 +350,20 @@ lbm_status autotune(Engine* E) {
     CU(cudaMemcpyAsync(backups[i], E->m[i]->f, bytes, cudaMemcpyDeviceToDevice, E->stream));
   }
   std::vector<StepConfig> cand;
-  for (int wpb : {4, 8, 16})
-    for (int scale : {1, 2}) {
-      StepConfig c = shape(E, wpb, scale);
-      bool dup = false;
-      for (auto& d : cand) dup |= (d.warps_per_block == c.warps_per_block && d.grid == c.grid);
-      if (!dup) cand.push_back(c);
-    }
+  for (int cpt : {1, 2})
+    for (int wpb : {4, 8, 16})
+      for (int scale : {1, 2}) {
+        if (wpb * 32 > (cpt == 1 ? 512 : 256)) continue;
+        StepConfig c = shape(E, wpb, scale, cpt);
+        bool dup = false;
+        for (auto& d : cand)
+          dup |= (d.warps_per_block == c.warps_per_block && d.grid == c.grid &&
+                  d.cells_per_thread == c.cells_per_thread);
+        if (!dup) cand.push_back(c);
+      }
   if (persistent_enabled())
-    for (int wpb : {8, 16}) {
-      StepConfig c = persistent_shape(E, wpb);
+    for (int cpt : {1, 2}) {
+      StepConfig c = persistent_shape(E, 8, cpt);
       if (c.grid > 0) cand.push_back(c);
     }
   cudaEvent_t a, b;
@@ -916,19 +929,25 @@ lbm_status engine_read(Engine* E, int i, uint32_t which, void* dst, size_t dst_b
   return LBM_OK;
 }
 
-lbm_status engine_step_config(Engine* E, int32_t* warps_per_block, int32_t* grid, int32_t* persistent) {
+lbm_status engine_step_config(Engine* E, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
+                              int32_t* cells_per_thread) {
   if (warps_per_block) *warps_per_block = E->step.warps_per_block;
   if (grid) *grid = E->step.grid;
   if (persistent) *persistent = E->step.persistent;
+  if (cells_per_thread) *cells_per_thread = E->step.cells_per_thread;
   return LBM_OK;
 }
 
-lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t persistent) {
+lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t persistent, int32_t cells_per_thread) {
   if (warps_per_block != 4 && warps_per_block != 8 && warps_per_block != 16)
     return fail(LBM_ERR_ARG, "warps_per_block must be 4, 8 or 16");
   if (persistent != 0 && persistent != 1) return fail(LBM_ERR_ARG, "persistent must be 0 or 1");
+  if (cells_per_thread != 1 && cells_per_thread != 2) return fail(LBM_ERR_ARG, "cells_per_thread must be 1 or 2");
+  if (cells_per_thread == 2 && warps_per_block == 16)
+    return fail(LBM_ERR_ARG, "two cells per thread take 4 or 8 warps per block");
   if (persistent && warps_per_block == 4) return fail(LBM_ERR_ARG, "the persistent kernel takes 8 or 16 warps per block");
-  StepConfig c = persistent ? persistent_shape(E, warps_per_block) : shape(E, warps_per_block, 1);
+  StepConfig c = persistent ? persistent_shape(E, warps_per_block, cells_per_thread)
+                            : shape(E, warps_per_block, 1, cells_per_thread);
   if (c.grid < 1) return fail(LBM_ERR_CUDA, "no resident block for the persistent kernel");
   E->step = c;
   E->tuned = true;

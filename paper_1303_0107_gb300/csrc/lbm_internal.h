@@ -19,7 +19,8 @@ namespace lbm {
 
 // Work unit of the stream-collide kernel: one row segment, the 32 cells of
 // one mask word (row y, cells 32w .. 32w+31), taken by one warp (lane l ->
-// cell 32w + l).  The segment list holds only segments with a fluid cell.
+// cell 32w + l), one or two segments per warp task.  The segment list holds
+// only segments with a fluid cell.
 // Default block shape (the engine tunes it on its own lattices).
 constexpr int kStepWarps = 8;
 // Row pitch of every per-cell array, in elements: a multiple of 64 so that
@@ -101,27 +102,29 @@ struct StepConfig {
   int warps_per_block;  // 4, 8 or 16
   int grid;             // blocks
   int persistent;       // 1: all pairs of a solve in one cooperative launch
+  int cells_per_thread; // 1 or 2: row segments per warp task (2: at most 8 warps per block)
 };
 // Grid barrier state of the persistent kernel (device memory, 16 bytes).
 struct StepBarrier {
-  unsigned count;  // arrivals in the current generation
-  unsigned gen;    // completed barriers
+  unsigned count;  // arrivals since the launch began
+  unsigned gen;    // unused
   int error;       // set when a wait gave up (the launch then stops early)
   int pad;
 };
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
                                   const SegRef* segs, const int* n_segs, StepConfig cfg,
                                   cudaStream_t stream);
-int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block);
+int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int cells_per_thread);
 // n_pairs time-step pairs (phase A then B, no moments) in one cooperative
 // launch with a grid barrier between phases; sc.grid must not exceed
-// stream_collide_persistent_grid (every block resident at once).  The
+// stream_collide_persistent_grid (every block resident at once), and
+// 2 * n_pairs * sc.grid must stay below 2^32.  The
 // barrier is reset on the stream first; a barrier wait that gives up sets
 // bar->error and ends the launch early.
 cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* views, const SegRef* segs,
                                              const int* n_segs, int n_pairs, StepConfig sc, StepBarrier* bar,
                                              cudaStream_t stream);
-int stream_collide_persistent_grid(int precision, int warps_per_block);
+int stream_collide_persistent_grid(int precision, int warps_per_block, int cells_per_thread);
 
 // ---- geometry / work-list (worklist.cu) ------------------------------------
 cudaError_t launch_pack_mask(const uint8_t* cells, int nx, int ny, int wpr, uint32_t* mask,

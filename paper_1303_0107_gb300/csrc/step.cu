@@ -19,14 +19,18 @@
 // Each slot is read and then written by exactly one thread per phase, so the
 // pair needs one lattice and no barrier.  Solid cells are never read.
 //
-// Thread mapping.  Each warp takes one row segment (the 32 cells of one mask
-// word) from a device-resident list holding only segments with fluid cells;
-// lane l handles cell 32w + l, so every plane access of a warp is one
-// contiguous 32-element row segment (shifted by at most one element).  Warps
-// stride over the list; the list may span several lattices (batches).
-// Consecutive steps are programmatic dependent launches: a step's warps load
-// their segment, descriptor and mask words while the previous step is still
-// finishing, and wait for it only before touching populations.
+// Thread mapping.  Each warp takes one or two consecutive row segments (the
+// 32 cells of one mask word each) from a device-resident list holding only
+// segments with fluid cells; lane l handles cell 32w + l of each, so every
+// plane access of a warp is one contiguous 32-element row segment (shifted by
+// at most one element).  With two segments (two cells per thread) all 18
+// loads are in flight before the first cell is updated.  Warps stride over
+// the list; the list may span several lattices (batches).  Consecutive steps
+// are programmatic dependent launches: a step's warps load their segment,
+// descriptor and mask words while the previous step is still finishing, and
+// wait for it only before touching populations.  Alternatively one
+// cooperative launch runs all steps of a solve with grid barriers between
+// phases (the persistent kernel).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -193,187 +197,233 @@ __device__ __forceinline__ void outlet_rule(float (&g)[9], float rho0, int schem
 }
 
 // population access with optional bounds checks (offset in elements from F)
-#define FLD(off) (LBM_OK_IDX((off), fe) ? (PERSIST ? P::ldcg(F + (off)) : P::ld(F + (off))) : 0.0f)
-#define FST(off, v)                                   \
-  do {                                                \
-    if (LBM_OK_IDX((off), fe)) P::st(F + (off), (v)); \
+#define FLD(off) (LBM_OK_IDX((off), s.fe) ? (CG ? P::ldcg(F + (off)) : P::ld(F + (off))) : 0.0f)
+#define FST(off, v)                                     \
+  do {                                                  \
+    if (LBM_OK_IDX((off), s.fe)) P::st(F + (off), (v)); \
   } while (0)
 
 // neighbour solid flags, bit i-1 = solid(x + c_i), i = 1..8 (E N W S NE NW SW SE)
 constexpr unsigned kE = 1u, kN = 2u, kW = 4u, kS = 8u, kNE = 16u, kNW = 32u, kSW = 64u, kSE = 128u;
 
-// Block size is 128, 256 or 512 threads (chosen per launch); the register
-// budget is the same (at most 64 per thread) for all of them.
-constexpr int kMaxStepThreads = 512;
+// Threads per block at most, by cells per thread (the register budget per
+// thread is 64 with one cell, 80 with two).
+__host__ __device__ constexpr int max_step_threads(int cpt) { return cpt == 1 ? 512 : 256; }
+__host__ __device__ constexpr int min_step_blocks(int cpt) { return cpt == 1 ? 2 : 3; }
 
-// One phase of one time step on one row segment (lane = cell 32w + lane).
-// PERSIST: called from the persistent kernel (populations read through L2
-// only; no programmatic-launch wait); otherwise from a programmatic dependent
-// launch, which waits for the previous step once, just before its first
-// population access (`waited`).
-template <class T, int PHASE, int MOM, bool PERSIST>
-__device__ __forceinline__ void update_segment(const LatticeView* __restrict__ views, const SegRef sr,
-                                               const int lane, bool& waited) {
-  using P = Pop<T>;
-  {
-    const LatticeView* __restrict__ L = views + sr.lattice;
-    const int y = sr.yw >> kSegWordBits;
-    const int w = sr.yw & ((1 << kSegWordBits) - 1);
+// What one lane knows about its cell of one row segment before touching
+// populations: everything here comes from the segment list, the lattice
+// descriptor and the mask, none of which a time step writes.
+template <class T>
+struct SegCtx {
+  const LatticeView* L;
+  T* F;
+  int y, c, pitch, pl;
+  unsigned nb;  // solid flags of the 8 neighbours (phase A)
+  bool fluid, inlet, outlet;
+  long long fe;  // population elements (bounds-checked builds)
+};
+
+template <class T, int PHASE>
+__device__ __forceinline__ void seg_prologue(const LatticeView* __restrict__ views, const SegRef sr, bool valid,
+                                             const int lane, SegCtx<T>& s) {
+  const LatticeView* __restrict__ L = views + (valid ? sr.lattice : 0);
+  const int y = sr.yw >> kSegWordBits;
+  const int w = sr.yw & ((1 << kSegWordBits) - 1);
 #ifdef LBM_CHECK_BOUNDS
-    if (sr.lattice < 0 || y < 1 || y > L->ny - 2 || w < 0 || w >= L->wpr) {
-      if (lane == 0) printf("lbm bounds: bad segment: lattice %d y %d w %d\n", sr.lattice, y, w);
-      return;
-    }
+  if (valid && (sr.lattice < 0 || y < 1 || y > L->ny - 2 || w < 0 || w >= L->wpr)) {
+    if (lane == 0) printf("lbm bounds: bad segment: lattice %d y %d w %d\n", sr.lattice, y, w);
+    valid = false;
+    L = views;
+  }
 #endif
-    const int ms = mask_stride(L->wpr);
-    const uint32_t* mr = L->mask + (long long)y * ms;
-    const uint32_t mc = mr[w];
-    const int nx = L->nx;
-    const int x = (w << 5) + lane;
-    const bool fluid = !((mc >> lane) & 1u);  // bits beyond nx are set (solid)
-    const bool inlet = (x == 0);
-    const bool outlet = (x == nx - 1);
-
-    unsigned nb = 0;  // solid flags of the 8 neighbours (phase A only)
-    if (PHASE == 0) {
-      // padded mask: words w-1 and w+1 of rows y-1..y+1 always exist and are
-      // solid outside the lattice
-      const uint32_t* rn = mr + ms;
-      const uint32_t* rs = mr - ms;
-      const uint32_t mn = rn[w], msth = rs[w];
-      const uint32_t eC = __funnelshift_r(mc, mr[w + 1], 1), wC = __funnelshift_l(mr[w - 1], mc, 1);
-      const uint32_t eN = __funnelshift_r(mn, rn[w + 1], 1), wN = __funnelshift_l(rn[w - 1], mn, 1);
-      const uint32_t eS = __funnelshift_r(msth, rs[w + 1], 1), wS = __funnelshift_l(rs[w - 1], msth, 1);
-      nb = ((eC >> lane) & 1u) | (((mn >> lane) & 1u) << 1) | (((wC >> lane) & 1u) << 2) |
+  s.L = L;
+  s.F = static_cast<T*>(L->f);
+  s.pitch = L->pitch;
+  s.pl = (int)L->plane;  // 32-bit element offsets: lattices are limited to 9 * plane < 2^31
+  s.fe = L->f_elems;
+  s.nb = 0;
+  if (!valid) {
+    s.y = 0;
+    s.c = 0;
+    s.fluid = s.inlet = s.outlet = false;
+    return;
+  }
+  const int ms = mask_stride(L->wpr);
+  const uint32_t* mr = L->mask + (long long)y * ms;
+  const uint32_t mc = mr[w];
+  const int x = (w << 5) + lane;
+  s.y = y;
+  s.c = y * s.pitch + x;
+  s.fluid = !((mc >> lane) & 1u);  // bits beyond nx are set (solid)
+  s.inlet = (x == 0);
+  s.outlet = (x == L->nx - 1);
+  if (PHASE == 0) {
+    // padded mask: words w-1 and w+1 of rows y-1..y+1 always exist and are
+    // solid outside the lattice
+    const uint32_t* rn = mr + ms;
+    const uint32_t* rs = mr - ms;
+    const uint32_t mn = rn[w], msth = rs[w];
+    const uint32_t eC = __funnelshift_r(mc, mr[w + 1], 1), wC = __funnelshift_l(mr[w - 1], mc, 1);
+    const uint32_t eN = __funnelshift_r(mn, rn[w + 1], 1), wN = __funnelshift_l(rn[w - 1], mn, 1);
+    const uint32_t eS = __funnelshift_r(msth, rs[w + 1], 1), wS = __funnelshift_l(rs[w - 1], msth, 1);
+    s.nb = ((eC >> lane) & 1u) | (((mn >> lane) & 1u) << 1) | (((wC >> lane) & 1u) << 2) |
            (((msth >> lane) & 1u) << 3) | (((eN >> lane) & 1u) << 4) | (((wN >> lane) & 1u) << 5) |
            (((wS >> lane) & 1u) << 6) | (((eS >> lane) & 1u) << 7);
-    }
-    // 32-bit element offsets: lattices are limited to 9 * plane < 2^31
-    const int pitch = L->pitch;
-    const int pl = (int)L->plane;
-    const float rho0 = L->rho0;
-    const float omega = L->omega;
-    const int rule = L->outlet_rule;
-    T* __restrict__ F = static_cast<T*>(L->f);
-    const long long fe = L->f_elems;
-    (void)fe;
-    const int c = y * pitch + x;
+  }
+}
 
-    if (!PERSIST && !waited) {  // warp-uniform: populations of the previous step are final from here on
-      asm volatile("griddepcontrol.wait;" ::: "memory");
-      waited = true;
-    }
-
-    float g[9];
+// The nine incoming populations of the lane's cell (0 where unknown or solid).
+// CG: read through L2 only (the persistent kernel: within one launch a slot
+// written by another block must not be served from this SM's L1).
+template <class T, int PHASE, bool CG>
+__device__ __forceinline__ void seg_load(const SegCtx<T>& s, float (&g)[9]) {
+  using P = Pop<T>;
+  const T* __restrict__ F = s.F;
+  const int c = s.c, pl = s.pl, pitch = s.pitch;
+  const unsigned nb = s.nb;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = 0.0f;
-    if (fluid) {
-      if (PHASE == 0) {
-        g[0] = FLD(c);
-        g[2] = (nb & kS) ? FLD(4 * pl + c) : FLD(2 * pl + c - pitch);
-        g[4] = (nb & kN) ? FLD(2 * pl + c) : FLD(4 * pl + c + pitch);
-        if (!inlet) {  // sources on the west side (unknown at the inlet)
-          g[1] = (nb & kW) ? FLD(3 * pl + c) : FLD(1 * pl + c - 1);
-          g[5] = (nb & kSW) ? FLD(7 * pl + c) : FLD(5 * pl + c - pitch - 1);
-          g[8] = (nb & kNW) ? FLD(6 * pl + c) : FLD(8 * pl + c + pitch - 1);
-        }
-        if (!outlet) {  // sources on the east side (unknown at the outlet)
-          g[3] = (nb & kE) ? FLD(1 * pl + c) : FLD(3 * pl + c + 1);
-          g[6] = (nb & kSE) ? FLD(8 * pl + c) : FLD(6 * pl + c - pitch + 1);
-          g[7] = (nb & kNE) ? FLD(5 * pl + c) : FLD(7 * pl + c + pitch + 1);
-        }
-      } else {
-        g[0] = FLD(c);
-        g[2] = FLD(4 * pl + c);
-        g[4] = FLD(2 * pl + c);
-        if (!inlet) {
-          g[1] = FLD(3 * pl + c);
-          g[5] = FLD(7 * pl + c);
-          g[8] = FLD(6 * pl + c);
-        }
-        if (!outlet) {
-          g[3] = FLD(1 * pl + c);
-          g[6] = FLD(8 * pl + c);
-          g[7] = FLD(5 * pl + c);
-        }
-      }
+  for (int i = 0; i < 9; ++i) g[i] = 0.0f;
+  if (!s.fluid) return;
+  if (PHASE == 0) {
+    g[0] = FLD(c);
+    g[2] = (nb & kS) ? FLD(4 * pl + c) : FLD(2 * pl + c - pitch);
+    g[4] = (nb & kN) ? FLD(2 * pl + c) : FLD(4 * pl + c + pitch);
+    if (!s.inlet) {  // sources on the west side (unknown at the inlet)
+      g[1] = (nb & kW) ? FLD(3 * pl + c) : FLD(1 * pl + c - 1);
+      g[5] = (nb & kSW) ? FLD(7 * pl + c) : FLD(5 * pl + c - pitch - 1);
+      g[8] = (nb & kNW) ? FLD(6 * pl + c) : FLD(8 * pl + c + pitch - 1);
     }
-
-    if (rule == LBM_OUT_NEUMANN) {
-      // zero-gradient outlet: the unknown g3, g6, g7 of cell (nx-1, y) are the
-      // streamed g3, g6, g7 of cell (nx-2, y), held by the lane to the left
-      // (nx is even, so both cells are in this warp's row segment).
-      const float n3 = __shfl_up_sync(0xffffffffu, g[3], 1);
-      const float n6 = __shfl_up_sync(0xffffffffu, g[6], 1);
-      const float n7 = __shfl_up_sync(0xffffffffu, g[7], 1);
-      if (outlet) {
-        g[3] = n3;
-        g[6] = n6;
-        g[7] = n7;
-      }
+    if (!s.outlet) {  // sources on the east side (unknown at the outlet)
+      g[3] = (nb & kE) ? FLD(1 * pl + c) : FLD(3 * pl + c + 1);
+      g[6] = (nb & kSE) ? FLD(8 * pl + c) : FLD(6 * pl + c - pitch + 1);
+      g[7] = (nb & kNE) ? FLD(5 * pl + c) : FLD(7 * pl + c + pitch + 1);
     }
-
-    if (!fluid) return;
-    if (inlet) {
-      inlet_rule(g, L->u_in[y], rho0, L->port_scheme);
-    } else if (outlet && rule == LBM_OUT_CONST_RHO) {
-      outlet_rule(g, rho0, L->port_scheme);
+  } else {
+    g[0] = FLD(c);
+    g[2] = FLD(4 * pl + c);
+    g[4] = FLD(2 * pl + c);
+    if (!s.inlet) {
+      g[1] = FLD(3 * pl + c);
+      g[5] = FLD(7 * pl + c);
+      g[8] = FLD(6 * pl + c);
     }
-    float drho, ux, uy;
-    bgk(g, rho0, omega, drho, ux, uy);
-
-    if (PHASE == 0) {
-      FST(c, g[0]);
-      if (nb & kN) FST(2 * pl + c, g[2]); else FST(4 * pl + c + pitch, g[2]);
-      if (nb & kS) FST(4 * pl + c, g[4]); else FST(2 * pl + c - pitch, g[4]);
-      if (!outlet) {  // destinations on the east side leave through the outlet
-        if (nb & kE) FST(1 * pl + c, g[1]); else FST(3 * pl + c + 1, g[1]);
-        if (nb & kNE) FST(5 * pl + c, g[5]); else FST(7 * pl + c + pitch + 1, g[5]);
-        if (nb & kSE) FST(8 * pl + c, g[8]); else FST(6 * pl + c - pitch + 1, g[8]);
-      }
-      if (!inlet) {  // destinations on the west side leave through the inlet
-        if (nb & kW) FST(3 * pl + c, g[3]); else FST(1 * pl + c - 1, g[3]);
-        if (nb & kNW) FST(6 * pl + c, g[6]); else FST(8 * pl + c + pitch - 1, g[6]);
-        if (nb & kSW) FST(7 * pl + c, g[7]); else FST(5 * pl + c - pitch - 1, g[7]);
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) FST(i * pl + c, g[i]);
-      if (MOM != 0 && LBM_OK_IDX(c, pl)) {
-        L->drho[c] = drho;
-        (MOM == 1 ? L->ux : L->ux_prev)[c] = ux;
-        (MOM == 1 ? L->uy : L->uy_prev)[c] = uy;
-      }
+    if (!s.outlet) {
+      g[3] = FLD(1 * pl + c);
+      g[6] = FLD(8 * pl + c);
+      g[7] = FLD(5 * pl + c);
     }
   }
 }
 
+// Boundary rules, collision and stores of the lane's cell.  Every lane of the
+// warp calls it (the zero-gradient outlet shuffles across lanes).
 template <class T, int PHASE, int MOM>
-__global__ void __launch_bounds__(kMaxStepThreads, 2)
+__device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
+  using P = Pop<T>;
+  const LatticeView* __restrict__ L = s.L;
+  const int rule = L->outlet_rule;
+  if (rule == LBM_OUT_NEUMANN) {
+    // zero-gradient outlet: the unknown g3, g6, g7 of cell (nx-1, y) are the
+    // streamed g3, g6, g7 of cell (nx-2, y), held by the lane to the left
+    // (nx is even, so both cells are in this warp's row segment).
+    const float n3 = __shfl_up_sync(0xffffffffu, g[3], 1);
+    const float n6 = __shfl_up_sync(0xffffffffu, g[6], 1);
+    const float n7 = __shfl_up_sync(0xffffffffu, g[7], 1);
+    if (s.outlet) {
+      g[3] = n3;
+      g[6] = n6;
+      g[7] = n7;
+    }
+  }
+  if (!s.fluid) return;
+  const float rho0 = L->rho0;
+  if (s.inlet) {
+    inlet_rule(g, L->u_in[s.y], rho0, L->port_scheme);
+  } else if (s.outlet && rule == LBM_OUT_CONST_RHO) {
+    outlet_rule(g, rho0, L->port_scheme);
+  }
+  float drho, ux, uy;
+  bgk(g, rho0, L->omega, drho, ux, uy);
+
+  T* __restrict__ F = s.F;
+  const int c = s.c, pl = s.pl, pitch = s.pitch;
+  const unsigned nb = s.nb;
+  if (PHASE == 0) {
+    FST(c, g[0]);
+    if (nb & kN) FST(2 * pl + c, g[2]); else FST(4 * pl + c + pitch, g[2]);
+    if (nb & kS) FST(4 * pl + c, g[4]); else FST(2 * pl + c - pitch, g[4]);
+    if (!s.outlet) {  // destinations on the east side leave through the outlet
+      if (nb & kE) FST(1 * pl + c, g[1]); else FST(3 * pl + c + 1, g[1]);
+      if (nb & kNE) FST(5 * pl + c, g[5]); else FST(7 * pl + c + pitch + 1, g[5]);
+      if (nb & kSE) FST(8 * pl + c, g[8]); else FST(6 * pl + c - pitch + 1, g[8]);
+    }
+    if (!s.inlet) {  // destinations on the west side leave through the inlet
+      if (nb & kW) FST(3 * pl + c, g[3]); else FST(1 * pl + c - 1, g[3]);
+      if (nb & kNW) FST(6 * pl + c, g[6]); else FST(8 * pl + c + pitch - 1, g[6]);
+      if (nb & kSW) FST(7 * pl + c, g[7]); else FST(5 * pl + c - pitch - 1, g[7]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) FST(i * pl + c, g[i]);
+    if (MOM != 0 && LBM_OK_IDX(c, pl)) {
+      L->drho[c] = drho;
+      (MOM == 1 ? L->ux : L->ux_prev)[c] = ux;
+      (MOM == 1 ? L->uy : L->uy_prev)[c] = uy;
+    }
+  }
+}
+
+// One phase on CPT consecutive segments of the list: their loads are all
+// issued before the first cell is updated (more bytes in flight per thread).
+template <class T, int PHASE, int MOM, int CPT, bool CG>
+__device__ __forceinline__ void phase_task(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
+                                           int nseg, int task, int lane, bool pdl_wait) {
+  SegCtx<T> s[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int idx = task * CPT + k;
+    const bool valid = idx < nseg;
+    seg_prologue<T, PHASE>(views, segs[valid ? idx : 0], valid, lane, s[k]);
+  }
+  // populations of the previous step are final from here on
+  if (pdl_wait) asm volatile("griddepcontrol.wait;" ::: "memory");
+  float g[CPT][9];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) seg_load<T, PHASE, CG>(s[k], g[k]);
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) seg_update<T, PHASE, MOM>(s[k], g[k]);
+}
+
+// One phase of one time step over the whole segment list.  Launched as a
+// programmatic dependent of the previous step: descriptors, segments and
+// masks are read before waiting for it, populations after.
+template <class T, int PHASE, int MOM, int CPT>
+__global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
     k_stream_collide(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
                      const int* __restrict__ n_segs) {
   // The next time step may be scheduled now; it reads populations only after
   // waiting for this grid to complete.
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31;
-  // the segment list, descriptors and mask are never written by a time step,
-  // so they may be read before the previous step has finished
   const int nseg = *n_segs;
+  const int ntask = (nseg + CPT - 1) / CPT;
   const int wpb = blockDim.x >> 5;
   const int stride = gridDim.x * wpb;
-  bool waited = false;
-  for (int sidx = blockIdx.x * wpb + (threadIdx.x >> 5); sidx < nseg; sidx += stride)
-    update_segment<T, PHASE, MOM, false>(views, segs[sidx], lane, waited);
-  if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
+  for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntask; t += stride)
+    phase_task<T, PHASE, MOM, CPT, false>(views, segs, nseg, t, lane, true);
+  // every thread waits at least once, so this grid completes only after the
+  // previous one (the next step relies on that)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Grid-wide barrier of the persistent kernel (all blocks co-resident: the
-// kernel is launched cooperatively).  Sense by generation: a block reads the
-// generation, publishes its writes, arrives; the last arrival resets the
-// count and advances the generation; the others wait for the advance.  The
-// wait gives up after kSpinLimit polls, flags the failure and makes every
-// block leave the kernel at its next barrier.
-constexpr unsigned kSpinLimit = 1u << 24;
+// kernel is launched cooperatively).  One monotonic arrival counter, reset
+// before the launch: at its k-th barrier a block publishes its writes,
+// arrives, and waits until the counter reaches k * gridDim.x.  The wait gives
+// up after kSpinLimit polls (or when another block has given up), flags the
+// failure and makes every block leave the kernel at its next barrier.
+constexpr unsigned kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -381,26 +431,20 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-__device__ bool grid_barrier(StepBarrier* b) {
+__device__ bool grid_barrier(StepBarrier* b, unsigned& target) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned gen = ld_acquire(&b->gen);
+    target += gridDim.x;
     __threadfence();  // this block's population writes before its arrival
-    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
-      atomicExch(&b->count, 0u);
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
-      unsigned spins = 0;
-      while (ld_acquire(&b->gen) == gen) {
-        if (++spins > kSpinLimit || ld_acquire(reinterpret_cast<const unsigned*>(&b->error)) != 0) {
-          atomicExch(&b->error, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
+    atomicAdd(&b->count, 1u);
+    unsigned spins = 0;
+    while (ld_acquire(&b->count) < target) {
+      if (++spins > kSpinLimit || ld_acquire(reinterpret_cast<const unsigned*>(&b->error)) != 0) {
+        atomicExch(&b->error, 1);
+        ok = 0;
+        break;
       }
     }
     __threadfence();
@@ -412,42 +456,65 @@ __device__ bool grid_barrier(StepBarrier* b) {
 
 // n_pairs (A, B) time-step pairs in one launch, a grid barrier after every
 // phase but the last.  Same per-cell arithmetic as k_stream_collide.
-template <class T>
-__global__ void __launch_bounds__(kMaxStepThreads, 2)
+template <class T, int CPT>
+__global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
     k_stream_collide_persistent(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
                                 const int* __restrict__ n_segs, int n_pairs, StepBarrier* bar) {
   const int lane = threadIdx.x & 31;
   const int nseg = *n_segs;
+  const int ntask = (nseg + CPT - 1) / CPT;
   const int wpb = blockDim.x >> 5;
   const int stride = gridDim.x * wpb;
   const int first = blockIdx.x * wpb + (threadIdx.x >> 5);
-  bool waited = true;
+  unsigned target = 0;
   for (int p = 0; p < n_pairs; ++p) {
-    for (int sidx = first; sidx < nseg; sidx += stride)
-      update_segment<T, 0, 0, true>(views, segs[sidx], lane, waited);
-    if (!grid_barrier(bar)) return;
-    for (int sidx = first; sidx < nseg; sidx += stride)
-      update_segment<T, 1, 0, true>(views, segs[sidx], lane, waited);
-    if (p + 1 < n_pairs && !grid_barrier(bar)) return;
+    for (int t = first; t < ntask; t += stride) phase_task<T, 0, 0, CPT, true>(views, segs, nseg, t, lane, false);
+    if (!grid_barrier(bar, target)) return;
+    for (int t = first; t < ntask; t += stride) phase_task<T, 1, 0, CPT, true>(views, segs, nseg, t, lane, false);
+    if (p + 1 < n_pairs && !grid_barrier(bar, target)) return;
   }
 }
 
+template <class T, int CPT>
+void* pick(int phase, int moments) {
+  if (phase == 0) return (void*)k_stream_collide<T, 0, 0, CPT>;
+  if (moments == 1) return (void*)k_stream_collide<T, 1, 1, CPT>;
+  if (moments == 2) return (void*)k_stream_collide<T, 1, 2, CPT>;
+  return (void*)k_stream_collide<T, 1, 0, CPT>;
+}
 
 template <class T>
-void* pick(int phase, int moments) {
-  if (phase == 0) return (void*)k_stream_collide<T, 0, 0>;
-  if (moments == 1) return (void*)k_stream_collide<T, 1, 1>;
-  if (moments == 2) return (void*)k_stream_collide<T, 1, 2>;
-  return (void*)k_stream_collide<T, 1, 0>;
+void* pick_cpt(int phase, int moments, int cpt) {
+  return cpt == 1 ? pick<T, 1>(phase, moments) : cpt == 2 ? pick<T, 2>(phase, moments) : nullptr;
 }
 
-void* kernel_for(int precision, int phase, int moments) {
+void* kernel_for(int precision, int phase, int moments, int cpt) {
   switch (precision) {
-    case LBM_F32: return pick<float>(phase, moments);
-    case LBM_BF16_SHIFTED: return pick<__nv_bfloat16>(phase, moments);
-    case LBM_F16_SHIFTED: return pick<__half>(phase, moments);
+    case LBM_F32: return pick_cpt<float>(phase, moments, cpt);
+    case LBM_BF16_SHIFTED: return pick_cpt<__nv_bfloat16>(phase, moments, cpt);
+    case LBM_F16_SHIFTED: return pick_cpt<__half>(phase, moments, cpt);
     default: return nullptr;
   }
+}
+
+template <class T>
+void* persistent_pick(int cpt) {
+  return cpt == 1 ? (void*)k_stream_collide_persistent<T, 1>
+                  : cpt == 2 ? (void*)k_stream_collide_persistent<T, 2> : nullptr;
+}
+
+void* persistent_kernel_for(int precision, int cpt) {
+  switch (precision) {
+    case LBM_F32: return persistent_pick<float>(cpt);
+    case LBM_BF16_SHIFTED: return persistent_pick<__nv_bfloat16>(cpt);
+    case LBM_F16_SHIFTED: return persistent_pick<__half>(cpt);
+    default: return nullptr;
+  }
+}
+
+bool shape_ok(const StepConfig& sc) {
+  return (sc.cells_per_thread == 1 || sc.cells_per_thread == 2) && sc.warps_per_block >= 1 &&
+         sc.warps_per_block * 32 <= max_step_threads(sc.cells_per_thread) && sc.grid >= 1;
 }
 
 }  // namespace
@@ -455,9 +522,8 @@ void* kernel_for(int precision, int phase, int moments) {
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
                                   const SegRef* segs, const int* n_segs, StepConfig sc,
                                   cudaStream_t stream) {
-  void* k = kernel_for(precision, phase, moments);
-  if (!k || sc.warps_per_block < 1 || sc.warps_per_block * 32 > kMaxStepThreads || sc.grid < 1)
-    return cudaErrorInvalidValue;
+  void* k = kernel_for(precision, phase, moments, sc.cells_per_thread);
+  if (!k || !shape_ok(sc)) return cudaErrorInvalidValue;
   void* args[] = {(void*)&views, (void*)&segs, (void*)&n_segs};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -474,21 +540,10 @@ cudaError_t launch_stream_collide(int precision, int phase, int moments, const L
   return e;
 }
 
-namespace {
-void* persistent_kernel_for(int precision) {
-  switch (precision) {
-    case LBM_F32: return (void*)k_stream_collide_persistent<float>;
-    case LBM_BF16_SHIFTED: return (void*)k_stream_collide_persistent<__nv_bfloat16>;
-    case LBM_F16_SHIFTED: return (void*)k_stream_collide_persistent<__half>;
-    default: return nullptr;
-  }
-}
-}  // namespace
-
-int stream_collide_persistent_grid(int precision, int warps_per_block) {
-  void* k = persistent_kernel_for(precision);
+int stream_collide_persistent_grid(int precision, int warps_per_block, int cells_per_thread) {
+  void* k = persistent_kernel_for(precision, cells_per_thread);
   int dev = 0, sms = 0, n = 0;
-  if (!k || cudaGetDevice(&dev) != cudaSuccess ||
+  if (!k || warps_per_block * 32 > max_step_threads(cells_per_thread) || cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, 0) != cudaSuccess)
     return 0;
@@ -498,11 +553,12 @@ int stream_collide_persistent_grid(int precision, int warps_per_block) {
 cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* views, const SegRef* segs,
                                              const int* n_segs, int n_pairs, StepConfig sc, StepBarrier* bar,
                                              cudaStream_t stream) {
-  void* k = persistent_kernel_for(precision);
-  if (!k || n_pairs < 1 || sc.warps_per_block < 1 || sc.warps_per_block * 32 > kMaxStepThreads || sc.grid < 1 ||
-      sc.grid > stream_collide_persistent_grid(precision, sc.warps_per_block))
+  void* k = persistent_kernel_for(precision, sc.cells_per_thread);
+  if (!k || !shape_ok(sc) || n_pairs < 1 ||
+      sc.grid > stream_collide_persistent_grid(precision, sc.warps_per_block, sc.cells_per_thread) ||
+      2ull * (unsigned long long)n_pairs * (unsigned long long)sc.grid >= (1ull << 32))
     return cudaErrorInvalidValue;
-  // a fresh barrier: count 0, generation 0, no error
+  // a fresh barrier: count 0, no error
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(StepBarrier), stream);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&views, (void*)&segs, (void*)&n_segs, (void*)&n_pairs, (void*)&bar};
@@ -521,8 +577,8 @@ cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* v
   return e;
 }
 
-int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block) {
-  void* k = kernel_for(precision, phase, moments);
+int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int cells_per_thread) {
+  void* k = kernel_for(precision, phase, moments, cells_per_thread);
   int n = 0;
   if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, 0) != cudaSuccess)
     return 1;

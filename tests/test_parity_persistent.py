@@ -34,20 +34,27 @@ def _cases():
     ]
 
 
-def _handle(case, precision, persistent, wpb=8):
+def _handle(case, precision, persistent, wpb=8, cpt=1):
     h = L.Lattice(case["cells"], case["tau"], case["u_max"], precision=precision, outlet=case.get("outlet", 0),
                   ports=case.get("ports", 0), residual_every=100)
-    h.set_step_config(wpb, persistent=persistent)
+    h.set_step_config(wpb, persistent=persistent, cells_per_thread=cpt)
     return h
+
+
+# (persistent, warps per block, cells per thread)
+SHAPES = [(True, 8, 1), (True, 8, 2), (False, 8, 2), (False, 4, 2)]
 
 
 @pytest.mark.parametrize("precision", [L.F32, L.BF16_SHIFTED])
 @pytest.mark.parametrize("k", range(4))
-def test_persistent_equals_per_phase_launches(k, precision):
+def test_launch_shapes_compute_the_same_values(k, precision):
+    """Each launch shape -- persistent or per-phase, one or two cells per
+    thread -- against the default shape, bit for bit."""
     case = _cases()[k]
+    pers, wpb, cpt = SHAPES[k]
     a = _handle(case, precision, False)
-    b = _handle(case, precision, True, wpb=16 if k % 2 else 8)
-    assert b.step_config()[2] == 1 and a.step_config()[2] == 0
+    b = _handle(case, precision, pers, wpb=wpb, cpt=cpt)
+    assert b.step_config()[2] == int(pers) and b.step_config()[3] == cpt and a.step_config()[2] == 0
     ra, rb = a.solve(600), b.solve(600)
     assert ra["dp"] == rb["dp"] and ra["residual"] == rb["residual"]
     assert np.array_equal(a.read(L.FIELD_POPS), b.read(L.FIELD_POPS))
@@ -65,7 +72,7 @@ def test_persistent_tree_2048_matches_oracle(ora):
     cells = cfg["cells"]
     ny, nx = cells.shape
     h = L.Lattice(cells, cfg["tau"], cfg["u_max"], residual_every=0)
-    h.set_step_config(16, persistent=True)
+    h.set_step_config(8, persistent=True, cells_per_thread=2)
     g = h.solve(300)
     s = ora.Solver(ora.make_params(nx, ny, cfg["tau"], 1.0, cfg["u_max"]), cells, residual_every=0)
     o = s.solve(300)
@@ -78,12 +85,12 @@ def test_persistent_tree_2048_matches_oracle(ora):
     h.close()
 
 
-def test_persistent_batch_equals_per_phase_batch():
+def test_two_cells_per_thread_batch_equals_default_batch():
     members = _cases()
     a = L.Batch(members, residual_every=0)
     b = L.Batch(members, residual_every=0)
     a.set_step_config(8, persistent=False)
-    b.set_step_config(16, persistent=True)
+    b.set_step_config(8, persistent=False, cells_per_thread=2)
     ra, rb = a.solve(400), b.solve(400)
     assert [x["dp"] for x in ra] == [x["dp"] for x in rb]
     oa, ob = a.optimize_step([3, 2, 1, 4], 200), b.optimize_step([3, 2, 1, 4], 200)
@@ -97,8 +104,8 @@ def test_persistent_batch_equals_per_phase_batch():
 def test_set_step_config_errors():
     t = I.config_t_junction()
     h = L.Lattice(t["cells"], t["tau"], t["u_max"])
-    for wpb, pers in ((3, 0), (32, 0), (4, 1), (8, 2)):
+    for wpb, pers, cpt in ((3, 0, 1), (32, 0, 1), (4, 1, 1), (8, 2, 1), (8, 0, 3), (16, 0, 2), (8, 1, 0)):
         with pytest.raises(L.LbmError) as e:
-            h.set_step_config(wpb, persistent=pers)
+            h.set_step_config(wpb, persistent=pers, cells_per_thread=cpt)
         assert e.value.status == 1
     h.close()
