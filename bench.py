@@ -274,7 +274,7 @@ def leg_batched(L, I, stream, prec, n=256, iters=10, S=2000, sample=32):
         dp_b.append([x["dp"] for x in rb])
     t_batch = time.perf_counter() - t0
     ms, nl, nu = b.kernel_time()
-    w, g, pers, cpt = b.step_config()
+    w, g, pers, cpt, stg = b.step_config()
     b.close()
     upd = sum(fluid) * S * (iters + 1)
     idx = list(range(0, n, max(1, n // sample)))[:sample]
@@ -298,7 +298,7 @@ def leg_batched(L, I, stream, prec, n=256, iters=10, S=2000, sample=32):
     g_plain = upd_plain / t_plain / 1e9
     return {"candidates": n, "fluid_cells": sum(fluid), "iterations": iters, "steps_per_solve": S,
             "batched_glups": g_batch, "batched_step_glups": nu / (ms / 1e3) / 1e9,
-            "batched_s": t_batch, "step_config": [w, g, pers, cpt],
+            "batched_s": t_batch, "step_config": [w, g, pers, cpt, stg],
             "one_at_a_time_glups": g_plain, "one_at_a_time_sample": len(idx),
             "speedup": g_batch / g_plain, "dp_rel_diff_batched_vs_alone_max": worst}
 

@@ -229,18 +229,21 @@ lbm_status lbm_kernel_time(lbm_handle h, int reset, double* ms, int64_t* launche
 
 /* Launch shape the handle's time steps use: warps per block, blocks,
  * persistent = 1 when every run of time steps is one cooperative launch with
- * grid-wide barriers between phases (0: one launch per phase), and
- * cells_per_thread = row segments each warp updates at once (1 or 2).
- * Tuned on the handle's own lattice at its first solve of 256 steps or more,
- * unless set with lbm_set_step_config.  Any output pointer may be NULL.    */
+ * grid-wide barriers between phases (0: one launch per phase),
+ * cells_per_thread = row segments each warp updates at once (1 or 2), and
+ * stages = 0 (populations loaded straight into registers) or 2 / 3 (copied
+ * into shared memory that many segments ahead of their update).  Tuned on
+ * the handle's own lattice at its first solve of 256 steps or more, unless
+ * set with lbm_set_step_config.  Any output pointer may be NULL.          */
 lbm_status lbm_step_config(lbm_handle h, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
-                           int32_t* cells_per_thread);
+                           int32_t* cells_per_thread, int32_t* stages);
 /* Fix the launch shape (and skip tuning): warps_per_block 4, 8 or 16 (4 or 8
  * with two cells per thread; 8 or 16 when persistent), cells_per_thread 1
- * or 2; the grid is sized for the device.  Every shape computes the same
- * values, so this changes timings only.                                   */
+ * or 2, stages 0, 2 or 3 (staged loads: one cell per thread, not
+ * persistent); the grid is sized for the device.  Every shape computes the
+ * same values, so this changes timings only.                              */
 lbm_status lbm_set_step_config(lbm_handle h, int32_t warps_per_block, int32_t persistent,
-                               int32_t cells_per_thread);
+                               int32_t cells_per_thread, int32_t stages);
 
 /* ---- batches -------------------------------------------------------------
  * Many candidate geometries (Sec. 2.3 applied to each) stepped together: one
@@ -271,9 +274,9 @@ lbm_status lbm_batch_kernel_time(lbm_batch b, int reset, double* ms, int64_t* la
                                  int64_t* fluid_updates);
 /* As lbm_step_config / lbm_set_step_config.                               */
 lbm_status lbm_batch_step_config(lbm_batch b, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
-                                 int32_t* cells_per_thread);
+                                 int32_t* cells_per_thread, int32_t* stages);
 lbm_status lbm_batch_set_step_config(lbm_batch b, int32_t warps_per_block, int32_t persistent,
-                                     int32_t cells_per_thread);
+                                     int32_t cells_per_thread, int32_t stages);
 void lbm_batch_destroy(lbm_batch b);
 
 /* ---- serving ---------------------------------------------------------------

@@ -114,14 +114,15 @@ lbm_status lbm_kernel_time(lbm_handle h, int reset, double* ms, int64_t* launche
 }
 
 lbm_status lbm_step_config(lbm_handle h, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
-                           int32_t* cells_per_thread) {
+                           int32_t* cells_per_thread, int32_t* stages) {
   if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
-  return engine_step_config(h->e, warps_per_block, grid, persistent, cells_per_thread);
+  return engine_step_config(h->e, warps_per_block, grid, persistent, cells_per_thread, stages);
 }
 
-lbm_status lbm_set_step_config(lbm_handle h, int32_t warps_per_block, int32_t persistent, int32_t cells_per_thread) {
+lbm_status lbm_set_step_config(lbm_handle h, int32_t warps_per_block, int32_t persistent, int32_t cells_per_thread,
+                               int32_t stages) {
   if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
-  return engine_set_step_config(h->e, warps_per_block, persistent, cells_per_thread);
+  return engine_set_step_config(h->e, warps_per_block, persistent, cells_per_thread, stages);
 }
 
 lbm_status lbm_select_swaps(lbm_handle h, const float* drho, const float* ux, const float* uy,
@@ -226,14 +227,15 @@ lbm_status lbm_batch_kernel_time(lbm_batch b, int reset, double* ms, int64_t* la
 }
 
 lbm_status lbm_batch_step_config(lbm_batch b, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
-                                 int32_t* cells_per_thread) {
+                                 int32_t* cells_per_thread, int32_t* stages) {
   if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
-  return engine_step_config(b->e, warps_per_block, grid, persistent, cells_per_thread);
+  return engine_step_config(b->e, warps_per_block, grid, persistent, cells_per_thread, stages);
 }
 
-lbm_status lbm_batch_set_step_config(lbm_batch b, int32_t warps_per_block, int32_t persistent, int32_t cells_per_thread) {
+lbm_status lbm_batch_set_step_config(lbm_batch b, int32_t warps_per_block, int32_t persistent,
+                                     int32_t cells_per_thread, int32_t stages) {
   if (!b) return fail(LBM_ERR_ARG, "batch is NULL");
-  return engine_set_step_config(b->e, warps_per_block, persistent, cells_per_thread);
+  return engine_set_step_config(b->e, warps_per_block, persistent, cells_per_thread, stages);
 }
 
 }  // extern "C"

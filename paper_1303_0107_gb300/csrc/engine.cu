@@ -306,8 +306,8 @@ lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
 // Launch shape: every segment its own warp, but never more blocks than fit
 // on the device at once; a fixed-grid engine always takes the device-sized
 // grid, so its captured graphs outlive changes of the member list.
-StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale, int cpt = 1) {
-  const int bps = stream_collide_blocks_per_sm(E->precision, 0, 0, wpb, cpt);
+StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale, int cpt = 1, int stages = 0) {
+  const int bps = stream_collide_blocks_per_sm(E->precision, 0, 0, wpb, cpt, stages);
   const long long cap = (long long)E->sm_count * bps * blocks_per_sm_scale;
   const long long tasks = ((long long)E->L.total_seg_words + cpt - 1) / cpt;
   const long long need = (tasks + wpb - 1) / wpb;
@@ -316,6 +316,7 @@ StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale, int cpt = 1) {
   c.grid = (int)(E->fixed_grid ? cap : std::max<long long>(1, std::min(need, cap)));
   c.persistent = 0;
   c.cells_per_thread = cpt;
+  c.stages = stages;
   return c;
 }
 
@@ -327,6 +328,7 @@ StepConfig persistent_shape(Engine* E, int wpb, int cpt = 1) {
   c.grid = stream_collide_persistent_grid(E->precision, wpb, cpt);
   c.persistent = 1;
   c.cells_per_thread = cpt;
+  c.stages = 0;
   return c;
 }
 
@@ -361,6 +363,8 @@ lbm_status autotune(Engine* E) {
                   d.cells_per_thread == c.cells_per_thread);
         if (!dup) cand.push_back(c);
       }
+  for (int stages : {2, 3})
+    for (int wpb : {4, 8}) cand.push_back(shape(E, wpb, 1, 1, stages));
   if (persistent_enabled())
     for (int cpt : {1, 2}) {
       StepConfig c = persistent_shape(E, 8, cpt);
@@ -930,15 +934,20 @@ lbm_status engine_read(Engine* E, int i, uint32_t which, void* dst, size_t dst_b
 }
 
 lbm_status engine_step_config(Engine* E, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
-                              int32_t* cells_per_thread) {
+                              int32_t* cells_per_thread, int32_t* stages) {
   if (warps_per_block) *warps_per_block = E->step.warps_per_block;
   if (grid) *grid = E->step.grid;
   if (persistent) *persistent = E->step.persistent;
   if (cells_per_thread) *cells_per_thread = E->step.cells_per_thread;
+  if (stages) *stages = E->step.stages;
   return LBM_OK;
 }
 
-lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t persistent, int32_t cells_per_thread) {
+lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t persistent, int32_t cells_per_thread,
+                                  int32_t stages) {
+  if (stages != 0 && stages != 2 && stages != 3) return fail(LBM_ERR_ARG, "stages must be 0, 2 or 3");
+  if (stages != 0 && (persistent || cells_per_thread != 1))
+    return fail(LBM_ERR_ARG, "staged loads take one cell per thread and per-phase launches");
   if (warps_per_block != 4 && warps_per_block != 8 && warps_per_block != 16)
     return fail(LBM_ERR_ARG, "warps_per_block must be 4, 8 or 16");
   if (persistent != 0 && persistent != 1) return fail(LBM_ERR_ARG, "persistent must be 0 or 1");
@@ -947,7 +956,7 @@ lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t pe
     return fail(LBM_ERR_ARG, "two cells per thread take 4 or 8 warps per block");
   if (persistent && warps_per_block == 4) return fail(LBM_ERR_ARG, "the persistent kernel takes 8 or 16 warps per block");
   StepConfig c = persistent ? persistent_shape(E, warps_per_block, cells_per_thread)
-                            : shape(E, warps_per_block, 1, cells_per_thread);
+                            : shape(E, warps_per_block, 1, cells_per_thread, stages);
   if (c.grid < 1) return fail(LBM_ERR_CUDA, "no resident block for the persistent kernel");
   E->step = c;
   E->tuned = true;

@@ -99,7 +99,7 @@ struct Engine {
 
   cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};  // views, segs, n_segs, shape
-  StepConfig step{kStepWarps, 1, 0, 1};
+  StepConfig step{kStepWarps, 1, 0, 1, 0};
   bool tuned = false;
   cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
   double step_ms = 0.0;
@@ -138,8 +138,9 @@ lbm_status engine_solve(Engine* E, int64_t n_steps, lbm_solve_result* out);
 lbm_status engine_optimize(Engine* E, const int32_t* n_swap, int64_t n_steps, lbm_opt_result* out);
 lbm_status engine_read(Engine* E, int i, uint32_t which, void* dst, size_t dst_bytes);
 lbm_status engine_step_config(Engine* E, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
-                              int32_t* cells_per_thread);
-lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t persistent, int32_t cells_per_thread);
+                              int32_t* cells_per_thread, int32_t* stages);
+lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t persistent, int32_t cells_per_thread,
+                                  int32_t stages);
 lbm_status engine_kernel_time(Engine* E, int reset, double* ms, int64_t* launches, int64_t* fluid_updates);
 
 // thread-local last error and launch counter state shared with api.cu

@@ -103,6 +103,8 @@ struct StepConfig {
   int grid;             // blocks
   int persistent;       // 1: all pairs of a solve in one cooperative launch
   int cells_per_thread; // 1 or 2: row segments per warp task (2: at most 8 warps per block)
+  int stages;           // 0: populations loaded into registers; 2 or 3: staged through shared
+                        //    memory that many segments ahead (one cell per thread, per-phase launches)
 };
 // Grid barrier state of the persistent kernel (device memory, 16 bytes).
 struct StepBarrier {
@@ -114,7 +116,8 @@ struct StepBarrier {
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
                                   const SegRef* segs, const int* n_segs, StepConfig cfg,
                                   cudaStream_t stream);
-int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int cells_per_thread);
+int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int cells_per_thread,
+                                 int stages);
 // n_pairs time-step pairs (phase A then B, no moments) in one cooperative
 // launch with a grid barrier between phases; sc.grid must not exceed
 // stream_collide_persistent_grid (every block resident at once), and

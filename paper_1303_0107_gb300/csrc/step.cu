@@ -49,18 +49,26 @@ struct Pop<float> {
   static __device__ __forceinline__ float ld(const float* p) { return *p; }
   static __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
   static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+  // the element held in a 4-byte word (hi: the upper of two 16-bit halves)
+  static __device__ __forceinline__ float from_word(uint32_t w, int) { return __uint_as_float(w); }
 };
 template <>
 struct Pop<__nv_bfloat16> {
   static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   static __device__ __forceinline__ float ldcg(const __nv_bfloat16* p) { return __bfloat162float(__ldcg(p)); }
   static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ float from_word(uint32_t w, int hi) {
+    return __bfloat162float(__ushort_as_bfloat16((unsigned short)(w >> (hi ? 16 : 0))));
+  }
 };
 template <>
 struct Pop<__half> {
   static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
   static __device__ __forceinline__ float ldcg(const __half* p) { return __half2float(__ldcg(p)); }
   static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+  static __device__ __forceinline__ float from_word(uint32_t w, int hi) {
+    return __half2float(__ushort_as_half((unsigned short)(w >> (hi ? 16 : 0))));
+  }
 };
 
 constexpr float kW0 = 4.0f / 9.0f;
@@ -417,6 +425,140 @@ __global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+
+// ---- staged variant: populations copied into shared memory ahead of use ----
+//
+// Each warp keeps NS stages of one row segment each in shared memory (nine
+// population words and two context words per lane).  While it updates the
+// segment in stage k, the copies for the next NS-1 segments of its list are
+// in flight (cp.async, 4 bytes per lane and direction: the word holding the
+// lane's element), so the bytes in flight per SM no longer depend on the
+// registers a thread can hold.
+
+// Element offset (from F) of direction i's incoming population for the cell
+// at offset c, or -1 where it is unknown (the open side of a port cell).
+// The same selection as seg_load.
+template <int PHASE>
+__device__ __forceinline__ int src_off(const int i, const int c, const int pitch, const int pl, const unsigned nb,
+                                       const bool inlet, const bool outlet) {
+  if (PHASE == 1) {
+    switch (i) {
+      case 0: return c;
+      case 1: return inlet ? -1 : 3 * pl + c;
+      case 2: return 4 * pl + c;
+      case 3: return outlet ? -1 : 1 * pl + c;
+      case 4: return 2 * pl + c;
+      case 5: return inlet ? -1 : 7 * pl + c;
+      case 6: return outlet ? -1 : 8 * pl + c;
+      case 7: return outlet ? -1 : 5 * pl + c;
+      default: return inlet ? -1 : 6 * pl + c;
+    }
+  }
+  switch (i) {
+    case 0: return c;
+    case 1: return inlet ? -1 : (nb & kW) ? 3 * pl + c : 1 * pl + c - 1;
+    case 2: return (nb & kS) ? 4 * pl + c : 2 * pl + c - pitch;
+    case 3: return outlet ? -1 : (nb & kE) ? 1 * pl + c : 3 * pl + c + 1;
+    case 4: return (nb & kN) ? 2 * pl + c : 4 * pl + c + pitch;
+    case 5: return inlet ? -1 : (nb & kSW) ? 7 * pl + c : 5 * pl + c - pitch - 1;
+    case 6: return outlet ? -1 : (nb & kSE) ? 8 * pl + c : 6 * pl + c - pitch + 1;
+    case 7: return outlet ? -1 : (nb & kNE) ? 5 * pl + c : 7 * pl + c + pitch + 1;
+    default: return inlet ? -1 : (nb & kNW) ? 6 * pl + c : 8 * pl + c + pitch - 1;
+  }
+}
+
+constexpr int kStageWords = 9 * 32 + 2 * 32;  // populations, then cell offset and flags per lane
+
+// Copy the 4-byte word holding element `off` of F into shared memory
+// (zero-filled, nothing read, where off < 0).
+template <class T>
+__device__ __forceinline__ void cp_async_word(uint32_t* dst, const T* F, int off, long long fe) {
+  if (off >= 0 && !LBM_OK_IDX(off, fe)) off = -1;
+  const char* src = reinterpret_cast<const char*>(F) + ((off < 0 ? 0ll : (long long)off * (long long)sizeof(T)) & ~3ll);
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = off < 0 ? 0 : 4;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+
+template <class T, int PHASE>
+__device__ __forceinline__ void stage_issue(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
+                                            int nseg, int t, int lane, uint32_t* buf) {
+  const bool valid = t < nseg;
+  const SegRef sr = segs[valid ? t : 0];
+  SegCtx<T> s;
+  seg_prologue<T, PHASE>(views, sr, valid, lane, s);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int off = s.fluid ? src_off<PHASE>(i, s.c, s.pitch, s.pl, s.nb, s.inlet, s.outlet) : -1;
+    cp_async_word<T>(buf + i * 32 + lane, s.F, off, s.fe);
+  }
+  buf[9 * 32 + lane] = (uint32_t)s.c;
+  buf[10 * 32 + lane] = s.nb | ((uint32_t)s.fluid << 8) | ((uint32_t)s.inlet << 9) | ((uint32_t)s.outlet << 10) |
+                        ((uint32_t)(valid ? sr.lattice : 0) << 12);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <class T, int PHASE, int MOM>
+__device__ __forceinline__ void stage_consume(const LatticeView* __restrict__ views, const uint32_t* buf, int lane) {
+  using P = Pop<T>;
+  const uint32_t fl = buf[10 * 32 + lane];
+  SegCtx<T> s;
+  const LatticeView* __restrict__ L = views + (fl >> 12);
+  s.L = L;
+  s.F = static_cast<T*>(L->f);
+  s.pitch = L->pitch;
+  s.pl = (int)L->plane;
+  s.fe = L->f_elems;
+  s.c = (int)buf[9 * 32 + lane];
+  s.nb = fl & 0xffu;
+  s.fluid = (fl >> 8) & 1u;
+  s.inlet = (fl >> 9) & 1u;
+  s.outlet = (fl >> 10) & 1u;
+  s.y = s.inlet ? s.c / s.pitch : 0;  // the inlet rule looks up the row's speed
+  float g[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int off = s.fluid ? src_off<PHASE>(i, s.c, s.pitch, s.pl, s.nb, s.inlet, s.outlet) : -1;
+    g[i] = off < 0 ? 0.0f : P::from_word(buf[i * 32 + lane], off & 1);
+  }
+  seg_update<T, PHASE, MOM>(s, g);
+}
+
+template <int NS>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
+}
+
+template <class T, int PHASE, int MOM, int NS>
+__global__ void __launch_bounds__(512, 2)
+    k_stream_collide_staged(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
+                            const int* __restrict__ n_segs) {
+  extern __shared__ uint32_t stage_smem[];
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int nseg = *n_segs;
+  const int stride = gridDim.x * wpb;
+  const int first = blockIdx.x * wpb + warp;
+  uint32_t* wbuf = stage_smem + (size_t)warp * NS * kStageWords;
+  // populations of the previous step are final from here on
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k) stage_issue<T, PHASE>(views, segs, nseg, first + k * stride, lane, wbuf + k * kStageWords);
+  for (int k = 0; first + k * stride < nseg; ++k) {
+    stage_issue<T, PHASE>(views, segs, nseg, first + (k + NS - 1) * stride, lane,
+                          wbuf + ((k + NS - 1) % NS) * kStageWords);
+    cp_async_wait<NS>();  // the stage of task k has landed
+    stage_consume<T, PHASE, MOM>(views, wbuf + (k % NS) * kStageWords, lane);
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+size_t staged_smem_bytes(int warps_per_block, int stages) {
+  return (size_t)warps_per_block * stages * kStageWords * sizeof(uint32_t);
+}
+
 // Grid-wide barrier of the persistent kernel (all blocks co-resident: the
 // kernel is launched cooperatively).  One monotonic arrival counter, reset
 // before the launch: at its k-th barrier a block publishes its writes,
@@ -483,18 +625,37 @@ void* pick(int phase, int moments) {
   return (void*)k_stream_collide<T, 1, 0, CPT>;
 }
 
+template <class T, int NS>
+void* pick_staged(int phase, int moments) {
+  if (phase == 0) return (void*)k_stream_collide_staged<T, 0, 0, NS>;
+  if (moments == 1) return (void*)k_stream_collide_staged<T, 1, 1, NS>;
+  if (moments == 2) return (void*)k_stream_collide_staged<T, 1, 2, NS>;
+  return (void*)k_stream_collide_staged<T, 1, 0, NS>;
+}
+
 template <class T>
-void* pick_cpt(int phase, int moments, int cpt) {
+void* pick_cpt(int phase, int moments, int cpt, int stages) {
+  if (stages == 2) return cpt == 1 ? pick_staged<T, 2>(phase, moments) : nullptr;
+  if (stages == 3) return cpt == 1 ? pick_staged<T, 3>(phase, moments) : nullptr;
+  if (stages != 0) return nullptr;
   return cpt == 1 ? pick<T, 1>(phase, moments) : cpt == 2 ? pick<T, 2>(phase, moments) : nullptr;
 }
 
-void* kernel_for(int precision, int phase, int moments, int cpt) {
+void* kernel_for(int precision, int phase, int moments, int cpt, int stages) {
   switch (precision) {
-    case LBM_F32: return pick_cpt<float>(phase, moments, cpt);
-    case LBM_BF16_SHIFTED: return pick_cpt<__nv_bfloat16>(phase, moments, cpt);
-    case LBM_F16_SHIFTED: return pick_cpt<__half>(phase, moments, cpt);
+    case LBM_F32: return pick_cpt<float>(phase, moments, cpt, stages);
+    case LBM_BF16_SHIFTED: return pick_cpt<__nv_bfloat16>(phase, moments, cpt, stages);
+    case LBM_F16_SHIFTED: return pick_cpt<__half>(phase, moments, cpt, stages);
     default: return nullptr;
   }
+}
+
+// Dynamic shared memory of a launch; the kernel is allowed that much once.
+size_t launch_smem(void* k, const StepConfig& sc) {
+  if (sc.stages == 0) return 0;
+  const size_t bytes = staged_smem_bytes(sc.warps_per_block, sc.stages);
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return bytes;
 }
 
 template <class T>
@@ -514,7 +675,8 @@ void* persistent_kernel_for(int precision, int cpt) {
 
 bool shape_ok(const StepConfig& sc) {
   return (sc.cells_per_thread == 1 || sc.cells_per_thread == 2) && sc.warps_per_block >= 1 &&
-         sc.warps_per_block * 32 <= max_step_threads(sc.cells_per_thread) && sc.grid >= 1;
+         sc.warps_per_block * 32 <= max_step_threads(sc.cells_per_thread) && sc.grid >= 1 &&
+         (sc.stages == 0 || ((sc.stages == 2 || sc.stages == 3) && sc.cells_per_thread == 1 && !sc.persistent));
 }
 
 }  // namespace
@@ -522,7 +684,7 @@ bool shape_ok(const StepConfig& sc) {
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
                                   const SegRef* segs, const int* n_segs, StepConfig sc,
                                   cudaStream_t stream) {
-  void* k = kernel_for(precision, phase, moments, sc.cells_per_thread);
+  void* k = kernel_for(precision, phase, moments, sc.cells_per_thread, sc.stages);
   if (!k || !shape_ok(sc)) return cudaErrorInvalidValue;
   void* args[] = {(void*)&views, (void*)&segs, (void*)&n_segs};
   cudaLaunchAttribute attr[1];
@@ -531,7 +693,7 @@ cudaError_t launch_stream_collide(int precision, int phase, int moments, const L
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(sc.grid);
   cfg.blockDim = dim3(32 * sc.warps_per_block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = launch_smem(k, sc);
   cfg.stream = stream;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -577,10 +739,13 @@ cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* v
   return e;
 }
 
-int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int cells_per_thread) {
-  void* k = kernel_for(precision, phase, moments, cells_per_thread);
+int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int cells_per_thread,
+                                 int stages) {
+  void* k = kernel_for(precision, phase, moments, cells_per_thread, stages);
+  StepConfig sc{warps_per_block, 1, 0, cells_per_thread, stages};
   int n = 0;
-  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, 0) != cudaSuccess)
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, launch_smem(k, sc)) !=
+                cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }

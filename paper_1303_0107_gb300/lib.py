@@ -119,8 +119,8 @@ def load_library(path=None):
     L.lbm_kernel_launches.restype = ctypes.c_uint64
     L.lbm_kernel_time.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
-    L.lbm_step_config.argtypes = [H] + [ctypes.POINTER(ctypes.c_int32)] * 4
-    L.lbm_set_step_config.argtypes = [H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    L.lbm_step_config.argtypes = [H] + [ctypes.POINTER(ctypes.c_int32)] * 5
+    L.lbm_set_step_config.argtypes = [H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     B = _VP
     L.lbm_batch_create.argtypes = [ctypes.c_int32, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p), _VP,
                                    ctypes.POINTER(B)]
@@ -131,8 +131,8 @@ def load_library(path=None):
     L.lbm_batch_reset.argtypes = [B]
     L.lbm_batch_kernel_time.argtypes = [B, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
-    L.lbm_batch_step_config.argtypes = [B] + [ctypes.POINTER(ctypes.c_int32)] * 4
-    L.lbm_batch_set_step_config.argtypes = [B, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    L.lbm_batch_step_config.argtypes = [B] + [ctypes.POINTER(ctypes.c_int32)] * 5
+    L.lbm_batch_set_step_config.argtypes = [B, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     L.lbm_batch_destroy.argtypes = [B]
     L.lbm_batch_destroy.restype = None
     L.lbm_select_swaps_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
@@ -274,14 +274,15 @@ class Lattice:
         _check(load_library().lbm_reset(self._h), "lbm_reset")
 
     def step_config(self):
-        """(warps per block, blocks, persistent, cells per thread) of the time-step launches (autotuned)."""
-        v = [ctypes.c_int32() for _ in range(4)]
+        """(warps per block, blocks, persistent, cells per thread, stages) of the time-step launches
+        (autotuned)."""
+        v = [ctypes.c_int32() for _ in range(5)]
         _check(load_library().lbm_step_config(self._h, *[ctypes.byref(x) for x in v]), "lbm_step_config")
         return tuple(x.value for x in v)
 
-    def set_step_config(self, warps_per_block, persistent=False, cells_per_thread=1):
+    def set_step_config(self, warps_per_block, persistent=False, cells_per_thread=1, stages=0):
         _check(load_library().lbm_set_step_config(self._h, int(warps_per_block), int(persistent),
-                                                  int(cells_per_thread)), "lbm_set_step_config")
+                                                  int(cells_per_thread), int(stages)), "lbm_set_step_config")
 
     def select_swaps(self, drho, ux, uy, n_swap: int):
         arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (drho, ux, uy)]
@@ -379,13 +380,14 @@ class Batch:
         return ms.value, n.value, u.value
 
     def step_config(self):
-        v = [ctypes.c_int32() for _ in range(4)]
+        v = [ctypes.c_int32() for _ in range(5)]
         _check(load_library().lbm_batch_step_config(self._b, *[ctypes.byref(x) for x in v]), "lbm_batch_step_config")
         return tuple(x.value for x in v)
 
-    def set_step_config(self, warps_per_block, persistent=False, cells_per_thread=1):
+    def set_step_config(self, warps_per_block, persistent=False, cells_per_thread=1, stages=0):
         _check(load_library().lbm_batch_set_step_config(self._b, int(warps_per_block), int(persistent),
-                                                        int(cells_per_thread)), "lbm_batch_set_step_config")
+                                                        int(cells_per_thread), int(stages)),
+               "lbm_batch_set_step_config")
 
 
 class Server:

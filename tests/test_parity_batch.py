@@ -56,7 +56,7 @@ def test_batch_members_equal_single_handles_bitwise():
         assert ob[i]["dp"] == os_["dp"], i
         assert np.array_equal(batch.read(i, L.FIELD_MASK), h.read(L.FIELD_MASK))
         h.close()
-    w, g, _, _ = batch.step_config()
+    w, g, _, _, _ = batch.step_config()
     assert w in (4, 8, 16) and g >= 1
     batch.close()
 

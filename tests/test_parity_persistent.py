@@ -34,27 +34,30 @@ def _cases():
     ]
 
 
-def _handle(case, precision, persistent, wpb=8, cpt=1):
+def _handle(case, precision, persistent, wpb=8, cpt=1, stages=0):
     h = L.Lattice(case["cells"], case["tau"], case["u_max"], precision=precision, outlet=case.get("outlet", 0),
                   ports=case.get("ports", 0), residual_every=100)
-    h.set_step_config(wpb, persistent=persistent, cells_per_thread=cpt)
+    h.set_step_config(wpb, persistent=persistent, cells_per_thread=cpt, stages=stages)
     return h
 
 
-# (persistent, warps per block, cells per thread)
-SHAPES = [(True, 8, 1), (True, 8, 2), (False, 8, 2), (False, 4, 2)]
+# (persistent, warps per block, cells per thread, shared-memory stages)
+SHAPES = [(True, 8, 1, 0), (True, 8, 2, 0), (False, 8, 2, 0), (False, 4, 2, 0), (False, 8, 1, 3), (False, 4, 1, 2),
+          (False, 16, 1, 3), (False, 8, 1, 2)]
 
 
-@pytest.mark.parametrize("precision", [L.F32, L.BF16_SHIFTED])
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("precision", [L.F32, L.BF16_SHIFTED, L.F16_SHIFTED])
+@pytest.mark.parametrize("k", range(len(SHAPES)))
 def test_launch_shapes_compute_the_same_values(k, precision):
     """Each launch shape -- persistent or per-phase, one or two cells per
-    thread -- against the default shape, bit for bit."""
-    case = _cases()[k]
-    pers, wpb, cpt = SHAPES[k]
+    thread, loads into registers or staged through shared memory -- against
+    the default shape, bit for bit."""
+    case = _cases()[k % 4]
+    pers, wpb, cpt, stages = SHAPES[k]
     a = _handle(case, precision, False)
-    b = _handle(case, precision, pers, wpb=wpb, cpt=cpt)
-    assert b.step_config()[2] == int(pers) and b.step_config()[3] == cpt and a.step_config()[2] == 0
+    b = _handle(case, precision, pers, wpb=wpb, cpt=cpt, stages=stages)
+    cfg = b.step_config()
+    assert cfg[2] == int(pers) and cfg[3] == cpt and cfg[4] == stages and a.step_config()[2] == 0
     ra, rb = a.solve(600), b.solve(600)
     assert ra["dp"] == rb["dp"] and ra["residual"] == rb["residual"]
     assert np.array_equal(a.read(L.FIELD_POPS), b.read(L.FIELD_POPS))
@@ -85,12 +88,14 @@ def test_persistent_tree_2048_matches_oracle(ora):
     h.close()
 
 
-def test_two_cells_per_thread_batch_equals_default_batch():
+@pytest.mark.parametrize("shape", [(8, 2, 0), (8, 1, 3)])
+def test_batch_shapes_equal_default_batch(shape):
+    wpb, cpt, stages = shape
     members = _cases()
     a = L.Batch(members, residual_every=0)
     b = L.Batch(members, residual_every=0)
     a.set_step_config(8, persistent=False)
-    b.set_step_config(8, persistent=False, cells_per_thread=2)
+    b.set_step_config(wpb, persistent=False, cells_per_thread=cpt, stages=stages)
     ra, rb = a.solve(400), b.solve(400)
     assert [x["dp"] for x in ra] == [x["dp"] for x in rb]
     oa, ob = a.optimize_step([3, 2, 1, 4], 200), b.optimize_step([3, 2, 1, 4], 200)
@@ -104,8 +109,9 @@ def test_two_cells_per_thread_batch_equals_default_batch():
 def test_set_step_config_errors():
     t = I.config_t_junction()
     h = L.Lattice(t["cells"], t["tau"], t["u_max"])
-    for wpb, pers, cpt in ((3, 0, 1), (32, 0, 1), (4, 1, 1), (8, 2, 1), (8, 0, 3), (16, 0, 2), (8, 1, 0)):
+    for wpb, pers, cpt, stg in ((3, 0, 1, 0), (32, 0, 1, 0), (4, 1, 1, 0), (8, 2, 1, 0), (8, 0, 3, 0), (16, 0, 2, 0),
+                                (8, 1, 0, 0), (8, 0, 1, 1), (8, 0, 1, 4), (8, 1, 1, 2), (8, 0, 2, 3)):
         with pytest.raises(L.LbmError) as e:
-            h.set_step_config(wpb, persistent=pers, cells_per_thread=cpt)
+            h.set_step_config(wpb, persistent=pers, cells_per_thread=cpt, stages=stg)
         assert e.value.status == 1
     h.close()
