@@ -17,13 +17,15 @@ from .scaling import eq8_widths, reynolds, viscosity  # noqa: F401
 OUT_CONST_RHO, OUT_NEUMANN = 0, 1
 PORTS_REGULARIZED, PORTS_ZOU_HE = 0, 1
 REINIT_WARM, REINIT_COLD = 0, 1
+COLLIDE_BGK, COLLIDE_REGULARIZED, COLLIDE_SMAGORINSKY = 0, 1, 2
 
 
 class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("tau", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("u_max", ctypes.c_double),
                 ("outlet_rule", ctypes.c_int32), ("periodic", ctypes.c_int32),
-                ("port_scheme", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("port_scheme", ctypes.c_int32), ("guard", ctypes.c_int32), ("collision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("c_smag", ctypes.c_double)]
 
 
 _LIB = None
@@ -59,6 +61,10 @@ def lib():
         L.ora_residual.argtypes = [P, _U8, _D, _D, _D, _D]
         L.ora_residual.restype = ctypes.c_double
         L.ora_scores.argtypes = [P, _U8, _D, _D, _D, ctypes.c_double, _U8, _D]
+        L.ora_simple.argtypes = [P, _U8, ctypes.c_int32, ctypes.c_int32]
+        L.ora_smagorinsky_tau.argtypes = [ctypes.c_double] * 6
+        L.ora_smagorinsky_tau.restype = ctypes.c_double
+        L.ora_simple.restype = ctypes.c_int32
         L.ora_select.argtypes = [P, _U8, _D, ctypes.c_int32, _I32, _I32, _I32]
         L.ora_select.restype = ctypes.c_int32
         L.ora_apply.argtypes = [P, _U8, _D, _I32, _I32, ctypes.c_int32, ctypes.c_int32]
@@ -80,9 +86,9 @@ def _u8(a):
 
 
 def make_params(nx, ny, tau, rho0=1.0, u_max=0.0, outlet_rule=OUT_CONST_RHO, periodic=False,
-                port_scheme=PORTS_REGULARIZED):
+                port_scheme=PORTS_REGULARIZED, guard=False, collision=0, c_smag=0.0):
     return Params(int(nx), int(ny), float(tau), float(rho0), float(u_max), int(outlet_rule),
-                  int(bool(periodic)), int(port_scheme), 0)
+                  int(bool(periodic)), int(port_scheme), int(bool(guard)), int(collision), 0, float(c_smag))
 
 
 def lattice():
@@ -188,6 +194,11 @@ def residual(params, solid, ux, uy, ux_prev, uy_prev):
                               *[_p(_f64(a), ctypes.c_double) for a in (ux, uy, ux_prev, uy_prev)])
 
 
+def simple(params, solid, x, y):
+    """1 if interior fluid cell (x, y) may turn solid under the connectivity guard."""
+    return int(lib().ora_simple(ctypes.byref(params), _p(_u8(solid), ctypes.c_uint8), int(x), int(y)))
+
+
 def mu_of(params):
     """Dynamic viscosity mu = rho0 nu with nu = (tau - 1/2)/3."""
     return params.rho0 * ((params.tau - 0.5) / 3.0)
@@ -225,6 +236,34 @@ def apply(params, solid, f, fluid_idx, solid_idx, reinit=REINIT_WARM):
     assert len(fi) == len(si)
     return lib().ora_apply(ctypes.byref(params), _p(solid, ctypes.c_uint8), _p(f, ctypes.c_double),
                            _p(fi, ctypes.c_int32), _p(si, ctypes.c_int32), len(fi), int(reinit))
+
+
+def run_plan(solve, step, n_swap, max_iter, tol=0.0, patience=3, adapt=False):
+    """The outer loop of Sec. 2.3 with its stopping test (step 5, "the pressure
+    drop tends to extremum") read as: stop after an iteration once
+    |dp_k - dp_(k-1)| <= tol |dp_k| has held on `patience` consecutive
+    iterations (tol <= 0: run max_iter iterations).  With adapt, n_swap is
+    halved (down to 1) after every iteration that raised dp.  The lowest dp
+    (earliest on ties) is the best.
+
+    solve() -> dp of the first solve; step(n_swap) -> dp after one exchange and
+    re-solve.  Returns the history and the decisions."""
+    hist = [solve()]
+    best, calm, stopped = 0, 0, False
+    for k in range(1, max_iter + 1):
+        dp = step(n_swap)
+        hist.append(dp)
+        if dp < hist[best]:
+            best = k
+        if adapt and dp > hist[k - 1]:
+            n_swap = max(1, n_swap // 2)
+        if tol > 0:
+            calm = calm + 1 if abs(dp - hist[k - 1]) <= tol * abs(dp) else 0
+            if calm >= patience:
+                stopped = True
+                break
+    return dict(history=hist, best_iter=best, dp_best=hist[best], stopped=stopped, n_swap_final=n_swap,
+                iterations=len(hist) - 1)
 
 
 class Solver:
@@ -281,4 +320,27 @@ class Solver:
         fluid = self.exchange(fi, si)
         out = self.solve(n_steps)
         out.update(n_swapped=len(fi), fluid_count=fluid, fluid_idx=fi, solid_idx=si)
+        return out
+
+    def _state(self):
+        return (self.solid.copy(), self.f.copy(), self.rho.copy(), self.ux.copy(), self.uy.copy())
+
+    def optimize_run(self, n_steps, max_iter, n_swap, tol=0.0, patience=3, adapt=False, keep_best=False):
+        """run_plan on this solver; with keep_best the solver ends in the state
+        of the best iteration."""
+        saved = {}
+
+        def solve():
+            dp = self.solve(n_steps)["dp"]
+            saved[0] = self._state()
+            return dp
+
+        def step(ns):
+            dp = self.optimize_step(ns, n_steps)["dp"]
+            saved[len(saved)] = self._state()
+            return dp
+
+        out = run_plan(solve, step, n_swap, max_iter, tol, patience, adapt)
+        if keep_best:
+            self.solid, self.f, self.rho, self.ux, self.uy = saved[out["best_iter"]]
         return out

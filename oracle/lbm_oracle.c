@@ -55,6 +55,7 @@ static const double CS2 = 1.0 / 3.0;
 enum { ORA_OUT_CONST_RHO = 0, ORA_OUT_NEUMANN = 1 };
 enum { ORA_PORTS_REGULARIZED = 0, ORA_PORTS_ZOU_HE = 1 };
 enum { ORA_REINIT_WARM = 0, ORA_REINIT_COLD = 1 };
+enum { ORA_COLLIDE_BGK = 0, ORA_COLLIDE_REGULARIZED = 1, ORA_COLLIDE_SMAGORINSKY = 2 };
 enum { ORA_OK = 0, ORA_ERR_ARG = 1, ORA_ERR_GEOMETRY = 2, ORA_ERR_DIVERGED = 5 };
 
 typedef struct {
@@ -68,7 +69,11 @@ typedef struct {
   int32_t port_scheme; /* ORA_PORTS_REGULARIZED or ORA_PORTS_ZOU_HE: how the
                           velocity inlet and the constant-density outlet are
                           imposed                                            */
+  int32_t guard;       /* 1: a fluid cell may turn solid only if it is a
+                          simple cell of the fluid region (see ora_simple)  */
+  int32_t collision;   /* ORA_COLLIDE_*: how the collision of Eq. 1 relaxes */
   int32_t reserved;
+  double c_smag;       /* Smagorinsky constant (ORA_COLLIDE_SMAGORINSKY)     */
 } ora_params;
 
 /* Export the lattice tables so that tests can check them against the
@@ -209,6 +214,61 @@ static void regularize(double* f, double rho, double ux, double uy) {
   }
 }
 
+/* Second moment of the non-equilibrium populations, Pi = sum_i c_i c_i (f_i - f_i^eq). */
+static void pi_neq(const double* f, double rho, double ux, double uy, double* pxx, double* pyy, double* pxy) {
+  *pxx = *pyy = *pxy = 0.0;
+  for (int i = 0; i < 9; ++i) {
+    double fneq = f[i] - ora_feq(i, rho, ux, uy);
+    *pxx += CX[i] * CX[i] * fneq;
+    *pyy += CY[i] * CY[i] * fneq;
+    *pxy += CX[i] * CY[i] * fneq;
+  }
+}
+
+/* Relaxation time of the Smagorinsky model (large-eddy closure; the paper
+ * names LES as a way to higher Reynolds numbers).  The eddy viscosity is
+ * nu_t = (C delta)^2 |S| with delta = 1 and |S| = sqrt(2 S:S); in the lattice
+ * the strain rate follows from the non-equilibrium stress,
+ * S = -Pi / (2 rho c_s^2 tau_eff).  With tau_eff = tau + nu_t / c_s^2 this is a
+ * quadratic in tau_eff:
+ *   tau_eff^2 - tau tau_eff - C^2 sqrt(2 Pi:Pi) / (2 rho c_s^4) = 0,
+ * whose positive root is
+ *   tau_eff = (tau + sqrt(tau^2 + 2 sqrt(2) C^2 sqrt(Pi:Pi) / (rho c_s^4))) / 2. */
+static double smagorinsky_tau(double tau, double c, double rho, double pxx, double pyy, double pxy) {
+  double pp = pxx * pxx + pyy * pyy + 2.0 * pxy * pxy;
+  return 0.5 * (tau + sqrt(tau * tau + 2.0 * sqrt(2.0) * c * c * sqrt(pp) / (rho * CS2 * CS2)));
+}
+
+/* The collision of one cell with moments (rho, ux, uy), in place:
+ *   BGK (Eq. 1):        f_i <- f_i - (f_i - f_i^eq) / tau;
+ *   regularised:        f_i <- f_i^eq + (1 - 1/tau) f_i^(1), where f^(1) is the
+ *                       non-equilibrium part projected on the second-order
+ *                       Hermite tensor, w_i / (2 c_s^4) Q_i : Pi (Latt & Chopard);
+ *   Smagorinsky:        BGK with the local tau_eff of smagorinsky_tau.      */
+static void collide(const ora_params* p, double* f, double rho, double ux, double uy) {
+  if (p->collision == ORA_COLLIDE_REGULARIZED) {
+    double fr[9];
+    for (int i = 0; i < 9; ++i) fr[i] = f[i];
+    regularize(fr, rho, ux, uy);
+    for (int i = 0; i < 9; ++i) {
+      double eq = ora_feq(i, rho, ux, uy);
+      f[i] = eq + (1.0 - 1.0 / p->tau) * (fr[i] - eq);
+    }
+    return;
+  }
+  double tau = p->tau;
+  if (p->collision == ORA_COLLIDE_SMAGORINSKY) {
+    double pxx, pyy, pxy;
+    pi_neq(f, rho, ux, uy, &pxx, &pyy, &pxy);
+    tau = smagorinsky_tau(p->tau, p->c_smag, rho, pxx, pyy, pxy);
+  }
+  for (int i = 0; i < 9; ++i) f[i] = f[i] - (f[i] - ora_feq(i, rho, ux, uy)) / tau;
+}
+
+double ora_smagorinsky_tau(double tau, double c, double rho, double pxx, double pyy, double pxy) {
+  return smagorinsky_tau(tau, c, rho, pxx, pyy, pxy);
+}
+
 /* One time step of Eq. 1 over columns [x_begin, x_end) (the whole lattice when
  * x_begin = 0, x_end = nx): stream (pull, bounce-back), apply the port rules,
  * take the moments (Eq. 2), relax towards f^eq with 1/tau.  fp is the
@@ -305,8 +365,8 @@ void ora_step_columns(const ora_params* p, const uint8_t* solid, const double* u
         jy += CY[i] * f[i];
       }
       double ux = jx / rho, uy = jy / rho;
-      /* Eq. 1: f_i <- f_i - (f_i - f_i^eq) / tau */
-      for (int i = 0; i < 9; ++i) fn[i * n + c] = f[i] - (f[i] - ora_feq(i, rho, ux, uy)) / p->tau;
+      collide(p, f, rho, ux, uy);
+      for (int i = 0; i < 9; ++i) fn[i * n + c] = f[i];
       if (rho_out) { rho_out[c] = rho; ux_out[c] = ux; uy_out[c] = uy; }
     }
   }
@@ -414,6 +474,28 @@ double ora_residual(const ora_params* p, const uint8_t* solid, const double* ux,
  * nu = (tau - 1/2)/3.
  * cand[c] = 1 for an interface fluid cell, 2 for an interface solid cell,
  * 0 otherwise; score[c] holds q or sigma there and 0 elsewhere.              */
+/* Connectivity guard (a reading of Sec. 2.3 step 3, which does not say
+ * whether an exchange may cut the fluid region apart).  Fluid cells connect
+ * through faces (4-neighbourhood), solid cells through faces and corners.
+ * Interior cell (x, y) is "simple" when removing it from the fluid changes
+ * neither count locally: its 4-connectivity number
+ *   N4 = sum over k in {E, N, W, S} of  f_k (1 - f_k+1 f_k+2),
+ * with f the fluid indicators of the eight neighbours taken counter-
+ * clockwise E, NE, N, NW, W, SW, S, SE (and around again), equals 1.
+ * N4 counts the fluid 4-neighbours that stay separated from each other
+ * inside the 3 x 3 block once the cell is gone. */
+int32_t ora_simple(const ora_params* p, const uint8_t* solid, int32_t x, int32_t y) {
+  static const int DX[8] = {1, 1, 0, -1, -1, -1, 0, 1};
+  static const int DY[8] = {0, 1, 1, 1, 0, -1, -1, -1};
+  int f[10];
+  for (int k = 0; k < 8; ++k) f[k] = !solid[(size_t)(y + DY[k]) * p->nx + (x + DX[k])];
+  f[8] = f[0];
+  f[9] = f[1];
+  int n4 = 0;
+  for (int k = 0; k < 8; k += 2) n4 += f[k] * (1 - f[k + 1] * f[k + 2]);
+  return n4 == 1;
+}
+
 void ora_scores(const ora_params* p, const uint8_t* solid, const double* rho, const double* ux,
                 const double* uy, double mu, uint8_t* cand, double* score) {
   int nx = p->nx, ny = p->ny;
@@ -430,7 +512,7 @@ void ora_scores(const ora_params* p, const uint8_t* solid, const double* rho, co
           int i = NB[k];
           if (solid[(size_t)(y + CY[i]) * nx + (x + CX[i])]) touches_wall = 1;
         }
-        if (touches_wall) {
+        if (touches_wall && (!p->guard || ora_simple(p, solid, x, y))) {
           cand[c] = 1;
           double s = ux[c] * ux[c] + uy[c] * uy[c];
           score[c] = 0.5 * rho[c] * s;

@@ -162,3 +162,185 @@ def test_t_junction_optimisation_lowers_pressure_drop(ora):
         out = s.optimize_step(2, cfg["steps"])
         assert out["fluid_count"] == n0
     assert out["dp"] < 0.95 * dp_unchanged
+
+
+# ---- the outer loop's decisions (stopping test, n_swap adaptation, best) ----
+
+def _fake(seq):
+    it = iter(seq)
+    calls = []
+
+    def solve():
+        return next(it)
+
+    def step(ns):
+        calls.append(ns)
+        return next(it)
+    return solve, step, calls
+
+
+def test_run_plan_without_tolerance_runs_every_iteration(ora):
+    seq = [5.0, 4.0, 4.5, 3.0, 3.0, 3.5]
+    solve, step, calls = _fake(seq)
+    out = ora.run_plan(solve, step, n_swap=8, max_iter=5)
+    assert out["history"] == seq and out["iterations"] == 5 and not out["stopped"]
+    assert out["best_iter"] == 3 and out["dp_best"] == 3.0  # earliest of the two equal minima
+    assert calls == [8] * 5 and out["n_swap_final"] == 8
+
+
+def test_run_plan_stops_after_patience_calm_iterations(ora):
+    # relative changes: 0.1, 1e-4, 2e-4, 5e-2, 1e-4, 1e-4, 1e-4 (stop here with patience 3)
+    seq = [1.0, 0.9, 0.90009, 0.90027, 0.95, 0.950095, 0.95019, 0.950285, 0.5]
+    solve, step, calls = _fake(seq)
+    out = ora.run_plan(solve, step, n_swap=4, max_iter=8, tol=1e-3, patience=3)
+    assert out["stopped"] and out["iterations"] == 7 and len(calls) == 7
+    assert out["best_iter"] == 1
+    solve, step, calls = _fake(seq)
+    out = ora.run_plan(solve, step, n_swap=4, max_iter=8, tol=1e-3, patience=4)
+    assert not out["stopped"] and out["iterations"] == 8 and out["best_iter"] == 8
+
+
+def test_run_plan_halves_n_swap_after_a_rise(ora):
+    seq = [10.0, 9.0, 9.5, 8.0, 8.5, 8.6, 8.7, 7.0]
+    solve, step, calls = _fake(seq)
+    out = ora.run_plan(solve, step, n_swap=10, max_iter=7, adapt=True)
+    # rises after iterations 2, 4, 5, 6: 10 -> 5 -> 2 -> 1 -> 1
+    assert calls == [10, 10, 5, 5, 2, 1, 1]
+    assert out["n_swap_final"] == 1 and out["best_iter"] == 7
+
+
+def test_optimize_run_keep_best_restores_the_best_state(ora):
+    cfg = I.config_t_junction()
+    p = ora.make_params(cfg["nx"], cfg["ny"], cfg["tau"], 1.0, cfg["u_max"])
+    ref = ora.Solver(p, cfg["cells"], residual_every=0)
+    states = [None]
+    dps = [ref.solve(200)["dp"]]
+    states[0] = ref.solid.copy()
+    for _ in range(4):
+        dps.append(ref.optimize_step(3, 200)["dp"])
+        states.append(ref.solid.copy())
+    s = ora.Solver(p, cfg["cells"], residual_every=0)
+    out = s.optimize_run(200, 4, 3, keep_best=True)
+    assert out["history"] == dps
+    assert out["best_iter"] == int(np.argmin(dps))
+    assert np.array_equal(s.solid, states[out["best_iter"]])
+    assert int((s.solid == 0).sum()) == int((cfg["cells"] == 0).sum())
+
+
+# ---- connectivity guard (simple cells only may turn solid) ----
+
+def _components(fluid):
+    """Number of 4-connected components of a boolean array (brute force)."""
+    seen = np.zeros_like(fluid, dtype=bool)
+    ny, nx = fluid.shape
+    n = 0
+    for y0 in range(ny):
+        for x0 in range(nx):
+            if not fluid[y0, x0] or seen[y0, x0]:
+                continue
+            n += 1
+            stack = [(y0, x0)]
+            seen[y0, x0] = True
+            while stack:
+                y, x = stack.pop()
+                for dy, dx in ((0, 1), (1, 0), (0, -1), (-1, 0)):
+                    yy, xx = y + dy, x + dx
+                    if 0 <= yy < ny and 0 <= xx < nx and fluid[yy, xx] and not seen[yy, xx]:
+                        seen[yy, xx] = True
+                        stack.append((yy, xx))
+    return n
+
+
+def _solid_components8(solid):
+    """8-connected components of the solid cells (brute force)."""
+    seen = np.zeros_like(solid, dtype=bool)
+    ny, nx = solid.shape
+    n = 0
+    for y0 in range(ny):
+        for x0 in range(nx):
+            if not solid[y0, x0] or seen[y0, x0]:
+                continue
+            n += 1
+            stack = [(y0, x0)]
+            seen[y0, x0] = True
+            while stack:
+                y, x = stack.pop()
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        yy, xx = y + dy, x + dx
+                        if 0 <= yy < ny and 0 <= xx < nx and solid[yy, xx] and not seen[yy, xx]:
+                            seen[yy, xx] = True
+                            stack.append((yy, xx))
+    return n
+
+
+def test_simple_cells_are_exactly_those_whose_removal_keeps_the_local_topology(ora):
+    """Brute force over every 3 x 3 neighbourhood: the centre is simple iff
+    removing it leaves one 4-connected fluid part among its fluid 4-neighbour
+    connections and merges no solid parts -- checked as: the fluid cells of
+    the 3 x 3 block that were 4-connected to the centre stay in one
+    4-component, and the solid 8-components of the block do not change."""
+    p = ora.make_params(3, 3, 0.8, guard=True)
+    for code in range(256):
+        ring = [(code >> k) & 1 for k in range(8)]  # fluid flags E, NE, N, NW, W, SW, S, SE
+        DX = [1, 1, 0, -1, -1, -1, 0, 1]
+        DY = [0, 1, 1, 1, 0, -1, -1, -1]
+        fluid = np.zeros((3, 3), bool)
+        fluid[1, 1] = True
+        for k in range(8):
+            fluid[1 + DY[k], 1 + DX[k]] = bool(ring[k])
+        solid = (~fluid).astype(np.uint8)
+        got = ora.simple(p, solid, 1, 1)
+        after = fluid.copy()
+        after[1, 1] = False
+        # fluid 4-neighbours of the centre must stay 4-connected to one another (within the block)
+        nb4 = [(1 + DY[k], 1 + DX[k]) for k in (0, 2, 4, 6) if ring[k]]
+        lab = np.zeros((3, 3), int)
+        comp = 0
+        for (y, x) in nb4:
+            if lab[y, x]:
+                continue
+            comp += 1
+            stack = [(y, x)]
+            lab[y, x] = comp
+            while stack:
+                cy, cx = stack.pop()
+                for dy, dx in ((0, 1), (1, 0), (0, -1), (-1, 0)):
+                    yy, xx = cy + dy, cx + dx
+                    if 0 <= yy < 3 and 0 <= xx < 3 and after[yy, xx] and not lab[yy, xx]:
+                        lab[yy, xx] = comp
+                        stack.append((yy, xx))
+        keeps_fluid = comp == 1
+        # the removed cell joins the solid: it must touch exactly one 8-component of the block's solid
+        sol = ~fluid
+        sol[1, 1] = False
+        n_before = _solid_components8(sol)
+        sol2 = sol.copy()
+        sol2[1, 1] = True
+        keeps_solid = n_before >= 1 and _solid_components8(sol2) == n_before
+        assert got == int(keeps_fluid and keeps_solid), (code, ring)
+
+
+def test_guarded_choice_never_cuts_a_one_cell_neck(ora):
+    """A channel pinched to a neck one to three cells wide: every fluid cell
+    the guard lets turn solid leaves the number of fluid components as it
+    was."""
+    rng = np.random.default_rng(3)
+    for trial in range(20):
+        nx, ny = 12, 9
+        solid = np.ones((ny, nx), np.uint8)
+        solid[2:7, :] = 0
+        # a random wall bump leaves a neck one to three cells wide
+        xb = int(rng.integers(4, nx - 4))
+        w = int(rng.integers(1, 4))
+        solid[2:7 - w, xb] = 1
+        p = ora.make_params(nx, ny, 0.8, u_max=0.02, guard=True)
+        rho = np.ones((ny, nx))
+        ux = rng.random((ny, nx)) * (solid == 0)
+        uy = rng.random((ny, nx)) * (solid == 0) * 0.1
+        cand, score = ora.scores(p, solid, rho, ux, uy)
+        for c in np.flatnonzero(cand == 1):
+            y, x = divmod(int(c), nx)
+            after = solid.copy()
+            after[y, x] = 1
+            assert _components(after == 0) == _components(solid == 0), (trial, x, y)
