@@ -584,7 +584,9 @@ def main():
                            "ny": cfg["ny"], "fluid_cells": fluid, "n_swap": n_swap,
                            "solves_per_step": iters + 1, "time_steps_per_solve": S,
                            "l2": "flushed between timed steps (256 MB write)",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}",
+                           "step_config": dict(zip(("warps_per_block", "grid", "persistent", "cells_per_thread",
+                                                    "stages"), lat.step_config()))},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
                 "cpu_baseline": cpu,
                 "dense_glups": cfg["nx"] * cfg["ny"] * S * (iters + 1) * args.steps * world / total_s / 1e9,

@@ -79,6 +79,15 @@ typedef enum {
   LBM_REINIT_COLD = 1  /* after an exchange every fluid cell restarts at f^eq(rho0, 0) */
 } lbm_reinit;
 
+typedef enum {
+  LBM_COLLIDE_BGK = 0,         /* single relaxation time, Eq. 1 */
+  LBM_COLLIDE_REGULARIZED = 1, /* BGK applied to the regularised populations: the
+                                  non-equilibrium part is projected on its second
+                                  moment before relaxing (more stable as tau -> 1/2) */
+  LBM_COLLIDE_SMAGORINSKY = 2  /* BGK with a local relaxation time from the
+                                  Smagorinsky eddy viscosity (constant c_smag) */
+} lbm_collision;
+
 typedef struct {
   int32_t nx, ny;         /* lattice size */
   double tau;             /* BGK relaxation time of Eq. 1 (> 1/2); nu = (tau - 1/2)/3 */
@@ -90,7 +99,13 @@ typedef struct {
   int32_t residual_every; /* K: the residual compares u at the last step with u
                              K steps earlier; even, >= 2 (0 disables it) */
   int32_t ports;          /* lbm_port_scheme */
+  int32_t guard;          /* 1: connectivity guard -- a fluid cell may turn solid
+                             only if it is simple: its fluid 4-neighbours stay
+                             connected within its 3 x 3 block without it and it
+                             joins exactly one solid part (4-connectivity number 1) */
+  int32_t collision;      /* lbm_collision */
   int32_t reserved;       /* must be 0 */
+  double c_smag;          /* Smagorinsky constant (LBM_COLLIDE_SMAGORINSKY; >= 0) */
 } lbm_params;
 
 typedef struct {
@@ -171,6 +186,44 @@ lbm_status lbm_reset(lbm_handle h);
 lbm_status lbm_select_swaps(lbm_handle h, const float* drho, const float* ux, const float* uy,
                             int32_t n_swap, int32_t* fluid_idx_out, int32_t* solid_idx_out,
                             int32_t* n_out);
+
+/* ---- the whole optimisation loop ------------------------------------------
+ * Sec. 2.3 run end to end on one handle: a first solve, then up to max_iter
+ * iterations of {exchange, re-solve} (lbm_optimize_step).  The paper stops
+ * when the pressure drop "tends to extremum" without a tolerance; the reading
+ * here: stop after an iteration once |dp_k - dp_(k-1)| <= tol |dp_k| has held
+ * for `patience` consecutive iterations (tol <= 0: run all max_iter).  The
+ * paper fixes neither the number of cells per exchange nor what to keep: with
+ * adapt = 1, n_swap is halved (down to 1) after every iteration that raised
+ * dp; with keep_best = 1, the handle ends in the state (cell map,
+ * populations and fields) of the lowest dp seen.                           */
+typedef struct {
+  int64_t n_steps;   /* time steps of every solve (even, >= 2) */
+  int32_t max_iter;  /* exchange iterations at most (>= 0) */
+  int32_t n_swap;    /* exchanges per iteration at the start (>= 1) */
+  double tol;        /* extremum test tolerance (relative); <= 0 disables it */
+  int32_t patience;  /* consecutive calm iterations that stop the loop (>= 1) */
+  int32_t adapt;     /* 0 or 1 */
+  int32_t keep_best; /* 0 or 1 */
+  int32_t reserved;  /* must be 0 */
+} lbm_opt_plan;
+
+typedef struct {
+  int32_t iterations;   /* exchange iterations run */
+  int32_t best_iter;    /* iteration with the lowest dp (0: the first solve) */
+  int32_t stopped;      /* 1 if the extremum test ended the loop */
+  int32_t n_swap_final; /* n_swap in force at the end */
+  int64_t swapped;      /* cells exchanged over all iterations (each way) */
+  double dp_first;      /* dp of the first solve */
+  double dp_best;       /* lowest dp */
+  double dp_last;       /* dp of the last solve run */
+} lbm_opt_summary;
+
+/* dp_history: host double[max_iter + 1] or NULL; receives dp of the first
+ * solve and of every iteration run (summary.iterations + 1 values).
+ * out: host, caller-owned.  On an error the history up to the failure has
+ * been written and the handle holds the state of the failing call.        */
+lbm_status lbm_optimize(lbm_handle h, const lbm_opt_plan* plan, double* dp_history, lbm_opt_summary* out);
 
 /* Largest lattice (nx * ny cells) accepted by lbm_select_swaps_noalloc;
  * nx and ny are also limited to 4096 each.                              */

@@ -9,6 +9,6 @@ workloads.
 """
 from . import inputs  # noqa: F401
 from .lib import (F32, BF16_SHIFTED, F16_SHIFTED, OUT_CONST_RHO, OUT_NEUMANN, REINIT_WARM,  # noqa: F401
-                  PORTS_REGULARIZED, PORTS_ZOU_HE,
+                  PORTS_REGULARIZED, PORTS_ZOU_HE, COLLIDE_BGK, COLLIDE_REGULARIZED, COLLIDE_SMAGORINSKY,
                   REINIT_COLD, FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_MASK, FIELD_POPS, FIELD_DRHO,
                   Lattice, Batch, Server, LbmError, bytes_per_fluid_update, kernel_launches, load_library)

@@ -86,6 +86,11 @@ lbm_status lbm_optimize_step(lbm_handle h, int32_t n_swap, int64_t n_steps, lbm_
   return engine_optimize(h->e, &n_swap, n_steps, out);
 }
 
+lbm_status lbm_optimize(lbm_handle h, const lbm_opt_plan* plan, double* dp_history, lbm_opt_summary* out) {
+  if (!h || !plan || !out) return fail(LBM_ERR_ARG, "handle, plan or out is NULL");
+  return engine_optimize_loop(h->e, *plan, dp_history, out);
+}
+
 lbm_status lbm_read_fields(lbm_handle h, uint32_t which, void* dst, size_t dst_bytes, int dst_is_device) {
   if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
   (void)dst_is_device;  // unified addressing: cudaMemcpyDefault handles both

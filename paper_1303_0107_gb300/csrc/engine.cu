@@ -307,7 +307,7 @@ lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
 // on the device at once; a fixed-grid engine always takes the device-sized
 // grid, so its captured graphs outlive changes of the member list.
 StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale, int cpt = 1, int stages = 0) {
-  const int bps = stream_collide_blocks_per_sm(E->precision, 0, 0, wpb, cpt, stages);
+  const int bps = stream_collide_blocks_per_sm(E->precision, 0, 0, wpb, cpt, stages, E->models ? 1 : 0);
   const long long cap = (long long)E->sm_count * bps * blocks_per_sm_scale;
   const long long tasks = ((long long)E->L.total_seg_words + cpt - 1) / cpt;
   const long long need = (tasks + wpb - 1) / wpb;
@@ -317,6 +317,7 @@ StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale, int cpt = 1, int s
   c.persistent = 0;
   c.cells_per_thread = cpt;
   c.stages = stages;
+  c.models = E->models ? 1 : 0;
   return c;
 }
 
@@ -329,6 +330,7 @@ StepConfig persistent_shape(Engine* E, int wpb, int cpt = 1) {
   c.persistent = 1;
   c.cells_per_thread = cpt;
   c.stages = 0;
+  c.models = 0;
   return c;
 }
 
@@ -352,10 +354,13 @@ lbm_status autotune(Engine* E) {
     CU(cudaMemcpyAsync(backups[i], E->m[i]->f, bytes, cudaMemcpyDeviceToDevice, E->stream));
   }
   std::vector<StepConfig> cand;
+  // the collision models beyond BGK have one kernel shape: one cell per
+  // thread, register loads, one launch per phase
+  const bool only_plain = E->models;
   for (int cpt : {1, 2})
     for (int wpb : {4, 8, 16})
-      for (int scale : {1, 2}) {
-        if (wpb * 32 > (cpt == 1 ? 512 : 256)) continue;
+      for (int scale : {1, 2, 4}) {
+        if (wpb * 32 > (cpt == 1 ? 512 : 256) || (cpt == 2 && scale == 4) || (only_plain && cpt == 2)) continue;
         StepConfig c = shape(E, wpb, scale, cpt);
         bool dup = false;
         for (auto& d : cand)
@@ -363,9 +368,10 @@ lbm_status autotune(Engine* E) {
                   d.cells_per_thread == c.cells_per_thread);
         if (!dup) cand.push_back(c);
       }
-  for (int stages : {2, 3})
-    for (int wpb : {4, 8}) cand.push_back(shape(E, wpb, 1, 1, stages));
-  if (persistent_enabled())
+  if (!only_plain)
+    for (int stages : {2, 3})
+      for (int wpb : {4, 8}) cand.push_back(shape(E, wpb, 1, 1, stages));
+  if (persistent_enabled() && !only_plain)
     for (int cpt : {1, 2}) {
       StepConfig c = persistent_shape(E, 8, cpt);
       if (c.grid > 0) cand.push_back(c);
@@ -373,17 +379,42 @@ lbm_status autotune(Engine* E) {
   cudaEvent_t a, b;
   CU(cudaEventCreate(&a));
   CU(cudaEventCreate(&b));
-  float best = 1e30f;
-  StepConfig best_cfg = E->step;
+  // Each per-phase candidate runs as a CUDA graph of kTunePairs pairs -- as
+  // the solves do -- so that host launch costs do not favour one shape; the
+  // persistent candidates are one launch anyway.  One untimed pass, then
+  // kTunePasses timed passes over all candidates (slow moments of the device
+  // hit every candidate alike); a candidate's time is its fastest pass.
+  constexpr int kTunePasses = 3, kTunePairs = 32;
+  std::vector<cudaGraphExec_t> tg(cand.size(), nullptr);
   lbm_status st = LBM_OK;
-  for (int rep = 0; rep < 2 && st == LBM_OK; ++rep) {  // first pass warms up
-    for (const StepConfig& c : cand) {
+  for (size_t ci = 0; ci < cand.size() && st == LBM_OK; ++ci) {
+    if (cand[ci].persistent) continue;
+    E->step = cand[ci];
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(E->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      st = fail(LBM_ERR_CUDA, "autotune capture");
+      break;
+    }
+    t_capturing = true;
+    for (int k = 0; k < kTunePairs && st == LBM_OK; ++k) st = launch_pair(E, 0);
+    t_capturing = false;
+    const cudaError_t e = cudaStreamEndCapture(E->stream, &g);
+    if (st == LBM_OK && (e != cudaSuccess || cudaGraphInstantiate(&tg[ci], g, 0) != cudaSuccess))
+      st = fail(LBM_ERR_CUDA, "autotune graph");
+    if (g) cudaGraphDestroy(g);
+  }
+  std::vector<float> t_min(cand.size(), 1e30f);
+  for (int rep = 0; rep <= kTunePasses && st == LBM_OK; ++rep) {
+    for (size_t ci = 0; ci < cand.size() && st == LBM_OK; ++ci) {
+      const StepConfig& c = cand[ci];
       E->step = c;
       cudaEventRecord(a, E->stream);
       if (c.persistent) {
-        st = run_persistent(E, 16);
+        st = run_persistent(E, kTunePairs);
+      } else if (cudaGraphLaunch(tg[ci], E->stream) != cudaSuccess) {
+        st = fail(LBM_ERR_CUDA, "autotune graph launch");
       } else {
-        for (int k = 0; k < 16 && st == LBM_OK; ++k) st = launch_pair(E, 0);
+        count_launches(2 * kTunePairs);
       }
       cudaEventRecord(b, E->stream);
       if (cudaEventSynchronize(b) != cudaSuccess) st = fail(LBM_ERR_CUDA, "autotune timing");
@@ -396,12 +427,18 @@ lbm_status autotune(Engine* E) {
           st = fail(LBM_ERR_CUDA, "autotune barrier flag");
         if (err != 0) st = fail(LBM_ERR_TIMEOUT, "persistent step kernel: a grid barrier wait gave up");
       }
-      if (rep == 1 && ms < best) {
-        best = ms;
-        best_cfg = c;
-      }
+      if (rep > 0) t_min[ci] = std::min(t_min[ci], ms);
     }
   }
+  for (cudaGraphExec_t g : tg)
+    if (g) cudaGraphExecDestroy(g);
+  StepConfig best_cfg = cand[0];
+  float best = 1e30f;
+  for (size_t ci = 0; ci < cand.size(); ++ci)
+    if (t_min[ci] < best) {
+      best = t_min[ci];
+      best_cfg = cand[ci];
+    }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   E->bar_used = false;
@@ -462,6 +499,12 @@ lbm_status check_params(const lbm_params& p) {
   if (p.reinit != LBM_REINIT_WARM && p.reinit != LBM_REINIT_COLD) return fail(LBM_ERR_ARG, "reinit");
   if (p.residual_every < 0 || (p.residual_every % 2) != 0) return fail(LBM_ERR_ARG, "residual_every must be even");
   if (p.ports != LBM_PORTS_REGULARIZED && p.ports != LBM_PORTS_ZOU_HE) return fail(LBM_ERR_ARG, "ports");
+  if (p.guard != 0 && p.guard != 1) return fail(LBM_ERR_ARG, "guard must be 0 or 1");
+  if (p.collision != LBM_COLLIDE_BGK && p.collision != LBM_COLLIDE_REGULARIZED &&
+      p.collision != LBM_COLLIDE_SMAGORINSKY)
+    return fail(LBM_ERR_ARG, "collision");
+  if (p.reserved != 0) return fail(LBM_ERR_ARG, "reserved must be 0");
+  if (!std::isfinite(p.c_smag) || p.c_smag < 0) return fail(LBM_ERR_ARG, "c_smag must be finite and >= 0");
   return LBM_OK;
 }
 
@@ -556,6 +599,9 @@ lbm_status member_create(const lbm_params& p, const uint8_t* cells, cudaStream_t
   v.outlet_rule = p.outlet;
   v.port_scheme = p.ports;
   v.n_outlets = (int)m->out_start.size();
+  v.guard = p.guard;
+  v.collision = p.collision;
+  v.c_smag = (float)p.c_smag;
   *out = m;
   return LBM_OK;
 }
@@ -602,7 +648,8 @@ Engine::~Engine() {
   if (own_members)
     for (Member* x : m) delete x;
   for (GrowBuf* b : {&L.views, &L.word_off, &L.seg_word_off, &XL.views, &XL.word_off, &XL.seg_word_off, &segs,
-                     &n_segs, &seg_scratch, &partials, &result, &fluid_dev, &n_swap_dev, &dense_f, &oc_buf, &bar})
+                     &n_segs, &seg_scratch, &partials, &result, &fluid_dev, &n_swap_dev, &dense_f, &oc_buf, &bar,
+                     &best})
     b->release();
   if (h_bar_error) cudaFreeHost(h_bar_error);
   if (h_result) cudaFreeHost(h_result);
@@ -661,8 +708,18 @@ lbm_status rebuild_worklist(Engine* E) {
 }
 
 lbm_status engine_set_members(Engine* E, const std::vector<Member*>& members) {
-  for (Member* mb : members)
+  bool models = false;
+  for (Member* mb : members) {
     if (mb->p.precision != E->precision) return fail(LBM_ERR_ARG, "all lattices of a set share one precision");
+    models |= mb->p.collision != LBM_COLLIDE_BGK;
+  }
+  if (models != E->models) {  // a different kernel build: the tuned shape and graphs no longer apply
+    E->models = models;
+    E->tuned = false;
+    E->step.cells_per_thread = 1;
+    E->step.stages = 0;
+    E->step.persistent = 0;
+  }
   E->m = members;
   const size_t n = members.size();
   lbm_status st = layout_build(E->L, E->m, E->stream);
@@ -893,6 +950,93 @@ lbm_status engine_optimize(Engine* E, const int32_t* n_swap, int64_t n_steps, lb
   return LBM_OK;
 }
 
+namespace {
+
+// A member's state: populations, current mask and the moment fields of the
+// last step (drho, ux, uy: the first three field planes of the slab).
+struct StateCopy {
+  size_t f, mask, fields;
+};
+
+StateCopy state_sizes(const Member* m) {
+  return {9 * m->plane * storage_bytes(m->p.precision), m->mask_bytes, 3 * align_up(m->plane * 4)};
+}
+
+lbm_status save_state(Engine* E, const Member* m) {
+  const StateCopy z = state_sizes(m);
+  CU(E->best.reserve(z.f + z.mask + z.fields));
+  char* b = static_cast<char*>(E->best.p);
+  CU(cudaMemcpyAsync(b, m->f, z.f, cudaMemcpyDeviceToDevice, E->stream));
+  CU(cudaMemcpyAsync(b + z.f, m->mask_base, z.mask, cudaMemcpyDeviceToDevice, E->stream));
+  CU(cudaMemcpyAsync(b + z.f + z.mask, m->drho, z.fields, cudaMemcpyDeviceToDevice, E->stream));
+  return LBM_OK;
+}
+
+lbm_status restore_state(Engine* E, Member* m) {
+  const StateCopy z = state_sizes(m);
+  const char* b = static_cast<const char*>(E->best.p);
+  CU(cudaMemcpyAsync(m->f, b, z.f, cudaMemcpyDeviceToDevice, E->stream));
+  CU(cudaMemcpyAsync(m->mask_base, b + z.f, z.mask, cudaMemcpyDeviceToDevice, E->stream));
+  CU(cudaMemcpyAsync(m->drho, b + z.f + z.mask, z.fields, cudaMemcpyDeviceToDevice, E->stream));
+  lbm_status st = rebuild_worklist(E);
+  if (st != LBM_OK) return st;
+  CU(cudaMemcpyAsync(E->h_count, E->fluid_dev.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, E->stream));
+  CU(cudaStreamSynchronize(E->stream));
+  m->fluid_cells = (int64_t)E->h_count[0];
+  return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status engine_optimize_loop(Engine* E, const lbm_opt_plan& P, double* hist, lbm_opt_summary* out) {
+  if (E->n() != 1) return fail(LBM_ERR_ARG, "the optimisation loop runs on a single lattice");
+  if (P.n_steps < 2 || (P.n_steps % 2) != 0 || P.max_iter < 0 || P.n_swap < 1 || P.patience < 1 ||
+      (P.adapt != 0 && P.adapt != 1) || (P.keep_best != 0 && P.keep_best != 1) || P.reserved != 0 ||
+      !std::isfinite(P.tol))
+    return fail(LBM_ERR_ARG, "plan: n_steps even >= 2, max_iter >= 0, n_swap >= 1, patience >= 1, flags 0/1");
+  std::memset(out, 0, sizeof(*out));
+  Member* m = E->m[0];
+  lbm_solve_result r;
+  lbm_status st = engine_solve(E, P.n_steps, &r);
+  if (st != LBM_OK) return st;
+  std::vector<double> h{r.dp};
+  if (hist) hist[0] = r.dp;
+  int best = 0, calm = 0;
+  int32_t n_swap = P.n_swap;
+  if (P.keep_best && (st = save_state(E, m)) != LBM_OK) return st;
+  for (int k = 1; k <= P.max_iter; ++k) {
+    lbm_opt_result o;
+    out->iterations = k - 1;
+    out->n_swap_final = n_swap;
+    st = engine_optimize(E, &n_swap, P.n_steps, &o);
+    if (st != LBM_OK) return st;
+    out->swapped += o.n_swapped;
+    const double dp = o.solve.dp;
+    h.push_back(dp);
+    if (hist) hist[k] = dp;
+    if (dp < h[best]) {
+      best = k;
+      if (P.keep_best && (st = save_state(E, m)) != LBM_OK) return st;
+    }
+    if (P.adapt && dp > h[k - 1]) n_swap = std::max(1, n_swap / 2);
+    if (P.tol > 0.0) {
+      calm = std::fabs(dp - h[k - 1]) <= P.tol * std::fabs(dp) ? calm + 1 : 0;
+      if (calm >= P.patience) {
+        out->stopped = 1;
+        break;
+      }
+    }
+  }
+  out->iterations = (int32_t)h.size() - 1;
+  out->n_swap_final = n_swap;
+  out->best_iter = best;
+  out->dp_first = h.front();
+  out->dp_best = h[best];
+  out->dp_last = h.back();
+  if (P.keep_best && best != out->iterations && (st = restore_state(E, m)) != LBM_OK) return st;
+  return LBM_OK;
+}
+
 lbm_status engine_read(Engine* E, int i, uint32_t which, void* dst, size_t dst_bytes) {
   if (i < 0 || i >= E->n()) return fail(LBM_ERR_ARG, "member out of range");
   if (!dst) return fail(LBM_ERR_ARG, "dst is NULL");
@@ -955,6 +1099,8 @@ lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t pe
   if (cells_per_thread == 2 && warps_per_block == 16)
     return fail(LBM_ERR_ARG, "two cells per thread take 4 or 8 warps per block");
   if (persistent && warps_per_block == 4) return fail(LBM_ERR_ARG, "the persistent kernel takes 8 or 16 warps per block");
+  if (E->models && (persistent || cells_per_thread != 1 || stages != 0))
+    return fail(LBM_ERR_ARG, "lattices with a collision other than BGK take the plain launch shape");
   StepConfig c = persistent ? persistent_shape(E, warps_per_block, cells_per_thread)
                             : shape(E, warps_per_block, 1, cells_per_thread, stages);
   if (c.grid < 1) return fail(LBM_ERR_CUDA, "no resident block for the persistent kernel");

@@ -88,6 +88,7 @@ struct Engine {
   SetLayout XL;  // members of the next exchange (server only)
   GrowBuf segs, n_segs, seg_scratch, partials, result, fluid_dev, n_swap_dev, dense_f, bar;
   GrowBuf oc_buf;  // exchange scratch, carved into `oc`
+  GrowBuf best;    // saved state of the best iteration (lbm_optimize with keep_best)
   OcScratch oc{};
   size_t pinned_n = 0;
   double* h_result = nullptr;             // pinned [n * kResultDoubles]
@@ -99,7 +100,8 @@ struct Engine {
 
   cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};  // views, segs, n_segs, shape
-  StepConfig step{kStepWarps, 1, 0, 1, 0};
+  StepConfig step{kStepWarps, 1, 0, 1, 0, 0};
+  bool models = false;  // some member uses a collision other than BGK
   bool tuned = false;
   cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
   double step_ms = 0.0;
@@ -136,6 +138,9 @@ void account_steps(Engine* E, int64_t n_steps);
 
 lbm_status engine_solve(Engine* E, int64_t n_steps, lbm_solve_result* out);
 lbm_status engine_optimize(Engine* E, const int32_t* n_swap, int64_t n_steps, lbm_opt_result* out);
+// The loop of Sec. 2.3 with the stopping test, n_swap adaptation and
+// best-state keeping of lbm_opt_plan (engines of one member).
+lbm_status engine_optimize_loop(Engine* E, const lbm_opt_plan& plan, double* history, lbm_opt_summary* out);
 lbm_status engine_read(Engine* E, int i, uint32_t which, void* dst, size_t dst_bytes);
 lbm_status engine_step_config(Engine* E, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
                               int32_t* cells_per_thread, int32_t* stages);

@@ -66,6 +66,9 @@ struct alignas(16) LatticeView {
   int sel_off;             // start of this lattice's picks in the shared pick arrays
   int word_off;            // start of this lattice's words in the concatenated word space
   int seg_word_off;        // start of its interior-row words (rows 1..ny-2)
+  int guard;               // connectivity guard on fluid candidates (lbm_params.guard)
+  int collision;           // lbm_collision
+  float c_smag;            // Smagorinsky constant
 };
 
 // A row segment: lattice index and (y << 12) | w (w < 4096, so nx <= 131072).
@@ -105,6 +108,8 @@ struct StepConfig {
   int cells_per_thread; // 1 or 2: row segments per warp task (2: at most 8 warps per block)
   int stages;           // 0: populations loaded into registers; 2 or 3: staged through shared
                         //    memory that many segments ahead (one cell per thread, per-phase launches)
+  int models;           // 1: kernels with the collision models beyond BGK (one cell per thread,
+                        //    register loads, per-phase launches)
 };
 // Grid barrier state of the persistent kernel (device memory, 16 bytes).
 struct StepBarrier {
@@ -117,7 +122,7 @@ cudaError_t launch_stream_collide(int precision, int phase, int moments, const L
                                   const SegRef* segs, const int* n_segs, StepConfig cfg,
                                   cudaStream_t stream);
 int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int cells_per_thread,
-                                 int stages);
+                                 int stages, int models);
 // n_pairs time-step pairs (phase A then B, no moments) in one cooperative
 // launch with a grid barrier between phases; sc.grid must not exceed
 // stream_collide_persistent_grid (every block resident at once), and

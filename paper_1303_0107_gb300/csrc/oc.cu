@@ -43,8 +43,27 @@ __device__ __forceinline__ uint32_t region_bits(int w, int nx) {
   return m;
 }
 
+// Connectivity guard: bits of the cells whose 4-connectivity number is 1,
+//   N4 = sum over k in {E, N, W, S} of f_k (1 - f_k+1 f_k+2),
+// f the fluid flags of the eight neighbours counter-clockwise from E -- the
+// fluid cells that may turn solid without separating their fluid
+// 4-neighbours within the 3 x 3 block (the same rule as the oracle's).
+__device__ __forceinline__ uint32_t simple_bits(const uint32_t* row, int ms, int w, uint32_t e, uint32_t wb,
+                                                uint32_t n, uint32_t s) {
+  const uint32_t* rn = row + ms;
+  const uint32_t* rs = row - ms;
+  const uint32_t ne = __funnelshift_r(rn[w], rn[w + 1], 1), nw = __funnelshift_l(rn[w - 1], rn[w], 1);
+  const uint32_t se = __funnelshift_r(rs[w], rs[w + 1], 1), sw = __funnelshift_l(rs[w - 1], rs[w], 1);
+  // fluid flags (mask bit set = solid)
+  const uint32_t fE = ~e, fNE = ~ne, fN = ~n, fNW = ~nw, fW = ~wb, fSW = ~sw, fS = ~s, fSE = ~se;
+  const uint32_t t1 = fE & ~(fNE & fN), t3 = fN & ~(fNW & fW), t5 = fW & ~(fSW & fS), t7 = fS & ~(fSE & fE);
+  const uint32_t any = t1 | t3 | t5 | t7;
+  const uint32_t two = (t1 & t3) | (t5 & t7) | ((t1 | t3) & (t5 | t7));
+  return any & ~two;
+}
+
 __device__ __forceinline__ WordMasks word_masks(const uint32_t* __restrict__ mask, int nx, int ny,
-                                                int wpr, int y, int w) {
+                                                int wpr, int y, int w, int guard) {
   WordMasks r{0, 0, 0, 0, 0, 0};
   if (y < 1 || y > ny - 2) return r;
   const int ms = mask_stride(wpr);
@@ -57,6 +76,7 @@ __device__ __forceinline__ WordMasks word_masks(const uint32_t* __restrict__ mas
   r.s = row[w - ms];
   const uint32_t reg = region_bits(w, nx);
   r.fluid_cand = ~mc & (r.e | r.w | r.n | r.s) & reg;
+  if (guard) r.fluid_cand &= simple_bits(row, ms, w, r.e, r.w, r.n, r.s);
   r.solid_cand = mc & (~r.e | ~r.w | ~r.n | ~r.s) & reg;
   return r;
 }
@@ -79,7 +99,7 @@ __global__ void k_oc_count(const LatticeView* __restrict__ views, const int* __r
   int l, y, w;
   word_of(views, word_off, n, i, l, y, w);
   const LatticeView& L = views[l];
-  const WordMasks m = word_masks(L.mask, L.nx, L.ny, L.wpr, y, w);
+  const WordMasks m = word_masks(L.mask, L.nx, L.ny, L.wpr, y, w, L.guard);
   cnt_f[i] = __popc(m.fluid_cand);
   cnt_s[i] = __popc(m.solid_cand);
 }
@@ -103,7 +123,7 @@ __global__ void k_oc_emit(const LatticeView* __restrict__ views, const int* __re
   const LatticeView* L = views + l;
   const int nx = L->nx, pitch = L->pitch;
   const double rho0 = L->rho0d, mu = L->mu;
-  const WordMasks m = word_masks(L->mask, nx, L->ny, L->wpr, y, w);
+  const WordMasks m = word_masks(L->mask, nx, L->ny, L->wpr, y, w, L->guard);
   int of = off_f[i], os = off_s[i];
   bool bad = false;
   uint32_t fc = m.fluid_cand;

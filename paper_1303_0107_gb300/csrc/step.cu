@@ -88,6 +88,17 @@ __device__ __forceinline__ void relax_pair(float& gi, float& go, float cu, float
   go += omega * (eo - go);
 }
 
+// BGK conserves mass and momentum; rounded FP32 relaxation does not quite,
+// and the drift dominates the FP32 error over thousands of steps.  Close
+// both exactly: g1 and g2 carry the momentum balance, the rest population
+// the mass balance (an identity in exact arithmetic; so for every collision
+// model here, which all conserve both).
+__device__ __forceinline__ void close_moments(float (&g)[9], float drho, float jx, float jy) {
+  g[1] = jx + g[3] - ((g[5] - g[7]) + (g[8] - g[6]));
+  g[2] = jy + g[4] - ((g[5] - g[7]) + (g[6] - g[8]));
+  g[0] = drho - (((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
+}
+
 // Moments (Eq. 2) and BGK relaxation (Eq. 1) of one cell, in place.
 __device__ __forceinline__ void bgk(float (&g)[9], float rho0, float omega, float& drho, float& ux,
                                     float& uy) {
@@ -103,13 +114,7 @@ __device__ __forceinline__ void bgk(float (&g)[9], float rho0, float omega, floa
   relax_pair(g[2], g[4], uy, kW1, rho, t0, omega);
   relax_pair(g[5], g[7], ux + uy, kW5, rho, t0, omega);
   relax_pair(g[8], g[6], ux - uy, kW5, rho, t0, omega);
-  // BGK conserves mass and momentum; rounded FP32 relaxation does not quite,
-  // and the drift dominates the FP32 error over thousands of steps.  Close
-  // both exactly: g1 and g2 carry the momentum balance, the rest population
-  // the mass balance (an identity in exact arithmetic).
-  g[1] = jx + g[3] - ((g[5] - g[7]) + (g[8] - g[6]));
-  g[2] = jy + g[4] - ((g[5] - g[7]) + (g[6] - g[8]));
-  g[0] = drho - (((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
+  close_moments(g, drho, jx, jy);
 }
 
 // Shifted equilibria of all nine directions for (rho0 + drho, ux, uy).
@@ -156,6 +161,49 @@ __device__ __forceinline__ void regularize(float (&g)[9], const float (&e)[9]) {
   g[7] = e[7] + dp;
   g[6] = e[6] + dm;
   g[8] = e[8] + dm;
+}
+
+// Collision beyond BGK, of one cell in place (moments as in bgk()):
+//   regularised: g_i <- g^eq_i + (1 - omega) [w_i/(2 c_s^4) Q_i : Pi], the
+//                non-equilibrium part projected on its second moment Pi before
+//                relaxing (regularize() builds g^eq + that projection);
+//   Smagorinsky: BGK with the local relaxation time
+//                tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2 |Pi| / rho)) / 2,
+//                |Pi| = sqrt(Pi:Pi): the positive root of
+//                tau_eff^2 - tau tau_eff = C^2 sqrt(2 Pi:Pi) / (2 rho c_s^4),
+//                i.e. nu_t = C^2 |S| with the strain rate S = -Pi / (2 rho c_s^2 tau_eff).
+__device__ __forceinline__ void collide_other(float (&g)[9], float rho0, float omega, int model, float c_smag,
+                                           float& drho, float& ux, float& uy) {
+  drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+  const float rho = rho0 + drho;
+  const float jx = (g[1] - g[3]) + (g[5] - g[7]) + (g[8] - g[6]);
+  const float jy = (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
+  const float inv = 1.0f / rho;
+  ux = jx * inv;
+  uy = jy * inv;
+  float e[9];
+  shifted_equilibria(e, rho0, drho, ux, uy);
+  if (model == LBM_COLLIDE_REGULARIZED) {
+    regularize(g, e);
+    const float keep = 1.0f - omega;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = e[i] + keep * (g[i] - e[i]);
+  } else {
+    float n[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) n[i] = g[i] - e[i];
+    const float dsum = (n[5] + n[6]) + (n[7] + n[8]);
+    const float pxx = (n[1] + n[3]) + dsum;
+    const float pyy = (n[2] + n[4]) + dsum;
+    const float pxy = (n[5] + n[7]) - (n[6] + n[8]);
+    const float pp = pxx * pxx + pyy * pyy + 2.0f * pxy * pxy;
+    const float tau = 1.0f / omega;
+    const float tau_eff = 0.5f * (tau + sqrtf(tau * tau + 18.0f * 1.41421356f * c_smag * c_smag * sqrtf(pp) / rho));
+    const float w = 1.0f / tau_eff;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] += w * (e[i] - g[i]);
+  }
+  close_moments(g, drho, jx, jy);
 }
 
 // Inlet (x = 0), imposed velocity (u, 0).  Density from mass and x-momentum of
@@ -229,6 +277,8 @@ struct SegCtx {
   int y, c, pitch, pl;
   unsigned nb;  // solid flags of the 8 neighbours (phase A)
   bool fluid, inlet, outlet;
+  float rho0, omega;
+  int rule;      // outlet rule
   long long fe;  // population elements (bounds-checked builds)
 };
 
@@ -250,6 +300,9 @@ __device__ __forceinline__ void seg_prologue(const LatticeView* __restrict__ vie
   s.pitch = L->pitch;
   s.pl = (int)L->plane;  // 32-bit element offsets: lattices are limited to 9 * plane < 2^31
   s.fe = L->f_elems;
+  s.rho0 = L->rho0;
+  s.omega = L->omega;
+  s.rule = L->outlet_rule;
   s.nb = 0;
   if (!valid) {
     s.y = 0;
@@ -326,11 +379,11 @@ __device__ __forceinline__ void seg_load(const SegCtx<T>& s, float (&g)[9]) {
 
 // Boundary rules, collision and stores of the lane's cell.  Every lane of the
 // warp calls it (the zero-gradient outlet shuffles across lanes).
-template <class T, int PHASE, int MOM>
+template <class T, int PHASE, int MOM, int MODELS>
 __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
   using P = Pop<T>;
   const LatticeView* __restrict__ L = s.L;
-  const int rule = L->outlet_rule;
+  const int rule = s.rule;
   if (rule == LBM_OUT_NEUMANN) {
     // zero-gradient outlet: the unknown g3, g6, g7 of cell (nx-1, y) are the
     // streamed g3, g6, g7 of cell (nx-2, y), held by the lane to the left
@@ -345,14 +398,17 @@ __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
     }
   }
   if (!s.fluid) return;
-  const float rho0 = L->rho0;
+  const float rho0 = s.rho0;
   if (s.inlet) {
     inlet_rule(g, L->u_in[s.y], rho0, L->port_scheme);
   } else if (s.outlet && rule == LBM_OUT_CONST_RHO) {
     outlet_rule(g, rho0, L->port_scheme);
   }
   float drho, ux, uy;
-  bgk(g, rho0, L->omega, drho, ux, uy);
+  if (MODELS && L->collision != LBM_COLLIDE_BGK)  // kernels built for BGK only skip this branch
+    collide_other(g, rho0, s.omega, L->collision, L->c_smag, drho, ux, uy);
+  else
+    bgk(g, rho0, s.omega, drho, ux, uy);
 
   T* __restrict__ F = s.F;
   const int c = s.c, pl = s.pl, pitch = s.pitch;
@@ -384,29 +440,33 @@ __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
 
 // One phase on CPT consecutive segments of the list: their loads are all
 // issued before the first cell is updated (more bytes in flight per thread).
-template <class T, int PHASE, int MOM, int CPT, bool CG>
+template <class T, int PHASE, int MOM, int CPT, bool CG, int MODELS = 0>
 __device__ __forceinline__ void phase_task(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
-                                           int nseg, int task, int lane, bool pdl_wait) {
+                                           int nseg, int task, int lane, bool& waited) {
   SegCtx<T> s[CPT];
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
     const int idx = task * CPT + k;
-    const bool valid = idx < nseg;
+    const bool valid = CPT == 1 || idx < nseg;  // one segment per task: task < nseg already
     seg_prologue<T, PHASE>(views, segs[valid ? idx : 0], valid, lane, s[k]);
   }
-  // populations of the previous step are final from here on
-  if (pdl_wait) asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (!waited) {  // warp-uniform: populations of the previous step are final from here on
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    waited = true;
+  }
   float g[CPT][9];
 #pragma unroll
   for (int k = 0; k < CPT; ++k) seg_load<T, PHASE, CG>(s[k], g[k]);
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) seg_update<T, PHASE, MOM>(s[k], g[k]);
+  for (int k = 0; k < CPT; ++k) seg_update<T, PHASE, MOM, MODELS>(s[k], g[k]);
 }
 
 // One phase of one time step over the whole segment list.  Launched as a
 // programmatic dependent of the previous step: descriptors, segments and
 // masks are read before waiting for it, populations after.
-template <class T, int PHASE, int MOM, int CPT>
+// MODELS: 1 if some lattice of the set uses a collision other than BGK (a
+// separate build, so that the BGK kernels keep their register budget).
+template <class T, int PHASE, int MOM, int CPT, int MODELS>
 __global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
     k_stream_collide(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
                      const int* __restrict__ n_segs) {
@@ -418,11 +478,12 @@ __global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
   const int ntask = (nseg + CPT - 1) / CPT;
   const int wpb = blockDim.x >> 5;
   const int stride = gridDim.x * wpb;
+  bool waited = false;
   for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntask; t += stride)
-    phase_task<T, PHASE, MOM, CPT, false>(views, segs, nseg, t, lane, true);
-  // every thread waits at least once, so this grid completes only after the
-  // previous one (the next step relies on that)
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+    phase_task<T, PHASE, MOM, CPT, false, MODELS>(views, segs, nseg, t, lane, waited);
+  // every thread waits once, so this grid completes only after the previous
+  // one (the next step relies on that)
+  if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 
@@ -509,6 +570,9 @@ __device__ __forceinline__ void stage_consume(const LatticeView* __restrict__ vi
   s.pitch = L->pitch;
   s.pl = (int)L->plane;
   s.fe = L->f_elems;
+  s.rho0 = L->rho0;
+  s.omega = L->omega;
+  s.rule = L->outlet_rule;
   s.c = (int)buf[9 * 32 + lane];
   s.nb = fl & 0xffu;
   s.fluid = (fl >> 8) & 1u;
@@ -521,7 +585,7 @@ __device__ __forceinline__ void stage_consume(const LatticeView* __restrict__ vi
     const int off = s.fluid ? src_off<PHASE>(i, s.c, s.pitch, s.pl, s.nb, s.inlet, s.outlet) : -1;
     g[i] = off < 0 ? 0.0f : P::from_word(buf[i * 32 + lane], off & 1);
   }
-  seg_update<T, PHASE, MOM>(s, g);
+  seg_update<T, PHASE, MOM, 0>(s, g);
 }
 
 template <int NS>
@@ -609,20 +673,21 @@ __global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
   const int stride = gridDim.x * wpb;
   const int first = blockIdx.x * wpb + (threadIdx.x >> 5);
   unsigned target = 0;
+  bool waited = true;  // a cooperative launch follows the stream order: nothing to wait for
   for (int p = 0; p < n_pairs; ++p) {
-    for (int t = first; t < ntask; t += stride) phase_task<T, 0, 0, CPT, true>(views, segs, nseg, t, lane, false);
+    for (int t = first; t < ntask; t += stride) phase_task<T, 0, 0, CPT, true>(views, segs, nseg, t, lane, waited);
     if (!grid_barrier(bar, target)) return;
-    for (int t = first; t < ntask; t += stride) phase_task<T, 1, 0, CPT, true>(views, segs, nseg, t, lane, false);
+    for (int t = first; t < ntask; t += stride) phase_task<T, 1, 0, CPT, true>(views, segs, nseg, t, lane, waited);
     if (p + 1 < n_pairs && !grid_barrier(bar, target)) return;
   }
 }
 
-template <class T, int CPT>
+template <class T, int CPT, int MODELS = 0>
 void* pick(int phase, int moments) {
-  if (phase == 0) return (void*)k_stream_collide<T, 0, 0, CPT>;
-  if (moments == 1) return (void*)k_stream_collide<T, 1, 1, CPT>;
-  if (moments == 2) return (void*)k_stream_collide<T, 1, 2, CPT>;
-  return (void*)k_stream_collide<T, 1, 0, CPT>;
+  if (phase == 0) return (void*)k_stream_collide<T, 0, 0, CPT, MODELS>;
+  if (moments == 1) return (void*)k_stream_collide<T, 1, 1, CPT, MODELS>;
+  if (moments == 2) return (void*)k_stream_collide<T, 1, 2, CPT, MODELS>;
+  return (void*)k_stream_collide<T, 1, 0, CPT, MODELS>;
 }
 
 template <class T, int NS>
@@ -634,18 +699,19 @@ void* pick_staged(int phase, int moments) {
 }
 
 template <class T>
-void* pick_cpt(int phase, int moments, int cpt, int stages) {
+void* pick_cpt(int phase, int moments, int cpt, int stages, int models) {
+  if (models) return cpt == 1 && stages == 0 ? pick<T, 1, 1>(phase, moments) : nullptr;
   if (stages == 2) return cpt == 1 ? pick_staged<T, 2>(phase, moments) : nullptr;
   if (stages == 3) return cpt == 1 ? pick_staged<T, 3>(phase, moments) : nullptr;
   if (stages != 0) return nullptr;
   return cpt == 1 ? pick<T, 1>(phase, moments) : cpt == 2 ? pick<T, 2>(phase, moments) : nullptr;
 }
 
-void* kernel_for(int precision, int phase, int moments, int cpt, int stages) {
+void* kernel_for(int precision, int phase, int moments, int cpt, int stages, int models) {
   switch (precision) {
-    case LBM_F32: return pick_cpt<float>(phase, moments, cpt, stages);
-    case LBM_BF16_SHIFTED: return pick_cpt<__nv_bfloat16>(phase, moments, cpt, stages);
-    case LBM_F16_SHIFTED: return pick_cpt<__half>(phase, moments, cpt, stages);
+    case LBM_F32: return pick_cpt<float>(phase, moments, cpt, stages, models);
+    case LBM_BF16_SHIFTED: return pick_cpt<__nv_bfloat16>(phase, moments, cpt, stages, models);
+    case LBM_F16_SHIFTED: return pick_cpt<__half>(phase, moments, cpt, stages, models);
     default: return nullptr;
   }
 }
@@ -676,7 +742,8 @@ void* persistent_kernel_for(int precision, int cpt) {
 bool shape_ok(const StepConfig& sc) {
   return (sc.cells_per_thread == 1 || sc.cells_per_thread == 2) && sc.warps_per_block >= 1 &&
          sc.warps_per_block * 32 <= max_step_threads(sc.cells_per_thread) && sc.grid >= 1 &&
-         (sc.stages == 0 || ((sc.stages == 2 || sc.stages == 3) && sc.cells_per_thread == 1 && !sc.persistent));
+         (sc.stages == 0 || ((sc.stages == 2 || sc.stages == 3) && sc.cells_per_thread == 1 && !sc.persistent)) &&
+         (!sc.models || (sc.cells_per_thread == 1 && sc.stages == 0 && !sc.persistent));
 }
 
 }  // namespace
@@ -684,7 +751,7 @@ bool shape_ok(const StepConfig& sc) {
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
                                   const SegRef* segs, const int* n_segs, StepConfig sc,
                                   cudaStream_t stream) {
-  void* k = kernel_for(precision, phase, moments, sc.cells_per_thread, sc.stages);
+  void* k = kernel_for(precision, phase, moments, sc.cells_per_thread, sc.stages, sc.models);
   if (!k || !shape_ok(sc)) return cudaErrorInvalidValue;
   void* args[] = {(void*)&views, (void*)&segs, (void*)&n_segs};
   cudaLaunchAttribute attr[1];
@@ -716,7 +783,7 @@ cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* v
                                              const int* n_segs, int n_pairs, StepConfig sc, StepBarrier* bar,
                                              cudaStream_t stream) {
   void* k = persistent_kernel_for(precision, sc.cells_per_thread);
-  if (!k || !shape_ok(sc) || n_pairs < 1 ||
+  if (!k || !shape_ok(sc) || sc.models || n_pairs < 1 ||
       sc.grid > stream_collide_persistent_grid(precision, sc.warps_per_block, sc.cells_per_thread) ||
       2ull * (unsigned long long)n_pairs * (unsigned long long)sc.grid >= (1ull << 32))
     return cudaErrorInvalidValue;
@@ -740,9 +807,9 @@ cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* v
 }
 
 int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int cells_per_thread,
-                                 int stages) {
-  void* k = kernel_for(precision, phase, moments, cells_per_thread, stages);
-  StepConfig sc{warps_per_block, 1, 0, cells_per_thread, stages};
+                                 int stages, int models) {
+  void* k = kernel_for(precision, phase, moments, cells_per_thread, stages, models);
+  StepConfig sc{warps_per_block, 1, 0, cells_per_thread, stages, models};
   int n = 0;
   if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, launch_smem(k, sc)) !=
                 cudaSuccess)

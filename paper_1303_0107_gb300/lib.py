@@ -15,6 +15,7 @@ import os
 from .build import LIB, LIB_CHECKED
 
 F32, BF16_SHIFTED, F16_SHIFTED = 0, 1, 2
+COLLIDE_BGK, COLLIDE_REGULARIZED, COLLIDE_SMAGORINSKY = 0, 1, 2
 OUT_CONST_RHO, OUT_NEUMANN = 0, 1
 PORTS_REGULARIZED, PORTS_ZOU_HE = 0, 1
 REINIT_WARM, REINIT_COLD = 0, 1
@@ -35,7 +36,15 @@ class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("tau", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("u_max", ctypes.c_double), ("outlet", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("reinit", ctypes.c_int32),
-                ("residual_every", ctypes.c_int32), ("ports", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("residual_every", ctypes.c_int32), ("ports", ctypes.c_int32), ("guard", ctypes.c_int32),
+                ("collision", ctypes.c_int32), ("reserved", ctypes.c_int32), ("c_smag", ctypes.c_double)]
+
+
+def make_params(nx, ny, tau, u_max, rho0=1.0, outlet=0, precision=0, reinit=0, residual_every=0, ports=0,
+                guard=False, collision=0, c_smag=0.0):
+    return Params(int(nx), int(ny), float(tau), float(rho0), float(u_max), int(outlet), int(precision),
+                  int(reinit), int(residual_every), int(ports), int(bool(guard)), int(collision), 0,
+                  float(c_smag))
 
 
 class SolveResult(ctypes.Structure):
@@ -54,6 +63,18 @@ class SolveResult(ctypes.Structure):
 class OptResult(ctypes.Structure):
     _fields_ = [("n_swapped", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("fluid_count", ctypes.c_int64), ("solve", SolveResult)]
+
+
+class OptPlan(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int64), ("max_iter", ctypes.c_int32), ("n_swap", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("patience", ctypes.c_int32), ("adapt", ctypes.c_int32),
+                ("keep_best", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class OptSummary(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("best_iter", ctypes.c_int32), ("stopped", ctypes.c_int32),
+                ("n_swap_final", ctypes.c_int32), ("swapped", ctypes.c_int64), ("dp_first", ctypes.c_double),
+                ("dp_best", ctypes.c_double), ("dp_last", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -106,6 +127,7 @@ def load_library(path=None):
     L.lbm_solve.argtypes = [H, ctypes.c_int64, ctypes.POINTER(SolveResult)]
     L.lbm_optimize_step.argtypes = [H, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(OptResult)]
     L.lbm_read_fields.argtypes = [H, ctypes.c_uint32, _VP, ctypes.c_size_t, ctypes.c_int]
+    L.lbm_optimize.argtypes = [H, ctypes.POINTER(OptPlan), _VP, ctypes.POINTER(OptSummary)]
     L.lbm_load_state.argtypes = [H, _VP, ctypes.c_size_t, ctypes.c_int]
     L.lbm_reset.argtypes = [H]
     L.lbm_select_swaps.argtypes = [H, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, ctypes.POINTER(ctypes.c_int32)]
@@ -152,7 +174,7 @@ def load_library(path=None):
     L.lbm_server_destroy.restype = None
     L.lbm_bytes_per_fluid_update.argtypes = [ctypes.c_int32]
     L.lbm_bytes_per_fluid_update.restype = ctypes.c_double
-    for name in ("lbm_create_geometry", "lbm_solve", "lbm_optimize_step", "lbm_read_fields",
+    for name in ("lbm_create_geometry", "lbm_solve", "lbm_optimize_step", "lbm_optimize", "lbm_read_fields",
                  "lbm_load_state", "lbm_reset", "lbm_select_swaps", "lbm_kernel_time",
                  "lbm_select_swaps_noalloc", "lbm_step_config", "lbm_set_step_config", "lbm_batch_create", "lbm_batch_solve",
                  "lbm_batch_optimize_step", "lbm_batch_read_fields", "lbm_batch_reset",
@@ -198,14 +220,15 @@ class Lattice:
     """One lattice (cell map + populations) resident on the GPU."""
 
     def __init__(self, cells, tau, u_max, rho0=1.0, outlet=OUT_CONST_RHO, precision=F32,
-                 reinit=REINIT_WARM, residual_every=100, stream=None, ports=PORTS_REGULARIZED):
+                 reinit=REINIT_WARM, residual_every=100, stream=None, ports=PORTS_REGULARIZED, guard=False,
+                 collision=COLLIDE_BGK, c_smag=0.0):
         L = load_library()
         cells = np.ascontiguousarray(cells, dtype=np.uint8)
         ny, nx = cells.shape
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
-        self.params = Params(nx, ny, float(tau), float(rho0), float(u_max), int(outlet), int(precision),
-                             int(reinit), int(residual_every), int(ports), 0)
+        self.params = make_params(nx, ny, tau, u_max, rho0, outlet, precision, reinit, residual_every, ports,
+                                  guard, collision, c_smag)
         self.nx, self.ny, self.precision = nx, ny, int(precision)
         self._h = _VP()
         _check(L.lbm_create_geometry(ctypes.byref(self.params), cells.ctypes.data, _stream_ptr(stream),
@@ -240,6 +263,19 @@ class Lattice:
         out = r.solve.to_dict()
         out.update(n_swapped=r.n_swapped, fluid_count=r.fluid_count)
         return out
+
+    def optimize(self, n_steps, max_iter, n_swap, tol=0.0, patience=3, adapt=False, keep_best=False):
+        """The whole loop of Sec. 2.3 (lbm_optimize): first solve, then up to
+        max_iter exchange iterations; returns the summary with the dp history."""
+        plan = OptPlan(int(n_steps), int(max_iter), int(n_swap), float(tol), int(patience), int(bool(adapt)),
+                       int(bool(keep_best)), 0)
+        hist = np.zeros(int(max_iter) + 1, np.float64)
+        out = OptSummary()
+        _check(load_library().lbm_optimize(self._h, ctypes.byref(plan), hist.ctypes.data, ctypes.byref(out)),
+               "lbm_optimize")
+        d = {k: getattr(out, k) for k, _ in OptSummary._fields_}
+        d["history"] = hist[:out.iterations + 1].copy()
+        return d
 
     def _field_shape_dtype(self, field):
         if field == FIELD_MASK:
@@ -314,10 +350,10 @@ class Batch:
         params = (Params * self.n)()
         for i, m in enumerate(members):
             ny, nx = self._cells[i].shape
-            params[i] = Params(nx, ny, float(m["tau"]), float(m.get("rho0", 1.0)), float(m["u_max"]),
-                               int(m.get("outlet", OUT_CONST_RHO)), int(precision),
-                               int(m.get("reinit", REINIT_WARM)), int(residual_every),
-                               int(m.get("ports", PORTS_REGULARIZED)), 0)
+            params[i] = make_params(nx, ny, m["tau"], m["u_max"], m.get("rho0", 1.0), m.get("outlet", OUT_CONST_RHO),
+                                    precision, m.get("reinit", REINIT_WARM), residual_every,
+                                    m.get("ports", PORTS_REGULARIZED), m.get("guard", False),
+                                    m.get("collision", COLLIDE_BGK), m.get("c_smag", 0.0))
         ptrs = (ctypes.c_void_p * self.n)(*[c.ctypes.data for c in self._cells])
         self._b = _VP()
         _check(L.lbm_batch_create(self.n, params, ptrs, _stream_ptr(stream), ctypes.byref(self._b)),
@@ -414,14 +450,13 @@ class Server:
 
     @staticmethod
     def params_for(cells, tau, u_max, precision=F32, rho0=1.0, outlet=OUT_CONST_RHO, reinit=REINIT_WARM,
-                   ports=PORTS_REGULARIZED):
+                   ports=PORTS_REGULARIZED, guard=False, collision=COLLIDE_BGK, c_smag=0.0):
         ny, nx = np.asarray(cells).shape
-        return Params(nx, ny, float(tau), float(rho0), float(u_max), int(outlet), int(precision), int(reinit), 0,
-                      int(ports), 0)
+        return make_params(nx, ny, tau, u_max, rho0, outlet, precision, reinit, 0, ports, guard, collision, c_smag)
 
     @staticmethod
     def footprint(nx, ny, n_iter=0, precision=F32):
-        p = Params(int(nx), int(ny), 0.6, 1.0, 0.0, 0, int(precision), 0, 0, 0, 0)
+        p = make_params(nx, ny, 0.6, 0.0, precision=precision)
         return int(load_library().lbm_server_footprint(ctypes.byref(p), int(n_iter)))
 
     def submit(self, tag, cells, tau, u_max, n_steps, n_iter=0, n_swap=0, keep_fields=False, **kw):

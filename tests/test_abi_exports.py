@@ -56,16 +56,16 @@ def test_host_only_entry_points(built_lib):
     odd = lib.ServerConfig(lib.F32, 4, 0, 101, 0)  # odd tick
     assert L.lbm_server_create(ctypes.byref(odd), None, ctypes.byref(srv)) == 1
     L.lbm_server_destroy(None)
-    small = L.lbm_server_footprint(ctypes.byref(lib.Params(128, 64, 0.8, 1.0, 0.05, 0, 0, 0, 0, 0, 0)), 0)
-    opt = L.lbm_server_footprint(ctypes.byref(lib.Params(128, 64, 0.8, 1.0, 0.05, 0, 0, 0, 0, 0, 0)), 5)
-    half = L.lbm_server_footprint(ctypes.byref(lib.Params(128, 64, 0.8, 1.0, 0.05, 0, 1, 0, 0, 0, 0)), 0)
+    small = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05)), 0)
+    opt = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05)), 5)
+    half = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05, precision=1)), 0)
     # FP32 populations alone are 9 * 64 * 128 * 4 bytes; optimising adds exchange scratch
     assert small > 9 * 64 * 128 * 4 and opt > small > half
 
 
 def test_struct_layouts_match_header():
     from paper_1303_0107_gb300 import lib
-    assert ctypes.sizeof(lib.Params) == 56
+    assert ctypes.sizeof(lib.Params) == 72
     assert ctypes.sizeof(lib.SolveResult) == 8 * 3 + 8 + 8 * 64 + 8 * 2 + 8 * 2
     assert ctypes.sizeof(lib.OptResult) == 16 + ctypes.sizeof(lib.SolveResult)
 
@@ -78,13 +78,15 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
     from paper_1303_0107_gb300 import lib
     if not shutil.which("gcc"):
         pytest.skip("no gcc")
-    checks = [("lbm_params", lib.Params, ["tau", "ports"]),
+    checks = [("lbm_params", lib.Params, ["tau", "ports", "guard", "collision", "c_smag"]),
               ("lbm_solve_result", lib.SolveResult, ["m_out", "fluid_cells"]),
               ("lbm_opt_result", lib.OptResult, ["solve"]),
               ("lbm_server_config", lib.ServerConfig, ["hbm_budget_bytes", "max_tick_steps"]),
               ("lbm_request", lib.Request, ["cell_types", "n_steps", "tag", "out_uy"]),
               ("lbm_served", lib.Served, ["t_done", "dp_first", "last"]),
-              ("lbm_server_stats", lib.ServerStats, ["active", "busy_s", "budget_bytes"])]
+              ("lbm_server_stats", lib.ServerStats, ["active", "busy_s", "budget_bytes"]),
+              ("lbm_opt_plan", lib.OptPlan, ["tol", "patience", "reserved"]),
+              ("lbm_opt_summary", lib.OptSummary, ["swapped", "dp_last"])]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', "int main(void) {"]
     for cname, _, fields in checks:
         lines.append(f'  printf("%zu\\n", sizeof({cname}));')

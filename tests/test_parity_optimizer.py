@@ -140,3 +140,39 @@ def test_cold_reinit(ora):
     r = lat.optimize_step(3, 200)
     o = s.solve(200)
     assert abs(r["dp"] - o["dp"]) <= 1e-5 * abs(o["dp"])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_guarded_selection_bit_exact(ora, seed):
+    """The connectivity guard on the GPU (word-parallel 4-connectivity
+    numbers) against the oracle's cell-by-cell rule, on ragged random masks
+    with thin walls and necks."""
+    nx, ny = [(64, 24), (70, 33), (130, 17), (256, 40)][seed]
+    cells = I.random_blobs(nx, ny, seed + 30, density=0.35)
+    rng = np.random.default_rng(seed + 5)
+    f = [(0.02 * rng.standard_normal((ny, nx))).astype(np.float32) for _ in range(3)]
+    lat = L.Lattice(cells, 0.7, 0.02, guard=True)
+    p = ora.make_params(nx, ny, 0.7, 1.0, 0.02, guard=True)
+    p0 = ora.make_params(nx, ny, 0.7, 1.0, 0.02)
+    for n in (1, 5, 50, 100000):
+        fi, si = lat.select_swaps(*f, n)
+        fo, so = _oracle_pick(ora, p, cells, *f, n)
+        assert np.array_equal(fi, fo) and np.array_equal(si, so), (seed, n)
+    # the guard removes candidates: the unguarded choice of all candidates is larger
+    fu, _ = _oracle_pick(ora, p0, cells, *f, 100000)
+    assert len(fu) >= len(fi)
+
+
+def test_guarded_loop_keeps_the_channel_connected(ora):
+    """Many aggressive exchanges on the T-junction: with the guard every
+    iteration's mask keeps a single 4-connected fluid region."""
+    from test_oracle_optimizer import _components
+    cfg = I.config_t_junction()
+    lat = L.Lattice(cfg["cells"], cfg["tau"], cfg["u_max"], residual_every=0, guard=True)
+    lat.solve(400)
+    for _ in range(12):
+        r = lat.optimize_step(12, 200)
+        mask = lat.read(L.FIELD_MASK)
+        assert _components(mask == 0) == 1
+        assert r["fluid_count"] == int((cfg["cells"] == 0).sum())
+    lat.close()
