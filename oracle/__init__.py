@@ -25,7 +25,7 @@ class Params(ctypes.Structure):
                 ("rho0", ctypes.c_double), ("u_max", ctypes.c_double),
                 ("outlet_rule", ctypes.c_int32), ("periodic", ctypes.c_int32),
                 ("port_scheme", ctypes.c_int32), ("guard", ctypes.c_int32), ("collision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("c_smag", ctypes.c_double)]
+                ("mirror", ctypes.c_int32), ("c_smag", ctypes.c_double)]
 
 
 _LIB = None
@@ -86,9 +86,10 @@ def _u8(a):
 
 
 def make_params(nx, ny, tau, rho0=1.0, u_max=0.0, outlet_rule=OUT_CONST_RHO, periodic=False,
-                port_scheme=PORTS_REGULARIZED, guard=False, collision=0, c_smag=0.0):
+                port_scheme=PORTS_REGULARIZED, guard=False, collision=0, c_smag=0.0, mirror=False):
     return Params(int(nx), int(ny), float(tau), float(rho0), float(u_max), int(outlet_rule),
-                  int(bool(periodic)), int(port_scheme), int(bool(guard)), int(collision), 0, float(c_smag))
+                  int(bool(periodic)), int(port_scheme), int(bool(guard)), int(collision), int(bool(mirror)),
+                  float(c_smag))
 
 
 def lattice():

@@ -47,6 +47,8 @@ static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 /* index of the direction opposite to i: c_OPP[i] = -c_i */
 static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+/* direction with the y component reversed (reflection in a plane y = const) */
+static const int MIR[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
 /* weights: 4/9 rest, 1/9 axis, 1/36 diagonal; c_s = sqrt(3)/3 */
 static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
@@ -72,7 +74,10 @@ typedef struct {
   int32_t guard;       /* 1: a fluid cell may turn solid only if it is a
                           simple cell of the fluid region (see ora_simple)  */
   int32_t collision;   /* ORA_COLLIDE_*: how the collision of Eq. 1 relaxes */
-  int32_t reserved;
+  int32_t mirror;      /* 1: a symmetry plane lies half a cell below row 0
+                          (Sec. 3.3 computes half of the domain): row 0 may
+                          be fluid, and what streams in across the plane is
+                          the mirror image of what row 0 sends out          */
   double c_smag;       /* Smagorinsky constant (ORA_COLLIDE_SMAGORINSKY)     */
 } ora_params;
 
@@ -115,8 +120,15 @@ int32_t ora_inlet_profile(const ora_params* p, const uint8_t* solid, double* u_i
     int y_lo = y;
     while (y < ny && !solid[y * nx + 0]) ++y;
     int width = y - y_lo;
+    /* a run that touches the symmetry plane is half of a run twice as wide,
+       centred on the plane: rows -width .. width-1 of the whole domain */
+    int lo = y_lo, w = width;
+    if (p->mirror && y_lo == 0) {
+      lo = -width;
+      w = 2 * width;
+    }
     for (int yy = y_lo; yy < y; ++yy) {
-      double s = ((double)(yy - y_lo) + 0.5) / (double)width;
+      double s = ((double)(yy - lo) + 0.5) / (double)w;
       u_in[yy] = 4.0 * p->u_max * s * (1.0 - s);
     }
     ++runs;
@@ -144,7 +156,7 @@ int32_t ora_check_geometry(const ora_params* p, const uint8_t* solid) {
   if (nx < 4 || ny < 3) return ORA_ERR_ARG;
   if (p->periodic) return ORA_OK;
   for (int x = 0; x < nx; ++x)
-    if (!solid[x] || !solid[(ny - 1) * nx + x]) return ORA_ERR_GEOMETRY;
+    if ((!p->mirror && !solid[x]) || !solid[(ny - 1) * nx + x]) return ORA_ERR_GEOMETRY;
   for (int y = 0; y < ny; ++y) {
     if (!solid[y * nx] && solid[y * nx + 1]) return ORA_ERR_GEOMETRY;
     if (!solid[y * nx + nx - 1] && solid[y * nx + nx - 2]) return ORA_ERR_GEOMETRY;
@@ -186,6 +198,16 @@ static int pull(const ora_params* p, const uint8_t* solid, const double* fp, int
   if (p->periodic) {
     sx = (sx + nx) % nx;
     sy = (sy + ny) % ny;
+  } else if (p->mirror && sy == -1 && sx >= 0 && sx < nx) {
+    /* the ghost row below the symmetry plane is the mirror image of row 0:
+       a solid image reflects as a wall (halfway bounce-back), a fluid one
+       sends the reflected population of its original cell */
+    size_t src = (size_t)sx, here = (size_t)y * nx + x;
+    if (solid[src])
+      *out = fp[OPP[i] * n + here];
+    else
+      *out = fp[MIR[i] * n + src];
+    return 1;
   } else if (sx < 0 || sx >= nx || sy < 0 || sy >= ny) {
     return 0;
   }

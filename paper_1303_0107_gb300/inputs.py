@@ -153,6 +153,25 @@ def config_tree_2048(seed: int = 0):
                 u_max=0.01171875, n_iter=50, steps=5000)
 
 
+def config_collector():
+    """The paper's own LBM case, re-derived (Sec. 3.3; its figures are not
+    available): an arborescent collector on a half domain of 360 x 180 cells
+    (flow along x) with a symmetry plane below row 0.  Eight inlets of 11
+    cells on column 0 (sixteen in the whole domain), one outlet of 52 cells
+    on column 359 against the plane (104 in the whole domain), joined by a
+    four-generation binary tree with Eq. 7's 2:2:1:1 segment lengths and
+    widths shrinking by (11/104)^(1/4) per generation; parabolic inlets of
+    mean speed 0.08 (u_max 0.12), zero-gradient outlet, rho0 = 1, nu = 0.04
+    (tau = 0.62): Re = 11 * 0.08 / 0.04 = 22."""
+    nx, ny_full = 360, 360
+    ratio = (11.0 / 104.0) ** 0.25
+    full = tree(nx, ny_full, 4, 104, ratio=ratio, jitter=0, seed=0)
+    collector = full[:, ::-1]            # branches on column 0, trunk on column nx-1
+    half = np.ascontiguousarray(collector[ny_full // 2:, :])  # rows above the plane
+    return dict(name="collector_360x180_half", cells=half, nx=nx, ny=ny_full // 2, tau=0.62, u_max=0.12,
+                outlet=1, mirror=True, n_iter=151)
+
+
 def config_candidates(n: int = 256, base_seed: int = 0):
     """Uneven candidate distributors: nx log-uniform in [256, 1024] (multiple of 32),
     ny = nx/2, G in {2,3,4}, width ratio in [0.6, 0.8], W0 = ny/16; tau 0.53 and

@@ -81,3 +81,21 @@ def test_candidates_and_requests_are_valid():
 def test_poisson_arrivals_rate():
     t = I.poisson_arrivals(200.0, 30.0, seed=1)
     assert 5400 < len(t) < 6600 and all(np.diff(t) > 0)
+
+
+def test_collector_replica_geometry(ora):
+    """The paper's half-domain collector (Sec. 3.3): 8 inlets of 11 cells,
+    one 52-cell outlet against the symmetry plane, Re = 22."""
+    c = I.config_collector()
+    cells = c["cells"]
+    assert cells.shape == (180, 360)
+    col0 = np.flatnonzero(cells[:, 0] == 0)
+    runs = np.split(col0, np.flatnonzero(np.diff(col0) > 1) + 1)
+    assert [len(r) for r in runs] == [11] * 8
+    out = np.flatnonzero(cells[:, -1] == 0)
+    assert out[0] == 0 and len(out) == 52 and np.all(np.diff(out) == 1)
+    assert cells[-1].all() and not cells[0].all()
+    p = ora.make_params(360, 180, c["tau"], 1.0, c["u_max"], outlet_rule=c["outlet"], mirror=True)
+    assert ora.check_geometry(p, cells) == 0
+    nu = (c["tau"] - 0.5) / 3
+    assert abs(11 * (2 / 3) * c["u_max"] / nu - 22) < 1e-9
