@@ -51,9 +51,13 @@ def parse():
     ap.add_argument("--lattice-steps", type=int, default=5000, help="time steps per solve")
     ap.add_argument("--precision", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-extras", action="store_true", help="skip every leg after the main run")
-    ap.add_argument("--legs", default="large,precision,batched,served",
+    ap.add_argument("--legs", default="large,tjunction,precision,models,collector,batched,served",
                     help="legs after the main run: large (8192 x 4096 lattice), precision (BF16/FP16 vs the "
-                         "FP64 oracle; also the CPU baseline), batched (256 candidates), served (request loop)")
+                         "FP64 oracle; also the CPU baseline), tjunction (128 x 64 T, launch-bound), "
+                         "models (collision models on the tree), "
+                         "collector (the paper's half-domain collector, 151 optimisation steps), "
+                         "batched (256 candidates), served (request loop), "
+                         "sweep (served at 50, 100, 200 and 400 requests/s, 10 s each; not in the default run)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="served leg: Poisson arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="served leg: arrival window")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -248,10 +252,90 @@ def leg_precision(L, I, stream):
                      "dg_abs_err": abs(r["dg"] - o["dg"]), "theta_abs_err": abs(r["theta"] - o["theta"]),
                      "glups_steps": glups[name], "glups_vs_f32": glups[name] / glups["f32"]}
         h.close()
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = ora.set_threads(0)
+    # one host thread, on a short sample of the same lattice
+    ora.set_threads(1)
+    s1 = ora.Solver(ora.make_params(nx, ny, tau, 1.0, u_max), cells, residual_every=0)
+    t0 = time.perf_counter()
+    s1.solve(100)
+    t_one = time.perf_counter() - t0
+    ora.set_threads(cores)
     cpu = {"value": fluid * S / t_ora / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"{cfg['name']}: the run's first solve, {S} FP64 time steps from rest, {t_ora:.1f} s"}
+           "sample": f"{cfg['name']}: the run's first solve, {S} FP64 time steps from rest, {t_ora:.1f} s",
+           "single_thread_value": fluid * 100 / t_one / 1e9,
+           "single_thread_sample": f"100 FP64 time steps of the same lattice on 1 thread, {t_one:.1f} s"}
     return out, cpu
+
+
+def leg_tjunction(L, I, stream):
+    """The 128 x 64 T-junction (1136 fluid cells, 10 x 2000 steps after a
+    2000-step solve): on-chip and bound by the launch latency of a step."""
+    c = I.config_t_junction()
+    fluid = int((c["cells"] == 0).sum())
+    h = L.Lattice(c["cells"], c["tau"], c["u_max"], residual_every=0, stream=stream)
+    h.solve(256)
+    h.reset()
+    h.kernel_time(reset=True)
+    t0 = time.perf_counter()
+    out = h.optimize(2000, 10, 2)
+    dt = time.perf_counter() - t0
+    ms, nl, nu = h.kernel_time()
+    res = {"fluid_cells": fluid, "glups": fluid * 2000 * 11 / dt / 1e9, "step_glups": nu / (ms / 1e3) / 1e9,
+           "us_per_step": 1e3 * ms / nl, "dp_first": out["dp_first"], "dp_last": out["dp_last"],
+           "step_config": list(h.step_config())}
+    h.close()
+    return res
+
+
+def leg_collector(L, I, stream):
+    """The paper's own LBM case, re-derived: the half-domain collector with a
+    symmetry plane (Sec. 3.3), optimised from the first to the 151st step with
+    lbm_optimize (1000 time steps per solve, n_swap = 0.2 % of the fluid)."""
+    c = I.config_collector()
+    fluid = int((c["cells"] == 0).sum())
+    n_swap = max(1, fluid // 500)
+    h = L.Lattice(c["cells"], c["tau"], c["u_max"], outlet=c["outlet"], residual_every=0, mirror=True,
+                  stream=stream)
+    h.solve(256)
+    h.reset()
+    h.kernel_time(reset=True)
+    t0 = time.perf_counter()
+    out = h.optimize(1000, c["n_iter"] - 1, n_swap)
+    dt = time.perf_counter() - t0
+    ms, nl, nu = h.kernel_time()
+    first = out["history"][0]
+    res = {"workload": f"{c['name']}: {c['n_iter']} solves of 1000 steps, n_swap {n_swap}, Neumann outlet",
+           "fluid_cells": fluid, "glups": fluid * 1000 * len(out["history"]) / dt / 1e9,
+           "step_glups": nu / (ms / 1e3) / 1e9, "seconds": dt, "dp_first": first, "dp_last": out["dp_last"],
+           "dp_best": out["dp_best"], "best_iter": out["best_iter"],
+           "dp_change_first_to_best": out["dp_best"] / first - 1.0, "step_config": list(h.step_config())}
+    h.close()
+    return res
+
+
+def leg_models(L, I, stream):
+    """Cost of the collision models beyond BGK on the 2048 x 1024 tree (FP32):
+    step GLUPS of a 5000-step solve with each model, and the oracle-free
+    difference of the pressure drop to BGK (the models agree with BGK to
+    first order at this Reynolds number)."""
+    cfg = I.config_tree_2048()
+    out = {}
+    for name, coll, c in (("bgk", L.COLLIDE_BGK, 0.0), ("regularized", L.COLLIDE_REGULARIZED, 0.0),
+                          ("smagorinsky_c0.1", L.COLLIDE_SMAGORINSKY, 0.1)):
+        h = L.Lattice(cfg["cells"], cfg["tau"], cfg["u_max"], residual_every=0, collision=coll, c_smag=c,
+                      stream=stream)
+        h.solve(1000)
+        h.reset()
+        h.kernel_time(reset=True)
+        r = h.solve(5000)
+        ms, nl, nu = h.kernel_time()
+        out[name] = {"glups_steps": nu / (ms / 1e3) / 1e9, "us_per_step": 1e3 * ms / nl, "dp": r["dp"],
+                     "step_config": list(h.step_config())}
+        h.close()
+    for k in out:
+        out[k]["glups_vs_bgk"] = out[k]["glups_steps"] / out["bgk"]["glups_steps"]
+        out[k]["dp_rel_to_bgk"] = out[k]["dp"] / out["bgk"]["dp"] - 1.0
+    return out
 
 
 def leg_batched(L, I, stream, prec, n=256, iters=10, S=2000, sample=32):
@@ -370,6 +454,8 @@ def leg_served(L, I, prec, rate, seconds, seed=5, plain_sample=120):
            "ticks": st["ticks"] - base["ticks"], "peak_active": st["peak_active"],
            "peak_resident_gb": st["peak_resident_bytes"] / 1e9, "peak_device_gb": st["peak_device_bytes"] / 1e9,
            "budget_gb": st["budget_bytes"] / 1e9, "scheduler_busy_s": st["busy_s"] - base["busy_s"]}
+    if plain_sample <= 0:
+        return out
     # one at a time through handles, back to back, on the first requests
     service, upd_p, worst = [], 0, 0.0
     for k in range(min(plain_sample, len(arrivals))):
@@ -564,11 +650,20 @@ def main():
         extras["precision_tree_2048"], cpu_p = leg_precision(L, I, stream)
         if world == 1:
             cpu = cpu_p
+    if rank == 0 and "tjunction" in legs:
+        extras["t_junction_128x64"] = leg_tjunction(L, I, stream)
+    if rank == 0 and "collector" in legs:
+        extras["collector_half_360x180"] = leg_collector(L, I, stream)
+    if rank == 0 and "models" in legs:
+        extras["collision_models_tree_2048"] = leg_models(L, I, stream)
     if rank == 0 and "batched" in legs:
         for pname, pv in (("f32", L.F32), ("bf16", L.BF16_SHIFTED)):
             extras[f"batched_256_{pname}"] = leg_batched(L, I, stream, pv)
     if rank == 0 and "served" in legs:
         extras["served_f32"] = leg_served(L, I, L.F32, args.serve_rate, args.serve_seconds)
+    if rank == 0 and "sweep" in legs:
+        extras["served_sweep_f32"] = {str(int(r)): leg_served(L, I, L.F32, r, 10.0, plain_sample=0)
+                                      for r in (50.0, 100.0, 200.0, 400.0)}
     if cpu is None and legs and rank == 0 and world == 1:
         r, n, dt, cores = oracle_rate(cells, cfg["tau"], cfg["u_max"], args.cpu_seconds)
         cpu = {"value": r / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",

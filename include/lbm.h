@@ -14,7 +14,8 @@
  * 0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE.
  *
  * Geometry rules (checked by lbm_create_geometry, LBM_ERR_GEOMETRY otherwise):
- *   - rows 0 and ny-1 are solid (the frame);
+ *   - rows 0 and ny-1 are solid (the frame; row 0 may be fluid when
+ *     lbm_params.mirror puts a symmetry plane below it);
  *   - inlet cells are the fluid cells of column 0, outlet cells those of
  *     column nx-1; each fluid cell (0,y) has a fluid (1,y) and each fluid
  *     (nx-1,y) a fluid (nx-2,y);
@@ -50,7 +51,8 @@ typedef enum {
   LBM_ERR_CUDA = 4,      /* a CUDA call failed; the handle must be destroyed */
   LBM_ERR_DIVERGED = 5,  /* a reduction or a score is not finite */
   LBM_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
-  LBM_ERR_BUSY = 7       /* resource temporarily unavailable (admission refused) */
+  LBM_ERR_BUSY = 7,      /* resource temporarily unavailable (admission refused) */
+  LBM_ERR_CANCELLED = 8  /* a served request withdrawn with lbm_server_cancel */
 } lbm_status;
 
 typedef enum {
@@ -104,7 +106,11 @@ typedef struct {
                              connected within its 3 x 3 block without it and it
                              joins exactly one solid part (4-connectivity number 1) */
   int32_t collision;      /* lbm_collision */
-  int32_t reserved;       /* must be 0 */
+  int32_t mirror;         /* 1: a symmetry plane lies half a cell below row 0 (Sec. 3.3
+                             computes half of the domain): row 0 may be fluid, and
+                             what streams in across the plane is the mirror image of
+                             what row 0 sends out; an inlet run touching the plane is
+                             half of a run twice as wide centred on it */
   double c_smag;          /* Smagorinsky constant (LBM_COLLIDE_SMAGORINSKY; >= 0) */
 } lbm_params;
 
@@ -268,6 +274,11 @@ const char* lbm_status_str(lbm_status s);
 /* Description of the last failure on the calling thread ("" if none).   */
 const char* lbm_last_error(void);
 
+/* Test hook for the failure paths: the device allocation made after `after`
+ * further successful ones fails as if the device were full (LBM_ERR_OOM from
+ * the call that needed it); after < 0 switches the hook off.  One-shot.   */
+void lbm_debug_fail_alloc(int64_t after);
+
 /* Number of device kernels this process has launched through the library
  * (graph launches count every kernel node).                             */
 uint64_t lbm_kernel_launches(void);
@@ -407,6 +418,10 @@ lbm_status lbm_server_submit(lbm_server s, const lbm_request* r);
 /* Move up to max_out finished requests into out (host lbm_served[max_out]),
  * waiting up to wait_ms milliseconds for the first; returns how many.     */
 int32_t lbm_server_poll(lbm_server s, lbm_served* out, int32_t max_out, int32_t wait_ms);
+/* Withdraw request `tag`: a queued one leaves the queue at once, a resident
+ * one is retired at the next tick boundary; either way its result carries
+ * LBM_ERR_CANCELLED.  LBM_ERR_ARG if no queued or resident request has the tag. */
+lbm_status lbm_server_cancel(lbm_server s, int64_t tag);
 /* Wait until nothing is queued or resident; LBM_ERR_TIMEOUT after timeout_ms. */
 lbm_status lbm_server_wait_idle(lbm_server s, int32_t timeout_ms);
 lbm_status lbm_server_get_stats(lbm_server s, lbm_server_stats* out);

@@ -62,6 +62,8 @@ def lib():
         L.ora_residual.restype = ctypes.c_double
         L.ora_scores.argtypes = [P, _U8, _D, _D, _D, ctypes.c_double, _U8, _D]
         L.ora_simple.argtypes = [P, _U8, ctypes.c_int32, ctypes.c_int32]
+        L.ora_set_threads.argtypes = [ctypes.c_int32]
+        L.ora_set_threads.restype = ctypes.c_int32
         L.ora_smagorinsky_tau.argtypes = [ctypes.c_double] * 6
         L.ora_smagorinsky_tau.restype = ctypes.c_double
         L.ora_simple.restype = ctypes.c_int32
@@ -198,6 +200,11 @@ def residual(params, solid, ux, uy, ux_prev, uy_prev):
 def simple(params, solid, x, y):
     """1 if interior fluid cell (x, y) may turn solid under the connectivity guard."""
     return int(lib().ora_simple(ctypes.byref(params), _p(_u8(solid), ctypes.c_uint8), int(x), int(y)))
+
+
+def set_threads(n):
+    """Host threads of the time steps (n <= 0: leave as is); returns the number in force."""
+    return int(lib().ora_set_threads(int(n)))
 
 
 def mu_of(params):

@@ -37,6 +37,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---- Sec. 2.1: the D2Q9 lattice ------------------------------------------
  * c_0 = 0; c_1..c_4 = (cos((i-1)pi/2), sin((i-1)pi/2)) = E, N, W, S.
@@ -80,6 +83,19 @@ typedef struct {
                           the mirror image of what row 0 sends out          */
   double c_smag;       /* Smagorinsky constant (ORA_COLLIDE_SMAGORINSKY)     */
 } ora_params;
+
+/* Host threads of the time steps (OpenMP over rows; 0 or less: the
+ * default).  Returns the number in force.  The results do not depend on it:
+ * every cell is computed by one thread from the previous lattice. */
+int32_t ora_set_threads(int32_t n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 /* Export the lattice tables so that tests can check them against the
  * closed forms of Sec. 2.1. */

@@ -38,6 +38,7 @@ const char* lbm_status_str(lbm_status s) {
     case LBM_ERR_DIVERGED: return "diverged (non-finite value)";
     case LBM_ERR_TIMEOUT: return "timeout";
     case LBM_ERR_BUSY: return "busy";
+    case LBM_ERR_CANCELLED: return "cancelled";
   }
   return "unknown status";
 }
@@ -45,6 +46,8 @@ const char* lbm_status_str(lbm_status s) {
 const char* lbm_last_error(void) { return t_last_error.c_str(); }
 
 uint64_t lbm_kernel_launches(void) { return launches_total(); }
+
+void lbm_debug_fail_alloc(int64_t after) { set_alloc_failure(after); }
 
 double lbm_bytes_per_fluid_update(int32_t precision) {
   return 2.0 * 9.0 * (double)storage_bytes(precision) + 1.0 / 8.0;
@@ -142,8 +145,8 @@ lbm_status lbm_select_swaps(lbm_handle h, const float* drho, const float* ux, co
   // the member's view with its fields replaced by copies of the given ones
   float* tmp = nullptr;
   LatticeView* vdev = nullptr;
-  CU(cudaMalloc(&tmp, 3 * m->plane * sizeof(float)));
-  if (cudaMalloc(&vdev, sizeof(LatticeView)) != cudaSuccess) {
+  CU(dev_malloc(reinterpret_cast<void**>(&tmp), 3 * m->plane * sizeof(float)));
+  if (dev_malloc(reinterpret_cast<void**>(&vdev), sizeof(LatticeView)) != cudaSuccess) {
     cudaFree(tmp);
     return fail(LBM_ERR_OOM, "cudaMalloc(view)");
   }

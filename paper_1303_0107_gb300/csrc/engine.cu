@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -52,6 +54,23 @@ bool autotune_enabled() {
   return on;
 }
 
+// Test hook for the failure paths: the allocation that brings the countdown
+// from 0 to -1 fails as if the device were full.
+static std::atomic<int64_t> g_fail_after{-1};
+
+void set_alloc_failure(int64_t after) { g_fail_after.store(after < 0 ? -1 : after); }
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  int64_t v = g_fail_after.load();
+  while (v >= 0 && !g_fail_after.compare_exchange_weak(v, v - 1)) {
+  }
+  if (v == 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 lbm_status fail(lbm_status s, const std::string& msg) {
   t_last_error = msg;
   return s;
@@ -79,6 +98,10 @@ size_t storage_bytes(int precision) { return precision == LBM_F32 ? 4 : 2; }
 namespace {
 
 constexpr int kGraphPairs[3] = {64, 8, 1};
+// Untuned launch shape: kStepWarps warps per block, the grid twice the blocks
+// resident at once (the tuner's usual choice; it leaves the tail of a step
+// to blocks that start as the first ones finish).
+constexpr int kDefaultGridScale = 2;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -111,8 +134,8 @@ SlabPlan plan_slab(const lbm_params& p) {
 lbm_status check_and_describe(Member& m, const uint8_t* cells, std::vector<float>& u_in) {
   const int nx = m.nx, ny = m.ny;
   for (int x = 0; x < nx; ++x)
-    if (!cells[x] || !cells[(size_t)(ny - 1) * nx + x])
-      return fail(LBM_ERR_GEOMETRY, "rows 0 and ny-1 must be solid");
+    if ((!m.p.mirror && !cells[x]) || !cells[(size_t)(ny - 1) * nx + x])
+      return fail(LBM_ERR_GEOMETRY, "rows 0 and ny-1 must be solid (row 0 may be fluid next to a symmetry plane)");
   int n_in = 0;
   for (int y = 0; y < ny; ++y) {
     const uint8_t* r = cells + (size_t)y * nx;
@@ -127,8 +150,11 @@ lbm_status check_and_describe(Member& m, const uint8_t* cells, std::vector<float
     const int y_lo = y;
     while (y < ny && !cells[(size_t)y * nx]) ++y;
     const int width = y - y_lo;
+    // a run touching the symmetry plane is half of a run twice as wide centred on it
+    const bool half = m.p.mirror && y_lo == 0;
+    const int lo = half ? -width : y_lo, w = half ? 2 * width : width;
     for (int yy = y_lo; yy < y; ++yy) {
-      const double s = ((double)(yy - y_lo) + 0.5) / (double)width;
+      const double s = ((double)(yy - lo) + 0.5) / (double)w;
       u_in[yy] = (float)(4.0 * m.p.u_max * s * (1.0 - s));
     }
   }
@@ -162,7 +188,7 @@ lbm_status layout_build(SetLayout& S, const std::vector<Member*>& ms, cudaStream
     v.sel_off = (int)sel;
     S.h_views[i] = v;
     words += (long long)mb->ny * mb->wpr;
-    swords += (long long)(mb->ny - 2) * mb->wpr;
+    swords += (long long)(mb->ny - 1 - first_step_row(mb->view)) * mb->wpr;
     sel += sel_capacity(mb->nx, mb->ny);
     cells += (long long)mb->nx * mb->ny;
     S.h_woff[i + 1] = (int)std::min<long long>(words, INT32_MAX);
@@ -307,7 +333,7 @@ lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
 // on the device at once; a fixed-grid engine always takes the device-sized
 // grid, so its captured graphs outlive changes of the member list.
 StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale, int cpt = 1, int stages = 0) {
-  const int bps = stream_collide_blocks_per_sm(E->precision, 0, 0, wpb, cpt, stages, E->models ? 1 : 0);
+  const int bps = stream_collide_blocks_per_sm(E->precision, 0, 0, wpb, cpt, stages, E->features);
   const long long cap = (long long)E->sm_count * bps * blocks_per_sm_scale;
   const long long tasks = ((long long)E->L.total_seg_words + cpt - 1) / cpt;
   const long long need = (tasks + wpb - 1) / wpb;
@@ -317,7 +343,7 @@ StepConfig shape(Engine* E, int wpb, int blocks_per_sm_scale, int cpt = 1, int s
   c.persistent = 0;
   c.cells_per_thread = cpt;
   c.stages = stages;
-  c.models = E->models ? 1 : 0;
+  c.features = E->features;
   return c;
 }
 
@@ -330,23 +356,60 @@ StepConfig persistent_shape(Engine* E, int wpb, int cpt = 1) {
   c.persistent = 1;
   c.cells_per_thread = cpt;
   c.stages = 0;
-  c.models = 0;
+  c.features = 0;
   return c;
 }
 
 // Pick the step launch shape by timing candidate shapes on the engine's own
 // lattices.  The populations are saved and restored around the trials, and
 // every shape computes the same values per cell, so tuning changes no result.
+// Shapes already tuned in this process, by set signature: device,
+// precision, kernel build, member count and each member's size and
+// fluid-cell count.  A new
+// engine over the same lattices takes the stored shape instead of timing the
+// candidates again (LBM_TUNE_CACHE=0 turns the cache off).
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, StepConfig> g_tune_cache;
+
+bool tune_cache_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("LBM_TUNE_CACHE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+std::vector<long long> tune_key(const Engine* E) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<long long> k{dev, E->precision, E->features, E->fixed_grid ? 1 : 0, (long long)E->m.size()};
+  for (const Member* m : E->m) {
+    k.push_back(m->nx);
+    k.push_back(m->ny);
+    k.push_back(m->fluid_cells);
+  }
+  return k;
+}
+
 lbm_status autotune(Engine* E) {
   E->tuned = true;
-  E->step = shape(E, kStepWarps, 1);
+  E->step = shape(E, kStepWarps, kDefaultGridScale);
   if (!autotune_enabled() || debug_sync()) return LBM_OK;
+  const std::vector<long long> key = tune_key(E);
+  if (tune_cache_enabled()) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      E->step = it->second;
+      return LBM_OK;
+    }
+  }
   const size_t sb = storage_bytes(E->precision);
   const int n = E->n();
   std::vector<void*> backups(n, nullptr);
   for (int i = 0; i < n; ++i) {
     const size_t bytes = 9 * E->m[i]->plane * sb;
-    if (cudaMalloc(&backups[i], bytes) != cudaSuccess) {  // no room: keep the default shape
+    if (dev_malloc(&backups[i], bytes) != cudaSuccess) {  // no room: keep the default shape
       for (void* b : backups) cudaFree(b);
       cudaGetLastError();
       return LBM_OK;
@@ -354,9 +417,9 @@ lbm_status autotune(Engine* E) {
     CU(cudaMemcpyAsync(backups[i], E->m[i]->f, bytes, cudaMemcpyDeviceToDevice, E->stream));
   }
   std::vector<StepConfig> cand;
-  // the collision models beyond BGK have one kernel shape: one cell per
-  // thread, register loads, one launch per phase
-  const bool only_plain = E->models;
+  // the builds with features (collision models, symmetry plane) have one
+  // kernel shape: one cell per thread, register loads, one launch per phase
+  const bool only_plain = E->features != 0;
   for (int cpt : {1, 2})
     for (int wpb : {4, 8, 16})
       for (int scale : {1, 2, 4}) {
@@ -432,13 +495,26 @@ lbm_status autotune(Engine* E) {
   }
   for (cudaGraphExec_t g : tg)
     if (g) cudaGraphExecDestroy(g);
-  StepConfig best_cfg = cand[0];
-  float best = 1e30f;
-  for (size_t ci = 0; ci < cand.size(); ++ci)
+  // The fastest candidate, except that a shape with two cells per thread,
+  // staged loads or one persistent launch must beat the fastest plain shape
+  // (one cell per thread, register loads, per-phase launches) by kMargin:
+  // near-ties are within the timing noise, and the plain shape is the one
+  // the profiles and the default use.
+  constexpr float kMargin = 0.97f;
+  StepConfig best_cfg = cand[0], best_plain = cand[0];
+  float best = 1e30f, best_p = 1e30f;
+  for (size_t ci = 0; ci < cand.size(); ++ci) {
+    const StepConfig& c = cand[ci];
     if (t_min[ci] < best) {
       best = t_min[ci];
-      best_cfg = cand[ci];
+      best_cfg = c;
     }
+    if (!c.persistent && c.cells_per_thread == 1 && c.stages == 0 && t_min[ci] < best_p) {
+      best_p = t_min[ci];
+      best_plain = c;
+    }
+  }
+  if (best_p < 1e30f && best > kMargin * best_p) best_cfg = best_plain;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   E->bar_used = false;
@@ -447,6 +523,10 @@ lbm_status autotune(Engine* E) {
   cudaStreamSynchronize(E->stream);
   for (void* q : backups) cudaFree(q);
   E->step = best_cfg;
+  if (st == LBM_OK && tune_cache_enabled()) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_cfg;
+  }
   return st;
 }
 
@@ -503,7 +583,7 @@ lbm_status check_params(const lbm_params& p) {
   if (p.collision != LBM_COLLIDE_BGK && p.collision != LBM_COLLIDE_REGULARIZED &&
       p.collision != LBM_COLLIDE_SMAGORINSKY)
     return fail(LBM_ERR_ARG, "collision");
-  if (p.reserved != 0) return fail(LBM_ERR_ARG, "reserved must be 0");
+  if (p.mirror != 0 && p.mirror != 1) return fail(LBM_ERR_ARG, "mirror must be 0 or 1");
   if (!std::isfinite(p.c_smag) || p.c_smag < 0) return fail(LBM_ERR_ARG, "c_smag must be finite and >= 0");
   return LBM_OK;
 }
@@ -548,7 +628,7 @@ lbm_status member_create(const lbm_params& p, const uint8_t* cells, cudaStream_t
     }                                                                                    \
   } while (0)
   const SlabPlan s = plan_slab(p);
-  CUM(cudaMalloc(&m->slab, s.total));
+  CUM(dev_malloc(&m->slab, s.total));
   m->slab_bytes = s.total;
   char* b = static_cast<char*>(m->slab);
   m->f = b + s.f;
@@ -573,6 +653,10 @@ lbm_status member_create(const lbm_params& p, const uint8_t* cells, cudaStream_t
   CUM(cudaMemcpyAsync(m->d_out, outs.data(), outs.size() * 4, cudaMemcpyHostToDevice, stream));
   CUM(cudaMemcpyAsync(m->cells, cells, (size_t)m->nx * m->ny, cudaMemcpyHostToDevice, stream));
   CUM(launch_pack_mask(m->cells, m->nx, m->ny, m->wpr, m->mask0, stream));
+  if (p.mirror) {  // the padding row below row 0 is row 0's mirror image (the exchange never moves row 0)
+    const size_t row = (size_t)mask_stride(m->wpr) * 4;
+    CUM(cudaMemcpyAsync(m->mask0_base, m->mask0_base + mask_stride(m->wpr), row, cudaMemcpyDeviceToDevice, stream));
+  }
 #undef CUM
   LatticeView& v = m->view;
   std::memset(&v, 0, sizeof(v));
@@ -600,6 +684,7 @@ lbm_status member_create(const lbm_params& p, const uint8_t* cells, cudaStream_t
   v.port_scheme = p.ports;
   v.n_outlets = (int)m->out_start.size();
   v.guard = p.guard;
+  v.mirror = p.mirror;
   v.collision = p.collision;
   v.c_smag = (float)p.c_smag;
   *out = m;
@@ -623,7 +708,7 @@ cudaError_t GrowBuf::reserve(size_t bytes, bool* moved) {
   if (p) cudaFree(p);
   p = nullptr;
   cap = 0;
-  cudaError_t e = cudaMalloc(&p, want);
+  cudaError_t e = dev_malloc(&p, want);
   if (e != cudaSuccess) {
     p = nullptr;
     return e;
@@ -691,7 +776,7 @@ lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool
   CUE(E->bar.reserve(sizeof(StepBarrier)));
   CUE(cudaMemsetAsync(E->bar.p, 0, sizeof(StepBarrier), E->stream));
 #undef CUE
-  E->step = shape(E, kStepWarps, 1);
+  E->step = shape(E, kStepWarps, kDefaultGridScale);
   *out = E;
   return LBM_OK;
 }
@@ -708,13 +793,14 @@ lbm_status rebuild_worklist(Engine* E) {
 }
 
 lbm_status engine_set_members(Engine* E, const std::vector<Member*>& members) {
-  bool models = false;
+  int features = 0;
   for (Member* mb : members) {
     if (mb->p.precision != E->precision) return fail(LBM_ERR_ARG, "all lattices of a set share one precision");
-    models |= mb->p.collision != LBM_COLLIDE_BGK;
+    if (mb->p.collision != LBM_COLLIDE_BGK) features |= 1;
+    if (mb->p.mirror) features |= 2;
   }
-  if (models != E->models) {  // a different kernel build: the tuned shape and graphs no longer apply
-    E->models = models;
+  if (features != E->features) {  // a different kernel build: the tuned shape and graphs no longer apply
+    E->features = features;
     E->tuned = false;
     E->step.cells_per_thread = 1;
     E->step.stages = 0;
@@ -736,7 +822,7 @@ lbm_status engine_set_members(Engine* E, const std::vector<Member*>& members) {
   CU(E->dense_f.reserve((size_t)std::max<long long>(1, max_cells) * 4));
   st = ensure_pinned(E, nn);
   if (st != LBM_OK) return st;
-  if (!E->tuned || E->fixed_grid) E->step = shape(E, E->step.warps_per_block, 1);
+  if (!E->tuned || E->fixed_grid) E->step = shape(E, E->step.warps_per_block, kDefaultGridScale);
   if (n == 0) return LBM_OK;
   st = rebuild_worklist(E);
   if (st != LBM_OK) return st;
@@ -1099,10 +1185,10 @@ lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t pe
   if (cells_per_thread == 2 && warps_per_block == 16)
     return fail(LBM_ERR_ARG, "two cells per thread take 4 or 8 warps per block");
   if (persistent && warps_per_block == 4) return fail(LBM_ERR_ARG, "the persistent kernel takes 8 or 16 warps per block");
-  if (E->models && (persistent || cells_per_thread != 1 || stages != 0))
-    return fail(LBM_ERR_ARG, "lattices with a collision other than BGK take the plain launch shape");
+  if (E->features && (persistent || cells_per_thread != 1 || stages != 0))
+    return fail(LBM_ERR_ARG, "lattices with collision models or a symmetry plane take the plain launch shape");
   StepConfig c = persistent ? persistent_shape(E, warps_per_block, cells_per_thread)
-                            : shape(E, warps_per_block, 1, cells_per_thread, stages);
+                            : shape(E, warps_per_block, kDefaultGridScale, cells_per_thread, stages);
   if (c.grid < 1) return fail(LBM_ERR_CUDA, "no resident block for the persistent kernel");
   E->step = c;
   E->tuned = true;

@@ -18,6 +18,10 @@
 namespace lbm {
 
 lbm_status fail(lbm_status s, const std::string& msg);
+// Every device allocation of the library goes through dev_malloc, so that
+// a test can make the n-th one fail (set_alloc_failure).
+cudaError_t dev_malloc(void** p, size_t bytes);
+void set_alloc_failure(int64_t after);
 uint64_t launches_total();
 size_t storage_bytes(int precision);
 lbm_status check_params(const lbm_params& p);
@@ -101,7 +105,7 @@ struct Engine {
   cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};  // views, segs, n_segs, shape
   StepConfig step{kStepWarps, 1, 0, 1, 0, 0};
-  bool models = false;  // some member uses a collision other than BGK
+  int features = 0;  // kernel build the members need: 1 collision models, 2 symmetry plane
   bool tuned = false;
   cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
   double step_ms = 0.0;

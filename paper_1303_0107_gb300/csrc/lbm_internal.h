@@ -29,8 +29,10 @@ constexpr int kPitchAlign = 64;
 
 // Cell mask layout: one bit per cell, bit (x & 31) of word x >> 5 of a row,
 // set = solid.  Rows are stored with a stride of wpr + 2 words and one solid
-// padding word on each side, plus one solid padding row above row 0 and one
-// below row ny-1; the mask pointer addresses word 0 of row 0.  Every
+// padding word on each side, plus one padding row below row 0 and one above
+// row ny-1, both solid -- except that with a symmetry plane below row 0 the
+// row below holds a copy of row 0 (its mirror image); the mask pointer
+// addresses word 0 of row 0.  Every
 // neighbour word a kernel forms (rows y-1..y+1, words w-1..w+1) therefore lies
 // inside the allocation and reads as wall outside the lattice.
 __host__ __device__ constexpr int mask_stride(int wpr) { return wpr + 2; }
@@ -67,6 +69,7 @@ struct alignas(16) LatticeView {
   int word_off;            // start of this lattice's words in the concatenated word space
   int seg_word_off;        // start of its interior-row words (rows 1..ny-2)
   int guard;               // connectivity guard on fluid candidates (lbm_params.guard)
+  int mirror;              // symmetry plane below row 0 (lbm_params.mirror)
   int collision;           // lbm_collision
   float c_smag;            // Smagorinsky constant
 };
@@ -79,6 +82,10 @@ struct alignas(8) SegRef {
 constexpr int kSegWordBits = 12;
 static_assert(sizeof(LatticeView) % 16 == 0 && alignof(LatticeView) == 16, "LatticeView layout");
 static_assert(sizeof(SegRef) == 8, "SegRef layout");
+
+// First row of the step work-list: row 0 is fluid-capable only next to a
+// symmetry plane; the last row (ny - 1) is always a wall.
+__host__ __device__ inline int first_step_row(const LatticeView& v) { return v.mirror ? 0 : 1; }
 
 // Index of the lattice whose range [off[l], off[l+1]) holds i (off ascending,
 // off[0] = 0, n lattices).
@@ -108,8 +115,8 @@ struct StepConfig {
   int cells_per_thread; // 1 or 2: row segments per warp task (2: at most 8 warps per block)
   int stages;           // 0: populations loaded into registers; 2 or 3: staged through shared
                         //    memory that many segments ahead (one cell per thread, per-phase launches)
-  int models;           // 1: kernels with the collision models beyond BGK (one cell per thread,
-                        //    register loads, per-phase launches)
+  int features;         // kernel build: bit 0 collision models beyond BGK, bit 1 symmetry plane
+                        //    (non-zero: one cell per thread, register loads, per-phase launches)
 };
 // Grid barrier state of the persistent kernel (device memory, 16 bytes).
 struct StepBarrier {
@@ -122,7 +129,7 @@ cudaError_t launch_stream_collide(int precision, int phase, int moments, const L
                                   const SegRef* segs, const int* n_segs, StepConfig cfg,
                                   cudaStream_t stream);
 int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int cells_per_thread,
-                                 int stages, int models);
+                                 int stages, int features);
 // n_pairs time-step pairs (phase A then B, no moments) in one cooperative
 // launch with a grid barrier between phases; sc.grid must not exceed
 // stream_collide_persistent_grid (every block resident at once), and

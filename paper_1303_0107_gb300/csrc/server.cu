@@ -20,6 +20,7 @@
 // the member, so a request's results do not depend on what else is resident.
 #include <algorithm>
 #include <chrono>
+#include <set>
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
@@ -97,6 +98,8 @@ struct lbm_server_s {
   int64_t resident = 0;        // guarded by mu
   int64_t resident_cells = 0;  // guarded by mu
   lbm_server_stats st{};       // guarded by mu
+  std::set<int64_t> cancel;    // tags of resident requests to withdraw; guarded by mu
+  std::set<int64_t> resident_tags;  // guarded by mu
   bool stop = false;           // guarded by mu
   bool fatal = false;          // guarded by mu
   std::vector<Slot> slots;     // scheduler thread only
@@ -122,6 +125,9 @@ struct lbm_server_s {
     std::lock_guard<std::mutex> lk(mu);
     done.push_back(d);
     resident -= s.q.footprint;
+    st.resident_bytes = resident;
+    resident_tags.erase(s.q.r.tag);
+    cancel.erase(s.q.r.tag);
     resident_cells -= cells_of(s.q);
     if (status == LBM_OK) ++st.completed; else ++st.failed;
     cv_done.notify_all();
@@ -146,6 +152,10 @@ struct lbm_server_s {
       std::lock_guard<std::mutex> lk(mu);
       fatal = true;
       q.swap(queue);
+      for (const Pending& p : q) {  // finish() releases what admission would have charged
+        resident += p.footprint;
+        resident_cells += cells_of(p);
+      }
     }
     for (Pending& p : q) finish_pending(p, status, now());
   }
@@ -167,6 +177,7 @@ void lbm_server_s::loop() {
              resident_cells + cells_of(queue.front()) < kMaxSetCells) {
         resident += queue.front().footprint;
         resident_cells += cells_of(queue.front());
+        resident_tags.insert(queue.front().r.tag);
         adm.push_back(std::move(queue.front()));
         queue.pop_front();
       }
@@ -193,6 +204,27 @@ void lbm_server_s::loop() {
       sl.steps_left = sl.q.r.n_steps;
       slots.push_back(std::move(sl));
       changed = true;
+    }
+    {  // withdraw cancelled resident requests before this tick
+      std::vector<int64_t> gone;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        gone.assign(cancel.begin(), cancel.end());
+      }
+      if (!gone.empty()) {
+        std::vector<Slot> keep;
+        for (Slot& x : slots) {
+          if (std::find(gone.begin(), gone.end(), x.q.r.tag) != gone.end()) {
+            finish(x, LBM_ERR_CANCELLED);
+            delete x.m;
+            changed = true;
+          } else {
+            keep.push_back(std::move(x));
+          }
+        }
+        slots.swap(keep);
+        if (slots.empty()) E->m.clear();
+      }
     }
     if (slots.empty()) {
       // nothing resident and nothing admitted (only if a request can never fit)
@@ -394,6 +426,37 @@ int32_t lbm_server_poll(lbm_server s, lbm_served* out, int32_t max_out, int32_t 
     s->done.pop_front();
   }
   return k;
+}
+
+lbm_status lbm_server_cancel(lbm_server s, int64_t tag) {
+  if (!s) return fail(LBM_ERR_ARG, "server is NULL");
+  Pending p;
+  bool queued = false;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+      if (it->r.tag == tag) {
+        p = std::move(*it);
+        s->queue.erase(it);
+        queued = true;
+        s->st.queued = (int32_t)s->queue.size();
+        break;
+      }
+    if (!queued) {
+      if (!s->resident_tags.count(tag)) return fail(LBM_ERR_ARG, "no queued or resident request has this tag");
+      s->cancel.insert(tag);
+    }
+  }
+  if (queued) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->resident += p.footprint;  // finish() releases what admission would have charged
+      s->resident_cells += cells_of(p);
+    }
+    s->finish_pending(p, LBM_ERR_CANCELLED, s->now());
+  }
+  s->cv_work.notify_one();
+  return LBM_OK;
 }
 
 lbm_status lbm_server_wait_idle(lbm_server s, int32_t timeout_ms) {

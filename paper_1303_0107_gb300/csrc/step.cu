@@ -259,8 +259,15 @@ __device__ __forceinline__ void outlet_rule(float (&g)[9], float rho0, int schem
     if (LBM_OK_IDX((off), s.fe)) P::st(F + (off), (v)); \
   } while (0)
 
-// neighbour solid flags, bit i-1 = solid(x + c_i), i = 1..8 (E N W S NE NW SW SE)
-constexpr unsigned kE = 1u, kN = 2u, kW = 4u, kS = 8u, kNE = 16u, kNW = 32u, kSW = 64u, kSE = 128u;
+// Kernel builds by feature (template bit mask): kFeatModels -- collision
+// models beyond BGK; kFeatMirror -- a symmetry plane below row 0.  The plain
+// build has neither, so the common path keeps its registers and branches.
+constexpr int kFeatModels = 1, kFeatMirror = 2;
+
+// neighbour solid flags, bit i-1 = solid(x + c_i), i = 1..8 (E N W S NE NW SW SE);
+// kMirror marks a cell of row 0 next to a symmetry plane
+constexpr unsigned kE = 1u, kN = 2u, kW = 4u, kS = 8u, kNE = 16u, kNW = 32u, kSW = 64u, kSE = 128u,
+                   kMirror = 256u;
 
 // Threads per block at most, by cells per thread (the register budget per
 // thread is 64 with one cell, 80 with two).
@@ -282,7 +289,7 @@ struct SegCtx {
   long long fe;  // population elements (bounds-checked builds)
 };
 
-template <class T, int PHASE>
+template <class T, int PHASE, int FEAT = 0>
 __device__ __forceinline__ void seg_prologue(const LatticeView* __restrict__ views, const SegRef sr, bool valid,
                                              const int lane, SegCtx<T>& s) {
   const LatticeView* __restrict__ L = views + (valid ? sr.lattice : 0);
@@ -331,13 +338,21 @@ __device__ __forceinline__ void seg_prologue(const LatticeView* __restrict__ vie
     s.nb = ((eC >> lane) & 1u) | (((mn >> lane) & 1u) << 1) | (((wC >> lane) & 1u) << 2) |
            (((msth >> lane) & 1u) << 3) | (((eN >> lane) & 1u) << 4) | (((wN >> lane) & 1u) << 5) |
            (((wS >> lane) & 1u) << 6) | (((eS >> lane) & 1u) << 7);
+    // Symmetry plane half a cell below row 0 (the padding row below holds
+    // row 0's mirror image, so the SW / SE flags already tell whether the
+    // image cell is solid).  What row 0 sends across the plane comes back
+    // reflected: straight down returns as straight up into the same cell --
+    // the bounce-back slot -- and a diagonal returns into the row-0
+    // neighbour it was heading past: SW into (x-1, 0) as NW, SE into
+    // (x+1, 0) as NE.
+    if ((FEAT & kFeatMirror) && y == 0 && L->mirror) s.nb |= kS | kMirror;
   }
 }
 
 // The nine incoming populations of the lane's cell (0 where unknown or solid).
 // CG: read through L2 only (the persistent kernel: within one launch a slot
 // written by another block must not be served from this SM's L1).
-template <class T, int PHASE, bool CG>
+template <class T, int PHASE, bool CG, int FEAT = 0>
 __device__ __forceinline__ void seg_load(const SegCtx<T>& s, float (&g)[9]) {
   using P = Pop<T>;
   const T* __restrict__ F = s.F;
@@ -352,12 +367,14 @@ __device__ __forceinline__ void seg_load(const SegCtx<T>& s, float (&g)[9]) {
     g[4] = (nb & kN) ? FLD(2 * pl + c) : FLD(4 * pl + c + pitch);
     if (!s.inlet) {  // sources on the west side (unknown at the inlet)
       g[1] = (nb & kW) ? FLD(3 * pl + c) : FLD(1 * pl + c - 1);
-      g[5] = (nb & kSW) ? FLD(7 * pl + c) : FLD(5 * pl + c - pitch - 1);
+      g[5] = (nb & kSW) ? FLD(7 * pl + c)
+             : ((FEAT & kFeatMirror) && (nb & kMirror)) ? FLD(8 * pl + c - 1) : FLD(5 * pl + c - pitch - 1);
       g[8] = (nb & kNW) ? FLD(6 * pl + c) : FLD(8 * pl + c + pitch - 1);
     }
     if (!s.outlet) {  // sources on the east side (unknown at the outlet)
       g[3] = (nb & kE) ? FLD(1 * pl + c) : FLD(3 * pl + c + 1);
-      g[6] = (nb & kSE) ? FLD(8 * pl + c) : FLD(6 * pl + c - pitch + 1);
+      g[6] = (nb & kSE) ? FLD(8 * pl + c)
+             : ((FEAT & kFeatMirror) && (nb & kMirror)) ? FLD(7 * pl + c + 1) : FLD(6 * pl + c - pitch + 1);
       g[7] = (nb & kNE) ? FLD(5 * pl + c) : FLD(7 * pl + c + pitch + 1);
     }
   } else {
@@ -379,7 +396,7 @@ __device__ __forceinline__ void seg_load(const SegCtx<T>& s, float (&g)[9]) {
 
 // Boundary rules, collision and stores of the lane's cell.  Every lane of the
 // warp calls it (the zero-gradient outlet shuffles across lanes).
-template <class T, int PHASE, int MOM, int MODELS>
+template <class T, int PHASE, int MOM, int FEAT>
 __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
   using P = Pop<T>;
   const LatticeView* __restrict__ L = s.L;
@@ -405,7 +422,7 @@ __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
     outlet_rule(g, rho0, L->port_scheme);
   }
   float drho, ux, uy;
-  if (MODELS && L->collision != LBM_COLLIDE_BGK)  // kernels built for BGK only skip this branch
+  if ((FEAT & kFeatModels) && L->collision != LBM_COLLIDE_BGK)  // the plain build skips this branch
     collide_other(g, rho0, s.omega, L->collision, L->c_smag, drho, ux, uy);
   else
     bgk(g, rho0, s.omega, drho, ux, uy);
@@ -420,12 +437,16 @@ __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
     if (!s.outlet) {  // destinations on the east side leave through the outlet
       if (nb & kE) FST(1 * pl + c, g[1]); else FST(3 * pl + c + 1, g[1]);
       if (nb & kNE) FST(5 * pl + c, g[5]); else FST(7 * pl + c + pitch + 1, g[5]);
-      if (nb & kSE) FST(8 * pl + c, g[8]); else FST(6 * pl + c - pitch + 1, g[8]);
+      if (nb & kSE) FST(8 * pl + c, g[8]);
+      else if ((FEAT & kFeatMirror) && (nb & kMirror)) FST(7 * pl + c + 1, g[8]);
+      else FST(6 * pl + c - pitch + 1, g[8]);
     }
     if (!s.inlet) {  // destinations on the west side leave through the inlet
       if (nb & kW) FST(3 * pl + c, g[3]); else FST(1 * pl + c - 1, g[3]);
       if (nb & kNW) FST(6 * pl + c, g[6]); else FST(8 * pl + c + pitch - 1, g[6]);
-      if (nb & kSW) FST(7 * pl + c, g[7]); else FST(5 * pl + c - pitch - 1, g[7]);
+      if (nb & kSW) FST(7 * pl + c, g[7]);
+      else if ((FEAT & kFeatMirror) && (nb & kMirror)) FST(8 * pl + c - 1, g[7]);
+      else FST(5 * pl + c - pitch - 1, g[7]);
     }
   } else {
 #pragma unroll
@@ -440,7 +461,7 @@ __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
 
 // One phase on CPT consecutive segments of the list: their loads are all
 // issued before the first cell is updated (more bytes in flight per thread).
-template <class T, int PHASE, int MOM, int CPT, bool CG, int MODELS = 0>
+template <class T, int PHASE, int MOM, int CPT, bool CG, int FEAT = 0>
 __device__ __forceinline__ void phase_task(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
                                            int nseg, int task, int lane, bool& waited) {
   SegCtx<T> s[CPT];
@@ -448,7 +469,7 @@ __device__ __forceinline__ void phase_task(const LatticeView* __restrict__ views
   for (int k = 0; k < CPT; ++k) {
     const int idx = task * CPT + k;
     const bool valid = CPT == 1 || idx < nseg;  // one segment per task: task < nseg already
-    seg_prologue<T, PHASE>(views, segs[valid ? idx : 0], valid, lane, s[k]);
+    seg_prologue<T, PHASE, FEAT>(views, segs[valid ? idx : 0], valid, lane, s[k]);
   }
   if (!waited) {  // warp-uniform: populations of the previous step are final from here on
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -456,17 +477,18 @@ __device__ __forceinline__ void phase_task(const LatticeView* __restrict__ views
   }
   float g[CPT][9];
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) seg_load<T, PHASE, CG>(s[k], g[k]);
+  for (int k = 0; k < CPT; ++k) seg_load<T, PHASE, CG, FEAT>(s[k], g[k]);
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) seg_update<T, PHASE, MOM, MODELS>(s[k], g[k]);
+  for (int k = 0; k < CPT; ++k) seg_update<T, PHASE, MOM, FEAT>(s[k], g[k]);
 }
 
 // One phase of one time step over the whole segment list.  Launched as a
 // programmatic dependent of the previous step: descriptors, segments and
 // masks are read before waiting for it, populations after.
-// MODELS: 1 if some lattice of the set uses a collision other than BGK (a
-// separate build, so that the BGK kernels keep their register budget).
-template <class T, int PHASE, int MOM, int CPT, int MODELS>
+// FEAT: the features some lattice of the set uses (kFeatModels, kFeatMirror);
+// each combination is a separate build, so that the plain kernels keep their
+// register budget and straight-line loads.
+template <class T, int PHASE, int MOM, int CPT, int FEAT>
 __global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
     k_stream_collide(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
                      const int* __restrict__ n_segs) {
@@ -480,7 +502,7 @@ __global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
   const int stride = gridDim.x * wpb;
   bool waited = false;
   for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntask; t += stride)
-    phase_task<T, PHASE, MOM, CPT, false, MODELS>(views, segs, nseg, t, lane, waited);
+    phase_task<T, PHASE, MOM, CPT, false, FEAT>(views, segs, nseg, t, lane, waited);
   // every thread waits once, so this grid completes only after the previous
   // one (the next step relies on that)
   if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -554,7 +576,7 @@ __device__ __forceinline__ void stage_issue(const LatticeView* __restrict__ view
     cp_async_word<T>(buf + i * 32 + lane, s.F, off, s.fe);
   }
   buf[9 * 32 + lane] = (uint32_t)s.c;
-  buf[10 * 32 + lane] = s.nb | ((uint32_t)s.fluid << 8) | ((uint32_t)s.inlet << 9) | ((uint32_t)s.outlet << 10) |
+  buf[10 * 32 + lane] = s.nb | ((uint32_t)s.fluid << 9) | ((uint32_t)s.inlet << 10) | ((uint32_t)s.outlet << 11) |
                         ((uint32_t)(valid ? sr.lattice : 0) << 12);
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -574,10 +596,10 @@ __device__ __forceinline__ void stage_consume(const LatticeView* __restrict__ vi
   s.omega = L->omega;
   s.rule = L->outlet_rule;
   s.c = (int)buf[9 * 32 + lane];
-  s.nb = fl & 0xffu;
-  s.fluid = (fl >> 8) & 1u;
-  s.inlet = (fl >> 9) & 1u;
-  s.outlet = (fl >> 10) & 1u;
+  s.nb = fl & 0x1ffu;
+  s.fluid = (fl >> 9) & 1u;
+  s.inlet = (fl >> 10) & 1u;
+  s.outlet = (fl >> 11) & 1u;
   s.y = s.inlet ? s.c / s.pitch : 0;  // the inlet rule looks up the row's speed
   float g[9];
 #pragma unroll
@@ -682,12 +704,12 @@ __global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
   }
 }
 
-template <class T, int CPT, int MODELS = 0>
+template <class T, int CPT, int FEAT = 0>
 void* pick(int phase, int moments) {
-  if (phase == 0) return (void*)k_stream_collide<T, 0, 0, CPT, MODELS>;
-  if (moments == 1) return (void*)k_stream_collide<T, 1, 1, CPT, MODELS>;
-  if (moments == 2) return (void*)k_stream_collide<T, 1, 2, CPT, MODELS>;
-  return (void*)k_stream_collide<T, 1, 0, CPT, MODELS>;
+  if (phase == 0) return (void*)k_stream_collide<T, 0, 0, CPT, FEAT>;
+  if (moments == 1) return (void*)k_stream_collide<T, 1, 1, CPT, FEAT>;
+  if (moments == 2) return (void*)k_stream_collide<T, 1, 2, CPT, FEAT>;
+  return (void*)k_stream_collide<T, 1, 0, CPT, FEAT>;
 }
 
 template <class T, int NS>
@@ -699,19 +721,27 @@ void* pick_staged(int phase, int moments) {
 }
 
 template <class T>
-void* pick_cpt(int phase, int moments, int cpt, int stages, int models) {
-  if (models) return cpt == 1 && stages == 0 ? pick<T, 1, 1>(phase, moments) : nullptr;
+void* pick_cpt(int phase, int moments, int cpt, int stages, int features) {
+  if (features) {
+    if (cpt != 1 || stages != 0) return nullptr;
+    switch (features) {
+      case kFeatModels: return pick<T, 1, kFeatModels>(phase, moments);
+      case kFeatMirror: return pick<T, 1, kFeatMirror>(phase, moments);
+      case kFeatModels | kFeatMirror: return pick<T, 1, kFeatModels | kFeatMirror>(phase, moments);
+      default: return nullptr;
+    }
+  }
   if (stages == 2) return cpt == 1 ? pick_staged<T, 2>(phase, moments) : nullptr;
   if (stages == 3) return cpt == 1 ? pick_staged<T, 3>(phase, moments) : nullptr;
   if (stages != 0) return nullptr;
   return cpt == 1 ? pick<T, 1>(phase, moments) : cpt == 2 ? pick<T, 2>(phase, moments) : nullptr;
 }
 
-void* kernel_for(int precision, int phase, int moments, int cpt, int stages, int models) {
+void* kernel_for(int precision, int phase, int moments, int cpt, int stages, int features) {
   switch (precision) {
-    case LBM_F32: return pick_cpt<float>(phase, moments, cpt, stages, models);
-    case LBM_BF16_SHIFTED: return pick_cpt<__nv_bfloat16>(phase, moments, cpt, stages, models);
-    case LBM_F16_SHIFTED: return pick_cpt<__half>(phase, moments, cpt, stages, models);
+    case LBM_F32: return pick_cpt<float>(phase, moments, cpt, stages, features);
+    case LBM_BF16_SHIFTED: return pick_cpt<__nv_bfloat16>(phase, moments, cpt, stages, features);
+    case LBM_F16_SHIFTED: return pick_cpt<__half>(phase, moments, cpt, stages, features);
     default: return nullptr;
   }
 }
@@ -743,7 +773,7 @@ bool shape_ok(const StepConfig& sc) {
   return (sc.cells_per_thread == 1 || sc.cells_per_thread == 2) && sc.warps_per_block >= 1 &&
          sc.warps_per_block * 32 <= max_step_threads(sc.cells_per_thread) && sc.grid >= 1 &&
          (sc.stages == 0 || ((sc.stages == 2 || sc.stages == 3) && sc.cells_per_thread == 1 && !sc.persistent)) &&
-         (!sc.models || (sc.cells_per_thread == 1 && sc.stages == 0 && !sc.persistent));
+         (!sc.features || (sc.cells_per_thread == 1 && sc.stages == 0 && !sc.persistent));
 }
 
 }  // namespace
@@ -751,7 +781,7 @@ bool shape_ok(const StepConfig& sc) {
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
                                   const SegRef* segs, const int* n_segs, StepConfig sc,
                                   cudaStream_t stream) {
-  void* k = kernel_for(precision, phase, moments, sc.cells_per_thread, sc.stages, sc.models);
+  void* k = kernel_for(precision, phase, moments, sc.cells_per_thread, sc.stages, sc.features);
   if (!k || !shape_ok(sc)) return cudaErrorInvalidValue;
   void* args[] = {(void*)&views, (void*)&segs, (void*)&n_segs};
   cudaLaunchAttribute attr[1];
@@ -783,7 +813,7 @@ cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* v
                                              const int* n_segs, int n_pairs, StepConfig sc, StepBarrier* bar,
                                              cudaStream_t stream) {
   void* k = persistent_kernel_for(precision, sc.cells_per_thread);
-  if (!k || !shape_ok(sc) || sc.models || n_pairs < 1 ||
+  if (!k || !shape_ok(sc) || sc.features || n_pairs < 1 ||
       sc.grid > stream_collide_persistent_grid(precision, sc.warps_per_block, sc.cells_per_thread) ||
       2ull * (unsigned long long)n_pairs * (unsigned long long)sc.grid >= (1ull << 32))
     return cudaErrorInvalidValue;
@@ -807,9 +837,9 @@ cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* v
 }
 
 int stream_collide_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int cells_per_thread,
-                                 int stages, int models) {
-  void* k = kernel_for(precision, phase, moments, cells_per_thread, stages, models);
-  StepConfig sc{warps_per_block, 1, 0, cells_per_thread, stages, models};
+                                 int stages, int features) {
+  void* k = kernel_for(precision, phase, moments, cells_per_thread, stages, features);
+  StepConfig sc{warps_per_block, 1, 0, cells_per_thread, stages, features};
   int n = 0;
   if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, launch_smem(k, sc)) !=
                 cudaSuccess)

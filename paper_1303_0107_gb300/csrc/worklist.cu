@@ -33,16 +33,17 @@ __global__ void k_unpack_mask(const uint32_t* __restrict__ mask, int nx, int ny,
   cells[i] = (mask[(long long)y * mask_stride(wpr) + (x >> 5)] >> (x & 31)) & 1u;
 }
 
-// Interior-row words of all lattices in one index space: word i belongs to
-// lattice l = find_lattice(seg_word_off, n, i), row 1 + (i - off) / wpr.
+// Step-row words of all lattices in one index space: word i belongs to
+// lattice l = find_lattice(seg_word_off, n, i), row first_step_row + (i - off) / wpr.
 __device__ __forceinline__ void seg_word(const LatticeView* __restrict__ views,
                                          const int* __restrict__ seg_word_off, int n, int i, int& l,
                                          int& y, int& w) {
   l = find_lattice(seg_word_off, n, i);
   const int wpr = views[l].wpr;
   const int local = i - seg_word_off[l];
-  y = 1 + local / wpr;
-  w = local - (y - 1) * wpr;
+  const int r = local / wpr;
+  y = first_step_row(views[l]) + r;
+  w = local - r * wpr;
 }
 
 // 1 for every row segment (row y in 1..ny-2, word w) holding a fluid cell

@@ -23,7 +23,7 @@ FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_MASK, FIELD_POPS, FIELD_DRHO = 1, 2, 4, 8, 
 MAX_OUTLETS = 64
 PRECISIONS = {"f32": F32, "bf16": BF16_SHIFTED, "f16": F16_SHIFTED}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_GEOMETRY", 3: "LBM_ERR_OOM", 4: "LBM_ERR_CUDA",
-          5: "LBM_ERR_DIVERGED", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_BUSY"}
+          5: "LBM_ERR_DIVERGED", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_BUSY", 8: "LBM_ERR_CANCELLED"}
 
 
 class LbmError(RuntimeError):
@@ -37,14 +37,14 @@ class Params(ctypes.Structure):
                 ("rho0", ctypes.c_double), ("u_max", ctypes.c_double), ("outlet", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("reinit", ctypes.c_int32),
                 ("residual_every", ctypes.c_int32), ("ports", ctypes.c_int32), ("guard", ctypes.c_int32),
-                ("collision", ctypes.c_int32), ("reserved", ctypes.c_int32), ("c_smag", ctypes.c_double)]
+                ("collision", ctypes.c_int32), ("mirror", ctypes.c_int32), ("c_smag", ctypes.c_double)]
 
 
 def make_params(nx, ny, tau, u_max, rho0=1.0, outlet=0, precision=0, reinit=0, residual_every=0, ports=0,
-                guard=False, collision=0, c_smag=0.0):
+                guard=False, collision=0, c_smag=0.0, mirror=False):
     return Params(int(nx), int(ny), float(tau), float(rho0), float(u_max), int(outlet), int(precision),
-                  int(reinit), int(residual_every), int(ports), int(bool(guard)), int(collision), 0,
-                  float(c_smag))
+                  int(reinit), int(residual_every), int(ports), int(bool(guard)), int(collision),
+                  int(bool(mirror)), float(c_smag))
 
 
 class SolveResult(ctypes.Structure):
@@ -170,6 +170,9 @@ def load_library(path=None):
     L.lbm_server_now.restype = ctypes.c_double
     L.lbm_server_footprint.argtypes = [ctypes.POINTER(Params), ctypes.c_int32]
     L.lbm_server_footprint.restype = ctypes.c_int64
+    L.lbm_server_cancel.argtypes = [S, ctypes.c_int64]
+    L.lbm_debug_fail_alloc.argtypes = [ctypes.c_int64]
+    L.lbm_debug_fail_alloc.restype = None
     L.lbm_server_destroy.argtypes = [S]
     L.lbm_server_destroy.restype = None
     L.lbm_bytes_per_fluid_update.argtypes = [ctypes.c_int32]
@@ -179,7 +182,7 @@ def load_library(path=None):
                  "lbm_select_swaps_noalloc", "lbm_step_config", "lbm_set_step_config", "lbm_batch_create", "lbm_batch_solve",
                  "lbm_batch_optimize_step", "lbm_batch_read_fields", "lbm_batch_reset",
                  "lbm_batch_kernel_time", "lbm_batch_step_config", "lbm_batch_set_step_config", "lbm_server_create", "lbm_server_submit",
-                 "lbm_server_wait_idle", "lbm_server_get_stats"):
+                 "lbm_server_wait_idle", "lbm_server_get_stats", "lbm_server_cancel"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -188,6 +191,11 @@ def load_library(path=None):
 def _check(st, where):
     if st != 0:
         raise LbmError(st, where, load_library().lbm_last_error().decode())
+
+
+def debug_fail_alloc(after: int) -> None:
+    """Make the device allocation after `after` more successful ones fail (test hook; -1: off)."""
+    load_library().lbm_debug_fail_alloc(int(after))
 
 
 def kernel_launches() -> int:
@@ -221,14 +229,14 @@ class Lattice:
 
     def __init__(self, cells, tau, u_max, rho0=1.0, outlet=OUT_CONST_RHO, precision=F32,
                  reinit=REINIT_WARM, residual_every=100, stream=None, ports=PORTS_REGULARIZED, guard=False,
-                 collision=COLLIDE_BGK, c_smag=0.0):
+                 collision=COLLIDE_BGK, c_smag=0.0, mirror=False):
         L = load_library()
         cells = np.ascontiguousarray(cells, dtype=np.uint8)
         ny, nx = cells.shape
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         self.params = make_params(nx, ny, tau, u_max, rho0, outlet, precision, reinit, residual_every, ports,
-                                  guard, collision, c_smag)
+                                  guard, collision, c_smag, mirror)
         self.nx, self.ny, self.precision = nx, ny, int(precision)
         self._h = _VP()
         _check(L.lbm_create_geometry(ctypes.byref(self.params), cells.ctypes.data, _stream_ptr(stream),
@@ -353,7 +361,7 @@ class Batch:
             params[i] = make_params(nx, ny, m["tau"], m["u_max"], m.get("rho0", 1.0), m.get("outlet", OUT_CONST_RHO),
                                     precision, m.get("reinit", REINIT_WARM), residual_every,
                                     m.get("ports", PORTS_REGULARIZED), m.get("guard", False),
-                                    m.get("collision", COLLIDE_BGK), m.get("c_smag", 0.0))
+                                    m.get("collision", COLLIDE_BGK), m.get("c_smag", 0.0), m.get("mirror", False))
         ptrs = (ctypes.c_void_p * self.n)(*[c.ctypes.data for c in self._cells])
         self._b = _VP()
         _check(L.lbm_batch_create(self.n, params, ptrs, _stream_ptr(stream), ctypes.byref(self._b)),
@@ -450,9 +458,10 @@ class Server:
 
     @staticmethod
     def params_for(cells, tau, u_max, precision=F32, rho0=1.0, outlet=OUT_CONST_RHO, reinit=REINIT_WARM,
-                   ports=PORTS_REGULARIZED, guard=False, collision=COLLIDE_BGK, c_smag=0.0):
+                   ports=PORTS_REGULARIZED, guard=False, collision=COLLIDE_BGK, c_smag=0.0, mirror=False):
         ny, nx = np.asarray(cells).shape
-        return make_params(nx, ny, tau, u_max, rho0, outlet, precision, reinit, 0, ports, guard, collision, c_smag)
+        return make_params(nx, ny, tau, u_max, rho0, outlet, precision, reinit, 0, ports, guard, collision, c_smag,
+                           mirror)
 
     @staticmethod
     def footprint(nx, ny, n_iter=0, precision=F32):
@@ -489,6 +498,9 @@ class Server:
                 d["fields"] = f
             out.append(d)
         return out
+
+    def cancel(self, tag):
+        _check(load_library().lbm_server_cancel(self._s, int(tag)), "lbm_server_cancel")
 
     def wait_idle(self, timeout_s=600.0):
         _check(load_library().lbm_server_wait_idle(self._s, int(timeout_s * 1000)), "lbm_server_wait_idle")

@@ -56,6 +56,8 @@ def test_host_only_entry_points(built_lib):
     odd = lib.ServerConfig(lib.F32, 4, 0, 101, 0)  # odd tick
     assert L.lbm_server_create(ctypes.byref(odd), None, ctypes.byref(srv)) == 1
     L.lbm_server_destroy(None)
+    assert L.lbm_server_cancel(None, 1) == 1
+    L.lbm_debug_fail_alloc(-1)  # host-only switch
     small = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05)), 0)
     opt = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05)), 5)
     half = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05, precision=1)), 0)
@@ -78,7 +80,7 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
     from paper_1303_0107_gb300 import lib
     if not shutil.which("gcc"):
         pytest.skip("no gcc")
-    checks = [("lbm_params", lib.Params, ["tau", "ports", "guard", "collision", "c_smag"]),
+    checks = [("lbm_params", lib.Params, ["tau", "ports", "guard", "collision", "mirror", "c_smag"]),
               ("lbm_solve_result", lib.SolveResult, ["m_out", "fluid_cells"]),
               ("lbm_opt_result", lib.OptResult, ["solve"]),
               ("lbm_server_config", lib.ServerConfig, ["hbm_budget_bytes", "max_tick_steps"]),

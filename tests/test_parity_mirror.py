@@ -1,0 +1,92 @@
+"""The symmetry plane below row 0 on the GPU: against the FP64 oracle's
+mirror rule, against the GPU's own run of the whole symmetric domain, and
+through the optimiser on the paper's half-domain collector."""
+import numpy as np
+import pytest
+
+import paper_1303_0107_gb300 as L
+from paper_1303_0107_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    L.load_library()
+
+
+def _half_channel(nx=96, ny=24, w=8):
+    cells = np.ones((ny, nx), np.uint8)
+    cells[0:w, :] = 0
+    cells[3:6, 40:44] = 1  # an obstacle near the plane
+    return cells
+
+
+@pytest.mark.parametrize("outlet", [L.OUT_CONST_RHO, L.OUT_NEUMANN])
+@pytest.mark.parametrize("ports", [L.PORTS_REGULARIZED, L.PORTS_ZOU_HE])
+def test_mirror_matches_oracle(ora, outlet, ports):
+    for cells, tau, u, steps in ((_half_channel(), 0.7, 0.04, 600), (I.config_collector()["cells"], 0.62, 0.12, 400)):
+        ny, nx = cells.shape
+        lat = L.Lattice(cells, tau, u, outlet=outlet, ports=ports, residual_every=0, mirror=True)
+        g = lat.solve(steps)
+        p = ora.make_params(nx, ny, tau, 1.0, u, outlet_rule=outlet, port_scheme=ports, mirror=True)
+        s = ora.Solver(p, cells, residual_every=0)
+        o = s.solve(steps)
+        ux = lat.read(L.FIELD_UX).astype(np.float64)
+        uy = lat.read(L.FIELD_UY).astype(np.float64)
+        scale = np.abs(s.ux).max()
+        assert np.abs(ux - s.ux).max() <= TOL * scale
+        assert np.abs(uy - s.uy).max() <= TOL * scale
+        drho = lat.read(L.FIELD_DRHO).astype(np.float64)
+        ref = (s.rho - 1.0) * (cells == 0)
+        assert np.abs(drho - ref).max() <= TOL * np.abs(ref).max()
+        assert abs(g["dp"] - o["dp"]) <= TOL * abs(o["dp"])
+        lat.close()
+
+
+def test_half_domain_equals_upper_half_of_whole_domain():
+    nx, ny = 160, 64
+    full = I.tree(nx, ny, 2, 16, ratio=0.5, jitter=0, seed=0)
+    half = full[ny // 2:].copy()
+    a = L.Lattice(full, 0.7, 0.04, residual_every=0)
+    b = L.Lattice(half, 0.7, 0.04, residual_every=0, mirror=True)
+    ra, rb = a.solve(600), b.solve(600)
+    ux_a, ux_b = a.read(L.FIELD_UX), b.read(L.FIELD_UX)
+    scale = np.abs(ux_a).max()
+    assert np.abs(ux_a[ny // 2:] - ux_b).max() <= TOL * scale  # FP32, sums in other orders
+    assert abs(ra["dp"] - rb["dp"]) <= TOL * abs(ra["dp"])
+    a.close()
+    b.close()
+
+
+def test_mirror_optimisation_selection_bit_exact(ora):
+    c = I.config_collector()
+    cells = c["cells"]
+    ny, nx = cells.shape
+    lat = L.Lattice(cells, c["tau"], c["u_max"], outlet=c["outlet"], residual_every=0, mirror=True)
+    lat.solve(400)
+    p = ora.make_params(nx, ny, c["tau"], 1.0, c["u_max"], outlet_rule=c["outlet"], mirror=True)
+    for _ in range(3):
+        drho, ux, uy = lat.read(L.FIELD_DRHO), lat.read(L.FIELD_UX), lat.read(L.FIELD_UY)
+        cand, score = ora.scores(p, lat.read(L.FIELD_MASK), 1.0 + drho.astype(np.float64), ux.astype(np.float64),
+                                 uy.astype(np.float64))
+        fo, so = ora.select(p, cand, score, 60)
+        fi, si = lat.select_swaps(drho, ux, uy, 60)
+        assert np.array_equal(fi, fo) and np.array_equal(si, so)
+        r = lat.optimize_step(60, 400)
+        assert r["fluid_count"] == int((cells == 0).sum())
+        mask = lat.read(L.FIELD_MASK)
+        assert np.array_equal(mask[0], cells[0]) and mask[-1].all()  # the plane row and the wall never move
+    lat.close()
+
+
+def test_mirror_row_zero_requires_the_flag():
+    cells = _half_channel()
+    with pytest.raises(L.LbmError) as e:
+        L.Lattice(cells, 0.7, 0.04)
+    assert e.value.status == 2

@@ -34,9 +34,13 @@ def _cases():
     ]
 
 
+def _mirror_case():
+    return dict(cells=I.config_collector()["cells"], tau=0.62, u_max=0.12, outlet=L.OUT_NEUMANN, mirror=True)
+
+
 def _handle(case, precision, persistent, wpb=8, cpt=1, stages=0):
     h = L.Lattice(case["cells"], case["tau"], case["u_max"], precision=precision, outlet=case.get("outlet", 0),
-                  ports=case.get("ports", 0), residual_every=100)
+                  ports=case.get("ports", 0), residual_every=100, mirror=case.get("mirror", False))
     h.set_step_config(wpb, persistent=persistent, cells_per_thread=cpt, stages=stages)
     return h
 
@@ -86,6 +90,32 @@ def test_persistent_tree_2048_matches_oracle(ora):
     assert np.abs(uy - s.uy).max() / np.abs(s.ux).max() <= 1e-5
     assert abs(g["dp"] - o["dp"]) <= 1e-5 * abs(o["dp"])
     h.close()
+
+
+@pytest.mark.parametrize("wpb", [4, 16])
+def test_feature_builds_keep_values_across_shapes(wpb):
+    """Lattices with a symmetry plane or a collision model run the feature
+    builds (plain shapes only): every block shape gives the same values, and
+    in a batch with plain lattices each member equals its run alone."""
+    m = _mirror_case()
+    a = _handle(m, L.F32, False)
+    b = _handle(m, L.F32, False, wpb=wpb)
+    assert a.solve(600)["dp"] == b.solve(600)["dp"]
+    assert np.array_equal(a.read(L.FIELD_POPS), b.read(L.FIELD_POPS))
+    with pytest.raises(L.LbmError):
+        b.set_step_config(8, persistent=True)
+    members = _cases()[:2] + [m]
+    bt = L.Batch(members, residual_every=0)
+    rb = bt.solve(400)
+    for i, mm in enumerate(members):
+        h = L.Lattice(mm["cells"], mm["tau"], mm["u_max"], outlet=mm.get("outlet", 0), residual_every=0,
+                      mirror=mm.get("mirror", False))
+        assert h.solve(400)["dp"] == rb[i]["dp"]
+        assert np.array_equal(h.read(L.FIELD_POPS), bt.read(i, L.FIELD_POPS)), i
+        h.close()
+    a.close()
+    b.close()
+    bt.close()
 
 
 @pytest.mark.parametrize("shape", [(8, 2, 0), (8, 1, 3)])

@@ -232,3 +232,16 @@ def test_reduced_precision_storage_error_reported(ora, prec):
     rel = abs(g["dp"] - o["dp"]) / abs(o["dp"])
     print(f"{prec}: relative dp error {rel:.3e}")
     assert np.isfinite(g["dp"]) and rel < 0.5
+
+
+def test_failed_allocation_is_reported_and_recoverable():
+    cfg = I.config_t_junction()
+    for after in (0, 1, 3):
+        L.lib.debug_fail_alloc(after)
+        with pytest.raises(L.LbmError) as e:
+            L.Lattice(cfg["cells"], cfg["tau"], cfg["u_max"])
+        assert e.value.status == 3  # LBM_ERR_OOM
+    L.lib.debug_fail_alloc(-1)
+    lat = L.Lattice(cfg["cells"], cfg["tau"], cfg["u_max"])
+    assert np.isfinite(lat.solve(100)["dp"])
+    lat.close()

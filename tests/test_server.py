@@ -157,3 +157,44 @@ def test_submit_errors():
         L.lib._check(L.load_library().lbm_server_submit(srv._s, r), "lbm_server_submit")
     assert srv.stats()["submitted"] == 0
     srv.close()
+
+
+def test_cancel_queued_and_resident_requests():
+    reqs = _requests(5, 900, n_steps=400)
+    reqs[0]["n_steps"] = 400000  # long enough to be resident when it is withdrawn
+    srv = L.Server(precision=L.F32, max_active=1, max_tick_steps=200)
+    for q in reqs:
+        srv.submit(q["tag"], q["cells"], q["tau"], q["u_max"], q["n_steps"], n_iter=q["n_iter"], n_swap=q["n_swap"])
+    srv.cancel(reqs[3]["tag"])  # queued behind the long one
+    t0 = time.time()
+    while srv.stats()["admitted"] < 1 and time.time() - t0 < 30:
+        time.sleep(0.005)
+    srv.cancel(reqs[0]["tag"])  # resident: withdrawn at the next tick boundary
+    with pytest.raises(L.LbmError):
+        srv.cancel(123456789)
+    srv.wait_idle(300)
+    done = {d["tag"]: d for d in srv.poll(64)}
+    srv.close()
+    assert len(done) == 5
+    assert done[reqs[3]["tag"]]["status"] == 8 and done[reqs[0]["tag"]]["status"] == 8
+    assert done[reqs[0]["tag"]]["fluid_updates"] < int((reqs[0]["cells"] == 0).sum()) * 400000
+    for k in (1, 2, 4):
+        assert done[reqs[k]["tag"]]["status"] == 0
+        _, last, _, _ = _alone(reqs[k], L.F32)
+        assert done[reqs[k]["tag"]]["last"]["dp"] == last["dp"]
+
+
+def test_failed_allocation_fails_only_its_request():
+    reqs = _requests(3, 950, n_steps=200)
+    srv = L.Server(precision=L.F32, max_active=4, max_tick_steps=100)
+    L.lib.debug_fail_alloc(0)  # the next device allocation: the first request's storage
+    for q in reqs:
+        srv.submit(q["tag"], q["cells"], q["tau"], q["u_max"], q["n_steps"])
+    srv.wait_idle(300)
+    L.lib.debug_fail_alloc(-1)
+    done = {d["tag"]: d for d in srv.poll(64)}
+    st = srv.stats()
+    srv.close()
+    assert done[reqs[0]["tag"]]["status"] == 3  # LBM_ERR_OOM
+    assert [done[q["tag"]]["status"] for q in reqs[1:]] == [0, 0]
+    assert st["failed"] == 1 and st["resident_bytes"] == 0
