@@ -160,16 +160,22 @@ def config_collector():
     cells on column 0 (sixteen in the whole domain), one outlet of 52 cells
     on column 359 against the plane (104 in the whole domain), joined by a
     four-generation binary tree with Eq. 7's 2:2:1:1 segment lengths and
-    widths shrinking by (11/104)^(1/4) per generation; parabolic inlets of
-    mean speed 0.08 (u_max 0.12), zero-gradient outlet, rho0 = 1, nu = 0.04
-    (tau = 0.62): Re = 11 * 0.08 / 0.04 = 22."""
+    widths shrinking by (11/104)^(1/4) per generation; parabolic inlets,
+    rho0 = 1, and the paper's inlet Reynolds number Re = W_in u_in / nu = 22.
+    The paper's lattice values (nu = 0.04, mean inlet speed 0.08) diverge on
+    this geometry in both the oracle and the GPU path (density swings of a
+    third within 2000 steps), so the same Re is taken at nu = 0.01
+    (tau = 0.53) and a mean inlet speed of 0.02 (u_max 0.03).  The paper's
+    zero-gradient outlet leaves the density level free: over the 151
+    optimisation steps it climbs by an order of one (measured), so the
+    outlet holds rho0 instead."""
     nx, ny_full = 360, 360
     ratio = (11.0 / 104.0) ** 0.25
     full = tree(nx, ny_full, 4, 104, ratio=ratio, jitter=0, seed=0)
     collector = full[:, ::-1]            # branches on column 0, trunk on column nx-1
     half = np.ascontiguousarray(collector[ny_full // 2:, :])  # rows above the plane
-    return dict(name="collector_360x180_half", cells=half, nx=nx, ny=ny_full // 2, tau=0.62, u_max=0.12,
-                outlet=1, mirror=True, n_iter=151)
+    return dict(name="collector_360x180_half", cells=half, nx=nx, ny=ny_full // 2, tau=0.53, u_max=0.03,
+                outlet=0, mirror=True, n_iter=151)
 
 
 def config_candidates(n: int = 256, base_seed: int = 0):

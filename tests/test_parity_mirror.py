@@ -30,7 +30,8 @@ def _half_channel(nx=96, ny=24, w=8):
 @pytest.mark.parametrize("outlet", [L.OUT_CONST_RHO, L.OUT_NEUMANN])
 @pytest.mark.parametrize("ports", [L.PORTS_REGULARIZED, L.PORTS_ZOU_HE])
 def test_mirror_matches_oracle(ora, outlet, ports):
-    for cells, tau, u, steps in ((_half_channel(), 0.7, 0.04, 600), (I.config_collector()["cells"], 0.62, 0.12, 400)):
+    c = I.config_collector()
+    for cells, tau, u, steps in ((_half_channel(), 0.7, 0.04, 600), (c["cells"], c["tau"], c["u_max"], 600)):
         ny, nx = cells.shape
         lat = L.Lattice(cells, tau, u, outlet=outlet, ports=ports, residual_every=0, mirror=True)
         g = lat.solve(steps)
