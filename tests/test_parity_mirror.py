@@ -27,27 +27,36 @@ def _half_channel(nx=96, ny=24, w=8):
     return cells
 
 
+def _compare(ora, cells, tau, u, steps, outlet, ports):
+    ny, nx = cells.shape
+    lat = L.Lattice(cells, tau, u, outlet=outlet, ports=ports, residual_every=0, mirror=True)
+    g = lat.solve(steps)
+    p = ora.make_params(nx, ny, tau, 1.0, u, outlet_rule=outlet, port_scheme=ports, mirror=True)
+    s = ora.Solver(p, cells, residual_every=0)
+    o = s.solve(steps)
+    ux = lat.read(L.FIELD_UX).astype(np.float64)
+    uy = lat.read(L.FIELD_UY).astype(np.float64)
+    scale = np.abs(s.ux).max()
+    assert np.abs(ux - s.ux).max() <= TOL * scale
+    assert np.abs(uy - s.uy).max() <= TOL * scale
+    drho = lat.read(L.FIELD_DRHO).astype(np.float64)
+    ref = (s.rho - 1.0) * (cells == 0)
+    assert np.abs(drho - ref).max() <= TOL * np.abs(ref).max()
+    assert abs(g["dp"] - o["dp"]) <= TOL * abs(o["dp"])
+    lat.close()
+
+
 @pytest.mark.parametrize("outlet", [L.OUT_CONST_RHO, L.OUT_NEUMANN])
 @pytest.mark.parametrize("ports", [L.PORTS_REGULARIZED, L.PORTS_ZOU_HE])
-def test_mirror_matches_oracle(ora, outlet, ports):
+def test_mirror_matches_oracle_half_channel(ora, outlet, ports):
+    _compare(ora, _half_channel(), 0.7, 0.04, 600, outlet, ports)
+
+
+@pytest.mark.parametrize("ports", [L.PORTS_REGULARIZED, L.PORTS_ZOU_HE])
+def test_mirror_matches_oracle_collector(ora, ports):
+    """The paper's half-domain collector as configured (outlet at rho0)."""
     c = I.config_collector()
-    for cells, tau, u, steps in ((_half_channel(), 0.7, 0.04, 600), (c["cells"], c["tau"], c["u_max"], 600)):
-        ny, nx = cells.shape
-        lat = L.Lattice(cells, tau, u, outlet=outlet, ports=ports, residual_every=0, mirror=True)
-        g = lat.solve(steps)
-        p = ora.make_params(nx, ny, tau, 1.0, u, outlet_rule=outlet, port_scheme=ports, mirror=True)
-        s = ora.Solver(p, cells, residual_every=0)
-        o = s.solve(steps)
-        ux = lat.read(L.FIELD_UX).astype(np.float64)
-        uy = lat.read(L.FIELD_UY).astype(np.float64)
-        scale = np.abs(s.ux).max()
-        assert np.abs(ux - s.ux).max() <= TOL * scale
-        assert np.abs(uy - s.uy).max() <= TOL * scale
-        drho = lat.read(L.FIELD_DRHO).astype(np.float64)
-        ref = (s.rho - 1.0) * (cells == 0)
-        assert np.abs(drho - ref).max() <= TOL * np.abs(ref).max()
-        assert abs(g["dp"] - o["dp"]) <= TOL * abs(o["dp"])
-        lat.close()
+    _compare(ora, c["cells"], c["tau"], c["u_max"], 600, c["outlet"], ports)
 
 
 def test_half_domain_equals_upper_half_of_whole_domain():
