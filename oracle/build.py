@@ -9,17 +9,17 @@ import pathlib
 import subprocess
 
 HERE = pathlib.Path(__file__).resolve().parent
-SRC = HERE / "lbm_oracle.c"
+SRCS = [HERE / "lbm_oracle.c", HERE / "lbm3d_oracle.c"]
 LIB = HERE / "liblbm_oracle.so"
 
 
 def build(force: bool = False) -> pathlib.Path:
-    if not force and LIB.exists() and LIB.stat().st_mtime >= SRC.stat().st_mtime:
+    if not force and LIB.exists() and all(LIB.stat().st_mtime >= s.stat().st_mtime for s in SRCS):
         return LIB
     cc = os.environ.get("CC", "gcc")
     tmp = LIB.with_suffix(f".so.tmp{os.getpid()}")
     cmd = [cc, "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-fPIC", "-shared", str(SRC), "-o", str(tmp), "-lm"]
+           "-fPIC", "-shared", *[str(s) for s in SRCS], "-o", str(tmp), "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
