@@ -1,0 +1,593 @@
+// D3Q19 form of the hot path: fused stream + collide on a single lattice
+// (AA access pattern), the FP64 port reductions, and the exchange of Sec.
+// 2.2-2.3 on the 6-neighbourhood.
+//
+// Storage.  Populations shifted, g_i = f_i - w_i rho0, in 19 planes
+// F[i][z][y][x] (row pitch nxp = 32 nsx), FP32, BF16 or FP16; FP32
+// arithmetic.  Between steps F[i][cell] is the post-collision g_i of the
+// cell.  Steps come in pairs, as in 2D:
+//   phase A  cell x takes g_i from F[i][x - c_i] (or, where x - c_i is
+//            solid, the reversed F[opp(i)][x]), relaxes, and writes g_i to
+//            F[opp(i)][x + c_i] -- the slot it read for direction opp(i) --
+//            or, where x + c_i is solid, to F[i][x];
+//   phase B  cell x finds its incoming g_i in F[opp(i)][x], relaxes, writes
+//            F[i][x].
+// Each slot is read and then written by one thread per phase: one lattice,
+// no barrier, solid cells never read.
+//
+// Thread mapping.  A warp takes one row segment (32 cells of one mask word,
+// row (y, z)) from a device-resident list of the segments holding fluid;
+// lane l is cell 32 s + l.  Lanes 0..26 load the 27 mask words around the
+// segment (rows y-1..y+1 x z-1..z+1, words s-1..s+1) in one instruction and
+// the warp shares them by shuffles: no per-cell neighbour table in memory.
+// Each population access of a warp is one contiguous 32-element row piece,
+// shifted by at most one element.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm3d_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr int kQ = 19;
+
+// D3Q19 velocity set (the order of include/lbm3d.h); opposites are (1,2),
+// (3,4), ..., (17,18).  Called with loop indices of unrolled loops, these
+// fold to constants.
+__host__ __device__ constexpr int cx3(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy3(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz3(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp3(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr float w3(int i) { return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f); }
+// c * v for c in {-1, 0, 1} without a multiply (0 * v is not 0 for v = inf/NaN)
+__device__ __forceinline__ float cmul(int c, float v) { return c == 0 ? 0.0f : (c > 0 ? v : -v); }
+
+template <class T>
+struct P3;
+template <>
+struct P3<float> {
+  static __device__ __forceinline__ float ld(const float* p) { return *p; }
+  static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <>
+struct P3<__nv_bfloat16> {
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <>
+struct P3<__half> {
+  static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+  static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+
+// Shifted second-order equilibrium g^eq_i = f^eq_i(rho0 + drho, u) - w_i rho0
+//   = w_i (t0 + 3 rho c.u + 4.5 rho (c.u)^2),  t0 = drho - 1.5 rho u.u.
+__device__ __forceinline__ float geq3(int i, float rho, float t0, float ux, float uy, float uz) {
+  const float cu = cmul(cx3(i), ux) + cmul(cy3(i), uy) + cmul(cz3(i), uz);
+  return w3(i) * (t0 + 3.0f * rho * cu + 4.5f * rho * cu * cu);
+}
+
+// Relax a pair of opposite directions towards their equilibria (c_o = -c_i).
+__device__ __forceinline__ void relax_pair3(float& gi, float& go, float cu, float w, float rho, float t0,
+                                            float omega) {
+  const float a = 3.0f * rho * cu;
+  const float b = 4.5f * rho * cu * cu;
+  gi += omega * (w * (t0 + a + b) - gi);
+  go += omega * (w * (t0 - a + b) - go);
+}
+
+// Rounded FP32 relaxation drifts in mass and momentum over thousands of
+// steps; BGK conserves both exactly, so restore them: g1, g3, g5 carry the
+// three momentum balances, the rest population the mass balance.
+__device__ __forceinline__ void close_moments3(float (&g)[kQ], float drho, float jx, float jy, float jz) {
+  g[1] = jx + g[2] - (((g[7] - g[8]) + (g[9] - g[10])) + ((g[11] - g[12]) + (g[13] - g[14])));
+  g[3] = jy + g[4] - (((g[7] - g[8]) + (g[10] - g[9])) + ((g[15] - g[16]) + (g[17] - g[18])));
+  g[5] = jz + g[6] - (((g[11] - g[12]) + (g[14] - g[13])) + ((g[15] - g[16]) + (g[18] - g[17])));
+  float s = 0.0f;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) s += g[i];
+  g[0] = drho - s;
+}
+
+__device__ __forceinline__ void moments3(const float (&g)[kQ], float& drho, float& jx, float& jy, float& jz) {
+  float s = g[0];
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) s += g[i];
+  drho = s;
+  jx = ((g[1] - g[2]) + (g[7] - g[8])) + ((g[9] - g[10]) + (g[11] - g[12])) + (g[13] - g[14]);
+  jy = ((g[3] - g[4]) + (g[7] - g[8])) + ((g[10] - g[9]) + (g[15] - g[16])) + (g[17] - g[18]);
+  jz = ((g[5] - g[6]) + (g[11] - g[12])) + ((g[14] - g[13]) + (g[15] - g[16])) + (g[18] - g[17]);
+}
+
+// Moments and BGK relaxation of one cell, in place.
+__device__ __forceinline__ void bgk3(float (&g)[kQ], float rho0, float omega, float& drho, float& ux, float& uy,
+                                     float& uz) {
+  float jx, jy, jz;
+  moments3(g, drho, jx, jy, jz);
+  const float rho = rho0 + drho;
+  const float inv = 1.0f / rho;
+  ux = jx * inv;
+  uy = jy * inv;
+  uz = jz * inv;
+  const float t0 = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
+  g[0] += omega * (w3(0) * t0 - g[0]);
+  constexpr float wf = 1.0f / 18.0f, we = 1.0f / 36.0f;
+  relax_pair3(g[1], g[2], ux, wf, rho, t0, omega);
+  relax_pair3(g[3], g[4], uy, wf, rho, t0, omega);
+  relax_pair3(g[5], g[6], uz, wf, rho, t0, omega);
+  relax_pair3(g[7], g[8], ux + uy, we, rho, t0, omega);
+  relax_pair3(g[9], g[10], ux - uy, we, rho, t0, omega);
+  relax_pair3(g[11], g[12], ux + uz, we, rho, t0, omega);
+  relax_pair3(g[13], g[14], ux - uz, we, rho, t0, omega);
+  relax_pair3(g[15], g[16], uy + uz, we, rho, t0, omega);
+  relax_pair3(g[17], g[18], uy - uz, we, rho, t0, omega);
+  close_moments3(g, drho, jx, jy, jz);
+}
+
+// Port cell (x = 0 inlet, x = nx-1 outlet).  Known sums: G0 over c_x = 0,
+// Gk over the directions arriving from inside (c_x < 0 at the inlet, > 0 at
+// the outlet).  With sum_{c_x=0} w = 2/3 and sum_{c_x<0} w = 1/6:
+//   inlet   u = u_in,  rho - rho0 = (G0 + 2 Gk + rho0 u) / (1 - u);
+//   outlet  rho = rho0, u = (G0 + 2 Gk) / rho0;
+// unknown populations g_i = g^eq_i + (g_opp(i) - g^eq_opp(i)); then every
+// population is regularised, g_i = g^eq_i + 4.5 w_i Q_i : Pi with
+// Pi = sum c c (g - g^eq), Q_i = c_i c_i - I/3 (w_i / (2 c_s^4) = 4.5 w_i).
+__device__ __forceinline__ void port3(float (&g)[kQ], bool inlet, float u_in, float rho0) {
+  float G0 = g[0] + ((g[3] + g[4]) + (g[5] + g[6])) + ((g[15] + g[16]) + (g[17] + g[18]));
+  float dr, u;
+  if (inlet) {
+    const float Gk = (g[2] + g[8]) + (g[10] + g[12]) + g[14];
+    u = u_in;
+    dr = (G0 + 2.0f * Gk + rho0 * u) / (1.0f - u);
+  } else {
+    const float Gk = (g[1] + g[7]) + (g[9] + g[11]) + g[13];
+    u = (G0 + 2.0f * Gk) / rho0;
+    dr = 0.0f;
+  }
+  const float rho = rho0 + dr;
+  const float t0 = dr - 1.5f * rho * u * u;
+  float e[kQ];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) e[i] = geq3(i, rho, t0, u, 0.0f, 0.0f);
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const bool unknown = inlet ? cx3(i) > 0 : cx3(i) < 0;
+    if (unknown) g[i] = e[i] + (g[opp3(i)] - e[opp3(i)]);
+  }
+  float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const float nq = g[i] - e[i];
+    if (cx3(i) != 0) pxx += nq;
+    if (cy3(i) != 0) pyy += nq;
+    if (cz3(i) != 0) pzz += nq;
+    pxy += cmul(cx3(i) * cy3(i), nq);
+    pxz += cmul(cx3(i) * cz3(i), nq);
+    pyz += cmul(cy3(i) * cz3(i), nq);
+  }
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const float qxx = (float)(cx3(i) * cx3(i)) - 1.0f / 3.0f;
+    const float qyy = (float)(cy3(i) * cy3(i)) - 1.0f / 3.0f;
+    const float qzz = (float)(cz3(i) * cz3(i)) - 1.0f / 3.0f;
+    const float q = qxx * pxx + qyy * pyy + qzz * pzz +
+                    2.0f * (cmul(cx3(i) * cy3(i), pxy) + cmul(cx3(i) * cz3(i), pxz) + cmul(cy3(i) * cz3(i), pyz));
+    g[i] = e[i] + 4.5f * w3(i) * q;
+  }
+}
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <class T, int PHASE, int MOM>
+__global__ void __launch_bounds__(512) k_step3(const View3 v, const int* __restrict__ segs,
+                                               const int* __restrict__ n_segs) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  if (warp >= *n_segs) return;  // whole warps leave together
+  const int seg = segs[warp];
+  const int row = seg / v.nsx;
+  const int s = seg - row * v.nsx;
+  const int z = row / v.ny;
+  const int y = row - z * v.ny;
+  // lanes 0..8: word s of row r = (dz+1)*3 + (dy+1); 9..17: word s-1; 18..26: word s+1
+  uint32_t wv = 0xffffffffu;
+  if (lane < 27) {
+    const int part = lane / 9, r = lane - 9 * part;
+    const int dy = r % 3 - 1, dz = r / 3 - 1;
+    const int dw = part == 0 ? 0 : (part == 1 ? -1 : 1);
+    wv = v.mask[mask3_row(v.ny, v.ms, y + dy, z + dz) + 1 + s + dw];
+  }
+  uint32_t M[9], Lw[9], H[9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    M[r] = __shfl_sync(kFull, wv, r);
+    Lw[r] = __shfl_sync(kFull, wv, 9 + r);
+    H[r] = __shfl_sync(kFull, wv, 18 + r);
+  }
+  if ((M[4] >> lane) & 1u) return;  // solid (or past the row's end)
+  uint32_t nb = 0;                  // bit i: cell x + c_i is solid
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const int r = (cz3(i) + 1) * 3 + (cy3(i) + 1);
+    const uint32_t word = cx3(i) == 0 ? M[r]
+                          : cx3(i) > 0 ? __funnelshift_r(M[r], H[r], 1)
+                                       : __funnelshift_l(Lw[r], M[r], 1);
+    nb |= ((word >> lane) & 1u) << i;
+  }
+  const int x = 32 * s + lane;
+  const long long sy = v.nxp, sz = (long long)v.ny * v.nxp;
+  const long long c = ((long long)z * v.ny + y) * v.nxp + x;
+  const long long pl = v.plane;
+  T* F = static_cast<T*>(v.f);
+  float g[kQ];
+  g[0] = P3<T>::ld(F + c);
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const long long off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
+    if (PHASE == 1 || ((nb >> opp3(i)) & 1u))
+      g[i] = P3<T>::ld(F + opp3(i) * pl + c);
+    else
+      g[i] = P3<T>::ld(F + i * pl + c - off);
+  }
+  if (x == 0 || x == v.nx - 1) port3(g, x == 0, v.u_in[(long long)z * v.ny + y], v.rho0);
+  float drho, ux, uy, uz;
+  bgk3(g, v.rho0, v.omega, drho, ux, uy, uz);
+  P3<T>::st(F + c, g[0]);
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const long long off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
+    if (PHASE == 1 || ((nb >> i) & 1u))
+      P3<T>::st(F + i * pl + c, g[i]);
+    else
+      P3<T>::st(F + opp3(i) * pl + c + off, g[i]);
+  }
+  if (MOM) {
+    v.drho[c] = drho;
+    v.ux[c] = ux;
+    v.uy[c] = uy;
+    v.uz[c] = uz;
+    if (!(isfinite(drho) && isfinite(ux) && isfinite(uy) && isfinite(uz))) atomicOr(v.flag, 1);
+  }
+}
+
+inline int blocks_for(long long n, int threads) {
+  const long long b = (n + threads - 1) / threads;
+  return (int)(b > 0 ? b : 1);
+}
+
+// ---- work-list ---------------------------------------------------------------
+__device__ __forceinline__ void word3_of(const View3& v, int i, int& y, int& z, int& s) {
+  const int per_z = (v.ny - 2) * v.nsx;
+  const int zi = i / per_z;
+  const int rest = i - zi * per_z;
+  const int yi = rest / v.nsx;
+  s = rest - yi * v.nsx;
+  y = 1 + yi;
+  z = 1 + zi;
+}
+
+__global__ void k_seg3_flags(const View3 v, int total, int* __restrict__ flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int y, z, s;
+  word3_of(v, i, y, z, s);
+  flags[i] = ~v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + s] != 0u;
+}
+
+__global__ void k_seg3_scatter(const View3 v, int total, const int* __restrict__ flags,
+                               const int* __restrict__ offs, int* __restrict__ segs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total || !flags[i]) return;
+  int y, z, s;
+  word3_of(v, i, y, z, s);
+  segs[offs[i]] = (z * v.ny + y) * v.nsx + s;
+}
+
+// ---- reductions ----------------------------------------------------------------
+constexpr int kObsThreads = 256;
+
+// fixed-order block sum (deterministic for a fixed block size)
+__device__ double block_sum(double a, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = a;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+  return t;  // valid in thread 0
+}
+
+// block 0: dp and m_in; block 1 + r: m_out of region r.  Port lists hold row
+// indices z * ny + y (the column is 0 at the inlet, nx-1 at the outlet).
+__global__ void __launch_bounds__(kObsThreads) k_obs3(const View3 v, const int* __restrict__ in_rows, int n_in,
+                                                      const int* __restrict__ out_rows,
+                                                      const int* __restrict__ out_off, int n_regions,
+                                                      double* __restrict__ result) {
+  __shared__ double sh[kObsThreads / 32];
+  const double rho0 = (double)v.rho0;
+  if (blockIdx.x == 0) {
+    double di = 0.0, mi = 0.0, dout = 0.0;
+    for (int k = threadIdx.x; k < n_in; k += blockDim.x) {
+      const long long c = (long long)in_rows[k] * v.nxp;
+      const double d = (double)v.drho[c];
+      di += d;
+      mi += (rho0 + d) * (double)v.ux[c];
+    }
+    const int n_out = out_off[n_regions];
+    for (int k = threadIdx.x; k < n_out; k += blockDim.x)
+      dout += (double)v.drho[(long long)out_rows[k] * v.nxp + (v.nx - 1)];
+    const double s_di = block_sum(di, sh);
+    const double s_mi = block_sum(mi, sh);
+    const double s_do = block_sum(dout, sh);
+    if (threadIdx.x == 0) {
+      result[0] = (s_di / (double)n_in - s_do / (double)n_out) / 3.0;
+      result[1] = s_mi;
+    }
+  } else {
+    const int r = blockIdx.x - 1;
+    double m = 0.0;
+    for (int k = out_off[r] + threadIdx.x; k < out_off[r + 1]; k += blockDim.x) {
+      const long long c = (long long)out_rows[k] * v.nxp + (v.nx - 1);
+      m += (rho0 + (double)v.drho[c]) * (double)v.ux[c];
+    }
+    const double t = block_sum(m, sh);
+    if (threadIdx.x == 0) result[2 + r] = t;
+  }
+}
+
+// ---- exchange ------------------------------------------------------------------
+struct Words3 {
+  uint32_t fluid_cand, solid_cand, e, w, n, s, u, d;  // neighbour words: bit set = solid
+};
+
+__device__ __forceinline__ uint32_t region3_bits(int s, int nx) {
+  // bits b with 2 <= 32 s + b <= nx - 3
+  uint32_t m = 0xffffffffu;
+  const int x0 = s * 32;
+  if (x0 < 2) m &= ~((1u << (2 - x0)) - 1u);
+  const int hi = nx - 3 - x0;
+  if (hi < 0) return 0u;
+  if (hi < 31) m &= (2u << hi) - 1u;
+  return m;
+}
+
+__device__ __forceinline__ Words3 words3(const View3& v, int y, int z, int s) {
+  const uint32_t* row = v.mask + mask3_row(v.ny, v.ms, y, z) + 1;
+  const long long ry = v.ms, rz = (long long)(v.ny + 2) * v.ms;
+  Words3 r;
+  const uint32_t mc = row[s];
+  r.e = __funnelshift_r(mc, row[s + 1], 1);
+  r.w = __funnelshift_l(row[s - 1], mc, 1);
+  r.n = row[s + ry];
+  r.s = row[s - ry];
+  r.u = row[s + rz];
+  r.d = row[s - rz];
+  const uint32_t reg = region3_bits(s, v.nx);
+  r.fluid_cand = ~mc & (r.e | r.w | r.n | r.s | r.u | r.d) & reg;
+  r.solid_cand = mc & (~r.e | ~r.w | ~r.n | ~r.s | ~r.u | ~r.d) & reg;
+  return r;
+}
+
+__global__ void k_oc3_count(const View3 v, int total, int* __restrict__ cnt_f, int* __restrict__ cnt_s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int y, z, s;
+  word3_of(v, i, y, z, s);
+  const Words3 m = words3(v, y, z, s);
+  cnt_f[i] = __popc(m.fluid_cand);
+  cnt_s[i] = __popc(m.solid_cand);
+}
+
+__device__ __forceinline__ unsigned long long order_key3(double x) {
+  x = __dadd_rn(x, 0.0);  // -0 -> +0
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// |u_t| of a face neighbour: the magnitude of its two velocity components
+// along the face, sqrt(a^2 + b^2), FP64 and correctly rounded
+__device__ __forceinline__ double tangential(float a, float b) {
+  const double da = (double)a, db = (double)b;
+  return __dsqrt_rn(__dadd_rn(__dmul_rn(da, da), __dmul_rn(db, db)));
+}
+
+__global__ void k_oc3_emit(const View3 v, const float* __restrict__ drho, const float* __restrict__ ux,
+                           const float* __restrict__ uy, const float* __restrict__ uz, double mu, int total,
+                           const int* __restrict__ off_f, const int* __restrict__ off_s,
+                           unsigned long long* __restrict__ key_f, int* __restrict__ idx_f,
+                           unsigned long long* __restrict__ key_s, int* __restrict__ idx_s,
+                           int* __restrict__ info) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int y, z, s;
+  word3_of(v, i, y, z, s);
+  const Words3 m = words3(v, y, z, s);
+  const double rho0 = (double)v.rho0;
+  const long long sy = v.nxp, sz = (long long)v.ny * v.nxp;
+  const long long rowc = ((long long)z * v.ny + y) * v.nxp;
+  const int rowd = (z * v.ny + y) * v.nx;
+  int of = off_f[i], os = off_s[i];
+  bool bad = false;
+  uint32_t fc = m.fluid_cand;
+  while (fc) {
+    const int b = __ffs(fc) - 1;
+    fc &= fc - 1;
+    const int x = 32 * s + b;
+    const long long c = rowc + x;
+    const double a = (double)ux[c], bb = (double)uy[c], cc = (double)uz[c];
+    const double rho = __dadd_rn(rho0, (double)drho[c]);
+    const double sq = __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(bb, bb)), __dmul_rn(cc, cc));
+    const double q = __dmul_rn(__dmul_rn(0.5, rho), sq);
+    bad |= isnan(q);
+    key_f[of] = order_key3(q);
+    idx_f[of] = rowd + x;
+    ++of;
+  }
+  uint32_t sc = m.solid_cand;
+  while (sc) {
+    const int b = __ffs(sc) - 1;
+    sc &= sc - 1;
+    const int x = 32 * s + b;
+    const long long c = rowc + x;
+    // fluid face neighbours in the order +x, +y, -x, -y, +z, -z
+    double sigma = 0.0;
+    if (!((m.e >> b) & 1u)) sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, tangential(uy[c + 1], uz[c + 1])), 0.5));
+    if (!((m.n >> b) & 1u))
+      sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, tangential(ux[c + sy], uz[c + sy])), 0.5));
+    if (!((m.w >> b) & 1u)) sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, tangential(uy[c - 1], uz[c - 1])), 0.5));
+    if (!((m.s >> b) & 1u))
+      sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, tangential(ux[c - sy], uz[c - sy])), 0.5));
+    if (!((m.u >> b) & 1u))
+      sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, tangential(ux[c + sz], uy[c + sz])), 0.5));
+    if (!((m.d >> b) & 1u))
+      sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, tangential(ux[c - sz], uy[c - sz])), 0.5));
+    bad |= isnan(sigma);
+    key_s[os] = ~order_key3(sigma);  // ascending key = descending sigma
+    idx_s[os] = rowd + x;
+    ++os;
+  }
+  if (bad) atomicOr(info + 3, 1);
+}
+
+template <class T>
+__global__ void k_oc3_apply(const View3 v, const int* __restrict__ sel_f, const int* __restrict__ sel_s,
+                            const int* __restrict__ info) {
+  const int n = info[0];
+  T* F = static_cast<T*>(v.f);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int id = side == 0 ? sel_f[k] : sel_s[k];
+      const int row = id / v.nx, x = id - row * v.nx;
+      const int z = row / v.ny, y = row - z * v.ny;
+      uint32_t* w = v.mask + mask3_row(v.ny, v.ms, y, z) + 1 + (x >> 5);
+      const long long c = (long long)row * v.nxp + x;
+      if (side == 0) {  // fluid -> solid
+        atomicOr(w, 1u << (x & 31));
+      } else {          // solid -> fluid at the rest equilibrium of rho0: g_i = 0
+        atomicAnd(w, ~(1u << (x & 31)));
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) P3<T>::st(F + i * v.plane + c, 0.0f);
+      }
+      v.drho[c] = 0.0f;
+      v.ux[c] = 0.0f;
+      v.uy[c] = 0.0f;
+      v.uz[c] = 0.0f;
+    }
+  }
+}
+
+__global__ void k_unpack3(const View3 v, uint8_t* __restrict__ cells) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = (long long)v.nx * v.ny * v.nz;
+  if (i >= n) return;
+  const long long row = i / v.nx;
+  const int x = (int)(i - row * v.nx);
+  const int z = (int)(row / v.ny), y = (int)(row - (long long)z * v.ny);
+  cells[i] = (uint8_t)((v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + (x >> 5)] >> (x & 31)) & 1u);
+}
+
+template <class T>
+cudaError_t step3_typed(int phase, int moments, const View3& v, const int* segs, const int* n_segs, int blocks,
+                        int threads, cudaStream_t stream) {
+  if (phase == 0)
+    k_step3<T, 0, 0><<<blocks, threads, 0, stream>>>(v, segs, n_segs);
+  else if (moments)
+    k_step3<T, 1, 1><<<blocks, threads, 0, stream>>>(v, segs, n_segs);
+  else
+    k_step3<T, 1, 0><<<blocks, threads, 0, stream>>>(v, segs, n_segs);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t seg3_scratch_ints(long long total) { return 2 * (size_t)total + 1 + scan_tmp_ints(total); }
+
+cudaError_t launch_build_segments3(const View3& v, int* scratch, int* segs, int* n_segs, cudaStream_t stream) {
+  const int total = (v.ny - 2) * (v.nz - 2) * v.nsx;
+  int* flags = scratch;
+  int* offs = scratch + total;  // total + 1
+  int* tmp = scratch + 2 * total + 1;
+  k_seg3_flags<<<blocks_for(total, 256), 256, 0, stream>>>(v, total, flags);
+  count_launches(1);
+  cudaError_t e = launch_scan(flags, offs, total, tmp, stream);
+  if (e != cudaSuccess) return e;
+  k_seg3_scatter<<<blocks_for(total, 256), 256, 0, stream>>>(v, total, flags, offs, segs);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaMemcpyAsync(n_segs, offs + total, sizeof(int), cudaMemcpyDeviceToDevice, stream);
+}
+
+cudaError_t launch_step3(int precision, int phase, int moments, const View3& v, const int* segs,
+                         const int* n_segs, int grid_warps, int warps_per_block, cudaStream_t stream) {
+  const int threads = 32 * warps_per_block;
+  const int blocks = blocks_for(grid_warps, warps_per_block);
+  cudaError_t e;
+  switch (precision) {
+    case LBM_F32: e = step3_typed<float>(phase, moments, v, segs, n_segs, blocks, threads, stream); break;
+    case LBM_BF16_SHIFTED:
+      e = step3_typed<__nv_bfloat16>(phase, moments, v, segs, n_segs, blocks, threads, stream);
+      break;
+    case LBM_F16_SHIFTED: e = step3_typed<__half>(phase, moments, v, segs, n_segs, blocks, threads, stream); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launches(1);
+  return e;
+}
+
+cudaError_t launch_observables3(const View3& v, const int* in_rows, int n_in, const int* out_rows,
+                                const int* out_off, int n_regions, double* result, cudaStream_t stream) {
+  k_obs3<<<1 + n_regions, kObsThreads, 0, stream>>>(v, in_rows, n_in, out_rows, out_off, n_regions, result);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oc_select3(const View3& v, const float* drho, const float* ux, const float* uy,
+                              const float* uz, double mu, const LatticeView* one, const int* word_off,
+                              const int* n_swap, const OcScratch& s, cudaStream_t stream) {
+  const int total = (v.ny - 2) * (v.nz - 2) * v.nsx;
+  cudaError_t e = cudaMemsetAsync(s.info, 0, 8 * sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  k_oc3_count<<<blocks_for(total, 256), 256, 0, stream>>>(v, total, s.cnt_f, s.cnt_s);
+  count_launches(1);
+  if ((e = launch_scan(s.cnt_f, s.off_f, total, s.scan_tmp, stream)) != cudaSuccess) return e;
+  if ((e = launch_scan(s.cnt_s, s.off_s, total, s.scan_tmp, stream)) != cudaSuccess) return e;
+  k_oc3_emit<<<blocks_for(total, 256), 256, 0, stream>>>(v, drho, ux, uy, uz, mu, total, s.off_f, s.off_s, s.key_f,
+                                                         s.idx_f, s.key_s, s.idx_s, s.info);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_oc_select_only(one, word_off, 1, n_swap, s, stream);
+}
+
+cudaError_t launch_oc_apply3(int precision, const View3& v, const OcScratch& s, cudaStream_t stream) {
+  switch (precision) {
+    case LBM_F32: k_oc3_apply<float><<<8, 128, 0, stream>>>(v, s.sel_f, s.sel_s, s.info); break;
+    case LBM_BF16_SHIFTED: k_oc3_apply<__nv_bfloat16><<<8, 128, 0, stream>>>(v, s.sel_f, s.sel_s, s.info); break;
+    case LBM_F16_SHIFTED: k_oc3_apply<__half><<<8, 128, 0, stream>>>(v, s.sel_f, s.sel_s, s.info); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_mask3(const View3& v, uint8_t* cells, cudaStream_t stream) {
+  const long long n = (long long)v.nx * v.ny * v.nz;
+  k_unpack3<<<blocks_for(n, 256), 256, 0, stream>>>(v, cells);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -201,6 +201,13 @@ cudaError_t launch_oc_select(const LatticeView* views, const int* word_off, int 
                              cudaStream_t stream);
 cudaError_t launch_oc_apply(int precision, const LatticeView* views, int n_lattices,
                             const OcScratch& s, cudaStream_t stream);
+// The choice alone, on keys and indices already emitted (key_f/idx_f,
+// key_s/idx_s in ascending idx order, off_f/off_s their per-word offsets over
+// the word space word_off[0 .. n]) -- the D3Q19 exchange uses it with a
+// one-entry table whose nx * ny is the cell count.  info must be zeroed
+// before the emit stage.
+cudaError_t launch_oc_select_only(const LatticeView* views, const int* word_off, int n_lattices, const int* n_swap,
+                                  const OcScratch& s, cudaStream_t stream);
 
 // ---- counters / debugging ----------------------------------------------------
 void count_launches(uint64_t n);

@@ -333,6 +333,14 @@ cudaError_t launch_oc_select(const LatticeView* views, const int* word_off, int 
   return cudaGetLastError();
 }
 
+cudaError_t launch_oc_select_only(const LatticeView* views, const int* word_off, int n_lattices, const int* n_swap,
+                                  const OcScratch& s, cudaStream_t stream) {
+  k_oc_select<<<dim3(2, n_lattices), kSelThreads, 0, stream>>>(views, word_off, s.key_f, s.idx_f, s.key_s, s.idx_s,
+                                                               s.off_f, s.off_s, n_swap, s.sel_f, s.sel_s, s.info);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_oc_apply(int precision, const LatticeView* views, int n_lattices, const OcScratch& s,
                             cudaStream_t stream) {
   const dim3 grid(4, n_lattices);

@@ -135,6 +135,77 @@ def random_blobs(nx: int, ny: int, seed: int, density: float = 0.15) -> np.ndarr
 
 
 # ---------------------------------------------------------------------------
+# Three-dimensional cell maps: uint8 arrays of shape (nz, ny, nx), 1 = solid.
+# ---------------------------------------------------------------------------
+
+def extrude(cells2d: np.ndarray, depth: int) -> np.ndarray:
+    """A plate device of finite depth: the 2D map repeated over `depth` fluid
+    layers z = 1..depth between two solid plates (z = 0 and z = depth + 1)."""
+    ny, nx = cells2d.shape
+    out = np.ones((depth + 2, ny, nx), np.uint8)
+    out[1:depth + 1] = cells2d[None]
+    return out
+
+
+def tree3d(nx: int, ny: int, nz: int, generations: int, w0: int, ratio: float = 2.0 ** (-1.0 / 3.0),
+           min_width: int = 3) -> np.ndarray:
+    """Binary distributor of square ducts: a trunk of width w0 on the axis
+    (ny/2, nz/2) from x = 0 splits 2^G ways, generation k (k = 0, 1, ...)
+    splitting along y when k is even and along z when k is odd, each child
+    taking the middle of its half of the parent's cross-section.  A split is
+    a header duct across the split axis at the parent's last w_k columns.
+    Widths w_k = max(min_width, round(w0 ratio^k)) (ratio 2^(-1/3): Murray's
+    law for equal children); the trunk is two segments long, every
+    generation one, segment = nx // (G + 2); the last generation runs out to
+    x = nx - 1, giving 2^G outlet regions."""
+    cells = np.ones((nz, ny, nx), np.uint8)
+    seg = nx // (generations + 2)
+    widths = [max(min_width, int(round(w0 * ratio ** k))) for k in range(generations + 1)]
+
+    def carve(z0, z1, y0, y1, x0, x1):
+        cells[max(z0, 1):min(z1, nz - 1), max(y0, 1):min(y1, ny - 1), max(x0, 0):min(x1, nx)] = 0
+
+    def rec(k, x0, yc, zc, hy, hz):
+        w = widths[k]
+        x1 = nx if k == generations else x0 + (2 * seg if k == 0 else seg)
+        carve(zc - w // 2, zc - w // 2 + w, yc - w // 2, yc - w // 2 + w, x0, x1)
+        if k == generations:
+            return
+        wc = widths[k + 1]
+        if k % 2 == 0:
+            c1, c2 = yc - hy // 2, yc + hy // 2
+            carve(zc - w // 2, zc - w // 2 + w, c1 - wc // 2, c2 - wc // 2 + wc, x1 - w, x1)
+            rec(k + 1, x1 - wc, c1, zc, hy // 2, hz)
+            rec(k + 1, x1 - wc, c2, zc, hy // 2, hz)
+        else:
+            c1, c2 = zc - hz // 2, zc + hz // 2
+            carve(c1 - wc // 2, c2 - wc // 2 + wc, yc - w // 2, yc - w // 2 + w, x1 - w, x1)
+            rec(k + 1, x1 - wc, yc, c1, hy, hz // 2)
+            rec(k + 1, x1 - wc, yc, c2, hy, hz // 2)
+
+    rec(0, 0, ny // 2, nz // 2, ny // 2, nz // 2)
+    return cells
+
+
+def duct3d(nx: int, wy: int, wz: int) -> np.ndarray:
+    """Straight rectangular duct of wy x wz fluid cells, open at both ends."""
+    cells = np.ones((wz + 2, wy + 2, nx), np.uint8)
+    cells[1:wz + 1, 1:wy + 1, :] = 0
+    return cells
+
+
+def random_blobs3d(nx: int, ny: int, nz: int, seed: int, density: float = 0.15) -> np.ndarray:
+    """Duct with random solid cells (x in [3, nx-4]), for parity of irregular walls."""
+    cells = duct3d(nx, ny - 2, nz - 2)
+    for z in range(1, nz - 1):
+        for y in range(1, ny - 1):
+            for x in range(3, nx - 3):
+                if uniform01(seed, (z * ny + y) * nx + x) < density:
+                    cells[z, y, x] = 1
+    return cells
+
+
+# ---------------------------------------------------------------------------
 # Workload recipes.  Lattice units: dx = dt = 1, rho0 = 1.
 # ---------------------------------------------------------------------------
 
@@ -195,6 +266,23 @@ def config_candidates(n: int = 256, base_seed: int = 0):
         out.append(dict(name=f"cand{c}", cells=cells, nx=nx, ny=ny, tau=0.53,
                         u_max=1.5 * 50 * 0.01 / w0, generations=G, ratio=r, seed=s))
     return out
+
+
+def config_tree3d_small():
+    """72 x 34 x 34 D3Q19 distributor, two generations (4 outlets), trunk 10 wide;
+    tau 0.8, u_max 0.05."""
+    cells = tree3d(72, 34, 34, 2, 10)
+    return dict(name="tree3d_72x34x34_g2", cells=cells, nx=72, ny=34, nz=34, tau=0.8, u_max=0.05)
+
+
+def config_tree3d(nx: int = 384, ny: int = 192, nz: int = 192):
+    """D3Q19 distributor of 384 x 192 x 192 cells: four generations (16 outlet
+    ducts), trunk 48 wide, widths shrinking by 2^(-1/3); Re = 50 on the trunk at
+    nu = 0.01 (tau 0.53): mean inlet speed 50 * 0.01 / 48; the product of two
+    parabolas has a mean of 4/9 of its peak, so u_max = 9/4 of the mean."""
+    cells = tree3d(nx, ny, nz, 4, 48)
+    return dict(name=f"tree3d_{nx}x{ny}x{nz}_g4", cells=cells, nx=nx, ny=ny, nz=nz, tau=0.53,
+                u_max=2.25 * 50 * 0.01 / 48, steps=2000)
 
 
 def config_served_request(seed: int):

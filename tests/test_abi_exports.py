@@ -1,5 +1,6 @@
 """The C-ABI library builds, loads on a machine without a GPU, and exports
-every function that include/lbm.h declares (no compute calls here)."""
+every function that include/lbm.h and include/lbm3d.h declare (no compute
+calls here)."""
 import ctypes
 import os
 import re
@@ -16,7 +17,7 @@ def _declared_functions():
             continue
         text = open(os.path.join(ROOT, "include", fn)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\**\s+\**(lbm_[a-z_0-9]+)\s*\(", text, flags=re.M)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\**\s+\**(lbm(?:3d)?_[a-z_0-9]+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
@@ -29,7 +30,8 @@ def built_lib():
 
 def test_header_declares_the_boundary():
     names = _declared_functions()
-    for required in ("lbm_create_geometry", "lbm_solve", "lbm_optimize_step", "lbm_read_fields"):
+    for required in ("lbm_create_geometry", "lbm_solve", "lbm_optimize_step", "lbm_read_fields",
+                     "lbm3d_create", "lbm3d_solve", "lbm3d_optimize_step", "lbm3d_read_fields"):
         assert required in names
 
 
@@ -58,6 +60,12 @@ def test_host_only_entry_points(built_lib):
     L.lbm_server_destroy(None)
     assert L.lbm_server_cancel(None, 1) == 1
     L.lbm_debug_fail_alloc(-1)  # host-only switch
+    from paper_1303_0107_gb300 import lib3d
+    L3 = lib3d._lib()
+    h3 = ctypes.c_void_p()
+    assert L3.lbm3d_create(None, None, None, ctypes.byref(h3)) == 1 and not h3.value
+    L3.lbm3d_destroy(None)
+    assert L3.lbm3d_set_block(None, 8) == 1
     small = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05)), 0)
     opt = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05)), 5)
     half = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05, precision=1)), 0)
@@ -77,7 +85,7 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
     include/lbm.h, against the ctypes mirrors of the binding."""
     import shutil
     import subprocess
-    from paper_1303_0107_gb300 import lib
+    from paper_1303_0107_gb300 import lib, lib3d
     if not shutil.which("gcc"):
         pytest.skip("no gcc")
     checks = [("lbm_params", lib.Params, ["tau", "ports", "guard", "collision", "mirror", "c_smag"]),
@@ -88,8 +96,12 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
               ("lbm_served", lib.Served, ["t_done", "dp_first", "last"]),
               ("lbm_server_stats", lib.ServerStats, ["active", "busy_s", "budget_bytes"]),
               ("lbm_opt_plan", lib.OptPlan, ["tol", "patience", "reserved"]),
-              ("lbm_opt_summary", lib.OptSummary, ["swapped", "dp_last"])]
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', "int main(void) {"]
+              ("lbm_opt_summary", lib.OptSummary, ["swapped", "dp_last"]),
+              ("lbm3d_params", lib3d.Params3, ["precision", "tau", "u_max", "reinit", "reserved"]),
+              ("lbm3d_solve_result", lib3d.SolveResult3, ["n_outlets", "m_out", "fluid_cells"]),
+              ("lbm3d_opt_result", lib3d.OptResult3, ["fluid_count", "solve"])]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', '#include "lbm3d.h"',
+             "int main(void) {"]
     for cname, _, fields in checks:
         lines.append(f'  printf("%zu\\n", sizeof({cname}));')
         for f in fields:

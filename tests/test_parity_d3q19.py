@@ -1,0 +1,207 @@
+"""D3Q19 path on the GPU against the FP64 D3Q19 oracle: fields, pressure drop
+and outlet flows within the FP32 tolerance of the hot path, one step pair
+from a random state (every direction, bounce-back on irregular walls,
+ragged row ends), the exchange bit for bit, and the argument checks."""
+import numpy as np
+import pytest
+
+import paper_1303_0107_gb300 as L
+from paper_1303_0107_gb300 import inputs as I
+from oracle import lbm3d as o3
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    L.load_library()
+
+
+def _w3():
+    return o3.lattice3()[4]
+
+
+def _compare_fields(lat, sv, cells, tol=TOL):
+    fluid = cells == 0
+    for name, field, ref in (("ux", L.FIELD3_UX, sv.ux), ("uy", L.FIELD3_UY, sv.uy), ("uz", L.FIELD3_UZ, sv.uz)):
+        got = lat.read(field).astype(np.float64)
+        scale = np.abs(sv.ux).max()
+        err = np.abs(got - ref * fluid).max()
+        assert err <= tol * scale, (name, err, scale)
+    drho = lat.read(L.FIELD3_DRHO).astype(np.float64)
+    ref = (sv.rho - 1.0) * fluid
+    assert np.abs(drho - ref).max() <= tol * np.abs(ref).max()
+
+
+def _check_solve(cfg_cells, tau, u_max, steps, tol=TOL, precision=L.F32):
+    nz, ny, nx = cfg_cells.shape
+    lat = L.Lattice3(cfg_cells, tau, u_max, precision=precision)
+    g = lat.solve(steps)
+    sv = o3.Solver3(o3.make_params3(nx, ny, nz, tau, u_max=u_max), cfg_cells)
+    o = sv.solve(steps)
+    _compare_fields(lat, sv, cfg_cells, tol)
+    assert abs(g["dp"] - o["dp"]) <= tol * abs(o["dp"])
+    assert abs(g["m_in"] - o["m_in"]) <= tol * abs(o["m_in"])
+    assert g["n_outlets"] == len(o["m_out"])
+    assert np.abs(g["m_out"] - o["m_out"]).max() <= tol * np.abs(o["m_out"]).max()
+    assert g["fluid_cells"] == int((cfg_cells == 0).sum()) and g["steps_done"] == steps
+    return lat, sv, g, o
+
+
+def test_tree3d_matches_oracle():
+    cfg = I.config_tree3d_small()
+    lat, *_ = _check_solve(cfg["cells"], cfg["tau"], cfg["u_max"], 300)
+    lat.close()
+
+
+@pytest.mark.parametrize("nx", [33, 64, 70])  # ragged tail of one cell, whole segments, ragged tail
+def test_irregular_walls_match_oracle(nx):
+    cells = I.random_blobs3d(nx, 12, 11, seed=nx, density=0.2)
+    lat, *_ = _check_solve(cells, 0.7, 0.04, 200)
+    lat.close()
+
+
+def test_duct_with_two_outlet_regions():
+    cells = I.duct3d(40, 16, 10)
+    cells[1:-1, 8, -6:] = 1  # a wall splits the last six columns in two
+    lat, sv, g, o = _check_solve(cells, 0.8, 0.05, 400)
+    assert g["n_outlets"] == 2
+    lat.close()
+
+
+def test_one_pair_from_a_random_state():
+    """Two steps (phase A, phase B) from random post-collision populations:
+    every direction of streaming and bounce-back, and the port rules, in
+    one comparison."""
+    cells = I.random_blobs3d(45, 10, 9, seed=7, density=0.3)
+    nz, ny, nx = cells.shape
+    rng = np.random.default_rng(1)
+    w = _w3()
+    g0 = (w[:, None, None, None] * 0.05 * rng.standard_normal((19, nz, ny, nx))).astype(np.float32)
+    lat = L.Lattice3(cells, 0.9, 0.03)
+    lat.load_state(g0)
+    lat.solve(2)
+    p = o3.make_params3(nx, ny, nz, 0.9, u_max=0.03)
+    f0 = g0.astype(np.float64) + w[:, None, None, None] * 1.0
+    f0 *= (cells == 0)[None]
+    f, rho, ux, uy, uz, st = o3.run3(p, cells, o3.inlet_profile3(p, cells), f0, 2)
+    got = lat.read(L.FIELD3_POPS).astype(np.float64) + w[:, None, None, None]
+    fluid = (cells == 0)[None]
+    assert np.abs((got - f) * fluid).max() <= 2e-6
+    for field, ref in ((L.FIELD3_UX, ux), (L.FIELD3_UY, uy), (L.FIELD3_UZ, uz)):
+        assert np.abs(lat.read(field) - ref * fluid[0]).max() <= 2e-6
+    lat.close()
+
+
+def test_selection_is_bit_exact():
+    """Candidates and scores on a supplied FP32 field: the GPU's choice equals
+    the oracle's on the same field."""
+    cfg = I.config_tree3d_small()
+    cells = cfg["cells"]
+    nz, ny, nx = cells.shape
+    rng = np.random.default_rng(5)
+    fluid = cells == 0
+    drho = (0.01 * rng.standard_normal(cells.shape) * fluid).astype(np.float32)
+    u = [(0.05 * rng.standard_normal(cells.shape) * fluid).astype(np.float32) for _ in range(3)]
+    u[0][fluid & (rng.random(cells.shape) < 0.2)] = 0.0  # ties in q
+    lat = L.Lattice3(cells, cfg["tau"], cfg["u_max"])
+    p = o3.make_params3(nx, ny, nz, cfg["tau"], u_max=cfg["u_max"])
+    cand, score = o3.scores3(p, cells, 1.0 + drho.astype(np.float64), *[a.astype(np.float64) for a in u])
+    for n_swap in (0, 1, 17, 400, 10 ** 6):
+        fi, si = lat.select_swaps(drho, *u, n_swap)
+        ofi, osi = o3.select3(p, cand, score, n_swap)
+        assert np.array_equal(fi, ofi) and np.array_equal(si, osi)
+    lat.close()
+
+
+def test_optimize_step_matches_oracle_exchange():
+    cfg = I.config_tree3d_small()
+    cells = cfg["cells"]
+    nz, ny, nx = cells.shape
+    lat = L.Lattice3(cells, cfg["tau"], cfg["u_max"])
+    lat.solve(200)
+    fields = [lat.read(f) for f in (L.FIELD3_DRHO, L.FIELD3_UX, L.FIELD3_UY, L.FIELD3_UZ)]
+    p = o3.make_params3(nx, ny, nz, cfg["tau"], u_max=cfg["u_max"])
+    cand, score = o3.scores3(p, cells, 1.0 + fields[0].astype(np.float64), *[a.astype(np.float64) for a in fields[1:]])
+    fi, si = o3.select3(p, cand, score, 30)
+    before = lat.read(L.FIELD3_MASK)
+    out = lat.optimize_step(30, 200)
+    after = lat.read(L.FIELD3_MASK)
+    assert out["n_swapped"] == len(fi) == 30
+    assert out["fluid_count"] == int((cells == 0).sum()) == int((after == 0).sum())
+    flipped = np.flatnonzero((before != after).reshape(-1))
+    assert np.array_equal(np.sort(np.concatenate([fi, si])), flipped)
+    assert np.all(after.reshape(-1)[fi] == 1) and np.all(after.reshape(-1)[si] == 0)
+    # the re-solve from the exchanged state follows the oracle's, the same cells exchanged
+    sv = o3.Solver3(p, cells)
+    sv.solve(200)
+    o3.apply3(p, sv.solid, sv.f, fi, si)
+    o = sv.solve(200)
+    assert np.array_equal(sv.solid, after)
+    assert abs(out["dp"] - o["dp"]) <= TOL * abs(o["dp"])
+    _compare_fields(lat, sv, after)
+    lat.close()
+
+
+def test_cold_reinit_and_state_roundtrip():
+    cfg = I.config_tree3d_small()
+    lat = L.Lattice3(cfg["cells"], cfg["tau"], cfg["u_max"], reinit=L.REINIT_COLD)
+    lat.solve(100)
+    pops = lat.read(L.FIELD3_POPS)
+    lat.optimize_step(5, 2)
+    lat.load_state(pops)  # state round trip through the host
+    again = lat.read(L.FIELD3_POPS)
+    fluid = (lat.read(L.FIELD3_MASK) == 0)[None]
+    assert np.array_equal(again * fluid, pops * fluid)
+    lat.close()
+
+
+def test_bf16_storage_stays_close():
+    cfg = I.config_tree3d_small()
+    lat, sv, g, o = _check_solve(cfg["cells"], cfg["tau"], cfg["u_max"], 300, tol=2e-2, precision=L.BF16_SHIFTED)
+    lat.close()
+
+
+def test_block_shapes_agree_bit_for_bit():
+    cfg = I.config_tree3d_small()
+    ref = None
+    for wpb in (4, 8, 16):
+        lat = L.Lattice3(cfg["cells"], cfg["tau"], cfg["u_max"])
+        lat.set_block(wpb)
+        lat.solve(100)
+        pops = lat.read(L.FIELD3_POPS)
+        if ref is None:
+            ref = pops
+        assert np.array_equal(pops, ref)
+        lat.close()
+
+
+def test_argument_and_geometry_checks():
+    cells = I.duct3d(16, 6, 5)
+    for bad in (np.zeros_like(cells),):  # open frame
+        with pytest.raises(L.LbmError) as e:
+            L.Lattice3(bad, 0.8, 0.05)
+        assert e.value.status == 2
+    c2 = cells.copy()
+    c2[:, :, 1] = 1  # inlet cells without a fluid cell behind
+    with pytest.raises(L.LbmError) as e:
+        L.Lattice3(c2, 0.8, 0.05)
+    assert e.value.status == 2
+    with pytest.raises(L.LbmError) as e:
+        L.Lattice3(cells, 0.5, 0.05)
+    assert e.value.status == 1
+    lat = L.Lattice3(cells, 0.8, 0.05)
+    for n in (0, 3, -2):
+        with pytest.raises(L.LbmError) as e:
+            lat.solve(n)
+        assert e.value.status == 1
+    with pytest.raises(L.LbmError):
+        lat.optimize_step(2, 10)  # no field yet
+    with pytest.raises(L.LbmError):
+        lat.set_block(5)
+    lat.close()
