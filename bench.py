@@ -51,19 +51,21 @@ def parse():
     ap.add_argument("--lattice-steps", type=int, default=5000, help="time steps per solve")
     ap.add_argument("--precision", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-extras", action="store_true", help="skip every leg after the main run")
-    ap.add_argument("--legs", default="large,tjunction,precision,models,collector,batched,served",
+    ap.add_argument("--legs", default="large,tjunction,precision,models,collector,d3q19,batched,served",
                     help="legs after the main run: large (8192 x 4096 lattice), precision (BF16/FP16 vs the "
                          "FP64 oracle; also the CPU baseline), tjunction (128 x 64 T, launch-bound), "
                          "models (collision models on the tree), "
                          "collector (the paper's half-domain collector, 151 optimisation steps), "
+                         "d3q19 (the D3Q19 path: step rates, optimisation loop, oracle rate), "
                          "batched (256 candidates), served (request loop), "
                          "sweep (served at 50, 100, 200 and 400 requests/s, 10 s each; not in the default run)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="served leg: Poisson arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="served leg: arrival window")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--kernel-case", choices=["tree", "large"], default=None,
+    ap.add_argument("--kernel-case", choices=["tree", "large", "tree3d", "duct3d"], default=None,
                     help="only create one lattice and run two solves of --kernel-steps steps (for ncu "
-                         "captures): tree = 2048 x 1024 distributor, large = 8192 x 4096 channel array")
+                         "captures): tree = 2048 x 1024 distributor, large = 8192 x 4096 channel array, "
+                         "tree3d = 384 x 192 x 192 D3Q19 distributor, duct3d = 256 x 128 x 128 D3Q19 duct")
     ap.add_argument("--kernel-steps", type=int, default=4)
     return ap.parse_args()
 
@@ -74,6 +76,19 @@ def kernel_case(args):
     import paper_1303_0107_gb300 as L
     from paper_1303_0107_gb300 import inputs as I
     prec = L.lib.PRECISIONS[args.precision]
+    if args.kernel_case in ("tree3d", "duct3d"):
+        if args.kernel_case == "tree3d":
+            cfg = I.config_tree3d()
+            cells, tau, u_max = cfg["cells"], cfg["tau"], cfg["u_max"]
+        else:
+            cells, tau, u_max = I.duct3d(256, 126, 126), 0.6, 0.05
+        lat = L.Lattice3(cells, tau, u_max, precision=prec)
+        lat.solve(args.kernel_steps)
+        r = lat.solve(args.kernel_steps)
+        lat.close()
+        print(json.dumps({"kernel_case": args.kernel_case, "precision": args.precision,
+                          "fluid_cells": int((cells == 0).sum()), "dp": r["dp"]}))
+        return 0
     if args.kernel_case == "tree":
         cfg = I.config_tree_2048()
         cells, tau, u_max = cfg["cells"], cfg["tau"], cfg["u_max"]
@@ -335,6 +350,72 @@ def leg_models(L, I, stream):
     for k in out:
         out[k]["glups_vs_bgk"] = out[k]["glups_steps"] / out["bgk"]["glups_steps"]
         out[k]["dp_rel_to_bgk"] = out[k]["dp"] / out["bgk"]["dp"] - 1.0
+    return out
+
+
+def oracle3_rate(cells, tau, u_max, seconds):
+    """Fluid updates per second of the FP64 D3Q19 oracle on a bounded sample."""
+    from oracle import lbm3d as o3
+    nz, ny, nx = cells.shape
+    p = o3.make_params3(nx, ny, nz, tau, u_max=u_max)
+    u_in = o3.inlet_profile3(p, cells)
+    f = o3.init3(p, cells)
+    fluid = int((cells == 0).sum())
+    n = 2
+    while True:
+        t0 = time.perf_counter()
+        f, *_ = o3.run3(p, cells, u_in, f, n)
+        t = time.perf_counter() - t0
+        if t >= 0.25:
+            break
+        n *= 2
+    n = max(2, int(seconds * n / t) // 2 * 2)
+    t0 = time.perf_counter()
+    o3.run3(p, cells, u_in, f, n)
+    dt = time.perf_counter() - t0
+    return fluid * n / dt, n, dt
+
+
+def leg_d3q19(L, I, stream, peak, cpu_seconds=4.0):
+    """The D3Q19 form of the path: step GLUPS and HBM fraction of the stream-
+    collide kernels on the 384 x 192 x 192 distributor (FP32 and BF16
+    storage) and on a full 256 x 128 x 128 duct, the optimisation loop on the
+    distributor (exchange + re-solve), and the FP64 oracle's rate."""
+    cfg = I.config_tree3d()
+    out = {}
+    cases = (("tree3d_384x192x192", cfg["cells"], cfg["tau"], cfg["u_max"]),
+             ("duct3d_256x128x128", I.duct3d(256, 126, 126), 0.6, 0.05))
+    for name, cells, tau, u_max in cases:
+        fluid = int((cells == 0).sum())
+        for pname, pv in (("f32", L.F32), ("bf16", L.BF16_SHIFTED)):
+            h = L.Lattice3(cells, tau, u_max, precision=pv, stream=stream)
+            h.solve(100)
+            h.kernel_time(reset=True)
+            r = h.solve(1000)
+            ms, nl, nu = h.kernel_time()
+            bpu = 2.0 * 19.0 * (4.0 if pv == L.F32 else 2.0) + 1.0 / 8.0
+            gbs = fluid * bpu / ((ms / 1e3) / nl) / 1e9
+            out[f"{name}_{pname}"] = {"fluid_cells": fluid, "glups": nu / (ms / 1e3) / 1e9,
+                                      "us_per_step": 1e3 * ms / nl, "achieved_gbs": gbs,
+                                      "frac_of_measured_hbm": gbs / peak, "dp": r["dp"]}
+            h.close()
+    h = L.Lattice3(cfg["cells"], cfg["tau"], cfg["u_max"], stream=stream)
+    fluid = int((cfg["cells"] == 0).sum())
+    n_swap = max(1, fluid // 500)
+    t0 = time.perf_counter()
+    first = h.solve(cfg["steps"])
+    dps = [first["dp"]]
+    for _ in range(5):
+        dps.append(h.optimize_step(n_swap, cfg["steps"])["dp"])
+    dt = time.perf_counter() - t0
+    out["optimize_tree3d_f32"] = {"workload": f"{cfg['name']}: 6 solves of {cfg['steps']} steps, n_swap {n_swap}",
+                                  "glups": fluid * cfg["steps"] * 6 / dt / 1e9, "seconds": dt, "dp": dps}
+    h.close()
+    small = I.config_tree3d_small()
+    r, n, dt = oracle3_rate(small["cells"], small["tau"], small["u_max"], cpu_seconds)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    out["oracle3_cpu"] = {"glups": r / 1e9, "cores": cores,
+                          "sample": f"{small['name']}: {n} FP64 time steps, {dt:.1f} s"}
     return out
 
 
@@ -646,6 +727,8 @@ def main():
             extras[f"large_8192x4096_{pname}"] = {"glups": nu / (ms / 1e3) / 1e9, "achieved_gbs": gbs,
                                                   "frac_of_measured_hbm": gbs / peak, "fluid_cells": bf}
             hb.close()
+    if rank == 0 and "d3q19" in legs:
+        extras["d3q19"] = leg_d3q19(L, I, stream, peak)
     if rank == 0 and "precision" in legs:
         extras["precision_tree_2048"], cpu_p = leg_precision(L, I, stream)
         if world == 1:

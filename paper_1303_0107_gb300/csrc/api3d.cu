@@ -2,6 +2,7 @@
 // device buffers of one lattice, and the solve / exchange sequence.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -20,7 +21,7 @@ struct lbm3d_handle_s {
   int total_words = 0;    // interior-row words = work-list capacity
   long long ncells = 0;
   std::vector<void*> allocs;
-  int* segs = nullptr;
+  Seg3* segs = nullptr;
   int* seg_scratch = nullptr;
   int* n_segs = nullptr;
   int* in_rows = nullptr;
@@ -36,7 +37,9 @@ struct lbm3d_handle_s {
   float* t_fields = nullptr;  // [4][plane] test-hook field copies (allocated on first use)
   uint8_t* d_cells = nullptr; // [ncells] unpacked mask (allocated on first use)
   double* h_result = nullptr; // pinned
-  int* h_small = nullptr;     // pinned: [0] flag, [1..8] info, [9] n_swap
+  int* h_small = nullptr;     // pinned: [0] flag, [1..8] info, [9] n_swap, [10] n_segs
+  int nseg = 0;               // segments in the work-list (host copy)
+  int resident[3] = {0, 0, 0};  // resident blocks of phase A, B, B with moments at wpb
   int64_t steps_done = 0;
   int64_t fluid = 0;
   bool solved = false;
@@ -174,12 +177,41 @@ lbm_status geometry3(const lbm3d_params& p, const uint8_t* solid, Geometry3& g) 
 
 size_t storage_bytes3(int precision) { return precision == LBM_F32 ? 4 : 2; }
 
+// blocks of one phase launch: one warp per segment, at most what is resident at once
+int step_blocks(lbm3d_handle h, int which) {
+  const int need = (h->nseg + h->wpb - 1) / h->wpb;
+  const int cap = h->resident[which] > 0 ? h->resident[which] : need;
+  return std::max(1, std::min(need, cap));
+}
+
+lbm_status set_shape(lbm3d_handle h, int wpb) {
+  const int phase[3] = {0, 1, 1}, mom[3] = {0, 0, 1};
+  int res[3];
+  for (int k = 0; k < 3; ++k) {
+    res[k] = step3_resident_blocks(h->p.precision, phase[k], mom[k], wpb, h->v);
+    if (res[k] <= 0) return fail(LBM_ERR_CUDA, "occupancy query of the step kernel failed");
+  }
+  h->wpb = wpb;
+  std::copy(res, res + 3, h->resident);
+  return LBM_OK;
+}
+
+// (re)build the step work-list and read its length back
+lbm_status build_worklist(lbm3d_handle h) {
+  CU3(launch_build_segments3(h->v, h->seg_scratch, h->segs, h->n_segs, h->stream));
+  CU3(cudaMemcpyAsync(h->h_small + 10, h->n_segs, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU3(cudaStreamSynchronize(h->stream));
+  h->nseg = h->h_small[10];
+  return LBM_OK;
+}
+
 lbm_status run_steps(lbm3d_handle h, int64_t n_steps) {
+  const int ba = step_blocks(h, 0), bb = step_blocks(h, 1), bm = step_blocks(h, 2);
   CU3(cudaEventRecord(h->ev0, h->stream));
   for (int64_t k = 0; k < n_steps / 2; ++k) {
     const bool last = k == n_steps / 2 - 1;
-    CU3(launch_step3(h->p.precision, 0, 0, h->v, h->segs, h->n_segs, h->total_words, h->wpb, h->stream));
-    CU3(launch_step3(h->p.precision, 1, last ? 1 : 0, h->v, h->segs, h->n_segs, h->total_words, h->wpb,
+    CU3(launch_step3(h->p.precision, 0, 0, h->v, h->segs, h->n_segs, ba, h->wpb, h->stream));
+    CU3(launch_step3(h->p.precision, 1, last ? 1 : 0, h->v, h->segs, h->n_segs, last ? bm : bb, h->wpb,
                      h->stream));
     if (debug_sync()) CU3(cudaStreamSynchronize(h->stream));
   }
@@ -261,6 +293,8 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   v.nxp = 32 * v.nsx;
   v.ms = v.nsx + 2;
   v.plane = (long long)p.nz * p.ny * v.nxp;
+  const char* force64 = std::getenv("LBM3D_INDEX64");
+  v.idx64 = ((long long)kQ3 * v.plane >= (1ll << 31) || (force64 && std::strcmp(force64, "1") == 0)) ? 1 : 0;
   v.omega = (float)(1.0 / p.tau);
   v.rho0 = (float)p.rho0;
   h->elem = storage_bytes3(p.precision);
@@ -292,7 +326,7 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   CU3(h->alloc(&u_in, sizeof(float) * g.u_in.size()));
   v.u_in = u_in;
   CU3(h->alloc(&v.flag, sizeof(int)));
-  CU3(h->alloc(&h->segs, sizeof(int) * h->total_words));
+  CU3(h->alloc(&h->segs, sizeof(Seg3) * h->total_words));
   CU3(h->alloc(&h->seg_scratch, sizeof(int) * seg3_scratch_ints(h->total_words)));
   CU3(h->alloc(&h->n_segs, sizeof(int)));
   CU3(h->alloc(&h->in_rows, sizeof(int) * g.in_rows.size()));
@@ -337,9 +371,8 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   CU3(cudaMemcpyAsync(h->d_word_off, word_off, sizeof(word_off), cudaMemcpyHostToDevice, h->stream));
   CU3(cudaMemsetAsync(v.f, 0, (size_t)kQ3 * v.plane * h->elem, h->stream));  // rest equilibrium: g = 0
   CU3(cudaMemsetAsync(fields, 0, sizeof(float) * 4 * v.plane, h->stream));
-  CU3(launch_build_segments3(v, h->seg_scratch, h->segs, h->n_segs, h->stream));
-  CU3(cudaStreamSynchronize(h->stream));  // the host vectors above go out of scope
-  return LBM_OK;
+  if ((st = build_worklist(h)) != LBM_OK) return st;  // also waits for the uploads above
+  return set_shape(h, 8);
 }
 
 }  // namespace
@@ -378,7 +411,7 @@ lbm_status lbm3d_optimize_step(lbm3d_handle h, int32_t n_swap, int64_t n_steps, 
   CU3(launch_oc_apply3(h->p.precision, h->v, h->oc, h->stream));
   if (h->p.reinit == LBM_REINIT_COLD)
     CU3(cudaMemsetAsync(h->v.f, 0, (size_t)kQ3 * h->v.plane * h->elem, h->stream));
-  CU3(launch_build_segments3(h->v, h->seg_scratch, h->segs, h->n_segs, h->stream));
+  if ((st = build_worklist(h)) != LBM_OK) return st;
   std::memset(out, 0, sizeof(*out));
   out->n_swapped = n;
   out->fluid_count = h->fluid;
@@ -465,8 +498,7 @@ lbm_status lbm3d_set_block(lbm3d_handle h, int32_t warps_per_block) {
   if (!h) return fail(LBM_ERR_ARG, "handle is NULL");
   if (warps_per_block != 4 && warps_per_block != 8 && warps_per_block != 16)
     return fail(LBM_ERR_ARG, "warps_per_block must be 4, 8 or 16");
-  h->wpb = warps_per_block;
-  return LBM_OK;
+  return set_shape(h, warps_per_block);
 }
 
 }  // extern "C"

@@ -188,68 +188,50 @@ __device__ __forceinline__ void port3(float (&g)[kQ], bool inlet, float u_in, fl
 
 constexpr unsigned kFull = 0xffffffffu;
 
-template <class T, int PHASE, int MOM>
-__global__ void __launch_bounds__(512) k_step3(const View3 v, const int* __restrict__ segs,
-                                               const int* __restrict__ n_segs) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-  if (warp >= *n_segs) return;  // whole warps leave together
-  const int seg = segs[warp];
-  const int row = seg / v.nsx;
-  const int s = seg - row * v.nsx;
-  const int z = row / v.ny;
-  const int y = row - z * v.ny;
-  // lanes 0..8: word s of row r = (dz+1)*3 + (dy+1); 9..17: word s-1; 18..26: word s+1
-  uint32_t wv = 0xffffffffu;
-  if (lane < 27) {
-    const int part = lane / 9, r = lane - 9 * part;
-    const int dy = r % 3 - 1, dz = r / 3 - 1;
-    const int dw = part == 0 ? 0 : (part == 1 ? -1 : 1);
-    wv = v.mask[mask3_row(v.ny, v.ms, y + dy, z + dz) + 1 + s + dw];
-  }
-  uint32_t M[9], Lw[9], H[9];
-#pragma unroll
-  for (int r = 0; r < 9; ++r) {
-    M[r] = __shfl_sync(kFull, wv, r);
-    Lw[r] = __shfl_sync(kFull, wv, 9 + r);
-    H[r] = __shfl_sync(kFull, wv, 18 + r);
-  }
-  if ((M[4] >> lane) & 1u) return;  // solid (or past the row's end)
-  uint32_t nb = 0;                  // bit i: cell x + c_i is solid
-#pragma unroll
-  for (int i = 1; i < kQ; ++i) {
-    const int r = (cz3(i) + 1) * 3 + (cy3(i) + 1);
-    const uint32_t word = cx3(i) == 0 ? M[r]
-                          : cx3(i) > 0 ? __funnelshift_r(M[r], H[r], 1)
-                                       : __funnelshift_l(Lw[r], M[r], 1);
-    nb |= ((word >> lane) & 1u) << i;
-  }
-  const int x = 32 * s + lane;
-  const long long sy = v.nxp, sz = (long long)v.ny * v.nxp;
-  const long long c = ((long long)z * v.ny + y) * v.nxp + x;
-  const long long pl = v.plane;
+// keep a value opaque to the optimiser at this point (no hoisting or reuse)
+__device__ __forceinline__ void opaque(int& a) { asm volatile("" : "+r"(a)); }
+__device__ __forceinline__ void opaque(long long& a) { asm volatile("" : "+l"(a)); }
+
+// The populations of one fluid cell: load (pull or local), port rule,
+// collision, store.  NB0: no neighbour of this cell is solid (no
+// bounce-back selects at all).  IX: element index type -- int when all 19
+// planes have fewer than 2^31 elements (one IMAD per address), else long long.
+template <class T, int PHASE, int MOM, bool NB0, class IX>
+__device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z, uint32_t nb) {
+  IX sy = (IX)v.nxp, sz = (IX)v.ny * (IX)v.nxp;
+  IX c = ((IX)z * v.ny + y) * (IX)v.nxp + x;
+  IX pl = (IX)v.plane;
+  // opaque per cell: keeps the compiler from hoisting 18 plane and neighbour
+  // offsets out of the warp's loop into registers
+  opaque(pl);
+  opaque(sy);
+  opaque(sz);
   T* F = static_cast<T*>(v.f);
   float g[kQ];
   g[0] = P3<T>::ld(F + c);
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
-    const long long off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
-    if (PHASE == 1 || ((nb >> opp3(i)) & 1u))
-      g[i] = P3<T>::ld(F + opp3(i) * pl + c);
+    const IX off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
+    if (PHASE == 1 || (!NB0 && ((nb >> opp3(i)) & 1u)))
+      g[i] = P3<T>::ld(F + (opp3(i) * pl + c));
     else
-      g[i] = P3<T>::ld(F + i * pl + c - off);
+      g[i] = P3<T>::ld(F + (i * pl + c - off));
   }
-  if (x == 0 || x == v.nx - 1) port3(g, x == 0, v.u_in[(long long)z * v.ny + y], v.rho0);
+  if (!NB0 && (x == 0 || x == v.nx - 1)) port3(g, x == 0, v.u_in[(long long)z * v.ny + y], v.rho0);
   float drho, ux, uy, uz;
   bgk3(g, v.rho0, v.omega, drho, ux, uy, uz);
+  // Recompute the store addresses from the cell index instead of keeping the
+  // 18 load addresses alive across the collision (halves the registers).
+  opaque(c);
+  opaque(pl);
   P3<T>::st(F + c, g[0]);
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
-    const long long off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
-    if (PHASE == 1 || ((nb >> i) & 1u))
-      P3<T>::st(F + i * pl + c, g[i]);
+    const IX off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
+    if (PHASE == 1 || (!NB0 && ((nb >> i) & 1u)))
+      P3<T>::st(F + (i * pl + c), g[i]);
     else
-      P3<T>::st(F + opp3(i) * pl + c + off, g[i]);
+      P3<T>::st(F + (opp3(i) * pl + c + off), g[i]);
   }
   if (MOM) {
     v.drho[c] = drho;
@@ -258,6 +240,75 @@ __global__ void __launch_bounds__(512) k_step3(const View3 v, const int* __restr
     v.uz[c] = uz;
     if (!(isfinite(drho) && isfinite(ux) && isfinite(uy) && isfinite(uz))) atomicOr(v.flag, 1);
   }
+}
+
+// One phase on one row segment.  The mask words are read before waiting for
+// the previous step (they change only between solves), the populations after.
+// Phase A on a segment whose fluid cells have no solid neighbour (and hence
+// no port cell: outside the row reads as solid) takes the select-free path.
+template <class T, int PHASE, int MOM, class IX>
+__device__ __forceinline__ void seg_task3(const View3& v, Seg3 sg, int lane, bool& waited) {
+  const int seg = sg.seg & kSegIndexMask;
+  const bool open = PHASE == 0 && (sg.seg & kSegOpen);
+  const int row = seg / v.nsx;
+  const int s = seg - row * v.nsx;
+  const int z = row / v.ny;
+  const int y = row - z * v.ny;
+  uint32_t nb = 0;  // bit i: cell x + c_i is solid (phase A only)
+  if (PHASE == 0 && !open) {
+    // lanes 0..8: word s of row r = (dz+1)*3 + (dy+1); 9..17: word s-1; 18..26: word s+1
+    uint32_t wv = 0xffffffffu;
+    if (lane < 27) {
+      const int part = lane / 9, r = lane - 9 * part;
+      const int dy = r % 3 - 1, dz = r / 3 - 1;
+      const int dw = part == 0 ? 0 : (part == 1 ? -1 : 1);
+      wv = v.mask[mask3_row(v.ny, v.ms, y + dy, z + dz) + 1 + s + dw];
+    }
+    uint32_t M[9], Lw[9], H[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+      M[r] = __shfl_sync(kFull, wv, r);
+      Lw[r] = __shfl_sync(kFull, wv, 9 + r);
+      H[r] = __shfl_sync(kFull, wv, 18 + r);
+    }
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+      const int r = (cz3(i) + 1) * 3 + (cy3(i) + 1);
+      const uint32_t word = cx3(i) == 0 ? M[r]
+                            : cx3(i) > 0 ? __funnelshift_r(M[r], H[r], 1)
+                                         : __funnelshift_l(Lw[r], M[r], 1);
+      nb |= ((word >> lane) & 1u) << i;
+    }
+  }
+  if (!waited) {  // warp-uniform: the previous step's populations are final from here on
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    waited = true;
+  }
+  if ((sg.word >> lane) & 1u) return;  // solid, or past the row's end
+  const int x = 32 * s + lane;
+  if (open)
+    cell_update3<T, PHASE, MOM, true, IX>(v, x, y, z, 0u);
+  else
+    cell_update3<T, PHASE, MOM, false, IX>(v, x, y, z, nb);
+}
+
+// One phase of one time step over the segment list (warps stride over it).
+// Launched as a programmatic dependent of the previous step.
+template <class T, int PHASE, int MOM, class IX>
+__global__ void __launch_bounds__(512) k_step3(const View3 v, const Seg3* __restrict__ segs,
+                                               const int* __restrict__ n_segs) {
+  // the next step may be scheduled now; it touches populations only after
+  // waiting for this grid to complete
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  const int nseg = *n_segs;
+  const int wpb = blockDim.x >> 5;
+  const int stride = gridDim.x * wpb;
+  bool waited = false;
+  for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < nseg; t += stride)
+    seg_task3<T, PHASE, MOM, IX>(v, segs[t], lane, waited);
+  // every thread waits once, so this grid completes only after the previous one
+  if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 inline int blocks_for(long long n, int threads) {
@@ -284,13 +335,29 @@ __global__ void k_seg3_flags(const View3 v, int total, int* __restrict__ flags) 
   flags[i] = ~v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + s] != 0u;
 }
 
+// Entry of a segment holding fluid: its index, its own mask word, and
+// kSegOpen when none of its fluid cells has a solid cell among its 18
+// neighbours (the bits past the row's end and the padding count as solid).
 __global__ void k_seg3_scatter(const View3 v, int total, const int* __restrict__ flags,
-                               const int* __restrict__ offs, int* __restrict__ segs) {
+                               const int* __restrict__ offs, Seg3* __restrict__ segs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total || !flags[i]) return;
   int y, z, s;
   word3_of(v, i, y, z, s);
-  segs[offs[i]] = (z * v.ny + y) * v.nsx + s;
+  const uint32_t own = v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + s];
+  uint32_t solid_nb = 0;  // bit l: some neighbour of cell 32 s + l is solid
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy) {
+      const uint32_t* row = v.mask + mask3_row(v.ny, v.ms, y + dy, z + dz) + 1;
+      const uint32_t m = row[s];
+      solid_nb |= (dy == 0 && dz == 0) ? 0u : m;        // c_x = 0 (not the cell itself)
+      if (dy != 0 && dz != 0) continue;                 // D3Q19 has no (+-1, +-1, +-1)
+      solid_nb |= __funnelshift_r(m, row[s + 1], 1);    // c_x = +1
+      solid_nb |= __funnelshift_l(row[s - 1], m, 1);    // c_x = -1
+    }
+  const bool open = (solid_nb & ~own) == 0u;
+  const int seg = (z * v.ny + y) * v.nsx + s;
+  segs[offs[i]] = Seg3{seg | (open ? kSegOpen : 0), own};
 }
 
 // ---- reductions ----------------------------------------------------------------
@@ -500,23 +567,33 @@ __global__ void k_unpack3(const View3 v, uint8_t* __restrict__ cells) {
   cells[i] = (uint8_t)((v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + (x >> 5)] >> (x & 31)) & 1u);
 }
 
-template <class T>
-cudaError_t step3_typed(int phase, int moments, const View3& v, const int* segs, const int* n_segs, int blocks,
-                        int threads, cudaStream_t stream) {
-  if (phase == 0)
-    k_step3<T, 0, 0><<<blocks, threads, 0, stream>>>(v, segs, n_segs);
-  else if (moments)
-    k_step3<T, 1, 1><<<blocks, threads, 0, stream>>>(v, segs, n_segs);
-  else
-    k_step3<T, 1, 0><<<blocks, threads, 0, stream>>>(v, segs, n_segs);
-  return cudaGetLastError();
+template <class T, class IX>
+void* step3_kernel(int phase, int moments) {
+  if (phase == 0) return (void*)k_step3<T, 0, 0, IX>;
+  return moments ? (void*)k_step3<T, 1, 1, IX> : (void*)k_step3<T, 1, 0, IX>;
 }
+
+template <class T>
+void* step3_kernel(int phase, int moments, bool idx64) {
+  return idx64 ? step3_kernel<T, long long>(phase, moments) : step3_kernel<T, int>(phase, moments);
+}
+
+void* step3_for(int precision, int phase, int moments, bool idx64) {
+  switch (precision) {
+    case LBM_F32: return step3_kernel<float>(phase, moments, idx64);
+    case LBM_BF16_SHIFTED: return step3_kernel<__nv_bfloat16>(phase, moments, idx64);
+    case LBM_F16_SHIFTED: return step3_kernel<__half>(phase, moments, idx64);
+    default: return nullptr;
+  }
+}
+
+inline bool needs_idx64(const View3& v) { return v.idx64 != 0; }
 
 }  // namespace
 
 size_t seg3_scratch_ints(long long total) { return 2 * (size_t)total + 1 + scan_tmp_ints(total); }
 
-cudaError_t launch_build_segments3(const View3& v, int* scratch, int* segs, int* n_segs, cudaStream_t stream) {
+cudaError_t launch_build_segments3(const View3& v, int* scratch, Seg3* segs, int* n_segs, cudaStream_t stream) {
   const int total = (v.ny - 2) * (v.nz - 2) * v.nsx;
   int* flags = scratch;
   int* offs = scratch + total;  // total + 1
@@ -531,20 +608,33 @@ cudaError_t launch_build_segments3(const View3& v, int* scratch, int* segs, int*
   return cudaMemcpyAsync(n_segs, offs + total, sizeof(int), cudaMemcpyDeviceToDevice, stream);
 }
 
-cudaError_t launch_step3(int precision, int phase, int moments, const View3& v, const int* segs,
-                         const int* n_segs, int grid_warps, int warps_per_block, cudaStream_t stream) {
-  const int threads = 32 * warps_per_block;
-  const int blocks = blocks_for(grid_warps, warps_per_block);
-  cudaError_t e;
-  switch (precision) {
-    case LBM_F32: e = step3_typed<float>(phase, moments, v, segs, n_segs, blocks, threads, stream); break;
-    case LBM_BF16_SHIFTED:
-      e = step3_typed<__nv_bfloat16>(phase, moments, v, segs, n_segs, blocks, threads, stream);
-      break;
-    case LBM_F16_SHIFTED: e = step3_typed<__half>(phase, moments, v, segs, n_segs, blocks, threads, stream); break;
-    default: return cudaErrorInvalidValue;
-  }
-  count_launches(1);
+int step3_resident_blocks(int precision, int phase, int moments, int warps_per_block, const View3& v) {
+  void* k = step3_for(precision, phase, moments, needs_idx64(v));
+  int dev = 0, sms = 0, n = 0;
+  if (!k || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, 0) != cudaSuccess)
+    return 0;
+  return n * sms;
+}
+
+cudaError_t launch_step3(int precision, int phase, int moments, const View3& v, const Seg3* segs,
+                         const int* n_segs, int blocks, int warps_per_block, cudaStream_t stream) {
+  void* k = step3_for(precision, phase, moments, needs_idx64(v));
+  if (!k || blocks < 1) return cudaErrorInvalidValue;
+  void* args[] = {(void*)&v, (void*)&segs, (void*)&n_segs};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(32 * warps_per_block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, k, args);
+  if (e == cudaSuccess) count_launches(1);
   return e;
 }
 

@@ -33,6 +33,8 @@ struct View3 {
   int nsx;               // 32-cell segments per row
   int ms;                // mask words per row: nsx + 2
   float omega, rho0;
+  int idx64;             // step kernels index populations in 64 bits (19 planes reach 2^31
+                         // elements, or LBM3D_INDEX64=1 in the environment), else in 32
 };
 
 __host__ __device__ inline long long mask3_row(int ny, int ms, int y, int z) {
@@ -42,21 +44,34 @@ __host__ __device__ inline long long mask3_words(int ny, int nz, int ms) {
   return (long long)(ny + 2) * (nz + 2) * ms;
 }
 
+// Step work-list entry: segment (z * ny + y) * nsx + s (bits 0..29) with
+// kSegOpen set when no fluid cell of it has a solid neighbour, and its own
+// mask word (bit set = solid), so that the local phase reads no mask.
+struct alignas(8) Seg3 {
+  int seg;
+  uint32_t word;
+};
+constexpr int kSegIndexMask = (1 << 30) - 1;
+constexpr int kSegOpen = 1 << 30;
+static_assert(sizeof(Seg3) == 8, "Seg3 layout");
+
 // Step work-list: the segments (z, y, s) of rows y in [1, ny-2], z in
-// [1, nz-2] holding a fluid cell, as ints (z * ny + y) * nsx + s in
-// ascending order; *n_segs their count.  scratch holds
-// seg3_scratch_ints(total) ints, total = (ny-2)(nz-2) nsx.
+// [1, nz-2] holding a fluid cell, in ascending order; *n_segs their count.
+// scratch holds seg3_scratch_ints(total) ints, total = (ny-2)(nz-2) nsx.
 size_t seg3_scratch_ints(long long total);
-cudaError_t launch_build_segments3(const View3& v, int* scratch, int* segs, int* n_segs, cudaStream_t stream);
+cudaError_t launch_build_segments3(const View3& v, int* scratch, Seg3* segs, int* n_segs, cudaStream_t stream);
 
 // One time step over the work-list.  phase 0 ("A"): pulls from the
 // neighbours' slots and pushes into the slots the neighbours read next
 // (its own where the neighbour is solid); phase 1 ("B"): the cell's own
 // slots only, leaving F[i][cell] = post-collision population i.  moments
 // (phase 1 only): write drho, ux, uy, uz and flag non-finite values.
-// grid_warps: warps launched (>= the work-list's capacity).
-cudaError_t launch_step3(int precision, int phase, int moments, const View3& v, const int* segs,
-                         const int* n_segs, int grid_warps, int warps_per_block, cudaStream_t stream);
+// Warps stride over the list (blocks of warps_per_block warps); launched as
+// a programmatic dependent of the previous kernel on the stream.
+cudaError_t launch_step3(int precision, int phase, int moments, const View3& v, const Seg3* segs,
+                         const int* n_segs, int blocks, int warps_per_block, cudaStream_t stream);
+// blocks of the given shape resident on the whole device at once (0 on error)
+int step3_resident_blocks(int precision, int phase, int moments, int warps_per_block, const View3& v);
 
 // FP64 reductions of the last moments step: result[0] dp, [1] m_in,
 // [2 + r] m_out of region r.  in_cells: cells (dense idx) of the inlet, n_in

@@ -181,6 +181,21 @@ def test_block_shapes_agree_bit_for_bit():
         lat.close()
 
 
+def test_64bit_indexing_gives_the_same_bits(monkeypatch):
+    """The step kernels index populations in 32 bits below 2^31 elements and
+    in 64 bits above; both builds compute the same bits (the 64-bit one forced
+    here on a small lattice)."""
+    cfg = I.config_tree3d_small()
+    out = []
+    for force in ("0", "1"):
+        monkeypatch.setenv("LBM3D_INDEX64", force)
+        lat = L.Lattice3(cfg["cells"], cfg["tau"], cfg["u_max"])
+        r = lat.solve(100)
+        out.append((r["dp"], lat.read(L.FIELD3_POPS)))
+        lat.close()
+    assert out[0][0] == out[1][0] and np.array_equal(out[0][1], out[1][1])
+
+
 def test_argument_and_geometry_checks():
     cells = I.duct3d(16, 6, 5)
     for bad in (np.zeros_like(cells),):  # open frame
