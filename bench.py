@@ -67,6 +67,8 @@ def parse():
                          "captures): tree = 2048 x 1024 distributor, large = 8192 x 4096 channel array, "
                          "tree3d = 384 x 192 x 192 D3Q19 distributor, duct3d = 256 x 128 x 128 D3Q19 duct")
     ap.add_argument("--kernel-steps", type=int, default=4)
+    ap.add_argument("--kernel-cpt", type=int, default=0,
+                    help="kernel case (2D): run with this many cells per thread (0: the tuner's choice)")
     return ap.parse_args()
 
 
@@ -95,11 +97,14 @@ def kernel_case(args):
     else:
         cells, tau, u_max = I.channel_array(8192, 4096, 16, fill=0.5), 0.6, 0.05
     lat = L.Lattice(cells, tau, u_max, precision=prec, residual_every=0)
+    if args.kernel_cpt:
+        lat.set_step_config(8, cells_per_thread=args.kernel_cpt)
     lat.solve(args.kernel_steps)
     r = lat.solve(args.kernel_steps)
+    shape = lat.step_config()
     lat.close()
     print(json.dumps({"kernel_case": args.kernel_case, "precision": args.precision,
-                      "fluid_cells": int((cells == 0).sum()), "dp": r["dp"]}))
+                      "fluid_cells": int((cells == 0).sum()), "dp": r["dp"], "step_config": list(shape)}))
     return 0
 
 

@@ -396,7 +396,10 @@ __device__ __forceinline__ void seg_load(const SegCtx<T>& s, float (&g)[9]) {
 
 // Boundary rules, collision and stores of the lane's cell.  Every lane of the
 // warp calls it (the zero-gradient outlet shuffles across lanes).
-template <class T, int PHASE, int MOM, int FEAT>
+// OPQ: recompute the store offsets after the collision instead of keeping
+// the load offsets alive across it (fewer registers: pays where two cells per
+// thread press on the budget, costs a little elsewhere -- measured).
+template <class T, int PHASE, int MOM, int FEAT, bool OPQ = false>
 __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
   using P = Pop<T>;
   const LatticeView* __restrict__ L = s.L;
@@ -428,7 +431,8 @@ __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
     bgk(g, rho0, s.omega, drho, ux, uy);
 
   T* __restrict__ F = s.F;
-  const int c = s.c, pl = s.pl, pitch = s.pitch;
+  int c = s.c, pl = s.pl, pitch = s.pitch;
+  if (OPQ) asm volatile("" : "+r"(c), "+r"(pl), "+r"(pitch));
   const unsigned nb = s.nb;
   if (PHASE == 0) {
     FST(c, g[0]);
@@ -479,7 +483,7 @@ __device__ __forceinline__ void phase_task(const LatticeView* __restrict__ views
 #pragma unroll
   for (int k = 0; k < CPT; ++k) seg_load<T, PHASE, CG, FEAT>(s[k], g[k]);
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) seg_update<T, PHASE, MOM, FEAT>(s[k], g[k]);
+  for (int k = 0; k < CPT; ++k) seg_update<T, PHASE, MOM, FEAT, (CPT > 1)>(s[k], g[k]);
 }
 
 // One phase of one time step over the whole segment list.  Launched as a
