@@ -74,6 +74,54 @@ def test_duct_with_two_outlet_regions():
     lat.close()
 
 
+def test_medium_tree_matches_oracle():
+    """A 192 x 96 x 96 distributor (four generations, 16 outlet regions; the
+    benchmark tree at half size in each axis), 600 steps: long enough for the
+    flow to reach every outlet (a sound wave needs ~330 steps to cross)."""
+    cfg = I.config_tree3d(192, 96, 96)
+    lat, sv, g, o = _check_solve(cfg["cells"], cfg["tau"], cfg["u_max"], 600)
+    assert g["n_outlets"] == 16 and np.all(o["m_out"] > 1e-3 * o["m_in"] / 16)
+    lat.close()
+
+
+def test_full_size_pair_on_sampled_cells():
+    """The benchmark's 384 x 192 x 192 distributor in its launch configuration:
+    one step pair from random populations on the GPU; for each sampled cell
+    the oracle runs the same two steps on the 5 x 5 x 5 block around it
+    (two steps reach two cells, so the centre is exact; at the inlet and the
+    outlet the block is cut at the lattice's end, where the port rules act)."""
+    cfg = I.config_tree3d()
+    cells = cfg["cells"]
+    nz, ny, nx = cells.shape
+    w = _w3()
+    rng = np.random.default_rng(11)
+    g0 = rng.standard_normal((19, nz, ny, nx), dtype=np.float32)
+    g0 *= (0.05 * w).astype(np.float32)[:, None, None, None]
+    lat = L.Lattice3(cells, cfg["tau"], cfg["u_max"])
+    lat.load_state(g0)
+    lat.solve(2)
+    got = lat.read(L.FIELD3_POPS)
+    lat.close()
+    p_full = o3.make_params3(nx, ny, nz, cfg["tau"], u_max=cfg["u_max"])
+    u_in = o3.inlet_profile3(p_full, cells)
+    zf, yf, xf = np.nonzero(cells == 0)
+    picks = list(rng.choice(len(xf), 48, replace=False))
+    picks += list(np.flatnonzero(xf == 0)[:4]) + list(np.flatnonzero(xf == nx - 1)[:4])  # port cells
+    for k in picks:
+        z, y, x = int(zf[k]), int(yf[k]), int(xf[k])
+        z0, y0, x0 = max(0, z - 2), max(0, y - 2), max(0, x - 2)
+        z1, y1, x1 = min(nz, z + 3), min(ny, y + 3), min(nx, x + 3)
+        sub = np.ascontiguousarray(cells[z0:z1, y0:y1, x0:x1])
+        f0 = g0[:, z0:z1, y0:y1, x0:x1].astype(np.float64) + w[:, None, None, None]
+        f0 *= (sub == 0)[None]
+        p = o3.make_params3(x1 - x0, y1 - y0, z1 - z0, cfg["tau"], u_max=cfg["u_max"])
+        ui = np.ascontiguousarray(u_in[z0:z1, y0:y1]) if x0 == 0 else np.zeros((z1 - z0, y1 - y0))
+        f, *_ = o3.run3(p, sub, ui, np.ascontiguousarray(f0), 2)
+        ref = f[:, z - z0, y - y0, x - x0]
+        g = got[:, z, y, x].astype(np.float64) + w
+        assert np.abs(g - ref).max() <= 2e-6, (z, y, x, np.abs(g - ref).max())
+
+
 def test_one_pair_from_a_random_state():
     """Two steps (phase A, phase B) from random post-collision populations:
     every direction of streaming and bounce-back, and the port rules, in
