@@ -105,6 +105,13 @@ lbm_status lbm3d_solve(lbm3d_handle h, int64_t n_steps, lbm3d_solve_result* out)
  * smaller idx); re-initialise (params.reinit), then solve n_steps.       */
 lbm_status lbm3d_optimize_step(lbm3d_handle h, int32_t n_swap, int64_t n_steps, lbm3d_opt_result* out);
 
+/* The whole loop of Sec. 2.3 on a 3D lattice, with the plan and summary of
+ * lbm_optimize (lbm.h): a first solve, then up to max_iter iterations of
+ * lbm3d_optimize_step, the same stopping test, n_swap halving and keeping
+ * of the best state (populations, mask and fields) as in 2D.  dp_history:
+ * host double[max_iter + 1] or NULL.  out: host, caller-owned.           */
+lbm_status lbm3d_optimize(lbm3d_handle h, const lbm_opt_plan* plan, double* dp_history, lbm_opt_summary* out);
+
 /* Copy one field (a single LBM3D_FIELD_* bit) into dst; dst_is_device != 0:
  * dst is device memory, written on the handle's stream.                   */
 lbm_status lbm3d_read_fields(lbm3d_handle h, uint32_t which, void* dst, size_t dst_bytes, int dst_is_device);

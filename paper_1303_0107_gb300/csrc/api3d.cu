@@ -38,6 +38,10 @@ struct lbm3d_handle_s {
   uint8_t* d_cells = nullptr; // [ncells] unpacked mask (allocated on first use)
   double* h_result = nullptr; // pinned
   int* h_small = nullptr;     // pinned: [0] flag, [1..8] info, [9] n_swap, [10] n_segs
+  long long mask_words = 0;
+  void* best_f = nullptr;      // saved state of the optimisation loop (allocated on first use)
+  uint32_t* best_mask = nullptr;
+  float* best_fields = nullptr;
   int nseg = 0;               // segments in the work-list (host copy)
   int resident[3] = {0, 0, 0};  // resident blocks of phase A, B, B with moments at wpb
   int64_t steps_done = 0;
@@ -305,6 +309,7 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   h->n_regions = (int)g.out_off.size() - 1;
   // mask: all padding set, fluid cells cleared
   const long long mw = mask3_words(p.ny, p.nz, v.ms);
+  h->mask_words = mw;
   std::vector<uint32_t> mask((size_t)mw, 0xffffffffu);
   for (int z = 0; z < p.nz; ++z)
     for (int y = 0; y < p.ny; ++y) {
@@ -375,6 +380,29 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   return set_shape(h, 8);
 }
 
+// populations, mask and fields copied aside (save) or back (restore) on the device
+lbm_status keep_state(lbm3d_handle h, bool save) {
+  const size_t fb = (size_t)kQ3 * h->v.plane * h->elem, mb = sizeof(uint32_t) * h->mask_words,
+               vb = sizeof(float) * 4 * h->v.plane;
+  if (!h->best_f) {
+    CU3(h->alloc(&h->best_f, fb));
+    CU3(h->alloc(&h->best_mask, mb));
+    CU3(h->alloc(&h->best_fields, vb));
+  }
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  if (save) {
+    CU3(cudaMemcpyAsync(h->best_f, h->v.f, fb, k, h->stream));
+    CU3(cudaMemcpyAsync(h->best_mask, h->v.mask, mb, k, h->stream));
+    CU3(cudaMemcpyAsync(h->best_fields, h->v.drho, vb, k, h->stream));
+    CU3(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+  }
+  CU3(cudaMemcpyAsync(h->v.f, h->best_f, fb, k, h->stream));
+  CU3(cudaMemcpyAsync(h->v.mask, h->best_mask, mb, k, h->stream));
+  CU3(cudaMemcpyAsync(h->v.drho, h->best_fields, vb, k, h->stream));
+  return build_worklist(h);  // the restored mask has its own segments
+}
+
 }  // namespace
 
 extern "C" {
@@ -416,6 +444,54 @@ lbm_status lbm3d_optimize_step(lbm3d_handle h, int32_t n_swap, int64_t n_steps, 
   out->n_swapped = n;
   out->fluid_count = h->fluid;
   return solve3(h, n_steps, &out->solve);
+}
+
+lbm_status lbm3d_optimize(lbm3d_handle h, const lbm_opt_plan* plan, double* dp_history, lbm_opt_summary* out) {
+  if (!h || !plan || !out) return fail(LBM_ERR_ARG, "handle, plan or out is NULL");
+  const lbm_opt_plan& P = *plan;
+  if (P.n_steps < 2 || (P.n_steps % 2) != 0 || P.max_iter < 0 || P.n_swap < 1 || P.patience < 1 ||
+      (P.adapt != 0 && P.adapt != 1) || (P.keep_best != 0 && P.keep_best != 1) || P.reserved != 0 ||
+      !std::isfinite(P.tol))
+    return fail(LBM_ERR_ARG, "plan: n_steps even >= 2, max_iter >= 0, n_swap >= 1, patience >= 1, flags 0/1");
+  std::memset(out, 0, sizeof(*out));
+  lbm3d_solve_result r;
+  lbm_status st = solve3(h, P.n_steps, &r);
+  if (st != LBM_OK) return st;
+  std::vector<double> hist{r.dp};
+  if (dp_history) dp_history[0] = r.dp;
+  int best = 0, calm = 0;
+  int32_t n_swap = P.n_swap;
+  if (P.keep_best && (st = keep_state(h, true)) != LBM_OK) return st;
+  for (int k = 1; k <= P.max_iter; ++k) {
+    out->iterations = k - 1;
+    out->n_swap_final = n_swap;
+    lbm3d_opt_result o;
+    if ((st = lbm3d_optimize_step(h, n_swap, P.n_steps, &o)) != LBM_OK) return st;
+    out->swapped += o.n_swapped;
+    const double dp = o.solve.dp;
+    hist.push_back(dp);
+    if (dp_history) dp_history[k] = dp;
+    if (dp < hist[best]) {
+      best = k;
+      if (P.keep_best && (st = keep_state(h, true)) != LBM_OK) return st;
+    }
+    if (P.adapt && dp > hist[k - 1]) n_swap = std::max(1, n_swap / 2);
+    if (P.tol > 0.0) {
+      calm = std::fabs(dp - hist[k - 1]) <= P.tol * std::fabs(dp) ? calm + 1 : 0;
+      if (calm >= P.patience) {
+        out->stopped = 1;
+        break;
+      }
+    }
+  }
+  out->iterations = (int32_t)hist.size() - 1;
+  out->n_swap_final = n_swap;
+  out->best_iter = best;
+  out->dp_first = hist.front();
+  out->dp_best = hist[best];
+  out->dp_last = hist.back();
+  if (P.keep_best && best != out->iterations && (st = keep_state(h, false)) != LBM_OK) return st;
+  return LBM_OK;
 }
 
 lbm_status lbm3d_read_fields(lbm3d_handle h, uint32_t which, void* dst, size_t dst_bytes, int dst_is_device) {

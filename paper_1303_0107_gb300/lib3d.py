@@ -4,8 +4,8 @@ import ctypes
 
 import numpy as np
 
-from .lib import (F32, MAX_OUTLETS, PRECISIONS, REINIT_WARM, _VP, _buffer, _check, _stream_ptr,
-                  load_library)
+from .lib import (F32, MAX_OUTLETS, PRECISIONS, REINIT_WARM, OptPlan, OptSummary, _VP, _buffer, _check,
+                  _stream_ptr, load_library)
 
 FIELD3_DRHO, FIELD3_UX, FIELD3_UY, FIELD3_UZ, FIELD3_MASK, FIELD3_POPS = 1, 2, 4, 8, 16, 32
 Q3 = 19
@@ -53,8 +53,9 @@ def _lib():
         L.lbm3d_kernel_time.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.lbm3d_set_block.argtypes = [H, ctypes.c_int32]
+        L.lbm3d_optimize.argtypes = [H, ctypes.POINTER(OptPlan), _VP, ctypes.POINTER(OptSummary)]
         for name in ("lbm3d_create", "lbm3d_solve", "lbm3d_optimize_step", "lbm3d_read_fields", "lbm3d_load_state",
-                     "lbm3d_select_swaps", "lbm3d_kernel_time", "lbm3d_set_block"):
+                     "lbm3d_select_swaps", "lbm3d_kernel_time", "lbm3d_set_block", "lbm3d_optimize"):
             getattr(L, name).restype = ctypes.c_int
         _bound = True
     return L
@@ -109,6 +110,18 @@ class Lattice3:
         out = r.solve.to_dict()
         out.update(n_swapped=r.n_swapped, fluid_count=r.fluid_count)
         return out
+
+    def optimize(self, n_steps, max_iter, n_swap, tol=0.0, patience=3, adapt=False, keep_best=False):
+        """The whole loop of Sec. 2.3 (lbm3d_optimize); returns the summary with the dp history."""
+        plan = OptPlan(int(n_steps), int(max_iter), int(n_swap), float(tol), int(patience), int(bool(adapt)),
+                       int(bool(keep_best)), 0)
+        hist = np.zeros(int(max_iter) + 1, np.float64)
+        out = OptSummary()
+        _check(_lib().lbm3d_optimize(self._h, ctypes.byref(plan), hist.ctypes.data, ctypes.byref(out)),
+               "lbm3d_optimize")
+        d = {k: getattr(out, k) for k, _ in OptSummary._fields_}
+        d["history"] = hist[:out.iterations + 1].copy()
+        return d
 
     def _shape_dtype(self, field):
         cells = (self.nz, self.ny, self.nx)

@@ -196,6 +196,53 @@ def test_optimize_step_matches_oracle_exchange():
     lat.close()
 
 
+def _loop_reference(cfg, n_steps, max_iter, n_swap, **plan):
+    """The plan driven from Python through the per-step entry points, with the
+    oracle's run_plan taking the decisions."""
+    import oracle as ora
+    h = L.Lattice3(cfg["cells"], cfg["tau"], cfg["u_max"])
+    masks, ux = [], []
+
+    def record(dp):
+        masks.append(h.read(L.FIELD3_MASK))
+        ux.append(h.read(L.FIELD3_UX))
+        return dp
+
+    out = ora.run_plan(lambda: record(h.solve(n_steps)["dp"]), lambda ns: record(h.optimize_step(ns, n_steps)["dp"]),
+                       n_swap, max_iter, **plan)
+    h.close()
+    return out, masks, ux
+
+
+@pytest.mark.parametrize("plan", [dict(), dict(adapt=True), dict(tol=2e-2, patience=2, adapt=True)])
+def test_optimize_loop_equals_per_step_calls_and_oracle_decisions(plan):
+    cfg = I.config_tree3d_small()
+    ref, masks, _ = _loop_reference(cfg, 100, 6, 40, **plan)
+    h = L.Lattice3(cfg["cells"], cfg["tau"], cfg["u_max"])
+    got = h.optimize(100, 6, 40, keep_best=False, **plan)
+    assert list(got["history"]) == ref["history"]
+    assert got["iterations"] == ref["iterations"] and bool(got["stopped"]) == ref["stopped"]
+    assert got["best_iter"] == ref["best_iter"] and got["dp_best"] == ref["dp_best"]
+    assert got["n_swap_final"] == ref["n_swap_final"]
+    assert np.array_equal(h.read(L.FIELD3_MASK), masks[-1])
+    h.close()
+
+
+def test_optimize_loop_keeps_the_best_state():
+    cfg = I.config_tree3d_small()
+    ref, masks, ux = _loop_reference(cfg, 100, 5, 60)
+    h = L.Lattice3(cfg["cells"], cfg["tau"], cfg["u_max"])
+    got = h.optimize(100, 5, 60, keep_best=True)
+    b = got["best_iter"]
+    assert b == ref["best_iter"] and list(got["history"]) == ref["history"]
+    assert np.array_equal(h.read(L.FIELD3_MASK), masks[b]) and np.array_equal(h.read(L.FIELD3_UX), ux[b])
+    assert h.solve(2)["fluid_cells"] == int((cfg["cells"] == 0).sum())  # the restored state steps on
+    with pytest.raises(L.LbmError) as e:
+        h.optimize(101, 2, 2)
+    assert e.value.status == 1
+    h.close()
+
+
 def test_cold_reinit_and_state_roundtrip():
     cfg = I.config_tree3d_small()
     lat = L.Lattice3(cfg["cells"], cfg["tau"], cfg["u_max"], reinit=L.REINIT_COLD)
