@@ -8,10 +8,14 @@ import numpy as np
 from . import lib, make_params, select, REINIT_WARM
 
 
+COLLIDE_BGK, COLLIDE_REGULARIZED, COLLIDE_SMAGORINSKY = 0, 1, 2
+
+
 class Params3(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("periodic", ctypes.c_int32), ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
-                ("u_max", ctypes.c_double)]
+                ("u_max", ctypes.c_double), ("collision", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("c_smag", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -42,6 +46,8 @@ def _lib():
         L.ora3_apply.argtypes = [P, _U8, _D, _I32, _I32, ctypes.c_int32, ctypes.c_int32]
         L.ora3_apply.restype = ctypes.c_int64
         L.ora3_regularize.argtypes = [_D] + [ctypes.c_double] * 4
+        L.ora3_collide.argtypes = [P, _D]
+        L.ora3_collide.restype = ctypes.c_double
         _ready = True
     return L
 
@@ -50,8 +56,16 @@ def _p(a, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
-def make_params3(nx, ny, nz, tau, rho0=1.0, u_max=0.0, periodic=0):
-    return Params3(int(nx), int(ny), int(nz), int(periodic), float(tau), float(rho0), float(u_max))
+def make_params3(nx, ny, nz, tau, rho0=1.0, u_max=0.0, periodic=0, collision=COLLIDE_BGK, c_smag=0.0):
+    return Params3(int(nx), int(ny), int(nz), int(periodic), float(tau), float(rho0), float(u_max), int(collision),
+                   0, float(c_smag))
+
+
+def collide3(p, f):
+    """One cell's moments and collision (a copy); returns (f_post, tau_eff)."""
+    f = np.ascontiguousarray(f, np.float64).copy()
+    tau = _lib().ora3_collide(ctypes.byref(p), _p(f, ctypes.c_double))
+    return f, tau
 
 
 def lattice3():

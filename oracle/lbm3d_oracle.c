@@ -33,6 +33,7 @@ static const double CS2_3 = 1.0 / 3.0;
 
 enum { ORA3_OK = 0, ORA3_ERR_ARG = 1, ORA3_ERR_GEOMETRY = 2, ORA3_ERR_DIVERGED = 5 };
 enum { ORA3_REINIT_WARM = 0, ORA3_REINIT_COLD = 1 };
+enum { ORA3_COLLIDE_BGK = 0, ORA3_COLLIDE_REGULARIZED = 1, ORA3_COLLIDE_SMAGORINSKY = 2 };
 
 typedef struct {
   int32_t nx, ny, nz;  /* x along the flow, y across, z through the depth   */
@@ -40,6 +41,9 @@ typedef struct {
                           wrapped x axis has no ports (checks of the bulk
                           scheme only)                                       */
   double tau, rho0, u_max;
+  int32_t collision;   /* ORA3_COLLIDE_*, as in 2D                           */
+  int32_t pad;
+  double c_smag;       /* Smagorinsky constant                               */
 } ora3_params;
 
 void ora3_lattice(int32_t* cx, int32_t* cy, int32_t* cz, int32_t* opp, double* w, double* cs2) {
@@ -213,7 +217,67 @@ static void regularize3(double* f, double rho, double ux, double uy, double uz) 
 
 void ora3_regularize(double* f, double rho, double ux, double uy, double uz) { regularize3(f, rho, ux, uy, uz); }
 
+/* Relaxation time of the Smagorinsky closure (the 2D oracle's derivation
+ * with the six components of the symmetric 3D stress): nu_t = C^2 |S|,
+ * |S| = sqrt(2 S:S), S = -Pi / (2 rho c_s^2 tau_eff), tau_eff = tau + nu_t /
+ * c_s^2, whose positive root is
+ *   tau_eff = (tau + sqrt(tau^2 + 2 sqrt(2) C^2 sqrt(Pi:Pi) / (rho c_s^4))) / 2,
+ * Pi:Pi = Pxx^2 + Pyy^2 + Pzz^2 + 2 (Pxy^2 + Pxz^2 + Pyz^2).                */
+static double smagorinsky_tau3(double tau, double c, double rho, const double* f, double ux, double uy,
+                               double uz) {
+  double pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+  for (int i = 0; i < 19; ++i) {
+    double nq = f[i] - ora3_feq(i, rho, ux, uy, uz);
+    pxx += C3X[i] * C3X[i] * nq;
+    pyy += C3Y[i] * C3Y[i] * nq;
+    pzz += C3Z[i] * C3Z[i] * nq;
+    pxy += C3X[i] * C3Y[i] * nq;
+    pxz += C3X[i] * C3Z[i] * nq;
+    pyz += C3Y[i] * C3Z[i] * nq;
+  }
+  double pp = pxx * pxx + pyy * pyy + pzz * pzz + 2.0 * (pxy * pxy + pxz * pxz + pyz * pyz);
+  return 0.5 * (tau + sqrt(tau * tau + 2.0 * sqrt(2.0) * c * c * sqrt(pp) / (rho * CS2_3 * CS2_3)));
+}
+
+/* The collision of one cell with moments (rho, u), in place, as in 2D:
+ *   BGK:          f_i <- f_i - (f_i - f_i^eq) / tau;
+ *   regularised:  f_i <- f_i^eq + (1 - 1/tau) (second-order Hermite projection
+ *                 of f - f^eq);
+ *   Smagorinsky:  BGK with the local tau_eff above.                          */
+static void collide3(const ora3_params* p, double* f, double rho, double ux, double uy, double uz) {
+  if (p->collision == ORA3_COLLIDE_REGULARIZED) {
+    double fr[19];
+    for (int i = 0; i < 19; ++i) fr[i] = f[i];
+    regularize3(fr, rho, ux, uy, uz);
+    for (int i = 0; i < 19; ++i) {
+      double eq = ora3_feq(i, rho, ux, uy, uz);
+      f[i] = eq + (1.0 - 1.0 / p->tau) * (fr[i] - eq);
+    }
+    return;
+  }
+  double tau = p->tau;
+  if (p->collision == ORA3_COLLIDE_SMAGORINSKY) tau = smagorinsky_tau3(p->tau, p->c_smag, rho, f, ux, uy, uz);
+  for (int i = 0; i < 19; ++i) f[i] = f[i] - (f[i] - ora3_feq(i, rho, ux, uy, uz)) / tau;
+}
+
+/* The moments and collision of one cell (for the pins); returns tau_eff. */
+double ora3_collide(const ora3_params* p, double* f) {
+  double rho = 0, jx = 0, jy = 0, jz = 0;
+  for (int i = 0; i < 19; ++i) {
+    rho += f[i];
+    jx += C3X[i] * f[i];
+    jy += C3Y[i] * f[i];
+    jz += C3Z[i] * f[i];
+  }
+  double ux = jx / rho, uy = jy / rho, uz = jz / rho;
+  double tau = p->collision == ORA3_COLLIDE_SMAGORINSKY ? smagorinsky_tau3(p->tau, p->c_smag, rho, f, ux, uy, uz)
+                                                         : p->tau;
+  collide3(p, f, rho, ux, uy, uz);
+  return tau;
+}
+
 /* One time step (stream with halfway bounce-back, ports, BGK collision).
+ * Collision: BGK, regularised or Smagorinsky (collide3).
  * Ports (the 2D rules of Sec. 3.3 carried to 3D, regularised):
  *   inlet x = 0: velocity (u_in, 0, 0); rho from mass and x-momentum of the
  *     known populations, rho = (sum_{c_x=0} f + 2 sum_{c_x<0} f) / (1 - u);
@@ -269,7 +333,8 @@ void ora3_step(const ora3_params* p, const uint8_t* solid, const double* u_in, c
           jz += C3Z[i] * f[i];
         }
         double ux = jx / rho, uy = jy / rho, uz = jz / rho;
-        for (int i = 0; i < 19; ++i) fn[i * n + c] = f[i] - (f[i] - ora3_feq(i, rho, ux, uy, uz)) / p->tau;
+        collide3(p, f, rho, ux, uy, uz);
+        for (int i = 0; i < 19; ++i) fn[i * n + c] = f[i];
         if (rho_out) { rho_out[c] = rho; ux_out[c] = ux; uy_out[c] = uy; uz_out[c] = uz; }
       }
 }

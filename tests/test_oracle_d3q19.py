@@ -370,3 +370,99 @@ def test_exchange_keeps_the_volume_and_resets_the_swapped_cells():
     assert out["fluid_count"] == before and int((sv.solid == 0).sum()) == before
     assert np.all(sv.solid.reshape(-1)[out["solid_idx"]] == 0)
     assert np.all(sv.solid.reshape(-1)[out["fluid_idx"]] == 1)
+
+
+def _random_cell(rng, scale=0.1):
+    cx, cy, cz, _, w, _ = o3.lattice3()
+    return w * (1 + scale * rng.standard_normal(19))
+
+
+def _moments(f):
+    cx, cy, cz, _, _, _ = o3.lattice3()
+    c = np.stack([cx, cy, cz], 1).astype(float)
+    rho = f.sum()
+    return rho, c.T @ f / rho, c
+
+
+@pytest.mark.parametrize("collision,c_smag", [(o3.COLLIDE_BGK, 0.0), (o3.COLLIDE_REGULARIZED, 0.0),
+                                              (o3.COLLIDE_SMAGORINSKY, 0.0), (o3.COLLIDE_SMAGORINSKY, 0.3)])
+def test_collision_models_relax_the_stress_as_defined(collision, c_smag):
+    """One cell: every model keeps rho and j; BGK scales f - f^eq by
+    (1 - 1/tau); the regularised model scales the six components of the
+    non-equilibrium stress by (1 - 1/tau) and leaves f - f^eq in the
+    second-order Hermite span; the Smagorinsky model is BGK at tau_eff, where
+    tau_eff - tau = nu_t / c_s^2 with nu_t = C^2 |S|, |S| = sqrt(2 S:S) and
+    S = -Pi / (2 rho c_s^2 tau_eff) (the closure's definition)."""
+    cx, cy, cz, _, w, cs2 = o3.lattice3()
+    tau = 0.7
+    p = o3.make_params3(4, 3, 3, tau, collision=collision, c_smag=c_smag)
+    rng = np.random.default_rng(21)
+    for _ in range(4):
+        f = _random_cell(rng)
+        rho, u, c = _moments(f)
+        fe = np.array([o3.feq3(i, rho, *u) for i in range(19)])
+        g, tau_eff = o3.collide3(p, f)
+        assert g.sum() == pytest.approx(rho, abs=1e-15) and np.allclose(c.T @ g, c.T @ f, atol=1e-15)
+        pi0 = np.einsum("i,ia,ib->ab", f - fe, c, c)
+        pi1 = np.einsum("i,ia,ib->ab", g - fe, c, c)
+        if collision == o3.COLLIDE_REGULARIZED:
+            assert np.allclose(pi1, (1 - 1 / tau) * pi0, atol=1e-16)
+            basis = np.stack([w * (c[:, a] * c[:, b] - cs2 * (a == b))
+                              for a, b in ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))], 1)
+            coef = np.linalg.lstsq(basis, g - fe, rcond=None)[0]
+            assert np.abs(basis @ coef - (g - fe)).max() < 1e-16
+        else:
+            if collision == o3.COLLIDE_SMAGORINSKY:
+                S = -pi0 / (2 * rho * cs2 * tau_eff)
+                nu_t = c_smag ** 2 * np.sqrt(2 * (S * S).sum())
+                assert (tau_eff - tau) * cs2 == pytest.approx(nu_t, rel=1e-12, abs=1e-18)
+                assert (tau_eff > tau) == (c_smag > 0)
+            else:
+                assert tau_eff == tau
+            assert np.allclose(g - fe, (1 - 1 / tau_eff) * (f - fe), atol=1e-16)
+    if collision == o3.COLLIDE_SMAGORINSKY and c_smag == 0.0:  # C = 0 is BGK to the bit
+        f = _random_cell(rng)
+        assert np.array_equal(o3.collide3(p, f)[0], o3.collide3(o3.make_params3(4, 3, 3, tau), f)[0])
+
+
+def test_regularised_shear_wave_decays_at_the_lattice_viscosity():
+    """The regularised model keeps the viscosity of BGK, nu = (tau - 1/2)/3:
+    its shear-wave decay converges to nu |k|^2 at second order."""
+    def rate_error(n, tau=0.8):
+        z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        k = 2 * np.pi / n
+        phase = k * z
+        solid = np.zeros((n, n, n), np.uint8)
+        p = o3.make_params3(n, n, n, tau, periodic=WRAP_ALL, collision=o3.COLLIDE_REGULARIZED)
+        nu = (tau - 0.5) / 3
+        T = int(1 / (nu * k * k))
+        f0 = o3.init_state3(p, solid, np.ones_like(phase), 1e-4 * np.sin(phase), np.zeros_like(phase),
+                            np.zeros_like(phase))
+        f1, _, u1, *_ = o3.run3(p, solid, np.zeros((n, n)), f0, T // 5)
+        _, _, u2, *_ = o3.run3(p, solid, np.zeros((n, n)), f1, T)
+        a1, a2 = (2 * (u * np.sin(phase)).mean() for u in (u1, u2))
+        return -math.log(a2 / a1) / T / (nu * k * k) - 1
+    e16, e32 = rate_error(16), rate_error(32)
+    assert abs(e32) < 4e-3 and 3.3 < e16 / e32 < 4.7
+
+
+def test_smagorinsky_damps_a_shear_wave_more_as_c_grows_and_c0_is_bgk():
+    """The eddy viscosity is non-negative and grows with C: a shear wave of
+    finite amplitude ends weaker for every larger C; C = 0 is BGK exactly."""
+    n, tau = 16, 0.55
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    phase = 2 * np.pi / n * z
+    solid = np.zeros((n, n, n), np.uint8)
+
+    def run(coll, c):
+        p = o3.make_params3(n, n, n, tau, periodic=WRAP_ALL, collision=coll, c_smag=c)
+        f0 = o3.init_state3(p, solid, np.ones_like(phase), 0.05 * np.sin(phase), np.zeros_like(phase),
+                            np.zeros_like(phase))
+        f, _, ux, *_ = o3.run3(p, solid, np.zeros((n, n)), f0, 200)
+        return f, 2 * (ux * np.sin(phase)).mean()
+
+    f_bgk, a_bgk = run(o3.COLLIDE_BGK, 0.0)
+    f_c0, a_c0 = run(o3.COLLIDE_SMAGORINSKY, 0.0)
+    assert np.array_equal(f_bgk, f_c0)
+    amps = [run(o3.COLLIDE_SMAGORINSKY, c)[1] for c in (0.1, 0.2, 0.5, 1.0)]
+    assert a_bgk > amps[0] > amps[1] > amps[2] > amps[3] > 0
