@@ -404,6 +404,17 @@ def leg_d3q19(L, I, stream, peak, cpu_seconds=4.0):
                                       "us_per_step": 1e3 * ms / nl, "achieved_gbs": gbs,
                                       "frac_of_measured_hbm": gbs / peak, "dp": r["dp"]}
             h.close()
+    for name, coll, c in (("regularized", L.COLLIDE_REGULARIZED, 0.0), ("smagorinsky_c0.1", L.COLLIDE_SMAGORINSKY, 0.1)):
+        h = L.Lattice3(cfg["cells"], cfg["tau"], cfg["u_max"], collision=coll, c_smag=c, stream=stream)
+        h.solve(100)
+        h.kernel_time(reset=True)
+        r = h.solve(1000)
+        ms, nl, nu = h.kernel_time()
+        out[f"tree3d_384x192x192_f32_{name}"] = {"glups": nu / (ms / 1e3) / 1e9, "us_per_step": 1e3 * ms / nl,
+                                                 "glups_vs_bgk": (nu / (ms / 1e3) / 1e9)
+                                                 / out["tree3d_384x192x192_f32"]["glups"],
+                                                 "dp_rel_to_bgk": r["dp"] / out["tree3d_384x192x192_f32"]["dp"] - 1}
+        h.close()
     h = L.Lattice3(cfg["cells"], cfg["tau"], cfg["u_max"], stream=stream)
     fluid = int((cfg["cells"] == 0).sum())
     n_swap = max(1, fluid // 500)

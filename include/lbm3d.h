@@ -49,7 +49,11 @@ typedef struct {
                           the inlet cell's fluid run along y and along z, s the cell
                           centre's position in its run (Sec. 3.3's parabola per axis) */
   int32_t reinit;      /* lbm_reinit, as in 2D */
-  int32_t reserved[3]; /* zero */
+  int32_t collision;   /* lbm_collision, as in 2D: BGK, regularised BGK (the non-equilibrium
+                          part relaxed on its second-order Hermite projection) or Smagorinsky
+                          (BGK at the local tau_eff of the closure nu_t = C^2 |S|) */
+  double c_smag;       /* Smagorinsky constant C (>= 0) */
+  int32_t reserved[2]; /* zero */
 } lbm3d_params;
 
 typedef struct {

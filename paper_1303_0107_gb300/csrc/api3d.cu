@@ -101,7 +101,11 @@ lbm_status check_params3(const lbm3d_params& p) {
   if (p.precision != LBM_F32 && p.precision != LBM_BF16_SHIFTED && p.precision != LBM_F16_SHIFTED)
     return fail(LBM_ERR_ARG, "unknown precision");
   if (p.reinit != LBM_REINIT_WARM && p.reinit != LBM_REINIT_COLD) return fail(LBM_ERR_ARG, "unknown reinit");
-  if (p.reserved[0] || p.reserved[1] || p.reserved[2]) return fail(LBM_ERR_ARG, "reserved fields must be 0");
+  if (p.collision != LBM_COLLIDE_BGK && p.collision != LBM_COLLIDE_REGULARIZED &&
+      p.collision != LBM_COLLIDE_SMAGORINSKY)
+    return fail(LBM_ERR_ARG, "unknown collision model");
+  if (!(p.c_smag >= 0.0) || !std::isfinite(p.c_smag)) return fail(LBM_ERR_ARG, "c_smag must be >= 0");
+  if (p.reserved[0] || p.reserved[1]) return fail(LBM_ERR_ARG, "reserved fields must be 0");
   return LBM_OK;
 }
 
@@ -300,6 +304,9 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   const char* force64 = std::getenv("LBM3D_INDEX64");
   v.idx64 = ((long long)kQ3 * v.plane >= (1ll << 31) || (force64 && std::strcmp(force64, "1") == 0)) ? 1 : 0;
   v.omega = (float)(1.0 / p.tau);
+  v.tau = (float)p.tau;
+  v.collision = p.collision;
+  v.c_smag = (float)p.c_smag;
   v.rho0 = (float)p.rho0;
   h->elem = storage_bytes3(p.precision);
   h->ncells = (long long)p.nx * p.ny * p.nz;

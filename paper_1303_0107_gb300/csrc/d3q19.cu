@@ -134,6 +134,58 @@ __device__ __forceinline__ void bgk3(float (&g)[kQ], float rho0, float omega, fl
   close_moments3(g, drho, jx, jy, jz);
 }
 
+// The collision models beyond BGK (regularised, Smagorinsky), in place, in
+// the shifted form: with e_i the shifted equilibria and Pi = sum c c (g - e),
+//   regularised   g_i = e_i + (1 - omega) 4.5 w_i Q_i : Pi  (Q_i = c_i c_i - I/3);
+//   Smagorinsky   g_i += omega_eff (e_i - g_i), omega_eff = 1 / tau_eff,
+//                 tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C^2 sqrt(Pi:Pi) / rho)) / 2,
+// the positive root of the closure nu_t = C^2 |S| with S from Pi (c_s^4 = 1/9).
+// Mass and momentum are then closed exactly, as for BGK.
+__device__ __forceinline__ void collide_other3(float (&g)[kQ], float rho0, float omega, float tau, int model,
+                                               float c_smag, float& drho, float& ux, float& uy, float& uz) {
+  float jx, jy, jz;
+  moments3(g, drho, jx, jy, jz);
+  const float rho = rho0 + drho;
+  const float inv = 1.0f / rho;
+  ux = jx * inv;
+  uy = jy * inv;
+  uz = jz * inv;
+  const float t0 = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
+  float e[kQ];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) e[i] = geq3(i, rho, t0, ux, uy, uz);
+  float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const float nq = g[i] - e[i];
+    if (cx3(i) != 0) pxx += nq;
+    if (cy3(i) != 0) pyy += nq;
+    if (cz3(i) != 0) pzz += nq;
+    pxy += cmul(cx3(i) * cy3(i), nq);
+    pxz += cmul(cx3(i) * cz3(i), nq);
+    pyz += cmul(cy3(i) * cz3(i), nq);
+  }
+  if (model == LBM_COLLIDE_REGULARIZED) {
+    const float keep = 1.0f - omega;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const float qxx = (float)(cx3(i) * cx3(i)) - 1.0f / 3.0f;
+      const float qyy = (float)(cy3(i) * cy3(i)) - 1.0f / 3.0f;
+      const float qzz = (float)(cz3(i) * cz3(i)) - 1.0f / 3.0f;
+      const float q = qxx * pxx + qyy * pyy + qzz * pzz +
+                      2.0f * (cmul(cx3(i) * cy3(i), pxy) + cmul(cx3(i) * cz3(i), pxz) + cmul(cy3(i) * cz3(i), pyz));
+      g[i] = e[i] + keep * (4.5f * w3(i) * q);
+    }
+  } else {
+    const float pp = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz);
+    const float tau_eff = 0.5f * (tau + sqrtf(tau * tau + 18.0f * 1.41421356f * c_smag * c_smag * sqrtf(pp) / rho));
+    const float om = 1.0f / tau_eff;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) g[i] += om * (e[i] - g[i]);
+  }
+  close_moments3(g, drho, jx, jy, jz);
+}
+
 // Port cell (x = 0 inlet, x = nx-1 outlet).  Known sums: G0 over c_x = 0,
 // Gk over the directions arriving from inside (c_x < 0 at the inlet, > 0 at
 // the outlet).  With sum_{c_x=0} w = 2/3 and sum_{c_x<0} w = 1/6:
@@ -196,7 +248,7 @@ __device__ __forceinline__ void opaque(long long& a) { asm volatile("" : "+l"(a)
 // collision, store.  NB0: no neighbour of this cell is solid (no
 // bounce-back selects at all).  IX: element index type -- int when all 19
 // planes have fewer than 2^31 elements (one IMAD per address), else long long.
-template <class T, int PHASE, int MOM, bool NB0, class IX>
+template <class T, int PHASE, int MOM, bool NB0, class IX, bool MODELS>
 __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z, uint32_t nb) {
   IX sy = (IX)v.nxp, sz = (IX)v.ny * (IX)v.nxp;
   IX c = ((IX)z * v.ny + y) * (IX)v.nxp + x;
@@ -219,7 +271,10 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
   }
   if (!NB0 && (x == 0 || x == v.nx - 1)) port3(g, x == 0, v.u_in[(long long)z * v.ny + y], v.rho0);
   float drho, ux, uy, uz;
-  bgk3(g, v.rho0, v.omega, drho, ux, uy, uz);
+  if (MODELS && v.collision != LBM_COLLIDE_BGK)  // the plain build has no branch here
+    collide_other3(g, v.rho0, v.omega, v.tau, v.collision, v.c_smag, drho, ux, uy, uz);
+  else
+    bgk3(g, v.rho0, v.omega, drho, ux, uy, uz);
   // Recompute the store addresses from the cell index instead of keeping the
   // 18 load addresses alive across the collision (halves the registers).
   opaque(c);
@@ -246,7 +301,7 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
 // the previous step (they change only between solves), the populations after.
 // Phase A on a segment whose fluid cells have no solid neighbour (and hence
 // no port cell: outside the row reads as solid) takes the select-free path.
-template <class T, int PHASE, int MOM, class IX>
+template <class T, int PHASE, int MOM, class IX, bool MODELS>
 __device__ __forceinline__ void seg_task3(const View3& v, Seg3 sg, int lane, bool& waited) {
   const int seg = sg.seg & kSegIndexMask;
   const bool open = PHASE == 0 && (sg.seg & kSegOpen);
@@ -287,14 +342,14 @@ __device__ __forceinline__ void seg_task3(const View3& v, Seg3 sg, int lane, boo
   if ((sg.word >> lane) & 1u) return;  // solid, or past the row's end
   const int x = 32 * s + lane;
   if (open)
-    cell_update3<T, PHASE, MOM, true, IX>(v, x, y, z, 0u);
+    cell_update3<T, PHASE, MOM, true, IX, MODELS>(v, x, y, z, 0u);
   else
-    cell_update3<T, PHASE, MOM, false, IX>(v, x, y, z, nb);
+    cell_update3<T, PHASE, MOM, false, IX, MODELS>(v, x, y, z, nb);
 }
 
 // One phase of one time step over the segment list (warps stride over it).
 // Launched as a programmatic dependent of the previous step.
-template <class T, int PHASE, int MOM, class IX>
+template <class T, int PHASE, int MOM, class IX, bool MODELS>
 __global__ void __launch_bounds__(512) k_step3(const View3 v, const Seg3* __restrict__ segs,
                                                const int* __restrict__ n_segs) {
   // the next step may be scheduled now; it touches populations only after
@@ -306,7 +361,7 @@ __global__ void __launch_bounds__(512) k_step3(const View3 v, const Seg3* __rest
   const int stride = gridDim.x * wpb;
   bool waited = false;
   for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < nseg; t += stride)
-    seg_task3<T, PHASE, MOM, IX>(v, segs[t], lane, waited);
+    seg_task3<T, PHASE, MOM, IX, MODELS>(v, segs[t], lane, waited);
   // every thread waits once, so this grid completes only after the previous one
   if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
@@ -567,22 +622,26 @@ __global__ void k_unpack3(const View3 v, uint8_t* __restrict__ cells) {
   cells[i] = (uint8_t)((v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + (x >> 5)] >> (x & 31)) & 1u);
 }
 
-template <class T, class IX>
+// MODELS: the build with the collision models beyond BGK (kept apart so that
+// the BGK build keeps its registers)
+template <class T, class IX, bool MODELS>
 void* step3_kernel(int phase, int moments) {
-  if (phase == 0) return (void*)k_step3<T, 0, 0, IX>;
-  return moments ? (void*)k_step3<T, 1, 1, IX> : (void*)k_step3<T, 1, 0, IX>;
+  if (phase == 0) return (void*)k_step3<T, 0, 0, IX, MODELS>;
+  return moments ? (void*)k_step3<T, 1, 1, IX, MODELS> : (void*)k_step3<T, 1, 0, IX, MODELS>;
 }
 
 template <class T>
-void* step3_kernel(int phase, int moments, bool idx64) {
-  return idx64 ? step3_kernel<T, long long>(phase, moments) : step3_kernel<T, int>(phase, moments);
+void* step3_kernel(int phase, int moments, bool idx64, bool models) {
+  if (models)
+    return idx64 ? step3_kernel<T, long long, true>(phase, moments) : step3_kernel<T, int, true>(phase, moments);
+  return idx64 ? step3_kernel<T, long long, false>(phase, moments) : step3_kernel<T, int, false>(phase, moments);
 }
 
-void* step3_for(int precision, int phase, int moments, bool idx64) {
+void* step3_for(int precision, int phase, int moments, bool idx64, bool models) {
   switch (precision) {
-    case LBM_F32: return step3_kernel<float>(phase, moments, idx64);
-    case LBM_BF16_SHIFTED: return step3_kernel<__nv_bfloat16>(phase, moments, idx64);
-    case LBM_F16_SHIFTED: return step3_kernel<__half>(phase, moments, idx64);
+    case LBM_F32: return step3_kernel<float>(phase, moments, idx64, models);
+    case LBM_BF16_SHIFTED: return step3_kernel<__nv_bfloat16>(phase, moments, idx64, models);
+    case LBM_F16_SHIFTED: return step3_kernel<__half>(phase, moments, idx64, models);
     default: return nullptr;
   }
 }
@@ -609,7 +668,7 @@ cudaError_t launch_build_segments3(const View3& v, int* scratch, Seg3* segs, int
 }
 
 int step3_resident_blocks(int precision, int phase, int moments, int warps_per_block, const View3& v) {
-  void* k = step3_for(precision, phase, moments, needs_idx64(v));
+  void* k = step3_for(precision, phase, moments, needs_idx64(v), v.collision != LBM_COLLIDE_BGK);
   int dev = 0, sms = 0, n = 0;
   if (!k || cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -620,7 +679,7 @@ int step3_resident_blocks(int precision, int phase, int moments, int warps_per_b
 
 cudaError_t launch_step3(int precision, int phase, int moments, const View3& v, const Seg3* segs,
                          const int* n_segs, int blocks, int warps_per_block, cudaStream_t stream) {
-  void* k = step3_for(precision, phase, moments, needs_idx64(v));
+  void* k = step3_for(precision, phase, moments, needs_idx64(v), v.collision != LBM_COLLIDE_BGK);
   if (!k || blocks < 1) return cudaErrorInvalidValue;
   void* args[] = {(void*)&v, (void*)&segs, (void*)&n_segs};
   cudaLaunchAttribute attr[1];

@@ -35,6 +35,9 @@ struct View3 {
   float omega, rho0;
   int idx64;             // step kernels index populations in 64 bits (19 planes reach 2^31
                          // elements, or LBM3D_INDEX64=1 in the environment), else in 32
+  int collision;         // lbm_collision (non-BGK: the models build of the step kernels)
+  float tau;             // relaxation time (the Smagorinsky root needs it)
+  float c_smag;          // Smagorinsky constant
 };
 
 __host__ __device__ inline long long mask3_row(int ny, int ms, int y, int z) {

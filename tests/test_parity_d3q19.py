@@ -38,11 +38,11 @@ def _compare_fields(lat, sv, cells, tol=TOL):
     assert np.abs(drho - ref).max() <= tol * np.abs(ref).max()
 
 
-def _check_solve(cfg_cells, tau, u_max, steps, tol=TOL, precision=L.F32):
+def _check_solve(cfg_cells, tau, u_max, steps, tol=TOL, precision=L.F32, collision=0, c_smag=0.0):
     nz, ny, nx = cfg_cells.shape
-    lat = L.Lattice3(cfg_cells, tau, u_max, precision=precision)
+    lat = L.Lattice3(cfg_cells, tau, u_max, precision=precision, collision=collision, c_smag=c_smag)
     g = lat.solve(steps)
-    sv = o3.Solver3(o3.make_params3(nx, ny, nz, tau, u_max=u_max), cfg_cells)
+    sv = o3.Solver3(o3.make_params3(nx, ny, nz, tau, u_max=u_max, collision=collision, c_smag=c_smag), cfg_cells)
     o = sv.solve(steps)
     _compare_fields(lat, sv, cfg_cells, tol)
     assert abs(g["dp"] - o["dp"]) <= tol * abs(o["dp"])
@@ -57,6 +57,25 @@ def test_tree3d_matches_oracle():
     cfg = I.config_tree3d_small()
     lat, *_ = _check_solve(cfg["cells"], cfg["tau"], cfg["u_max"], 300)
     lat.close()
+
+
+@pytest.mark.parametrize("collision,c_smag", [(L.COLLIDE_REGULARIZED, 0.0), (L.COLLIDE_SMAGORINSKY, 0.1),
+                                              (L.COLLIDE_SMAGORINSKY, 0.3)])
+def test_collision_models_match_oracle(collision, c_smag):
+    cfg = I.config_tree3d_small()
+    lat, *_ = _check_solve(cfg["cells"], cfg["tau"], cfg["u_max"], 300, collision=collision, c_smag=c_smag)
+    lat.close()
+    cells = I.random_blobs3d(45, 12, 11, seed=3, density=0.2)
+    lat, *_ = _check_solve(cells, 0.56, 0.05, 300, collision=collision, c_smag=c_smag)
+    lat.close()
+
+
+def test_collision_model_argument_checks():
+    cells = I.duct3d(16, 6, 5)
+    for kw in (dict(collision=3), dict(collision=L.COLLIDE_SMAGORINSKY, c_smag=-0.1)):
+        with pytest.raises(L.LbmError) as e:
+            L.Lattice3(cells, 0.8, 0.05, **kw)
+        assert e.value.status == 1
 
 
 @pytest.mark.parametrize("nx", [33, 64, 70])  # ragged tail of one cell, whole segments, ragged tail
