@@ -62,9 +62,10 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=200.0, help="served leg: Poisson arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="served leg: arrival window")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--kernel-case", choices=["tree", "large", "tree3d", "duct3d"], default=None,
+    ap.add_argument("--kernel-case", choices=["tree", "large", "batch", "tree3d", "duct3d"], default=None,
                     help="only create one lattice and run two solves of --kernel-steps steps (for ncu "
                          "captures): tree = 2048 x 1024 distributor, large = 8192 x 4096 channel array, "
+                         "batch = the 256 candidate distributors in one batch, "
                          "tree3d = 384 x 192 x 192 D3Q19 distributor, duct3d = 256 x 128 x 128 D3Q19 duct")
     ap.add_argument("--kernel-steps", type=int, default=4)
     ap.add_argument("--kernel-cpt", type=int, default=0,
@@ -90,6 +91,18 @@ def kernel_case(args):
         lat.close()
         print(json.dumps({"kernel_case": args.kernel_case, "precision": args.precision,
                           "fluid_cells": int((cells == 0).sum()), "dp": r["dp"]}))
+        return 0
+    if args.kernel_case == "batch":
+        cands = I.config_candidates(256)
+        b = L.Batch([dict(cells=c["cells"], tau=c["tau"], u_max=c["u_max"]) for c in cands], precision=prec,
+                    residual_every=0)
+        b.solve(args.kernel_steps)
+        r = b.solve(args.kernel_steps)
+        shape = b.step_config()
+        b.close()
+        print(json.dumps({"kernel_case": "batch", "precision": args.precision,
+                          "fluid_cells": sum(int((c["cells"] == 0).sum()) for c in cands), "dp0": r[0]["dp"],
+                          "step_config": list(shape)}))
         return 0
     if args.kernel_case == "tree":
         cfg = I.config_tree_2048()
