@@ -279,6 +279,14 @@ const char* lbm_last_error(void);
  * the call that needed it); after < 0 switches the hook off.  One-shot.   */
 void lbm_debug_fail_alloc(int64_t after);
 
+/* Test hook for the bounded device-side waits (process-wide; on != 0 until
+ * called again with 0): the persistent step kernel's grid barriers then wait
+ * for one arrival more than the grid makes, so every wait gives up after its
+ * poll limit (2^22 acquire loads, a few seconds), the launch ends early and
+ * the solve returns LBM_ERR_TIMEOUT; the handle stays usable (lbm_reset or
+ * lbm_load_state restores a state).  No device fault is involved.         */
+void lbm_debug_barrier_timeout(int32_t on);
+
 /* Number of device kernels this process has launched through the library
  * (graph launches count every kernel node).                             */
 uint64_t lbm_kernel_launches(void);

@@ -49,6 +49,8 @@ uint64_t lbm_kernel_launches(void) { return launches_total(); }
 
 void lbm_debug_fail_alloc(int64_t after) { set_alloc_failure(after); }
 
+void lbm_debug_barrier_timeout(int32_t on) { set_barrier_timeout_test(on); }
+
 double lbm_bytes_per_fluid_update(int32_t precision) {
   return 2.0 * 9.0 * (double)storage_bytes(precision) + 1.0 / 8.0;
 }

@@ -54,6 +54,10 @@ bool autotune_enabled() {
   return on;
 }
 
+static std::atomic<int> g_barrier_timeout{0};
+void set_barrier_timeout_test(int on) { g_barrier_timeout.store(on ? 1 : 0); }
+int barrier_timeout_test() { return g_barrier_timeout.load(); }
+
 // Test hook for the failure paths: the allocation that brings the countdown
 // from 0 to -1 fails as if the device were full.
 static std::atomic<int64_t> g_fail_after{-1};

@@ -123,8 +123,13 @@ struct StepBarrier {
   unsigned count;  // arrivals since the launch began
   unsigned gen;    // unused
   int error;       // set when a wait gave up (the launch then stops early)
-  int pad;
+  int extra;       // arrivals awaited beyond the grid: 0, or 1 under the test hook
+                   // (lbm_debug_barrier_timeout) so that every wait runs out
 };
+// lbm_debug_barrier_timeout: the next persistent launches wait for an arrival
+// that never comes (the bounded-wait failure path, tested without a fault)
+void set_barrier_timeout_test(int on);
+int barrier_timeout_test();
 cudaError_t launch_stream_collide(int precision, int phase, int moments, const LatticeView* views,
                                   const SegRef* segs, const int* n_segs, StepConfig cfg,
                                   cudaStream_t stream);

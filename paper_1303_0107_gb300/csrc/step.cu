@@ -31,6 +31,8 @@
 // wait for it only before touching populations.  Alternatively one
 // cooperative launch runs all steps of a solve with grid barriers between
 // phases (the persistent kernel).
+#include <cstddef>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -668,7 +670,7 @@ __device__ bool grid_barrier(StepBarrier* b, unsigned& target) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    target += gridDim.x;
+    target += gridDim.x + (unsigned)b->extra;
     __threadfence();  // this block's population writes before its arrival
     atomicAdd(&b->count, 1u);
     unsigned spins = 0;
@@ -824,6 +826,9 @@ cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* v
   // a fresh barrier: count 0, no error
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(StepBarrier), stream);
   if (e != cudaSuccess) return e;
+  if (barrier_timeout_test() &&
+      (e = cudaMemsetAsync(reinterpret_cast<char*>(bar) + offsetof(StepBarrier, extra), 1, 1, stream)) != cudaSuccess)
+    return e;
   void* args[] = {(void*)&views, (void*)&segs, (void*)&n_segs, (void*)&n_pairs, (void*)&bar};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;  // all blocks co-resident: the barrier can complete

@@ -173,6 +173,8 @@ def load_library(path=None):
     L.lbm_server_cancel.argtypes = [S, ctypes.c_int64]
     L.lbm_debug_fail_alloc.argtypes = [ctypes.c_int64]
     L.lbm_debug_fail_alloc.restype = None
+    L.lbm_debug_barrier_timeout.argtypes = [ctypes.c_int32]
+    L.lbm_debug_barrier_timeout.restype = None
     L.lbm_server_destroy.argtypes = [S]
     L.lbm_server_destroy.restype = None
     L.lbm_bytes_per_fluid_update.argtypes = [ctypes.c_int32]
@@ -196,6 +198,12 @@ def _check(st, where):
 def debug_fail_alloc(after: int) -> None:
     """Make the device allocation after `after` more successful ones fail (test hook; -1: off)."""
     load_library().lbm_debug_fail_alloc(int(after))
+
+
+def debug_barrier_timeout(on: bool) -> None:
+    """Make the persistent kernel's grid barriers wait for an arrival that never
+    comes, so that their bounded waits give up (test hook)."""
+    load_library().lbm_debug_barrier_timeout(int(bool(on)))
 
 
 def kernel_launches() -> int:

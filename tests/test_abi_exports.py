@@ -59,7 +59,8 @@ def test_host_only_entry_points(built_lib):
     assert L.lbm_server_create(ctypes.byref(odd), None, ctypes.byref(srv)) == 1
     L.lbm_server_destroy(None)
     assert L.lbm_server_cancel(None, 1) == 1
-    L.lbm_debug_fail_alloc(-1)  # host-only switch
+    L.lbm_debug_fail_alloc(-1)  # host-only switches
+    L.lbm_debug_barrier_timeout(0)
     from paper_1303_0107_gb300 import lib3d
     L3 = lib3d._lib()
     h3 = ctypes.c_void_p()

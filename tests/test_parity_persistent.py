@@ -145,3 +145,28 @@ def test_set_step_config_errors():
             h.set_step_config(wpb, persistent=pers, cells_per_thread=cpt, stages=stg)
         assert e.value.status == 1
     h.close()
+
+
+def test_barrier_wait_gives_up_and_the_handle_stays_usable():
+    """The bounded-wait failure path without a device fault: under the test
+    hook every grid barrier waits for one arrival too many, gives up after its
+    poll limit, the launch ends early and the solve reports LBM_ERR_TIMEOUT;
+    afterwards the context and the handle work as before."""
+    import time
+    cfg = I.config_t_junction()
+    ref = _handle(dict(cells=cfg["cells"], tau=cfg["tau"], u_max=cfg["u_max"]), L.F32, True)
+    r_ref = ref.solve(200)
+    ref.close()
+    h = _handle(dict(cells=cfg["cells"], tau=cfg["tau"], u_max=cfg["u_max"]), L.F32, True)
+    L.lib.debug_barrier_timeout(True)
+    try:
+        t0 = time.perf_counter()
+        with pytest.raises(L.LbmError) as e:
+            h.solve(200)
+        assert e.value.status == 6  # LBM_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 60
+    finally:
+        L.lib.debug_barrier_timeout(False)
+    h.reset()
+    assert h.solve(200)["dp"] == r_ref["dp"]
+    h.close()
