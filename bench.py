@@ -615,10 +615,16 @@ def run_reference(args, world, rank):
     value = total_updates / total_s / 1e9
     sample = (f"{cfg['name']}: {args.steps} samples of ~{args.cpu_seconds / max(1, args.steps):.1f} s "
               f"of FP64 time steps from rest (exchange and reductions excluded)")
+    fluid = int((cfg["cells"] == 0).sum())
+    S, iters = args.lattice_steps, args.iters
+    # the GPU arm's config (the same workload); the oracle times a bounded sample of it
+    config = {"workload": cfg["name"] + f"_{args.precision}_{iters + 1}x{S}", "nx": cfg["nx"], "ny": cfg["ny"],
+              "fluid_cells": fluid, "n_swap": max(1, fluid // 500), "solves_per_step": iters + 1,
+              "time_steps_per_solve": S, "parallelism": "replicas x1 (rank 0 only)"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": cfg["name"], "nx": cfg["nx"], "ny": cfg["ny"]},
+            "data": "synthetic", "config": config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
