@@ -14,7 +14,7 @@ COLLIDE_BGK, COLLIDE_REGULARIZED, COLLIDE_SMAGORINSKY = 0, 1, 2
 class Params3(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("periodic", ctypes.c_int32), ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
-                ("u_max", ctypes.c_double), ("collision", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("u_max", ctypes.c_double), ("collision", ctypes.c_int32), ("mirror", ctypes.c_int32),
                 ("c_smag", ctypes.c_double)]
 
 
@@ -56,9 +56,10 @@ def _p(a, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
-def make_params3(nx, ny, nz, tau, rho0=1.0, u_max=0.0, periodic=0, collision=COLLIDE_BGK, c_smag=0.0):
+def make_params3(nx, ny, nz, tau, rho0=1.0, u_max=0.0, periodic=0, collision=COLLIDE_BGK, c_smag=0.0,
+                 mirror=False):
     return Params3(int(nx), int(ny), int(nz), int(periodic), float(tau), float(rho0), float(u_max), int(collision),
-                   0, float(c_smag))
+                   int(bool(mirror)), float(c_smag))
 
 
 def collide3(p, f):

@@ -466,3 +466,36 @@ def test_smagorinsky_damps_a_shear_wave_more_as_c_grows_and_c0_is_bgk():
     assert np.array_equal(f_bgk, f_c0)
     amps = [run(o3.COLLIDE_SMAGORINSKY, c)[1] for c in (0.1, 0.2, 0.5, 1.0)]
     assert a_bgk > amps[0] > amps[1] > amps[2] > amps[3] > 0
+
+
+def _half_and_whole():
+    """A half domain against a plane below its row 0 (the upper half of the
+    small 3D tree) and the whole symmetric domain it stands for."""
+    from paper_1303_0107_gb300 import inputs as I
+    cfg = I.config_tree3d_small()
+    half = np.ascontiguousarray(cfg["cells"][:, 17:, :])
+    whole = np.ascontiguousarray(np.concatenate([half[:, ::-1, :], half], axis=1))
+    return cfg, half, whole
+
+
+def test_mirror_half_domain_equals_upper_half_of_whole_domain():
+    """Sec. 3.3 computes half of a symmetric domain: with the plane below row
+    0, the half must follow the upper half of the whole domain (fields, the
+    inlet profile, dp; u_y odd across the plane), up to rounding order."""
+    cfg, half, whole = _half_and_whole()
+    nz, nyh, nx = half.shape
+    ph = o3.make_params3(nx, nyh, nz, cfg["tau"], u_max=cfg["u_max"], mirror=True)
+    pw = o3.make_params3(nx, 2 * nyh, nz, cfg["tau"], u_max=cfg["u_max"])
+    assert o3.check_geometry3(ph, half) == 0 and o3.check_geometry3(pw, whole) == 0
+    assert o3.check_geometry3(o3.make_params3(nx, nyh, nz, cfg["tau"]), half) != 0  # row 0 fluid needs the plane
+    sh, sw = o3.Solver3(ph, half), o3.Solver3(pw, whole)
+    assert np.array_equal(sh.u_in, sw.u_in[:, nyh:])
+    oh, ow = sh.solve(300), sw.solve(300)
+    up = slice(nyh, 2 * nyh)
+    scale = np.abs(sw.ux).max()
+    for a, b in ((sh.ux, sw.ux[:, up]), (sh.uy, sw.uy[:, up]), (sh.uz, sw.uz[:, up]), (sh.rho, sw.rho[:, up])):
+        assert np.abs(a - b).max() <= 1e-12 * max(scale, 1.0)
+    assert np.abs(sw.uy[:, :nyh][:, ::-1] + sw.uy[:, up]).max() <= 1e-12 * scale  # odd across the plane
+    assert oh["dp"] == pytest.approx(ow["dp"], rel=1e-12)
+    assert oh["m_in"] == pytest.approx(ow["m_in"] / 2, rel=1e-12)
+    assert abs(sum(oh["m_out"]) - sum(ow["m_out"]) / 2) <= 1e-12 * abs(sum(ow["m_out"]))
