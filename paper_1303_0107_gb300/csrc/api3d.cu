@@ -18,7 +18,8 @@ struct lbm3d_handle_s {
   bool own_stream = false;
   View3 v{};
   size_t elem = 4;        // bytes per stored population
-  int total_words = 0;    // interior-row words = work-list capacity
+  int total_words = 0;    // words of the work-list's rows = its capacity
+  int oc_words = 0;       // words of the movable rows (y, z in [1, n-2]): the exchange's word space
   long long ncells = 0;
   std::vector<void*> allocs;
   Seg3* segs = nullptr;
@@ -105,7 +106,8 @@ lbm_status check_params3(const lbm3d_params& p) {
       p.collision != LBM_COLLIDE_SMAGORINSKY)
     return fail(LBM_ERR_ARG, "unknown collision model");
   if (!(p.c_smag >= 0.0) || !std::isfinite(p.c_smag)) return fail(LBM_ERR_ARG, "c_smag must be >= 0");
-  if (p.reserved[0] || p.reserved[1]) return fail(LBM_ERR_ARG, "reserved fields must be 0");
+  if (p.mirror != 0 && p.mirror != 1) return fail(LBM_ERR_ARG, "mirror must be 0 or 1");
+  if (p.reserved) return fail(LBM_ERR_ARG, "reserved fields must be 0");
   return LBM_OK;
 }
 
@@ -114,11 +116,12 @@ lbm_status geometry3(const lbm3d_params& p, const uint8_t* solid, Geometry3& g) 
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y) {
-      const bool frame = y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
+      const bool frame = (y == 0 && !p.mirror) || y == ny - 1 || z == 0 || z == nz - 1;
       for (int x = 0; x < nx; ++x) {
         const uint8_t s = solid[cell(p, x, y, z)];
         if (s > 1) return fail(LBM_ERR_GEOMETRY, "cell types must be 0 or 1");
-        if (frame && !s) return fail(LBM_ERR_GEOMETRY, "the faces y = 0, ny-1, z = 0, nz-1 must be solid");
+        if (frame && !s)
+          return fail(LBM_ERR_GEOMETRY, "the faces y = 0 (unless mirror), ny-1, z = 0, nz-1 must be solid");
         g.fluid += !s;
       }
     }
@@ -132,6 +135,7 @@ lbm_status geometry3(const lbm3d_params& p, const uint8_t* solid, Geometry3& g) 
         int lo = y, hi = y;
         while (lo > 0 && !solid[cell(p, 0, lo - 1, z)]) --lo;
         while (hi < ny && !solid[cell(p, 0, hi, z)]) ++hi;
+        if (p.mirror && lo == 0) lo = -hi;  // half of a run twice as wide, centred on the plane
         const double sy = ((double)(y - lo) + 0.5) / (double)(hi - lo);
         lo = z;
         hi = z;
@@ -303,6 +307,7 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   v.plane = (long long)p.nz * p.ny * v.nxp;
   const char* force64 = std::getenv("LBM3D_INDEX64");
   v.idx64 = ((long long)kQ3 * v.plane >= (1ll << 31) || (force64 && std::strcmp(force64, "1") == 0)) ? 1 : 0;
+  v.mirror = p.mirror;
   v.omega = (float)(1.0 / p.tau);
   v.tau = (float)p.tau;
   v.collision = p.collision;
@@ -311,7 +316,8 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   h->elem = storage_bytes3(p.precision);
   h->ncells = (long long)p.nx * p.ny * p.nz;
   h->fluid = g.fluid;
-  h->total_words = (p.ny - 2) * (p.nz - 2) * v.nsx;
+  h->total_words = seg3_words(v);
+  h->oc_words = (p.ny - 2) * (p.nz - 2) * v.nsx;
   h->n_in = (int)g.in_rows.size();
   h->n_regions = (int)g.out_off.size() - 1;
   // mask: all padding set, fluid cells cleared
@@ -324,6 +330,10 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
       for (int x = 0; x < p.nx; ++x)
         if (!cells[cell(p, x, y, z)]) row[x >> 5] &= ~(1u << (x & 31));
     }
+  if (p.mirror)  // the padding row below row 0 is its mirror image
+    for (int z = 0; z < p.nz; ++z)
+      std::copy(mask.begin() + mask3_row(p.ny, v.ms, 0, z), mask.begin() + mask3_row(p.ny, v.ms, 0, z) + v.ms,
+                mask.begin() + mask3_row(p.ny, v.ms, -1, z));
   void* f = nullptr;
   CU3(h->alloc(&f, (size_t)kQ3 * v.plane * h->elem));
   v.f = f;
@@ -345,7 +355,7 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   CU3(h->alloc(&h->out_rows, sizeof(int) * g.out_rows.size()));
   CU3(h->alloc(&h->out_off, sizeof(int) * g.out_off.size()));
   CU3(h->alloc(&h->d_result, sizeof(double) * (2 + LBM_MAX_OUTLETS)));
-  const size_t tw = (size_t)h->total_words;
+  const size_t tw = (size_t)h->oc_words;
   const size_t cap = (size_t)sel_capacity((int)h->ncells, 1);
   OcScratch& s = h->oc;
   CU3(h->alloc(&s.cnt_f, sizeof(int) * tw));
@@ -359,7 +369,7 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   CU3(h->alloc(&s.sel_f, sizeof(int) * cap));
   CU3(h->alloc(&s.sel_s, sizeof(int) * cap));
   CU3(h->alloc(&s.info, sizeof(int) * 8));
-  CU3(h->alloc(&s.scan_tmp, sizeof(int) * scan_tmp_ints(h->total_words)));
+  CU3(h->alloc(&s.scan_tmp, sizeof(int) * scan_tmp_ints(h->oc_words)));
   CU3(h->alloc(&h->d_one, sizeof(LatticeView)));
   CU3(h->alloc(&h->d_word_off, sizeof(int) * 2));
   CU3(h->alloc(&h->d_nswap, sizeof(int)));
@@ -370,7 +380,7 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   one.nx = (int)h->ncells;
   one.ny = 1;
   one.sel_off = 0;
-  const int word_off[2] = {0, h->total_words};
+  const int word_off[2] = {0, h->oc_words};
   CU3(cudaMemcpyAsync(v.mask, mask.data(), sizeof(uint32_t) * mw, cudaMemcpyHostToDevice, h->stream));
   CU3(cudaMemcpyAsync(u_in, g.u_in.data(), sizeof(float) * g.u_in.size(), cudaMemcpyHostToDevice, h->stream));
   CU3(cudaMemcpyAsync(h->in_rows, g.in_rows.data(), sizeof(int) * g.in_rows.size(), cudaMemcpyHostToDevice,

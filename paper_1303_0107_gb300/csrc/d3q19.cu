@@ -48,6 +48,11 @@ __host__ __device__ constexpr int cz3(int i) {
          : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
 }
 __host__ __device__ constexpr int opp3(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// the direction with c_y negated (reflection in a plane normal to y)
+__host__ __device__ constexpr int mir3(int i) {
+  return (i == 3 || i == 4) ? 7 - i : (i == 7) ? 9 : (i == 9) ? 7 : (i == 8) ? 10 : (i == 10) ? 8
+         : (i == 15) ? 18 : (i == 18) ? 15 : (i == 16) ? 17 : (i == 17) ? 16 : i;
+}
 __host__ __device__ constexpr float w3(int i) { return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f); }
 // c * v for c in {-1, 0, 1} without a multiply (0 * v is not 0 for v = inf/NaN)
 __device__ __forceinline__ float cmul(int c, float v) { return c == 0 ? 0.0f : (c > 0 ? v : -v); }
@@ -248,7 +253,11 @@ __device__ __forceinline__ void opaque(long long& a) { asm volatile("" : "+l"(a)
 // collision, store.  NB0: no neighbour of this cell is solid (no
 // bounce-back selects at all).  IX: element index type -- int when all 19
 // planes have fewer than 2^31 elements (one IMAD per address), else long long.
-template <class T, int PHASE, int MOM, bool NB0, class IX, bool MODELS>
+// FEAT: kernel build, bit kFeat3Models (collision models beyond BGK), bit
+// kFeat3Mirror (symmetry plane below row 0)
+constexpr int kFeat3Models = 1, kFeat3Mirror = 2;
+
+template <class T, int PHASE, int MOM, bool NB0, class IX, int FEAT>
 __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z, uint32_t nb) {
   IX sy = (IX)v.nxp, sz = (IX)v.ny * (IX)v.nxp;
   IX c = ((IX)z * v.ny + y) * (IX)v.nxp + x;
@@ -259,6 +268,13 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
   opaque(sy);
   opaque(sz);
   T* F = static_cast<T*>(v.f);
+  // Symmetry plane below row 0: the ghost row y = -1 is the image of row 0
+  // (its mask row is a copy of row 0, so nb tells whether an image cell is
+  // solid).  A population arriving from a fluid image cell is the one its
+  // original cell sent with c_y negated; one sent towards a fluid image cell
+  // comes back into row 0 with c_y negated, into the slot the local phase
+  // reads for it.  Solid images reflect as walls (the nb path).
+  const bool plane = (FEAT & kFeat3Mirror) && PHASE == 0 && !NB0 && y == 0;
   float g[kQ];
   g[0] = P3<T>::ld(F + c);
 #pragma unroll
@@ -266,12 +282,14 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
     const IX off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
     if (PHASE == 1 || (!NB0 && ((nb >> opp3(i)) & 1u)))
       g[i] = P3<T>::ld(F + (opp3(i) * pl + c));
+    else if (cy3(i) > 0 && plane)
+      g[i] = P3<T>::ld(F + (mir3(i) * pl + c - (cx3(i) + cz3(i) * sz)));
     else
       g[i] = P3<T>::ld(F + (i * pl + c - off));
   }
   if (!NB0 && (x == 0 || x == v.nx - 1)) port3(g, x == 0, v.u_in[(long long)z * v.ny + y], v.rho0);
   float drho, ux, uy, uz;
-  if (MODELS && v.collision != LBM_COLLIDE_BGK)  // the plain build has no branch here
+  if ((FEAT & kFeat3Models) && v.collision != LBM_COLLIDE_BGK)  // the plain build has no branch here
     collide_other3(g, v.rho0, v.omega, v.tau, v.collision, v.c_smag, drho, ux, uy, uz);
   else
     bgk3(g, v.rho0, v.omega, drho, ux, uy, uz);
@@ -285,6 +303,8 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
     const IX off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
     if (PHASE == 1 || (!NB0 && ((nb >> i) & 1u)))
       P3<T>::st(F + (i * pl + c), g[i]);
+    else if (cy3(i) < 0 && plane)
+      P3<T>::st(F + (opp3(mir3(i)) * pl + c + (cx3(i) + cz3(i) * sz)), g[i]);
     else
       P3<T>::st(F + (opp3(i) * pl + c + off), g[i]);
   }
@@ -301,7 +321,7 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
 // the previous step (they change only between solves), the populations after.
 // Phase A on a segment whose fluid cells have no solid neighbour (and hence
 // no port cell: outside the row reads as solid) takes the select-free path.
-template <class T, int PHASE, int MOM, class IX, bool MODELS>
+template <class T, int PHASE, int MOM, class IX, int FEAT>
 __device__ __forceinline__ void seg_task3(const View3& v, Seg3 sg, int lane, bool& waited) {
   const int seg = sg.seg & kSegIndexMask;
   const bool open = PHASE == 0 && (sg.seg & kSegOpen);
@@ -342,14 +362,14 @@ __device__ __forceinline__ void seg_task3(const View3& v, Seg3 sg, int lane, boo
   if ((sg.word >> lane) & 1u) return;  // solid, or past the row's end
   const int x = 32 * s + lane;
   if (open)
-    cell_update3<T, PHASE, MOM, true, IX, MODELS>(v, x, y, z, 0u);
+    cell_update3<T, PHASE, MOM, true, IX, FEAT>(v, x, y, z, 0u);
   else
-    cell_update3<T, PHASE, MOM, false, IX, MODELS>(v, x, y, z, nb);
+    cell_update3<T, PHASE, MOM, false, IX, FEAT>(v, x, y, z, nb);
 }
 
 // One phase of one time step over the segment list (warps stride over it).
 // Launched as a programmatic dependent of the previous step.
-template <class T, int PHASE, int MOM, class IX, bool MODELS>
+template <class T, int PHASE, int MOM, class IX, int FEAT>
 __global__ void __launch_bounds__(512) k_step3(const View3 v, const Seg3* __restrict__ segs,
                                                const int* __restrict__ n_segs) {
   // the next step may be scheduled now; it touches populations only after
@@ -361,7 +381,7 @@ __global__ void __launch_bounds__(512) k_step3(const View3 v, const Seg3* __rest
   const int stride = gridDim.x * wpb;
   bool waited = false;
   for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < nseg; t += stride)
-    seg_task3<T, PHASE, MOM, IX, MODELS>(v, segs[t], lane, waited);
+    seg_task3<T, PHASE, MOM, IX, FEAT>(v, segs[t], lane, waited);
   // every thread waits once, so this grid completes only after the previous one
   if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
@@ -372,13 +392,15 @@ inline int blocks_for(long long n, int threads) {
 }
 
 // ---- work-list ---------------------------------------------------------------
-__device__ __forceinline__ void word3_of(const View3& v, int i, int& y, int& z, int& s) {
-  const int per_z = (v.ny - 2) * v.nsx;
+// word i of the rows y in [y0, ny-2], z in [1, nz-2] (y0 = 1, or 0 next to a
+// symmetry plane for the step work-list)
+__device__ __forceinline__ void word3_of(const View3& v, int y0, int i, int& y, int& z, int& s) {
+  const int per_z = (v.ny - 1 - y0) * v.nsx;
   const int zi = i / per_z;
   const int rest = i - zi * per_z;
   const int yi = rest / v.nsx;
   s = rest - yi * v.nsx;
-  y = 1 + yi;
+  y = y0 + yi;
   z = 1 + zi;
 }
 
@@ -386,7 +408,7 @@ __global__ void k_seg3_flags(const View3 v, int total, int* __restrict__ flags) 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   int y, z, s;
-  word3_of(v, i, y, z, s);
+  word3_of(v, first_row3(v), i, y, z, s);
   flags[i] = ~v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + s] != 0u;
 }
 
@@ -398,7 +420,7 @@ __global__ void k_seg3_scatter(const View3 v, int total, const int* __restrict__
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total || !flags[i]) return;
   int y, z, s;
-  word3_of(v, i, y, z, s);
+  word3_of(v, first_row3(v), i, y, z, s);
   const uint32_t own = v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + s];
   uint32_t solid_nb = 0;  // bit l: some neighbour of cell 32 s + l is solid
   for (int dz = -1; dz <= 1; ++dz)
@@ -410,7 +432,8 @@ __global__ void k_seg3_scatter(const View3 v, int total, const int* __restrict__
       solid_nb |= __funnelshift_r(m, row[s + 1], 1);    // c_x = +1
       solid_nb |= __funnelshift_l(row[s - 1], m, 1);    // c_x = -1
     }
-  const bool open = (solid_nb & ~own) == 0u;
+  // row 0 next to a symmetry plane pulls across it: never the open path
+  const bool open = (solid_nb & ~own) == 0u && y > 0;
   const int seg = (z * v.ny + y) * v.nsx + s;
   segs[offs[i]] = Seg3{seg | (open ? kSegOpen : 0), own};
 }
@@ -507,7 +530,7 @@ __global__ void k_oc3_count(const View3 v, int total, int* __restrict__ cnt_f, i
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   int y, z, s;
-  word3_of(v, i, y, z, s);
+  word3_of(v, 1, i, y, z, s);
   const Words3 m = words3(v, y, z, s);
   cnt_f[i] = __popc(m.fluid_cand);
   cnt_s[i] = __popc(m.solid_cand);
@@ -535,7 +558,7 @@ __global__ void k_oc3_emit(const View3 v, const float* __restrict__ drho, const 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   int y, z, s;
-  word3_of(v, i, y, z, s);
+  word3_of(v, 1, i, y, z, s);
   const Words3 m = words3(v, y, z, s);
   const double rho0 = (double)v.rho0;
   const long long sy = v.nxp, sz = (long long)v.ny * v.nxp;
@@ -622,38 +645,50 @@ __global__ void k_unpack3(const View3 v, uint8_t* __restrict__ cells) {
   cells[i] = (uint8_t)((v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + (x >> 5)] >> (x & 31)) & 1u);
 }
 
-// MODELS: the build with the collision models beyond BGK (kept apart so that
-// the BGK build keeps its registers)
-template <class T, class IX, bool MODELS>
+// FEAT: the build with the collision models beyond BGK and/or the symmetry
+// plane (kept apart so that the plain build keeps its registers)
+template <class T, class IX, int FEAT>
 void* step3_kernel(int phase, int moments) {
-  if (phase == 0) return (void*)k_step3<T, 0, 0, IX, MODELS>;
-  return moments ? (void*)k_step3<T, 1, 1, IX, MODELS> : (void*)k_step3<T, 1, 0, IX, MODELS>;
+  if (phase == 0) return (void*)k_step3<T, 0, 0, IX, FEAT>;
+  return moments ? (void*)k_step3<T, 1, 1, IX, FEAT> : (void*)k_step3<T, 1, 0, IX, FEAT>;
+}
+
+template <class T, class IX>
+void* step3_kernel(int phase, int moments, int feat) {
+  switch (feat) {
+    case 0: return step3_kernel<T, IX, 0>(phase, moments);
+    case kFeat3Models: return step3_kernel<T, IX, kFeat3Models>(phase, moments);
+    case kFeat3Mirror: return step3_kernel<T, IX, kFeat3Mirror>(phase, moments);
+    default: return step3_kernel<T, IX, kFeat3Models | kFeat3Mirror>(phase, moments);
+  }
 }
 
 template <class T>
-void* step3_kernel(int phase, int moments, bool idx64, bool models) {
-  if (models)
-    return idx64 ? step3_kernel<T, long long, true>(phase, moments) : step3_kernel<T, int, true>(phase, moments);
-  return idx64 ? step3_kernel<T, long long, false>(phase, moments) : step3_kernel<T, int, false>(phase, moments);
+void* step3_kernel(int phase, int moments, bool idx64, int feat) {
+  return idx64 ? step3_kernel<T, long long>(phase, moments, feat) : step3_kernel<T, int>(phase, moments, feat);
 }
 
-void* step3_for(int precision, int phase, int moments, bool idx64, bool models) {
+void* step3_for(int precision, int phase, int moments, bool idx64, int feat) {
   switch (precision) {
-    case LBM_F32: return step3_kernel<float>(phase, moments, idx64, models);
-    case LBM_BF16_SHIFTED: return step3_kernel<__nv_bfloat16>(phase, moments, idx64, models);
-    case LBM_F16_SHIFTED: return step3_kernel<__half>(phase, moments, idx64, models);
+    case LBM_F32: return step3_kernel<float>(phase, moments, idx64, feat);
+    case LBM_BF16_SHIFTED: return step3_kernel<__nv_bfloat16>(phase, moments, idx64, feat);
+    case LBM_F16_SHIFTED: return step3_kernel<__half>(phase, moments, idx64, feat);
     default: return nullptr;
   }
 }
 
 inline bool needs_idx64(const View3& v) { return v.idx64 != 0; }
 
+inline int feat3(const View3& v) {
+  return (v.collision != LBM_COLLIDE_BGK ? kFeat3Models : 0) | (v.mirror ? kFeat3Mirror : 0);
+}
+
 }  // namespace
 
 size_t seg3_scratch_ints(long long total) { return 2 * (size_t)total + 1 + scan_tmp_ints(total); }
 
 cudaError_t launch_build_segments3(const View3& v, int* scratch, Seg3* segs, int* n_segs, cudaStream_t stream) {
-  const int total = (v.ny - 2) * (v.nz - 2) * v.nsx;
+  const int total = seg3_words(v);
   int* flags = scratch;
   int* offs = scratch + total;  // total + 1
   int* tmp = scratch + 2 * total + 1;
@@ -668,7 +703,7 @@ cudaError_t launch_build_segments3(const View3& v, int* scratch, Seg3* segs, int
 }
 
 int step3_resident_blocks(int precision, int phase, int moments, int warps_per_block, const View3& v) {
-  void* k = step3_for(precision, phase, moments, needs_idx64(v), v.collision != LBM_COLLIDE_BGK);
+  void* k = step3_for(precision, phase, moments, needs_idx64(v), feat3(v));
   int dev = 0, sms = 0, n = 0;
   if (!k || cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -679,7 +714,7 @@ int step3_resident_blocks(int precision, int phase, int moments, int warps_per_b
 
 cudaError_t launch_step3(int precision, int phase, int moments, const View3& v, const Seg3* segs,
                          const int* n_segs, int blocks, int warps_per_block, cudaStream_t stream) {
-  void* k = step3_for(precision, phase, moments, needs_idx64(v), v.collision != LBM_COLLIDE_BGK);
+  void* k = step3_for(precision, phase, moments, needs_idx64(v), feat3(v));
   if (!k || blocks < 1) return cudaErrorInvalidValue;
   void* args[] = {(void*)&v, (void*)&segs, (void*)&n_segs};
   cudaLaunchAttribute attr[1];

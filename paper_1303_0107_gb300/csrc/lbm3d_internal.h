@@ -36,6 +36,7 @@ struct View3 {
   int idx64;             // step kernels index populations in 64 bits (19 planes reach 2^31
                          // elements, or LBM3D_INDEX64=1 in the environment), else in 32
   int collision;         // lbm_collision (non-BGK: the models build of the step kernels)
+  int mirror;            // symmetry plane below row 0 (the mirror build; row 0 may be fluid)
   float tau;             // relaxation time (the Smagorinsky root needs it)
   float c_smag;          // Smagorinsky constant
 };
@@ -46,6 +47,10 @@ __host__ __device__ inline long long mask3_row(int ny, int ms, int y, int z) {
 __host__ __device__ inline long long mask3_words(int ny, int nz, int ms) {
   return (long long)(ny + 2) * (nz + 2) * ms;
 }
+// first row of the step work-list: row 0 holds fluid only next to a symmetry plane
+__host__ __device__ inline int first_row3(const View3& v) { return v.mirror ? 0 : 1; }
+// words of the step work-list's rows: y in [first_row3, ny-2], z in [1, nz-2]
+__host__ __device__ inline int seg3_words(const View3& v) { return (v.ny - 1 - first_row3(v)) * (v.nz - 2) * v.nsx; }
 
 // Step work-list entry: segment (z * ny + y) * nsx + s (bits 0..29) with
 // kSegOpen set when no fluid cell of it has a solid neighbour, and its own
@@ -58,9 +63,9 @@ constexpr int kSegIndexMask = (1 << 30) - 1;
 constexpr int kSegOpen = 1 << 30;
 static_assert(sizeof(Seg3) == 8, "Seg3 layout");
 
-// Step work-list: the segments (z, y, s) of rows y in [1, ny-2], z in
-// [1, nz-2] holding a fluid cell, in ascending order; *n_segs their count.
-// scratch holds seg3_scratch_ints(total) ints, total = (ny-2)(nz-2) nsx.
+// Step work-list: the segments (z, y, s) of rows y in [first_row3, ny-2], z
+// in [1, nz-2] holding a fluid cell, in ascending order; *n_segs their count.
+// scratch holds seg3_scratch_ints(total) ints, total = seg3_words(v).
 size_t seg3_scratch_ints(long long total);
 cudaError_t launch_build_segments3(const View3& v, int* scratch, Seg3* segs, int* n_segs, cudaStream_t stream);
 

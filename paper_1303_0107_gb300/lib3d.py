@@ -15,7 +15,7 @@ class Params3(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("u_max", ctypes.c_double), ("reinit", ctypes.c_int32), ("collision", ctypes.c_int32),
-                ("c_smag", ctypes.c_double), ("reserved", ctypes.c_int32 * 2)]
+                ("c_smag", ctypes.c_double), ("mirror", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class SolveResult3(ctypes.Structure):
@@ -62,22 +62,24 @@ def _lib():
     return L
 
 
-def make_params3(nx, ny, nz, tau, u_max, rho0=1.0, precision=F32, reinit=REINIT_WARM, collision=0, c_smag=0.0):
+def make_params3(nx, ny, nz, tau, u_max, rho0=1.0, precision=F32, reinit=REINIT_WARM, collision=0, c_smag=0.0,
+                 mirror=False):
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     return Params3(int(nx), int(ny), int(nz), int(precision), float(tau), float(rho0), float(u_max), int(reinit),
-                   int(collision), float(c_smag), (ctypes.c_int32 * 2)(0, 0))
+                   int(collision), float(c_smag), int(bool(mirror)), 0)
 
 
 class Lattice3:
     """One D3Q19 lattice (cell map [nz][ny][nx] + populations) resident on the GPU."""
 
     def __init__(self, cells, tau, u_max, rho0=1.0, precision=F32, reinit=REINIT_WARM, collision=0, c_smag=0.0,
-                 stream=None):
+                 mirror=False, stream=None):
         L = _lib()
         cells = np.ascontiguousarray(cells, dtype=np.uint8)
         self.nz, self.ny, self.nx = cells.shape
-        self.params = make_params3(self.nx, self.ny, self.nz, tau, u_max, rho0, precision, reinit, collision, c_smag)
+        self.params = make_params3(self.nx, self.ny, self.nz, tau, u_max, rho0, precision, reinit, collision, c_smag,
+                                   mirror)
         self.precision = int(self.params.precision)
         self._h = _VP()
         _check(L.lbm3d_create(ctypes.byref(self.params), cells.ctypes.data, _stream_ptr(stream),

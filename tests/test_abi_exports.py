@@ -99,7 +99,7 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
               ("lbm_opt_plan", lib.OptPlan, ["tol", "patience", "reserved"]),
               ("lbm_opt_summary", lib.OptSummary, ["swapped", "dp_last"]),
               ("lbm3d_params", lib3d.Params3, ["precision", "tau", "u_max", "reinit", "collision", "c_smag",
-                                               "reserved"]),
+                                               "mirror", "reserved"]),
               ("lbm3d_solve_result", lib3d.SolveResult3, ["n_outlets", "m_out", "fluid_cells"]),
               ("lbm3d_opt_result", lib3d.OptResult3, ["fluid_count", "solve"])]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', '#include "lbm3d.h"',

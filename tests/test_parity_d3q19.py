@@ -334,3 +334,73 @@ def test_argument_and_geometry_checks():
     with pytest.raises(L.LbmError):
         lat.set_block(5)
     lat.close()
+
+
+def _half_and_whole():
+    """Half of a symmetric 3D tree against a plane below its row 0, and the whole."""
+    cfg = I.config_tree3d_small()
+    half = np.ascontiguousarray(cfg["cells"][:, 17:, :])
+    whole = np.ascontiguousarray(np.concatenate([half[:, ::-1, :], half], axis=1))
+    return cfg, half, whole
+
+
+@pytest.mark.parametrize("collision,c_smag", [(0, 0.0), (L.COLLIDE_SMAGORINSKY, 0.2)])
+def test_mirror_half_matches_oracle(collision, c_smag):
+    cfg, half, _ = _half_and_whole()
+    nz, ny, nx = half.shape
+    lat = L.Lattice3(half, cfg["tau"], cfg["u_max"], collision=collision, c_smag=c_smag, mirror=True)
+    g = lat.solve(300)
+    sv = o3.Solver3(o3.make_params3(nx, ny, nz, cfg["tau"], u_max=cfg["u_max"], collision=collision,
+                                    c_smag=c_smag, mirror=True), half)
+    o = sv.solve(300)
+    _compare_fields(lat, sv, half)
+    assert abs(g["dp"] - o["dp"]) <= TOL * abs(o["dp"])
+    assert np.abs(g["m_out"] - o["m_out"]).max() <= TOL * np.abs(o["m_out"]).max()
+    lat.close()
+
+
+def test_mirror_half_equals_upper_half_of_the_whole_on_the_gpu():
+    cfg, half, whole = _half_and_whole()
+    ny = half.shape[1]
+    a = L.Lattice3(half, cfg["tau"], cfg["u_max"], mirror=True)
+    b = L.Lattice3(whole, cfg["tau"], cfg["u_max"])
+    ra, rb = a.solve(300), b.solve(300)
+    for f in (L.FIELD3_UX, L.FIELD3_UY, L.FIELD3_UZ, L.FIELD3_DRHO):
+        ua, ub = a.read(f), b.read(f)[:, ny:]
+        assert np.abs(ua - ub).max() <= TOL * max(np.abs(ub).max(), 1e-30)
+    assert abs(ra["dp"] - rb["dp"]) <= TOL * abs(rb["dp"])
+    a.close()
+    b.close()
+
+
+def test_mirror_exchange_and_launch_shapes(monkeypatch):
+    """The exchange next to the plane (row 0 never moves) equals the oracle's
+    on the GPU's field; block shapes and 64-bit indexing give the same bits."""
+    cfg, half, _ = _half_and_whole()
+    nz, ny, nx = half.shape
+    lat = L.Lattice3(half, cfg["tau"], cfg["u_max"], mirror=True)
+    lat.solve(200)
+    fields = [lat.read(f) for f in (L.FIELD3_DRHO, L.FIELD3_UX, L.FIELD3_UY, L.FIELD3_UZ)]
+    p = o3.make_params3(nx, ny, nz, cfg["tau"], u_max=cfg["u_max"], mirror=True)
+    cand, score = o3.scores3(p, half, 1.0 + fields[0].astype(np.float64), *[f.astype(np.float64) for f in fields[1:]])
+    fi, si = o3.select3(p, cand, score, 25)
+    before = lat.read(L.FIELD3_MASK)
+    out = lat.optimize_step(25, 200)
+    after = lat.read(L.FIELD3_MASK)
+    assert np.array_equal(np.sort(np.concatenate([fi, si])), np.flatnonzero((before != after).reshape(-1)))
+    assert np.array_equal(after[:, 0, :], half[:, 0, :])
+    sv = o3.Solver3(p, half)
+    sv.solve(200)
+    o3.apply3(p, sv.solid, sv.f, fi, si)
+    o = sv.solve(200)
+    assert abs(out["dp"] - o["dp"]) <= TOL * abs(o["dp"])
+    ref = lat.read(L.FIELD3_POPS) * (after == 0)[None]
+    lat.close()
+    for wpb, force64 in ((4, "0"), (16, "0"), (8, "1")):
+        monkeypatch.setenv("LBM3D_INDEX64", force64)
+        h = L.Lattice3(half, cfg["tau"], cfg["u_max"], mirror=True)
+        h.set_block(wpb)
+        h.solve(200)
+        h.optimize_step(25, 200)
+        assert np.array_equal(h.read(L.FIELD3_POPS) * (after == 0)[None], ref)
+        h.close()
