@@ -859,9 +859,9 @@ lbm_status engine_create(int n, const lbm_params* params, const uint8_t* const* 
   for (int i = 1; i < n; ++i)
     if (params[i].precision != params[0].precision || params[i].residual_every != params[0].residual_every)
       return fail(LBM_ERR_ARG, "all lattices of a batch share precision and residual_every");
+  // every argument and geometry rule before any device call
   for (int i = 0; i < n; ++i) {
-    if (!cells[i]) return fail(LBM_ERR_ARG, "cell_types is NULL");
-    lbm_status st = check_params(params[i]);
+    lbm_status st = member_check(params[i], cells[i]);
     if (st != LBM_OK) return st;
   }
   Engine* E = nullptr;
