@@ -440,6 +440,26 @@ def leg_d3q19(L, I, stream, peak, cpu_seconds=4.0):
     out["optimize_tree3d_f32"] = {"workload": f"{cfg['name']}: 6 solves of {cfg['steps']} steps, n_swap {n_swap}",
                                   "glups": fluid * cfg["steps"] * 6 / dt / 1e9, "seconds": dt, "dp": dps}
     h.close()
+    # precision: 16-bit storage against the FP64 oracle on the 192 x 96 x 96 tree (800 steps from rest,
+    # long enough for the flow to reach every outlet)
+    import numpy as np
+    from oracle import lbm3d as o3
+    med = I.config_tree3d(192, 96, 96)
+    nz, ny, nx = med["cells"].shape
+    sv = o3.Solver3(o3.make_params3(nx, ny, nz, med["tau"], u_max=med["u_max"]), med["cells"])
+    o = sv.solve(800)
+    ref_frac = np.asarray(o["m_out"]) / np.sum(o["m_out"])
+    prec = {"workload": f"{med['name']}, 800 steps from rest", "oracle_dp": o["dp"]}
+    for pname, pv in (("f32", L.F32), ("bf16", L.BF16_SHIFTED), ("f16", L.F16_SHIFTED)):
+        h = L.Lattice3(med["cells"], med["tau"], med["u_max"], precision=pv, stream=stream)
+        r = h.solve(800)
+        frac = np.asarray(r["m_out"]) / np.sum(r["m_out"])
+        ux = h.read(L.FIELD3_UX).astype(np.float64)
+        prec[pname] = {"dp_rel_err": abs(r["dp"] - o["dp"]) / abs(o["dp"]),
+                       "outlet_fraction_max_abs_err": float(np.max(np.abs(frac - ref_frac))),
+                       "ux_max_err_rel": float(np.abs(ux - sv.ux).max() / np.abs(sv.ux).max())}
+        h.close()
+    out["precision_tree3d_192x96x96"] = prec
     small = I.config_tree3d_small()
     r, n, dt = oracle3_rate(small["cells"], small["tau"], small["u_max"], cpu_seconds)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
