@@ -57,9 +57,10 @@ def _p(a, ct):
 
 
 def make_params3(nx, ny, nz, tau, rho0=1.0, u_max=0.0, periodic=0, collision=COLLIDE_BGK, c_smag=0.0,
-                 mirror=False):
+                 mirror=0):
+    """mirror: bit 0 a symmetry plane below y = 0, bit 1 one below z = 0 (True = bit 0)."""
     return Params3(int(nx), int(ny), int(nz), int(periodic), float(tau), float(rho0), float(u_max), int(collision),
-                   int(bool(mirror)), float(c_smag))
+                   int(mirror), float(c_smag))
 
 
 def collide3(p, f):

@@ -27,6 +27,8 @@ static const int C3Z[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -
 static const int OPP3[19] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
 /* reflection in a plane normal to y: the direction with c_y negated */
 static const int MIR3[19] = {0, 1, 2, 4, 3, 5, 6, 9, 10, 7, 8, 11, 12, 13, 14, 18, 17, 16, 15};
+/* reflection in a plane normal to z: the direction with c_z negated */
+static const int MIRZ3[19] = {0, 1, 2, 3, 4, 6, 5, 7, 8, 9, 10, 13, 14, 11, 12, 17, 18, 15, 16};
 static const double W3[19] = {1.0 / 3.0,  1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0,
                               1.0 / 18.0, 1.0 / 18.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
                               1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
@@ -44,10 +46,12 @@ typedef struct {
                           scheme only)                                       */
   double tau, rho0, u_max;
   int32_t collision;   /* ORA3_COLLIDE_*, as in 2D                           */
-  int32_t mirror;      /* 1: a symmetry plane half a cell below row y = 0 (the
-                          2D rule of Sec. 3.3's half domain, normal to y): row
-                          0 may be fluid, and what crosses the plane comes back
-                          as the mirror image of what row 0 sends out         */
+  int32_t mirror;      /* bit 0: a symmetry plane half a cell below y = 0, bit
+                          1: one half a cell below z = 0 (the 2D rule of Sec.
+                          3.3's half domain, per plane): the layer next to a
+                          plane may be fluid, and what crosses a plane comes
+                          back as the mirror image of what that layer sends
+                          out (both components negated past the corner)      */
   double c_smag;       /* Smagorinsky constant                               */
 } ora3_params;
 
@@ -82,8 +86,8 @@ int32_t ora3_check_geometry(const ora3_params* p, const uint8_t* solid) {
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
-        int edge_y = !(p->periodic & 2) && ((y == 0 && !p->mirror) || y == ny - 1);
-        int edge_z = !(p->periodic & 4) && (z == 0 || z == nz - 1);
+        int edge_y = !(p->periodic & 2) && ((y == 0 && !(p->mirror & 1)) || y == ny - 1);
+        int edge_z = !(p->periodic & 4) && ((z == 0 && !(p->mirror & 2)) || z == nz - 1);
         if ((edge_y || edge_z) && !solid[cell3(p, x, y, z)]) return ORA3_ERR_GEOMETRY;
       }
   if (p->periodic & 1) return ORA3_OK;
@@ -122,7 +126,7 @@ void ora3_inlet_profile(const ora3_params* p, const uint8_t* solid, double* u_in
         while (hi < ny && !solid[cell3(p, 0, hi, z)]) ++hi;
         /* a run against the symmetry plane is half of a run twice as wide,
            centred on the plane */
-        if (p->mirror && lo == 0) lo = -hi;
+        if ((p->mirror & 1) && lo == 0) lo = -hi;
         double s = ((double)(y - lo) + 0.5) / (double)(hi - lo);
         ay = 4.0 * s * (1.0 - s);
       }
@@ -130,6 +134,7 @@ void ora3_inlet_profile(const ora3_params* p, const uint8_t* solid, double* u_in
         int lo = z, hi = z;
         while (lo > 0 && !solid[cell3(p, 0, y, lo - 1)]) --lo;
         while (hi < nz && !solid[cell3(p, 0, y, hi)]) ++hi;
+        if ((p->mirror & 2) && lo == 0) lo = -hi;
         double s = ((double)(z - lo) + 0.5) / (double)(hi - lo);
         az = 4.0 * s * (1.0 - s);
       }
@@ -197,12 +202,25 @@ static int pull3(const ora3_params* p, const uint8_t* solid, const double* fp, i
   if (p->periodic & 1) sx = (sx + p->nx) % p->nx;
   if (p->periodic & 2) sy = (sy + p->ny) % p->ny;
   if (p->periodic & 4) sz = (sz + p->nz) % p->nz;
-  if (p->mirror && !(p->periodic & 2) && sy == -1 && sx >= 0 && sx < p->nx && sz >= 0 && sz < p->nz) {
-    /* the ghost row below the symmetry plane is the mirror image of row 0: a
-       solid image reflects as a wall (halfway bounce-back); a fluid one sends
-       the population of its original cell with c_y negated */
-    size_t img = cell3(p, sx, 0, sz), here = cell3(p, x, y, z);
-    *out = solid[img] ? fp[OPP3[i] * n + here] : fp[MIR3[i] * n + img];
+  /* a ghost layer below a symmetry plane is the mirror image of the layer
+     next to it: a solid image reflects as a wall (halfway bounce-back); a
+     fluid one sends the population of its original cell with the crossed
+     components negated */
+  int ry = 0, rz = 0;
+  if ((p->mirror & 1) && !(p->periodic & 2) && sy == -1) {
+    ry = 1;
+    sy = 0;
+  }
+  if ((p->mirror & 2) && !(p->periodic & 4) && sz == -1) {
+    rz = 1;
+    sz = 0;
+  }
+  if ((ry || rz) && sx >= 0 && sx < p->nx && sy < p->ny && sz < p->nz) {
+    size_t img = cell3(p, sx, sy, sz), here = cell3(p, x, y, z);
+    int j = i;
+    if (ry) j = MIR3[j];
+    if (rz) j = MIRZ3[j];
+    *out = solid[img] ? fp[OPP3[i] * n + here] : fp[j * n + img];
     return 1;
   }
   if (sx < 0 || sx >= p->nx || sy < 0 || sy >= p->ny || sz < 0 || sz >= p->nz) return 0;

@@ -499,3 +499,30 @@ def test_mirror_half_domain_equals_upper_half_of_whole_domain():
     assert oh["dp"] == pytest.approx(ow["dp"], rel=1e-12)
     assert oh["m_in"] == pytest.approx(ow["m_in"] / 2, rel=1e-12)
     assert abs(sum(oh["m_out"]) - sum(ow["m_out"]) / 2) <= 1e-12 * abs(sum(ow["m_out"]))
+
+
+def test_mirror_quarter_domain_equals_a_quarter_of_the_whole_domain():
+    """Two planes (below y = 0 and below z = 0): the quarter follows the
+    corner block of the whole domain mirrored in both, including the edge
+    where both planes meet (both velocity components odd across their
+    planes)."""
+    from paper_1303_0107_gb300 import inputs as I
+    cfg = I.config_tree3d_small()
+    q = np.ascontiguousarray(cfg["cells"][17:, 17:, :])
+    half = np.concatenate([q[:, ::-1, :], q], axis=1)
+    whole = np.ascontiguousarray(np.concatenate([half[::-1], half], axis=0))
+    nzq, nyq, nx = q.shape
+    pq = o3.make_params3(nx, nyq, nzq, cfg["tau"], u_max=cfg["u_max"], mirror=3)
+    pw = o3.make_params3(nx, 2 * nyq, 2 * nzq, cfg["tau"], u_max=cfg["u_max"])
+    assert o3.check_geometry3(pq, q) == 0 and o3.check_geometry3(pw, whole) == 0
+    assert o3.check_geometry3(o3.make_params3(nx, nyq, nzq, cfg["tau"], mirror=1), q) != 0  # z = 0 fluid
+    sq, sw = o3.Solver3(pq, q), o3.Solver3(pw, whole)
+    assert np.array_equal(sq.u_in, sw.u_in[nzq:, nyq:])
+    oq, ow = sq.solve(300), sw.solve(300)
+    corner = (slice(nzq, None), slice(nyq, None))
+    scale = np.abs(sw.ux).max()
+    for a, b in ((sq.ux, sw.ux[corner]), (sq.uy, sw.uy[corner]), (sq.uz, sw.uz[corner]), (sq.rho, sw.rho[corner])):
+        assert np.abs(a - b).max() <= 1e-12 * max(scale, 1.0)
+    assert np.abs(sw.uz[:nzq][::-1] + sw.uz[nzq:]).max() <= 1e-12 * scale  # u_z odd across the z plane
+    assert oq["dp"] == pytest.approx(ow["dp"], rel=1e-12)
+    assert oq["m_in"] == pytest.approx(ow["m_in"] / 4, rel=1e-12)
