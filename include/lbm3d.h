@@ -18,7 +18,8 @@
  * weights 1/3, 1/18 (faces), 1/36 (edges); c_s^2 = 1/3.
  *
  * Geometry rules (lbm3d_create; LBM_ERR_GEOMETRY otherwise):
- *   - the faces y = 0 (unless mirror), y = ny-1, z = 0, z = nz-1 are solid;
+ *   - the faces y = 0, y = ny-1, z = 0, z = nz-1 are solid (but a face next
+ *     to a symmetry plane, see mirror);
  *   - inlet cells are the fluid cells of x = 0, outlet cells those of
  *     x = nx-1; a fluid (0,y,z) has a fluid (1,y,z), a fluid (nx-1,y,z) a
  *     fluid (nx-2,y,z); at least one inlet and one outlet cell;
@@ -26,7 +27,7 @@
  *     y, z), numbered in the order of their first cell (z-major, then y);
  *   - 4 <= nx, 3 <= ny, 3 <= nz, nx*ny*nz < 2^31 (LBM_ERR_ARG otherwise).
  * The optimiser never changes the cells with x < 2, x > nx-3, y = 0,
- * y = ny-1, z = 0 or z = nz-1 (row 0 stays as given next to a plane).
+ * y = ny-1, z = 0 or z = nz-1 (a plane's layer stays as given).
  */
 #ifndef LBM3D_GB300_H
 #define LBM3D_GB300_H
@@ -53,10 +54,12 @@ typedef struct {
                           part relaxed on its second-order Hermite projection) or Smagorinsky
                           (BGK at the local tau_eff of the closure nu_t = C^2 |S|) */
   double c_smag;       /* Smagorinsky constant C (>= 0) */
-  int32_t mirror;      /* 1: a symmetry plane lies half a cell below row y = 0 (Sec. 3.3's half
-                          domain, normal to y): row 0 may be fluid; what crosses the plane
-                          comes back with c_y negated, a solid image reflects as a wall, and
-                          an inlet run against the plane is half of a run twice as wide */
+  int32_t mirror;      /* symmetry planes (Sec. 3.3's half domain, per plane): bit 0 a plane
+                          half a cell below y = 0, bit 1 one below z = 0 (both: a quarter
+                          domain).  The layer next to a plane may be fluid; what crosses a
+                          plane comes back with that component of c negated (both past the
+                          corner), a solid image reflects as a wall, and an inlet run
+                          against a plane is half of a run twice as wide */
   int32_t reserved;    /* zero */
 } lbm3d_params;
 

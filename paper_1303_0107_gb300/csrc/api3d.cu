@@ -106,7 +106,7 @@ lbm_status check_params3(const lbm3d_params& p) {
       p.collision != LBM_COLLIDE_SMAGORINSKY)
     return fail(LBM_ERR_ARG, "unknown collision model");
   if (!(p.c_smag >= 0.0) || !std::isfinite(p.c_smag)) return fail(LBM_ERR_ARG, "c_smag must be >= 0");
-  if (p.mirror != 0 && p.mirror != 1) return fail(LBM_ERR_ARG, "mirror must be 0 or 1");
+  if (p.mirror < 0 || p.mirror > 3) return fail(LBM_ERR_ARG, "mirror must be a mask of bits 0 and 1");
   if (p.reserved) return fail(LBM_ERR_ARG, "reserved fields must be 0");
   return LBM_OK;
 }
@@ -116,12 +116,12 @@ lbm_status geometry3(const lbm3d_params& p, const uint8_t* solid, Geometry3& g) 
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y) {
-      const bool frame = (y == 0 && !p.mirror) || y == ny - 1 || z == 0 || z == nz - 1;
+      const bool frame = (y == 0 && !(p.mirror & 1)) || y == ny - 1 || (z == 0 && !(p.mirror & 2)) || z == nz - 1;
       for (int x = 0; x < nx; ++x) {
         const uint8_t s = solid[cell(p, x, y, z)];
         if (s > 1) return fail(LBM_ERR_GEOMETRY, "cell types must be 0 or 1");
         if (frame && !s)
-          return fail(LBM_ERR_GEOMETRY, "the faces y = 0 (unless mirror), ny-1, z = 0, nz-1 must be solid");
+          return fail(LBM_ERR_GEOMETRY, "the faces y = 0, ny-1, z = 0, nz-1 must be solid (but a plane's)");
         g.fluid += !s;
       }
     }
@@ -135,12 +135,13 @@ lbm_status geometry3(const lbm3d_params& p, const uint8_t* solid, Geometry3& g) 
         int lo = y, hi = y;
         while (lo > 0 && !solid[cell(p, 0, lo - 1, z)]) --lo;
         while (hi < ny && !solid[cell(p, 0, hi, z)]) ++hi;
-        if (p.mirror && lo == 0) lo = -hi;  // half of a run twice as wide, centred on the plane
+        if ((p.mirror & 1) && lo == 0) lo = -hi;  // half of a run twice as wide, centred on the plane
         const double sy = ((double)(y - lo) + 0.5) / (double)(hi - lo);
         lo = z;
         hi = z;
         while (lo > 0 && !solid[cell(p, 0, y, lo - 1)]) --lo;
         while (hi < nz && !solid[cell(p, 0, y, hi)]) ++hi;
+        if ((p.mirror & 2) && lo == 0) lo = -hi;
         const double sz = ((double)(z - lo) + 0.5) / (double)(hi - lo);
         g.u_in[(size_t)z * ny + y] = (float)(p.u_max * (4.0 * sy * (1.0 - sy)) * (4.0 * sz * (1.0 - sz)));
       }
@@ -330,10 +331,16 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
       for (int x = 0; x < p.nx; ++x)
         if (!cells[cell(p, x, y, z)]) row[x >> 5] &= ~(1u << (x & 31));
     }
-  if (p.mirror)  // the padding row below row 0 is its mirror image
+  // the padding rows past a symmetry plane are the mirror image of the layer next to it
+  // (the corner row below both planes the image of row (0, 0))
+  if (p.mirror & 1)
     for (int z = 0; z < p.nz; ++z)
       std::copy(mask.begin() + mask3_row(p.ny, v.ms, 0, z), mask.begin() + mask3_row(p.ny, v.ms, 0, z) + v.ms,
                 mask.begin() + mask3_row(p.ny, v.ms, -1, z));
+  if (p.mirror & 2)
+    for (int y = -1; y < p.ny; ++y)
+      std::copy(mask.begin() + mask3_row(p.ny, v.ms, y, 0), mask.begin() + mask3_row(p.ny, v.ms, y, 0) + v.ms,
+                mask.begin() + mask3_row(p.ny, v.ms, y, -1));
   void* f = nullptr;
   CU3(h->alloc(&f, (size_t)kQ3 * v.plane * h->elem));
   v.f = f;

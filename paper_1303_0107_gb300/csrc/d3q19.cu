@@ -53,6 +53,11 @@ __host__ __device__ constexpr int mir3(int i) {
   return (i == 3 || i == 4) ? 7 - i : (i == 7) ? 9 : (i == 9) ? 7 : (i == 8) ? 10 : (i == 10) ? 8
          : (i == 15) ? 18 : (i == 18) ? 15 : (i == 16) ? 17 : (i == 17) ? 16 : i;
 }
+// the direction with c_z negated (reflection in a plane normal to z)
+__host__ __device__ constexpr int mirz3(int i) {
+  return (i == 5 || i == 6) ? 11 - i : (i == 11) ? 13 : (i == 13) ? 11 : (i == 12) ? 14 : (i == 14) ? 12
+         : (i == 15) ? 17 : (i == 17) ? 15 : (i == 16) ? 18 : (i == 18) ? 16 : i;
+}
 __host__ __device__ constexpr float w3(int i) { return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f); }
 // c * v for c in {-1, 0, 1} without a multiply (0 * v is not 0 for v = inf/NaN)
 __device__ __forceinline__ float cmul(int c, float v) { return c == 0 ? 0.0f : (c > 0 ? v : -v); }
@@ -268,22 +273,29 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
   opaque(sy);
   opaque(sz);
   T* F = static_cast<T*>(v.f);
-  // Symmetry plane below row 0: the ghost row y = -1 is the image of row 0
-  // (its mask row is a copy of row 0, so nb tells whether an image cell is
-  // solid).  A population arriving from a fluid image cell is the one its
-  // original cell sent with c_y negated; one sent towards a fluid image cell
-  // comes back into row 0 with c_y negated, into the slot the local phase
-  // reads for it.  Solid images reflect as walls (the nb path).
-  const bool plane = (FEAT & kFeat3Mirror) && PHASE == 0 && !NB0 && y == 0;
+  // Symmetry planes below y = 0 and/or z = 0: a ghost layer is the image of
+  // the layer next to it (its mask rows are copies, so nb tells whether an
+  // image cell is solid).  A population arriving from a fluid image cell is
+  // the one its original cell sent with the crossed components negated; one
+  // sent towards a fluid image cell comes back into the plane's layer with
+  // those components negated, into the slot the local phase reads for it.
+  // Solid images reflect as walls (the nb path).
+  const bool py = (FEAT & kFeat3Mirror) && PHASE == 0 && !NB0 && (v.mirror & 1) && y == 0;
+  const bool pz = (FEAT & kFeat3Mirror) && PHASE == 0 && !NB0 && (v.mirror & 2) && z == 0;
   float g[kQ];
   g[0] = P3<T>::ld(F + c);
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const IX off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
+    const bool xy = cy3(i) > 0 && py, xz = cz3(i) > 0 && pz;  // the source lies past a plane
     if (PHASE == 1 || (!NB0 && ((nb >> opp3(i)) & 1u)))
       g[i] = P3<T>::ld(F + (opp3(i) * pl + c));
-    else if (cy3(i) > 0 && plane)
+    else if (xy && xz)
+      g[i] = P3<T>::ld(F + (mirz3(mir3(i)) * pl + c - cx3(i)));
+    else if (xy)
       g[i] = P3<T>::ld(F + (mir3(i) * pl + c - (cx3(i) + cz3(i) * sz)));
+    else if (xz)
+      g[i] = P3<T>::ld(F + (mirz3(i) * pl + c - (cx3(i) + cy3(i) * sy)));
     else
       g[i] = P3<T>::ld(F + (i * pl + c - off));
   }
@@ -301,10 +313,15 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const IX off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
+    const bool xy = cy3(i) < 0 && py, xz = cz3(i) < 0 && pz;  // the target lies past a plane
     if (PHASE == 1 || (!NB0 && ((nb >> i) & 1u)))
       P3<T>::st(F + (i * pl + c), g[i]);
-    else if (cy3(i) < 0 && plane)
+    else if (xy && xz)
+      P3<T>::st(F + (opp3(mirz3(mir3(i))) * pl + c + cx3(i)), g[i]);
+    else if (xy)
       P3<T>::st(F + (opp3(mir3(i)) * pl + c + (cx3(i) + cz3(i) * sz)), g[i]);
+    else if (xz)
+      P3<T>::st(F + (opp3(mirz3(i)) * pl + c + (cx3(i) + cy3(i) * sy)), g[i]);
     else
       P3<T>::st(F + (opp3(i) * pl + c + off), g[i]);
   }
@@ -392,23 +409,23 @@ inline int blocks_for(long long n, int threads) {
 }
 
 // ---- work-list ---------------------------------------------------------------
-// word i of the rows y in [y0, ny-2], z in [1, nz-2] (y0 = 1, or 0 next to a
-// symmetry plane for the step work-list)
-__device__ __forceinline__ void word3_of(const View3& v, int y0, int i, int& y, int& z, int& s) {
+// word i of the rows y in [y0, ny-2], z in [z0, nz-2] (y0 = z0 = 1, or 0
+// next to a symmetry plane for the step work-list)
+__device__ __forceinline__ void word3_of(const View3& v, int y0, int z0, int i, int& y, int& z, int& s) {
   const int per_z = (v.ny - 1 - y0) * v.nsx;
   const int zi = i / per_z;
   const int rest = i - zi * per_z;
   const int yi = rest / v.nsx;
   s = rest - yi * v.nsx;
   y = y0 + yi;
-  z = 1 + zi;
+  z = z0 + zi;
 }
 
 __global__ void k_seg3_flags(const View3 v, int total, int* __restrict__ flags) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   int y, z, s;
-  word3_of(v, first_row3(v), i, y, z, s);
+  word3_of(v, first_row3(v), first_layer3(v), i, y, z, s);
   flags[i] = ~v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + s] != 0u;
 }
 
@@ -420,7 +437,7 @@ __global__ void k_seg3_scatter(const View3 v, int total, const int* __restrict__
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total || !flags[i]) return;
   int y, z, s;
-  word3_of(v, first_row3(v), i, y, z, s);
+  word3_of(v, first_row3(v), first_layer3(v), i, y, z, s);
   const uint32_t own = v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + s];
   uint32_t solid_nb = 0;  // bit l: some neighbour of cell 32 s + l is solid
   for (int dz = -1; dz <= 1; ++dz)
@@ -432,8 +449,8 @@ __global__ void k_seg3_scatter(const View3 v, int total, const int* __restrict__
       solid_nb |= __funnelshift_r(m, row[s + 1], 1);    // c_x = +1
       solid_nb |= __funnelshift_l(row[s - 1], m, 1);    // c_x = -1
     }
-  // row 0 next to a symmetry plane pulls across it: never the open path
-  const bool open = (solid_nb & ~own) == 0u && y > 0;
+  // the layers next to a symmetry plane pull across it: never the open path
+  const bool open = (solid_nb & ~own) == 0u && y >= 1 && z >= 1;
   const int seg = (z * v.ny + y) * v.nsx + s;
   segs[offs[i]] = Seg3{seg | (open ? kSegOpen : 0), own};
 }
@@ -530,7 +547,7 @@ __global__ void k_oc3_count(const View3 v, int total, int* __restrict__ cnt_f, i
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   int y, z, s;
-  word3_of(v, 1, i, y, z, s);
+  word3_of(v, 1, 1, i, y, z, s);
   const Words3 m = words3(v, y, z, s);
   cnt_f[i] = __popc(m.fluid_cand);
   cnt_s[i] = __popc(m.solid_cand);
@@ -558,7 +575,7 @@ __global__ void k_oc3_emit(const View3 v, const float* __restrict__ drho, const 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   int y, z, s;
-  word3_of(v, 1, i, y, z, s);
+  word3_of(v, 1, 1, i, y, z, s);
   const Words3 m = words3(v, y, z, s);
   const double rho0 = (double)v.rho0;
   const long long sy = v.nxp, sz = (long long)v.ny * v.nxp;

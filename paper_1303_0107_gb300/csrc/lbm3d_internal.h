@@ -36,7 +36,8 @@ struct View3 {
   int idx64;             // step kernels index populations in 64 bits (19 planes reach 2^31
                          // elements, or LBM3D_INDEX64=1 in the environment), else in 32
   int collision;         // lbm_collision (non-BGK: the models build of the step kernels)
-  int mirror;            // symmetry plane below row 0 (the mirror build; row 0 may be fluid)
+  int mirror;            // symmetry planes (the mirror build): bit 0 below y = 0, bit 1 below
+                         // z = 0; the layer next to a plane may be fluid
   float tau;             // relaxation time (the Smagorinsky root needs it)
   float c_smag;          // Smagorinsky constant
 };
@@ -47,10 +48,14 @@ __host__ __device__ inline long long mask3_row(int ny, int ms, int y, int z) {
 __host__ __device__ inline long long mask3_words(int ny, int nz, int ms) {
   return (long long)(ny + 2) * (nz + 2) * ms;
 }
-// first row of the step work-list: row 0 holds fluid only next to a symmetry plane
-__host__ __device__ inline int first_row3(const View3& v) { return v.mirror ? 0 : 1; }
-// words of the step work-list's rows: y in [first_row3, ny-2], z in [1, nz-2]
-__host__ __device__ inline int seg3_words(const View3& v) { return (v.ny - 1 - first_row3(v)) * (v.nz - 2) * v.nsx; }
+// first row / layer of the step work-list: y = 0 (z = 0) holds fluid only next
+// to a symmetry plane below it
+__host__ __device__ inline int first_row3(const View3& v) { return (v.mirror & 1) ? 0 : 1; }
+__host__ __device__ inline int first_layer3(const View3& v) { return (v.mirror & 2) ? 0 : 1; }
+// words of the step work-list's rows: y in [first_row3, ny-2], z in [first_layer3, nz-2]
+__host__ __device__ inline int seg3_words(const View3& v) {
+  return (v.ny - 1 - first_row3(v)) * (v.nz - 1 - first_layer3(v)) * v.nsx;
+}
 
 // Step work-list entry: segment (z * ny + y) * nsx + s (bits 0..29) with
 // kSegOpen set when no fluid cell of it has a solid neighbour, and its own
@@ -64,7 +69,8 @@ constexpr int kSegOpen = 1 << 30;
 static_assert(sizeof(Seg3) == 8, "Seg3 layout");
 
 // Step work-list: the segments (z, y, s) of rows y in [first_row3, ny-2], z
-// in [1, nz-2] holding a fluid cell, in ascending order; *n_segs their count.
+// in [first_layer3, nz-2] holding a fluid cell, in ascending order; *n_segs
+// their count.
 // scratch holds seg3_scratch_ints(total) ints, total = seg3_words(v).
 size_t seg3_scratch_ints(long long total);
 cudaError_t launch_build_segments3(const View3& v, int* scratch, Seg3* segs, int* n_segs, cudaStream_t stream);

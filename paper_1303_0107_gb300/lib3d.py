@@ -67,11 +67,13 @@ def make_params3(nx, ny, nz, tau, u_max, rho0=1.0, precision=F32, reinit=REINIT_
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     return Params3(int(nx), int(ny), int(nz), int(precision), float(tau), float(rho0), float(u_max), int(reinit),
-                   int(collision), float(c_smag), int(bool(mirror)), 0)
+                   int(collision), float(c_smag), int(mirror), 0)
 
 
 class Lattice3:
-    """One D3Q19 lattice (cell map [nz][ny][nx] + populations) resident on the GPU."""
+    """One D3Q19 lattice (cell map [nz][ny][nx] + populations) resident on the GPU.
+
+    mirror: bit 0 a symmetry plane below y = 0, bit 1 one below z = 0 (True = bit 0)."""
 
     def __init__(self, cells, tau, u_max, rho0=1.0, precision=F32, reinit=REINIT_WARM, collision=0, c_smag=0.0,
                  mirror=False, stream=None):

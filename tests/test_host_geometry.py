@@ -140,4 +140,7 @@ def test_3d_geometry_verdicts_match_the_rules():
             n_bad += rule_bad
     assert n_bad > 5
     half = np.ascontiguousarray(I.config_tree3d_small()["cells"][:, 17:, :])
-    assert _verdict3(half) == GEOMETRY and _verdict3(half, mirror=True) != GEOMETRY
+    assert _verdict3(half) == GEOMETRY and _verdict3(half, mirror=1) != GEOMETRY
+    quarter = np.ascontiguousarray(I.config_tree3d_small()["cells"][17:, 17:, :])
+    assert _verdict3(quarter, mirror=1) == GEOMETRY and _verdict3(quarter, mirror=2) == GEOMETRY
+    assert _verdict3(quarter, mirror=3) != GEOMETRY

@@ -408,3 +408,62 @@ def test_mirror_exchange_and_launch_shapes(monkeypatch):
         h.optimize_step(25, 200)
         assert np.array_equal(h.read(L.FIELD3_POPS) * (after == 0)[None], ref)
         h.close()
+
+
+def _quarter_and_whole():
+    cfg = I.config_tree3d_small()
+    q = np.ascontiguousarray(cfg["cells"][17:, 17:, :])
+    half = np.concatenate([q[:, ::-1, :], q], axis=1)
+    whole = np.ascontiguousarray(np.concatenate([half[::-1], half], axis=0))
+    return cfg, q, whole
+
+
+def test_quarter_domain_matches_oracle_and_the_whole_on_the_gpu():
+    """Planes below y = 0 and z = 0 (mirror = 3): against the oracle at the
+    FP32 tolerance, and against the corner block of the GPU's whole domain."""
+    cfg, q, whole = _quarter_and_whole()
+    nz, ny, nx = q.shape
+    lat = L.Lattice3(q, cfg["tau"], cfg["u_max"], mirror=3)
+    g = lat.solve(300)
+    sv = o3.Solver3(o3.make_params3(nx, ny, nz, cfg["tau"], u_max=cfg["u_max"], mirror=3), q)
+    o = sv.solve(300)
+    _compare_fields(lat, sv, q)
+    assert abs(g["dp"] - o["dp"]) <= TOL * abs(o["dp"])
+    b = L.Lattice3(whole, cfg["tau"], cfg["u_max"])
+    rb = b.solve(300)
+    for f in (L.FIELD3_UX, L.FIELD3_UY, L.FIELD3_UZ, L.FIELD3_DRHO):
+        ua, ub = lat.read(f), b.read(f)[nz:, ny:]
+        assert np.abs(ua - ub).max() <= TOL * max(np.abs(ub).max(), 1e-30)
+    assert abs(g["dp"] - rb["dp"]) <= TOL * abs(rb["dp"])
+    lat.close()
+    b.close()
+
+
+def test_quarter_domain_exchange_and_shapes(monkeypatch):
+    cfg, q, _ = _quarter_and_whole()
+    nz, ny, nx = q.shape
+    lat = L.Lattice3(q, cfg["tau"], cfg["u_max"], mirror=3)
+    lat.solve(200)
+    fields = [lat.read(f) for f in (L.FIELD3_DRHO, L.FIELD3_UX, L.FIELD3_UY, L.FIELD3_UZ)]
+    p = o3.make_params3(nx, ny, nz, cfg["tau"], u_max=cfg["u_max"], mirror=3)
+    cand, score = o3.scores3(p, q, 1.0 + fields[0].astype(np.float64), *[f.astype(np.float64) for f in fields[1:]])
+    fi, si = o3.select3(p, cand, score, 15)
+    out = lat.optimize_step(15, 200)
+    after = lat.read(L.FIELD3_MASK)
+    assert np.array_equal(after[0], q[0]) and np.array_equal(after[:, 0], q[:, 0])  # the planes' layers stay
+    sv = o3.Solver3(p, q)
+    sv.solve(200)
+    o3.apply3(p, sv.solid, sv.f, fi, si)
+    o = sv.solve(200)
+    assert np.array_equal(sv.solid, after)
+    assert abs(out["dp"] - o["dp"]) <= TOL * abs(o["dp"])
+    ref = lat.read(L.FIELD3_POPS) * (after == 0)[None]
+    lat.close()
+    for wpb, force64 in ((4, "0"), (8, "1")):
+        monkeypatch.setenv("LBM3D_INDEX64", force64)
+        h = L.Lattice3(q, cfg["tau"], cfg["u_max"], mirror=3)
+        h.set_block(wpb)
+        h.solve(200)
+        h.optimize_step(15, 200)
+        assert np.array_equal(h.read(L.FIELD3_POPS) * (after == 0)[None], ref)
+        h.close()
