@@ -356,6 +356,9 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   v.u_in = u_in;
   CU3(h->alloc(&v.flag, sizeof(int)));
   CU3(h->alloc(&h->segs, sizeof(Seg3) * h->total_words));
+  uint32_t* nbs = nullptr;
+  CU3(h->alloc(&nbs, sizeof(uint32_t) * 32 * (size_t)h->total_words));
+  v.nbs = nbs;
   CU3(h->alloc(&h->seg_scratch, sizeof(int) * seg3_scratch_ints(h->total_words)));
   CU3(h->alloc(&h->n_segs, sizeof(int)));
   CU3(h->alloc(&h->in_rows, sizeof(int) * g.in_rows.size()));

@@ -334,44 +334,56 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
   }
 }
 
-// One phase on one row segment.  The mask words are read before waiting for
-// the previous step (they change only between solves), the populations after.
-// Phase A on a segment whose fluid cells have no solid neighbour (and hence
-// no port cell: outside the row reads as solid) takes the select-free path.
+// Solid flags of the 18 neighbours of the lane's cell of segment `seg` (bit
+// i: x + c_i is solid), from the mask: lanes 0..26 load the 27 words around
+// the segment (rows y-1..y+1 x z-1..z+1, words s-1..s+1) in one instruction
+// and the warp shares them by shuffles.
+__device__ __forceinline__ uint32_t neighbour_flags3(const View3& v, int seg, int lane) {
+  const int row = seg / v.nsx;
+  const int s = seg - row * v.nsx;
+  const int z = row / v.ny;
+  const int y = row - z * v.ny;
+  // lanes 0..8: word s of row r = (dz+1)*3 + (dy+1); 9..17: word s-1; 18..26: word s+1
+  uint32_t wv = 0xffffffffu;
+  if (lane < 27) {
+    const int part = lane / 9, r = lane - 9 * part;
+    const int dy = r % 3 - 1, dz = r / 3 - 1;
+    const int dw = part == 0 ? 0 : (part == 1 ? -1 : 1);
+    wv = v.mask[mask3_row(v.ny, v.ms, y + dy, z + dz) + 1 + s + dw];
+  }
+  uint32_t M[9], Lw[9], H[9];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    M[r] = __shfl_sync(kFull, wv, r);
+    Lw[r] = __shfl_sync(kFull, wv, 9 + r);
+    H[r] = __shfl_sync(kFull, wv, 18 + r);
+  }
+  uint32_t nb = 0;
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const int r = (cz3(i) + 1) * 3 + (cy3(i) + 1);
+    const uint32_t word = cx3(i) == 0 ? M[r]
+                          : cx3(i) > 0 ? __funnelshift_r(M[r], H[r], 1)
+                                       : __funnelshift_l(Lw[r], M[r], 1);
+    nb |= ((word >> lane) & 1u) << i;
+  }
+  return nb;
+}
+
+// One phase on task t of the list (one row segment).  The neighbour flags
+// (built with the list) are read before waiting for the previous step, the
+// populations after.  Phase A on a segment whose fluid cells have no solid
+// neighbour (and hence no port cell: outside the row reads as solid) takes
+// the select-free path.
 template <class T, int PHASE, int MOM, class IX, int FEAT>
-__device__ __forceinline__ void seg_task3(const View3& v, Seg3 sg, int lane, bool& waited) {
+__device__ __forceinline__ void seg_task3(const View3& v, Seg3 sg, int t, int lane, bool& waited) {
   const int seg = sg.seg & kSegIndexMask;
   const bool open = PHASE == 0 && (sg.seg & kSegOpen);
   const int row = seg / v.nsx;
   const int s = seg - row * v.nsx;
   const int z = row / v.ny;
   const int y = row - z * v.ny;
-  uint32_t nb = 0;  // bit i: cell x + c_i is solid (phase A only)
-  if (PHASE == 0 && !open) {
-    // lanes 0..8: word s of row r = (dz+1)*3 + (dy+1); 9..17: word s-1; 18..26: word s+1
-    uint32_t wv = 0xffffffffu;
-    if (lane < 27) {
-      const int part = lane / 9, r = lane - 9 * part;
-      const int dy = r % 3 - 1, dz = r / 3 - 1;
-      const int dw = part == 0 ? 0 : (part == 1 ? -1 : 1);
-      wv = v.mask[mask3_row(v.ny, v.ms, y + dy, z + dz) + 1 + s + dw];
-    }
-    uint32_t M[9], Lw[9], H[9];
-#pragma unroll
-    for (int r = 0; r < 9; ++r) {
-      M[r] = __shfl_sync(kFull, wv, r);
-      Lw[r] = __shfl_sync(kFull, wv, 9 + r);
-      H[r] = __shfl_sync(kFull, wv, 18 + r);
-    }
-#pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-      const int r = (cz3(i) + 1) * 3 + (cy3(i) + 1);
-      const uint32_t word = cx3(i) == 0 ? M[r]
-                            : cx3(i) > 0 ? __funnelshift_r(M[r], H[r], 1)
-                                         : __funnelshift_l(Lw[r], M[r], 1);
-      nb |= ((word >> lane) & 1u) << i;
-    }
-  }
+  const uint32_t nb = (PHASE == 0 && !open) ? v.nbs[(long long)t * 32 + lane] : 0u;
   if (!waited) {  // warp-uniform: the previous step's populations are final from here on
     asm volatile("griddepcontrol.wait;" ::: "memory");
     waited = true;
@@ -398,7 +410,7 @@ __global__ void __launch_bounds__(512) k_step3(const View3 v, const Seg3* __rest
   const int stride = gridDim.x * wpb;
   bool waited = false;
   for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < nseg; t += stride)
-    seg_task3<T, PHASE, MOM, IX, FEAT>(v, segs[t], lane, waited);
+    seg_task3<T, PHASE, MOM, IX, FEAT>(v, segs[t], t, lane, waited);
   // every thread waits once, so this grid completes only after the previous one
   if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
@@ -453,6 +465,20 @@ __global__ void k_seg3_scatter(const View3 v, int total, const int* __restrict__
   const bool open = (solid_nb & ~own) == 0u && y >= 1 && z >= 1;
   const int seg = (z * v.ny + y) * v.nsx + s;
   segs[offs[i]] = Seg3{seg | (open ? kSegOpen : 0), own};
+}
+
+// neighbour flags of every cell of the list's segments that are not open
+// (one warp per segment; open segments need none)
+__global__ void k_nb3(const View3 v, const Seg3* __restrict__ segs, const int* __restrict__ n_segs,
+                      uint32_t* __restrict__ nbs) {
+  const int lane = threadIdx.x & 31;
+  const int nseg = *n_segs;
+  const int stride = (gridDim.x * blockDim.x) >> 5;
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nseg; t += stride) {
+    const Seg3 sg = segs[t];
+    if (sg.seg & kSegOpen) continue;  // warp-uniform
+    nbs[(long long)t * 32 + lane] = neighbour_flags3(v, sg.seg & kSegIndexMask, lane);
+  }
 }
 
 // ---- reductions ----------------------------------------------------------------
@@ -716,7 +742,11 @@ cudaError_t launch_build_segments3(const View3& v, int* scratch, Seg3* segs, int
   k_seg3_scatter<<<blocks_for(total, 256), 256, 0, stream>>>(v, total, flags, offs, segs);
   count_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return cudaMemcpyAsync(n_segs, offs + total, sizeof(int), cudaMemcpyDeviceToDevice, stream);
+  if ((e = cudaMemcpyAsync(n_segs, offs + total, sizeof(int), cudaMemcpyDeviceToDevice, stream)) != cudaSuccess)
+    return e;
+  k_nb3<<<blocks_for((long long)total * 32, 256), 256, 0, stream>>>(v, segs, n_segs, const_cast<uint32_t*>(v.nbs));
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 int step3_resident_blocks(int precision, int phase, int moments, int warps_per_block, const View3& v) {

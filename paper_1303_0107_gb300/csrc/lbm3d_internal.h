@@ -26,6 +26,9 @@ struct View3 {
   float* uy;             // [plane]
   float* uz;             // [plane]
   const float* u_in;     // [nz * ny] inlet u_x of cell (0, y, z); 0 where no inlet cell
+  const uint32_t* nbs;   // [32 per work-list entry]: solid flags of the 18 neighbours of each
+                         // cell of a segment that is not open (bit i: x + c_i solid), built with
+                         // the work-list
   int* flag;             // bit 0: a moments step saw a non-finite value
   long long plane;       // elements per population plane: nz * ny * nxp
   int nx, ny, nz;
