@@ -776,7 +776,7 @@ lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool
   }
   CUE(cudaEventCreate(&E->ev_begin));
   CUE(cudaEventCreate(&E->ev_end));
-  CUE(E->n_segs.reserve(sizeof(int)));
+  CUE(E->n_segs.reserve(2 * sizeof(int)));
   CUE(E->bar.reserve(sizeof(StepBarrier)));
   CUE(cudaMemsetAsync(E->bar.p, 0, sizeof(StepBarrier), E->stream));
 #undef CUE
@@ -788,8 +788,9 @@ lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool
 lbm_status rebuild_worklist(Engine* E) {
   if (E->n() == 0) return LBM_OK;
   CU(launch_build_segments(static_cast<const LatticeView*>(E->L.views.p), static_cast<const int*>(E->L.seg_word_off.p),
-                           E->n(), E->L.total_seg_words, static_cast<int*>(E->seg_scratch.p),
-                           static_cast<SegRef*>(E->segs.p), static_cast<int*>(E->n_segs.p), E->stream));
+                           E->n(), E->L.total_seg_words, std::max(1, E->L.total_seg_words),
+                           static_cast<int*>(E->seg_scratch.p), static_cast<SegRef*>(E->segs.p),
+                           static_cast<int*>(E->n_segs.p), E->stream));
   CU(launch_count_fluid(static_cast<const LatticeView*>(E->L.views.p), static_cast<const int*>(E->L.word_off.p),
                         E->n(), E->L.total_words, static_cast<unsigned long long*>(E->fluid_dev.p), E->stream));
   DEBUG_SYNC(E, "work-list");
@@ -817,7 +818,7 @@ lbm_status engine_set_members(Engine* E, const std::vector<Member*>& members) {
   long long max_cells = 0;
   for (Member* mb : members) max_cells = std::max<long long>(max_cells, (long long)mb->nx * mb->ny);
   const size_t nn = std::max<size_t>(1, n);
-  CU(E->segs.reserve(sizeof(SegRef) * std::max(1, E->L.total_seg_words)));
+  CU(E->segs.reserve(segment_list_bytes(std::max(1, E->L.total_seg_words))));
   CU(E->seg_scratch.reserve(segment_scratch_ints(E->L.total_seg_words) * sizeof(int)));
   CU(E->partials.reserve(sizeof(double) * 2 * kResidualBlocks * nn));
   CU(E->result.reserve(sizeof(double) * kResultDoubles * nn));

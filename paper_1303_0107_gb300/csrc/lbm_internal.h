@@ -156,9 +156,21 @@ cudaError_t launch_unpack_mask(const uint32_t* mask, int nx, int ny, int wpr, ui
 // a device copy of the views' seg_word_off plus the total at [n]; scratch
 // holds segment_scratch_ints(total) ints, segs room for total entries.
 size_t segment_scratch_ints(long long total_words);
+// The list buffer holds `capacity` SegRef entries followed by 32 neighbour
+// flag words (uint16_t, see kNbE..kNbSE) per entry: those of the cells of
+// entry t at flags + 32 t, for phase A.  n_segs[0] receives the count,
+// n_segs[1] the capacity (so that kernels find the flags).
 cudaError_t launch_build_segments(const LatticeView* views, const int* seg_word_off, int n_lattices,
-                                  int total_words, int* scratch, SegRef* segs, int* n_segs,
+                                  int total_words, int capacity, int* scratch, SegRef* segs, int* n_segs,
                                   cudaStream_t stream);
+inline size_t segment_list_bytes(int capacity) { return (size_t)capacity * (sizeof(SegRef) + 32 * sizeof(uint16_t)); }
+__host__ __device__ inline const uint16_t* segment_flags(const SegRef* segs, const int* n_segs) {
+  return reinterpret_cast<const uint16_t*>(segs + n_segs[1]);
+}
+// neighbour solid flags of a cell, bit i-1 = solid(x + c_i), i = 1..8 (E N W S NE NW SW SE);
+// kNbMirror marks a cell of row 0 next to a symmetry plane (whose S flag is then set too)
+constexpr unsigned kNbE = 1u, kNbN = 2u, kNbW = 4u, kNbS = 8u, kNbNE = 16u, kNbNW = 32u, kNbSW = 64u,
+                   kNbSE = 128u, kNbMirror = 256u;
 // fluid cells of each lattice into count[l] (zeroed here); word_off as for
 // the exchange below
 cudaError_t launch_count_fluid(const LatticeView* views, const int* word_off, int n_lattices,

@@ -64,11 +64,12 @@ int64_t cells_of(const Pending& p) { return (int64_t)p.r.params.nx * p.r.params.
 int64_t footprint_of(const lbm_params& p, int32_t n_iter) {
   const int64_t cells = (int64_t)p.nx * p.ny;
   // the member's own allocation; its share of the set's work-list (segment
-  // list and scan scratch, under 1 byte per cell) and of the read-back buffer
-  // (4 bytes per cell); for optimising requests the exchange scratch: counts
-  // and offsets per mask word, 24 bytes of keys and indices per cell and
-  // 4 bytes of picks per cell
-  int64_t b = (int64_t)member_footprint(p) + 5 * cells + 4096;
+  // entries with their neighbour flags, 72 bytes per 32-cell word, and scan
+  // scratch: under 3 bytes per cell) and of the read-back buffer (4 bytes
+  // per cell); for optimising requests the exchange scratch: counts and
+  // offsets per mask word, 24 bytes of keys and indices per cell and 4 bytes
+  // of picks per cell
+  int64_t b = (int64_t)member_footprint(p) + 7 * cells + 4096;
   if (n_iter > 0) b += 29 * cells;
   return b;
 }
@@ -205,6 +206,7 @@ void lbm_server_s::loop() {
       slots.push_back(std::move(sl));
       changed = true;
     }
+    bool withdrew = false;
     {  // withdraw cancelled resident requests before this tick
       std::vector<int64_t> gone;
       {
@@ -218,6 +220,7 @@ void lbm_server_s::loop() {
             finish(x, LBM_ERR_CANCELLED);
             delete x.m;
             changed = true;
+            withdrew = true;
           } else {
             keep.push_back(std::move(x));
           }
@@ -227,6 +230,8 @@ void lbm_server_s::loop() {
       }
     }
     if (slots.empty()) {
+      // a withdrawal freed room after this tick's admission: admit again first
+      if (withdrew) continue;
       // nothing resident and nothing admitted (only if a request can never fit)
       std::unique_lock<std::mutex> lk(mu);
       if (!queue.empty() && adm.empty()) {

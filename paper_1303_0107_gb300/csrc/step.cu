@@ -266,10 +266,11 @@ __device__ __forceinline__ void outlet_rule(float (&g)[9], float rho0, int schem
 // build has neither, so the common path keeps its registers and branches.
 constexpr int kFeatModels = 1, kFeatMirror = 2;
 
-// neighbour solid flags, bit i-1 = solid(x + c_i), i = 1..8 (E N W S NE NW SW SE);
-// kMirror marks a cell of row 0 next to a symmetry plane
-constexpr unsigned kE = 1u, kN = 2u, kW = 4u, kS = 8u, kNE = 16u, kNW = 32u, kSW = 64u, kSE = 128u,
-                   kMirror = 256u;
+// neighbour solid flags (built with the work-list), bit i-1 = solid(x + c_i),
+// i = 1..8 (E N W S NE NW SW SE); kMirror marks a cell of row 0 next to a
+// symmetry plane
+constexpr unsigned kE = kNbE, kN = kNbN, kW = kNbW, kS = kNbS, kNE = kNbNE, kNW = kNbNW, kSW = kNbSW,
+                   kSE = kNbSE, kMirror = kNbMirror;
 
 // Threads per block at most, by cells per thread (the register budget per
 // thread is 64 with one cell, 80 with two).
@@ -293,7 +294,8 @@ struct SegCtx {
 
 template <class T, int PHASE, int FEAT = 0>
 __device__ __forceinline__ void seg_prologue(const LatticeView* __restrict__ views, const SegRef sr, bool valid,
-                                             const int lane, SegCtx<T>& s) {
+                                             const int lane, SegCtx<T>& s, const uint16_t* __restrict__ nbs,
+                                             int t) {
   const LatticeView* __restrict__ L = views + (valid ? sr.lattice : 0);
   const int y = sr.yw >> kSegWordBits;
   const int w = sr.yw & ((1 << kSegWordBits) - 1);
@@ -329,25 +331,35 @@ __device__ __forceinline__ void seg_prologue(const LatticeView* __restrict__ vie
   s.inlet = (x == 0);
   s.outlet = (x == L->nx - 1);
   if (PHASE == 0) {
-    // padded mask: words w-1 and w+1 of rows y-1..y+1 always exist and are
-    // solid outside the lattice
-    const uint32_t* rn = mr + ms;
-    const uint32_t* rs = mr - ms;
-    const uint32_t mn = rn[w], msth = rs[w];
-    const uint32_t eC = __funnelshift_r(mc, mr[w + 1], 1), wC = __funnelshift_l(mr[w - 1], mc, 1);
-    const uint32_t eN = __funnelshift_r(mn, rn[w + 1], 1), wN = __funnelshift_l(rn[w - 1], mn, 1);
-    const uint32_t eS = __funnelshift_r(msth, rs[w + 1], 1), wS = __funnelshift_l(rs[w - 1], msth, 1);
-    s.nb = ((eC >> lane) & 1u) | (((mn >> lane) & 1u) << 1) | (((wC >> lane) & 1u) << 2) |
-           (((msth >> lane) & 1u) << 3) | (((eN >> lane) & 1u) << 4) | (((wN >> lane) & 1u) << 5) |
-           (((wS >> lane) & 1u) << 6) | (((eS >> lane) & 1u) << 7);
-    // Symmetry plane half a cell below row 0 (the padding row below holds
-    // row 0's mirror image, so the SW / SE flags already tell whether the
-    // image cell is solid).  What row 0 sends across the plane comes back
-    // reflected: straight down returns as straight up into the same cell --
-    // the bounce-back slot -- and a diagonal returns into the row-0
-    // neighbour it was heading past: SW into (x-1, 0) as NW, SE into
-    // (x+1, 0) as NE.
-    if ((FEAT & kFeatMirror) && y == 0 && L->mirror) s.nb |= kS | kMirror;
+    if (sizeof(T) == 4) {
+      // FP32: the neighbour flags built with the work-list (one coalesced
+      // 16-bit word per cell, by task number, the symmetry-plane mark below
+      // included; builds without the plane drop it).  The 16-bit builds form
+      // them from the mask words instead: for them the extra bytes cost more
+      // than the saved instructions (measured).
+      s.nb = nbs[(long long)t * 32 + lane];
+      if (!(FEAT & kFeatMirror)) s.nb &= ~kMirror;
+    } else {
+      // padded mask: words w-1 and w+1 of rows y-1..y+1 always exist and are
+      // solid outside the lattice
+      const uint32_t* rn = mr + ms;
+      const uint32_t* rs = mr - ms;
+      const uint32_t mn = rn[w], msth = rs[w];
+      const uint32_t eC = __funnelshift_r(mc, mr[w + 1], 1), wC = __funnelshift_l(mr[w - 1], mc, 1);
+      const uint32_t eN = __funnelshift_r(mn, rn[w + 1], 1), wN = __funnelshift_l(rn[w - 1], mn, 1);
+      const uint32_t eS = __funnelshift_r(msth, rs[w + 1], 1), wS = __funnelshift_l(rs[w - 1], msth, 1);
+      s.nb = ((eC >> lane) & 1u) | (((mn >> lane) & 1u) << 1) | (((wC >> lane) & 1u) << 2) |
+             (((msth >> lane) & 1u) << 3) | (((eN >> lane) & 1u) << 4) | (((wN >> lane) & 1u) << 5) |
+             (((wS >> lane) & 1u) << 6) | (((eS >> lane) & 1u) << 7);
+      // Symmetry plane half a cell below row 0 (the padding row below holds
+      // row 0's mirror image, so the SW / SE flags already tell whether the
+      // image cell is solid).  What row 0 sends across the plane comes back
+      // reflected: straight down returns as straight up into the same cell
+      // -- the bounce-back slot -- and a diagonal returns into the row-0
+      // neighbour it was heading past: SW into (x-1, 0) as NW, SE into
+      // (x+1, 0) as NE.
+      if ((FEAT & kFeatMirror) && y == 0 && L->mirror) s.nb |= kS | kMirror;
+    }
   }
 }
 
@@ -469,13 +481,14 @@ __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
 // issued before the first cell is updated (more bytes in flight per thread).
 template <class T, int PHASE, int MOM, int CPT, bool CG, int FEAT = 0>
 __device__ __forceinline__ void phase_task(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
-                                           int nseg, int task, int lane, bool& waited) {
+                                           const uint16_t* __restrict__ nbs, int nseg, int task, int lane,
+                                           bool& waited) {
   SegCtx<T> s[CPT];
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
     const int idx = task * CPT + k;
     const bool valid = CPT == 1 || idx < nseg;  // one segment per task: task < nseg already
-    seg_prologue<T, PHASE, FEAT>(views, segs[valid ? idx : 0], valid, lane, s[k]);
+    seg_prologue<T, PHASE, FEAT>(views, segs[valid ? idx : 0], valid, lane, s[k], nbs, valid ? idx : 0);
   }
   if (!waited) {  // warp-uniform: populations of the previous step are final from here on
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -503,12 +516,13 @@ __global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31;
   const int nseg = *n_segs;
+  const uint16_t* nbs = segment_flags(segs, n_segs);
   const int ntask = (nseg + CPT - 1) / CPT;
   const int wpb = blockDim.x >> 5;
   const int stride = gridDim.x * wpb;
   bool waited = false;
   for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntask; t += stride)
-    phase_task<T, PHASE, MOM, CPT, false, FEAT>(views, segs, nseg, t, lane, waited);
+    phase_task<T, PHASE, MOM, CPT, false, FEAT>(views, segs, nbs, nseg, t, lane, waited);
   // every thread waits once, so this grid completes only after the previous
   // one (the next step relies on that)
   if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -571,11 +585,12 @@ __device__ __forceinline__ void cp_async_word(uint32_t* dst, const T* F, int off
 
 template <class T, int PHASE>
 __device__ __forceinline__ void stage_issue(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
-                                            int nseg, int t, int lane, uint32_t* buf) {
+                                            const uint16_t* __restrict__ nbs, int nseg, int t, int lane,
+                                            uint32_t* buf) {
   const bool valid = t < nseg;
   const SegRef sr = segs[valid ? t : 0];
   SegCtx<T> s;
-  seg_prologue<T, PHASE>(views, sr, valid, lane, s);
+  seg_prologue<T, PHASE>(views, sr, valid, lane, s, nbs, valid ? t : 0);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const int off = s.fluid ? src_off<PHASE>(i, s.c, s.pitch, s.pl, s.nb, s.inlet, s.outlet) : -1;
@@ -637,9 +652,11 @@ __global__ void __launch_bounds__(512, 2)
   // populations of the previous step are final from here on
   asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll
-  for (int k = 0; k < NS - 1; ++k) stage_issue<T, PHASE>(views, segs, nseg, first + k * stride, lane, wbuf + k * kStageWords);
+  const uint16_t* nbs = segment_flags(segs, n_segs);
+  for (int k = 0; k < NS - 1; ++k)
+    stage_issue<T, PHASE>(views, segs, nbs, nseg, first + k * stride, lane, wbuf + k * kStageWords);
   for (int k = 0; first + k * stride < nseg; ++k) {
-    stage_issue<T, PHASE>(views, segs, nseg, first + (k + NS - 1) * stride, lane,
+    stage_issue<T, PHASE>(views, segs, nbs, nseg, first + (k + NS - 1) * stride, lane,
                           wbuf + ((k + NS - 1) % NS) * kStageWords);
     cp_async_wait<NS>();  // the stage of task k has landed
     stage_consume<T, PHASE, MOM>(views, wbuf + (k % NS) * kStageWords, lane);
@@ -700,12 +717,13 @@ __global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
   const int wpb = blockDim.x >> 5;
   const int stride = gridDim.x * wpb;
   const int first = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const uint16_t* nbs = segment_flags(segs, n_segs);
   unsigned target = 0;
   bool waited = true;  // a cooperative launch follows the stream order: nothing to wait for
   for (int p = 0; p < n_pairs; ++p) {
-    for (int t = first; t < ntask; t += stride) phase_task<T, 0, 0, CPT, true>(views, segs, nseg, t, lane, waited);
+    for (int t = first; t < ntask; t += stride) phase_task<T, 0, 0, CPT, true>(views, segs, nbs, nseg, t, lane, waited);
     if (!grid_barrier(bar, target)) return;
-    for (int t = first; t < ntask; t += stride) phase_task<T, 1, 0, CPT, true>(views, segs, nseg, t, lane, waited);
+    for (int t = first; t < ntask; t += stride) phase_task<T, 1, 0, CPT, true>(views, segs, nbs, nseg, t, lane, waited);
     if (p + 1 < n_pairs && !grid_barrier(bar, target)) return;
   }
 }

@@ -58,11 +58,14 @@ __global__ void k_segment_flags(const LatticeView* __restrict__ views, const int
 }
 
 __global__ void k_segment_scatter(const LatticeView* __restrict__ views, const int* __restrict__ seg_word_off,
-                                  int n, int total, const int* __restrict__ flags,
+                                  int n, int total, int capacity, const int* __restrict__ flags,
                                   const int* __restrict__ offsets, SegRef* __restrict__ segs,
                                   int* __restrict__ n_segs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) *n_segs = offsets[total];
+  if (i == 0) {
+    n_segs[0] = offsets[total];
+    n_segs[1] = capacity;
+  }
   if (i >= total || !flags[i]) return;
   int l, y, w;
   seg_word(views, seg_word_off, n, i, l, y, w);
@@ -70,6 +73,36 @@ __global__ void k_segment_scatter(const LatticeView* __restrict__ views, const i
   r.lattice = l;
   r.yw = (y << kSegWordBits) | w;
   segs[offsets[i]] = r;
+}
+
+// Neighbour flags of every cell of the list's segments (one warp per entry,
+// lane l -> cell 32 w + l): the padded mask makes words w-1, w+1 of rows
+// y-1..y+1 exist and read as wall outside the lattice.  Next to a symmetry
+// plane, the padding row below row 0 holds row 0's image, and row-0 cells
+// are marked (their S neighbour is the plane).
+__global__ void k_segment_flags16(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
+                                  const int* __restrict__ n_segs, uint16_t* __restrict__ flags) {
+  const int lane = threadIdx.x & 31;
+  const int nseg = n_segs[0];
+  const int stride = (gridDim.x * blockDim.x) >> 5;
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nseg; t += stride) {
+    const SegRef sr = segs[t];
+    const LatticeView& L = views[sr.lattice];
+    const int y = sr.yw >> kSegWordBits, w = sr.yw & ((1 << kSegWordBits) - 1);
+    const int ms = mask_stride(L.wpr);
+    const uint32_t* mr = L.mask + (long long)y * ms;
+    const uint32_t* rn = mr + ms;
+    const uint32_t* rs = mr - ms;
+    const uint32_t mc = mr[w], mn = rn[w], msth = rs[w];
+    const uint32_t eC = __funnelshift_r(mc, mr[w + 1], 1), wC = __funnelshift_l(mr[w - 1], mc, 1);
+    const uint32_t eN = __funnelshift_r(mn, rn[w + 1], 1), wN = __funnelshift_l(rn[w - 1], mn, 1);
+    const uint32_t eS = __funnelshift_r(msth, rs[w + 1], 1), wS = __funnelshift_l(rs[w - 1], msth, 1);
+    unsigned nb = ((eC >> lane) & 1u) | (((mn >> lane) & 1u) << 1) | (((wC >> lane) & 1u) << 2) |
+                  (((msth >> lane) & 1u) << 3) | (((eN >> lane) & 1u) << 4) | (((wN >> lane) & 1u) << 5) |
+                  (((wS >> lane) & 1u) << 6) | (((eS >> lane) & 1u) << 7);
+    if (y == 0 && L.mirror) nb |= kNbS | kNbMirror;
+    flags[(long long)t * 32 + lane] = (uint16_t)nb;
+  }
 }
 
 // fluid cells per lattice over all words (rows 0..ny-1) of all lattices
@@ -225,7 +258,7 @@ size_t segment_scratch_ints(long long total_words) {
 }
 
 cudaError_t launch_build_segments(const LatticeView* views, const int* seg_word_off, int n_lattices,
-                                  int total, int* scratch, SegRef* segs, int* n_segs,
+                                  int total, int capacity, int* scratch, SegRef* segs, int* n_segs,
                                   cudaStream_t stream) {
   int* flags = scratch;
   int* offsets = scratch + total;      // total + 1
@@ -234,8 +267,12 @@ cudaError_t launch_build_segments(const LatticeView* views, const int* seg_word_
   count_launches(1);
   cudaError_t e = launch_scan(flags, offsets, total, tmp, stream);
   if (e != cudaSuccess) return e;
-  k_segment_scatter<<<blocks_for(total, 256), 256, 0, stream>>>(views, seg_word_off, n_lattices, total, flags,
-                                                                offsets, segs, n_segs);
+  k_segment_scatter<<<blocks_for(total, 256), 256, 0, stream>>>(views, seg_word_off, n_lattices, total, capacity,
+                                                                flags, offsets, segs, n_segs);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_segment_flags16<<<blocks_for((long long)total * 32, 256), 256, 0, stream>>>(
+      views, segs, n_segs, reinterpret_cast<uint16_t*>(segs + capacity));
   count_launches(1);
   return cudaGetLastError();
 }
