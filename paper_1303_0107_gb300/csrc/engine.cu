@@ -333,6 +333,14 @@ lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
   return LBM_OK;
 }
 
+// Block shapes the step kernels take: per-phase launches 4, 8, 16 or 32
+// warps per block with one cell per thread, 4, 8 or 24 with two; the
+// persistent kernel 8 or 16 (8 with two cells per thread).
+bool step_shape_allowed(int wpb, int cpt, int persistent) {
+  if (persistent) return wpb == 8 || (wpb == 16 && cpt == 1);
+  return cpt == 1 ? (wpb == 4 || wpb == 8 || wpb == 16 || wpb == 32) : (wpb == 4 || wpb == 8 || wpb == 24);
+}
+
 // Launch shape: every segment its own warp, but never more blocks than fit
 // on the device at once; a fixed-grid engine always takes the device-sized
 // grid, so its captured graphs outlive changes of the member list.
@@ -383,6 +391,14 @@ bool tune_cache_enabled() {
   return on;
 }
 
+bool tune_log_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("LBM_TUNE_LOG");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
 std::vector<long long> tune_key(const Engine* E) {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -424,10 +440,14 @@ lbm_status autotune(Engine* E) {
   // the builds with features (collision models, symmetry plane) have one
   // kernel shape: one cell per thread, register loads, one launch per phase
   const bool only_plain = E->features != 0;
+  // (one block per SM, the whole register budget: 32 warps with one cell
+  // per thread, 24 with two)
   for (int cpt : {1, 2})
-    for (int wpb : {4, 8, 16})
+    for (int wpb : {4, 8, 16, 24, 32})
       for (int scale : {1, 2, 4}) {
-        if (wpb * 32 > (cpt == 1 ? 512 : 256) || (cpt == 2 && scale == 4) || (only_plain && cpt == 2)) continue;
+        if (!step_shape_allowed(wpb, cpt, 0) || (cpt == 2 && scale == 4) || (only_plain && cpt == 2) ||
+            (wpb >= 24 && scale != 1))
+          continue;
         StepConfig c = shape(E, wpb, scale, cpt);
         bool dup = false;
         for (auto& d : cand)
@@ -451,7 +471,7 @@ lbm_status autotune(Engine* E) {
   // persistent candidates are one launch anyway.  One untimed pass, then
   // kTunePasses timed passes over all candidates (slow moments of the device
   // hit every candidate alike); a candidate's time is its fastest pass.
-  constexpr int kTunePasses = 3, kTunePairs = 32;
+  constexpr int kTunePasses = 5, kTunePairs = 64;
   std::vector<cudaGraphExec_t> tg(cand.size(), nullptr);
   lbm_status st = LBM_OK;
   for (size_t ci = 0; ci < cand.size() && st == LBM_OK; ++ci) {
@@ -503,8 +523,14 @@ lbm_status autotune(Engine* E) {
   // staged loads or one persistent launch must beat the fastest plain shape
   // (one cell per thread, register loads, per-phase launches) by kMargin:
   // near-ties are within the timing noise, and the plain shape is the one
-  // the profiles and the default use.
-  constexpr float kMargin = 0.97f;
+  // the profiles and the default use.  LBM_TUNE_LOG=1 prints every
+  // candidate's time to stderr.
+  constexpr float kMargin = 0.985f;
+  if (tune_log_enabled())
+    for (size_t ci = 0; ci < cand.size(); ++ci)
+      std::fprintf(stderr, "lbm tune: wpb %d grid %d cpt %d stages %d persistent %d: %.3f us per phase\n",
+                   cand[ci].warps_per_block, cand[ci].grid, cand[ci].cells_per_thread, cand[ci].stages,
+                   cand[ci].persistent, 1000.0 * t_min[ci] / (2 * kTunePairs));
   StepConfig best_cfg = cand[0], best_plain = cand[0];
   float best = 1e30f, best_p = 1e30f;
   for (size_t ci = 0; ci < cand.size(); ++ci) {
@@ -1183,13 +1209,14 @@ lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t pe
   if (stages != 0 && stages != 2 && stages != 3) return fail(LBM_ERR_ARG, "stages must be 0, 2 or 3");
   if (stages != 0 && (persistent || cells_per_thread != 1))
     return fail(LBM_ERR_ARG, "staged loads take one cell per thread and per-phase launches");
-  if (warps_per_block != 4 && warps_per_block != 8 && warps_per_block != 16)
-    return fail(LBM_ERR_ARG, "warps_per_block must be 4, 8 or 16");
   if (persistent != 0 && persistent != 1) return fail(LBM_ERR_ARG, "persistent must be 0 or 1");
   if (cells_per_thread != 1 && cells_per_thread != 2) return fail(LBM_ERR_ARG, "cells_per_thread must be 1 or 2");
-  if (cells_per_thread == 2 && warps_per_block == 16)
-    return fail(LBM_ERR_ARG, "two cells per thread take 4 or 8 warps per block");
-  if (persistent && warps_per_block == 4) return fail(LBM_ERR_ARG, "the persistent kernel takes 8 or 16 warps per block");
+  if (!step_shape_allowed(warps_per_block, cells_per_thread, persistent))
+    return fail(LBM_ERR_ARG,
+                persistent ? "the persistent kernel takes 8 or 16 warps per block (8 with two cells per thread)"
+                : cells_per_thread == 1 ? "one cell per thread takes 4, 8, 16 or 32 warps per block"
+                                        : "two cells per thread take 4, 8 or 24 warps per block");
+  if (stages != 0 && warps_per_block > 16) return fail(LBM_ERR_ARG, "staged loads take 4, 8 or 16 warps per block");
   if (E->features && (persistent || cells_per_thread != 1 || stages != 0))
     return fail(LBM_ERR_ARG, "lattices with collision models or a symmetry plane take the plain launch shape");
   StepConfig c = persistent ? persistent_shape(E, warps_per_block, cells_per_thread)

@@ -272,10 +272,14 @@ constexpr int kFeatModels = 1, kFeatMirror = 2;
 constexpr unsigned kE = kNbE, kN = kNbN, kW = kNbW, kS = kNbS, kNE = kNbNE, kNW = kNbNW, kSW = kNbSW,
                    kSE = kNbSE, kMirror = kNbMirror;
 
-// Threads per block at most, by cells per thread (the register budget per
-// thread is 64 with one cell, 80 with two).
-__host__ __device__ constexpr int max_step_threads(int cpt) { return cpt == 1 ? 512 : 256; }
-__host__ __device__ constexpr int min_step_blocks(int cpt) { return cpt == 1 ? 2 : 3; }
+// Threads per block at most, by cells per thread: the register budget per
+// thread is 64 with one cell (1024 threads per SM), 80 with two (768).  The
+// per-phase kernel may take the whole budget in one block (one block per SM
+// costs less to schedule at every launch than three or four smaller ones),
+// the persistent kernel in two or three.
+__host__ __device__ constexpr int max_step_threads(int cpt) { return cpt == 1 ? 1024 : 768; }
+__host__ __device__ constexpr int max_persistent_threads(int cpt) { return cpt == 1 ? 512 : 256; }
+__host__ __device__ constexpr int min_persistent_blocks(int cpt) { return cpt == 1 ? 2 : 3; }
 
 // What one lane knows about its cell of one row segment before touching
 // populations: everything here comes from the segment list, the lattice
@@ -508,7 +512,7 @@ __device__ __forceinline__ void phase_task(const LatticeView* __restrict__ views
 // each combination is a separate build, so that the plain kernels keep their
 // register budget and straight-line loads.
 template <class T, int PHASE, int MOM, int CPT, int FEAT>
-__global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
+__global__ void __launch_bounds__(max_step_threads(CPT), 1)
     k_stream_collide(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
                      const int* __restrict__ n_segs) {
   // The next time step may be scheduled now; it reads populations only after
@@ -708,7 +712,7 @@ __device__ bool grid_barrier(StepBarrier* b, unsigned& target) {
 // n_pairs (A, B) time-step pairs in one launch, a grid barrier after every
 // phase but the last.  Same per-cell arithmetic as k_stream_collide.
 template <class T, int CPT>
-__global__ void __launch_bounds__(max_step_threads(CPT), min_step_blocks(CPT))
+__global__ void __launch_bounds__(max_persistent_threads(CPT), min_persistent_blocks(CPT))
     k_stream_collide_persistent(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
                                 const int* __restrict__ n_segs, int n_pairs, StepBarrier* bar) {
   const int lane = threadIdx.x & 31;
@@ -795,7 +799,9 @@ void* persistent_kernel_for(int precision, int cpt) {
 
 bool shape_ok(const StepConfig& sc) {
   return (sc.cells_per_thread == 1 || sc.cells_per_thread == 2) && sc.warps_per_block >= 1 &&
-         sc.warps_per_block * 32 <= max_step_threads(sc.cells_per_thread) && sc.grid >= 1 &&
+         sc.warps_per_block * 32 <=
+             (sc.persistent ? max_persistent_threads : max_step_threads)(sc.cells_per_thread) &&
+         sc.grid >= 1 &&
          (sc.stages == 0 || ((sc.stages == 2 || sc.stages == 3) && sc.cells_per_thread == 1 && !sc.persistent)) &&
          (!sc.features || (sc.cells_per_thread == 1 && sc.stages == 0 && !sc.persistent));
 }
@@ -826,7 +832,7 @@ cudaError_t launch_stream_collide(int precision, int phase, int moments, const L
 int stream_collide_persistent_grid(int precision, int warps_per_block, int cells_per_thread) {
   void* k = persistent_kernel_for(precision, cells_per_thread);
   int dev = 0, sms = 0, n = 0;
-  if (!k || warps_per_block * 32 > max_step_threads(cells_per_thread) || cudaGetDevice(&dev) != cudaSuccess ||
+  if (!k || warps_per_block * 32 > max_persistent_threads(cells_per_thread) || cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, 0) != cudaSuccess)
     return 0;

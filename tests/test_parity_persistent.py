@@ -47,7 +47,7 @@ def _handle(case, precision, persistent, wpb=8, cpt=1, stages=0):
 
 # (persistent, warps per block, cells per thread, shared-memory stages)
 SHAPES = [(True, 8, 1, 0), (True, 8, 2, 0), (False, 8, 2, 0), (False, 4, 2, 0), (False, 8, 1, 3), (False, 4, 1, 2),
-          (False, 16, 1, 3), (False, 8, 1, 2)]
+          (False, 16, 1, 3), (False, 8, 1, 2), (False, 24, 2, 0), (False, 32, 1, 0)]
 
 
 @pytest.mark.parametrize("precision", [L.F32, L.BF16_SHIFTED, L.F16_SHIFTED])
@@ -139,8 +139,9 @@ def test_batch_shapes_equal_default_batch(shape):
 def test_set_step_config_errors():
     t = I.config_t_junction()
     h = L.Lattice(t["cells"], t["tau"], t["u_max"])
-    for wpb, pers, cpt, stg in ((3, 0, 1, 0), (32, 0, 1, 0), (4, 1, 1, 0), (8, 2, 1, 0), (8, 0, 3, 0), (16, 0, 2, 0),
-                                (8, 1, 0, 0), (8, 0, 1, 1), (8, 0, 1, 4), (8, 1, 1, 2), (8, 0, 2, 3)):
+    for wpb, pers, cpt, stg in ((3, 0, 1, 0), (64, 0, 1, 0), (24, 0, 1, 0), (32, 0, 2, 0), (4, 1, 1, 0), (8, 2, 1, 0),
+                                (8, 0, 3, 0), (16, 0, 2, 0), (24, 1, 2, 0), (32, 1, 1, 0), (32, 0, 1, 2), (8, 1, 0, 0),
+                                (8, 0, 1, 1), (8, 0, 1, 4), (8, 1, 1, 2), (8, 0, 2, 3)):
         with pytest.raises(L.LbmError) as e:
             h.set_step_config(wpb, persistent=pers, cells_per_thread=cpt, stages=stg)
         assert e.value.status == 1
