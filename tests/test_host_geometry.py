@@ -1,10 +1,10 @@
 """The C-ABI's geometry rules are host logic, checked before any device
 call: on random cell maps (valid distributors and mutated ones) the
-libraries' verdicts (LBM_ERR_GEOMETRY or not) must equal the oracles' rules
+libraries' answers (LBM_ERR_GEOMETRY or not) must equal the oracles' rules
 plus the rules the oracles leave to the caller (an inlet and an outlet cell,
 at most LBM_MAX_OUTLETS outlet runs or regions), computed here by brute
 force.  Runs without a GPU: a valid map then fails at the first device call
-(LBM_ERR_CUDA), which is not a geometry verdict."""
+(LBM_ERR_CUDA), which is not a geometry answer."""
 import ctypes
 
 import numpy as np
@@ -18,7 +18,7 @@ from paper_1303_0107_gb300 import lib, lib3d
 GEOMETRY = 2
 
 
-def _verdict2(cells, mirror=False):
+def _status2(cells, mirror=False):
     L = lib.load_library()
     ny, nx = cells.shape
     p = lib.make_params(nx, ny, 0.8, 0.05, mirror=mirror)
@@ -30,7 +30,7 @@ def _verdict2(cells, mirror=False):
     return st
 
 
-def _verdict3(cells, mirror=False):
+def _status3(cells, mirror=False):
     L = lib3d._lib()
     nz, ny, nx = cells.shape
     p = lib3d.make_params3(nx, ny, nz, 0.8, 0.05, mirror=mirror)
@@ -74,7 +74,7 @@ def _mutations2(base, rng):
     return out
 
 
-def test_2d_geometry_verdicts_match_the_rules():
+def test_2d_geometry_answers_match_the_rules():
     rng = np.random.default_rng(4)
     n_bad = 0
     for cand in I.config_candidates(6):
@@ -83,7 +83,7 @@ def test_2d_geometry_verdicts_match_the_rules():
             rule_bad = ora2.check_geometry(ora2.make_params(nx, ny, 0.8), c) != 0
             rule_bad |= (c[:, 0] == 0).sum() == 0 or (c[:, -1] == 0).sum() == 0
             rule_bad |= _runs(c[:, -1]) > lib.MAX_OUTLETS
-            st = _verdict2(c)
+            st = _status2(c)
             assert (st == GEOMETRY) == rule_bad, (st, rule_bad)
             n_bad += rule_bad
     assert n_bad > 10  # the mutations do break the rules
@@ -96,10 +96,10 @@ def test_2d_too_many_outlet_runs_and_the_mirror_row():
     c[2:-1:2, -8:] = 1  # 65 outlet runs separated by single walls
     assert _runs(c[:, -1]) == lib.MAX_OUTLETS + 1
     assert ora2.check_geometry(ora2.make_params(nx, ny, 0.8), c) == 0
-    assert _verdict2(c) == GEOMETRY
+    assert _status2(c) == GEOMETRY
     half = np.ones((12, 40), np.uint8)
     half[0:6, :] = 0  # row 0 fluid: valid next to a symmetry plane only
-    assert _verdict2(half) == GEOMETRY and _verdict2(half, mirror=True) != GEOMETRY
+    assert _status2(half) == GEOMETRY and _status2(half, mirror=True) != GEOMETRY
 
 
 def _mutations3(base, rng):
@@ -126,7 +126,7 @@ def _mutations3(base, rng):
     return out
 
 
-def test_3d_geometry_verdicts_match_the_rules():
+def test_3d_geometry_answers_match_the_rules():
     ndi = pytest.importorskip("scipy.ndimage")
     rng = np.random.default_rng(5)
     n_bad = 0
@@ -135,12 +135,12 @@ def test_3d_geometry_verdicts_match_the_rules():
             nz, ny, nx = c.shape
             rule_bad = o3.check_geometry3(o3.make_params3(nx, ny, nz, 0.8), c) != 0
             rule_bad |= ndi.label(c[:, :, -1] == 0)[1] > lib.MAX_OUTLETS
-            st = _verdict3(c)
+            st = _status3(c)
             assert (st == GEOMETRY) == rule_bad, (st, rule_bad)
             n_bad += rule_bad
     assert n_bad > 5
     half = np.ascontiguousarray(I.config_tree3d_small()["cells"][:, 17:, :])
-    assert _verdict3(half) == GEOMETRY and _verdict3(half, mirror=1) != GEOMETRY
+    assert _status3(half) == GEOMETRY and _status3(half, mirror=1) != GEOMETRY
     quarter = np.ascontiguousarray(I.config_tree3d_small()["cells"][17:, 17:, :])
-    assert _verdict3(quarter, mirror=1) == GEOMETRY and _verdict3(quarter, mirror=2) == GEOMETRY
-    assert _verdict3(quarter, mirror=3) != GEOMETRY
+    assert _status3(quarter, mirror=1) == GEOMETRY and _status3(quarter, mirror=2) == GEOMETRY
+    assert _status3(quarter, mirror=3) != GEOMETRY
