@@ -245,3 +245,53 @@ def test_failed_allocation_is_reported_and_recoverable():
     lat = L.Lattice(cfg["cells"], cfg["tau"], cfg["u_max"])
     assert np.isfinite(lat.solve(100)["dp"])
     lat.close()
+
+
+def test_largest_lattice_of_32bit_offsets(ora):
+    """The largest lattice the kernels' 32-bit element offsets allow: rows of
+    131072 cells (the widest row) and 1820 rows, so 9 * ny * pitch is just
+    below 2^31 (8.6 GB of FP32 populations).  A straight channel, 20 steps
+    from rest: nothing travels more than one cell per step, so the first 41
+    columns equal those of a 96-column channel of the same height (the
+    oracle), and every cell beyond them is still exactly at rest -- an
+    offset that wrapped would show in either."""
+    n, nx, height = 20, 131072, 1818
+    cells = I.channel(nx, height)
+    ny = cells.shape[0]
+    assert 9 * ny * nx < 2 ** 31 and 9 * (ny + 1) * nx >= 2 ** 31
+    lat = L.Lattice(cells, 0.8, 0.05, residual_every=0)
+    g = lat.solve(n)
+    small = I.channel(96, height)
+    s = ora.Solver(ora.make_params(96, ny, 0.8, 1.0, 0.05), small, residual_every=0)
+    s.solve(n)
+    k = 2 * n + 1
+    fields = {}
+    for name, fld in (("ux", L.FIELD_UX), ("uy", L.FIELD_UY), ("drho", L.FIELD_DRHO)):
+        a = lat.read(fld)
+        assert not np.any(a[:, k:]), name  # at rest: exactly zero
+        fields[name] = a[:, :k].astype(np.float64)
+    fluid = small[:, :k] == 0
+    assert _rel_inf(fields["ux"], s.ux[:, :k]) <= TOL_MAX
+    assert np.abs(fields["uy"] - s.uy[:, :k]).max() <= TOL_MAX * np.abs(s.ux).max()
+    assert _rel_inf(fields["drho"], (s.rho[:, :k] - 1.0) * fluid) <= TOL_MAX
+    assert g["fluid_cells"] == nx * height
+    lat.close()
+
+
+def test_exchange_of_no_cells_is_a_plain_continuation():
+    """n_swap = 0 (n = min(n_swap, ...) = 0): nothing moves, nothing is
+    re-initialised, and the solve that follows equals a plain solve bit for
+    bit."""
+    cfg = I.config_t_junction()
+    a = L.Lattice(cfg["cells"], cfg["tau"], cfg["u_max"])
+    b = L.Lattice(cfg["cells"], cfg["tau"], cfg["u_max"])
+    a.solve(400)
+    b.solve(400)
+    ra = a.optimize_step(0, 200)
+    rb = b.solve(200)
+    assert ra["n_swapped"] == 0 and ra["fluid_count"] == int((cfg["cells"] == 0).sum())
+    assert ra["dp"] == rb["dp"]
+    assert np.array_equal(a.read(L.FIELD_POPS), b.read(L.FIELD_POPS))
+    assert np.array_equal(a.read(L.FIELD_MASK), b.read(L.FIELD_MASK))
+    a.close()
+    b.close()
