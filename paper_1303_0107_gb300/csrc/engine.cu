@@ -101,7 +101,9 @@ size_t storage_bytes(int precision) { return precision == LBM_F32 ? 4 : 2; }
 
 namespace {
 
-constexpr int kGraphPairs[3] = {64, 8, 1};
+// Pairs per captured step graph: a programmatic launch overlaps its
+// predecessor only within one graph, so long solves run in few, large graphs.
+constexpr int kGraphPairs[4] = {512, 64, 8, 1};
 // Untuned launch shape: kStepWarps warps per block, the grid twice the blocks
 // resident at once (the tuner's usual choice; it leaves the tail of a step
 // to blocks that start as the first ones finish).
@@ -318,7 +320,7 @@ lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
     }
     return LBM_OK;
   }
-  for (int which = 0; which < 3 && pairs > 0; ++which) {
+  for (int which = 0; which < 4 && pairs > 0; ++which) {
     const int64_t chunk = kGraphPairs[which];
     const int64_t reps = pairs / chunk;
     if (reps == 0) continue;

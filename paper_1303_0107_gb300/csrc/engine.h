@@ -102,7 +102,7 @@ struct Engine {
   int* h_bar_error = nullptr;             // pinned: grid-barrier error flag of the last solve
   bool bar_used = false;                  // the last enqueued solve ran the persistent kernel
 
-  cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};  // 512, 64, 8 and 1 pairs
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};  // views, segs, n_segs, shape
   StepConfig step{kStepWarps, 1, 0, 1, 0, 0};
   int features = 0;  // kernel build the members need: 1 collision models, 2 symmetry plane
