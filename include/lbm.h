@@ -309,9 +309,9 @@ lbm_status lbm_kernel_time(lbm_handle h, int reset, double* ms, int64_t* launche
  * set with lbm_set_step_config.  Any output pointer may be NULL.          */
 lbm_status lbm_step_config(lbm_handle h, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
                            int32_t* cells_per_thread, int32_t* stages);
-/* Fix the launch shape (and skip tuning): warps_per_block 4, 8, 16 or 32
- * with one cell per thread, 4, 8 or 24 with two (32 and 24: one block per
- * SM); 8 or 16 when persistent (8 with two cells per thread); 4, 8 or 16
+/* Fix the launch shape (and skip tuning): warps_per_block 4, 8, 12, 16 or
+ * 32 with one cell per thread, 4, 8, 12 or 24 with two (32 and 24: one
+ * block per SM); 8 or 16 when persistent (8 with two cells per thread); 4, 8 or 16
  * with stages.  cells_per_thread 1 or 2, stages 0, 2 or 3 (staged loads:
  * one cell per thread, not persistent); the grid is sized for the device.  Every shape computes the
  * same values, so this changes timings only.                              */

@@ -335,12 +335,13 @@ lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
   return LBM_OK;
 }
 
-// Block shapes the step kernels take: per-phase launches 4, 8, 16 or 32
-// warps per block with one cell per thread, 4, 8 or 24 with two; the
+// Block shapes the step kernels take: per-phase launches 4, 8, 12, 16 or 32
+// warps per block with one cell per thread, 4, 8, 12 or 24 with two; the
 // persistent kernel 8 or 16 (8 with two cells per thread).
 bool step_shape_allowed(int wpb, int cpt, int persistent) {
   if (persistent) return wpb == 8 || (wpb == 16 && cpt == 1);
-  return cpt == 1 ? (wpb == 4 || wpb == 8 || wpb == 16 || wpb == 32) : (wpb == 4 || wpb == 8 || wpb == 24);
+  return cpt == 1 ? (wpb == 4 || wpb == 8 || wpb == 12 || wpb == 16 || wpb == 32)
+                  : (wpb == 4 || wpb == 8 || wpb == 12 || wpb == 24);
 }
 
 // Launch shape: every segment its own warp, but never more blocks than fit
@@ -445,7 +446,7 @@ lbm_status autotune(Engine* E) {
   // (one block per SM, the whole register budget: 32 warps with one cell
   // per thread, 24 with two)
   for (int cpt : {1, 2})
-    for (int wpb : {4, 8, 16, 24, 32})
+    for (int wpb : {4, 8, 12, 16, 24, 32})
       for (int scale : {1, 2, 4}) {
         if (!step_shape_allowed(wpb, cpt, 0) || (cpt == 2 && scale == 4) || (only_plain && cpt == 2) ||
             (wpb >= 24 && scale != 1))
@@ -1216,8 +1217,8 @@ lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t pe
   if (!step_shape_allowed(warps_per_block, cells_per_thread, persistent))
     return fail(LBM_ERR_ARG,
                 persistent ? "the persistent kernel takes 8 or 16 warps per block (8 with two cells per thread)"
-                : cells_per_thread == 1 ? "one cell per thread takes 4, 8, 16 or 32 warps per block"
-                                        : "two cells per thread take 4, 8 or 24 warps per block");
+                : cells_per_thread == 1 ? "one cell per thread takes 4, 8, 12, 16 or 32 warps per block"
+                                        : "two cells per thread take 4, 8, 12 or 24 warps per block");
   if (stages != 0 && warps_per_block > 16) return fail(LBM_ERR_ARG, "staged loads take 4, 8 or 16 warps per block");
   if (E->features && (persistent || cells_per_thread != 1 || stages != 0))
     return fail(LBM_ERR_ARG, "lattices with collision models or a symmetry plane take the plain launch shape");

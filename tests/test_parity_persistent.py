@@ -47,7 +47,7 @@ def _handle(case, precision, persistent, wpb=8, cpt=1, stages=0):
 
 # (persistent, warps per block, cells per thread, shared-memory stages)
 SHAPES = [(True, 8, 1, 0), (True, 8, 2, 0), (False, 8, 2, 0), (False, 4, 2, 0), (False, 8, 1, 3), (False, 4, 1, 2),
-          (False, 16, 1, 3), (False, 8, 1, 2), (False, 24, 2, 0), (False, 32, 1, 0)]
+          (False, 16, 1, 3), (False, 8, 1, 2), (False, 24, 2, 0), (False, 32, 1, 0), (False, 12, 2, 0), (False, 12, 1, 0)]
 
 
 @pytest.mark.parametrize("precision", [L.F32, L.BF16_SHIFTED, L.F16_SHIFTED])
