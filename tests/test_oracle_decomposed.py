@@ -6,7 +6,6 @@ import multiprocessing as mp
 import socket
 
 import numpy as np
-import pytest
 
 from paper_1303_0107_gb300 import inputs as I
 

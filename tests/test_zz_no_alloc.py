@@ -10,7 +10,6 @@ anything left over in the shared array from the first call would show), and
 its picks must equal those of lbm_select_swaps bit for bit.  This file is
 named to be collected last.
 """
-import ctypes
 
 import numpy as np
 import pytest
