@@ -655,8 +655,8 @@ __global__ void __launch_bounds__(512, 2)
   uint32_t* wbuf = stage_smem + (size_t)warp * NS * kStageWords;
   // populations of the previous step are final from here on
   asm volatile("griddepcontrol.wait;" ::: "memory");
-#pragma unroll
   const uint16_t* nbs = segment_flags(segs, n_segs);
+#pragma unroll
   for (int k = 0; k < NS - 1; ++k)
     stage_issue<T, PHASE>(views, segs, nbs, nseg, first + k * stride, lane, wbuf + k * kStageWords);
   for (int k = 0; first + k * stride < nseg; ++k) {
