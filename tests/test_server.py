@@ -198,3 +198,31 @@ def test_failed_allocation_fails_only_its_request():
     assert done[reqs[0]["tag"]]["status"] == 3  # LBM_ERR_OOM
     assert [done[q["tag"]]["status"] for q in reqs[1:]] == [0, 0]
     assert st["failed"] == 1 and st["resident_bytes"] == 0
+
+
+def test_a_diverging_request_fails_alone():
+    """A request that blows up (BGK at tau = 0.51 past a block: non-finite
+    density within 4000 steps) is reported LBM_ERR_DIVERGED; the requests
+    stepped in the same launches beside it finish as they would alone, bit
+    for bit."""
+    cells = np.ones((60, 200), np.uint8)
+    cells[1:-1, :] = 0
+    cells[22:38, 50:56] = 1
+    reqs = _requests(3, 700, n_steps=300)
+    srv = L.Server(precision=L.F32, max_active=8, max_tick_steps=500)
+    srv.submit(99, cells, 0.51, 0.05, 4000)
+    for q in reqs:
+        srv.submit(q["tag"], q["cells"], q["tau"], q["u_max"], q["n_steps"], n_iter=q["n_iter"],
+                   n_swap=q["n_swap"])
+    srv.wait_idle(300)
+    done = {d["tag"]: d for d in srv.poll(64)}
+    st = srv.stats()
+    srv.close()
+    assert done[99]["status"] == 5  # LBM_ERR_DIVERGED
+    assert st["failed"] == 1 and st["completed"] == len(reqs)
+    for q in reqs:
+        d = done[q["tag"]]
+        assert d["status"] == 0, d
+        first, last, swapped, _ = _alone(q, L.F32)
+        assert d["dp_first"] == first["dp"] and d["last"]["dp"] == last["dp"], q["tag"]
+        assert d["n_swapped"] == swapped
