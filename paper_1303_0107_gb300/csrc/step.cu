@@ -486,13 +486,14 @@ __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
 template <class T, int PHASE, int MOM, int CPT, bool CG, int FEAT = 0>
 __device__ __forceinline__ void phase_task(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
                                            const uint16_t* __restrict__ nbs, int nseg, int task, int lane,
-                                           bool& waited) {
+                                           bool& waited, const SegRef* pre = nullptr) {
   SegCtx<T> s[CPT];
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
     const int idx = task * CPT + k;
     const bool valid = CPT == 1 || idx < nseg;  // one segment per task: task < nseg already
-    seg_prologue<T, PHASE, FEAT>(views, segs[valid ? idx : 0], valid, lane, s[k], nbs, valid ? idx : 0);
+    seg_prologue<T, PHASE, FEAT>(views, (CPT == 1 && pre) ? *pre : segs[valid ? idx : 0], valid, lane, s[k], nbs,
+                                 valid ? idx : 0);
   }
   if (!waited) {  // warp-uniform: populations of the previous step are final from here on
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -525,8 +526,20 @@ __global__ void __launch_bounds__(max_step_threads(CPT), 1)
   const int wpb = blockDim.x >> 5;
   const int stride = gridDim.x * wpb;
   bool waited = false;
-  for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntask; t += stride)
-    phase_task<T, PHASE, MOM, CPT, false, FEAT>(views, segs, nbs, nseg, t, lane, waited);
+  if (CPT == 1) {
+    // one segment per task: the next task's list entry is loaded while this
+    // task's populations are in flight
+    int t = blockIdx.x * wpb + (threadIdx.x >> 5);
+    SegRef nxt = t < ntask ? segs[t] : SegRef{0, 0};
+    for (; t < ntask; t += stride) {
+      const SegRef cur = nxt;
+      if (t + stride < ntask) nxt = segs[t + stride];
+      phase_task<T, PHASE, MOM, CPT, false, FEAT>(views, segs, nbs, nseg, t, lane, waited, &cur);
+    }
+  } else {
+    for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntask; t += stride)
+      phase_task<T, PHASE, MOM, CPT, false, FEAT>(views, segs, nbs, nseg, t, lane, waited);
+  }
   // every thread waits once, so this grid completes only after the previous
   // one (the next step relies on that)
   if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
