@@ -333,6 +333,10 @@ class Lattice:
         return tuple(x.value for x in v)
 
     def set_step_config(self, warps_per_block, persistent=False, cells_per_thread=1, stages=0):
+        """Fix the launch shape instead of tuning it (lbm_set_step_config): warps per block 4, 8, 12,
+        16 or 32 with one cell per thread, 4, 8, 12 or 24 with two; persistent 8 or 16 (8 with two
+        cells); stages 0 (register loads) or 2 / 3 (shared-memory staging, one cell per thread, 4-16
+        warps).  Every shape computes the same values; LbmError (status 1) for any other shape."""
         _check(load_library().lbm_set_step_config(self._h, int(warps_per_block), int(persistent),
                                                   int(cells_per_thread), int(stages)), "lbm_set_step_config")
 
@@ -432,11 +436,13 @@ class Batch:
         return ms.value, n.value, u.value
 
     def step_config(self):
+        """(warps per block, blocks, persistent, cells per thread, stages) of the batch's launches."""
         v = [ctypes.c_int32() for _ in range(5)]
         _check(load_library().lbm_batch_step_config(self._b, *[ctypes.byref(x) for x in v]), "lbm_batch_step_config")
         return tuple(x.value for x in v)
 
     def set_step_config(self, warps_per_block, persistent=False, cells_per_thread=1, stages=0):
+        """As Lattice.set_step_config, for every lattice of the batch."""
         _check(load_library().lbm_batch_set_step_config(self._b, int(warps_per_block), int(persistent),
                                                         int(cells_per_thread), int(stages)),
                "lbm_batch_set_step_config")
