@@ -437,7 +437,10 @@ lbm_status autotune(Engine* E) {
       cudaGetLastError();
       return LBM_OK;
     }
-    CU(cudaMemcpyAsync(backups[i], E->m[i]->f, bytes, cudaMemcpyDeviceToDevice, E->stream));
+    if (cudaMemcpyAsync(backups[i], E->m[i]->f, bytes, cudaMemcpyDeviceToDevice, E->stream) != cudaSuccess) {
+      for (void* b : backups) cudaFree(b);
+      return fail(LBM_ERR_CUDA, "autotune: saving the populations");
+    }
   }
   std::vector<StepConfig> cand;
   // the builds with features (collision models, symmetry plane) have one
