@@ -639,8 +639,9 @@ def run_reference(args, world, rank):
     S, iters = args.lattice_steps, args.iters
     # the GPU arm's config (the same workload); the oracle times a bounded sample of it
     config = {"workload": cfg["name"] + f"_{args.precision}_{iters + 1}x{S}", "nx": cfg["nx"], "ny": cfg["ny"],
-              "fluid_cells": fluid, "n_swap": max(1, fluid // 500), "solves_per_step": iters + 1,
-              "time_steps_per_solve": S, "parallelism": "replicas x1 (rank 0 only)"}
+              "fluid_cells": fluid, "n_swap": max(1, int(0.002 * fluid)), "solves_per_step": iters + 1,
+              "time_steps_per_solve": S, "l2": "flushed between timed steps (256 MB write)",
+              "parallelism": f"replicas x{args.gpus}"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -687,10 +688,11 @@ def main():
     def one_run(handle):
         handle.reset()
         r = handle.solve(S)
-        dp0 = r["dp"]
+        hist = [r]
         for _ in range(iters):
             r = handle.optimize_step(n_swap, S)
-        return dp0, r
+            hist.append(r)
+        return hist
 
     for _ in range(args.warmup):
         one_run(lat)
@@ -737,11 +739,16 @@ def main():
                 "avg_launch_us": avg_launch_s * 1e6,
                 "note": "lattice working set (fluid cells) is L2-resident within a solve"}
 
-    # end to end through the public API: pinned host cell map in, cell map out
+    # end to end through the public API, as many runs as timed steps: pinned
+    # host cell map in, the whole optimisation run, the cell map back out.
+    # The bytes crossing are the library's own count of its host <-> device
+    # copies (uploads of the cell map and tables, result blocks, exchange
+    # counters, the final read).
     cells_pin = torch.from_numpy(cells).pin_memory()
     mask_out = torch.empty(cells.shape, dtype=torch.uint8).pin_memory()
     e2e_times = []
-    for _ in range(max(1, min(args.steps, 3))):
+    x0 = L.transfer_bytes()
+    for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = L.Lattice(cells_pin.numpy(), cfg["tau"], cfg["u_max"], precision=prec, residual_every=100,
@@ -752,18 +759,13 @@ def main():
         h.read(L.FIELD_MASK, out=mask_out.numpy())
         h.close()
         e2e_times.append(time.perf_counter() - t0)
+    x1 = L.transfer_bytes()
     e2e_s = sum(e2e_times) / len(e2e_times)
     e2e_s = max_over_ranks(e2e_s, dist, "cuda")
-    sz = ctypes_sizes()
-    # host -> device: the cell map, the per-row inlet speeds and the outlet
-    # table the library derives from it, the lattice descriptor and the set
-    # offsets, and n_swap of every iteration
-    h2d = cells.nbytes + 4 * cells.shape[0] + 8 * L.lib.MAX_OUTLETS + sz["view"] + 16 + 4 * iters
-    # device -> host: the reduction block of every solve, the exchange counters
-    # and fluid count of every iteration and of creation, and the final cell map
-    d2h = cells.nbytes + (iters + 1) * sz["result_block"] + iters * (32 + 8) + 8
-    e2e = {"value": replica_value(updates_per_step, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
+    e2e = {"value": replica_value(updates_per_step, world, e2e_s), "unit": UNIT,
+           "h2d_bytes_per_step": (x1[0] - x0[0]) // args.steps, "d2h_bytes_per_step": (x1[1] - x0[1]) // args.steps,
+           "ms_per_step": 1e3 * e2e_s, "runs": args.steps,
+           "bytes_source": "library transfer counters (lbm_transfer_bytes)"}
 
     extras = {}
     legs = set() if args.no_extras else set(x for x in args.legs.split(",") if x)
@@ -808,7 +810,14 @@ def main():
                "sample": f"{cfg['name']}: {n} FP64 time steps from rest, {dt:.1f} s"}
 
     if rank == 0:
-        dp0, r_last = last
+        dp_hist = [r["dp"] for r in last]
+        r_last = last[-1]
+        best_iter = min(range(len(dp_hist)), key=lambda k: dp_hist[k])
+        summary = {"summary": "per-leg rates (the full records are in the main line's extras)",
+                   "headline_glups": value, "headline_roofline_frac": roofline["frac"],
+                   "e2e_glups": e2e["value"]}
+        summary.update(leg_summary(extras))
+        print(json.dumps(summary))
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == L.F32 else args.precision,
@@ -817,14 +826,16 @@ def main():
                            "ny": cfg["ny"], "fluid_cells": fluid, "n_swap": n_swap,
                            "solves_per_step": iters + 1, "time_steps_per_solve": S,
                            "l2": "flushed between timed steps (256 MB write)",
-                           "parallelism": f"replicas x{world}",
-                           "step_config": dict(zip(("warps_per_block", "grid", "persistent", "cells_per_thread",
-                                                    "stages"), lat.step_config()))},
+                           "parallelism": f"replicas x{world}"},
+                "step_config": dict(zip(("warps_per_block", "grid", "persistent", "cells_per_thread", "stages"),
+                                        lat.step_config())),
                 "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
                 "cpu_baseline": cpu,
                 "dense_glups": cfg["nx"] * cfg["ny"] * S * (iters + 1) * args.steps * world / total_s / 1e9,
-                "dp_initial": dp0, "dp_final": r_last["dp"], "theta_final": r_last["theta"],
-                "dg_final": r_last["dg"], "extras": extras}
+                "dp_initial": dp_hist[0], "dp_best": dp_hist[best_iter], "best_iter": best_iter,
+                "dp_final": r_last["dp"], "theta_initial": last[0]["theta"], "theta_final": r_last["theta"],
+                "dg_initial": last[0]["dg"], "dg_final": r_last["dg"],
+                "dp_history": dp_hist, "theta_history": [r["theta"] for r in last], "extras": extras}
         print(json.dumps(line))
     lat.close()
     if dist is not None:
@@ -832,11 +843,34 @@ def main():
     return 0
 
 
-def ctypes_sizes():
-    import ctypes
-    from paper_1303_0107_gb300 import lib
-    return {"params": ctypes.sizeof(lib.Params), "solve_result": ctypes.sizeof(lib.SolveResult),
-            "opt_result": ctypes.sizeof(lib.OptResult), "view": 160, "result_block": 8 * (10 + lib.MAX_OUTLETS)}
+def leg_summary(extras):
+    """Compact rates of every leg that ran, for a short line ahead of the main one."""
+    out = {}
+
+    def put(key, d, field):
+        if isinstance(d, dict) and d.get(field) is not None:
+            out[key] = d[field]
+
+    for p in ("f32", "bf16"):
+        put(f"large_{p}_glups", extras.get(f"large_8192x4096_{p}"), "glups")
+        put(f"large_{p}_frac", extras.get(f"large_8192x4096_{p}"), "frac_of_measured_hbm")
+        put(f"batched_{p}_glups", extras.get(f"batched_256_{p}"), "batched_glups")
+        put(f"batched_{p}_step_glups", extras.get(f"batched_256_{p}"), "batched_step_glups")
+        put(f"batched_{p}_speedup", extras.get(f"batched_256_{p}"), "speedup")
+    prec = extras.get("precision_tree_2048", {})
+    for p in ("bf16", "f16"):
+        put(f"tree_{p}_vs_f32", prec.get(p), "glups_vs_f32")
+        put(f"tree_{p}_dp_rel_err", prec.get(p), "dp_rel_err")
+    d3 = extras.get("d3q19", {})
+    for k in ("tree3d_384x192x192_f32", "tree3d_384x192x192_bf16", "duct3d_256x128x128_f32"):
+        put(f"{k}_glups", d3.get(k), "glups")
+        put(f"{k}_frac", d3.get(k), "frac_of_measured_hbm")
+    srv = extras.get("served_f32", {})
+    for k in ("p50_ms", "p99_ms", "aggregate_glups", "served_vs_alone_dp_rel_diff_max"):
+        put(f"served_{k}", srv, k)
+    put("tjunction_glups", extras.get("t_junction_128x64"), "glups")
+    put("collector_glups", extras.get("collector_half_360x180"), "glups")
+    return out
 
 
 if __name__ == "__main__":

@@ -20,8 +20,11 @@
  *     column nx-1; each fluid cell (0,y) has a fluid (1,y) and each fluid
  *     (nx-1,y) a fluid (nx-2,y);
  *   - at least one inlet and one outlet cell, at most LBM_MAX_OUTLETS outlet
- *     runs; nx even, 4 <= nx <= 131072, 3 <= ny < 524288, and
- *     9 * ny * pitch < 2^31 with pitch = nx rounded up to 64 (LBM_ERR_ARG).
+ *     runs; 4 <= nx <= 131072, 3 <= ny < 524288, and 9 * ny * pitch < 2^31
+ *     with pitch = nx rounded up to 64; with the zero-gradient outlet
+ *     (LBM_OUT_NEUMANN) nx mod 32 != 1, because the outlet cell takes the
+ *     streamed populations of cell nx-2 from the neighbouring lane of its
+ *     32-cell row segment (LBM_ERR_ARG).
  * The optimiser never changes columns 0, 1, nx-2, nx-1 nor rows 0, ny-1.
  *
  * Threading: a handle is used by one host thread at a time.  All device work
@@ -250,11 +253,18 @@ lbm_status lbm_optimize(lbm_handle h, const lbm_opt_plan* plan, double* dp_histo
  *                ascending; n_out: device int32, receives n, or -1 if a score
  *                is not a number;
  *   cuda_stream  stream to enqueue on (NULL: the legacy default stream).
- * The call only enqueues work and returns; results are valid once that work
+ * The selection is that of lbm_select_swaps on a handle created with
+ * guard = 0: the connectivity guard of lbm_params.guard is not applied.
+ * The call only enqueues kernels and a memset on the stream (it copies
+ * nothing from host memory) and returns; results are valid once that work
  * has completed on the stream.  All intermediate storage is one static
  * device array of about 7.4 MB that every GPU loading the library keeps
- * until the process exits; the first call with a given device current looks
- * up its address there (make that first call before any stream capture).
+ * until the process exits; every call looks up its device address with
+ * cudaGetSymbolAddress.  The first call on each device is also where CUDA
+ * loads the library's device code for that device (module loading is lazy
+ * by default), which commits the array and the selection kernels in device
+ * memory: make that first call before any stream capture, and before the
+ * application reserves the device's memory for its own pool.
  * All calls share the array and it keeps the previous call's contents, so
  * calls whose work overlaps on the GPU (different streams, no ordering)
  * corrupt each other; calls on one stream are ordered and safe.  Errors
@@ -290,6 +300,13 @@ void lbm_debug_barrier_timeout(int32_t on);
 /* Number of device kernels this process has launched through the library
  * (graph launches count every kernel node).                             */
 uint64_t lbm_kernel_launches(void);
+
+/* Bytes the library has copied from host to device memory (*h2d) and from
+ * device to host memory (*d2h) in this process through the lbm_* and
+ * lbm_batch_* entry points (uploads of cell maps and tables, result blocks,
+ * exchange counters, field reads): the transfer cost of a run, for its
+ * end-to-end accounting.  Either pointer may be NULL.                     */
+void lbm_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
 
 /* Device time of the stream-collide kernels of this handle, measured with CUDA
  * events on the handle's stream around each solve's sequence of time steps

@@ -11,6 +11,7 @@ from . import inputs  # noqa: F401
 from .lib import (F32, BF16_SHIFTED, F16_SHIFTED, OUT_CONST_RHO, OUT_NEUMANN, REINIT_WARM,  # noqa: F401
                   PORTS_REGULARIZED, PORTS_ZOU_HE, COLLIDE_BGK, COLLIDE_REGULARIZED, COLLIDE_SMAGORINSKY,
                   REINIT_COLD, FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_MASK, FIELD_POPS, FIELD_DRHO,
-                  Lattice, Batch, Server, LbmError, bytes_per_fluid_update, kernel_launches, load_library)
+                  Lattice, Batch, Server, LbmError, bytes_per_fluid_update, kernel_launches, load_library,
+                  transfer_bytes)
 from .lib3d import (Lattice3, FIELD3_DRHO, FIELD3_UX, FIELD3_UY, FIELD3_UZ, FIELD3_MASK,  # noqa: F401
                     FIELD3_POPS)

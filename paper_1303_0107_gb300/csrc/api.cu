@@ -47,6 +47,8 @@ const char* lbm_last_error(void) { return t_last_error.c_str(); }
 
 uint64_t lbm_kernel_launches(void) { return launches_total(); }
 
+void lbm_transfer_bytes(uint64_t* h2d, uint64_t* d2h) { transfer_bytes(h2d, d2h); }
+
 void lbm_debug_fail_alloc(int64_t after) { set_alloc_failure(after); }
 
 void lbm_debug_barrier_timeout(int32_t on) { set_barrier_timeout_test(on); }
@@ -111,7 +113,7 @@ lbm_status lbm_load_state(lbm_handle h, const void* pops, size_t bytes, int src_
   const size_t sb = storage_bytes(E->precision);
   if (bytes < 9 * ncell * sb) return fail(LBM_ERR_ARG, "pops too small");
   for (int i = 0; i < 9; ++i)
-    CU(cudaMemcpy2DAsync(static_cast<char*>(m->f) + i * m->plane * sb, (size_t)m->pitch * sb,
+    CU(xfer2d(static_cast<char*>(m->f) + i * m->plane * sb, (size_t)m->pitch * sb,
                          static_cast<const char*>(pops) + i * ncell * sb, nx * sb, nx * sb, ny,
                          cudaMemcpyDefault, E->stream));
   CU(cudaStreamSynchronize(E->stream));
@@ -165,20 +167,20 @@ lbm_status lbm_select_swaps(lbm_handle h, const float* drho, const float* ux, co
   step(cudaMemsetAsync(tmp, 0, 3 * m->plane * sizeof(float), E->stream), "memset");
   const float* srcs[3] = {drho, ux, uy};
   for (int k = 0; k < 3; ++k)
-    step(cudaMemcpy2DAsync(tmp + k * m->plane, (size_t)m->pitch * 4, srcs[k], nx * 4, nx * 4, ny,
+    step(xfer2d(tmp + k * m->plane, (size_t)m->pitch * 4, srcs[k], nx * 4, nx * 4, ny,
                            cudaMemcpyDefault, E->stream), "copy field");
-  step(cudaMemcpyAsync(vdev, &v, sizeof(v), cudaMemcpyHostToDevice, E->stream), "view");
+  step(xfer(vdev, &v, sizeof(v), cudaMemcpyHostToDevice, E->stream), "view");
   E->h_nswap[0] = n_swap;
-  step(cudaMemcpyAsync(E->n_swap_dev.p, E->h_nswap, sizeof(int), cudaMemcpyHostToDevice, E->stream), "n_swap");
+  step(xfer(E->n_swap_dev.p, E->h_nswap, sizeof(int), cudaMemcpyHostToDevice, E->stream), "n_swap");
   // one lattice: E->word_off is {0, words}
   step(launch_oc_select(vdev, static_cast<const int*>(E->L.word_off.p), 1, E->L.total_words,
                                 static_cast<const int*>(E->n_swap_dev.p), E->oc, E->stream), "select");
-  step(cudaMemcpyAsync(E->h_info, E->oc.info, 8 * sizeof(int), cudaMemcpyDeviceToHost, E->stream), "info");
+  step(xfer(E->h_info, E->oc.info, 8 * sizeof(int), cudaMemcpyDeviceToHost, E->stream), "info");
   step(cudaStreamSynchronize(E->stream), "sync");
   const int n = st == LBM_OK ? E->h_info[0] : 0;
   if (st == LBM_OK && n > 0) {
-    step(cudaMemcpyAsync(fluid_idx_out, E->oc.sel_f, n * sizeof(int), cudaMemcpyDefault, E->stream), "out");
-    step(cudaMemcpyAsync(solid_idx_out, E->oc.sel_s, n * sizeof(int), cudaMemcpyDefault, E->stream), "out");
+    step(xfer(fluid_idx_out, E->oc.sel_f, n * sizeof(int), cudaMemcpyDefault, E->stream), "out");
+    step(xfer(solid_idx_out, E->oc.sel_s, n * sizeof(int), cudaMemcpyDefault, E->stream), "out");
     step(cudaStreamSynchronize(E->stream), "sync");
   }
   cudaFree(tmp);

@@ -27,6 +27,48 @@ void count_launches(uint64_t n) {
 }
 uint64_t launches_total() { return g_launches.load(); }
 
+static std::atomic<uint64_t> g_h2d{0}, g_d2h{0};
+
+namespace {
+bool is_host_memory(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+void count_transfer(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  bool from_host = kind == cudaMemcpyHostToDevice || kind == cudaMemcpyHostToHost;
+  bool to_host = kind == cudaMemcpyDeviceToHost || kind == cudaMemcpyHostToHost;
+  if (kind == cudaMemcpyDefault) {
+    from_host = is_host_memory(src);
+    to_host = is_host_memory(dst);
+  }
+  if (from_host && !to_host) g_h2d.fetch_add(bytes, std::memory_order_relaxed);
+  if (to_host && !from_host) g_d2h.fetch_add(bytes, std::memory_order_relaxed);
+}
+}  // namespace
+
+cudaError_t xfer(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t stream) {
+  const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, stream);
+  if (e == cudaSuccess && kind != cudaMemcpyDeviceToDevice) count_transfer(dst, src, bytes, kind);
+  return e;
+}
+
+cudaError_t xfer2d(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t height,
+                   cudaMemcpyKind kind, cudaStream_t stream) {
+  const cudaError_t e = cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, kind, stream);
+  if (e == cudaSuccess && kind != cudaMemcpyDeviceToDevice) count_transfer(dst, src, width * height, kind);
+  return e;
+}
+
+void transfer_bytes(uint64_t* h2d, uint64_t* d2h) {
+  if (h2d) *h2d = g_h2d.load();
+  if (d2h) *d2h = g_d2h.load();
+}
+
 void set_last_error(const std::string& msg) { t_last_error = msg; }
 
 bool debug_sync() {
@@ -210,9 +252,9 @@ lbm_status layout_build(SetLayout& S, const std::vector<Member*>& ms, cudaStream
   CU(S.word_off.reserve(sizeof(int) * (n + 1)));
   CU(S.seg_word_off.reserve(sizeof(int) * (n + 1)));
   if (n > 0)
-    CU(cudaMemcpyAsync(S.views.p, S.h_views.data(), sizeof(LatticeView) * n, cudaMemcpyHostToDevice, stream));
-  CU(cudaMemcpyAsync(S.word_off.p, S.h_woff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, stream));
-  CU(cudaMemcpyAsync(S.seg_word_off.p, S.h_swoff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, stream));
+    CU(xfer(S.views.p, S.h_views.data(), sizeof(LatticeView) * n, cudaMemcpyHostToDevice, stream));
+  CU(xfer(S.word_off.p, S.h_woff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, stream));
+  CU(xfer(S.seg_word_off.p, S.h_swoff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, stream));
   return LBM_OK;
 }
 
@@ -437,7 +479,7 @@ lbm_status autotune(Engine* E) {
       cudaGetLastError();
       return LBM_OK;
     }
-    if (cudaMemcpyAsync(backups[i], E->m[i]->f, bytes, cudaMemcpyDeviceToDevice, E->stream) != cudaSuccess) {
+    if (xfer(backups[i], E->m[i]->f, bytes, cudaMemcpyDeviceToDevice, E->stream) != cudaSuccess) {
       for (void* b : backups) cudaFree(b);
       return fail(LBM_ERR_CUDA, "autotune: saving the populations");
     }
@@ -555,7 +597,7 @@ lbm_status autotune(Engine* E) {
   cudaEventDestroy(b);
   E->bar_used = false;
   for (int i = 0; i < n; ++i)
-    cudaMemcpyAsync(E->m[i]->f, backups[i], 9 * E->m[i]->plane * sb, cudaMemcpyDeviceToDevice, E->stream);
+    xfer(E->m[i]->f, backups[i], 9 * E->m[i]->plane * sb, cudaMemcpyDeviceToDevice, E->stream);
   cudaStreamSynchronize(E->stream);
   for (void* q : backups) cudaFree(q);
   E->step = best_cfg;
@@ -601,9 +643,13 @@ Member::~Member() {
 size_t member_footprint(const lbm_params& p) { return plan_slab(p).total; }
 
 lbm_status check_params(const lbm_params& p) {
-  if (p.nx < 4 || p.ny < 3 || (p.nx % 2) != 0 || (int64_t)p.nx * p.ny >= (int64_t)1 << 31 ||
-      p.nx > (32 << kSegWordBits) || p.ny >= (1 << (31 - kSegWordBits)))
-    return fail(LBM_ERR_ARG, "nx must be even, 4 <= nx <= 131072, 3 <= ny < 524288, nx*ny < 2^31");
+  if (p.nx < 4 || p.ny < 3 || (int64_t)p.nx * p.ny >= (int64_t)1 << 31 || p.nx > (32 << kSegWordBits) ||
+      p.ny >= (1 << (31 - kSegWordBits)))
+    return fail(LBM_ERR_ARG, "need 4 <= nx <= 131072, 3 <= ny < 524288, nx*ny < 2^31");
+  // the zero-gradient outlet cell takes the streamed populations of cell
+  // nx-2 from the lane to its left: both must lie in one 32-cell segment
+  if (p.outlet == LBM_OUT_NEUMANN && (p.nx & 31) == 1)
+    return fail(LBM_ERR_ARG, "with the zero-gradient outlet, nx mod 32 must not be 1");
   const size_t pitch = (size_t)(p.nx + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
   if (9 * pitch * (size_t)p.ny >= ((size_t)1 << 31))
     return fail(LBM_ERR_ARG, "lattice too large: 9 * ny * pitch must stay below 2^31 elements");
@@ -685,13 +731,13 @@ lbm_status member_create(const lbm_params& p, const uint8_t* cells, cudaStream_t
   std::copy(m->out_start.begin(), m->out_start.end(), outs.begin());
   std::copy(m->out_len.begin(), m->out_len.end(), outs.begin() + LBM_MAX_OUTLETS);
   // pageable sources: each call returns once its source has been staged
-  CUM(cudaMemcpyAsync(m->u_in, u_in.data(), (size_t)m->ny * 4, cudaMemcpyHostToDevice, stream));
-  CUM(cudaMemcpyAsync(m->d_out, outs.data(), outs.size() * 4, cudaMemcpyHostToDevice, stream));
-  CUM(cudaMemcpyAsync(m->cells, cells, (size_t)m->nx * m->ny, cudaMemcpyHostToDevice, stream));
+  CUM(xfer(m->u_in, u_in.data(), (size_t)m->ny * 4, cudaMemcpyHostToDevice, stream));
+  CUM(xfer(m->d_out, outs.data(), outs.size() * 4, cudaMemcpyHostToDevice, stream));
+  CUM(xfer(m->cells, cells, (size_t)m->nx * m->ny, cudaMemcpyHostToDevice, stream));
   CUM(launch_pack_mask(m->cells, m->nx, m->ny, m->wpr, m->mask0, stream));
   if (p.mirror) {  // the padding row below row 0 is row 0's mirror image (the exchange never moves row 0)
     const size_t row = (size_t)mask_stride(m->wpr) * 4;
-    CUM(cudaMemcpyAsync(m->mask0_base, m->mask0_base + mask_stride(m->wpr), row, cudaMemcpyDeviceToDevice, stream));
+    CUM(xfer(m->mask0_base, m->mask0_base + mask_stride(m->wpr), row, cudaMemcpyDeviceToDevice, stream));
   }
 #undef CUM
   LatticeView& v = m->view;
@@ -728,7 +774,7 @@ lbm_status member_create(const lbm_params& p, const uint8_t* cells, cudaStream_t
 }
 
 lbm_status member_reset(Member* m, cudaStream_t stream) {
-  CU(cudaMemcpyAsync(m->mask_base, m->mask0_base, m->mask_bytes, cudaMemcpyDeviceToDevice, stream));
+  CU(xfer(m->mask_base, m->mask0_base, m->mask_bytes, cudaMemcpyDeviceToDevice, stream));
   CU(cudaMemsetAsync(m->f, 0, 9 * m->plane * storage_bytes(m->p.precision), stream));  // g = 0: rest at rho0
   CU(cudaMemsetAsync(m->drho, 0, 5 * align_up(m->plane * 4), stream));                 // the five fields
   m->steps_done = 0;
@@ -863,7 +909,7 @@ lbm_status engine_set_members(Engine* E, const std::vector<Member*>& members) {
   if (n == 0) return LBM_OK;
   st = rebuild_worklist(E);
   if (st != LBM_OK) return st;
-  CU(cudaMemcpyAsync(E->h_count, E->fluid_dev.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost,
+  CU(xfer(E->h_count, E->fluid_dev.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost,
                      E->stream));
   CU(cudaStreamSynchronize(E->stream));
   for (size_t i = 0; i < n; ++i) E->m[i]->fluid_cells = (int64_t)E->h_count[i];
@@ -877,7 +923,7 @@ lbm_status engine_reset(Engine* E) {
   }
   lbm_status st = rebuild_worklist(E);
   if (st != LBM_OK) return st;
-  CU(cudaMemcpyAsync(E->h_count, E->fluid_dev.p, sizeof(unsigned long long) * E->n(), cudaMemcpyDeviceToHost,
+  CU(xfer(E->h_count, E->fluid_dev.p, sizeof(unsigned long long) * E->n(), cudaMemcpyDeviceToHost,
                      E->stream));
   CU(cudaStreamSynchronize(E->stream));
   for (int i = 0; i < E->n(); ++i) E->m[i]->fluid_cells = (int64_t)E->h_count[i];
@@ -964,10 +1010,10 @@ lbm_status enqueue_steps_and_reduce(Engine* E, int64_t n_steps, bool with_res) {
   }
   CU(launch_finalize(views, E->n(), partials, with_res ? 1 : 0, static_cast<double*>(E->result.p), E->stream));
   DEBUG_SYNC(E, "finalize");
-  CU(cudaMemcpyAsync(E->h_result, E->result.p, sizeof(double) * kResultDoubles * E->n(), cudaMemcpyDeviceToHost,
+  CU(xfer(E->h_result, E->result.p, sizeof(double) * kResultDoubles * E->n(), cudaMemcpyDeviceToHost,
                      E->stream));
   if (E->bar_used)
-    CU(cudaMemcpyAsync(E->h_bar_error, &static_cast<StepBarrier*>(E->bar.p)->error, sizeof(int),
+    CU(xfer(E->h_bar_error, &static_cast<StepBarrier*>(E->bar.p)->error, sizeof(int),
                        cudaMemcpyDeviceToHost, E->stream));
   else
     *E->h_bar_error = 0;
@@ -999,7 +1045,7 @@ lbm_status enqueue_exchange(Engine* E, const std::vector<int>& which, const int3
   lbm_status st = reserve_oc(E, *X);
   if (st != LBM_OK) return st;
   for (int k = 0; k < nx_; ++k) E->h_nswap[k] = n_swap[k];
-  CU(cudaMemcpyAsync(E->n_swap_dev.p, E->h_nswap, sizeof(int) * nx_, cudaMemcpyHostToDevice, E->stream));
+  CU(xfer(E->n_swap_dev.p, E->h_nswap, sizeof(int) * nx_, cudaMemcpyHostToDevice, E->stream));
   const LatticeView* xv = static_cast<const LatticeView*>(X->views.p);
   CU(launch_oc_select(xv, static_cast<const int*>(X->word_off.p), nx_, X->total_words,
                       static_cast<const int*>(E->n_swap_dev.p), E->oc, E->stream));
@@ -1013,8 +1059,8 @@ lbm_status enqueue_exchange(Engine* E, const std::vector<int>& which, const int3
   }
   st = rebuild_worklist(E);
   if (st != LBM_OK) return st;
-  CU(cudaMemcpyAsync(E->h_info, E->oc.info, sizeof(int) * 8 * nx_, cudaMemcpyDeviceToHost, E->stream));
-  CU(cudaMemcpyAsync(E->h_count, E->fluid_dev.p, sizeof(unsigned long long) * E->n(), cudaMemcpyDeviceToHost,
+  CU(xfer(E->h_info, E->oc.info, sizeof(int) * 8 * nx_, cudaMemcpyDeviceToHost, E->stream));
+  CU(xfer(E->h_count, E->fluid_dev.p, sizeof(unsigned long long) * E->n(), cudaMemcpyDeviceToHost,
                      E->stream));
   return LBM_OK;
 }
@@ -1089,21 +1135,21 @@ lbm_status save_state(Engine* E, const Member* m) {
   const StateCopy z = state_sizes(m);
   CU(E->best.reserve(z.f + z.mask + z.fields));
   char* b = static_cast<char*>(E->best.p);
-  CU(cudaMemcpyAsync(b, m->f, z.f, cudaMemcpyDeviceToDevice, E->stream));
-  CU(cudaMemcpyAsync(b + z.f, m->mask_base, z.mask, cudaMemcpyDeviceToDevice, E->stream));
-  CU(cudaMemcpyAsync(b + z.f + z.mask, m->drho, z.fields, cudaMemcpyDeviceToDevice, E->stream));
+  CU(xfer(b, m->f, z.f, cudaMemcpyDeviceToDevice, E->stream));
+  CU(xfer(b + z.f, m->mask_base, z.mask, cudaMemcpyDeviceToDevice, E->stream));
+  CU(xfer(b + z.f + z.mask, m->drho, z.fields, cudaMemcpyDeviceToDevice, E->stream));
   return LBM_OK;
 }
 
 lbm_status restore_state(Engine* E, Member* m) {
   const StateCopy z = state_sizes(m);
   const char* b = static_cast<const char*>(E->best.p);
-  CU(cudaMemcpyAsync(m->f, b, z.f, cudaMemcpyDeviceToDevice, E->stream));
-  CU(cudaMemcpyAsync(m->mask_base, b + z.f, z.mask, cudaMemcpyDeviceToDevice, E->stream));
-  CU(cudaMemcpyAsync(m->drho, b + z.f + z.mask, z.fields, cudaMemcpyDeviceToDevice, E->stream));
+  CU(xfer(m->f, b, z.f, cudaMemcpyDeviceToDevice, E->stream));
+  CU(xfer(m->mask_base, b + z.f, z.mask, cudaMemcpyDeviceToDevice, E->stream));
+  CU(xfer(m->drho, b + z.f + z.mask, z.fields, cudaMemcpyDeviceToDevice, E->stream));
   lbm_status st = rebuild_worklist(E);
   if (st != LBM_OK) return st;
-  CU(cudaMemcpyAsync(E->h_count, E->fluid_dev.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, E->stream));
+  CU(xfer(E->h_count, E->fluid_dev.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, E->stream));
   CU(cudaStreamSynchronize(E->stream));
   m->fluid_cells = (int64_t)E->h_count[0];
   return LBM_OK;
@@ -1170,26 +1216,26 @@ lbm_status engine_read(Engine* E, int i, uint32_t which, void* dst, size_t dst_b
     case LBM_FIELD_MASK:
       if (dst_bytes < ncell) return fail(LBM_ERR_ARG, "dst too small");
       CU(launch_unpack_mask(m->mask, m->nx, m->ny, m->wpr, m->cells, E->stream));
-      CU(cudaMemcpyAsync(dst, m->cells, ncell, cudaMemcpyDefault, E->stream));
+      CU(xfer(dst, m->cells, ncell, cudaMemcpyDefault, E->stream));
       break;
     case LBM_FIELD_RHO:
       if (dst_bytes < ncell * 4) return fail(LBM_ERR_ARG, "dst too small");
       CU(launch_rho_from_drho(m->drho, (float)m->p.rho0, m->mask, m->nx, m->ny, m->pitch, m->wpr,
                               static_cast<float*>(E->dense_f.p), E->stream));
-      CU(cudaMemcpyAsync(dst, E->dense_f.p, ncell * 4, cudaMemcpyDefault, E->stream));
+      CU(xfer(dst, E->dense_f.p, ncell * 4, cudaMemcpyDefault, E->stream));
       break;
     case LBM_FIELD_DRHO:
     case LBM_FIELD_UX:
     case LBM_FIELD_UY: {
       if (dst_bytes < ncell * 4) return fail(LBM_ERR_ARG, "dst too small");
       const float* src = which == LBM_FIELD_DRHO ? m->drho : which == LBM_FIELD_UX ? m->ux : m->uy;
-      CU(cudaMemcpy2DAsync(dst, nx * 4, src, (size_t)m->pitch * 4, nx * 4, ny, cudaMemcpyDefault, E->stream));
+      CU(xfer2d(dst, nx * 4, src, (size_t)m->pitch * 4, nx * 4, ny, cudaMemcpyDefault, E->stream));
       break;
     }
     case LBM_FIELD_POPS:
       if (dst_bytes < 9 * ncell * sb) return fail(LBM_ERR_ARG, "dst too small");
       for (int k = 0; k < 9; ++k)
-        CU(cudaMemcpy2DAsync(static_cast<char*>(dst) + k * ncell * sb, nx * sb,
+        CU(xfer2d(static_cast<char*>(dst) + k * ncell * sb, nx * sb,
                              static_cast<const char*>(m->f) + k * m->plane * sb, (size_t)m->pitch * sb, nx * sb,
                              ny, cudaMemcpyDefault, E->stream));
       break;

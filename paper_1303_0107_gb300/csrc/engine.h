@@ -152,6 +152,16 @@ lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t pe
                                   int32_t stages);
 lbm_status engine_kernel_time(Engine* E, int reset, double* ms, int64_t* launches, int64_t* fluid_updates);
 
+// Copies through which the library moves data between host and device
+// memory: cudaMemcpyAsync / cudaMemcpy2DAsync that also count the bytes
+// crossing in each direction (process-wide; lbm_transfer_bytes reports
+// them).  cudaMemcpyDefault copies are classified by the pointers' memory
+// types; device-to-device copies count nothing.
+cudaError_t xfer(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t stream);
+cudaError_t xfer2d(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t height,
+                   cudaMemcpyKind kind, cudaStream_t stream);
+void transfer_bytes(uint64_t* h2d, uint64_t* d2h);
+
 // thread-local last error and launch counter state shared with api.cu
 extern thread_local bool t_capturing;
 extern thread_local std::string t_last_error;

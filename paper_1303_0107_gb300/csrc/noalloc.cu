@@ -15,7 +15,6 @@
 // oc.cu and worklist.cu are reused unchanged), so the chosen cells are
 // identical bit for bit.
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "lbm_internal.h"
@@ -56,12 +55,8 @@ constexpr size_t kScratchBytes = kOffWords + up(4 * sizeof(int));
 
 // The shared scratch (about 7.4 MB).  In host code this name is only a
 // stand-in for the symbol: its device address comes from
-// cudaGetSymbolAddress, looked up once per device below.
+// cudaGetSymbolAddress, looked up on every call below.
 static __device__ __align__(256) unsigned char g_select_scratch[kScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
 
 lbm_status fail(lbm_status s, const char* what, cudaError_t e = cudaSuccess) {
   std::string msg(what);
@@ -73,22 +68,28 @@ lbm_status fail(lbm_status s, const char* what, cudaError_t e = cudaSuccess) {
   return s;
 }
 
-// Device address of the scratch array on the current device (looked up on
-// the first call made with that device current).
+// Device address of the scratch array on the current device, looked up on
+// every call: once the library's device code is loaded on that device the
+// lookup is cheap, and a cached address would dangle after a cudaDeviceReset.
 lbm_status scratch_on_current_device(unsigned char** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "cudaGetDevice", e);
-  if (dev < 0 || dev >= kMaxDevices) return fail(LBM_ERR_ARG, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_select_scratch);
-    if (e != cudaSuccess || !p) return fail(LBM_ERR_CUDA, "cudaGetSymbolAddress(scratch)", e);
-    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_select_scratch);
+  if (e != cudaSuccess || !p) return fail(LBM_ERR_CUDA, "cudaGetSymbolAddress(scratch)", e);
+  *out = static_cast<unsigned char*>(p);
   return LBM_OK;
+}
+
+// The lattice descriptor and the word table {0, words, n_swap} travel as
+// kernel parameters, so the call copies nothing from host memory: one
+// thread stores them into the scratch.
+__global__ void k_put_descriptor(LatticeView v, int words, int n_swap, LatticeView* __restrict__ view_dst,
+                                 int* __restrict__ words_dst) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *view_dst = v;
+    words_dst[0] = 0;
+    words_dst[1] = words;
+    words_dst[2] = n_swap;
+  }
 }
 
 // picks -> caller's output buffers, count -> *n_out (all on the device)
@@ -146,7 +147,6 @@ extern "C" lbm_status lbm_select_swaps_noalloc(int32_t nx, int32_t ny, double ta
   v.word_off = 0;
   LatticeView* view_dev = reinterpret_cast<LatticeView*>(base + kOffView);
   int* words_dev = reinterpret_cast<int*>(base + kOffWords);  // [0] = 0, [1] = words, [2] = n_swap
-  const int host_words[3] = {0, ny * wpr, n_swap};
 
   OcScratch s;
   s.cnt_f = reinterpret_cast<int*>(base + kOffCntF);
@@ -166,11 +166,9 @@ extern "C" lbm_status lbm_select_swaps_noalloc(int32_t nx, int32_t ny, double ta
   // the array keeps the previous call's contents: the mask padding must read
   // as wall, so the whole mask region is reset (the selection clears its own
   // counters; every other part is fully written before it is read)
-  if ((e = cudaMemcpyAsync(view_dev, &v, sizeof(v), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
-    return fail(LBM_ERR_CUDA, "copy lattice descriptor", e);
-  if ((e = cudaMemcpyAsync(words_dev, host_words, sizeof(host_words), cudaMemcpyHostToDevice, stream)) !=
-      cudaSuccess)
-    return fail(LBM_ERR_CUDA, "copy word offsets", e);
+  k_put_descriptor<<<1, 32, 0, stream>>>(v, ny * wpr, n_swap, view_dev, words_dev);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(LBM_ERR_CUDA, "store lattice descriptor", e);
   if ((e = cudaMemsetAsync(mask_base, 0xff, (size_t)mask_alloc_words(wpr, ny) * 4, stream)) != cudaSuccess)
     return fail(LBM_ERR_CUDA, "reset mask", e);
   if ((e = launch_pack_mask(cell_types, nx, ny, wpr, mask, stream)) != cudaSuccess)

@@ -3,9 +3,10 @@
 // convergence residual -- for every lattice of a set in one launch.
 //
 // All sums are accumulated in double from the FP32 moments of the last step
-// and are deterministic: every thread owns a fixed set of cells, block sums
-// use a fixed tree, and partial sums are combined in ascending block order.
-// No floating-point atomics.
+// and are deterministic: every thread owns a fixed set of cells, warps sum
+// by a fixed shuffle butterfly, block sums take the warp sums in ascending
+// warp order, and partial sums are combined in ascending block order.  No
+// floating-point atomics.
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -13,17 +14,24 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-// Fixed-shape tree sum over a block of kRedThreads doubles held in smem.
+// Sum over a warp by shuffles: a fixed butterfly, so every lane gets the
+// same bits for the same inputs in the same lanes.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of kRedThreads doubles: each warp by shuffles, then the warp sums
+// by the first warp in ascending warp order.  Every thread gets the result.
 __device__ double block_sum(double v, double* sm) {
-  const int tid = threadIdx.x;
-  sm[tid] = v;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sm[warp] = v;
   __syncthreads();
-  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-    if (tid < s) sm[tid] += sm[tid + s];
-    __syncthreads();
-  }
-  const double r = sm[0];
-  __syncthreads();
+  double r = lane < kRedThreads / 32 ? sm[lane] : 0.0;
+  r = warp_sum(r);
+  __syncthreads();  // sm is reused by the next call
   return r;
 }
 
@@ -32,7 +40,7 @@ __device__ double block_sum(double v, double* sm) {
 // partials[l][2b+1] = sum |u|_1 (solid cells hold zeros in both fields).
 __global__ void __launch_bounds__(kRedThreads)
     k_residual_partials(const LatticeView* __restrict__ views, double* __restrict__ partials) {
-  __shared__ double sm[kRedThreads];
+  __shared__ double sm[kRedThreads / 32];
   const LatticeView* L = views + blockIdx.y;
   const int nx = L->nx, ny = L->ny, pitch = L->pitch;
   const int b = blockIdx.x;
@@ -61,7 +69,7 @@ __global__ void __launch_bounds__(kRedThreads)
 __global__ void __launch_bounds__(kRedThreads)
     k_finalize(const LatticeView* __restrict__ views, const double* __restrict__ partials_all,
                int with_residual, double* __restrict__ result_all) {
-  __shared__ double sm[kRedThreads];
+  __shared__ double sm[kRedThreads / 32];
   const LatticeView* L = views + blockIdx.x;
   double* result = result_all + (size_t)blockIdx.x * kResultDoubles;
   const double* partials = partials_all + (size_t)blockIdx.x * 2 * kResidualBlocks;
@@ -90,16 +98,21 @@ __global__ void __launch_bounds__(kRedThreads)
   m_in = block_sum(m_in, sm);
   n_in = block_sum(n_in, sm);
   n_out = block_sum(n_out, sm);
-  // each outlet run summed by one thread in ascending row order
-  for (int j = threadIdx.x; j < n_outlets; j += kRedThreads) {
-    double m = 0.0;
-    const int ya = L->out_start[j], yb = ya + L->out_len[j];
-    for (int y = ya; y < yb; ++y) {
-      const long long c = (long long)y * pitch + nx - 1;
-      if (!LBM_OK_IDX(c, L->plane)) continue;
-      m += (rho0 + (double)L->drho[c]) * (double)L->ux[c];
+  // each outlet run summed by one warp: lane l takes rows ya + l, ya + l + 32,
+  // ... in ascending order, then the lanes' sums by shuffles
+  {
+    const int lane = threadIdx.x & 31;
+    for (int j = threadIdx.x >> 5; j < n_outlets; j += kRedThreads / 32) {
+      double m = 0.0;
+      const int ya = L->out_start[j], yb = ya + L->out_len[j];
+      for (int y = ya + lane; y < yb; y += 32) {
+        const long long c = (long long)y * pitch + nx - 1;
+        if (!LBM_OK_IDX(c, L->plane)) continue;
+        m += (rho0 + (double)L->drho[c]) * (double)L->ux[c];
+      }
+      m = warp_sum(m);
+      if (lane == 0) result[10 + j] = m;
     }
-    result[10 + j] = m;
   }
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -425,7 +425,8 @@ __device__ __forceinline__ void seg_update(const SegCtx<T>& s, float (&g)[9]) {
   if (rule == LBM_OUT_NEUMANN) {
     // zero-gradient outlet: the unknown g3, g6, g7 of cell (nx-1, y) are the
     // streamed g3, g6, g7 of cell (nx-2, y), held by the lane to the left
-    // (nx is even, so both cells are in this warp's row segment).
+    // (nx mod 32 != 1 is required with this rule, so both cells are in
+    // this warp's row segment).
     const float n3 = __shfl_up_sync(0xffffffffu, g[3], 1);
     const float n6 = __shfl_up_sync(0xffffffffu, g[6], 1);
     const float n7 = __shfl_up_sync(0xffffffffu, g[7], 1);

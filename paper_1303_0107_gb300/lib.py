@@ -133,6 +133,8 @@ def load_library(path=None):
     L.lbm_select_swaps.argtypes = [H, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, ctypes.POINTER(ctypes.c_int32)]
     L.lbm_destroy.argtypes = [H]
     L.lbm_destroy.restype = None
+    L.lbm_transfer_bytes.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+    L.lbm_transfer_bytes.restype = None
     L.lbm_status_str.argtypes = [ctypes.c_int]
     L.lbm_status_str.restype = ctypes.c_char_p
     L.lbm_last_error.argtypes = []
@@ -208,6 +210,13 @@ def debug_barrier_timeout(on: bool) -> None:
 
 def kernel_launches() -> int:
     return int(load_library().lbm_kernel_launches())
+
+
+def transfer_bytes():
+    """(host-to-device, device-to-host) bytes the library has copied in this process."""
+    h2d, d2h = ctypes.c_uint64(), ctypes.c_uint64()
+    load_library().lbm_transfer_bytes(ctypes.byref(h2d), ctypes.byref(d2h))
+    return int(h2d.value), int(d2h.value)
 
 
 def bytes_per_fluid_update(precision: int) -> float:

@@ -64,3 +64,21 @@ def test_reference_arm_other_ranks_exit_without_work():
     class A:
         steps, warmup, cpu_seconds, gpus = 1, 0, 0.1, 2
     assert bench.run_reference(A(), 2, 1) == 0
+
+
+def test_leg_summary_picks_each_legs_rates():
+    sys.path.insert(0, ROOT)
+    import bench
+    extras = {"large_8192x4096_f32": {"glups": 69.3, "frac_of_measured_hbm": 0.74, "fluid_cells": 1},
+              "large_8192x4096_bf16": {"glups": 76.9, "frac_of_measured_hbm": 0.41},
+              "batched_256_f32": {"batched_glups": 43.3, "batched_step_glups": 45.0, "speedup": 3.0},
+              "precision_tree_2048": {"bf16": {"glups_vs_f32": 0.79, "dp_rel_err": 9.8e-3}},
+              "d3q19": {"tree3d_384x192x192_f32": {"glups": 28.4, "frac_of_measured_hbm": 0.64}},
+              "served_f32": {"p50_ms": 7.1, "p99_ms": 164.6, "aggregate_glups": 29.1}}
+    s = bench.leg_summary(extras)
+    assert s["large_f32_glups"] == 69.3 and s["large_bf16_frac"] == 0.41
+    assert s["batched_f32_glups"] == 43.3 and s["batched_f32_speedup"] == 3.0
+    assert s["tree_bf16_vs_f32"] == 0.79 and s["tree3d_384x192x192_f32_frac"] == 0.64
+    assert s["served_p50_ms"] == 7.1 and s["served_aggregate_glups"] == 29.1
+    assert "batched_bf16_glups" not in s  # legs that did not run are left out
+    assert bench.leg_summary({}) == {}

@@ -86,5 +86,5 @@ def test_batch_reset_and_errors():
     with pytest.raises(L.LbmError):
         batch.read(5, L.FIELD_UX)
     with pytest.raises(L.LbmError):
-        L.Batch([dict(cells=I.channel(33, 8), tau=0.8, u_max=0.01)])
+        L.Batch([dict(cells=I.channel(33, 8), tau=0.8, u_max=0.01, outlet=L.OUT_NEUMANN)])
     batch.close()

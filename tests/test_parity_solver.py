@@ -215,8 +215,21 @@ def test_argument_errors():
         L.Lattice(bad, 0.8, 0.05)
     assert e.value.status == 2
     with pytest.raises(L.LbmError) as e:
-        L.Lattice(I.channel(33, 8), 0.8, 0.05)  # odd nx
+        # zero-gradient outlet with nx mod 32 == 1: cells nx-2 and nx-1 in different segments
+        L.Lattice(I.channel(33, 8), 0.8, 0.05, outlet=L.OUT_NEUMANN)
     assert e.value.status == 1
+    lat.close()
+
+
+@pytest.mark.parametrize("nx,outlet", [(33, 0), (63, 1), (97, 0), (65, 0), (95, 1)])
+def test_odd_widths(ora, nx, outlet):
+    """Odd nx: the last row segment is ragged at any parity; the zero-gradient
+    outlet takes every odd nx but those with nx mod 32 == 1."""
+    cells = I.random_blobs(nx, 21, nx, density=0.15)
+    lat, g, s, o = _run_both(ora, cells, 0.7, 0.03, 60, outlet=outlet)
+    _check_pops(lat, s, cells, tol=2e-5)
+    _check_fields(lat, s, cells)
+    assert abs(g["dp"] - o["dp"]) <= TOL * abs(o["dp"])
     lat.close()
 
 

@@ -7,7 +7,10 @@ allocates).  lbm_select_swaps_noalloc takes only caller-owned device buffers
 and keeps its intermediate data in a static device array.  Here it is called
 through the C ABI twice in a row, on two lattices of different shapes (so
 anything left over in the shared array from the first call would show), and
-its picks must equal those of lbm_select_swaps bit for bit.  This file is
+its picks must equal those of lbm_select_swaps and of the FP64 oracle's
+selection on the same fields bit for bit.  The edge cases: more cells asked
+for than there are candidates (n is clamped), a field holding a NaN (n_out
+= -1), and n_swap = 0 with no output buffers (n_out = 0).  This file is
 named to be collected last.
 """
 
@@ -34,40 +37,94 @@ def _fields(shape, seed, ties):
     return drho, ux, uy
 
 
-def test_noalloc_selection_equals_handle_selection_twice():
+def _torch():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    return torch
+
+
+def _noalloc(lib, torch, cells, tau, drho, ux, uy, n_swap, with_outputs=True):
+    """One call through the C ABI on device copies; returns (status, n_out, fluid picks, solid picks)."""
+    ny, nx = cells.shape
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (cells, drho, ux, uy)]
+    cap = max(n_swap, 1)
+    out_f = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    out_s = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    n_dev = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    st = lib.lbm_select_swaps_noalloc(nx, ny, tau, 1.0, *[t.data_ptr() for t in dev], n_swap,
+                                      out_f.data_ptr() if with_outputs else None,
+                                      out_s.data_ptr() if with_outputs else None, n_dev.data_ptr(),
+                                      stream.cuda_stream)
+    torch.cuda.synchronize()
+    n = int(n_dev.item())
+    k = max(n, 0)
+    return st, n, out_f[:k].cpu().numpy(), out_s[:k].cpu().numpy()
+
+
+def _oracle_pick(ora, cells, tau, drho, ux, uy, n_swap):
+    ny, nx = cells.shape
+    p = ora.make_params(nx, ny, tau, 1.0)
+    rho = 1.0 + drho.astype(np.float64)
+    cand, score = ora.scores(p, cells, rho, ux.astype(np.float64), uy.astype(np.float64))
+    return ora.select(p, cand, score, n_swap)
+
+
+def test_noalloc_selection_equals_handle_and_oracle_twice(ora):
+    torch = _torch()
     lib = L.load_library()
     t_junction = I.config_t_junction()
     cases = [(t_junction["cells"], t_junction["tau"], 7, 0, False),
              (I.random_blobs(100, 40, 5, density=0.3), 0.7, 25, 1, True)]
-    stream = torch.cuda.current_stream()
     for cells, tau, n_swap, seed, ties in cases:
-        ny, nx = cells.shape
         drho, ux, uy = _fields(cells.shape, seed, ties)
         lat = L.Lattice(cells, tau, 0.02)
         ref_f, ref_s = lat.select_swaps(drho, ux, uy, n_swap)
         lat.close()
-        dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (cells, drho, ux, uy)]
-        out_f = torch.full((n_swap,), -7, dtype=torch.int32, device="cuda")
-        out_s = torch.full((n_swap,), -7, dtype=torch.int32, device="cuda")
-        n_dev = torch.full((1,), -7, dtype=torch.int32, device="cuda")
-        st = lib.lbm_select_swaps_noalloc(nx, ny, tau, 1.0, *[t.data_ptr() for t in dev], n_swap,
-                                          out_f.data_ptr(), out_s.data_ptr(), n_dev.data_ptr(),
-                                          stream.cuda_stream)
+        ora_f, ora_s = _oracle_pick(ora, cells, tau, drho, ux, uy, n_swap)
+        st, n, got_f, got_s = _noalloc(lib, torch, cells, tau, drho, ux, uy, n_swap)
         assert st == 0, lib.lbm_last_error().decode()
-        torch.cuda.synchronize()
-        n = int(n_dev.item())
-        assert n == len(ref_f) == len(ref_s)
-        assert np.array_equal(out_f[:n].cpu().numpy(), ref_f)
-        assert np.array_equal(out_s[:n].cpu().numpy(), ref_s)
+        assert n == len(ref_f) == len(ref_s) == len(ora_f) == n_swap
+        assert np.array_equal(got_f, ref_f) and np.array_equal(got_s, ref_s)
+        assert np.array_equal(got_f, ora_f) and np.array_equal(got_s, ora_s)
+
+
+def test_noalloc_edge_cases(ora):
+    torch = _torch()
+    lib = L.load_library()
+    cells = I.config_t_junction()["cells"]
+    tau = 0.8
+    drho, ux, uy = _fields(cells.shape, 3, False)
+    # more picks asked for than there are candidates: n = min(n_swap, |F|, |S|)
+    big = cells.size
+    ora_f, ora_s = _oracle_pick(ora, cells, tau, drho, ux, uy, big)
+    lat = L.Lattice(cells, tau, 0.02)
+    ref_f, ref_s = lat.select_swaps(drho, ux, uy, big)
+    st, n, got_f, got_s = _noalloc(lib, torch, cells, tau, drho, ux, uy, big)
+    assert st == 0, lib.lbm_last_error().decode()
+    assert 0 < n == len(ora_f) == len(ref_f) < big
+    assert np.array_equal(got_f, ora_f) and np.array_equal(got_s, ora_s)
+    assert np.array_equal(got_f, ref_f) and np.array_equal(got_s, ref_s)
+    # a NaN in the velocity of one fluid candidate: no picks, n_out = -1
+    ny, nx = cells.shape
+    p = ora.make_params(nx, ny, tau, 1.0)
+    cand, _ = ora.scores(p, cells, 1.0 + drho.astype(np.float64), ux.astype(np.float64), uy.astype(np.float64))
+    y, x = np.argwhere(cand == 1)[0]
+    ux_nan = ux.copy()
+    ux_nan[y, x] = np.nan
+    st, n, _, _ = _noalloc(lib, torch, cells, tau, drho, ux_nan, uy, 5)
+    assert st == 0 and n == -1
+    with pytest.raises(L.LbmError):
+        lat.select_swaps(drho, ux_nan, uy, 5)
+    lat.close()
+    # nothing asked for: no output buffers needed, n_out = 0
+    st, n, _, _ = _noalloc(lib, torch, cells, tau, drho, ux, uy, 0, with_outputs=False)
+    assert st == 0 and n == 0
 
 
 def test_noalloc_rejects_lattices_beyond_its_scratch():
-    torch = pytest.importorskip("torch")
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
+    torch = _torch()
     lib = L.load_library()
     one = torch.zeros(16, dtype=torch.int32, device="cuda")
     p = one.data_ptr()
