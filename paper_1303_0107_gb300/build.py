@@ -25,7 +25,7 @@ def _stale(lib=LIB) -> bool:
     if not lib.exists():
         return True
     t = lib.stat().st_mtime
-    deps = list(sources()) + list(CSRC.glob("*.h")) + list((ROOT / "include").glob("*.h"))
+    deps = list(sources()) + list(CSRC.glob("*.h")) + list(CSRC.glob("*.cuh")) + list((ROOT / "include").glob("*.h"))
     return any(p.stat().st_mtime > t for p in deps)
 
 

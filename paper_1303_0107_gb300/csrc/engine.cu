@@ -88,6 +88,15 @@ bool persistent_enabled() {
   return on;
 }
 
+// LBM_RESIDENT=0 keeps the on-chip resident steps out of the tuner's candidates.
+bool resident_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("LBM_RESIDENT");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 bool autotune_enabled() {
   static const bool on = [] {
     const char* e = std::getenv("LBM_AUTOTUNE");
@@ -353,7 +362,44 @@ lbm_status run_persistent(Engine* E, int64_t pairs) {
   return LBM_OK;
 }
 
+// One resident launch of n_steps steps (moments at the last step and, when
+// mom_prev >= 0, into the *_prev fields at that step).
+lbm_status run_resident(Engine* E, int64_t n_steps, int mom_prev) {
+  if (n_steps < 1) return LBM_OK;
+  if (n_steps >= (int64_t)1 << 30) return fail(LBM_ERR_ARG, "resident steps: at most 2^30 steps per solve");
+  if ((uint64_t)E->halo_epoch + (uint64_t)n_steps + 2 >= (1ull << 32)) {  // tags would wrap: start afresh
+    CU(cudaMemsetAsync(E->halo.p, 0, E->halo.cap, E->stream));
+    E->halo_epoch = 1;
+  }
+  const unsigned epoch0 = E->halo_epoch;
+  E->halo_epoch += (unsigned)n_steps + 1;
+  StepBarrier* bar = static_cast<StepBarrier*>(E->bar.p);
+  CU(cudaMemsetAsync(&bar->error, 0, sizeof(int), E->stream));
+  const int* scratch = static_cast<const int*>(E->seg_scratch.p);
+  CU(launch_stream_collide_resident(E->precision, static_cast<const LatticeView*>(E->L.views.p),
+                                    static_cast<const SegRef*>(E->segs.p), static_cast<const int*>(E->n_segs.p),
+                                    static_cast<const int*>(E->L.seg_word_off.p), scratch,
+                                    scratch + E->L.total_seg_words, E->rshape,
+                                    static_cast<unsigned long long*>(E->halo.p), E->halo_cap, epoch0, (int)n_steps,
+                                    mom_prev, &bar->error, E->stream));
+  E->bar_used = true;
+  DEBUG_SYNC(E, "resident steps");
+  return LBM_OK;
+}
+
+StepConfig resident_config(const Engine* E) {
+  StepConfig c{};
+  c.warps_per_block = E->rshape.warps;
+  c.grid = E->rshape.grid;
+  c.persistent = 2;
+  c.cells_per_thread = 2;
+  c.stages = 0;
+  c.features = 0;
+  return c;
+}
+
 lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
+  if (E->step.persistent == 2 && !debug_sync()) return run_resident(E, 2 * pairs, -1);
   if (E->step.persistent && !debug_sync()) return run_persistent(E, pairs);
   if (debug_sync()) {
     for (int64_t k = 0; k < pairs; ++k) {
@@ -511,6 +557,15 @@ lbm_status autotune(Engine* E) {
       StepConfig c = persistent_shape(E, 8, cpt);
       if (c.grid > 0) cand.push_back(c);
     }
+  if (resident_enabled() && !only_plain) {
+    bool ok = false;
+    lbm_status st = resident_prepare(E, &ok);
+    if (st != LBM_OK) {
+      for (void* b : backups) cudaFree(b);
+      return st;
+    }
+    if (ok) cand.push_back(resident_config(E));
+  }
   cudaEvent_t a, b;
   CU(cudaEventCreate(&a));
   CU(cudaEventCreate(&b));
@@ -544,7 +599,9 @@ lbm_status autotune(Engine* E) {
       const StepConfig& c = cand[ci];
       E->step = c;
       cudaEventRecord(a, E->stream);
-      if (c.persistent) {
+      if (c.persistent == 2) {
+        st = run_resident(E, 2 * kTunePairs, -1);
+      } else if (c.persistent) {
         st = run_persistent(E, kTunePairs);
       } else if (cudaGraphLaunch(tg[ci], E->stream) != cudaSuccess) {
         st = fail(LBM_ERR_CUDA, "autotune graph launch");
@@ -560,7 +617,7 @@ lbm_status autotune(Engine* E) {
         if (cudaMemcpy(&err, &static_cast<StepBarrier*>(E->bar.p)->error, sizeof(int), cudaMemcpyDeviceToHost) !=
             cudaSuccess)
           st = fail(LBM_ERR_CUDA, "autotune barrier flag");
-        if (err != 0) st = fail(LBM_ERR_TIMEOUT, "persistent step kernel: a grid barrier wait gave up");
+        if (err != 0) st = fail(LBM_ERR_TIMEOUT, "step kernel: a bounded device wait gave up");
       }
       if (rep > 0) t_min[ci] = std::min(t_min[ci], ms);
     }
@@ -576,7 +633,7 @@ lbm_status autotune(Engine* E) {
   constexpr float kMargin = 0.985f;
   if (tune_log_enabled())
     for (size_t ci = 0; ci < cand.size(); ++ci)
-      std::fprintf(stderr, "lbm tune: wpb %d grid %d cpt %d stages %d persistent %d: %.3f us per phase\n",
+      std::fprintf(stderr, "lbm tune: wpb %d grid %d cpt %d stages %d persistent %d: %.3f us per step\n",
                    cand[ci].warps_per_block, cand[ci].grid, cand[ci].cells_per_thread, cand[ci].stages,
                    cand[ci].persistent, 1000.0 * t_min[ci] / (2 * kTunePairs));
   StepConfig best_cfg = cand[0], best_plain = cand[0];
@@ -816,8 +873,9 @@ Engine::~Engine() {
     for (Member* x : m) delete x;
   for (GrowBuf* b : {&L.views, &L.word_off, &L.seg_word_off, &XL.views, &XL.word_off, &XL.seg_word_off, &segs,
                      &n_segs, &seg_scratch, &partials, &result, &fluid_dev, &n_swap_dev, &dense_f, &oc_buf, &bar,
-                     &best})
+                     &best, &rplan, &halo})
     b->release();
+  if (h_rplan) cudaFreeHost(h_rplan);
   if (h_bar_error) cudaFreeHost(h_bar_error);
   if (h_result) cudaFreeHost(h_result);
   if (h_info) cudaFreeHost(h_info);
@@ -864,6 +922,7 @@ lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool
 }
 
 lbm_status rebuild_worklist(Engine* E) {
+  E->rplan_valid = false;
   if (E->n() == 0) return LBM_OK;
   CU(launch_build_segments(static_cast<const LatticeView*>(E->L.views.p), static_cast<const int*>(E->L.seg_word_off.p),
                            E->n(), E->L.total_seg_words, std::max(1, E->L.total_seg_words),
@@ -872,6 +931,49 @@ lbm_status rebuild_worklist(Engine* E) {
   CU(launch_count_fluid(static_cast<const LatticeView*>(E->L.views.p), static_cast<const int*>(E->L.word_off.p),
                         E->n(), E->L.total_words, static_cast<unsigned long long*>(E->fluid_dev.p), E->stream));
   DEBUG_SYNC(E, "work-list");
+  return LBM_OK;
+}
+
+lbm_status resident_prepare(Engine* E, bool* ok) {
+  *ok = false;
+  if (E->features != 0 || E->fixed_grid || E->n() == 0 || debug_sync()) return LBM_OK;
+  if (!E->rplan_valid) {
+    CU(E->rplan.reserve(4 * sizeof(int)));
+    if (!E->h_rplan) CU(cudaMallocHost((void**)&E->h_rplan, 4 * sizeof(int)));
+    const int* scratch = static_cast<const int*>(E->seg_scratch.p);
+    CU(launch_resident_plan(static_cast<const LatticeView*>(E->L.views.p), static_cast<const SegRef*>(E->segs.p),
+                            static_cast<const int*>(E->n_segs.p), static_cast<const int*>(E->L.seg_word_off.p),
+                            scratch, scratch + E->L.total_seg_words, E->sm_count, static_cast<int*>(E->rplan.p),
+                            E->stream));
+    CU(xfer(E->h_rplan, E->rplan.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, E->stream));
+    CU(cudaStreamSynchronize(E->stream));
+    const int nseg = E->h_rplan[0];
+    ResidentShape rs{};
+    rs.grid = resident_grid(nseg, E->sm_count);
+    const int own = (nseg + rs.grid - 1) / std::max(1, rs.grid);
+    rs.warps = std::max(1, (own + 1) / 2);
+    rs.words = E->h_rplan[1];
+    rs.pairs = E->h_rplan[2];
+    bool fits = nseg > 0 && E->h_rplan[3] == 1 && own <= kResidentMaxOwn && rs.words <= 65536 &&
+                resident_smem_bytes(E->precision, rs.words, rs.pairs) <= (size_t)std::max(0, resident_max_smem());
+    if (fits) {
+      bool moved = false;
+      const size_t bytes = (size_t)2 * nseg * 9 * 32 * sizeof(unsigned long long);
+      CU(E->halo.reserve(bytes, &moved));
+      if (moved) {  // fresh memory: no tag in it may match a future one
+        CU(cudaMemsetAsync(E->halo.p, 0, E->halo.cap, E->stream));
+        E->halo_epoch = 1;
+      }
+      E->halo_cap = (int)(E->halo.cap / (2 * 9 * 32 * sizeof(unsigned long long)));
+    }
+    E->rshape = rs;
+    E->rplan_ok = fits;
+    E->rplan_valid = true;
+    if (tune_log_enabled())
+      std::fprintf(stderr, "lbm resident plan: segments %d blocks %d warps %d words %d ghost rows %d fits %d\n",
+                   nseg, rs.grid, rs.warps, rs.words, rs.pairs, fits ? 1 : 0);
+  }
+  *ok = E->rplan_ok;
   return LBM_OK;
 }
 
@@ -993,14 +1095,21 @@ lbm_status enqueue_steps_and_reduce(Engine* E, int64_t n_steps, bool with_res) {
   lbm_status st;
   E->bar_used = false;
   CU(cudaEventRecord(E->ev_begin, E->stream));
-  if (with_res) {
+  bool resident = false;
+  if (E->step.persistent == 2 && !debug_sync()) {
+    if ((st = resident_prepare(E, &resident)) != LBM_OK) return st;
+    if (!resident) E->step = shape(E, kStepWarps, kDefaultGridScale);  // the list outgrew the chip
+  }
+  if (resident) {
+    if ((st = run_resident(E, n_steps, with_res ? (int)(n_steps - K - 1) : -1)) != LBM_OK) return st;
+  } else if (with_res) {
     if ((st = run_plain_pairs(E, (n_steps - K) / 2 - 1)) != LBM_OK) return st;
     if ((st = launch_pair(E, 2)) != LBM_OK) return st;
     if ((st = run_plain_pairs(E, K / 2 - 1)) != LBM_OK) return st;
   } else {
     if ((st = run_plain_pairs(E, n_steps / 2 - 1)) != LBM_OK) return st;
   }
-  if ((st = launch_pair(E, 1)) != LBM_OK) return st;
+  if (!resident && (st = launch_pair(E, 1)) != LBM_OK) return st;
   CU(cudaEventRecord(E->ev_end, E->stream));
   const LatticeView* views = static_cast<const LatticeView*>(E->L.views.p);
   double* partials = static_cast<double*>(E->partials.p);
@@ -1073,7 +1182,7 @@ lbm_status engine_solve(Engine* E, int64_t n_steps, lbm_solve_result* out) {
   for (Member* m : E->m) m->steps_done += n_steps;
   E->solved = true;
   account_steps(E, n_steps);
-  if (*E->h_bar_error != 0) return fail(LBM_ERR_TIMEOUT, "persistent step kernel: a grid barrier wait gave up");
+  if (*E->h_bar_error != 0) return fail(LBM_ERR_TIMEOUT, "step kernel: a bounded device wait gave up");
   bool bad = false;
   for (int i = 0; i < E->n(); ++i) {
     fill_result(E, i, out + i);
@@ -1106,7 +1215,7 @@ lbm_status engine_optimize(Engine* E, const int32_t* n_swap, int64_t n_steps, lb
     bad |= E->h_result[(size_t)i * kResultDoubles + 7] != 0.0;
   }
   account_steps(E, n_steps);
-  if (*E->h_bar_error != 0) return fail(LBM_ERR_TIMEOUT, "persistent step kernel: a grid barrier wait gave up");
+  if (*E->h_bar_error != 0) return fail(LBM_ERR_TIMEOUT, "step kernel: a bounded device wait gave up");
   for (int i = 0; i < E->n(); ++i) {
     std::memset(out + i, 0, sizeof(lbm_opt_result));
     out[i].n_swapped = E->h_info[8 * i];
@@ -1258,10 +1367,20 @@ lbm_status engine_step_config(Engine* E, int32_t* warps_per_block, int32_t* grid
 
 lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t persistent, int32_t cells_per_thread,
                                   int32_t stages) {
+  if (persistent == 2) {  // on-chip resident steps: the shape follows from the work-list
+    bool ok = false;
+    lbm_status st = resident_prepare(E, &ok);
+    if (st != LBM_OK) return st;
+    if (!ok)
+      return fail(LBM_ERR_ARG, "resident steps need plain BGK lattices whose segments fit in shared memory");
+    E->step = resident_config(E);
+    E->tuned = true;
+    return LBM_OK;
+  }
   if (stages != 0 && stages != 2 && stages != 3) return fail(LBM_ERR_ARG, "stages must be 0, 2 or 3");
   if (stages != 0 && (persistent || cells_per_thread != 1))
     return fail(LBM_ERR_ARG, "staged loads take one cell per thread and per-phase launches");
-  if (persistent != 0 && persistent != 1) return fail(LBM_ERR_ARG, "persistent must be 0 or 1");
+  if (persistent != 0 && persistent != 1) return fail(LBM_ERR_ARG, "persistent must be 0, 1 or 2");
   if (cells_per_thread != 1 && cells_per_thread != 2) return fail(LBM_ERR_ARG, "cells_per_thread must be 1 or 2");
   if (!step_shape_allowed(warps_per_block, cells_per_thread, persistent))
     return fail(LBM_ERR_ARG,

@@ -102,6 +102,16 @@ struct Engine {
   int* h_bar_error = nullptr;             // pinned: grid-barrier error flag of the last solve
   bool bar_used = false;                  // the last enqueued solve ran the persistent kernel
 
+  // on-chip resident steps (step.persistent == 2): the plan of the current
+  // work-list (valid until the list is rebuilt), the halo buffer of tagged
+  // words and the next tag
+  GrowBuf rplan, halo;
+  int* h_rplan = nullptr;  // pinned [4]
+  bool rplan_valid = false, rplan_ok = false;
+  ResidentShape rshape{};
+  int halo_cap = 0;        // segments the halo buffer holds
+  unsigned halo_epoch = 1;
+
   cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};  // 512, 64, 8 and 1 pairs
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};  // views, segs, n_segs, shape
   StepConfig step{kStepWarps, 1, 0, 1, 0, 0};
@@ -126,6 +136,9 @@ lbm_status engine_create(int n, const lbm_params* params, const uint8_t* const* 
                          Engine** out);
 lbm_status engine_reset(Engine* E);
 lbm_status rebuild_worklist(Engine* E);
+// Plan the resident launch for the current work-list (synchronises the
+// stream when the list changed since the last plan); *ok: the set fits.
+lbm_status resident_prepare(Engine* E, bool* ok);
 
 // Enqueue n_steps (even) with moments in the last step, optional residual,
 // and the reductions of every member; results to pinned h_result.  The

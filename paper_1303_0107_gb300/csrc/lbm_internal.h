@@ -146,6 +146,47 @@ cudaError_t launch_stream_collide_persistent(int precision, const LatticeView* v
                                              cudaStream_t stream);
 int stream_collide_persistent_grid(int precision, int warps_per_block, int cells_per_thread);
 
+// ---- on-chip resident time steps (resident.cu) ------------------------------
+// A whole solve in one cooperative launch with the populations in shared
+// memory: block b of G owns segments [b n / G, (b+1) n / G) of the list
+// (at most kResidentMaxOwn), two per warp, and exchanges the rows its
+// neighbours need through a halo buffer of tagged words.
+constexpr int kResidentMaxOwn = 48;
+constexpr int kResidentMaxWarps = kResidentMaxOwn / 2;
+// blocks of a resident launch over n segments: as few as hold them, at most one per SM
+__host__ __device__ inline int resident_grid(int nseg, int sm_count) {
+  const int need = (nseg + kResidentMaxOwn - 1) / kResidentMaxOwn;
+  return need < 1 ? 1 : need > sm_count ? sm_count : need;
+}
+// elements between the two step buffers: words rounded up to 8, a multiple
+// of 16 bytes for 16-bit and 32-bit storage
+__host__ __device__ inline int resident_buffer_stride(int words) { return (words + 7) & ~7; }
+struct ResidentShape {
+  int grid;   // blocks
+  int warps;  // warps per block (two segments each)
+  int words;  // step-buffer size per block (elements of the storage type)
+  int pairs;  // ghost rows per block at most
+};
+// Plan for the current list (out: int[4], device): segments, largest
+// step-buffer size, largest ghost-row count, 1 if the list fits.  seg_flags /
+// seg_offs: the work-list build's per-word flags and their exclusive scan
+// (the list index of every segment word that holds fluid).
+cudaError_t launch_resident_plan(const LatticeView* views, const SegRef* segs, const int* n_segs,
+                                 const int* seg_word_off, const int* seg_flags, const int* seg_offs, int sm_count,
+                                 int* out, cudaStream_t stream);
+// Dynamic shared memory of a launch, and the most a block may take.
+size_t resident_smem_bytes(int precision, int words, int pairs);
+int resident_max_smem();
+// n_steps time steps; halo: [2][halo_cap][9][32] words of {value, tag}, tags
+// epoch0 + 1 .. epoch0 + n_steps - 1 written by this launch (older tags
+// must all be smaller); moments at the last step and at step mom_prev (-1:
+// none, else into the *_prev fields); *error is set when a wait gave up.
+cudaError_t launch_stream_collide_resident(int precision, const LatticeView* views, const SegRef* segs,
+                                           const int* n_segs, const int* seg_word_off, const int* seg_flags,
+                                           const int* seg_offs, const ResidentShape& rs,
+                                           unsigned long long* halo, int halo_cap, unsigned epoch0, int n_steps,
+                                           int mom_prev, int* error, cudaStream_t stream);
+
 // ---- geometry / work-list (worklist.cu) ------------------------------------
 cudaError_t launch_pack_mask(const uint8_t* cells, int nx, int ny, int wpr, uint32_t* mask,
                              cudaStream_t stream);
