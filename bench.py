@@ -206,9 +206,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel_file, name):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current kernel source (the summary records the source hash)."""
+def profiled_traffic(kernel_file, name, key="dram_bytes_per_launch_full_workload"):
+    """DRAM bytes per launch (or per time step: key) from a committed ncu
+    summary, if it was taken on the current kernel source (the summary
+    records the source hash)."""
     import hashlib
     src = ROOT / "paper_1303_0107_gb300" / "csrc" / kernel_file
     summ = ROOT / "profiles" / name
@@ -223,7 +224,7 @@ def profiled_traffic(kernel_file, name):
     if vals.get("source_sha256_16") != h:
         return None
     try:
-        return float(vals["dram_bytes_per_launch_full_workload"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
 
@@ -741,11 +742,18 @@ def main():
     bytes_per_launch = fluid * bpu
     achieved = bytes_per_launch / avg_launch_s / 1e9
     peak, peak_kind = measured_peaks()
+    resident = lat.step_config()[2] == 2
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic("step.cu", "stream_collide_tree_2048x1024.md"),
+                "traffic": (profiled_traffic("resident.cu", "resident_tree_2048x1024.md",
+                                             "dram_bytes_per_step_full_workload") if resident
+                            else profiled_traffic("step.cu", "stream_collide_tree_2048x1024.md")),
                 "peak_kind": peak_kind, "bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": avg_launch_s * 1e6,
-                "note": "lattice working set (fluid cells) is L2-resident within a solve"}
+                "per": "time step (fluid cells x algorithmic bytes per update; mean time per step)",
+                "kernel": "k_stream_collide_resident" if resident else "k_stream_collide",
+                "note": ("populations in shared memory for the whole solve (one launch per solve), halo words in L2; "
+                         "bound by SM instruction issue" if resident else
+                         "lattice working set (fluid cells) is L2-resident within a solve")}
 
     # end to end through the public API, as many runs as timed steps: pinned
     # host cell map in, the whole optimisation run, the cell map back out.

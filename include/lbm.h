@@ -291,11 +291,21 @@ void lbm_debug_fail_alloc(int64_t after);
 
 /* Test hook for the bounded device-side waits (process-wide; on != 0 until
  * called again with 0): the persistent step kernel's grid barriers then wait
- * for one arrival more than the grid makes, so every wait gives up after its
- * poll limit (2^22 acquire loads, a few seconds), the launch ends early and
- * the solve returns LBM_ERR_TIMEOUT; the handle stays usable (lbm_reset or
+ * for one arrival more than the grid makes, and the resident kernel's halo
+ * polls for a step tag that nobody writes, so every wait gives up after its
+ * poll limit (2^22 loads, a few seconds), the launch ends early and the
+ * solve returns LBM_ERR_TIMEOUT; the handle stays usable (lbm_reset or
  * lbm_load_state restores a state).  No device fault is involved.         */
 void lbm_debug_barrier_timeout(int32_t on);
+
+/* Test hook of the bounds-checked build (built with -DLBM_CHECK_BOUNDS, loaded
+ * with LBM_CHECKED=1 by the Python binding): that build surrounds every
+ * lattice's population planes with canary blocks and checks them after each
+ * solve and optimiser step (LBM_ERR_CUDA, naming the lattice, if one was
+ * overwritten).  This call overwrites a few bytes of the handle's upper canary
+ * with a host-side memset inside the allocation, so that the next solve
+ * reports it.  LBM_ERR_ARG in the normal build, which has no canaries.    */
+lbm_status lbm_debug_damage_canary(lbm_handle h);
 
 /* Number of device kernels this process has launched through the library
  * (graph launches count every kernel node).                             */

@@ -53,6 +53,11 @@ void lbm_debug_fail_alloc(int64_t after) { set_alloc_failure(after); }
 
 void lbm_debug_barrier_timeout(int32_t on) { set_barrier_timeout_test(on); }
 
+lbm_status lbm_debug_damage_canary(lbm_handle h) {
+  if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+  return debug_damage_canary(h->e);
+}
+
 double lbm_bytes_per_fluid_update(int32_t precision) {
   return 2.0 * 9.0 * (double)storage_bytes(precision) + 1.0 / 8.0;
 }

@@ -160,12 +160,20 @@ constexpr int kGraphPairs[4] = {512, 64, 8, 1};
 // to blocks that start as the first ones finish).
 constexpr int kDefaultGridScale = 2;
 constexpr size_t kAlign = 256;
+#ifdef LBM_CHECK_BOUNDS
+constexpr size_t kCanaryBytes = 256;
+#else
+constexpr size_t kCanaryBytes = 0;
+#endif
+constexpr unsigned char kCanaryByte = 0xA5;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Sub-arrays of a member's allocation, as byte offsets.
+// Sub-arrays of a member's allocation, as byte offsets.  The bounds-checked
+// build puts a canary block (kCanaryBytes of kCanaryByte) on each side of
+// the population planes and checks both after every solve.
 struct SlabPlan {
-  size_t f, mask, mask0, fields, u_in, d_out, cells, total;
+  size_t canary_lo, f, canary_hi, mask, mask0, fields, u_in, d_out, cells, total;
 };
 
 SlabPlan plan_slab(const lbm_params& p) {
@@ -175,7 +183,9 @@ SlabPlan plan_slab(const lbm_params& p) {
   const size_t mask_bytes = (size_t)mask_alloc_words((int)wpr, p.ny) * 4;
   SlabPlan s{};
   size_t o = 0;
+  s.canary_lo = o; o += kCanaryBytes;
   s.f = o;      o += align_up(9 * plane * storage_bytes(p.precision));
+  s.canary_hi = o; o += kCanaryBytes;
   s.mask = o;   o += align_up(mask_bytes);
   s.mask0 = o;  o += align_up(mask_bytes);
   s.fields = o; o += 5 * align_up(plane * 4);  // drho, ux, uy, ux_prev, uy_prev
@@ -503,6 +513,7 @@ std::vector<long long> tune_key(const Engine* E) {
 }
 
 lbm_status autotune(Engine* E) {
+  NvtxRange nvtx("lbm_autotune");
   E->tuned = true;
   E->step = shape(E, kStepWarps, kDefaultGridScale);
   if (!autotune_enabled() || debug_sync()) return LBM_OK;
@@ -771,6 +782,12 @@ lbm_status member_create(const lbm_params& p, const uint8_t* cells, cudaStream_t
   m->slab_bytes = s.total;
   char* b = static_cast<char*>(m->slab);
   m->f = b + s.f;
+  m->canary_lo = b + s.canary_lo;
+  m->canary_hi = b + s.canary_hi;
+  if (kCanaryBytes) {
+    CUM(cudaMemsetAsync(m->canary_lo, kCanaryByte, kCanaryBytes, stream));
+    CUM(cudaMemsetAsync(m->canary_hi, kCanaryByte, kCanaryBytes, stream));
+  }
   m->mask_bytes = (size_t)mask_alloc_words(m->wpr, m->ny) * 4;
   m->mask_base = reinterpret_cast<uint32_t*>(b + s.mask);
   m->mask0_base = reinterpret_cast<uint32_t*>(b + s.mask0);
@@ -938,6 +955,7 @@ lbm_status resident_prepare(Engine* E, bool* ok) {
   *ok = false;
   if (E->features != 0 || E->fixed_grid || E->n() == 0 || debug_sync()) return LBM_OK;
   if (!E->rplan_valid) {
+    NvtxRange nvtx("lbm_resident_plan");
     CU(E->rplan.reserve(4 * sizeof(int)));
     if (!E->h_rplan) CU(cudaMallocHost((void**)&E->h_rplan, 4 * sizeof(int)));
     const int* scratch = static_cast<const int*>(E->seg_scratch.p);
@@ -1094,6 +1112,7 @@ lbm_status enqueue_steps_and_reduce(Engine* E, int64_t n_steps, bool with_res) {
   const int K = E->residual_every;
   lbm_status st;
   E->bar_used = false;
+  NvtxRange nvtx("lbm_time_steps");
   CU(cudaEventRecord(E->ev_begin, E->stream));
   bool resident = false;
   if (E->step.persistent == 2 && !debug_sync()) {
@@ -1111,6 +1130,7 @@ lbm_status enqueue_steps_and_reduce(Engine* E, int64_t n_steps, bool with_res) {
   }
   if (!resident && (st = launch_pair(E, 1)) != LBM_OK) return st;
   CU(cudaEventRecord(E->ev_end, E->stream));
+  NvtxRange nvtx_red("lbm_reductions");
   const LatticeView* views = static_cast<const LatticeView*>(E->L.views.p);
   double* partials = static_cast<double*>(E->partials.p);
   if (with_res) {
@@ -1140,6 +1160,7 @@ lbm_status enqueue_solve(Engine* E, int64_t n_steps) {
 }
 
 lbm_status enqueue_exchange(Engine* E, const std::vector<int>& which, const int32_t* n_swap) {
+  NvtxRange nvtx("lbm_exchange");
   const int nx_ = (int)which.size();
   bool all = nx_ == E->n();
   for (int k = 0; all && k < nx_; ++k) all = which[k] == k;
@@ -1174,7 +1195,30 @@ lbm_status enqueue_exchange(Engine* E, const std::vector<int>& which, const int3
   return LBM_OK;
 }
 
+lbm_status check_canaries(Engine* E) {
+  if (!kCanaryBytes) return LBM_OK;
+  std::vector<unsigned char> h(2 * kCanaryBytes);
+  for (int i = 0; i < E->n(); ++i) {
+    const Member* m = E->m[i];
+    CU(cudaMemcpy(h.data(), m->canary_lo, kCanaryBytes, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(h.data() + kCanaryBytes, m->canary_hi, kCanaryBytes, cudaMemcpyDeviceToHost));
+    for (unsigned char c : h)
+      if (c != kCanaryByte)
+        return fail(LBM_ERR_CUDA, "lattice " + std::to_string(i) +
+                                      ": a canary next to the population planes was overwritten");
+  }
+  return LBM_OK;
+}
+
+lbm_status debug_damage_canary(Engine* E) {
+  if (!kCanaryBytes) return fail(LBM_ERR_ARG, "canaries exist only in the bounds-checked build");
+  CU(cudaStreamSynchronize(E->stream));
+  CU(cudaMemset(E->m[0]->canary_hi, 0, 4));
+  return LBM_OK;
+}
+
 lbm_status engine_solve(Engine* E, int64_t n_steps, lbm_solve_result* out) {
+  NvtxRange nvtx("lbm_solve");
   if (n_steps < 2 || (n_steps % 2) != 0) return fail(LBM_ERR_ARG, "n_steps must be even and >= 2");
   lbm_status st = enqueue_solve(E, n_steps);
   if (st != LBM_OK) return st;
@@ -1183,6 +1227,8 @@ lbm_status engine_solve(Engine* E, int64_t n_steps, lbm_solve_result* out) {
   E->solved = true;
   account_steps(E, n_steps);
   if (*E->h_bar_error != 0) return fail(LBM_ERR_TIMEOUT, "step kernel: a bounded device wait gave up");
+  lbm_status cst = check_canaries(E);
+  if (cst != LBM_OK) return cst;
   bool bad = false;
   for (int i = 0; i < E->n(); ++i) {
     fill_result(E, i, out + i);
@@ -1193,6 +1239,7 @@ lbm_status engine_solve(Engine* E, int64_t n_steps, lbm_solve_result* out) {
 }
 
 lbm_status engine_optimize(Engine* E, const int32_t* n_swap, int64_t n_steps, lbm_opt_result* out) {
+  NvtxRange nvtx("lbm_optimize_step");
   if (n_steps < 2 || (n_steps % 2) != 0) return fail(LBM_ERR_ARG, "n_steps must be even and >= 2");
   for (int i = 0; i < E->n(); ++i)
     if (n_swap[i] < 0) return fail(LBM_ERR_ARG, "n_swap must be >= 0");
@@ -1216,6 +1263,8 @@ lbm_status engine_optimize(Engine* E, const int32_t* n_swap, int64_t n_steps, lb
   }
   account_steps(E, n_steps);
   if (*E->h_bar_error != 0) return fail(LBM_ERR_TIMEOUT, "step kernel: a bounded device wait gave up");
+  lbm_status cst = check_canaries(E);
+  if (cst != LBM_OK) return cst;
   for (int i = 0; i < E->n(); ++i) {
     std::memset(out + i, 0, sizeof(lbm_opt_result));
     out[i].n_swapped = E->h_info[8 * i];

@@ -10,12 +10,24 @@
 // the buffers they point to do.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 #include <vector>
 
 #include "lbm_internal.h"
 
 namespace lbm {
+
+// A named range on the host timeline for profilers (NVTX: solve, time
+// steps, reductions, exchange, tuning, resident plan, server tick).  Costs
+// nothing measurable when no profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 lbm_status fail(lbm_status s, const std::string& msg);
 // Every device allocation of the library goes through dev_malloc, so that
@@ -35,6 +47,7 @@ struct Member {
   void* slab = nullptr;
   size_t slab_bytes = 0;
   void* f = nullptr;
+  void *canary_lo = nullptr, *canary_hi = nullptr;  // bounds-checked build: guard blocks around f
   uint32_t *mask_base = nullptr, *mask0_base = nullptr, *mask = nullptr, *mask0 = nullptr;
   size_t mask_bytes = 0;
   float *drho = nullptr, *ux = nullptr, *uy = nullptr, *ux_prev = nullptr, *uy_prev = nullptr;
@@ -164,6 +177,10 @@ lbm_status engine_step_config(Engine* E, int32_t* warps_per_block, int32_t* grid
 lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t persistent, int32_t cells_per_thread,
                                   int32_t stages);
 lbm_status engine_kernel_time(Engine* E, int reset, double* ms, int64_t* launches, int64_t* fluid_updates);
+// Bounds-checked build: overwrite a few bytes of the first member's upper
+// canary (host-side memset within the allocation), so that the next solve
+// reports the damage; LBM_ERR_ARG in the normal build.
+lbm_status debug_damage_canary(Engine* E);
 
 // Copies through which the library moves data between host and device
 // memory: cudaMemcpyAsync / cudaMemcpy2DAsync that also count the bytes

@@ -187,6 +187,7 @@ void lbm_server_s::loop() {
       st.resident_bytes = resident;
       st.peak_resident_bytes = std::max(st.peak_resident_bytes, resident);
     }
+    NvtxRange nvtx("lbm_server_tick");  // admission, exchange, steps, retirement
     const double t_tick = now();
     for (Pending& p : adm) {
       Member* m = nullptr;

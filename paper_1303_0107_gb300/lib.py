@@ -177,6 +177,7 @@ def load_library(path=None):
     L.lbm_debug_fail_alloc.restype = None
     L.lbm_debug_barrier_timeout.argtypes = [ctypes.c_int32]
     L.lbm_debug_barrier_timeout.restype = None
+    L.lbm_debug_damage_canary.argtypes = [H]
     L.lbm_server_destroy.argtypes = [S]
     L.lbm_server_destroy.restype = None
     L.lbm_bytes_per_fluid_update.argtypes = [ctypes.c_int32]
@@ -350,6 +351,10 @@ class Lattice:
         for any other shape, or for resident steps on a set that does not fit."""
         _check(load_library().lbm_set_step_config(self._h, int(warps_per_block), int(persistent),
                                                   int(cells_per_thread), int(stages)), "lbm_set_step_config")
+
+    def debug_damage_canary(self):
+        """Bounds-checked build: overwrite part of a canary next to the populations (test hook)."""
+        _check(load_library().lbm_debug_damage_canary(self._h), "lbm_debug_damage_canary")
 
     def select_swaps(self, drho, ux, uy, n_swap: int):
         arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (drho, ux, uy)]

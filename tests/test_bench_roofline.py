@@ -36,3 +36,15 @@ def test_traffic_is_null_once_the_source_hash_differs(tmp_path, monkeypatch):
     (csrc / "k.cu").write_text("// kernel v2\n")
     assert bench.profiled_traffic("k.cu", "k.md") is None
     assert bench.profiled_traffic("missing.cu", "k.md") is None
+
+
+def test_resident_summary_gives_traffic_per_step_for_its_source():
+    src = os.path.join(ROOT, "paper_1303_0107_gb300", "csrc", "resident.cu")
+    summ = os.path.join(ROOT, "profiles", "resident_tree_2048x1024.md")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    t = bench.profiled_traffic("resident.cu", "resident_tree_2048x1024.md", "dram_bytes_per_step_full_workload")
+    if os.path.exists(summ) and f"source_sha256_16: {h}" in open(summ).read():
+        # the populations stay on chip: far below the 11.5 MB of algorithmic bytes per step
+        assert t is not None and 0 <= t < 1e6
+    else:
+        assert t is None
