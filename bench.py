@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=200.0, help="served leg: Poisson arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="served leg: arrival window")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--log", default=None,
+                    help="write one JSON line per solve of the timed runs (run, iteration, dp, m_in, residual, "
+                         "theta, D_g, outlet flow rates, fluid cells, exchanged cells, time) to this file")
     ap.add_argument("--kernel-case", choices=["tree", "large", "batch", "tree3d", "duct3d"], default=None,
                     help="only create one lattice and run two solves of --kernel-steps steps (for ncu "
                          "captures): tree = 2048 x 1024 distributor, large = 8192 x 4096 channel array, "
@@ -696,12 +699,28 @@ def main():
 
     def one_run(handle):
         handle.reset()
+        t0 = time.perf_counter()
         r = handle.solve(S0)
+        r["wall_s"] = time.perf_counter() - t0
         hist = [r]
         for _ in range(iters):
+            t0 = time.perf_counter()
             r = handle.optimize_step(n_swap, S)
+            r["wall_s"] = time.perf_counter() - t0
             hist.append(r)
         return hist
+
+    log = open(args.log, "w") if (args.log and rank == 0) else None
+
+    def log_run(run, hist):
+        if log is None:
+            return
+        for it, r in enumerate(hist):
+            rec = {"run": run, "iteration": it, "steps": S0 if it == 0 else S, "dp": r["dp"], "m_in": r["m_in"],
+                   "residual": r["residual"], "theta": r["theta"], "dg": r["dg"],
+                   "m_out": [float(x) for x in r["m_out"]], "fluid_cells": r["fluid_cells"],
+                   "n_swapped": r.get("n_swapped", 0), "steps_done": r["steps_done"], "wall_s": r["wall_s"]}
+            log.write(json.dumps(rec) + "\n")
 
     for _ in range(args.warmup):
         one_run(lat)
@@ -715,6 +734,7 @@ def main():
     launches0 = L.kernel_launches()
     ev = []
     last = None
+    runs = []
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)  # evict the lattice from L2 between timed steps (not timed)
@@ -724,11 +744,16 @@ def main():
         last = one_run(lat)
         e1.record(stream)
         ev.append((e0, e1))
+        runs.append(last)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
     launches = L.kernel_launches() - launches0
+    for k, hist in enumerate(runs):  # after the timed region: the log costs it nothing
+        log_run(k, hist)
+    if log is not None:
+        log.close()
     k_ms, k_launches, k_updates = lat.kernel_time()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3

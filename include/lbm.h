@@ -326,22 +326,33 @@ void lbm_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
 lbm_status lbm_kernel_time(lbm_handle h, int reset, double* ms, int64_t* launches,
                            int64_t* fluid_updates);
 
-/* Launch shape the handle's time steps use: warps per block, blocks,
- * persistent = 1 when every run of time steps is one cooperative launch with
- * grid-wide barriers between phases (0: one launch per phase),
- * cells_per_thread = row segments each warp updates at once (1 or 2), and
- * stages = 0 (populations loaded straight into registers) or 2 / 3 (copied
- * into shared memory that many segments ahead of their update).  Tuned on
- * the handle's own lattice at its first solve of 256 steps or more, unless
- * set with lbm_set_step_config.  Any output pointer may be NULL.          */
+/* Launch shape the handle's time steps use: warps per block, blocks, the
+ * launch mode `persistent` -- 0: one launch per phase over the row segments;
+ * 1: every run of time steps in one cooperative launch with grid-wide
+ * barriers between phases; 2: on-chip resident solves (each solve one
+ * cooperative launch, the populations in shared memory, neighbouring blocks
+ * exchanging tagged halo words; plain BGK lattices whose cells fit on the
+ * device); 3: one launch per phase over compacted fluid-cell tasks (32
+ * consecutive fluid cells per warp; plain BGK lattices without a
+ * zero-gradient outlet) -- cells_per_thread = row segments each warp
+ * updates at once (1 or 2), and stages = 0 (populations loaded straight into
+ * registers) or 2 / 3 (copied into shared memory that many segments ahead of
+ * their update).  Tuned on the handle's own lattice at its first solve of
+ * 256 steps or more, unless set with lbm_set_step_config.  Any output
+ * pointer may be NULL.                                                    */
 lbm_status lbm_step_config(lbm_handle h, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
                            int32_t* cells_per_thread, int32_t* stages);
 /* Fix the launch shape (and skip tuning): warps_per_block 4, 8, 12, 16 or
  * 32 with one cell per thread, 4, 8, 12 or 24 with two (32 and 24: one
- * block per SM); 8 or 16 when persistent (8 with two cells per thread); 4, 8 or 16
- * with stages.  cells_per_thread 1 or 2, stages 0, 2 or 3 (staged loads:
- * one cell per thread, not persistent); the grid is sized for the device.  Every shape computes the
- * same values, so this changes timings only.                              */
+ * block per SM); 8 or 16 when persistent = 1 (8 with two cells per thread);
+ * 4, 8 or 16 with stages.  cells_per_thread 1 or 2, stages 0, 2 or 3
+ * (staged loads: one cell per thread, persistent = 0); persistent = 2:
+ * resident solves, the shape follows from the lattice (the other arguments
+ * are ignored); persistent = 3: cell tasks, warps_per_block 4, 8, 12, 16 or
+ * 32, one cell per thread, stages 0.  The grid is sized for the device.
+ * LBM_ERR_ARG for any other shape, or for modes 2 / 3 on lattices they do
+ * not serve.  Every shape computes the same values, so this changes timings
+ * only.                                                                   */
 lbm_status lbm_set_step_config(lbm_handle h, int32_t warps_per_block, int32_t persistent,
                                int32_t cells_per_thread, int32_t stages);
 

@@ -313,6 +313,15 @@ lbm_status launch_pair(Engine* E, int moments) {
   const LatticeView* views = static_cast<const LatticeView*>(E->L.views.p);
   const SegRef* segs = static_cast<const SegRef*>(E->segs.p);
   const int* n_segs = static_cast<const int*>(E->n_segs.p);
+  if (E->step.persistent == 3) {  // compacted fluid-cell tasks (the list is built before any capture)
+    const CellRef* cells = static_cast<const CellRef*>(E->cell_list.p);
+    const int* cpre = static_cast<const int*>(E->cell_scan.p) + std::max(1, E->L.total_seg_words);
+    CU(launch_stream_collide_cells(E->precision, 0, 0, views, cells, n_segs, cpre, E->step, E->stream));
+    DEBUG_SYNC(E, "stream-collide phase A (cell tasks)");
+    CU(launch_stream_collide_cells(E->precision, 1, moments, views, cells, n_segs, cpre, E->step, E->stream));
+    DEBUG_SYNC(E, "stream-collide phase B (cell tasks)");
+    return LBM_OK;
+  }
   CU(launch_stream_collide(E->precision, 0, 0, views, segs, n_segs, E->step, E->stream));
   DEBUG_SYNC(E, "stream-collide phase A");
   CU(launch_stream_collide(E->precision, 1, moments, views, segs, n_segs, E->step, E->stream));
@@ -331,12 +340,15 @@ void drop_graphs(Engine* E) {
 // A captured graph is valid while the buffers and the launch shape it was
 // captured with are unchanged.
 lbm_status ensure_graph(Engine* E, int which) {
-  const void* key[4] = {E->L.views.p, E->segs.p, E->n_segs.p,
-                        reinterpret_cast<const void*>((intptr_t)E->step.warps_per_block << 32 |
-                                                      (intptr_t)(uint32_t)E->step.grid)};
-  if (!std::equal(key, key + 4, E->graph_key)) {
+  const bool cells = E->step.persistent == 3;
+  const void* key[5] = {E->L.views.p, cells ? E->cell_list.p : E->segs.p, E->n_segs.p,
+                        reinterpret_cast<const void*>((intptr_t)E->step.persistent << 56 |
+                                                      (intptr_t)E->step.warps_per_block << 32 |
+                                                      (intptr_t)(uint32_t)E->step.grid),
+                        cells ? E->cell_scan.p : nullptr};
+  if (!std::equal(key, key + 5, E->graph_key)) {
     drop_graphs(E);
-    std::copy(key, key + 4, E->graph_key);
+    std::copy(key, key + 5, E->graph_key);
   }
   if (E->graphs[which]) return LBM_OK;
   cudaGraph_t g = nullptr;
@@ -410,7 +422,7 @@ StepConfig resident_config(const Engine* E) {
 
 lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
   if (E->step.persistent == 2 && !debug_sync()) return run_resident(E, 2 * pairs, -1);
-  if (E->step.persistent && !debug_sync()) return run_persistent(E, pairs);
+  if (E->step.persistent == 1 && !debug_sync()) return run_persistent(E, pairs);
   if (debug_sync()) {
     for (int64_t k = 0; k < pairs; ++k) {
       lbm_status st = launch_pair(E, 0);
@@ -437,6 +449,7 @@ lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
 // warps per block with one cell per thread, 4, 8, 12 or 24 with two; the
 // persistent kernel 8 or 16 (8 with two cells per thread).
 bool step_shape_allowed(int wpb, int cpt, int persistent) {
+  if (persistent == 3) return cpt == 1 && (wpb == 4 || wpb == 8 || wpb == 12 || wpb == 16 || wpb == 32);
   if (persistent) return wpb == 8 || (wpb == 16 && cpt == 1);
   return cpt == 1 ? (wpb == 4 || wpb == 8 || wpb == 12 || wpb == 16 || wpb == 32)
                   : (wpb == 4 || wpb == 8 || wpb == 12 || wpb == 24);
@@ -468,6 +481,23 @@ StepConfig persistent_shape(Engine* E, int wpb, int cpt = 1) {
   c.grid = stream_collide_persistent_grid(E->precision, wpb, cpt);
   c.persistent = 1;
   c.cells_per_thread = cpt;
+  c.stages = 0;
+  c.features = 0;
+  return c;
+}
+
+// The compacted-task shape: one cell per thread, 32 fluid cells a warp.
+StepConfig cells_shape(Engine* E, int wpb, int blocks_per_sm_scale) {
+  const int bps = stream_collide_cells_blocks_per_sm(E->precision, 0, 0, wpb);
+  const long long cap = (long long)E->sm_count * bps * blocks_per_sm_scale;
+  long long fluid = 0;
+  for (const Member* m : E->m) fluid += m->fluid_cells;
+  const long long need = ((fluid + 31) / 32 + wpb - 1) / wpb;
+  StepConfig c;
+  c.warps_per_block = wpb;
+  c.grid = (int)std::max<long long>(1, std::min(need, cap));
+  c.persistent = 3;
+  c.cells_per_thread = 1;
   c.stages = 0;
   c.features = 0;
   return c;
@@ -568,6 +598,18 @@ lbm_status autotune(Engine* E) {
       StepConfig c = persistent_shape(E, 8, cpt);
       if (c.grid > 0) cand.push_back(c);
     }
+  if (cells_eligible(E)) {
+    lbm_status cst = ensure_cells(E);
+    if (cst != LBM_OK) {
+      for (void* b : backups) cudaFree(b);
+      return cst;
+    }
+    for (int wpb : {4, 8, 16, 32})
+      for (int scale : {1, 2}) {
+        if (wpb == 32 && scale != 1) continue;
+        cand.push_back(cells_shape(E, wpb, scale));
+      }
+  }
   if (resident_enabled() && !only_plain) {
     bool ok = false;
     lbm_status st = resident_prepare(E, &ok);
@@ -589,7 +631,7 @@ lbm_status autotune(Engine* E) {
   std::vector<cudaGraphExec_t> tg(cand.size(), nullptr);
   lbm_status st = LBM_OK;
   for (size_t ci = 0; ci < cand.size() && st == LBM_OK; ++ci) {
-    if (cand[ci].persistent) continue;
+    if (cand[ci].persistent == 1 || cand[ci].persistent == 2) continue;  // one launch per run: no graph
     E->step = cand[ci];
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(E->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -612,7 +654,7 @@ lbm_status autotune(Engine* E) {
       cudaEventRecord(a, E->stream);
       if (c.persistent == 2) {
         st = run_resident(E, 2 * kTunePairs, -1);
-      } else if (c.persistent) {
+      } else if (c.persistent == 1) {
         st = run_persistent(E, kTunePairs);
       } else if (cudaGraphLaunch(tg[ci], E->stream) != cudaSuccess) {
         st = fail(LBM_ERR_CUDA, "autotune graph launch");
@@ -623,7 +665,7 @@ lbm_status autotune(Engine* E) {
       if (cudaEventSynchronize(b) != cudaSuccess) st = fail(LBM_ERR_CUDA, "autotune timing");
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, a, b);
-      if (c.persistent && st == LBM_OK) {  // a barrier that gave up would look fast: never pick it
+      if ((c.persistent == 1 || c.persistent == 2) && st == LBM_OK) {  // a barrier that gave up would look fast: never pick it
         int err = 0;
         if (cudaMemcpy(&err, &static_cast<StepBarrier*>(E->bar.p)->error, sizeof(int), cudaMemcpyDeviceToHost) !=
             cudaSuccess)
@@ -890,7 +932,7 @@ Engine::~Engine() {
     for (Member* x : m) delete x;
   for (GrowBuf* b : {&L.views, &L.word_off, &L.seg_word_off, &XL.views, &XL.word_off, &XL.seg_word_off, &segs,
                      &n_segs, &seg_scratch, &partials, &result, &fluid_dev, &n_swap_dev, &dense_f, &oc_buf, &bar,
-                     &best, &rplan, &halo})
+                     &best, &rplan, &halo, &cell_list, &cell_scan})
     b->release();
   if (h_rplan) cudaFreeHost(h_rplan);
   if (h_bar_error) cudaFreeHost(h_bar_error);
@@ -940,6 +982,7 @@ lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool
 
 lbm_status rebuild_worklist(Engine* E) {
   E->rplan_valid = false;
+  E->cells_valid = false;
   if (E->n() == 0) return LBM_OK;
   CU(launch_build_segments(static_cast<const LatticeView*>(E->L.views.p), static_cast<const int*>(E->L.seg_word_off.p),
                            E->n(), E->L.total_seg_words, std::max(1, E->L.total_seg_words),
@@ -948,6 +991,29 @@ lbm_status rebuild_worklist(Engine* E) {
   CU(launch_count_fluid(static_cast<const LatticeView*>(E->L.views.p), static_cast<const int*>(E->L.word_off.p),
                         E->n(), E->L.total_words, static_cast<unsigned long long*>(E->fluid_dev.p), E->stream));
   DEBUG_SYNC(E, "work-list");
+  return LBM_OK;
+}
+
+bool cells_eligible(const Engine* E) {
+  if (E->features != 0 || E->n() == 0 || E->n() >= (1 << kCellLatticeBits) || debug_sync()) return false;
+  for (const Member* m : E->m)
+    if (m->p.outlet == LBM_OUT_NEUMANN) return false;  // its shuffle needs cell nx-2 in the lane to the left
+  return true;
+}
+
+lbm_status ensure_cells(Engine* E) {
+  if (E->cells_valid) return LBM_OK;
+  const int cap = std::max(1, E->L.total_seg_words);
+  long long fluid = 0;
+  for (const Member* m : E->m) fluid += m->fluid_cells;
+  CU(E->cell_scan.reserve((2 * ((size_t)cap + 1) + scan_tmp_ints(cap)) * sizeof(int)));
+  CU(E->cell_list.reserve((size_t)std::max<long long>(1, fluid) * sizeof(CellRef)));
+  int* cnt = static_cast<int*>(E->cell_scan.p);
+  CU(launch_build_cells(static_cast<const LatticeView*>(E->L.views.p), static_cast<const SegRef*>(E->segs.p),
+                        static_cast<const int*>(E->n_segs.p), cap, cnt, cnt + cap, cnt + 2 * ((size_t)cap + 1),
+                        static_cast<CellRef*>(E->cell_list.p), E->stream));
+  DEBUG_SYNC(E, "cell list");
+  E->cells_valid = true;
   return LBM_OK;
 }
 
@@ -1118,6 +1184,10 @@ lbm_status enqueue_steps_and_reduce(Engine* E, int64_t n_steps, bool with_res) {
   if (E->step.persistent == 2 && !debug_sync()) {
     if ((st = resident_prepare(E, &resident)) != LBM_OK) return st;
     if (!resident) E->step = shape(E, kStepWarps, kDefaultGridScale);  // the list outgrew the chip
+  }
+  if (E->step.persistent == 3) {
+    if (!cells_eligible(E)) E->step = shape(E, kStepWarps, kDefaultGridScale);
+    else if ((st = ensure_cells(E)) != LBM_OK) return st;
   }
   if (resident) {
     if ((st = run_resident(E, n_steps, with_res ? (int)(n_steps - K - 1) : -1)) != LBM_OK) return st;
@@ -1429,7 +1499,18 @@ lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t pe
   if (stages != 0 && stages != 2 && stages != 3) return fail(LBM_ERR_ARG, "stages must be 0, 2 or 3");
   if (stages != 0 && (persistent || cells_per_thread != 1))
     return fail(LBM_ERR_ARG, "staged loads take one cell per thread and per-phase launches");
-  if (persistent != 0 && persistent != 1) return fail(LBM_ERR_ARG, "persistent must be 0, 1 or 2");
+  if (persistent == 3) {  // compacted fluid-cell tasks
+    if (!cells_eligible(E))
+      return fail(LBM_ERR_ARG, "cell tasks need plain BGK lattices without a zero-gradient outlet");
+    if (!step_shape_allowed(warps_per_block, 1, 3) || cells_per_thread != 1 || stages != 0)
+      return fail(LBM_ERR_ARG, "cell tasks take one cell per thread and 4, 8, 12, 16 or 32 warps per block");
+    lbm_status st = ensure_cells(E);
+    if (st != LBM_OK) return st;
+    E->step = cells_shape(E, warps_per_block, kDefaultGridScale);
+    E->tuned = true;
+    return LBM_OK;
+  }
+  if (persistent != 0 && persistent != 1) return fail(LBM_ERR_ARG, "persistent must be 0, 1, 2 or 3");
   if (cells_per_thread != 1 && cells_per_thread != 2) return fail(LBM_ERR_ARG, "cells_per_thread must be 1 or 2");
   if (!step_shape_allowed(warps_per_block, cells_per_thread, persistent))
     return fail(LBM_ERR_ARG,

@@ -125,8 +125,14 @@ struct Engine {
   int halo_cap = 0;        // segments the halo buffer holds
   unsigned halo_epoch = 1;
 
+  // compacted fluid-cell tasks (step.persistent == 3): the list and the
+  // per-segment counts / prefix / scan scratch, valid until the work-list is rebuilt
+  GrowBuf cell_list, cell_scan;
+  bool cells_valid = false;
+
   cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};  // 512, 64, 8 and 1 pairs
-  const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};  // views, segs, n_segs, shape
+  // views, segs (or the cell list), n_segs, shape, cell prefix
+  const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   StepConfig step{kStepWarps, 1, 0, 1, 0, 0};
   int features = 0;  // kernel build the members need: 1 collision models, 2 symmetry plane
   bool tuned = false;
@@ -152,6 +158,10 @@ lbm_status rebuild_worklist(Engine* E);
 // Plan the resident launch for the current work-list (synchronises the
 // stream when the list changed since the last plan); *ok: the set fits.
 lbm_status resident_prepare(Engine* E, bool* ok);
+// Compacted fluid-cell tasks: whether the set may use them (plain BGK, no
+// zero-gradient outlet), and the list built for the current work-list.
+bool cells_eligible(const Engine* E);
+lbm_status ensure_cells(Engine* E);
 
 // Enqueue n_steps (even) with moments in the last step, optional residual,
 // and the reductions of every member; results to pinned h_result.  The

@@ -111,13 +111,38 @@ __host__ __device__ inline int find_lattice(const int* off, int n, long long i) 
 struct StepConfig {
   int warps_per_block;  // 4, 8 or 16
   int grid;             // blocks
-  int persistent;       // 1: all pairs of a solve in one cooperative launch
+  int persistent;       // launch mode: 0 one launch per phase over the row segments; 1 all pairs of a
+                        //    solve in one cooperative launch; 2 on-chip resident solve (resident.cu);
+                        //    3 one launch per phase over compacted fluid-cell tasks (32 cells a warp)
   int cells_per_thread; // 1 or 2: row segments per warp task (2: at most 8 warps per block)
   int stages;           // 0: populations loaded into registers; 2 or 3: staged through shared
                         //    memory that many segments ahead (one cell per thread, per-phase launches)
   int features;         // kernel build: bit 0 collision models beyond BGK, bit 1 symmetry plane
                         //    (non-zero: one cell per thread, register loads, per-phase launches)
 };
+// A fluid cell of the compacted task list: c = y * pitch + x in its lattice;
+// meta = lattice | neighbour flags (kNbE..kNbMirror) << 20 | inlet << 29 |
+// outlet << 30.  The list holds a set's fluid cells in segment-list order
+// (lattice, row, x), so a warp's 32 cells are consecutive along x within
+// runs of fluid.
+struct alignas(8) CellRef {
+  int c;
+  unsigned meta;
+};
+constexpr int kCellLatticeBits = 20;
+// Build the compacted list: per-segment fluid counts cnt[capacity] (0 past
+// the list), their exclusive scan cpre[capacity + 1] (cells = cpre[n_segs[0]]),
+// and the cells; tmp holds scan_tmp_ints(capacity) ints.  Needs the segment
+// list and its neighbour flags (launch_build_segments).
+cudaError_t launch_build_cells(const LatticeView* views, const SegRef* segs, const int* n_segs, int capacity,
+                               int* cnt, int* cpre, int* tmp, CellRef* cells, cudaStream_t stream);
+// One phase over the compacted list (sc.warps_per_block, sc.grid; one cell
+// per thread), a programmatic dependent launch like launch_stream_collide.
+// Plain BGK lattices without a zero-gradient outlet only.
+cudaError_t launch_stream_collide_cells(int precision, int phase, int moments, const LatticeView* views,
+                                        const CellRef* cells, const int* n_segs, const int* cpre, StepConfig sc,
+                                        cudaStream_t stream);
+int stream_collide_cells_blocks_per_sm(int precision, int phase, int moments, int warps_per_block);
 // Grid barrier state of the persistent kernel (device memory, 16 bytes).
 struct StepBarrier {
   unsigned count;  // arrivals since the launch began

@@ -331,6 +331,75 @@ __global__ void __launch_bounds__(max_step_threads(CPT), 1)
 }
 
 
+// ---- compacted tasks: 32 consecutive fluid cells per warp ----------------
+//
+// On lattices of narrow channels a row segment holds few fluid cells (a
+// quarter to a third of the lanes idle on the batched candidates), and its
+// partly used 32-byte sectors cost DRAM bytes.  Here a warp takes 32
+// consecutive entries of the set's fluid-cell list: every lane has a cell,
+// and the cells run along x within each run of fluid, so the plane accesses
+// stay contiguous pieces.  The per-cell work is that of the segment kernel
+// (seg_load, seg_update) with the cell's offset and neighbour flags from its
+// list entry.
+template <class T, int PHASE, int MOM>
+__global__ void __launch_bounds__(1024, 1)
+    k_stream_collide_cells(const LatticeView* __restrict__ views, const CellRef* __restrict__ cells,
+                           const int* __restrict__ n_segs, const int* __restrict__ cpre) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  const int ncell = cpre[n_segs[0]];
+  const int ntask = (ncell + 31) >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int stride = gridDim.x * wpb;
+  bool waited = false;
+  for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < ntask; t += stride) {
+    const int e = (t << 5) + lane;
+    const bool valid = e < ncell;
+    const CellRef cr = cells[valid ? e : 0];
+    const LatticeView* __restrict__ L = views + (cr.meta & ((1u << kCellLatticeBits) - 1u));
+    SegCtx<T> s;
+    s.L = L;
+    s.F = static_cast<T*>(L->f);
+    s.pitch = L->pitch;
+    s.pl = (int)L->plane;
+    s.fe = L->f_elems;
+    s.rho0 = L->rho0;
+    s.omega = L->omega;
+    s.rule = L->outlet_rule;
+    s.c = cr.c;
+    s.nb = (cr.meta >> kCellLatticeBits) & 0x1ffu;
+    s.fluid = valid;
+    s.inlet = valid && ((cr.meta >> 29) & 1u);
+    s.outlet = valid && ((cr.meta >> 30) & 1u);
+    s.y = s.inlet ? cr.c / s.pitch : 0;  // the inlet rule looks up the row's speed
+    if (!waited) {  // warp-uniform: populations of the previous step are final from here on
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      waited = true;
+    }
+    float g[9];
+    seg_load<T, PHASE, false, 0>(s, g);
+    seg_update<T, PHASE, MOM, 0>(s, g);
+  }
+  if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <class T>
+void* pick_cells(int phase, int moments) {
+  if (phase == 0) return (void*)k_stream_collide_cells<T, 0, 0>;
+  if (moments == 1) return (void*)k_stream_collide_cells<T, 1, 1>;
+  if (moments == 2) return (void*)k_stream_collide_cells<T, 1, 2>;
+  return (void*)k_stream_collide_cells<T, 1, 0>;
+}
+
+void* cells_kernel_for(int precision, int phase, int moments) {
+  switch (precision) {
+    case LBM_F32: return pick_cells<float>(phase, moments);
+    case LBM_BF16_SHIFTED: return pick_cells<__nv_bfloat16>(phase, moments);
+    case LBM_F16_SHIFTED: return pick_cells<__half>(phase, moments);
+    default: return nullptr;
+  }
+}
+
 // ---- staged variant: populations copied into shared memory ahead of use ----
 //
 // Each warp keeps NS stages of one row segment each in shared memory (nine
@@ -625,6 +694,33 @@ cudaError_t launch_stream_collide(int precision, int phase, int moments, const L
   cudaError_t e = cudaLaunchKernelExC(&cfg, k, args);
   if (e == cudaSuccess) count_launches(1);
   return e;
+}
+
+cudaError_t launch_stream_collide_cells(int precision, int phase, int moments, const LatticeView* views,
+                                        const CellRef* cells, const int* n_segs, const int* cpre, StepConfig sc,
+                                        cudaStream_t stream) {
+  void* k = cells_kernel_for(precision, phase, moments);
+  if (!k || sc.warps_per_block < 1 || sc.warps_per_block > 32 || sc.grid < 1) return cudaErrorInvalidValue;
+  void* args[] = {(void*)&views, (void*)&cells, (void*)&n_segs, (void*)&cpre};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sc.grid);
+  cfg.blockDim = dim3(32 * sc.warps_per_block);
+  cfg.stream = stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, k, args);
+  if (e == cudaSuccess) count_launches(1);
+  return e;
+}
+
+int stream_collide_cells_blocks_per_sm(int precision, int phase, int moments, int warps_per_block) {
+  void* k = cells_kernel_for(precision, phase, moments);
+  int n = 0;
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, 0) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
 }
 
 int stream_collide_persistent_grid(int precision, int warps_per_block, int cells_per_thread) {

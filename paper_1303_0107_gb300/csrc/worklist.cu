@@ -211,6 +211,45 @@ __global__ void k_rho_from_drho(const float* __restrict__ drho, float rho0,
   rho[i] = solid ? 0.0f : rho0 + drho[(size_t)y * pitch + x];
 }
 
+// Fluid cells of list segment q into cnt[q] (0 past the list).
+__global__ void k_segment_cell_counts(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
+                                      const int* __restrict__ n_segs, int capacity, int* __restrict__ cnt) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= capacity) return;
+  int c = 0;
+  if (q < n_segs[0]) {
+    const SegRef sr = segs[q];
+    const LatticeView& L = views[sr.lattice];
+    const int y = sr.yw >> kSegWordBits, w = sr.yw & ((1 << kSegWordBits) - 1);
+    c = __popc(~L.mask[(long long)y * mask_stride(L.wpr) + w]);  // bits past nx are set: solid
+  }
+  cnt[q] = c;
+}
+
+// The compacted list: one warp per segment, each fluid lane writes its entry
+// at cpre[q] + (fluid lanes below it).
+__global__ void k_scatter_cells(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
+                                const int* __restrict__ n_segs, const int* __restrict__ cpre,
+                                CellRef* __restrict__ cells) {
+  const int lane = threadIdx.x & 31;
+  const int nseg = n_segs[0];
+  const uint16_t* nbs = segment_flags(segs, n_segs);
+  const int stride = (gridDim.x * blockDim.x) >> 5;
+  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nseg; q += stride) {
+    const SegRef sr = segs[q];
+    const LatticeView& L = views[sr.lattice];
+    const int y = sr.yw >> kSegWordBits, w = sr.yw & ((1 << kSegWordBits) - 1);
+    const uint32_t fl = ~L.mask[(long long)y * mask_stride(L.wpr) + w];
+    if (!((fl >> lane) & 1u)) continue;
+    const int x = (w << 5) + lane;
+    CellRef r;
+    r.c = y * L.pitch + x;
+    r.meta = (unsigned)sr.lattice | ((unsigned)nbs[(long long)q * 32 + lane] << kCellLatticeBits) |
+             (x == 0 ? 1u << 29 : 0u) | (x == L.nx - 1 ? 1u << 30 : 0u);
+    cells[cpre[q] + __popc(fl & ((1u << lane) - 1u))] = r;
+  }
+}
+
 inline int blocks_for(long long n, int threads) {
   const long long b = (n + threads - 1) / threads;
   return (int)(b > 0 ? b : 1);
@@ -273,6 +312,17 @@ cudaError_t launch_build_segments(const LatticeView* views, const int* seg_word_
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_segment_flags16<<<blocks_for((long long)total * 32, 256), 256, 0, stream>>>(
       views, segs, n_segs, reinterpret_cast<uint16_t*>(segs + capacity));
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_cells(const LatticeView* views, const SegRef* segs, const int* n_segs, int capacity,
+                               int* cnt, int* cpre, int* tmp, CellRef* cells, cudaStream_t stream) {
+  k_segment_cell_counts<<<blocks_for(capacity, 256), 256, 0, stream>>>(views, segs, n_segs, capacity, cnt);
+  count_launches(1);
+  cudaError_t e = launch_scan(cnt, cpre, capacity, tmp, stream);
+  if (e != cudaSuccess) return e;
+  k_scatter_cells<<<blocks_for((long long)capacity * 32, 256), 256, 0, stream>>>(views, segs, n_segs, cpre, cells);
   count_launches(1);
   return cudaGetLastError();
 }

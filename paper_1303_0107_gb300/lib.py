@@ -347,8 +347,9 @@ class Lattice:
         16 or 32 with one cell per thread, 4, 8, 12 or 24 with two; persistent 8 or 16 (8 with two
         cells); stages 0 (register loads) or 2 / 3 (shared-memory staging, one cell per thread, 4-16
         warps); persistent=2: on-chip resident steps (the shape follows from the lattice; the
-        other arguments are ignored).  Every shape computes the same values; LbmError (status 1)
-        for any other shape, or for resident steps on a set that does not fit."""
+        other arguments are ignored); persistent=3: compacted fluid-cell tasks (one cell per
+        thread, 4-32 warps).  Every shape computes the same values; LbmError (status 1) for any
+        other shape, or for modes 2 / 3 on lattices they do not serve."""
         _check(load_library().lbm_set_step_config(self._h, int(warps_per_block), int(persistent),
                                                   int(cells_per_thread), int(stages)), "lbm_set_step_config")
 

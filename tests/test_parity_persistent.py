@@ -171,3 +171,53 @@ def test_barrier_wait_gives_up_and_the_handle_stays_usable():
     h.reset()
     assert h.solve(200)["dp"] == r_ref["dp"]
     h.close()
+
+
+@pytest.mark.parametrize("precision", [L.F32, L.BF16_SHIFTED, L.F16_SHIFTED])
+@pytest.mark.parametrize("k", [0, 2, 3])
+def test_cell_tasks_compute_the_same_values(k, precision):
+    """Compacted fluid-cell tasks (32 consecutive fluid cells per warp)
+    against the default row-segment shape, bit for bit, through exchanges
+    (the cell list is rebuilt with the work-list)."""
+    case = _cases()[k]
+    a = _handle(case, precision, False)
+    b = _handle(case, precision, False)
+    b.set_step_config(8, persistent=3)
+    assert b.step_config()[2] == 3
+    ra, rb = a.solve(600), b.solve(600)
+    assert ra["dp"] == rb["dp"] and ra["residual"] == rb["residual"]
+    assert np.array_equal(a.read(L.FIELD_POPS), b.read(L.FIELD_POPS))
+    fl = int((case["cells"] == 0).sum())
+    for _ in range(2):
+        oa, ob = a.optimize_step(max(1, fl // 200), 300), b.optimize_step(max(1, fl // 200), 300)
+        assert oa["dp"] == ob["dp"] and oa["n_swapped"] == ob["n_swapped"]
+    for f in (L.FIELD_MASK, L.FIELD_UX, L.FIELD_UY, L.FIELD_DRHO, L.FIELD_POPS):
+        assert np.array_equal(a.read(f), b.read(f)), f
+    a.close()
+    b.close()
+
+
+def test_cell_tasks_in_a_batch_and_where_refused():
+    members = [c for c in _cases() if c.get("outlet", 0) == 0]
+    a = L.Batch(members, residual_every=0)
+    b = L.Batch(members, residual_every=0)
+    a.set_step_config(8, persistent=False)
+    b.set_step_config(16, persistent=3)
+    ra, rb = a.solve(400), b.solve(400)
+    assert [x["dp"] for x in ra] == [x["dp"] for x in rb]
+    n = [3, 1, 4][:len(members)]
+    oa, ob = a.optimize_step(n, 200), b.optimize_step(n, 200)
+    assert [x["dp"] for x in oa] == [x["dp"] for x in ob]
+    for i in range(len(members)):
+        assert np.array_equal(a.read(i, L.FIELD_POPS), b.read(i, L.FIELD_POPS)), i
+    a.close()
+    b.close()
+    neumann = _handle(_cases()[1], L.F32, False)  # a zero-gradient outlet: refused
+    with pytest.raises(L.LbmError) as e:
+        neumann.set_step_config(8, persistent=3)
+    assert e.value.status == 1
+    neumann.close()
+    m = _handle(_mirror_case(), L.F32, False)  # a symmetry plane: refused
+    with pytest.raises(L.LbmError):
+        m.set_step_config(8, persistent=3)
+    m.close()
