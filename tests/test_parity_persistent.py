@@ -139,7 +139,7 @@ def test_batch_shapes_equal_default_batch(shape):
 def test_set_step_config_errors():
     t = I.config_t_junction()
     h = L.Lattice(t["cells"], t["tau"], t["u_max"])
-    for wpb, pers, cpt, stg in ((3, 0, 1, 0), (64, 0, 1, 0), (24, 0, 1, 0), (32, 0, 2, 0), (4, 1, 1, 0), (8, 3, 1, 0),
+    for wpb, pers, cpt, stg in ((3, 0, 1, 0), (64, 0, 1, 0), (24, 0, 1, 0), (32, 0, 2, 0), (4, 1, 1, 0), (8, 5, 1, 0),
                                 (8, 0, 3, 0), (16, 0, 2, 0), (24, 1, 2, 0), (32, 1, 1, 0), (32, 0, 1, 2), (8, 1, 0, 0),
                                 (8, 0, 1, 1), (8, 0, 1, 4), (8, 1, 1, 2), (8, 0, 2, 3)):
         with pytest.raises(L.LbmError) as e:

@@ -233,10 +233,14 @@ def test_odd_widths(ora, nx, outlet):
     lat.close()
 
 
-@pytest.mark.parametrize("prec", ["bf16", "f16"])
-def test_reduced_precision_storage_error_reported(ora, prec):
-    """16-bit shifted storage: errors against the FP64 oracle are reported; the
-    bound here only guards against gross failure (a wrong layout or type)."""
+@pytest.mark.parametrize("prec,bound", [("bf16", 0.3), ("f16", 1e-2)])
+def test_reduced_precision_storage_error_reported(ora, prec, bound):
+    """16-bit shifted storage: errors against the FP64 oracle are reported, not
+    held to the FP32 bar.  On the strongly compressible 128 x 64 T (u_max
+    0.05, 2000 steps) the measured relative pressure-drop errors are 0.155
+    (BF16, 8 significant bits) and 3.5e-3 (FP16, 11 bits); the bounds are
+    twice those (three times for FP16), so a layout or type slip -- an error
+    of order one -- fails while the rounding of 16-bit storage passes."""
     cfg = I.config_t_junction()
     lat = L.Lattice(cfg["cells"], cfg["tau"], cfg["u_max"], precision=prec)
     g = lat.solve(cfg["steps"])
@@ -244,7 +248,7 @@ def test_reduced_precision_storage_error_reported(ora, prec):
     o = ora.Solver(p, cfg["cells"]).solve(cfg["steps"])
     rel = abs(g["dp"] - o["dp"]) / abs(o["dp"])
     print(f"{prec}: relative dp error {rel:.3e}")
-    assert np.isfinite(g["dp"]) and rel < 0.5
+    assert np.isfinite(g["dp"]) and rel < bound
 
 
 def test_failed_allocation_is_reported_and_recoverable():
