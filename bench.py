@@ -79,6 +79,8 @@ def parse():
                     help="kernel case (2D): run with this many cells per thread (0: the tuner's choice)")
     ap.add_argument("--kernel-resident", action="store_true",
                     help="kernel case (2D): on-chip resident steps (one launch per solve)")
+    ap.add_argument("--kernel-paired", action="store_true",
+                    help="kernel case (2D, batch): paired tasks (interior 64-cell windows two cells a lane)")
     return ap.parse_args()
 
 
@@ -105,6 +107,8 @@ def kernel_case(args):
         cands = I.config_candidates(256)
         b = L.Batch([dict(cells=c["cells"], tau=c["tau"], u_max=c["u_max"]) for c in cands], precision=prec,
                     residual_every=0)
+        if args.kernel_paired:
+            b.set_step_config(8, persistent=4, cells_per_thread=2)
         b.solve(args.kernel_steps)
         r = b.solve(args.kernel_steps)
         shape = b.step_config()
@@ -121,6 +125,8 @@ def kernel_case(args):
     lat = L.Lattice(cells, tau, u_max, precision=prec, residual_every=0)
     if args.kernel_resident:
         lat.set_step_config(8, persistent=2)
+    elif args.kernel_paired:
+        lat.set_step_config(8, persistent=4, cells_per_thread=2)
     elif args.kernel_cpt:
         lat.set_step_config(8, cells_per_thread=args.kernel_cpt)
     lat.solve(args.kernel_steps)

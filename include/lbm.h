@@ -307,6 +307,15 @@ void lbm_debug_barrier_timeout(int32_t on);
  * reports it.  LBM_ERR_ARG in the normal build, which has no canaries.    */
 lbm_status lbm_debug_damage_canary(lbm_handle h);
 
+/* Sizes of the handle's task lists (builds them if needed; synchronises the
+ * handle's stream): *segments = row segments holding a fluid cell (the work
+ * of launch mode 0), *windows = interior windows of 64 cells among them
+ * (row y, cells 64p .. 64p+63, p >= 0, with rows y-1..y+1 fluid over cells
+ * 64p-1 .. 64p+64; the columns beyond the lattice count as solid), which
+ * launch mode 4 takes two cells a lane.  0 windows on lattices with a
+ * symmetry plane.  Either pointer may be NULL.                            */
+lbm_status lbm_debug_task_counts(lbm_handle h, int32_t* segments, int32_t* windows);
+
 /* Number of device kernels this process has launched through the library
  * (graph launches count every kernel node).                             */
 uint64_t lbm_kernel_launches(void);
@@ -334,7 +343,10 @@ lbm_status lbm_kernel_time(lbm_handle h, int reset, double* ms, int64_t* launche
  * exchanging tagged halo words; plain BGK lattices whose cells fit on the
  * device); 3: one launch per phase over compacted fluid-cell tasks (32
  * consecutive fluid cells per warp; plain BGK lattices without a
- * zero-gradient outlet) -- cells_per_thread = row segments each warp
+ * zero-gradient outlet); 4: one launch per phase over paired tasks (a warp
+ * takes each interior window of 64 cells -- cells and neighbours all fluid
+ * -- two cells a lane with paired loads and stores, and every other row
+ * segment as in mode 0; plain BGK lattices) -- cells_per_thread = row segments each warp
  * updates at once (1 or 2), and stages = 0 (populations loaded straight into
  * registers) or 2 / 3 (copied into shared memory that many segments ahead of
  * their update).  Tuned on the handle's own lattice at its first solve of
@@ -349,9 +361,10 @@ lbm_status lbm_step_config(lbm_handle h, int32_t* warps_per_block, int32_t* grid
  * (staged loads: one cell per thread, persistent = 0); persistent = 2:
  * resident solves, the shape follows from the lattice (the other arguments
  * are ignored); persistent = 3: cell tasks, warps_per_block 4, 8, 12, 16 or
- * 32, one cell per thread, stages 0.  The grid is sized for the device.
- * LBM_ERR_ARG for any other shape, or for modes 2 / 3 on lattices they do
- * not serve.  Every shape computes the same values, so this changes timings
+ * 32, one cell per thread, stages 0; persistent = 4: paired tasks,
+ * warps_per_block 4, 8, 12 or 24, cells_per_thread 2, stages 0.  The grid is
+ * sized for the device.  LBM_ERR_ARG for any other shape, or for modes 2 - 4
+ * on lattices they do not serve.  Every shape computes the same values, so this changes timings
  * only.                                                                   */
 lbm_status lbm_set_step_config(lbm_handle h, int32_t warps_per_block, int32_t persistent,
                                int32_t cells_per_thread, int32_t stages);

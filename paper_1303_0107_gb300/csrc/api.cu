@@ -58,6 +58,11 @@ lbm_status lbm_debug_damage_canary(lbm_handle h) {
   return debug_damage_canary(h->e);
 }
 
+lbm_status lbm_debug_task_counts(lbm_handle h, int32_t* segments, int32_t* windows) {
+  if (!h) return fail(LBM_ERR_ARG, "NULL handle");
+  return debug_task_counts(h->e, segments, windows);
+}
+
 double lbm_bytes_per_fluid_update(int32_t precision) {
   return 2.0 * 9.0 * (double)storage_bytes(precision) + 1.0 / 8.0;
 }

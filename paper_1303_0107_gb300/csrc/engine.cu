@@ -322,6 +322,15 @@ lbm_status launch_pair(Engine* E, int moments) {
     DEBUG_SYNC(E, "stream-collide phase B (cell tasks)");
     return LBM_OK;
   }
+  if (E->step.persistent == 4) {  // paired tasks (the list is built before any capture)
+    const SegRef* tasks = static_cast<const SegRef*>(E->pair_list.p);
+    const int* n_tasks = static_cast<const int*>(E->pair_scan.p) + 2 * (size_t)std::max(1, E->L.total_seg_words);
+    CU(launch_stream_collide_pairs(E->precision, 0, 0, views, tasks, n_tasks, E->step, E->stream));
+    DEBUG_SYNC(E, "stream-collide phase A (paired tasks)");
+    CU(launch_stream_collide_pairs(E->precision, 1, moments, views, tasks, n_tasks, E->step, E->stream));
+    DEBUG_SYNC(E, "stream-collide phase B (paired tasks)");
+    return LBM_OK;
+  }
   CU(launch_stream_collide(E->precision, 0, 0, views, segs, n_segs, E->step, E->stream));
   DEBUG_SYNC(E, "stream-collide phase A");
   CU(launch_stream_collide(E->precision, 1, moments, views, segs, n_segs, E->step, E->stream));
@@ -340,12 +349,12 @@ void drop_graphs(Engine* E) {
 // A captured graph is valid while the buffers and the launch shape it was
 // captured with are unchanged.
 lbm_status ensure_graph(Engine* E, int which) {
-  const bool cells = E->step.persistent == 3;
-  const void* key[5] = {E->L.views.p, cells ? E->cell_list.p : E->segs.p, E->n_segs.p,
+  const bool cells = E->step.persistent == 3, paired = E->step.persistent == 4;
+  const void* key[5] = {E->L.views.p, cells ? E->cell_list.p : paired ? E->pair_list.p : E->segs.p, E->n_segs.p,
                         reinterpret_cast<const void*>((intptr_t)E->step.persistent << 56 |
                                                       (intptr_t)E->step.warps_per_block << 32 |
                                                       (intptr_t)(uint32_t)E->step.grid),
-                        cells ? E->cell_scan.p : nullptr};
+                        cells ? E->cell_scan.p : paired ? E->pair_scan.p : nullptr};
   if (!std::equal(key, key + 5, E->graph_key)) {
     drop_graphs(E);
     std::copy(key, key + 5, E->graph_key);
@@ -450,6 +459,7 @@ lbm_status run_plain_pairs(Engine* E, int64_t pairs) {
 // persistent kernel 8 or 16 (8 with two cells per thread).
 bool step_shape_allowed(int wpb, int cpt, int persistent) {
   if (persistent == 3) return cpt == 1 && (wpb == 4 || wpb == 8 || wpb == 12 || wpb == 16 || wpb == 32);
+  if (persistent == 4) return cpt == 2 && (wpb == 4 || wpb == 8 || wpb == 12 || wpb == 24);
   if (persistent) return wpb == 8 || (wpb == 16 && cpt == 1);
   return cpt == 1 ? (wpb == 4 || wpb == 8 || wpb == 12 || wpb == 16 || wpb == 32)
                   : (wpb == 4 || wpb == 8 || wpb == 12 || wpb == 24);
@@ -498,6 +508,23 @@ StepConfig cells_shape(Engine* E, int wpb, int blocks_per_sm_scale) {
   c.grid = (int)std::max<long long>(1, std::min(need, cap));
   c.persistent = 3;
   c.cells_per_thread = 1;
+  c.stages = 0;
+  c.features = 0;
+  return c;
+}
+
+// The paired-task shape: two cells a lane on interior windows, one segment
+// a warp elsewhere; at most one task per warp of the grid, the segment list
+// bounding the tasks.
+StepConfig pairs_shape(Engine* E, int wpb, int blocks_per_sm_scale) {
+  const int bps = stream_collide_pairs_blocks_per_sm(E->precision, 0, 0, wpb);
+  const long long cap = (long long)E->sm_count * bps * blocks_per_sm_scale;
+  const long long need = ((long long)E->L.total_seg_words + wpb - 1) / wpb;
+  StepConfig c;
+  c.warps_per_block = wpb;
+  c.grid = (int)(E->fixed_grid ? cap : std::max<long long>(1, std::min(need, cap)));
+  c.persistent = 4;
+  c.cells_per_thread = 2;
   c.stages = 0;
   c.features = 0;
   return c;
@@ -608,6 +635,18 @@ lbm_status autotune(Engine* E) {
       for (int scale : {1, 2}) {
         if (wpb == 32 && scale != 1) continue;
         cand.push_back(cells_shape(E, wpb, scale));
+      }
+  }
+  if (pairs_eligible(E)) {
+    lbm_status pst = ensure_pairs(E);
+    if (pst != LBM_OK) {
+      for (void* b : backups) cudaFree(b);
+      return pst;
+    }
+    for (int wpb : {4, 8, 12, 24})
+      for (int scale : {1, 2}) {
+        if (wpb == 24 && scale != 1) continue;
+        cand.push_back(pairs_shape(E, wpb, scale));
       }
   }
   if (resident_enabled() && !only_plain) {
@@ -983,6 +1022,7 @@ lbm_status engine_new(int precision, int residual_every, void* cuda_stream, bool
 lbm_status rebuild_worklist(Engine* E) {
   E->rplan_valid = false;
   E->cells_valid = false;
+  E->pairs_valid = false;
   if (E->n() == 0) return LBM_OK;
   CU(launch_build_segments(static_cast<const LatticeView*>(E->L.views.p), static_cast<const int*>(E->L.seg_word_off.p),
                            E->n(), E->L.total_seg_words, std::max(1, E->L.total_seg_words),
@@ -1014,6 +1054,24 @@ lbm_status ensure_cells(Engine* E) {
                         static_cast<CellRef*>(E->cell_list.p), E->stream));
   DEBUG_SYNC(E, "cell list");
   E->cells_valid = true;
+  return LBM_OK;
+}
+
+bool pairs_eligible(const Engine* E) {
+  return E->features == 0 && E->n() > 0 && E->n() < kPairTask;
+}
+
+lbm_status ensure_pairs(Engine* E) {
+  if (E->pairs_valid) return LBM_OK;
+  const int cap = std::max(1, E->L.total_seg_words);
+  CU(E->pair_scan.reserve((2 * (size_t)cap + 1 + scan_tmp_ints(cap)) * sizeof(int)));
+  CU(E->pair_list.reserve((size_t)cap * sizeof(SegRef)));
+  int* emit = static_cast<int*>(E->pair_scan.p);
+  CU(launch_build_pairs(static_cast<const LatticeView*>(E->L.views.p), static_cast<const SegRef*>(E->segs.p),
+                        static_cast<const int*>(E->n_segs.p), cap, emit, emit + cap, emit + 2 * (size_t)cap + 1,
+                        static_cast<SegRef*>(E->pair_list.p), E->stream));
+  DEBUG_SYNC(E, "paired list");
+  E->pairs_valid = true;
   return LBM_OK;
 }
 
@@ -1189,6 +1247,10 @@ lbm_status enqueue_steps_and_reduce(Engine* E, int64_t n_steps, bool with_res) {
     if (!cells_eligible(E)) E->step = shape(E, kStepWarps, kDefaultGridScale);
     else if ((st = ensure_cells(E)) != LBM_OK) return st;
   }
+  if (E->step.persistent == 4) {
+    if (!pairs_eligible(E)) E->step = shape(E, kStepWarps, kDefaultGridScale);
+    else if ((st = ensure_pairs(E)) != LBM_OK) return st;
+  }
   if (resident) {
     if ((st = run_resident(E, n_steps, with_res ? (int)(n_steps - K - 1) : -1)) != LBM_OK) return st;
   } else if (with_res) {
@@ -1277,6 +1339,27 @@ lbm_status check_canaries(Engine* E) {
         return fail(LBM_ERR_CUDA, "lattice " + std::to_string(i) +
                                       ": a canary next to the population planes was overwritten");
   }
+  return LBM_OK;
+}
+
+lbm_status debug_task_counts(Engine* E, int32_t* segments, int32_t* windows) {
+  int32_t n[2] = {0, 0};  // list segments, paired tasks
+  if (E->n() > 0) {
+    const bool paired = pairs_eligible(E);
+    if (paired) {
+      lbm_status st = ensure_pairs(E);
+      if (st != LBM_OK) return st;
+    }
+    CU(xfer(&n[0], E->n_segs.p, sizeof(int32_t), cudaMemcpyDeviceToHost, E->stream));
+    if (paired)
+      CU(xfer(&n[1], static_cast<const int*>(E->pair_scan.p) + 2 * (size_t)std::max(1, E->L.total_seg_words),
+              sizeof(int32_t), cudaMemcpyDeviceToHost, E->stream));
+    else
+      n[1] = n[0];
+    CU(cudaStreamSynchronize(E->stream));
+  }
+  if (segments) *segments = n[0];
+  if (windows) *windows = n[0] - n[1];  // each window merges two list segments into one task
   return LBM_OK;
 }
 
@@ -1510,7 +1593,17 @@ lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t pe
     E->tuned = true;
     return LBM_OK;
   }
-  if (persistent != 0 && persistent != 1) return fail(LBM_ERR_ARG, "persistent must be 0, 1, 2 or 3");
+  if (persistent == 4) {  // paired tasks
+    if (!pairs_eligible(E)) return fail(LBM_ERR_ARG, "paired tasks need plain BGK lattices");
+    if (!step_shape_allowed(warps_per_block, cells_per_thread, 4) || stages != 0)
+      return fail(LBM_ERR_ARG, "paired tasks take two cells per thread and 4, 8, 12 or 24 warps per block");
+    lbm_status st = ensure_pairs(E);
+    if (st != LBM_OK) return st;
+    E->step = pairs_shape(E, warps_per_block, kDefaultGridScale);
+    E->tuned = true;
+    return LBM_OK;
+  }
+  if (persistent != 0 && persistent != 1) return fail(LBM_ERR_ARG, "persistent must be 0, 1, 2, 3 or 4");
   if (cells_per_thread != 1 && cells_per_thread != 2) return fail(LBM_ERR_ARG, "cells_per_thread must be 1 or 2");
   if (!step_shape_allowed(warps_per_block, cells_per_thread, persistent))
     return fail(LBM_ERR_ARG,

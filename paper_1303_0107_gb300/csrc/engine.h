@@ -129,9 +129,14 @@ struct Engine {
   // per-segment counts / prefix / scan scratch, valid until the work-list is rebuilt
   GrowBuf cell_list, cell_scan;
   bool cells_valid = false;
+  // paired tasks (step.persistent == 4): the list and its emit flags /
+  // offsets / scan scratch (the count in offsets[capacity]), valid until the
+  // work-list is rebuilt
+  GrowBuf pair_list, pair_scan;
+  bool pairs_valid = false;
 
   cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};  // 512, 64, 8 and 1 pairs
-  // views, segs (or the cell list), n_segs, shape, cell prefix
+  // views, segs (or the cell or paired list), n_segs, shape, cell prefix (or paired count)
   const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   StepConfig step{kStepWarps, 1, 0, 1, 0, 0};
   int features = 0;  // kernel build the members need: 1 collision models, 2 symmetry plane
@@ -162,6 +167,8 @@ lbm_status resident_prepare(Engine* E, bool* ok);
 // zero-gradient outlet), and the list built for the current work-list.
 bool cells_eligible(const Engine* E);
 lbm_status ensure_cells(Engine* E);
+bool pairs_eligible(const Engine* E);
+lbm_status ensure_pairs(Engine* E);
 
 // Enqueue n_steps (even) with moments in the last step, optional residual,
 // and the reductions of every member; results to pinned h_result.  The
@@ -191,6 +198,7 @@ lbm_status engine_kernel_time(Engine* E, int reset, double* ms, int64_t* launche
 // canary (host-side memset within the allocation), so that the next solve
 // reports the damage; LBM_ERR_ARG in the normal build.
 lbm_status debug_damage_canary(Engine* E);
+lbm_status debug_task_counts(Engine* E, int32_t* segments, int32_t* windows);
 
 // Copies through which the library moves data between host and device
 // memory: cudaMemcpyAsync / cudaMemcpy2DAsync that also count the bytes

@@ -113,7 +113,9 @@ struct StepConfig {
   int grid;             // blocks
   int persistent;       // launch mode: 0 one launch per phase over the row segments; 1 all pairs of a
                         //    solve in one cooperative launch; 2 on-chip resident solve (resident.cu);
-                        //    3 one launch per phase over compacted fluid-cell tasks (32 cells a warp)
+                        //    3 one launch per phase over compacted fluid-cell tasks (32 cells a warp);
+                        //    4 one launch per phase over paired tasks (interior 64-cell windows, two
+                        //    cells a lane, and the other segments)
   int cells_per_thread; // 1 or 2: row segments per warp task (2: at most 8 warps per block)
   int stages;           // 0: populations loaded into registers; 2 or 3: staged through shared
                         //    memory that many segments ahead (one cell per thread, per-phase launches)
@@ -143,6 +145,23 @@ cudaError_t launch_stream_collide_cells(int precision, int phase, int moments, c
                                         const CellRef* cells, const int* n_segs, const int* cpre, StepConfig sc,
                                         cudaStream_t stream);
 int stream_collide_cells_blocks_per_sm(int precision, int phase, int moments, int warps_per_block);
+// Paired tasks: an entry {lattice | kPairTask, (y << kSegWordBits) | p} is
+// the interior window of 64 cells of row y, mask words 2p and 2p+1 (its
+// cells and all their neighbours fluid), taken by one warp two cells a
+// lane; any other entry is a row segment as in the segment list.
+constexpr int kPairTask = 1 << 30;
+// Build the paired list from the segment list, keeping its order: emit and
+// off hold capacity and capacity + 1 ints, tmp scan_tmp_ints(capacity); the
+// number of tasks lands in off[capacity].  Plain lattices without a symmetry
+// plane (a lattice with one keeps every segment).
+cudaError_t launch_build_pairs(const LatticeView* views, const SegRef* segs, const int* n_segs, int capacity,
+                               int* emit, int* off, int* tmp, SegRef* tasks, cudaStream_t stream);
+// One phase over the paired list (sc.warps_per_block up to 24, sc.grid), a
+// programmatic dependent launch like launch_stream_collide; plain BGK lattices.
+cudaError_t launch_stream_collide_pairs(int precision, int phase, int moments, const LatticeView* views,
+                                        const SegRef* tasks, const int* n_tasks, StepConfig sc,
+                                        cudaStream_t stream);
+int stream_collide_pairs_blocks_per_sm(int precision, int phase, int moments, int warps_per_block);
 // Grid barrier state of the persistent kernel (device memory, 16 bytes).
 struct StepBarrier {
   unsigned count;  // arrivals since the launch began

@@ -80,7 +80,10 @@ struct SegCtx {
   long long fe;  // population elements (bounds-checked builds)
 };
 
-template <class T, int PHASE, int FEAT = 0>
+// NBMASK: form the neighbour flags from the mask words at every precision
+// (for task lists whose entries are not the segment list's, whose flags
+// array is indexed by segment number).
+template <class T, int PHASE, int FEAT = 0, bool NBMASK = false>
 __device__ __forceinline__ void seg_prologue(const LatticeView* __restrict__ views, const SegRef sr, bool valid,
                                              const int lane, SegCtx<T>& s, const uint16_t* __restrict__ nbs,
                                              int t) {
@@ -119,7 +122,7 @@ __device__ __forceinline__ void seg_prologue(const LatticeView* __restrict__ vie
   s.inlet = (x == 0);
   s.outlet = (x == L->nx - 1);
   if (PHASE == 0) {
-    if (sizeof(T) == 4) {
+    if (sizeof(T) == 4 && !NBMASK) {
       // FP32: the neighbour flags built with the work-list (one coalesced
       // 16-bit word per cell, by task number, the symmetry-plane mark below
       // included; builds without the plane drop it).  The 16-bit builds form
@@ -396,6 +399,211 @@ void* cells_kernel_for(int precision, int phase, int moments) {
     case LBM_F32: return pick_cells<float>(phase, moments);
     case LBM_BF16_SHIFTED: return pick_cells<__nv_bfloat16>(phase, moments);
     case LBM_F16_SHIFTED: return pick_cells<__half>(phase, moments);
+    default: return nullptr;
+  }
+}
+
+// ---- paired tasks: interior 64-cell windows, two cells a lane ------------
+//
+// A window of 64 cells (row y, mask words 2p and 2p+1) is interior when its
+// cells and all eight neighbours of each are fluid: it has no bounce-back
+// and no port cell.  Lane l takes cells x = 64p + 2l and x + 1, so that
+// every plane access is one aligned pair of elements (one memory
+// instruction for two cells).  Phase B reads and writes the cells' own
+// slots.  Phase A's one-column shifts pass one half of each pair to the
+// neighbouring lane by a shuffle.  A pull from the west (c_x = +1) takes
+// the upper half of lane l-1's pair, and a pull from the east the lower
+// half of lane l+1's.  The pushes back pair each lane's value with the
+// neighbour's.  Lanes 0 and 31 reach one element past the window.
+// Segments outside interior windows are taken by the same launch, one per
+// warp, exactly as by k_stream_collide.  The per-cell arithmetic is the
+// same everywhere, so every task shape gives the same bits.
+#define PLD2(off, lo, hi)                                         \
+  do {                                                            \
+    if (LBM_OK_IDX((off), fe) && LBM_OK_IDX((off) + 1, fe)) {     \
+      P2::ld(F + (off), lo, hi);                                  \
+    } else {                                                      \
+      lo = 0.0f;                                                  \
+      hi = 0.0f;                                                  \
+    }                                                             \
+  } while (0)
+#define PST2(off, lo, hi)                                                             \
+  do {                                                                                \
+    if (LBM_OK_IDX((off), fe) && LBM_OK_IDX((off) + 1, fe)) P2::st(F + (off), lo, hi); \
+  } while (0)
+#define PLD1(off) (LBM_OK_IDX((off), fe) ? P::ld(F + (off)) : 0.0f)
+#define PST1(off, v)                                   \
+  do {                                                 \
+    if (LBM_OK_IDX((off), fe)) P::st(F + (off), (v)); \
+  } while (0)
+
+template <class T, int PHASE, int MOM>
+__device__ __forceinline__ void pair_task(const LatticeView* __restrict__ L, const int y, const int p,
+                                          const int lane, bool& waited) {
+  using P = Pop<T>;
+  using P2 = Pop2<T>;
+  constexpr unsigned kAll = 0xffffffffu;
+  T* __restrict__ F = static_cast<T*>(L->f);
+  const int pitch = L->pitch, pl = (int)L->plane;
+  const long long fe = L->f_elems;  // bounds-checked builds
+  (void)fe;
+  const float rho0 = L->rho0, omega = L->omega;
+  const int c = y * pitch + (p << 6) + 2 * lane;  // the lane's lower cell x (even)
+  const bool first = lane == 0, last = lane == 31;
+  if (!waited) {  // warp-uniform: populations of the previous step are final from here on
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    waited = true;
+  }
+  float a[9], b[9];  // cells x and x + 1
+  if (PHASE == 0) {
+    // pulls g_i from x - c_i: no x shift for 0, 2, 4
+    PLD2(c, a[0], b[0]);
+    PLD2(2 * pl + c - pitch, a[2], b[2]);
+    PLD2(4 * pl + c + pitch, a[4], b[4]);
+    // from the west (1, 5, 8): the lower half of the pair at x is cell
+    // x+1's source, the upper half lane l+1's lower cell's
+    float q1, q5, q8, r3, r6, r7;
+    PLD2(1 * pl + c, b[1], q1);
+    PLD2(5 * pl + c - pitch, b[5], q5);
+    PLD2(8 * pl + c + pitch, b[8], q8);
+    // from the east (3, 6, 7): the upper half is cell x's source, the lower
+    // half lane l-1's upper cell's
+    PLD2(3 * pl + c, r3, a[3]);
+    PLD2(6 * pl + c - pitch, r6, a[6]);
+    PLD2(7 * pl + c + pitch, r7, a[7]);
+    // one element past the window: lane 0 the west sources of cell 64p,
+    // lane 31 the east sources of cell 64p + 63
+    float e1 = 0.0f, e5 = 0.0f, e8 = 0.0f;
+    if (first || last) {
+      const int d = first ? -1 : 2;
+      e1 = PLD1((first ? 1 : 3) * pl + c + d);
+      e5 = PLD1((first ? 5 : 6) * pl + c - pitch + d);
+      e8 = PLD1((first ? 8 : 7) * pl + c + pitch + d);
+    }
+    const float u1 = __shfl_up_sync(kAll, q1, 1), u5 = __shfl_up_sync(kAll, q5, 1),
+                u8 = __shfl_up_sync(kAll, q8, 1);
+    const float d3 = __shfl_down_sync(kAll, r3, 1), d6 = __shfl_down_sync(kAll, r6, 1),
+                d7 = __shfl_down_sync(kAll, r7, 1);
+    a[1] = first ? e1 : u1;
+    a[5] = first ? e5 : u5;
+    a[8] = first ? e8 : u8;
+    b[3] = last ? e1 : d3;
+    b[6] = last ? e5 : d6;
+    b[7] = last ? e8 : d7;
+  } else {
+    // the cells' own slots: g_i of a cell is in F[opp(i)]
+    PLD2(c, a[0], b[0]);
+    PLD2(3 * pl + c, a[1], b[1]);
+    PLD2(4 * pl + c, a[2], b[2]);
+    PLD2(1 * pl + c, a[3], b[3]);
+    PLD2(2 * pl + c, a[4], b[4]);
+    PLD2(7 * pl + c, a[5], b[5]);
+    PLD2(8 * pl + c, a[6], b[6]);
+    PLD2(5 * pl + c, a[7], b[7]);
+    PLD2(6 * pl + c, a[8], b[8]);
+  }
+  float dra, uxa, uya, drb, uxb, uyb;
+  bgk(a, rho0, omega, dra, uxa, uya);
+  bgk(b, rho0, omega, drb, uxb, uyb);
+  if (PHASE == 0) {
+    // pushes g_i to F[opp(i)] at x + c_i
+    PST2(c, a[0], b[0]);
+    PST2(4 * pl + c + pitch, a[2], b[2]);
+    PST2(2 * pl + c - pitch, a[4], b[4]);
+    // east-going (1, 5, 8): the pair at x takes lane l-1's upper cell and
+    // this lane's lower one; lane 0's lower half is another task's
+    const float v1 = __shfl_up_sync(kAll, b[1], 1), v5 = __shfl_up_sync(kAll, b[5], 1),
+                v8 = __shfl_up_sync(kAll, b[8], 1);
+    if (!first) {
+      PST2(3 * pl + c, v1, a[1]);
+      PST2(7 * pl + c + pitch, v5, a[5]);
+      PST2(6 * pl + c - pitch, v8, a[8]);
+    }
+    // west-going (3, 6, 7): the pair at x takes this lane's upper cell and
+    // lane l+1's lower one; lane 31's upper half is another task's
+    const float v3 = __shfl_down_sync(kAll, a[3], 1), v6 = __shfl_down_sync(kAll, a[6], 1),
+                v7 = __shfl_down_sync(kAll, a[7], 1);
+    if (!last) {
+      PST2(1 * pl + c, b[3], v3);
+      PST2(8 * pl + c + pitch, b[6], v6);
+      PST2(5 * pl + c - pitch, b[7], v7);
+    }
+    // the single elements: lane 0's lower cell east into x + 1 and west
+    // into 64p - 1; lane 31's upper cell east into 64p + 64 and west into
+    // its own lower slot
+    if (first || last) {
+      const int de = first ? 1 : 2, dw = first ? -1 : 0;
+      PST1(3 * pl + c + de, first ? a[1] : b[1]);
+      PST1(7 * pl + c + pitch + de, first ? a[5] : b[5]);
+      PST1(6 * pl + c - pitch + de, first ? a[8] : b[8]);
+      PST1(1 * pl + c + dw, first ? a[3] : b[3]);
+      PST1(8 * pl + c + pitch + dw, first ? a[6] : b[6]);
+      PST1(5 * pl + c - pitch + dw, first ? a[7] : b[7]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) PST2(i * pl + c, a[i], b[i]);
+    if (MOM != 0 && LBM_OK_IDX(c + 1, pl)) {
+      *reinterpret_cast<float2*>(L->drho + c) = make_float2(dra, drb);
+      *reinterpret_cast<float2*>((MOM == 1 ? L->ux : L->ux_prev) + c) = make_float2(uxa, uxb);
+      *reinterpret_cast<float2*>((MOM == 1 ? L->uy : L->uy_prev) + c) = make_float2(uya, uyb);
+    }
+  }
+}
+#undef PLD2
+#undef PST2
+#undef PLD1
+#undef PST1
+
+// One phase over the paired task list (interior windows and the other
+// segments, in list order); one task per warp at a time, the next task's
+// entry loaded while this one's populations are in flight.
+template <class T, int PHASE, int MOM>
+__global__ void __launch_bounds__(max_step_threads(2), 1)
+    k_stream_collide_pairs(const LatticeView* __restrict__ views, const SegRef* __restrict__ tasks,
+                           const int* __restrict__ n_tasks) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  const int ntask = *n_tasks;
+  const int wpb = blockDim.x >> 5;
+  const int stride = gridDim.x * wpb;
+  bool waited = false;
+  int t = blockIdx.x * wpb + (threadIdx.x >> 5);
+  SegRef nxt = t < ntask ? tasks[t] : SegRef{0, 0};
+  for (; t < ntask; t += stride) {
+    const SegRef cur = nxt;
+    if (t + stride < ntask) nxt = tasks[t + stride];
+    if (cur.lattice & kPairTask) {
+      pair_task<T, PHASE, MOM>(views + (cur.lattice & ~kPairTask), cur.yw >> kSegWordBits,
+                               cur.yw & ((1 << kSegWordBits) - 1), lane, waited);
+    } else {
+      SegCtx<T> s;
+      seg_prologue<T, PHASE, 0, true>(views, cur, true, lane, s, nullptr, 0);
+      if (!waited) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        waited = true;
+      }
+      float g[9];
+      seg_load<T, PHASE, false, 0>(s, g);
+      seg_update<T, PHASE, MOM, 0>(s, g);
+    }
+  }
+  if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <class T>
+void* pick_pairs(int phase, int moments) {
+  if (phase == 0) return (void*)k_stream_collide_pairs<T, 0, 0>;
+  if (moments == 1) return (void*)k_stream_collide_pairs<T, 1, 1>;
+  if (moments == 2) return (void*)k_stream_collide_pairs<T, 1, 2>;
+  return (void*)k_stream_collide_pairs<T, 1, 0>;
+}
+
+void* pairs_kernel_for(int precision, int phase, int moments) {
+  switch (precision) {
+    case LBM_F32: return pick_pairs<float>(phase, moments);
+    case LBM_BF16_SHIFTED: return pick_pairs<__nv_bfloat16>(phase, moments);
+    case LBM_F16_SHIFTED: return pick_pairs<__half>(phase, moments);
     default: return nullptr;
   }
 }
@@ -714,6 +922,34 @@ cudaError_t launch_stream_collide_cells(int precision, int phase, int moments, c
   cudaError_t e = cudaLaunchKernelExC(&cfg, k, args);
   if (e == cudaSuccess) count_launches(1);
   return e;
+}
+
+cudaError_t launch_stream_collide_pairs(int precision, int phase, int moments, const LatticeView* views,
+                                        const SegRef* tasks, const int* n_tasks, StepConfig sc,
+                                        cudaStream_t stream) {
+  void* k = pairs_kernel_for(precision, phase, moments);
+  if (!k || sc.warps_per_block < 1 || 32 * sc.warps_per_block > max_step_threads(2) || sc.grid < 1)
+    return cudaErrorInvalidValue;
+  void* args[] = {(void*)&views, (void*)&tasks, (void*)&n_tasks};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sc.grid);
+  cfg.blockDim = dim3(32 * sc.warps_per_block);
+  cfg.stream = stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, k, args);
+  if (e == cudaSuccess) count_launches(1);
+  return e;
+}
+
+int stream_collide_pairs_blocks_per_sm(int precision, int phase, int moments, int warps_per_block) {
+  void* k = pairs_kernel_for(precision, phase, moments);
+  int n = 0;
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, 0) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
 }
 
 int stream_collide_cells_blocks_per_sm(int precision, int phase, int moments, int warps_per_block) {

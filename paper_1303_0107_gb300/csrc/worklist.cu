@@ -250,6 +250,55 @@ __global__ void k_scatter_cells(const LatticeView* __restrict__ views, const Seg
   }
 }
 
+// Interior window (row y, words 2p and 2p+1): its 64 cells and all their
+// neighbours fluid, i.e. rows y-1..y+1 fluid over cells 64p-1 .. 64p+64.
+// The columns beyond the inlet and the outlet read as wall, so such a window
+// holds no port cell; words 2p-1 and 2p+2 exist in the padded mask whenever
+// word 2p+1 is a lattice word.
+__device__ __forceinline__ bool window_interior(const LatticeView& L, int y, int p) {
+  const int w = 2 * p;
+  if (L.mirror || w + 1 >= L.wpr) return false;
+  const int ms = mask_stride(L.wpr);
+#pragma unroll
+  for (int r = -1; r <= 1; ++r) {
+    const uint32_t* m = L.mask + (long long)(y + r) * ms;
+    if ((m[w] | m[w + 1]) != 0u || (m[w - 1] >> 31) != 0u || (m[w + 2] & 1u) != 0u) return false;
+  }
+  return true;
+}
+
+// 1 where list segment q opens a paired task: the first word of an interior
+// window, or a segment outside interior windows (0 past the list)
+__global__ void k_pair_emit(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
+                            const int* __restrict__ n_segs, int capacity, int* __restrict__ emit) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= capacity) return;
+  int e = 0;
+  if (q < n_segs[0]) {
+    const SegRef sr = segs[q];
+    const int y = sr.yw >> kSegWordBits, w = sr.yw & ((1 << kSegWordBits) - 1);
+    e = ((w & 1) && window_interior(views[sr.lattice], y, w >> 1)) ? 0 : 1;
+  }
+  emit[q] = e;
+}
+
+// Both words of an interior window are in the list (they hold fluid), next
+// to each other; the even one writes the window's entry.
+__global__ void k_pair_scatter(const LatticeView* __restrict__ views, const SegRef* __restrict__ segs,
+                               const int* __restrict__ n_segs, const int* __restrict__ emit,
+                               const int* __restrict__ off, SegRef* __restrict__ tasks) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_segs[0] || !emit[q]) return;
+  const SegRef sr = segs[q];
+  const int y = sr.yw >> kSegWordBits, w = sr.yw & ((1 << kSegWordBits) - 1);
+  SegRef t = sr;
+  if (!(w & 1) && window_interior(views[sr.lattice], y, w >> 1)) {
+    t.lattice = sr.lattice | kPairTask;
+    t.yw = (y << kSegWordBits) | (w >> 1);
+  }
+  tasks[off[q]] = t;
+}
+
 inline int blocks_for(long long n, int threads) {
   const long long b = (n + threads - 1) / threads;
   return (int)(b > 0 ? b : 1);
@@ -323,6 +372,17 @@ cudaError_t launch_build_cells(const LatticeView* views, const SegRef* segs, con
   cudaError_t e = launch_scan(cnt, cpre, capacity, tmp, stream);
   if (e != cudaSuccess) return e;
   k_scatter_cells<<<blocks_for((long long)capacity * 32, 256), 256, 0, stream>>>(views, segs, n_segs, cpre, cells);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_pairs(const LatticeView* views, const SegRef* segs, const int* n_segs, int capacity,
+                               int* emit, int* off, int* tmp, SegRef* tasks, cudaStream_t stream) {
+  k_pair_emit<<<blocks_for(capacity, 256), 256, 0, stream>>>(views, segs, n_segs, capacity, emit);
+  count_launches(1);
+  cudaError_t e = launch_scan(emit, off, capacity, tmp, stream);
+  if (e != cudaSuccess) return e;
+  k_pair_scatter<<<blocks_for(capacity, 256), 256, 0, stream>>>(views, segs, n_segs, emit, off, tasks);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -178,6 +178,7 @@ def load_library(path=None):
     L.lbm_debug_barrier_timeout.argtypes = [ctypes.c_int32]
     L.lbm_debug_barrier_timeout.restype = None
     L.lbm_debug_damage_canary.argtypes = [H]
+    L.lbm_debug_task_counts.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p]
     L.lbm_server_destroy.argtypes = [S]
     L.lbm_server_destroy.restype = None
     L.lbm_bytes_per_fluid_update.argtypes = [ctypes.c_int32]
@@ -348,10 +349,20 @@ class Lattice:
         cells); stages 0 (register loads) or 2 / 3 (shared-memory staging, one cell per thread, 4-16
         warps); persistent=2: on-chip resident steps (the shape follows from the lattice; the
         other arguments are ignored); persistent=3: compacted fluid-cell tasks (one cell per
-        thread, 4-32 warps).  Every shape computes the same values; LbmError (status 1) for any
-        other shape, or for modes 2 / 3 on lattices they do not serve."""
+        thread, 4-32 warps); persistent=4: paired tasks (interior 64-cell windows two cells a lane,
+        cells_per_thread=2, 4, 8, 12 or 24 warps).  Every shape computes the same values; LbmError
+        (status 1) for any other shape, or for modes 2 - 4 on lattices they do not serve."""
         _check(load_library().lbm_set_step_config(self._h, int(warps_per_block), int(persistent),
                                                   int(cells_per_thread), int(stages)), "lbm_set_step_config")
+
+    def task_counts(self):
+        """(row segments holding fluid, interior 64-cell windows among them) of the work-list
+        (lbm_debug_task_counts)."""
+        seg = ctypes.c_int32()
+        win = ctypes.c_int32()
+        _check(load_library().lbm_debug_task_counts(self._h, ctypes.byref(seg), ctypes.byref(win)),
+               "lbm_debug_task_counts")
+        return seg.value, win.value
 
     def debug_damage_canary(self):
         """Bounds-checked build: overwrite part of a canary next to the populations (test hook)."""
