@@ -81,6 +81,9 @@ def parse():
                     help="kernel case (2D): on-chip resident steps (one launch per solve)")
     ap.add_argument("--kernel-paired", action="store_true",
                     help="kernel case (2D, batch): paired tasks (interior 64-cell windows two cells a lane)")
+    ap.add_argument("--kernel-wpb", type=int, default=8, help="kernel case: warps per block of a fixed shape")
+    ap.add_argument("--kernel-stages", type=int, default=0,
+                    help="kernel case, paired tasks: windows copied into shared memory this many tasks ahead")
     return ap.parse_args()
 
 
@@ -108,7 +111,7 @@ def kernel_case(args):
         b = L.Batch([dict(cells=c["cells"], tau=c["tau"], u_max=c["u_max"]) for c in cands], precision=prec,
                     residual_every=0)
         if args.kernel_paired:
-            b.set_step_config(8, persistent=4, cells_per_thread=2)
+            b.set_step_config(args.kernel_wpb, persistent=4, cells_per_thread=2, stages=args.kernel_stages)
         b.solve(args.kernel_steps)
         r = b.solve(args.kernel_steps)
         shape = b.step_config()
@@ -126,7 +129,7 @@ def kernel_case(args):
     if args.kernel_resident:
         lat.set_step_config(8, persistent=2)
     elif args.kernel_paired:
-        lat.set_step_config(8, persistent=4, cells_per_thread=2)
+        lat.set_step_config(args.kernel_wpb, persistent=4, cells_per_thread=2, stages=args.kernel_stages)
     elif args.kernel_cpt:
         lat.set_step_config(8, cells_per_thread=args.kernel_cpt)
     lat.solve(args.kernel_steps)
@@ -821,15 +824,17 @@ def main():
         # beyond-L2 lattice: 8192 x 4096 array of 16 straight channels (~50 % fluid)
         big = I.channel_array(8192, 4096, 16, fill=0.5)
         bf = int((big == 0).sum())
-        for pname, pv in (("f32", L.F32), ("bf16", L.BF16_SHIFTED)):
+        for pname, pv in (("f32", L.F32), ("bf16", L.BF16_SHIFTED), ("f16", L.F16_SHIFTED)):
             hb = L.Lattice(big, 0.6, 0.05, precision=pv, residual_every=0, stream=stream)
-            hb.solve(20)
+            hb.solve(300)  # the first solve of 256 steps or more picks the launch shape
             hb.kernel_time(reset=True)
-            hb.solve(200)
+            hb.solve(400)
             ms, nl, nu = hb.kernel_time()
             gbs = bf * L.bytes_per_fluid_update(pv) / ((ms / 1e3) / nl) / 1e9
             extras[f"large_8192x4096_{pname}"] = {"glups": nu / (ms / 1e3) / 1e9, "achieved_gbs": gbs,
-                                                  "frac_of_measured_hbm": gbs / peak, "fluid_cells": bf}
+                                                  "frac_of_measured_hbm": gbs / peak, "fluid_cells": bf,
+                                                  "step_config": list(hb.step_config()),
+                                                  "windows": hb.task_counts()[1]}
             hb.close()
     if rank == 0 and "d3q19" in legs:
         extras["d3q19"] = leg_d3q19(L, I, stream, peak)
@@ -898,9 +903,10 @@ def leg_summary(extras):
         if isinstance(d, dict) and d.get(field) is not None:
             out[key] = d[field]
 
-    for p in ("f32", "bf16"):
+    for p in ("f32", "bf16", "f16"):
         put(f"large_{p}_glups", extras.get(f"large_8192x4096_{p}"), "glups")
         put(f"large_{p}_frac", extras.get(f"large_8192x4096_{p}"), "frac_of_measured_hbm")
+    for p in ("f32", "bf16"):
         put(f"batched_{p}_glups", extras.get(f"batched_256_{p}"), "batched_glups")
         put(f"batched_{p}_step_glups", extras.get(f"batched_256_{p}"), "batched_step_glups")
         put(f"batched_{p}_speedup", extras.get(f"batched_256_{p}"), "speedup")

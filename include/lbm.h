@@ -362,7 +362,9 @@ lbm_status lbm_step_config(lbm_handle h, int32_t* warps_per_block, int32_t* grid
  * resident solves, the shape follows from the lattice (the other arguments
  * are ignored); persistent = 3: cell tasks, warps_per_block 4, 8, 12, 16 or
  * 32, one cell per thread, stages 0; persistent = 4: paired tasks,
- * warps_per_block 4, 8, 12 or 24, cells_per_thread 2, stages 0.  The grid is
+ * warps_per_block 4, 8, 12 or 24, cells_per_thread 2, stages 0 (windows
+ * loaded into registers) or 2, 3, 4 (copied into shared memory that many
+ * tasks ahead).  The grid is
  * sized for the device.  LBM_ERR_ARG for any other shape, or for modes 2 - 4
  * on lattices they do not serve.  Every shape computes the same values, so this changes timings
  * only.                                                                   */

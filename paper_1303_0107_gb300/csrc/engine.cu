@@ -241,6 +241,7 @@ lbm_status check_and_describe(Member& m, const uint8_t* cells, std::vector<float
 
 // Offsets and views of a member list, uploaded into the layout's buffers.
 lbm_status layout_build(SetLayout& S, const std::vector<Member*>& ms, cudaStream_t stream) {
+  ++S.gen;
   const int n = (int)ms.size();
   S.n = n;
   S.h_views.resize(std::max(1, n));
@@ -325,9 +326,11 @@ lbm_status launch_pair(Engine* E, int moments) {
   if (E->step.persistent == 4) {  // paired tasks (the list is built before any capture)
     const SegRef* tasks = static_cast<const SegRef*>(E->pair_list.p);
     const int* n_tasks = static_cast<const int*>(E->pair_scan.p) + 2 * (size_t)std::max(1, E->L.total_seg_words);
-    CU(launch_stream_collide_pairs(E->precision, 0, 0, views, tasks, n_tasks, E->step, E->stream));
+    // one lattice: its view by value (a graph captured with it is keyed by the layout build)
+    const LatticeView* one = E->n() == 1 ? &E->L.h_views[0] : nullptr;
+    CU(launch_stream_collide_pairs(E->precision, 0, 0, views, one, tasks, n_tasks, E->step, E->stream));
     DEBUG_SYNC(E, "stream-collide phase A (paired tasks)");
-    CU(launch_stream_collide_pairs(E->precision, 1, moments, views, tasks, n_tasks, E->step, E->stream));
+    CU(launch_stream_collide_pairs(E->precision, 1, moments, views, one, tasks, n_tasks, E->step, E->stream));
     DEBUG_SYNC(E, "stream-collide phase B (paired tasks)");
     return LBM_OK;
   }
@@ -350,14 +353,17 @@ void drop_graphs(Engine* E) {
 // captured with are unchanged.
 lbm_status ensure_graph(Engine* E, int which) {
   const bool cells = E->step.persistent == 3, paired = E->step.persistent == 4;
-  const void* key[5] = {E->L.views.p, cells ? E->cell_list.p : paired ? E->pair_list.p : E->segs.p, E->n_segs.p,
+  const void* key[6] = {E->L.views.p, cells ? E->cell_list.p : paired ? E->pair_list.p : E->segs.p, E->n_segs.p,
                         reinterpret_cast<const void*>((intptr_t)E->step.persistent << 56 |
+                                                      (intptr_t)E->step.stages << 52 |
+                                                      (intptr_t)E->step.cells_per_thread << 48 |
                                                       (intptr_t)E->step.warps_per_block << 32 |
                                                       (intptr_t)(uint32_t)E->step.grid),
-                        cells ? E->cell_scan.p : paired ? E->pair_scan.p : nullptr};
-  if (!std::equal(key, key + 5, E->graph_key)) {
+                        cells ? E->cell_scan.p : paired ? E->pair_scan.p : nullptr,
+                        reinterpret_cast<const void*>((uintptr_t)E->L.gen)};
+  if (!std::equal(key, key + 6, E->graph_key)) {
     drop_graphs(E);
-    std::copy(key, key + 5, E->graph_key);
+    std::copy(key, key + 6, E->graph_key);
   }
   if (E->graphs[which]) return LBM_OK;
   cudaGraph_t g = nullptr;
@@ -516,8 +522,8 @@ StepConfig cells_shape(Engine* E, int wpb, int blocks_per_sm_scale) {
 // The paired-task shape: two cells a lane on interior windows, one segment
 // a warp elsewhere; at most one task per warp of the grid, the segment list
 // bounding the tasks.
-StepConfig pairs_shape(Engine* E, int wpb, int blocks_per_sm_scale) {
-  const int bps = stream_collide_pairs_blocks_per_sm(E->precision, 0, 0, wpb);
+StepConfig pairs_shape(Engine* E, int wpb, int blocks_per_sm_scale, int stages = 0) {
+  const int bps = stream_collide_pairs_blocks_per_sm(E->precision, 0, 0, wpb, stages);
   const long long cap = (long long)E->sm_count * bps * blocks_per_sm_scale;
   const long long need = ((long long)E->L.total_seg_words + wpb - 1) / wpb;
   StepConfig c;
@@ -525,7 +531,7 @@ StepConfig pairs_shape(Engine* E, int wpb, int blocks_per_sm_scale) {
   c.grid = (int)(E->fixed_grid ? cap : std::max<long long>(1, std::min(need, cap)));
   c.persistent = 4;
   c.cells_per_thread = 2;
-  c.stages = 0;
+  c.stages = stages;
   c.features = 0;
   return c;
 }
@@ -643,11 +649,12 @@ lbm_status autotune(Engine* E) {
       for (void* b : backups) cudaFree(b);
       return pst;
     }
-    for (int wpb : {4, 8, 12, 24})
-      for (int scale : {1, 2}) {
-        if (wpb == 24 && scale != 1) continue;
-        cand.push_back(pairs_shape(E, wpb, scale));
-      }
+    for (int stages : {0, 2, 3})
+      for (int wpb : {4, 8, 12, 24})
+        for (int scale : {1, 2}) {
+          if (wpb == 24 && scale != 1) continue;
+          cand.push_back(pairs_shape(E, wpb, scale, stages));
+        }
   }
   if (resident_enabled() && !only_plain) {
     bool ok = false;
@@ -1579,6 +1586,17 @@ lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t pe
     E->tuned = true;
     return LBM_OK;
   }
+  if (persistent == 4) {  // paired tasks
+    if (!pairs_eligible(E)) return fail(LBM_ERR_ARG, "paired tasks need plain BGK lattices");
+    if (!step_shape_allowed(warps_per_block, cells_per_thread, 4) || (stages != 0 && (stages < 2 || stages > 4)))
+      return fail(LBM_ERR_ARG,
+                  "paired tasks take two cells per thread, 4, 8, 12 or 24 warps per block and stages 0 or 2-4");
+    lbm_status st = ensure_pairs(E);
+    if (st != LBM_OK) return st;
+    E->step = pairs_shape(E, warps_per_block, kDefaultGridScale, stages);
+    E->tuned = true;
+    return LBM_OK;
+  }
   if (stages != 0 && stages != 2 && stages != 3) return fail(LBM_ERR_ARG, "stages must be 0, 2 or 3");
   if (stages != 0 && (persistent || cells_per_thread != 1))
     return fail(LBM_ERR_ARG, "staged loads take one cell per thread and per-phase launches");
@@ -1590,16 +1608,6 @@ lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t pe
     lbm_status st = ensure_cells(E);
     if (st != LBM_OK) return st;
     E->step = cells_shape(E, warps_per_block, kDefaultGridScale);
-    E->tuned = true;
-    return LBM_OK;
-  }
-  if (persistent == 4) {  // paired tasks
-    if (!pairs_eligible(E)) return fail(LBM_ERR_ARG, "paired tasks need plain BGK lattices");
-    if (!step_shape_allowed(warps_per_block, cells_per_thread, 4) || stages != 0)
-      return fail(LBM_ERR_ARG, "paired tasks take two cells per thread and 4, 8, 12 or 24 warps per block");
-    lbm_status st = ensure_pairs(E);
-    if (st != LBM_OK) return st;
-    E->step = pairs_shape(E, warps_per_block, kDefaultGridScale);
     E->tuned = true;
     return LBM_OK;
   }

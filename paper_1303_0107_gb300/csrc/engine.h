@@ -89,6 +89,7 @@ struct SetLayout {
   GrowBuf views, word_off, seg_word_off;
   std::vector<LatticeView> h_views;
   std::vector<int> h_woff, h_swoff;
+  unsigned gen = 0;  // counts builds: kernels that took a view by value belong to one build
 };
 
 struct Engine {
@@ -136,8 +137,8 @@ struct Engine {
   bool pairs_valid = false;
 
   cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};  // 512, 64, 8 and 1 pairs
-  // views, segs (or the cell or paired list), n_segs, shape, cell prefix (or paired count)
-  const void* graph_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // views, segs (or the cell or paired list), n_segs, shape, cell prefix (or paired count), layout build
+  const void* graph_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   StepConfig step{kStepWarps, 1, 0, 1, 0, 0};
   int features = 0;  // kernel build the members need: 1 collision models, 2 symmetry plane
   bool tuned = false;

@@ -156,12 +156,16 @@ constexpr int kPairTask = 1 << 30;
 // plane (a lattice with one keeps every segment).
 cudaError_t launch_build_pairs(const LatticeView* views, const SegRef* segs, const int* n_segs, int capacity,
                                int* emit, int* off, int* tmp, SegRef* tasks, cudaStream_t stream);
-// One phase over the paired list (sc.warps_per_block up to 24, sc.grid), a
-// programmatic dependent launch like launch_stream_collide; plain BGK lattices.
+// One phase over the paired list (sc.warps_per_block up to 24, sc.grid;
+// sc.stages 0: windows loaded into registers, 2-4: copied into shared
+// memory that many tasks ahead), a programmatic dependent launch like
+// launch_stream_collide; plain BGK lattices.  one: for a set of one
+// lattice, a host copy of its view, passed to the kernel by value (NULL:
+// the kernel reads the device table views).
 cudaError_t launch_stream_collide_pairs(int precision, int phase, int moments, const LatticeView* views,
-                                        const SegRef* tasks, const int* n_tasks, StepConfig sc,
-                                        cudaStream_t stream);
-int stream_collide_pairs_blocks_per_sm(int precision, int phase, int moments, int warps_per_block);
+                                        const LatticeView* one, const SegRef* tasks, const int* n_tasks,
+                                        StepConfig sc, cudaStream_t stream);
+int stream_collide_pairs_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int stages);
 // Grid barrier state of the persistent kernel (device memory, 16 bytes).
 struct StepBarrier {
   unsigned count;  // arrivals since the launch began

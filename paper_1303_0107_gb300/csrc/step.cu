@@ -437,71 +437,82 @@ void* cells_kernel_for(int precision, int phase, int moments) {
     if (LBM_OK_IDX((off), fe)) P::st(F + (off), (v)); \
   } while (0)
 
+// Where a window's populations come from, by slot i (the population g_i of
+// the lane's two cells): phase A reads plane i of row y - c_iy (the x
+// shift is made by the shuffles of pair_assemble), phase B plane opp(i) of
+// row y.
+__host__ __device__ constexpr int pair_plane(int phase, int i) {
+  return phase == 0 ? i : (i == 0 ? 0 : i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+}
+__host__ __device__ constexpr int pair_row(int phase, int i) {  // row offset of the source, in rows
+  return phase == 0 ? (i == 2 || i == 5 || i == 6 ? -1 : i == 4 || i == 7 || i == 8 ? 1 : 0) : 0;
+}
+// One element past the window (phase A, slot k = 0, 1, 2): lane 0 reads
+// direction {1, 5, 8}[k] at x = 64p - 1, lane 31 direction {3, 6, 7}[k] at
+// x = 64p + 64 (2 past its lower cell), both in the row of the slot.
+__host__ __device__ constexpr int pair_edge_plane(bool first, int k) {
+  return first ? (k == 0 ? 1 : k == 1 ? 5 : 8) : (k == 0 ? 3 : k == 1 ? 6 : 7);
+}
+__host__ __device__ constexpr int pair_edge_row(int k) { return k == 0 ? 0 : k == 1 ? -1 : 1; }
+
+// The nine pairs of a window, straight from global memory into a (lower
+// cells) and b (upper cells), and the phase-A edge elements e.
+template <class T, int PHASE>
+__device__ __forceinline__ void pair_load(const T* __restrict__ F, const int c, const int pitch, const int pl,
+                                          const long long fe, const int lane, float (&a)[9], float (&b)[9],
+                                          float (&e)[3]) {
+  using P = Pop<T>;
+  using P2 = Pop2<T>;
+  (void)fe;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) PLD2(pair_plane(PHASE, i) * pl + c + pair_row(PHASE, i) * pitch, a[i], b[i]);
+  e[0] = e[1] = e[2] = 0.0f;
+  if (PHASE == 0 && (lane == 0 || lane == 31)) {
+    const bool first = lane == 0;
+    const int d = first ? -1 : 2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) e[k] = PLD1(pair_edge_plane(first, k) * pl + c + pair_edge_row(k) * pitch + d);
+  }
+}
+
+// Phase A's one-column shifts: a pull from the west (1, 5, 8) takes the
+// upper half of lane l-1's pair for the lower cell and the lower half of
+// the lane's own pair for the upper cell; a pull from the east (3, 6, 7)
+// the own upper half for the lower cell and lane l+1's lower half for the
+// upper cell; lanes 0 and 31 take the edge elements instead.
+template <int PHASE>
+__device__ __forceinline__ void pair_assemble(float (&a)[9], float (&b)[9], const float (&e)[3], const int lane) {
+  if (PHASE != 0) return;
+  constexpr unsigned kAll = 0xffffffffu;
+  const bool first = lane == 0, last = lane == 31;
+  const int west[3] = {1, 5, 8}, east[3] = {3, 6, 7};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int i = west[k];
+    const float u = __shfl_up_sync(kAll, b[i], 1);
+    b[i] = a[i];
+    a[i] = first ? e[k] : u;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int i = east[k];
+    const float d = __shfl_down_sync(kAll, a[i], 1);
+    a[i] = b[i];
+    b[i] = last ? e[k] : d;
+  }
+}
+
+// Collision of both cells and the stores of the window.
 template <class T, int PHASE, int MOM>
-__device__ __forceinline__ void pair_task(const LatticeView* __restrict__ L, const int y, const int p,
-                                          const int lane, bool& waited) {
+__device__ __forceinline__ void pair_finish(const LatticeView* __restrict__ L, T* __restrict__ F, const int c,
+                                            const int pitch, const int pl, const long long fe, const int lane,
+                                            float (&a)[9], float (&b)[9]) {
   using P = Pop<T>;
   using P2 = Pop2<T>;
   constexpr unsigned kAll = 0xffffffffu;
-  T* __restrict__ F = static_cast<T*>(L->f);
-  const int pitch = L->pitch, pl = (int)L->plane;
-  const long long fe = L->f_elems;  // bounds-checked builds
   (void)fe;
-  const float rho0 = L->rho0, omega = L->omega;
-  const int c = y * pitch + (p << 6) + 2 * lane;  // the lane's lower cell x (even)
   const bool first = lane == 0, last = lane == 31;
-  if (!waited) {  // warp-uniform: populations of the previous step are final from here on
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    waited = true;
-  }
-  float a[9], b[9];  // cells x and x + 1
-  if (PHASE == 0) {
-    // pulls g_i from x - c_i: no x shift for 0, 2, 4
-    PLD2(c, a[0], b[0]);
-    PLD2(2 * pl + c - pitch, a[2], b[2]);
-    PLD2(4 * pl + c + pitch, a[4], b[4]);
-    // from the west (1, 5, 8): the lower half of the pair at x is cell
-    // x+1's source, the upper half lane l+1's lower cell's
-    float q1, q5, q8, r3, r6, r7;
-    PLD2(1 * pl + c, b[1], q1);
-    PLD2(5 * pl + c - pitch, b[5], q5);
-    PLD2(8 * pl + c + pitch, b[8], q8);
-    // from the east (3, 6, 7): the upper half is cell x's source, the lower
-    // half lane l-1's upper cell's
-    PLD2(3 * pl + c, r3, a[3]);
-    PLD2(6 * pl + c - pitch, r6, a[6]);
-    PLD2(7 * pl + c + pitch, r7, a[7]);
-    // one element past the window: lane 0 the west sources of cell 64p,
-    // lane 31 the east sources of cell 64p + 63
-    float e1 = 0.0f, e5 = 0.0f, e8 = 0.0f;
-    if (first || last) {
-      const int d = first ? -1 : 2;
-      e1 = PLD1((first ? 1 : 3) * pl + c + d);
-      e5 = PLD1((first ? 5 : 6) * pl + c - pitch + d);
-      e8 = PLD1((first ? 8 : 7) * pl + c + pitch + d);
-    }
-    const float u1 = __shfl_up_sync(kAll, q1, 1), u5 = __shfl_up_sync(kAll, q5, 1),
-                u8 = __shfl_up_sync(kAll, q8, 1);
-    const float d3 = __shfl_down_sync(kAll, r3, 1), d6 = __shfl_down_sync(kAll, r6, 1),
-                d7 = __shfl_down_sync(kAll, r7, 1);
-    a[1] = first ? e1 : u1;
-    a[5] = first ? e5 : u5;
-    a[8] = first ? e8 : u8;
-    b[3] = last ? e1 : d3;
-    b[6] = last ? e5 : d6;
-    b[7] = last ? e8 : d7;
-  } else {
-    // the cells' own slots: g_i of a cell is in F[opp(i)]
-    PLD2(c, a[0], b[0]);
-    PLD2(3 * pl + c, a[1], b[1]);
-    PLD2(4 * pl + c, a[2], b[2]);
-    PLD2(1 * pl + c, a[3], b[3]);
-    PLD2(2 * pl + c, a[4], b[4]);
-    PLD2(7 * pl + c, a[5], b[5]);
-    PLD2(8 * pl + c, a[6], b[6]);
-    PLD2(5 * pl + c, a[7], b[7]);
-    PLD2(6 * pl + c, a[8], b[8]);
-  }
+  const float rho0 = L->rho0, omega = L->omega;
   float dra, uxa, uya, drb, uxb, uyb;
   bgk(a, rho0, omega, dra, uxa, uya);
   bgk(b, rho0, omega, drb, uxb, uyb);
@@ -550,6 +561,23 @@ __device__ __forceinline__ void pair_task(const LatticeView* __restrict__ L, con
     }
   }
 }
+
+template <class T, int PHASE, int MOM>
+__device__ __forceinline__ void pair_task(const LatticeView* __restrict__ L, const int y, const int p,
+                                          const int lane, bool& waited) {
+  T* __restrict__ F = static_cast<T*>(L->f);
+  const int pitch = L->pitch, pl = (int)L->plane;
+  const long long fe = L->f_elems;  // bounds-checked builds
+  const int c = y * pitch + (p << 6) + 2 * lane;  // the lane's lower cell x (even)
+  if (!waited) {  // warp-uniform: populations of the previous step are final from here on
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    waited = true;
+  }
+  float a[9], b[9], e[3];  // cells x and x + 1
+  pair_load<T, PHASE>(F, c, pitch, pl, fe, lane, a, b, e);
+  pair_assemble<PHASE>(a, b, e, lane);
+  pair_finish<T, PHASE, MOM>(L, F, c, pitch, pl, fe, lane, a, b);
+}
 #undef PLD2
 #undef PST2
 #undef PLD1
@@ -557,11 +585,12 @@ __device__ __forceinline__ void pair_task(const LatticeView* __restrict__ L, con
 
 // One phase over the paired task list (interior windows and the other
 // segments, in list order); one task per warp at a time, the next task's
-// entry loaded while this one's populations are in flight.
-template <class T, int PHASE, int MOM>
-__global__ void __launch_bounds__(max_step_threads(2), 1)
-    k_stream_collide_pairs(const LatticeView* __restrict__ views, const SegRef* __restrict__ tasks,
-                           const int* __restrict__ n_tasks) {
+// entry loaded while this one's populations are in flight.  ONE: a set of
+// one lattice whose descriptor is a kernel parameter (uniform values from
+// the constant bank instead of per-task loads of the table entry).
+template <class T, int PHASE, int MOM, bool ONE>
+__device__ __forceinline__ void pairs_loop(const LatticeView* __restrict__ views, const SegRef* __restrict__ tasks,
+                                           const int* __restrict__ n_tasks) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31;
   const int ntask = *n_tasks;
@@ -571,12 +600,13 @@ __global__ void __launch_bounds__(max_step_threads(2), 1)
   int t = blockIdx.x * wpb + (threadIdx.x >> 5);
   SegRef nxt = t < ntask ? tasks[t] : SegRef{0, 0};
   for (; t < ntask; t += stride) {
-    const SegRef cur = nxt;
+    SegRef cur = nxt;
     if (t + stride < ntask) nxt = tasks[t + stride];
     if (cur.lattice & kPairTask) {
-      pair_task<T, PHASE, MOM>(views + (cur.lattice & ~kPairTask), cur.yw >> kSegWordBits,
+      pair_task<T, PHASE, MOM>(views + (ONE ? 0 : (cur.lattice & ~kPairTask)), cur.yw >> kSegWordBits,
                                cur.yw & ((1 << kSegWordBits) - 1), lane, waited);
     } else {
+      if (ONE) cur.lattice = 0;
       SegCtx<T> s;
       seg_prologue<T, PHASE, 0, true>(views, cur, true, lane, s, nullptr, 0);
       if (!waited) {
@@ -591,21 +621,32 @@ __global__ void __launch_bounds__(max_step_threads(2), 1)
   if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+template <class T, int PHASE, int MOM>
+__global__ void __launch_bounds__(max_step_threads(2), 1)
+    k_stream_collide_pairs(const LatticeView* __restrict__ views, const SegRef* __restrict__ tasks,
+                           const int* __restrict__ n_tasks) {
+  pairs_loop<T, PHASE, MOM, false>(views, tasks, n_tasks);
+}
+
+template <class T, int PHASE, int MOM>
+__global__ void __launch_bounds__(max_step_threads(2), 1)
+    k_stream_collide_pairs_one(const __grid_constant__ LatticeView one, const SegRef* __restrict__ tasks,
+                               const int* __restrict__ n_tasks) {
+  pairs_loop<T, PHASE, MOM, true>(&one, tasks, n_tasks);
+}
+
 template <class T>
-void* pick_pairs(int phase, int moments) {
+void* pick_pairs(int phase, int moments, bool one) {
+  if (one) {
+    if (phase == 0) return (void*)k_stream_collide_pairs_one<T, 0, 0>;
+    if (moments == 1) return (void*)k_stream_collide_pairs_one<T, 1, 1>;
+    if (moments == 2) return (void*)k_stream_collide_pairs_one<T, 1, 2>;
+    return (void*)k_stream_collide_pairs_one<T, 1, 0>;
+  }
   if (phase == 0) return (void*)k_stream_collide_pairs<T, 0, 0>;
   if (moments == 1) return (void*)k_stream_collide_pairs<T, 1, 1>;
   if (moments == 2) return (void*)k_stream_collide_pairs<T, 1, 2>;
   return (void*)k_stream_collide_pairs<T, 1, 0>;
-}
-
-void* pairs_kernel_for(int precision, int phase, int moments) {
-  switch (precision) {
-    case LBM_F32: return pick_pairs<float>(phase, moments);
-    case LBM_BF16_SHIFTED: return pick_pairs<__nv_bfloat16>(phase, moments);
-    case LBM_F16_SHIFTED: return pick_pairs<__half>(phase, moments);
-    default: return nullptr;
-  }
 }
 
 // ---- staged variant: populations copied into shared memory ahead of use ----
@@ -741,6 +782,192 @@ __global__ void __launch_bounds__(512, 2)
     stage_consume<T, PHASE, MOM>(views, wbuf + (k % NS) * kStageWords, lane);
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// ---- staged paired tasks ----------------------------------------------------
+//
+// The paired kernel keeps one window's pairs in flight per lane (36 bytes
+// with 16-bit storage): at the occupancy its registers allow, too few bytes
+// per SM to cover the memory latency.  Here each warp copies the pairs of
+// the windows NS-1 tasks ahead into shared memory (cp.async: the lane's own
+// pair of each slot, lanes 0 and 31 also the edge elements), so that the
+// bytes in flight take no registers.  Row segments outside interior
+// windows are loaded directly when their turn comes.  A stage holds the
+// task entry (words 0-1), the edge words (2-7: lane 0's three, lane 31's
+// three) and the nine slots of 32 pairs.
+template <class T>
+struct PairStage {
+  static constexpr int kPairWords = 2 * (int)sizeof(T) / 4;  // 32-bit words per pair
+  static constexpr int kHead = 8;
+  static constexpr int kWords = kHead + 9 * 32 * kPairWords;  // a multiple of 4: stages stay 16-byte aligned
+};
+
+template <int N>
+__device__ __forceinline__ void cp_async_n(uint32_t* dst, const void* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = ok ? N : 0;  // 0: fill with zeros, read nothing
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(N), "r"(n) : "memory");
+}
+
+template <class T, int PHASE, bool ONE>
+__device__ __forceinline__ void pair_stage_issue(const LatticeView* __restrict__ views, const SegRef sr,
+                                                 const int lane, uint32_t* sb) {
+  constexpr int W = PairStage<T>::kPairWords;
+  if (lane == 0) {
+    sb[0] = (uint32_t)sr.lattice;
+    sb[1] = (uint32_t)sr.yw;
+  }
+  if (!(sr.lattice & kPairTask)) return;  // a row segment: loaded when its turn comes
+  const LatticeView* __restrict__ L = views + (ONE ? 0 : (sr.lattice & ~kPairTask));
+  const T* F = static_cast<const T*>(L->f);
+  const int pitch = L->pitch, pl = (int)L->plane;
+  const long long fe = L->f_elems;
+  (void)fe;
+  const int y = sr.yw >> kSegWordBits, p = sr.yw & ((1 << kSegWordBits) - 1);
+  const int c = y * pitch + (p << 6) + 2 * lane;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int off = pair_plane(PHASE, i) * pl + c + pair_row(PHASE, i) * pitch;
+    const bool ok = LBM_OK_IDX(off, fe) && LBM_OK_IDX(off + 1, fe);
+    cp_async_n<2 * sizeof(T)>(sb + PairStage<T>::kHead + (i * 32 + lane) * W, F + (ok ? off : 0), ok);
+  }
+  if (PHASE == 0 && (lane == 0 || lane == 31)) {
+    const bool first = lane == 0;
+    const int d = first ? -1 : 2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int off = pair_edge_plane(first, k) * pl + c + pair_edge_row(k) * pitch + d;
+      const bool ok = LBM_OK_IDX(off, fe);
+      // 16-bit: the aligned word holding the element (lane 0: its upper half, lane 31: its lower)
+      const int src = sizeof(T) == 4 ? off : (off & ~1);
+      cp_async_n<4>(sb + 2 + (first ? k : 3 + k), F + (ok ? src : 0), ok);
+    }
+  }
+}
+
+template <class T, int PHASE, int MOM, bool ONE>
+__device__ __forceinline__ void pair_stage_consume(const LatticeView* __restrict__ views, const SegRef sr,
+                                                   const uint32_t* sb, const int lane) {
+  using P = Pop<T>;
+  constexpr int W = PairStage<T>::kPairWords;
+  const LatticeView* __restrict__ L = views + (ONE ? 0 : (sr.lattice & ~kPairTask));
+  T* __restrict__ F = static_cast<T*>(L->f);
+  const int pitch = L->pitch, pl = (int)L->plane;
+  const long long fe = L->f_elems;
+  const int y = sr.yw >> kSegWordBits, p = sr.yw & ((1 << kSegWordBits) - 1);
+  const int c = y * pitch + (p << 6) + 2 * lane;
+  float a[9], b[9], e[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    Pop2<T>::ld(reinterpret_cast<const T*>(sb + PairStage<T>::kHead + (i * 32 + lane) * W), a[i], b[i]);
+  if (PHASE == 0 && (lane == 0 || lane == 31)) {
+    const bool first = lane == 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) e[k] = P::from_word(sb[2 + (first ? k : 3 + k)], first ? 1 : 0);
+  }
+  pair_assemble<PHASE>(a, b, e, lane);
+  pair_finish<T, PHASE, MOM>(L, F, c, pitch, pl, fe, lane, a, b);
+}
+
+template <class T, int PHASE, int MOM, int NS, bool ONE>
+__device__ __forceinline__ void pairs_staged_loop(const LatticeView* __restrict__ views,
+                                                  const SegRef* __restrict__ tasks, const int* __restrict__ n_tasks,
+                                                  uint32_t* pair_smem) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  constexpr int SW = PairStage<T>::kWords;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int stride = gridDim.x * wpb;
+  const int ntask = *n_tasks;
+  uint32_t* wbuf = pair_smem + warp * NS * SW;
+  const int t0 = blockIdx.x * wpb + warp;
+  // every copy reads populations: wait for the previous step first
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k) {
+    const int t = t0 + k * stride;
+    if (t < ntask) pair_stage_issue<T, PHASE, ONE>(views, tasks[t], lane, wbuf + k * SW);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  int ta = t0 + (NS - 1) * stride;  // the next task to stage, its entry loaded one turn early
+  SegRef ahead = ta < ntask ? tasks[ta] : SegRef{0, 0};
+  for (int k = 0, t = t0; t < ntask; ++k, t += stride) {
+    __syncwarp();  // every lane is done with the stage refilled now (task k - 1's)
+    if (ta < ntask) pair_stage_issue<T, PHASE, ONE>(views, ahead, lane, wbuf + ((k + NS - 1) % NS) * SW);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    ta += stride;
+    if (ta < ntask) ahead = tasks[ta];
+    cp_async_wait<NS>();  // this lane's copies of task k have landed
+    __syncwarp();         // and every lane's
+    const uint32_t* sb = wbuf + (k % NS) * SW;
+    SegRef cur{(int)sb[0], (int)sb[1]};
+    if (cur.lattice & kPairTask) {
+      pair_stage_consume<T, PHASE, MOM, ONE>(views, cur, sb, lane);
+    } else {
+      if (ONE) cur.lattice = 0;
+      SegCtx<T> sc;
+      seg_prologue<T, PHASE, 0, true>(views, cur, true, lane, sc, nullptr, 0);
+      float g[9];
+      seg_load<T, PHASE, false, 0>(sc, g);
+      seg_update<T, PHASE, MOM, 0>(sc, g);
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <class T, int PHASE, int MOM, int NS>
+__global__ void __launch_bounds__(max_step_threads(2), 1)
+    k_stream_collide_pairs_staged(const LatticeView* __restrict__ views, const SegRef* __restrict__ tasks,
+                                  const int* __restrict__ n_tasks) {
+  extern __shared__ uint32_t pair_smem[];
+  pairs_staged_loop<T, PHASE, MOM, NS, false>(views, tasks, n_tasks, pair_smem);
+}
+
+template <class T, int PHASE, int MOM, int NS>
+__global__ void __launch_bounds__(max_step_threads(2), 1)
+    k_stream_collide_pairs_staged_one(const __grid_constant__ LatticeView one, const SegRef* __restrict__ tasks,
+                                      const int* __restrict__ n_tasks) {
+  extern __shared__ uint32_t pair_smem[];
+  pairs_staged_loop<T, PHASE, MOM, NS, true>(&one, tasks, n_tasks, pair_smem);
+}
+
+template <class T, int NS>
+void* pick_pairs_staged(int phase, int moments, bool one) {
+  if (one) {
+    if (phase == 0) return (void*)k_stream_collide_pairs_staged_one<T, 0, 0, NS>;
+    if (moments == 1) return (void*)k_stream_collide_pairs_staged_one<T, 1, 1, NS>;
+    if (moments == 2) return (void*)k_stream_collide_pairs_staged_one<T, 1, 2, NS>;
+    return (void*)k_stream_collide_pairs_staged_one<T, 1, 0, NS>;
+  }
+  if (phase == 0) return (void*)k_stream_collide_pairs_staged<T, 0, 0, NS>;
+  if (moments == 1) return (void*)k_stream_collide_pairs_staged<T, 1, 1, NS>;
+  if (moments == 2) return (void*)k_stream_collide_pairs_staged<T, 1, 2, NS>;
+  return (void*)k_stream_collide_pairs_staged<T, 1, 0, NS>;
+}
+
+template <class T>
+void* pick_pairs_any(int phase, int moments, int stages, bool one) {
+  switch (stages) {
+    case 0: return pick_pairs<T>(phase, moments, one);
+    case 2: return pick_pairs_staged<T, 2>(phase, moments, one);
+    case 3: return pick_pairs_staged<T, 3>(phase, moments, one);
+    case 4: return pick_pairs_staged<T, 4>(phase, moments, one);
+    default: return nullptr;
+  }
+}
+
+void* pairs_kernel_for(int precision, int phase, int moments, int stages, bool one) {
+  switch (precision) {
+    case LBM_F32: return pick_pairs_any<float>(phase, moments, stages, one);
+    case LBM_BF16_SHIFTED: return pick_pairs_any<__nv_bfloat16>(phase, moments, stages, one);
+    case LBM_F16_SHIFTED: return pick_pairs_any<__half>(phase, moments, stages, one);
+    default: return nullptr;
+  }
+}
+
+size_t pairs_smem_bytes(int precision, int warps_per_block, int stages) {
+  if (stages < 2) return 0;
+  const int words = precision == LBM_F32 ? PairStage<float>::kWords : PairStage<__half>::kWords;
+  return (size_t)warps_per_block * stages * words * sizeof(uint32_t);
 }
 
 size_t staged_smem_bytes(int warps_per_block, int stages) {
@@ -925,18 +1152,21 @@ cudaError_t launch_stream_collide_cells(int precision, int phase, int moments, c
 }
 
 cudaError_t launch_stream_collide_pairs(int precision, int phase, int moments, const LatticeView* views,
-                                        const SegRef* tasks, const int* n_tasks, StepConfig sc,
-                                        cudaStream_t stream) {
-  void* k = pairs_kernel_for(precision, phase, moments);
+                                        const LatticeView* one, const SegRef* tasks, const int* n_tasks,
+                                        StepConfig sc, cudaStream_t stream) {
+  void* k = pairs_kernel_for(precision, phase, moments, sc.stages, one != nullptr);
   if (!k || sc.warps_per_block < 1 || 32 * sc.warps_per_block > max_step_threads(2) || sc.grid < 1)
     return cudaErrorInvalidValue;
-  void* args[] = {(void*)&views, (void*)&tasks, (void*)&n_tasks};
+  const size_t smem = pairs_smem_bytes(precision, sc.warps_per_block, sc.stages);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  void* args[] = {one ? (void*)one : (void*)&views, (void*)&tasks, (void*)&n_tasks};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(sc.grid);
   cfg.blockDim = dim3(32 * sc.warps_per_block);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -945,10 +1175,12 @@ cudaError_t launch_stream_collide_pairs(int precision, int phase, int moments, c
   return e;
 }
 
-int stream_collide_pairs_blocks_per_sm(int precision, int phase, int moments, int warps_per_block) {
-  void* k = pairs_kernel_for(precision, phase, moments);
+int stream_collide_pairs_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int stages) {
+  void* k = pairs_kernel_for(precision, phase, moments, stages, false);
+  const size_t smem = pairs_smem_bytes(precision, warps_per_block, stages);
   int n = 0;
-  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, 0) != cudaSuccess) return 1;
+  if (k && smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, smem) != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }
 

@@ -350,7 +350,7 @@ class Lattice:
         warps); persistent=2: on-chip resident steps (the shape follows from the lattice; the
         other arguments are ignored); persistent=3: compacted fluid-cell tasks (one cell per
         thread, 4-32 warps); persistent=4: paired tasks (interior 64-cell windows two cells a lane,
-        cells_per_thread=2, 4, 8, 12 or 24 warps).  Every shape computes the same values; LbmError
+        cells_per_thread=2, 4, 8, 12 or 24 warps, stages 0 or 2-4).  Every shape computes the same values; LbmError
         (status 1) for any other shape, or for modes 2 - 4 on lattices they do not serve."""
         _check(load_library().lbm_set_step_config(self._h, int(warps_per_block), int(persistent),
                                                   int(cells_per_thread), int(stages)), "lbm_set_step_config")

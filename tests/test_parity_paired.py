@@ -1,6 +1,7 @@
 """Paired tasks (launch mode 4): interior windows of 64 cells taken two cells
 a lane with paired loads and stores, every other row segment as in the
-default shape, in one launch per phase.
+default shape, in one launch per phase; the windows' pairs loaded into
+registers or copied into shared memory tasks ahead (stages).
 
 * The window count of the task list against a host-side count from the
   cell map (row y, cells 64p .. 64p+63 with rows y-1..y+1 fluid over cells
@@ -105,15 +106,19 @@ def test_window_count_after_an_exchange():
     h.close()
 
 
+@pytest.mark.parametrize("stages", [0, 3])
 @pytest.mark.parametrize("precision", [L.F32, L.BF16_SHIFTED, L.F16_SHIFTED])
 @pytest.mark.parametrize("k", range(4))
-def test_paired_tasks_compute_the_same_values(k, precision):
+def test_paired_tasks_compute_the_same_values(k, precision, stages):
+    """stages 0: windows loaded into registers; 3: copied into shared
+    memory two tasks ahead.  A single lattice takes the kernels with its
+    descriptor as a parameter; the batch test below the table-reading ones."""
     case = _cases()[k]
     a = _handle(case, precision)
     b = _handle(case, precision)
     a.set_step_config(8, persistent=False)
-    b.set_step_config(8, persistent=4, cells_per_thread=2)
-    assert b.step_config()[2] == 4 and b.step_config()[3] == 2
+    b.set_step_config(8, persistent=4, cells_per_thread=2, stages=stages)
+    assert b.step_config()[2] == 4 and b.step_config()[3] == 2 and b.step_config()[4] == stages
     ra, rb = a.solve(600), b.solve(600)
     assert ra["dp"] == rb["dp"] and ra["residual"] == rb["residual"]
     assert np.array_equal(ra["m_out"], rb["m_out"])
@@ -128,13 +133,14 @@ def test_paired_tasks_compute_the_same_values(k, precision):
     b.close()
 
 
-@pytest.mark.parametrize("wpb", [4, 12, 24])
-def test_block_shapes_compute_the_same_values(wpb):
+@pytest.mark.parametrize("precision", [L.F32, L.BF16_SHIFTED])
+@pytest.mark.parametrize("wpb,stages", [(4, 0), (12, 0), (24, 0), (4, 2), (12, 3), (24, 3), (8, 4), (24, 4)])
+def test_block_shapes_compute_the_same_values(wpb, stages, precision):
     case = _walls_case()
-    a = _handle(case, L.BF16_SHIFTED)
-    b = _handle(case, L.BF16_SHIFTED)
+    a = _handle(case, precision)
+    b = _handle(case, precision)
     a.set_step_config(8, persistent=4, cells_per_thread=2)
-    b.set_step_config(wpb, persistent=4, cells_per_thread=2)
+    b.set_step_config(wpb, persistent=4, cells_per_thread=2, stages=stages)
     ra, rb = a.solve(400), b.solve(400)
     assert ra["dp"] == rb["dp"]
     assert np.array_equal(a.read(L.FIELD_POPS), b.read(L.FIELD_POPS))
@@ -147,7 +153,7 @@ def test_paired_tasks_match_oracle(ora):
     cells = case["cells"]
     ny, nx = cells.shape
     h = L.Lattice(cells, case["tau"], case["u_max"], residual_every=0)
-    h.set_step_config(8, persistent=4, cells_per_thread=2)
+    h.set_step_config(8, persistent=4, cells_per_thread=2, stages=3)
     g = h.solve(400)
     s = ora.Solver(ora.make_params(nx, ny, case["tau"], 1.0, case["u_max"]), cells, residual_every=0)
     o = s.solve(400)
@@ -165,7 +171,7 @@ def test_paired_tasks_in_a_batch_and_where_refused():
     a = L.Batch(members, residual_every=0)
     b = L.Batch(members, residual_every=0)
     a.set_step_config(8, persistent=False)
-    b.set_step_config(12, persistent=4, cells_per_thread=2)
+    b.set_step_config(12, persistent=4, cells_per_thread=2, stages=3)
     ra, rb = a.solve(400), b.solve(400)
     assert [x["dp"] for x in ra] == [x["dp"] for x in rb]
     n = [5, 2, 7, 3]
@@ -176,9 +182,10 @@ def test_paired_tasks_in_a_batch_and_where_refused():
     a.close()
     b.close()
     h = _handle(_walls_case(), L.F32)
-    for wpb, cpt in ((16, 2), (32, 2), (8, 1)):  # block shapes the paired kernel does not take
+    # block shapes the paired kernel does not take
+    for wpb, cpt, stg in ((16, 2, 0), (32, 2, 0), (8, 1, 0), (8, 2, 1), (8, 2, 5), (8, 2, -1)):
         with pytest.raises(L.LbmError) as e:
-            h.set_step_config(wpb, persistent=4, cells_per_thread=cpt)
+            h.set_step_config(wpb, persistent=4, cells_per_thread=cpt, stages=stg)
         assert e.value.status == 1
     h.close()
     m = L.Lattice(I.config_collector()["cells"], 0.62, 0.12, outlet=L.OUT_NEUMANN, mirror=True)
