@@ -44,14 +44,17 @@ UNIT = "GLUPS"
 
 
 def parse():
+    from paper_1303_0107_gb300 import inputs as I
+    tree = I.load_config("tree_2048x1024_g4")
+    served = I.load_config("served_poisson_200")
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--iters", type=int, default=50, help="optimiser iterations per run")
-    ap.add_argument("--lattice-steps", type=int, default=5000, help="time steps per re-solve")
-    ap.add_argument("--first-steps", type=int, default=100000,
+    ap.add_argument("--iters", type=int, default=tree["n_iter"], help="optimiser iterations per run")
+    ap.add_argument("--lattice-steps", type=int, default=tree["steps"], help="time steps per re-solve")
+    ap.add_argument("--first-steps", type=int, default=tree["first_solve_steps"],
                     help="time steps of the first solve (run to a converged flow field)")
     ap.add_argument("--precision", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-extras", action="store_true", help="skip every leg after the main run")
@@ -63,8 +66,9 @@ def parse():
                          "d3q19 (the D3Q19 path: step rates, optimisation loop, oracle rate), "
                          "batched (256 candidates), served (request loop), "
                          "sweep (served at 50, 100, 200 and 400 requests/s, 10 s each; not in the default run)")
-    ap.add_argument("--serve-rate", type=float, default=200.0, help="served leg: Poisson arrivals per second")
-    ap.add_argument("--serve-seconds", type=float, default=30.0, help="served leg: arrival window")
+    ap.add_argument("--serve-rate", type=float, default=served["rate_per_s"],
+                    help="served leg: Poisson arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=served["seconds"], help="served leg: arrival window")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--log", default=None,
                     help="write one JSON line per solve of the timed runs (run, iteration, dp, m_in, residual, "

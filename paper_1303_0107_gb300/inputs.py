@@ -11,7 +11,9 @@ one inlet channel, 2^G parallel outlets, segment lengths in the 2:2:1:1
 proportion of Eq. 7 (the inlet trunk counted as 2), widths shrinking by a
 ratio r per generation.
 """
+import json
 import math
+import os
 
 import numpy as np
 
@@ -206,22 +208,44 @@ def random_blobs3d(nx: int, ny: int, nz: int, seed: int, density: float = 0.15) 
 
 
 # ---------------------------------------------------------------------------
-# Workload recipes.  Lattice units: dx = dt = 1, rho0 = 1.
+# Workload recipes.  Lattice units: dx = dt = 1, rho0 = 1.  The five
+# benchmark workloads are described by the JSON files in configs/ (the
+# generator and its parameters, tau, u_max, steps, iterations); the
+# functions below build them from those files.
 # ---------------------------------------------------------------------------
+
+CONFIG_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs")
+CONFIG_NAMES = ("t_junction_128x64", "tree_2048x1024_g4", "tree_2048x1024_g4_16bit", "candidates_256",
+                "served_poisson_200")
+
+
+def load_config(name: str) -> dict:
+    """The recipe configs/<name>.json (one of CONFIG_NAMES) as a dict."""
+    with open(os.path.join(CONFIG_DIR, name + ".json")) as f:
+        return json.load(f)
+
+
+def _tree_from(geo: dict, seed=None):
+    return tree(geo["nx"], geo["ny"], geo["generations"], geo["w0"], widths=geo.get("widths"),
+                jitter=geo["jitter"], seed=geo["seed"] if seed is None else seed)
+
 
 def config_t_junction(seed: int = 0):
     """128 x 64, one T: inlet 8 wide, two outlets 4 wide; tau 0.8, u_max 0.05, 10 x 2000 steps."""
-    cells = tree(128, 64, 1, 8, widths=[8, 4], jitter=2, seed=seed)
-    return dict(name="t_junction_128x64", cells=cells, nx=128, ny=64, tau=0.8, u_max=0.05,
-                n_iter=10, steps=2000)
+    c = load_config("t_junction_128x64")
+    g = c["geometry"]
+    return dict(name=c["name"], cells=_tree_from(g, seed), nx=g["nx"], ny=g["ny"], tau=c["tau"],
+                u_max=c["u_max"], n_iter=c["n_iter"], steps=c["steps"])
 
 
 def config_tree_2048(seed: int = 0):
     """2048 x 1024, four generations, widths 64/32/16/8/4, jitter +-2; Re = 50 on the
     64-wide inlet at nu = 0.01 (tau 0.53): mean inlet speed 0.0078125, u_max = 1.5x that."""
-    cells = tree(2048, 1024, 4, 64, widths=[64, 32, 16, 8, 4], jitter=2, seed=seed)
-    return dict(name="tree_2048x1024_g4", cells=cells, nx=2048, ny=1024, tau=0.53,
-                u_max=0.01171875, n_iter=50, steps=5000)
+    c = load_config("tree_2048x1024_g4")
+    g = c["geometry"]
+    return dict(name=c["name"], cells=_tree_from(g, seed), nx=g["nx"], ny=g["ny"], tau=c["tau"],
+                u_max=c["u_max"], n_iter=c["n_iter"], steps=c["steps"], first_solve_steps=c["first_solve_steps"],
+                n_swap=c["n_swap"])
 
 
 def config_collector():
@@ -253,18 +277,22 @@ def config_candidates(n: int = 256, base_seed: int = 0):
     """Uneven candidate distributors: nx log-uniform in [256, 1024] (multiple of 32),
     ny = nx/2, G in {2,3,4}, width ratio in [0.6, 0.8], W0 = ny/16; tau 0.53 and
     Re = 50 on the inlet (u_max = 1.5 * 50 * 0.01 / W0)."""
+    c = load_config("candidates_256")
+    lo, hi = c["nx_range"]
+    mult = c["nx_multiple"]
+    gens = c["generations"]
     out = []
-    for c in range(n):
-        s = base_seed + c
+    for k in range(n):
+        s = base_seed + k
         u = uniform01(s, 1)
-        nx = int(round(math.exp(math.log(256) + u * (math.log(1024) - math.log(256))) / 32.0)) * 32
+        nx = int(round(math.exp(math.log(lo) + u * (math.log(hi) - math.log(lo))) / float(mult))) * mult
         ny = nx // 2
-        G = 2 + int(splitmix64(s, 2) % 3)
-        r = 0.6 + 0.2 * uniform01(s, 3)
-        w0 = max(8, ny // 16)
-        cells = tree(nx, ny, G, w0, ratio=r, jitter=2, seed=s)
-        out.append(dict(name=f"cand{c}", cells=cells, nx=nx, ny=ny, tau=0.53,
-                        u_max=1.5 * 50 * 0.01 / w0, generations=G, ratio=r, seed=s))
+        G = gens[0] + int(splitmix64(s, 2) % len(gens))
+        r = c["ratio_min"] + c["ratio_span"] * uniform01(s, 3)
+        w0 = max(c["w0_min"], ny // c["w0_divisor"])
+        cells = tree(nx, ny, G, w0, ratio=r, jitter=c["jitter"], seed=s)
+        out.append(dict(name=f"cand{k}", cells=cells, nx=nx, ny=ny, tau=c["tau"],
+                        u_max=1.5 * c["reynolds"] * c["nu"] / w0, generations=G, ratio=r, seed=s))
     return out
 
 
@@ -288,16 +316,19 @@ def config_tree3d(nx: int = 384, ny: int = 192, nz: int = 192):
 def config_served_request(seed: int):
     """One served request: nx log-uniform in [128, 2048], ny = nx/2,
     G = clamp(floor(log2(nx/128)) + 1, 1, 4), W0 = max(8, ny/16), r = 0.5."""
+    c = load_config("served_poisson_200")
+    lo, hi = c["nx_range"]
+    mult = c["nx_multiple"]
     u = uniform01(seed, 11)
-    nx = int(round(math.exp(math.log(128) + u * (math.log(2048) - math.log(128))) / 32.0)) * 32
+    nx = int(round(math.exp(math.log(lo) + u * (math.log(hi) - math.log(lo))) / float(mult))) * mult
     ny = nx // 2
-    G = min(4, max(1, int(math.floor(math.log2(nx / 128.0))) + 1))
-    w0 = max(8, ny // 16)
-    cells = tree(nx, ny, G, w0, ratio=0.5, jitter=2, seed=seed)
-    optimize = uniform01(seed, 12) < 0.2
-    return dict(name=f"req{seed}", cells=cells, nx=nx, ny=ny, tau=0.53,
-                u_max=min(0.05, 1.5 * 50 * 0.01 / w0), optimize=optimize, steps=1000,
-                n_iter=20 if optimize else 0, seed=seed)
+    G = min(4, max(1, int(math.floor(math.log2(nx / float(lo)))) + 1))
+    w0 = max(c["w0_min"], ny // c["w0_divisor"])
+    cells = tree(nx, ny, G, w0, ratio=c["ratio"], jitter=c["jitter"], seed=seed)
+    optimize = uniform01(seed, 12) < c["optimize_fraction"]
+    return dict(name=f"req{seed}", cells=cells, nx=nx, ny=ny, tau=c["tau"],
+                u_max=min(c["u_max_cap"], 1.5 * c["reynolds"] * c["nu"] / w0), optimize=optimize,
+                steps=c["solve_steps"], n_iter=c["optimize_iterations"] if optimize else 0, seed=seed)
 
 
 def poisson_arrivals(rate_hz: float, duration_s: float, seed: int):
