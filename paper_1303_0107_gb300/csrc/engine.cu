@@ -503,8 +503,8 @@ StepConfig persistent_shape(Engine* E, int wpb, int cpt = 1) {
 }
 
 // The compacted-task shape: one cell per thread, 32 fluid cells a warp.
-StepConfig cells_shape(Engine* E, int wpb, int blocks_per_sm_scale) {
-  const int bps = stream_collide_cells_blocks_per_sm(E->precision, 0, 0, wpb);
+StepConfig cells_shape(Engine* E, int wpb, int blocks_per_sm_scale, int stages = 0) {
+  const int bps = stream_collide_cells_blocks_per_sm(E->precision, 0, 0, wpb, stages);
   const long long cap = (long long)E->sm_count * bps * blocks_per_sm_scale;
   long long fluid = 0;
   for (const Member* m : E->m) fluid += m->fluid_cells;
@@ -514,7 +514,7 @@ StepConfig cells_shape(Engine* E, int wpb, int blocks_per_sm_scale) {
   c.grid = (int)std::max<long long>(1, std::min(need, cap));
   c.persistent = 3;
   c.cells_per_thread = 1;
-  c.stages = 0;
+  c.stages = stages;
   c.features = 0;
   return c;
 }
@@ -637,11 +637,12 @@ lbm_status autotune(Engine* E) {
       for (void* b : backups) cudaFree(b);
       return cst;
     }
-    for (int wpb : {4, 8, 16, 32})
-      for (int scale : {1, 2}) {
-        if (wpb == 32 && scale != 1) continue;
-        cand.push_back(cells_shape(E, wpb, scale));
-      }
+    for (int stages : {0, 2, 3})
+      for (int wpb : {4, 8, 16, 32})
+        for (int scale : {1, 2}) {
+          if ((wpb == 32 && (scale != 1 || stages)) || (stages && scale != 1)) continue;
+          cand.push_back(cells_shape(E, wpb, scale, stages));
+        }
   }
   if (pairs_eligible(E)) {
     lbm_status pst = ensure_pairs(E);
@@ -1597,20 +1598,23 @@ lbm_status engine_set_step_config(Engine* E, int32_t warps_per_block, int32_t pe
     E->tuned = true;
     return LBM_OK;
   }
-  if (stages != 0 && stages != 2 && stages != 3) return fail(LBM_ERR_ARG, "stages must be 0, 2 or 3");
-  if (stages != 0 && (persistent || cells_per_thread != 1))
-    return fail(LBM_ERR_ARG, "staged loads take one cell per thread and per-phase launches");
   if (persistent == 3) {  // compacted fluid-cell tasks
     if (!cells_eligible(E))
       return fail(LBM_ERR_ARG, "cell tasks need plain BGK lattices without a zero-gradient outlet");
-    if (!step_shape_allowed(warps_per_block, 1, 3) || cells_per_thread != 1 || stages != 0)
-      return fail(LBM_ERR_ARG, "cell tasks take one cell per thread and 4, 8, 12, 16 or 32 warps per block");
+    if (!step_shape_allowed(warps_per_block, 1, 3) || cells_per_thread != 1 ||
+        (stages != 0 && (stages < 2 || stages > 4 || warps_per_block > 16)))
+      return fail(LBM_ERR_ARG,
+                  "cell tasks take one cell per thread, 4, 8, 12, 16 or 32 warps per block, and stages 0 or 2-4 "
+                  "(at most 16 warps with stages)");
     lbm_status st = ensure_cells(E);
     if (st != LBM_OK) return st;
-    E->step = cells_shape(E, warps_per_block, kDefaultGridScale);
+    E->step = cells_shape(E, warps_per_block, kDefaultGridScale, stages);
     E->tuned = true;
     return LBM_OK;
   }
+  if (stages != 0 && stages != 2 && stages != 3) return fail(LBM_ERR_ARG, "stages must be 0, 2 or 3");
+  if (stages != 0 && (persistent || cells_per_thread != 1))
+    return fail(LBM_ERR_ARG, "staged loads take one cell per thread and per-phase launches");
   if (persistent != 0 && persistent != 1) return fail(LBM_ERR_ARG, "persistent must be 0, 1, 2, 3 or 4");
   if (cells_per_thread != 1 && cells_per_thread != 2) return fail(LBM_ERR_ARG, "cells_per_thread must be 1 or 2");
   if (!step_shape_allowed(warps_per_block, cells_per_thread, persistent))

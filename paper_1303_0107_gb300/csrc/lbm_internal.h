@@ -139,12 +139,14 @@ constexpr int kCellLatticeBits = 20;
 cudaError_t launch_build_cells(const LatticeView* views, const SegRef* segs, const int* n_segs, int capacity,
                                int* cnt, int* cpre, int* tmp, CellRef* cells, cudaStream_t stream);
 // One phase over the compacted list (sc.warps_per_block, sc.grid; one cell
-// per thread), a programmatic dependent launch like launch_stream_collide.
+// per thread; sc.stages 0: populations into registers, 2-4: copied into
+// shared memory that many tasks ahead, at most 16 warps per block), a
+// programmatic dependent launch like launch_stream_collide.
 // Plain BGK lattices without a zero-gradient outlet only.
 cudaError_t launch_stream_collide_cells(int precision, int phase, int moments, const LatticeView* views,
                                         const CellRef* cells, const int* n_segs, const int* cpre, StepConfig sc,
                                         cudaStream_t stream);
-int stream_collide_cells_blocks_per_sm(int precision, int phase, int moments, int warps_per_block);
+int stream_collide_cells_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int stages);
 // Paired tasks: an entry {lattice | kPairTask, (y << kSegWordBits) | p} is
 // the interior window of 64 cells of row y, mask words 2p and 2p+1 (its
 // cells and all their neighbours fluid), taken by one warp two cells a

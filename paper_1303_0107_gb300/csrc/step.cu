@@ -394,14 +394,6 @@ void* pick_cells(int phase, int moments) {
   return (void*)k_stream_collide_cells<T, 1, 0>;
 }
 
-void* cells_kernel_for(int precision, int phase, int moments) {
-  switch (precision) {
-    case LBM_F32: return pick_cells<float>(phase, moments);
-    case LBM_BF16_SHIFTED: return pick_cells<__nv_bfloat16>(phase, moments);
-    case LBM_F16_SHIFTED: return pick_cells<__half>(phase, moments);
-    default: return nullptr;
-  }
-}
 
 // ---- paired tasks: interior 64-cell windows, two cells a lane ------------
 //
@@ -784,6 +776,93 @@ __global__ void __launch_bounds__(512, 2)
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// ---- staged cell tasks --------------------------------------------------------
+//
+// The compacted cell tasks of k_stream_collide_cells are bound by memory
+// latency on the candidate batches (one cell a lane, nine scalar loads; a
+// long-scoreboard stall of 20-28 per issued instruction at a quarter of the
+// issue slots).  Here each warp copies the nine incoming populations of its
+// task NS-1 tasks ahead into shared memory, as k_stream_collide_staged does
+// for row segments; the cell's offset and flags come from its list entry.
+template <class T, int PHASE>
+__device__ __forceinline__ void cell_stage_issue(const LatticeView* __restrict__ views,
+                                                 const CellRef* __restrict__ cells, int ncell, int t, int lane,
+                                                 uint32_t* buf) {
+  const int e = (t << 5) + lane;
+  const bool valid = e < ncell;
+  const CellRef cr = cells[valid ? e : 0];
+  const unsigned lat = valid ? (cr.meta & ((1u << kCellLatticeBits) - 1u)) : 0u;
+  const LatticeView* __restrict__ L = views + lat;
+  const T* F = static_cast<const T*>(L->f);
+  const unsigned nb = (cr.meta >> kCellLatticeBits) & 0x1ffu;
+  const bool inlet = valid && ((cr.meta >> 29) & 1u), outlet = valid && ((cr.meta >> 30) & 1u);
+  const int pitch = L->pitch, pl = (int)L->plane;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int off = valid ? src_off<PHASE>(i, cr.c, pitch, pl, nb, inlet, outlet) : -1;
+    cp_async_word<T>(buf + i * 32 + lane, F, off, L->f_elems);
+  }
+  buf[9 * 32 + lane] = valid ? (uint32_t)cr.c : 0u;
+  buf[10 * 32 + lane] = nb | ((uint32_t)valid << 9) | ((uint32_t)inlet << 10) | ((uint32_t)outlet << 11) | (lat << 12);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <class T, int PHASE, int MOM, int NS>
+__global__ void __launch_bounds__(512, 2)
+    k_stream_collide_cells_staged(const LatticeView* __restrict__ views, const CellRef* __restrict__ cells,
+                                  const int* __restrict__ n_segs, const int* __restrict__ cpre) {
+  extern __shared__ uint32_t stage_smem[];
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int ncell = cpre[n_segs[0]];
+  const int ntask = (ncell + 31) >> 5;
+  const int stride = gridDim.x * wpb;
+  const int first = blockIdx.x * wpb + warp;
+  uint32_t* wbuf = stage_smem + (size_t)warp * NS * kStageWords;
+  // populations of the previous step are final from here on
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k)
+    cell_stage_issue<T, PHASE>(views, cells, ncell, first + k * stride, lane, wbuf + k * kStageWords);
+  for (int k = 0; first + k * stride < ntask; ++k) {
+    cell_stage_issue<T, PHASE>(views, cells, ncell, first + (k + NS - 1) * stride, lane,
+                               wbuf + ((k + NS - 1) % NS) * kStageWords);
+    cp_async_wait<NS>();  // this lane's copies of task k have landed (each lane reads only its own)
+    stage_consume<T, PHASE, MOM>(views, wbuf + (k % NS) * kStageWords, lane);
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <class T, int NS>
+void* pick_cells_staged(int phase, int moments) {
+  if (phase == 0) return (void*)k_stream_collide_cells_staged<T, 0, 0, NS>;
+  if (moments == 1) return (void*)k_stream_collide_cells_staged<T, 1, 1, NS>;
+  if (moments == 2) return (void*)k_stream_collide_cells_staged<T, 1, 2, NS>;
+  return (void*)k_stream_collide_cells_staged<T, 1, 0, NS>;
+}
+
+template <class T>
+void* pick_cells_any(int phase, int moments, int stages) {
+  switch (stages) {
+    case 0: return pick_cells<T>(phase, moments);
+    case 2: return pick_cells_staged<T, 2>(phase, moments);
+    case 3: return pick_cells_staged<T, 3>(phase, moments);
+    case 4: return pick_cells_staged<T, 4>(phase, moments);
+    default: return nullptr;
+  }
+}
+
+void* cells_kernel_for(int precision, int phase, int moments, int stages) {
+  switch (precision) {
+    case LBM_F32: return pick_cells_any<float>(phase, moments, stages);
+    case LBM_BF16_SHIFTED: return pick_cells_any<__nv_bfloat16>(phase, moments, stages);
+    case LBM_F16_SHIFTED: return pick_cells_any<__half>(phase, moments, stages);
+    default: return nullptr;
+  }
+}
+
 // ---- staged paired tasks ----------------------------------------------------
 //
 // The paired kernel keeps one window's pairs in flight per lane (36 bytes
@@ -1134,8 +1213,11 @@ cudaError_t launch_stream_collide(int precision, int phase, int moments, const L
 cudaError_t launch_stream_collide_cells(int precision, int phase, int moments, const LatticeView* views,
                                         const CellRef* cells, const int* n_segs, const int* cpre, StepConfig sc,
                                         cudaStream_t stream) {
-  void* k = cells_kernel_for(precision, phase, moments);
-  if (!k || sc.warps_per_block < 1 || sc.warps_per_block > 32 || sc.grid < 1) return cudaErrorInvalidValue;
+  void* k = cells_kernel_for(precision, phase, moments, sc.stages);
+  if (!k || sc.warps_per_block < 1 || sc.warps_per_block > (sc.stages ? 16 : 32) || sc.grid < 1)
+    return cudaErrorInvalidValue;
+  const size_t smem = sc.stages ? staged_smem_bytes(sc.warps_per_block, sc.stages) : 0;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   void* args[] = {(void*)&views, (void*)&cells, (void*)&n_segs, (void*)&cpre};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1143,6 +1225,7 @@ cudaError_t launch_stream_collide_cells(int precision, int phase, int moments, c
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(sc.grid);
   cfg.blockDim = dim3(32 * sc.warps_per_block);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -1184,10 +1267,12 @@ int stream_collide_pairs_blocks_per_sm(int precision, int phase, int moments, in
   return n > 0 ? n : 1;
 }
 
-int stream_collide_cells_blocks_per_sm(int precision, int phase, int moments, int warps_per_block) {
-  void* k = cells_kernel_for(precision, phase, moments);
+int stream_collide_cells_blocks_per_sm(int precision, int phase, int moments, int warps_per_block, int stages) {
+  void* k = cells_kernel_for(precision, phase, moments, stages);
+  const size_t smem = stages ? staged_smem_bytes(warps_per_block, stages) : 0;
   int n = 0;
-  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, 0) != cudaSuccess) return 1;
+  if (k && smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * warps_per_block, smem) != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }
 

@@ -173,17 +173,19 @@ def test_barrier_wait_gives_up_and_the_handle_stays_usable():
     h.close()
 
 
+@pytest.mark.parametrize("stages", [0, 2, 3])
 @pytest.mark.parametrize("precision", [L.F32, L.BF16_SHIFTED, L.F16_SHIFTED])
 @pytest.mark.parametrize("k", [0, 2, 3])
-def test_cell_tasks_compute_the_same_values(k, precision):
-    """Compacted fluid-cell tasks (32 consecutive fluid cells per warp)
-    against the default row-segment shape, bit for bit, through exchanges
-    (the cell list is rebuilt with the work-list)."""
+def test_cell_tasks_compute_the_same_values(k, precision, stages):
+    """Compacted fluid-cell tasks (32 consecutive fluid cells per warp; their
+    populations into registers, or copied into shared memory 1-2 tasks
+    ahead) against the default row-segment shape, bit for bit, through
+    exchanges (the cell list is rebuilt with the work-list)."""
     case = _cases()[k]
     a = _handle(case, precision, False)
     b = _handle(case, precision, False)
-    b.set_step_config(8, persistent=3)
-    assert b.step_config()[2] == 3
+    b.set_step_config(8, persistent=3, stages=stages)
+    assert b.step_config()[2] == 3 and b.step_config()[4] == stages
     ra, rb = a.solve(600), b.solve(600)
     assert ra["dp"] == rb["dp"] and ra["residual"] == rb["residual"]
     assert np.array_equal(a.read(L.FIELD_POPS), b.read(L.FIELD_POPS))
@@ -202,7 +204,7 @@ def test_cell_tasks_in_a_batch_and_where_refused():
     a = L.Batch(members, residual_every=0)
     b = L.Batch(members, residual_every=0)
     a.set_step_config(8, persistent=False)
-    b.set_step_config(16, persistent=3)
+    b.set_step_config(16, persistent=3, stages=3)
     ra, rb = a.solve(400), b.solve(400)
     assert [x["dp"] for x in ra] == [x["dp"] for x in rb]
     n = [3, 1, 4][:len(members)]
@@ -212,6 +214,12 @@ def test_cell_tasks_in_a_batch_and_where_refused():
         assert np.array_equal(a.read(i, L.FIELD_POPS), b.read(i, L.FIELD_POPS)), i
     a.close()
     b.close()
+    t = _handle(_cases()[0], L.F32, False)
+    for wpb, stg in ((32, 2), (8, 1), (8, 5)):  # 32 warps with stages; stages outside 0, 2-4
+        with pytest.raises(L.LbmError) as e:
+            t.set_step_config(wpb, persistent=3, stages=stg)
+        assert e.value.status == 1
+    t.close()
     neumann = _handle(_cases()[1], L.F32, False)  # a zero-gradient outlet: refused
     with pytest.raises(L.LbmError) as e:
         neumann.set_step_config(8, persistent=3)
