@@ -89,7 +89,8 @@ def parse():
                     help="kernel case (2D, batch): compacted fluid-cell tasks (32 consecutive fluid cells a warp)")
     ap.add_argument("--kernel-wpb", type=int, default=8, help="kernel case: warps per block of a fixed shape")
     ap.add_argument("--kernel-stages", type=int, default=0,
-                    help="kernel case, paired tasks: windows copied into shared memory this many tasks ahead")
+                    help="kernel case, paired or cell tasks: populations copied into shared memory this many "
+                         "tasks ahead")
     return ap.parse_args()
 
 
@@ -119,7 +120,7 @@ def kernel_case(args):
         if args.kernel_paired:
             b.set_step_config(args.kernel_wpb, persistent=4, cells_per_thread=2, stages=args.kernel_stages)
         elif args.kernel_cells:
-            b.set_step_config(args.kernel_wpb, persistent=3)
+            b.set_step_config(args.kernel_wpb, persistent=3, stages=args.kernel_stages)
         b.solve(args.kernel_steps)
         r = b.solve(args.kernel_steps)
         shape = b.step_config()

@@ -319,7 +319,10 @@ lbm_status launch_pair(Engine* E, int moments) {
     const int* cpre = static_cast<const int*>(E->cell_scan.p) + std::max(1, E->L.total_seg_words);
     CU(launch_stream_collide_cells(E->precision, 0, 0, views, cells, n_segs, cpre, E->step, E->stream));
     DEBUG_SYNC(E, "stream-collide phase A (cell tasks)");
-    CU(launch_stream_collide_cells(E->precision, 1, moments, views, cells, n_segs, cpre, E->step, E->stream));
+    // staging pays in the shifted phase only (measured): the local phase loads directly
+    StepConfig local = E->step;
+    local.stages = 0;
+    CU(launch_stream_collide_cells(E->precision, 1, moments, views, cells, n_segs, cpre, local, E->stream));
     DEBUG_SYNC(E, "stream-collide phase B (cell tasks)");
     return LBM_OK;
   }
