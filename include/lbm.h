@@ -398,9 +398,20 @@ lbm_status lbm_batch_reset(lbm_batch b);
 /* As lbm_kernel_time, for the batch's time steps (fluid_updates over all members). */
 lbm_status lbm_batch_kernel_time(lbm_batch b, int reset, double* ms, int64_t* launches,
                                  int64_t* fluid_updates);
-/* As lbm_step_config / lbm_set_step_config.                               */
+/* As lbm_step_config / lbm_set_step_config.  A batch whose populations
+ * exceed the L2 cache runs its time steps in member groups of about a third
+ * of the L2 each (members in order, each group with its own work-list and
+ * tuned shape), so that a group stays L2-resident through a solve;
+ * reductions and exchanges run over the whole batch, and every member
+ * evolves exactly as alone.  lbm_batch_step_config then reports the first
+ * group's shape; lbm_batch_set_step_config fixes one shape for the whole
+ * batch and ends the grouping.  LBM_GROUPS=0 in the environment turns it
+ * off.                                                                    */
 lbm_status lbm_batch_step_config(lbm_batch b, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
                                  int32_t* cells_per_thread, int32_t* stages);
+/* Number of member groups the batch's time steps run in (1: not grouped;
+ * decided at the first solve of 256 steps or more).  n_groups: host.      */
+lbm_status lbm_batch_step_groups(lbm_batch b, int32_t* n_groups);
 lbm_status lbm_batch_set_step_config(lbm_batch b, int32_t warps_per_block, int32_t persistent,
                                      int32_t cells_per_thread, int32_t stages);
 void lbm_batch_destroy(lbm_batch b);

@@ -248,6 +248,12 @@ lbm_status lbm_batch_kernel_time(lbm_batch b, int reset, double* ms, int64_t* la
   return engine_kernel_time(b->e, reset, ms, launches, fluid_updates);
 }
 
+lbm_status lbm_batch_step_groups(lbm_batch b, int32_t* n_groups) {
+  if (!b || !n_groups) return fail(LBM_ERR_ARG, "batch or output is NULL");
+  *n_groups = engine_step_groups(b->e);
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_step_config(lbm_batch b, int32_t* warps_per_block, int32_t* grid, int32_t* persistent,
                                  int32_t* cells_per_thread, int32_t* stages) {
   if (!b) return fail(LBM_ERR_ARG, "batch is NULL");

@@ -142,6 +142,14 @@ struct Engine {
   StepConfig step{kStepWarps, 1, 0, 1, 0, 0};
   int features = 0;  // kernel build the members need: 1 collision models, 2 symmetry plane
   bool tuned = false;
+  bool shape_fixed = false;  // set with engine_set_step_config: no tuning, no member groups
+  // Member groups of a batch whose populations exceed the L2 cache: each
+  // group's time steps run on an engine of its own (sharing the members and
+  // the stream, with its own work-list and tuned shape) so that they stay
+  // L2-resident; reductions and exchanges stay with this engine.
+  std::vector<Engine*> groups;
+  bool groups_decided = false;
+  bool in_group = false;  // this engine steps one group of another engine's members
   cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
   double step_ms = 0.0;
   int64_t step_launches = 0, fluid_updates = 0;
@@ -160,6 +168,8 @@ lbm_status engine_set_members(Engine* E, const std::vector<Member*>& members);
 lbm_status engine_create(int n, const lbm_params* params, const uint8_t* const* cells, void* cuda_stream,
                          Engine** out);
 lbm_status engine_reset(Engine* E);
+// Number of member groups the time steps run in (1 when not grouped).
+int engine_step_groups(const Engine* E);
 lbm_status rebuild_worklist(Engine* E);
 // Plan the resident launch for the current work-list (synchronises the
 // stream when the list changed since the last plan); *ok: the set fits.

@@ -156,6 +156,7 @@ def load_library(path=None):
     L.lbm_batch_kernel_time.argtypes = [B, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.lbm_batch_step_config.argtypes = [B] + [ctypes.POINTER(ctypes.c_int32)] * 5
+    L.lbm_batch_step_groups.argtypes = [B, ctypes.c_void_p]
     L.lbm_batch_set_step_config.argtypes = [B, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     L.lbm_batch_destroy.argtypes = [B]
     L.lbm_batch_destroy.restype = None
@@ -468,6 +469,12 @@ class Batch:
         v = [ctypes.c_int32() for _ in range(5)]
         _check(load_library().lbm_batch_step_config(self._b, *[ctypes.byref(x) for x in v]), "lbm_batch_step_config")
         return tuple(x.value for x in v)
+
+    def step_groups(self) -> int:
+        """Member groups the time steps run in (lbm_batch_step_groups; 1: not grouped)."""
+        n = ctypes.c_int32()
+        _check(load_library().lbm_batch_step_groups(self._b, ctypes.byref(n)), "lbm_batch_step_groups")
+        return n.value
 
     def set_step_config(self, warps_per_block, persistent=False, cells_per_thread=1, stages=0):
         """As Lattice.set_step_config, for every lattice of the batch."""

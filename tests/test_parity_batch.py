@@ -88,3 +88,41 @@ def test_batch_reset_and_errors():
     with pytest.raises(L.LbmError):
         L.Batch([dict(cells=I.channel(33, 8), tau=0.8, u_max=0.01, outlet=L.OUT_NEUMANN)])
     batch.close()
+
+
+def test_member_groups_equal_the_ungrouped_batch(monkeypatch):
+    """A batch whose populations exceed the group budget runs its time steps
+    in member groups (each with its own work-list and tuned shape); every
+    member's populations, fields and reductions equal those of the same
+    batch stepped as one set with a fixed shape, bit for bit, through
+    solves with the residual and through exchanges (the groups' lists are
+    rebuilt with the batch's)."""
+    cands = [c for c in I.config_candidates(80, base_seed=40) if int((c["cells"] == 0).sum()) < 25000][:14]
+    members = [dict(cells=c["cells"], tau=c["tau"], u_max=c["u_max"]) for c in cands]
+    fluid = [int((c["cells"] == 0).sum()) for c in cands]
+    budget = 4 * 9 * 4 * max(fluid)  # FP32 population bytes of four of the largest members
+    assert 9 * 4 * sum(fluid) > 1.5 * budget
+    monkeypatch.setenv("LBM_GROUP_BYTES", str(budget))
+    a = L.Batch(members, residual_every=100)
+    b = L.Batch(members, residual_every=100)
+    b.set_step_config(8, persistent=False)
+    ra, rb = a.solve(400), b.solve(400)
+    assert a.step_groups() > 1 and b.step_groups() == 1
+    assert [x["dp"] for x in ra] == [x["dp"] for x in rb]
+    assert [x["residual"] for x in ra] == [x["residual"] for x in rb]
+    n = [max(1, f // 400) for f in fluid]
+    for _ in range(2):
+        oa, ob = a.optimize_step(n, 300), b.optimize_step(n, 300)
+        assert [x["dp"] for x in oa] == [x["dp"] for x in ob]
+        assert [x["n_swapped"] for x in oa] == [x["n_swapped"] for x in ob]
+    for i in range(len(members)):
+        for f in (L.FIELD_MASK, L.FIELD_POPS, L.FIELD_UX, L.FIELD_DRHO):
+            assert np.array_equal(a.read(i, f), b.read(i, f)), (i, f)
+    ta, tb = a.kernel_time(), b.kernel_time()
+    assert ta[2] == tb[2]  # the same fluid-cell updates counted
+    a.set_step_config(8, persistent=False)  # a fixed shape ends the grouping
+    assert a.step_groups() == 1
+    ra, rb = a.solve(200), b.solve(200)
+    assert [x["dp"] for x in ra] == [x["dp"] for x in rb]
+    a.close()
+    b.close()
