@@ -1296,11 +1296,17 @@ lbm_status ensure_groups(Engine* E) {
   for (const auto& part : parts) {
     Engine* g = nullptr;
     lbm_status st = engine_new(E->precision, E->residual_every, E->stream, false, &g);
-    if (st != LBM_OK) return st;
-    g->own_members = false;
-    g->in_group = true;
-    E->groups.push_back(g);  // owned by E from here on
-    if ((st = engine_set_members(g, part)) != LBM_OK) return st;
+    if (st == LBM_OK) {
+      g->own_members = false;
+      g->in_group = true;
+      E->groups.push_back(g);  // owned by E from here on
+      st = engine_set_members(g, part);
+    }
+    if (st != LBM_OK) {  // no half-built grouping: the batch steps as one set
+      for (Engine* x : E->groups) delete x;
+      E->groups.clear();
+      return st;
+    }
   }
   return LBM_OK;
 }
