@@ -126,3 +126,32 @@ def test_member_groups_equal_the_ungrouped_batch(monkeypatch):
     assert [x["dp"] for x in ra] == [x["dp"] for x in rb]
     a.close()
     b.close()
+
+
+def test_full_candidate_batch_in_groups_matches_alone_and_oracle(ora):
+    """The benchmark's batch at full size, in the launch configuration the
+    bench times (member groups, tuned shapes): sampled members equal their
+    runs alone bit for bit (a handle may pick another kernel; every kernel
+    computes the same bits per cell), and one member matches the FP64
+    oracle at the FP32 tolerance."""
+    cands = I.config_candidates(256)
+    members = [dict(cells=c["cells"], tau=c["tau"], u_max=c["u_max"]) for c in cands]
+    b = L.Batch(members, residual_every=0)
+    rb = b.solve(600)
+    assert b.step_groups() > 1
+    for i in (0, 37, 101, 200, 255):
+        c = cands[i]
+        h = L.Lattice(c["cells"], c["tau"], c["u_max"], residual_every=0)
+        r = h.solve(600)
+        assert r["dp"] == rb[i]["dp"] and np.array_equal(r["m_out"], rb[i]["m_out"]), i
+        assert np.array_equal(h.read(L.FIELD_POPS), b.read(i, L.FIELD_POPS)), i
+        h.close()
+    k = 37
+    cells = cands[k]["cells"]
+    ny, nx = cells.shape
+    s = ora.Solver(ora.make_params(nx, ny, cands[k]["tau"], 1.0, cands[k]["u_max"]), cells, residual_every=0)
+    o = s.solve(600)
+    ux = b.read(k, L.FIELD_UX).astype(np.float64)
+    assert np.abs(ux - s.ux).max() / np.abs(s.ux).max() <= 1e-5
+    assert abs(rb[k]["dp"] - o["dp"]) <= 1e-5 * abs(o["dp"])
+    b.close()
