@@ -498,7 +498,7 @@ def leg_d3q19(L, I, stream, peak, cpu_seconds=4.0):
     return out
 
 
-def leg_batched(L, I, stream, prec, n=256, iters=10, S=2000, sample=32):
+def leg_batched(L, I, stream, prec, n=256, iters=10, S=2000, sample=32, peak=None):
     """256 uneven candidate distributors in one batch (one launch per stage
     for all) against the same candidates one at a time through their own
     handles (a sample of them, creation excluded)."""
@@ -519,6 +519,7 @@ def leg_batched(L, I, stream, prec, n=256, iters=10, S=2000, sample=32):
     t_batch = time.perf_counter() - t0
     ms, nl, nu = b.kernel_time()
     w, g, pers, cpt, stg = b.step_config()
+    n_groups = b.step_groups()
     b.close()
     upd = sum(fluid) * S * (iters + 1)
     idx = list(range(0, n, max(1, n // sample)))[:sample]
@@ -542,6 +543,9 @@ def leg_batched(L, I, stream, prec, n=256, iters=10, S=2000, sample=32):
     g_plain = upd_plain / t_plain / 1e9
     return {"candidates": n, "fluid_cells": sum(fluid), "iterations": iters, "steps_per_solve": S,
             "batched_glups": g_batch, "batched_step_glups": nu / (ms / 1e3) / 1e9,
+            "batched_step_frac_of_measured_hbm": (nu / (ms / 1e3) * L.bytes_per_fluid_update(prec) / 1e9 / peak
+                                                  if peak else None),
+            "member_groups": n_groups,
             "batched_s": t_batch, "step_config": [w, g, pers, cpt, stg],
             "one_at_a_time_glups": g_plain, "one_at_a_time_sample": len(idx),
             "speedup": g_batch / g_plain, "dp_rel_diff_batched_vs_alone_max": worst}
@@ -859,7 +863,7 @@ def main():
         extras["collision_models_tree_2048"] = leg_models(L, I, stream)
     if rank == 0 and "batched" in legs:
         for pname, pv in (("f32", L.F32), ("bf16", L.BF16_SHIFTED)):
-            extras[f"batched_256_{pname}"] = leg_batched(L, I, stream, pv)
+            extras[f"batched_256_{pname}"] = leg_batched(L, I, stream, pv, peak=peak)
     if rank == 0 and "served" in legs:
         extras["served_f32"] = leg_served(L, I, L.F32, args.serve_rate, args.serve_seconds)
     if rank == 0 and "sweep" in legs:
@@ -919,6 +923,7 @@ def leg_summary(extras):
         put(f"batched_{p}_glups", extras.get(f"batched_256_{p}"), "batched_glups")
         put(f"batched_{p}_step_glups", extras.get(f"batched_256_{p}"), "batched_step_glups")
         put(f"batched_{p}_speedup", extras.get(f"batched_256_{p}"), "speedup")
+        put(f"batched_{p}_step_frac", extras.get(f"batched_256_{p}"), "batched_step_frac_of_measured_hbm")
     prec = extras.get("precision_tree_2048", {})
     for p in ("bf16", "f16"):
         put(f"tree_{p}_vs_f32", prec.get(p), "glups_vs_f32")
