@@ -514,7 +514,7 @@ StepConfig cells_shape(Engine* E, int wpb, int blocks_per_sm_scale, int stages =
   const long long need = ((fluid + 31) / 32 + wpb - 1) / wpb;
   StepConfig c;
   c.warps_per_block = wpb;
-  c.grid = (int)std::max<long long>(1, std::min(need, cap));
+  c.grid = (int)(E->fixed_grid ? cap : std::max<long long>(1, std::min(need, cap)));
   c.persistent = 3;
   c.cells_per_thread = 1;
   c.stages = stages;
@@ -1165,7 +1165,17 @@ lbm_status engine_set_members(Engine* E, const std::vector<Member*>& members) {
   CU(E->dense_f.reserve((size_t)std::max<long long>(1, max_cells) * 4));
   st = ensure_pinned(E, nn);
   if (st != LBM_OK) return st;
-  if (!E->tuned || E->fixed_grid) E->step = shape(E, E->step.warps_per_block, kDefaultGridScale);
+  if (E->fixed_grid) {
+    // the request loop's engine is never tuned (its members change every
+    // tick): compacted cell tasks at 4 warps a block, the tuner's pick for
+    // L2-resident sets of candidate distributors, where every request allows
+    // them; the grid is sized for the device either way
+    const char* e = std::getenv("LBM_SERVER_CELLS");
+    const bool cells = !(e && e[0] == '0') && cells_eligible(E);
+    E->step = cells ? cells_shape(E, 4, kDefaultGridScale) : shape(E, kStepWarps, kDefaultGridScale);
+  } else if (!E->tuned) {
+    E->step = shape(E, E->step.warps_per_block, kDefaultGridScale);
+  }
   if (n == 0) return LBM_OK;
   st = rebuild_worklist(E);
   if (st != LBM_OK) return st;
