@@ -1480,10 +1480,13 @@ lbm_status debug_task_counts(Engine* E, int32_t* segments, int32_t* windows) {
 }
 
 lbm_status debug_damage_canary(Engine* E) {
-  if (!kCanaryBytes) return fail(LBM_ERR_ARG, "canaries exist only in the bounds-checked build");
-  CU(cudaStreamSynchronize(E->stream));
-  CU(cudaMemset(E->m[0]->canary_hi, 0, 4));
-  return LBM_OK;
+  if constexpr (kCanaryBytes == 0) {
+    return fail(LBM_ERR_ARG, "canaries exist only in the bounds-checked build");
+  } else {
+    CU(cudaStreamSynchronize(E->stream));
+    CU(cudaMemset(E->m[0]->canary_hi, 0, 4));
+    return LBM_OK;
+  }
 }
 
 lbm_status engine_solve(Engine* E, int64_t n_steps, lbm_solve_result* out) {
