@@ -146,6 +146,16 @@ lbm_status lbm3d_kernel_time(lbm3d_handle h, int reset, double* ms, int64_t* lau
 /* Block shape of the stream-collide kernels: warps per block (4, 8 or 16). */
 lbm_status lbm3d_set_block(lbm3d_handle h, int32_t warps_per_block);
 
+/* Test hook: the stream-collide tasks of the current work-list.  A row
+ * segment (32 cells of one mask word) holding at least P fluid cells is one
+ * warp task; the fluid cells of the sparser segments (but for the first and
+ * last word of a row and the layers next to a symmetry plane) are packed 32
+ * to a warp task.  P is 16 with FP32 storage and 24 with 16-bit storage,
+ * or LBM3D_PACK_BELOW (environment at lbm3d_create, 0 .. 32; 0: every
+ * segment holding fluid is a task).  Both give the same bits per cell
+ * (Eq. 1-2 with the rules of Sec. 3.3).  Host int32 outputs.              */
+lbm_status lbm3d_debug_task_counts(lbm3d_handle h, int32_t* segment_tasks, int32_t* packed_tasks);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@ struct lbm3d_handle_s {
   std::vector<void*> allocs;
   Seg3* segs = nullptr;
   int* seg_scratch = nullptr;
-  int* n_segs = nullptr;
+  int* n_segs = nullptr;      // device {segment tasks, all tasks}
   int* in_rows = nullptr;
   int n_in = 0;
   int* out_rows = nullptr;
@@ -38,12 +38,14 @@ struct lbm3d_handle_s {
   float* t_fields = nullptr;  // [4][plane] test-hook field copies (allocated on first use)
   uint8_t* d_cells = nullptr; // [ncells] unpacked mask (allocated on first use)
   double* h_result = nullptr; // pinned
-  int* h_small = nullptr;     // pinned: [0] flag, [1..8] info, [9] n_swap, [10] n_segs
+  int* h_small = nullptr;     // pinned: [0] flag, [1..8] info, [9] n_swap, [10..11] task counts
   long long mask_words = 0;
   void* best_f = nullptr;      // saved state of the optimisation loop (allocated on first use)
   uint32_t* best_mask = nullptr;
   float* best_fields = nullptr;
-  int nseg = 0;               // segments in the work-list (host copy)
+  int nseg = 0;               // tasks in the work-list (host copy)
+  int nseg_rows = 0;          // of them, row-segment tasks
+  int pack_below = 16;        // segments with fewer fluid cells go to packed tasks
   int resident[3] = {0, 0, 0};  // resident blocks of phase A, B, B with moments at wpb
   int64_t steps_done = 0;
   int64_t fluid = 0;
@@ -190,7 +192,7 @@ lbm_status geometry3(const lbm3d_params& p, const uint8_t* solid, Geometry3& g) 
 
 size_t storage_bytes3(int precision) { return precision == LBM_F32 ? 4 : 2; }
 
-// blocks of one phase launch: one warp per segment, at most what is resident at once
+// blocks of one phase launch: one warp per task, at most what is resident at once
 int step_blocks(lbm3d_handle h, int which) {
   const int need = (h->nseg + h->wpb - 1) / h->wpb;
   const int cap = h->resident[which] > 0 ? h->resident[which] : need;
@@ -211,10 +213,11 @@ lbm_status set_shape(lbm3d_handle h, int wpb) {
 
 // (re)build the step work-list and read its length back
 lbm_status build_worklist(lbm3d_handle h) {
-  CU3(launch_build_segments3(h->v, h->seg_scratch, h->segs, h->n_segs, h->stream));
-  CU3(cudaMemcpyAsync(h->h_small + 10, h->n_segs, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU3(launch_build_segments3(h->v, h->pack_below, h->seg_scratch, h->segs, h->n_segs, h->stream));
+  CU3(cudaMemcpyAsync(h->h_small + 10, h->n_segs, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU3(cudaStreamSynchronize(h->stream));
-  h->nseg = h->h_small[10];
+  h->nseg_rows = h->h_small[10];
+  h->nseg = h->h_small[11];
   return LBM_OK;
 }
 
@@ -308,6 +311,18 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   v.plane = (long long)p.nz * p.ny * v.nxp;
   const char* force64 = std::getenv("LBM3D_INDEX64");
   v.idx64 = ((long long)kQ3 * v.plane >= (1ll << 31) || (force64 && std::strcmp(force64, "1") == 0)) ? 1 : 0;
+  // Segments with fewer fluid cells than this are stepped as packed cells (0:
+  // none).  16-bit storage is bound by instruction issue, so filling lanes
+  // pays down to fuller segments; FP32 by the row pieces a warp touches, so
+  // only the sparsest segments are worth packing (measured on the 384 x 192
+  // x 192 tree: thresholds 16 and 24 best).
+  h->pack_below = p.precision == LBM_F32 ? 16 : 24;
+  if (const char* pb = std::getenv("LBM3D_PACK_BELOW")) {
+    char* end = nullptr;
+    const long n = std::strtol(pb, &end, 10);
+    if (end == pb || *end != '\0' || n < 0 || n > 32) return fail(LBM_ERR_ARG, "LBM3D_PACK_BELOW must be 0 .. 32");
+    h->pack_below = (int)n;
+  }
   v.mirror = p.mirror;
   v.omega = (float)(1.0 / p.tau);
   v.tau = (float)p.tau;
@@ -359,8 +374,11 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   uint32_t* nbs = nullptr;
   CU3(h->alloc(&nbs, sizeof(uint32_t) * 32 * (size_t)h->total_words));
   v.nbs = nbs;
+  uint32_t* cidx = nullptr;
+  CU3(h->alloc(&cidx, sizeof(uint32_t) * packed3_capacity(h->total_words)));
+  v.cidx = cidx;
   CU3(h->alloc(&h->seg_scratch, sizeof(int) * seg3_scratch_ints(h->total_words)));
-  CU3(h->alloc(&h->n_segs, sizeof(int)));
+  CU3(h->alloc(&h->n_segs, 2 * sizeof(int)));
   CU3(h->alloc(&h->in_rows, sizeof(int) * g.in_rows.size()));
   CU3(h->alloc(&h->out_rows, sizeof(int) * g.out_rows.size()));
   CU3(h->alloc(&h->out_off, sizeof(int) * g.out_off.size()));
@@ -594,6 +612,13 @@ lbm_status lbm3d_kernel_time(lbm3d_handle h, int reset, double* ms, int64_t* lau
     h->kt_launches = 0;
     h->kt_updates = 0;
   }
+  return LBM_OK;
+}
+
+lbm_status lbm3d_debug_task_counts(lbm3d_handle h, int32_t* segment_tasks, int32_t* packed_tasks) {
+  if (!h || !segment_tasks || !packed_tasks) return fail(LBM_ERR_ARG, "NULL argument");
+  *segment_tasks = h->nseg_rows;
+  *packed_tasks = h->nseg - h->nseg_rows;
   return LBM_OK;
 }
 

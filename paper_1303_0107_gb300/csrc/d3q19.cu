@@ -15,13 +15,15 @@
 // Each slot is read and then written by one thread per phase: one lattice,
 // no barrier, solid cells never read.
 //
-// Thread mapping.  A warp takes one row segment (32 cells of one mask word,
-// row (y, z)) from a device-resident list of the segments holding fluid;
-// lane l is cell 32 s + l.  Lanes 0..26 load the 27 mask words around the
-// segment (rows y-1..y+1 x z-1..z+1, words s-1..s+1) in one instruction and
-// the warp shares them by shuffles: no per-cell neighbour table in memory.
-// Each population access of a warp is one contiguous 32-element row piece,
-// shifted by at most one element.
+// Thread mapping.  A warp takes one task of a device-resident list.  A
+// segment task is a row segment (32 cells of one mask word, row (y, z))
+// holding at least pack_below fluid cells; lane l is cell 32 s + l, and each
+// population access of the warp is one contiguous 32-element row piece,
+// shifted by at most one element.  A packed task holds 32 fluid cells of
+// the sparser segments (at branch walls), one a lane, in index order.  The
+// neighbour flags of segments that are not open, and the flags of packed
+// cells, are built with the list (lanes 0..26 of a warp load the 27 mask
+// words around a segment and share them by shuffles).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -255,17 +257,22 @@ __device__ __forceinline__ void opaque(int& a) { asm volatile("" : "+r"(a)); }
 __device__ __forceinline__ void opaque(long long& a) { asm volatile("" : "+l"(a)); }
 
 // The populations of one fluid cell: load (pull or local), port rule,
-// collision, store.  NB0: no neighbour of this cell is solid (no
-// bounce-back selects at all).  IX: element index type -- int when all 19
-// planes have fewer than 2^31 elements (one IMAD per address), else long long.
-// FEAT: kernel build, bit kFeat3Models (collision models beyond BGK), bit
-// kFeat3Mirror (symmetry plane below row 0)
+// collision, store.  c: the cell's element index within a plane,
+// (z ny + y) nxp + x.  NB0: no neighbour of this cell is solid (no
+// bounce-back selects at all, no port).  nb: bit i set when x + c_i is solid.
+// on_py / on_pz: the cell lies on the layer next to a symmetry plane below
+// y = 0 / z = 0 (mirror build, phase A).  port: 0 none, 1 inlet (x = 0), 2
+// outlet (x = nx - 1); urow() gives z ny + y, called only for a port cell.
+// IX: element index type -- int when all 19 planes have fewer than 2^31
+// elements (one IMAD per address), else long long.  FEAT: kernel build, bit
+// kFeat3Models (collision models beyond BGK), bit kFeat3Mirror (symmetry
+// planes)
 constexpr int kFeat3Models = 1, kFeat3Mirror = 2;
 
-template <class T, int PHASE, int MOM, bool NB0, class IX, int FEAT>
-__device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z, uint32_t nb) {
+template <class T, int PHASE, int MOM, bool NB0, class IX, int FEAT, class URow>
+__device__ __forceinline__ void cell_core3(const View3& v, IX c, uint32_t nb, bool on_py, bool on_pz, int port,
+                                           URow urow) {
   IX sy = (IX)v.nxp, sz = (IX)v.ny * (IX)v.nxp;
-  IX c = ((IX)z * v.ny + y) * (IX)v.nxp + x;
   IX pl = (IX)v.plane;
   // opaque per cell: keeps the compiler from hoisting 18 plane and neighbour
   // offsets out of the warp's loop into registers
@@ -280,8 +287,8 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
   // sent towards a fluid image cell comes back into the plane's layer with
   // those components negated, into the slot the local phase reads for it.
   // Solid images reflect as walls (the nb path).
-  const bool py = (FEAT & kFeat3Mirror) && PHASE == 0 && !NB0 && (v.mirror & 1) && y == 0;
-  const bool pz = (FEAT & kFeat3Mirror) && PHASE == 0 && !NB0 && (v.mirror & 2) && z == 0;
+  const bool py = (FEAT & kFeat3Mirror) && PHASE == 0 && !NB0 && on_py;
+  const bool pz = (FEAT & kFeat3Mirror) && PHASE == 0 && !NB0 && on_pz;
   float g[kQ];
   g[0] = P3<T>::ld(F + c);
 #pragma unroll
@@ -299,7 +306,7 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
     else
       g[i] = P3<T>::ld(F + (i * pl + c - off));
   }
-  if (!NB0 && (x == 0 || x == v.nx - 1)) port3(g, x == 0, v.u_in[(long long)z * v.ny + y], v.rho0);
+  if (!NB0 && port != 0) port3(g, port == 1, v.u_in[urow()], v.rho0);
   float drho, ux, uy, uz;
   if ((FEAT & kFeat3Models) && v.collision != LBM_COLLIDE_BGK)  // the plain build has no branch here
     collide_other3(g, v.rho0, v.omega, v.tau, v.collision, v.c_smag, drho, ux, uy, uz);
@@ -332,6 +339,31 @@ __device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z
     v.uz[c] = uz;
     if (!(isfinite(drho) && isfinite(ux) && isfinite(uy) && isfinite(uz))) atomicOr(v.flag, 1);
   }
+}
+
+// cell_core3 for cell x of row (y, z)
+template <class T, int PHASE, int MOM, bool NB0, class IX, int FEAT>
+__device__ __forceinline__ void cell_update3(const View3& v, int x, int y, int z, uint32_t nb) {
+  const IX c = ((IX)z * v.ny + y) * (IX)v.nxp + x;
+  const int port = NB0 ? 0 : (x == 0 ? 1 : (x == v.nx - 1 ? 2 : 0));
+  cell_core3<T, PHASE, MOM, NB0, IX, FEAT>(v, c, nb, (v.mirror & 1) && y == 0, (v.mirror & 2) && z == 0, port,
+                                           [&] { return (long long)z * v.ny + y; });
+}
+
+// Bit l set when some D3Q19 neighbour of cell 32 s + l of row (y, z) is solid
+// (bits past the row's end and the padding words count as solid).
+__device__ __forceinline__ uint32_t solid_nb3(const View3& v, int y, int z, int s) {
+  uint32_t solid_nb = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy) {
+      const uint32_t* row = v.mask + mask3_row(v.ny, v.ms, y + dy, z + dz) + 1;
+      const uint32_t m = row[s];
+      solid_nb |= (dy == 0 && dz == 0) ? 0u : m;        // c_x = 0 (not the cell itself)
+      if (dy != 0 && dz != 0) continue;                 // D3Q19 has no (+-1, +-1, +-1)
+      solid_nb |= __funnelshift_r(m, row[s + 1], 1);    // c_x = +1
+      solid_nb |= __funnelshift_l(row[s - 1], m, 1);    // c_x = -1
+    }
+  return solid_nb;
 }
 
 // Solid flags of the 18 neighbours of the lane's cell of segment `seg` (bit
@@ -396,21 +428,46 @@ __device__ __forceinline__ void seg_task3(const View3& v, Seg3 sg, int t, int la
     cell_update3<T, PHASE, MOM, false, IX, FEAT>(v, x, y, z, nb);
 }
 
-// One phase of one time step over the segment list (warps stride over it).
-// Launched as a programmatic dependent of the previous step.
+constexpr uint32_t kCell3Pad = 0xffffffffu;  // cell index of a padding entry of the packed list
+
+// One phase on packed task t (t >= n_seg): entries 32 (t - n_seg) .. + 31 of
+// the packed-cell list, the fluid cells of sparse segments one a lane.  No
+// packed cell is a port cell or lies next to a symmetry plane (those
+// segments stay segment tasks), so phase A needs only the neighbour flags
+// (the task's flag block) and phase B only the index.  They are read before
+// waiting for the previous step, the populations after.
+template <class T, int PHASE, int MOM, class IX, int FEAT>
+__device__ __forceinline__ void packed_task3(const View3& v, int t, int n_seg, int lane, bool& waited) {
+  const uint32_t c = v.cidx[(long long)(t - n_seg) * 32 + lane];
+  const uint32_t nb = PHASE == 0 ? v.nbs[(long long)t * 32 + lane] : 0u;
+  if (!waited) {  // warp-uniform: the previous step's populations are final from here on
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    waited = true;
+  }
+  if (c == kCell3Pad) return;
+  cell_core3<T, PHASE, MOM, PHASE == 1, IX, FEAT>(v, (IX)c, nb, false, false, 0, [] { return 0ll; });
+}
+
+// One phase of one time step over the task list (warps stride over it):
+// tasks 0 .. counts[0]-1 are row segments, the rest packed cells.  Launched
+// as a programmatic dependent of the previous step.
 template <class T, int PHASE, int MOM, class IX, int FEAT>
 __global__ void __launch_bounds__(512) k_step3(const View3 v, const Seg3* __restrict__ segs,
-                                               const int* __restrict__ n_segs) {
+                                               const int* __restrict__ counts) {
   // the next step may be scheduled now; it touches populations only after
   // waiting for this grid to complete
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31;
-  const int nseg = *n_segs;
+  const int n_seg = counts[0], n_task = counts[1];
   const int wpb = blockDim.x >> 5;
   const int stride = gridDim.x * wpb;
   bool waited = false;
-  for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < nseg; t += stride)
-    seg_task3<T, PHASE, MOM, IX, FEAT>(v, segs[t], t, lane, waited);
+  for (int t = blockIdx.x * wpb + (threadIdx.x >> 5); t < n_task; t += stride) {
+    if (t < n_seg)  // warp-uniform
+      seg_task3<T, PHASE, MOM, IX, FEAT>(v, segs[t], t, lane, waited);
+    else
+      packed_task3<T, PHASE, MOM, IX, FEAT>(v, t, n_seg, lane, waited);
+  }
   // every thread waits once, so this grid completes only after the previous one
   if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
@@ -433,12 +490,21 @@ __device__ __forceinline__ void word3_of(const View3& v, int y0, int z0, int i, 
   z = z0 + zi;
 }
 
-__global__ void k_seg3_flags(const View3 v, int total, int* __restrict__ flags) {
+// Word i: cnt[i] = its fluid cells when it goes to packed tasks (fewer than
+// pack_below, and neither a word holding a port column -- the first or the
+// last of its row -- nor one on a layer next to a symmetry plane), else 0;
+// flags[i] = 1 for a segment task (any other word holding fluid).
+__global__ void k_seg3_flags(const View3 v, int total, int pack_below, int* __restrict__ flags,
+                             int* __restrict__ cnt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   int y, z, s;
   word3_of(v, first_row3(v), first_layer3(v), i, y, z, s);
-  flags[i] = ~v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + s] != 0u;
+  const int fill = __popc(~v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + s]);
+  const bool packable = fill < pack_below && s != 0 && s != v.nsx - 1 && !((v.mirror & 1) && y == 0) &&
+                        !((v.mirror & 2) && z == 0);
+  cnt[i] = packable ? fill : 0;
+  flags[i] = fill > 0 && !packable;
 }
 
 // Entry of a segment holding fluid: its index, its own mask word, and
@@ -451,28 +517,56 @@ __global__ void k_seg3_scatter(const View3 v, int total, const int* __restrict__
   int y, z, s;
   word3_of(v, first_row3(v), first_layer3(v), i, y, z, s);
   const uint32_t own = v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + s];
-  uint32_t solid_nb = 0;  // bit l: some neighbour of cell 32 s + l is solid
-  for (int dz = -1; dz <= 1; ++dz)
-    for (int dy = -1; dy <= 1; ++dy) {
-      const uint32_t* row = v.mask + mask3_row(v.ny, v.ms, y + dy, z + dz) + 1;
-      const uint32_t m = row[s];
-      solid_nb |= (dy == 0 && dz == 0) ? 0u : m;        // c_x = 0 (not the cell itself)
-      if (dy != 0 && dz != 0) continue;                 // D3Q19 has no (+-1, +-1, +-1)
-      solid_nb |= __funnelshift_r(m, row[s + 1], 1);    // c_x = +1
-      solid_nb |= __funnelshift_l(row[s - 1], m, 1);    // c_x = -1
-    }
+  const uint32_t solid_nb = solid_nb3(v, y, z, s);
   // the layers next to a symmetry plane pull across it: never the open path
   const bool open = (solid_nb & ~own) == 0u && y >= 1 && z >= 1;
   const int seg = (z * v.ny + y) * v.nsx + s;
   segs[offs[i]] = Seg3{seg | (open ? kSegOpen : 0), own};
 }
 
-// neighbour flags of every cell of the list's segments that are not open
-// (one warp per segment; open segments need none)
-__global__ void k_nb3(const View3 v, const Seg3* __restrict__ segs, const int* __restrict__ n_segs,
+// Packed cells: one warp per word; lane l places cell 32 s + l of a sparse
+// segment at its offset in the packed list, with its neighbour flags in the
+// flag block after the segment tasks'.  Block 0 also pads the packed list to
+// whole tasks and writes counts {segment tasks, tasks}.
+__global__ void k_pack3_scatter(const View3 v, int total, const int* __restrict__ cnt,
+                                const int* __restrict__ offs, const int* __restrict__ coffs,
+                                uint32_t* __restrict__ cidx, uint32_t* __restrict__ nbs, int* __restrict__ counts) {
+  const int lane = threadIdx.x & 31;
+  const int n_seg = offs[total], n_packed = coffs[total];
+  const int packed_end = (n_packed + 31) & ~31;
+  uint32_t* flags = nbs + (long long)n_seg * 32;
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    if (n_packed + lane < packed_end) {
+      cidx[n_packed + lane] = kCell3Pad;
+      flags[n_packed + lane] = 0u;
+    }
+    if (lane == 0) {
+      counts[0] = n_seg;
+      counts[1] = n_seg + (packed_end >> 5);
+    }
+  }
+  const uint32_t bit = 1u << lane, below = bit - 1u;
+  const int stride = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < total; i += stride) {
+    if (cnt[i] == 0) continue;  // warp-uniform
+    int y, z, s;
+    word3_of(v, first_row3(v), first_layer3(v), i, y, z, s);
+    const uint32_t fluid = ~v.mask[mask3_row(v.ny, v.ms, y, z) + 1 + s];
+    const uint32_t nb = neighbour_flags3(v, (z * v.ny + y) * v.nsx + s, lane);  // the whole warp
+    if (fluid & bit) {
+      const int k = coffs[i] + __popc(fluid & below);
+      cidx[k] = (uint32_t)(((long long)z * v.ny + y) * v.nxp + 32 * s + lane);
+      flags[k] = nb;
+    }
+  }
+}
+
+// neighbour flags of every cell of the list's segment tasks that are not
+// open (one warp per segment; open segments need none)
+__global__ void k_nb3(const View3 v, const Seg3* __restrict__ segs, const int* __restrict__ counts,
                       uint32_t* __restrict__ nbs) {
   const int lane = threadIdx.x & 31;
-  const int nseg = *n_segs;
+  const int nseg = counts[0];
   const int stride = (gridDim.x * blockDim.x) >> 5;
   for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nseg; t += stride) {
     const Seg3 sg = segs[t];
@@ -728,23 +822,32 @@ inline int feat3(const View3& v) {
 
 }  // namespace
 
-size_t seg3_scratch_ints(long long total) { return 2 * (size_t)total + 1 + scan_tmp_ints(total); }
+size_t seg3_scratch_ints(long long total) { return 4 * (size_t)total + 2 + scan_tmp_ints(total); }
 
-cudaError_t launch_build_segments3(const View3& v, int* scratch, Seg3* segs, int* n_segs, cudaStream_t stream) {
+size_t packed3_capacity(long long total) { return 32 * (size_t)total + 32; }
+
+cudaError_t launch_build_segments3(const View3& v, int pack_below, int* scratch, Seg3* segs, int* counts,
+                                   cudaStream_t stream) {
   const int total = seg3_words(v);
   int* flags = scratch;
-  int* offs = scratch + total;  // total + 1
-  int* tmp = scratch + 2 * total + 1;
-  k_seg3_flags<<<blocks_for(total, 256), 256, 0, stream>>>(v, total, flags);
+  int* offs = scratch + total;           // total + 1
+  int* cnt = scratch + 2 * total + 1;
+  int* coffs = scratch + 3 * total + 1;  // total + 1
+  int* tmp = scratch + 4 * total + 2;
+  k_seg3_flags<<<blocks_for(total, 256), 256, 0, stream>>>(v, total, pack_below, flags, cnt);
   count_launches(1);
-  cudaError_t e = launch_scan(flags, offs, total, tmp, stream);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if ((e = launch_scan(flags, offs, total, tmp, stream)) != cudaSuccess) return e;
+  if ((e = launch_scan(cnt, coffs, total, tmp, stream)) != cudaSuccess) return e;
   k_seg3_scatter<<<blocks_for(total, 256), 256, 0, stream>>>(v, total, flags, offs, segs);
   count_launches(1);
+  uint32_t* nbs = const_cast<uint32_t*>(v.nbs);
+  k_pack3_scatter<<<blocks_for((long long)total * 32, 256), 256, 0, stream>>>(
+      v, total, cnt, offs, coffs, const_cast<uint32_t*>(v.cidx), nbs, counts);
+  count_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = cudaMemcpyAsync(n_segs, offs + total, sizeof(int), cudaMemcpyDeviceToDevice, stream)) != cudaSuccess)
-    return e;
-  k_nb3<<<blocks_for((long long)total * 32, 256), 256, 0, stream>>>(v, segs, n_segs, const_cast<uint32_t*>(v.nbs));
+  k_nb3<<<blocks_for((long long)total * 32, 256), 256, 0, stream>>>(v, segs, counts, nbs);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -760,10 +863,10 @@ int step3_resident_blocks(int precision, int phase, int moments, int warps_per_b
 }
 
 cudaError_t launch_step3(int precision, int phase, int moments, const View3& v, const Seg3* segs,
-                         const int* n_segs, int blocks, int warps_per_block, cudaStream_t stream) {
+                         const int* counts, int blocks, int warps_per_block, cudaStream_t stream) {
   void* k = step3_for(precision, phase, moments, needs_idx64(v), feat3(v));
   if (!k || blocks < 1) return cudaErrorInvalidValue;
-  void* args[] = {(void*)&v, (void*)&segs, (void*)&n_segs};
+  void* args[] = {(void*)&v, (void*)&segs, (void*)&counts};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;

@@ -26,9 +26,11 @@ struct View3 {
   float* uy;             // [plane]
   float* uz;             // [plane]
   const float* u_in;     // [nz * ny] inlet u_x of cell (0, y, z); 0 where no inlet cell
-  const uint32_t* nbs;   // [32 per work-list entry]: solid flags of the 18 neighbours of each
-                         // cell of a segment that is not open (bit i: x + c_i solid), built with
-                         // the work-list
+  const uint32_t* nbs;   // [32 per task]: solid flags of the 18 neighbours of each cell of a
+                         // segment task that is not open, and of each packed cell (bit i:
+                         // x + c_i solid), built with the work-list
+  const uint32_t* cidx;  // [32 per packed task]: element indices (z ny + y) nxp + x of the
+                         // packed cells, 0xffffffff for padding
   int* flag;             // bit 0: a moments step saw a non-finite value
   long long plane;       // elements per population plane: nz * ny * nxp
   int nx, ny, nz;
@@ -71,14 +73,21 @@ constexpr int kSegIndexMask = (1 << 30) - 1;
 constexpr int kSegOpen = 1 << 30;
 static_assert(sizeof(Seg3) == 8, "Seg3 layout");
 
-// Step work-list: the segments (z, y, s) of rows y in [first_row3, ny-2], z
-// in [first_layer3, nz-2] holding a fluid cell, in ascending order; *n_segs
-// their count.
-// scratch holds seg3_scratch_ints(total) ints, total = seg3_words(v).
+// Step work-list of rows y in [first_row3, ny-2], z in [first_layer3, nz-2]:
+// segs lists the segments (z, y, s) holding fluid, in ascending order, one
+// warp task each, but for those with fewer than pack_below fluid cells (not
+// the first or last word of a row, not on a layer next to a symmetry
+// plane): their fluid cells follow as packed tasks of 32 cells, their indices in v.cidx (ascending, padded to whole tasks) and
+// their flags in v.nbs after the segment tasks' blocks.  counts = {segment
+// tasks, all tasks}.  scratch holds seg3_scratch_ints(total) ints, segs
+// total entries, v.nbs 32 total and v.cidx packed3_capacity(total),
+// total = seg3_words(v).
 size_t seg3_scratch_ints(long long total);
-cudaError_t launch_build_segments3(const View3& v, int* scratch, Seg3* segs, int* n_segs, cudaStream_t stream);
+size_t packed3_capacity(long long total);
+cudaError_t launch_build_segments3(const View3& v, int pack_below, int* scratch, Seg3* segs, int* counts,
+                                   cudaStream_t stream);
 
-// One time step over the work-list.  phase 0 ("A"): pulls from the
+// One time step over the work-list (counts as built above).  phase 0 ("A"): pulls from the
 // neighbours' slots and pushes into the slots the neighbours read next
 // (its own where the neighbour is solid); phase 1 ("B"): the cell's own
 // slots only, leaving F[i][cell] = post-collision population i.  moments
@@ -86,7 +95,7 @@ cudaError_t launch_build_segments3(const View3& v, int* scratch, Seg3* segs, int
 // Warps stride over the list (blocks of warps_per_block warps); launched as
 // a programmatic dependent of the previous kernel on the stream.
 cudaError_t launch_step3(int precision, int phase, int moments, const View3& v, const Seg3* segs,
-                         const int* n_segs, int blocks, int warps_per_block, cudaStream_t stream);
+                         const int* counts, int blocks, int warps_per_block, cudaStream_t stream);
 // blocks of the given shape resident on the whole device at once (0 on error)
 int step3_resident_blocks(int precision, int phase, int moments, int warps_per_block, const View3& v);
 

@@ -54,9 +54,11 @@ def _lib():
         L.lbm3d_kernel_time.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.lbm3d_set_block.argtypes = [H, ctypes.c_int32]
+        L.lbm3d_debug_task_counts.argtypes = [H, I32P, I32P]
         L.lbm3d_optimize.argtypes = [H, ctypes.POINTER(OptPlan), _VP, ctypes.POINTER(OptSummary)]
         for name in ("lbm3d_create", "lbm3d_solve", "lbm3d_optimize_step", "lbm3d_read_fields", "lbm3d_load_state",
-                     "lbm3d_select_swaps", "lbm3d_kernel_time", "lbm3d_set_block", "lbm3d_optimize"):
+                     "lbm3d_select_swaps", "lbm3d_kernel_time", "lbm3d_set_block", "lbm3d_optimize",
+                     "lbm3d_debug_task_counts"):
             getattr(L, name).restype = ctypes.c_int
         _bound = True
     return L
@@ -168,3 +170,9 @@ class Lattice3:
 
     def set_block(self, warps_per_block: int):
         _check(_lib().lbm3d_set_block(self._h, int(warps_per_block)), "lbm3d_set_block")
+
+    def task_counts(self):
+        """(row-segment tasks, packed-cell tasks) of the current work-list."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib().lbm3d_debug_task_counts(self._h, ctypes.byref(a), ctypes.byref(b)), "lbm3d_debug_task_counts")
+        return a.value, b.value

@@ -67,6 +67,8 @@ def test_host_only_entry_points(built_lib):
     assert L3.lbm3d_create(None, None, None, ctypes.byref(h3)) == 1 and not h3.value
     L3.lbm3d_destroy(None)
     assert L3.lbm3d_set_block(None, 8) == 1
+    k = ctypes.c_int32()
+    assert L3.lbm3d_debug_task_counts(None, ctypes.byref(k), ctypes.byref(k)) == 1
     small = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05)), 0)
     opt = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05)), 5)
     half = L.lbm_server_footprint(ctypes.byref(lib.make_params(128, 64, 0.8, 0.05, precision=1)), 0)

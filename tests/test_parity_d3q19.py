@@ -467,3 +467,107 @@ def test_quarter_domain_exchange_and_shapes(monkeypatch):
         h.optimize_step(15, 200)
         assert np.array_equal(h.read(L.FIELD3_POPS) * (after == 0)[None], ref)
         h.close()
+
+
+def _host_task_counts(cells, pack_below, mirror=0):
+    """Segment and packed tasks of the step work-list, counted on the host
+    from the cell map: a word of the list rows with 0 < fill < pack_below
+    that is neither the first nor the last word of its row nor on a layer
+    next to a symmetry plane is packed, any other word holding fluid is a
+    segment task; packed cells go 32 to a task."""
+    nz, ny, nx = cells.shape
+    nsx = (nx + 31) // 32
+    y0, z0 = (0 if mirror & 1 else 1), (0 if mirror & 2 else 1)
+    pad = np.ones((nz, ny, 32 * nsx), np.uint8)
+    pad[:, :, :nx] = cells
+    fill = (pad[z0:nz - 1, y0:ny - 1] == 0).reshape(nz - 1 - z0, ny - 1 - y0, nsx, 32).sum(-1)
+    s = np.arange(nsx)[None, None, :]
+    y = np.arange(y0, ny - 1)[None, :, None]
+    z = np.arange(z0, nz - 1)[:, None, None]
+    packable = (fill < pack_below) & (s != 0) & (s != nsx - 1)
+    if mirror & 1:
+        packable &= y != 0
+    if mirror & 2:
+        packable &= z != 0
+    seg = int(((fill > 0) & ~packable).sum())
+    packed = int(fill[packable].sum())
+    return seg, (packed + 31) // 32
+
+
+@pytest.mark.parametrize("precision", [L.F32, L.BF16_SHIFTED, L.F16_SHIFTED])
+def test_packed_cells_give_the_same_bits(monkeypatch, precision):
+    """The sparse segments' cells packed 32 to a task (thresholds 16 and 32)
+    against every segment a task (0) on the 192 x 96 x 96 tree: task counts
+    equal the host's, populations and fields equal bit for bit."""
+    cfg = I.config_tree3d(192, 96, 96)
+    assert _host_task_counts(cfg["cells"], 16)[1] > 0  # the tree has sparse segments
+    out = {}
+    for pb in (0, 16, 32):
+        monkeypatch.setenv("LBM3D_PACK_BELOW", str(pb))
+        lat = L.Lattice3(cfg["cells"], cfg["tau"], cfg["u_max"], precision=precision)
+        assert lat.task_counts() == _host_task_counts(cfg["cells"], pb)
+        r = lat.solve(100)
+        out[pb] = (r["dp"], lat.read(L.FIELD3_POPS), lat.read(L.FIELD3_UX))
+        lat.close()
+    for pb in (16, 32):
+        assert out[pb][0] == out[0][0]
+        assert np.array_equal(out[pb][1].view(np.uint8), out[0][1].view(np.uint8))
+        assert np.array_equal(out[pb][2].view(np.uint32), out[0][2].view(np.uint32))
+
+
+def test_packed_cells_one_pair_from_a_random_state(monkeypatch):
+    """Sparse random walls (rows of 130 cells, five words, half the cells
+    solid) with every packable segment packed: one step pair from random
+    populations against the oracle's two steps, per population."""
+    monkeypatch.setenv("LBM3D_PACK_BELOW", "32")
+    cells = I.random_blobs3d(130, 10, 9, seed=3, density=0.5)
+    nz, ny, nx = cells.shape
+    seg, packed = _host_task_counts(cells, 32)
+    assert packed > 0
+    rng = np.random.default_rng(5)
+    w = _w3()
+    g0 = (w[:, None, None, None] * 0.05 * rng.standard_normal((19, nz, ny, nx))).astype(np.float32)
+    lat = L.Lattice3(cells, 0.9, 0.03)
+    assert lat.task_counts() == (seg, packed)
+    lat.load_state(g0)
+    lat.solve(2)
+    p = o3.make_params3(nx, ny, nz, 0.9, u_max=0.03)
+    f0 = g0.astype(np.float64) + w[:, None, None, None]
+    f0 *= (cells == 0)[None]
+    f, *_ = o3.run3(p, cells, o3.inlet_profile3(p, cells), f0, 2)
+    got = lat.read(L.FIELD3_POPS).astype(np.float64) + w[:, None, None, None]
+    assert np.abs((got - f) * (cells == 0)[None]).max() <= 2e-6
+    lat.close()
+
+
+@pytest.mark.parametrize("mirror,collision", [(1, 0), (3, L.COLLIDE_SMAGORINSKY)])
+def test_packed_cells_with_planes_models_and_64bit_indices(monkeypatch, mirror, collision):
+    """Packing next to symmetry planes (whose layers stay segment tasks), with
+    a collision model, and in the 64-bit index build: the same bits as every
+    segment a task, through an exchange (the list is rebuilt)."""
+    cfg = I.config_tree3d(192, 96, 96)
+    c = cfg["cells"]
+    sub = np.ascontiguousarray(c[:, 48:, :] if mirror == 1 else c[48:, 48:, :])
+    ref = None
+    for pb, force64 in ((0, "0"), (32, "0"), (32, "1")):
+        monkeypatch.setenv("LBM3D_PACK_BELOW", str(pb))
+        monkeypatch.setenv("LBM3D_INDEX64", force64)
+        lat = L.Lattice3(sub, cfg["tau"], cfg["u_max"], mirror=mirror, collision=collision, c_smag=0.1)
+        assert lat.task_counts() == _host_task_counts(sub, pb, mirror)
+        lat.solve(60)
+        o = lat.optimize_step(40, 60)
+        mask = lat.read(L.FIELD3_MASK)
+        got = (o["dp"], mask, lat.read(L.FIELD3_POPS) * (mask == 0)[None])
+        lat.close()
+        if ref is None:
+            ref = got
+            continue
+        assert got[0] == ref[0] and np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
+
+
+@pytest.mark.parametrize("bad", ["33", "-1", "x", ""])
+def test_pack_threshold_is_checked(monkeypatch, bad):
+    monkeypatch.setenv("LBM3D_PACK_BELOW", bad)
+    with pytest.raises(L.LbmError) as e:
+        L.Lattice3(I.duct3d(16, 6, 5), 0.8, 0.05)
+    assert e.value.status == 1
