@@ -65,11 +65,12 @@ int64_t footprint_of(const lbm_params& p, int32_t n_iter) {
   const int64_t cells = (int64_t)p.nx * p.ny;
   // the member's own allocation; its share of the set's work-list (segment
   // entries with their neighbour flags, 72 bytes per 32-cell word, and scan
-  // scratch: under 3 bytes per cell) and of the read-back buffer (4 bytes
-  // per cell); for optimising requests the exchange scratch: counts and
-  // offsets per mask word, 24 bytes of keys and indices per cell and 4 bytes
-  // of picks per cell
-  int64_t b = (int64_t)member_footprint(p) + 7 * cells + 4096;
+  // scratch: under 3 bytes per cell), of the compacted cell list the request
+  // loop steps (an 8-byte entry per fluid cell, and its scan scratch: under
+  // 9 bytes per cell) and of the read-back buffer (4 bytes per cell); for
+  // optimising requests the exchange scratch: counts and offsets per mask
+  // word, 24 bytes of keys and indices per cell and 4 bytes of picks per cell
+  int64_t b = (int64_t)member_footprint(p) + 16 * cells + 4096;
   if (n_iter > 0) b += 29 * cells;
   return b;
 }
