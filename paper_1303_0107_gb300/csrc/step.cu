@@ -888,6 +888,16 @@ __device__ __forceinline__ void cp_async_n(uint32_t* dst, const void* src, bool 
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(N), "r"(n) : "memory");
 }
 
+// 16 bytes global -> shared, cached in L2 only (ok false: zeros, nothing read)
+__device__ __forceinline__ void cp_async_16(uint32_t* dst, const void* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+
+// Stage a paired task: the window's nine aligned row pieces (32 pairs, 128 or
+// 256 bytes each) in 16-byte chunks spread over the lanes, so a lane may fill
+// another lane's words (the loop synchronises the warp around each stage),
+// and in phase A the six edge elements by lanes 0 and 31.
 template <class T, int PHASE, bool ONE>
 __device__ __forceinline__ void pair_stage_issue(const LatticeView* __restrict__ views, const SegRef sr,
                                                  const int lane, uint32_t* sb) {
@@ -903,13 +913,20 @@ __device__ __forceinline__ void pair_stage_issue(const LatticeView* __restrict__
   const long long fe = L->f_elems;
   (void)fe;
   const int y = sr.yw >> kSegWordBits, p = sr.yw & ((1 << kSegWordBits) - 1);
-  const int c = y * pitch + (p << 6) + 2 * lane;
+  const int base = y * pitch + (p << 6);  // the window's first cell: rows start 128-byte aligned
+  constexpr int kChunks = 8 * W;           // 16-byte chunks per piece
+  constexpr int kPer = 16 / (int)sizeof(T);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const int off = pair_plane(PHASE, i) * pl + c + pair_row(PHASE, i) * pitch;
-    const bool ok = LBM_OK_IDX(off, fe) && LBM_OK_IDX(off + 1, fe);
-    cp_async_n<2 * sizeof(T)>(sb + PairStage<T>::kHead + (i * 32 + lane) * W, F + (ok ? off : 0), ok);
+  for (int r = 0; r < (9 * kChunks + 31) / 32; ++r) {
+    const int j = lane + 32 * r;
+    if (j < 9 * kChunks) {
+      const int i = j / kChunks, q = j - i * kChunks;
+      const int off = pair_plane(PHASE, i) * pl + base + pair_row(PHASE, i) * pitch + q * kPer;
+      const bool ok = LBM_OK_IDX(off, fe) && LBM_OK_IDX(off + kPer - 1, fe);
+      cp_async_16(sb + PairStage<T>::kHead + i * 32 * W + 4 * q, F + (ok ? off : 0), ok);
+    }
   }
+  const int c = base + 2 * lane;
   if (PHASE == 0 && (lane == 0 || lane == 31)) {
     const bool first = lane == 0;
     const int d = first ? -1 : 2;
