@@ -1259,12 +1259,16 @@ void fill_result(Engine* E, int i, lbm_solve_result* out) {
 }
 
 // Member groups (decided once, at the first solve of 256 steps or more).
-// A batch is split when its members' population bytes exceed 1.5 times a
-// third of the L2 cache and every member is below a quarter of that third:
-// members in order, each group up to a third of the L2.  Measured on the
-// 256 candidates: 32-48 candidates at a time step 1.5x faster (FP32) than
-// all 256, which stream from DRAM.  LBM_GROUPS=0 turns grouping off;
-// LBM_GROUP_BYTES sets the budget (tests).
+// A batch is split when its members' population bytes exceed 1.5 times the
+// group budget and every member is below a quarter of it: members in order,
+// each group up to the budget.  The budget is a third of the L2 cache of
+// FP32 populations, two thirds of that with 16-bit storage: a group's other
+// per-cell data (cell-list entry, flags) does not shrink with the storage,
+// and on the 256 candidates the 16-bit groups ran fastest at about 4/3 of
+// the FP32 groups' cells (budget 14 / 21 / 28 / 42 MB: 61.3 / 62.6 / 65.8 /
+// 62.2 GLUPS; FP32 at 28 / 42 MB: 77.1 / 79.0).  32-48 candidates at a
+// time step 1.5x faster (FP32) than all 256, which stream from DRAM.
+// LBM_GROUPS=0 turns grouping off; LBM_GROUP_BYTES sets the budget (tests).
 bool groups_enabled() {
   static const bool on = [] {
     const char* e = std::getenv("LBM_GROUPS");
@@ -1283,7 +1287,7 @@ lbm_status ensure_groups(Engine* E) {
     int dev = 0, l2 = 0;
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
-    budget = l2 / 3.0;
+    budget = l2 / 3.0 * (E->precision == LBM_F32 ? 1.0 : 2.0 / 3.0);
   }
   const double sb = 9.0 * (double)storage_bytes(E->precision);
   double total = 0.0, largest = 0.0;
