@@ -280,6 +280,14 @@ __device__ __forceinline__ void cell_core3(const View3& v, IX c, uint32_t nb, bo
   opaque(sy);
   opaque(sz);
   T* F = static_cast<T*>(v.f);
+  // every population access is checked against the 19 planes in the
+  // bounds-checked build (a violation is printed and skipped)
+  const long long fe = (long long)kQ * v.plane;
+  (void)fe;
+  auto ld3 = [&](IX i) { return LBM_OK_IDX(i, fe) ? P3<T>::ld(F + i) : 0.0f; };
+  auto st3 = [&](IX i, float val) {
+    if (LBM_OK_IDX(i, fe)) P3<T>::st(F + i, val);
+  };
   // Symmetry planes below y = 0 and/or z = 0: a ghost layer is the image of
   // the layer next to it (its mask rows are copies, so nb tells whether an
   // image cell is solid).  A population arriving from a fluid image cell is
@@ -290,21 +298,21 @@ __device__ __forceinline__ void cell_core3(const View3& v, IX c, uint32_t nb, bo
   const bool py = (FEAT & kFeat3Mirror) && PHASE == 0 && !NB0 && on_py;
   const bool pz = (FEAT & kFeat3Mirror) && PHASE == 0 && !NB0 && on_pz;
   float g[kQ];
-  g[0] = P3<T>::ld(F + c);
+  g[0] = ld3(c);
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const IX off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
     const bool xy = cy3(i) > 0 && py, xz = cz3(i) > 0 && pz;  // the source lies past a plane
     if (PHASE == 1 || (!NB0 && ((nb >> opp3(i)) & 1u)))
-      g[i] = P3<T>::ld(F + (opp3(i) * pl + c));
+      g[i] = ld3(opp3(i) * pl + c);
     else if (xy && xz)
-      g[i] = P3<T>::ld(F + (mirz3(mir3(i)) * pl + c - cx3(i)));
+      g[i] = ld3(mirz3(mir3(i)) * pl + c - cx3(i));
     else if (xy)
-      g[i] = P3<T>::ld(F + (mir3(i) * pl + c - (cx3(i) + cz3(i) * sz)));
+      g[i] = ld3(mir3(i) * pl + c - (cx3(i) + cz3(i) * sz));
     else if (xz)
-      g[i] = P3<T>::ld(F + (mirz3(i) * pl + c - (cx3(i) + cy3(i) * sy)));
+      g[i] = ld3(mirz3(i) * pl + c - (cx3(i) + cy3(i) * sy));
     else
-      g[i] = P3<T>::ld(F + (i * pl + c - off));
+      g[i] = ld3(i * pl + c - off);
   }
   if (!NB0 && port != 0) port3(g, port == 1, v.u_in[urow()], v.rho0);
   float drho, ux, uy, uz;
@@ -316,23 +324,23 @@ __device__ __forceinline__ void cell_core3(const View3& v, IX c, uint32_t nb, bo
   // 18 load addresses alive across the collision (halves the registers).
   opaque(c);
   opaque(pl);
-  P3<T>::st(F + c, g[0]);
+  st3(c, g[0]);
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const IX off = cx3(i) + cy3(i) * sy + cz3(i) * sz;
     const bool xy = cy3(i) < 0 && py, xz = cz3(i) < 0 && pz;  // the target lies past a plane
     if (PHASE == 1 || (!NB0 && ((nb >> i) & 1u)))
-      P3<T>::st(F + (i * pl + c), g[i]);
+      st3(i * pl + c, g[i]);
     else if (xy && xz)
-      P3<T>::st(F + (opp3(mirz3(mir3(i))) * pl + c + cx3(i)), g[i]);
+      st3(opp3(mirz3(mir3(i))) * pl + c + cx3(i), g[i]);
     else if (xy)
-      P3<T>::st(F + (opp3(mir3(i)) * pl + c + (cx3(i) + cz3(i) * sz)), g[i]);
+      st3(opp3(mir3(i)) * pl + c + (cx3(i) + cz3(i) * sz), g[i]);
     else if (xz)
-      P3<T>::st(F + (opp3(mirz3(i)) * pl + c + (cx3(i) + cy3(i) * sy)), g[i]);
+      st3(opp3(mirz3(i)) * pl + c + (cx3(i) + cy3(i) * sy), g[i]);
     else
-      P3<T>::st(F + (opp3(i) * pl + c + off), g[i]);
+      st3(opp3(i) * pl + c + off, g[i]);
   }
-  if (MOM) {
+  if (MOM && LBM_OK_IDX(c, v.plane)) {
     v.drho[c] = drho;
     v.ux[c] = ux;
     v.uy[c] = uy;

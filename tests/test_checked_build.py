@@ -5,7 +5,8 @@ printed and skipped), and canary blocks on both sides of each lattice's
 population planes are checked after every solve and optimiser step.
 
 Run in a child process (the binding loads one library per process): a solve
-and an exchange on the 128 x 64 T-junction report no violation; after the
+and an exchange on the 128 x 64 T-junction, and on the 72 x 34 x 34 D3Q19
+tree with and without packed cell tasks, report no violation; after the
 test hook overwrites part of a canary (a host-side memset inside the
 allocation: no device fault) the next solve fails with LBM_ERR_CUDA naming
 the canary.  The normal build has no canaries and refuses the hook.
@@ -32,6 +33,14 @@ cfg = I.config_t_junction()
 lat = L.Lattice(cfg["cells"], cfg["tau"], cfg["u_max"])
 lat.solve(400)
 lat.optimize_step(3, 200)
+import os
+c3 = I.config_tree3d_small()
+for pb in ("24", "32"):  # the D3Q19 step on row segments and packed cells, through an exchange
+    os.environ["LBM3D_PACK_BELOW"] = pb
+    l3 = L.Lattice3(c3["cells"], c3["tau"], c3["u_max"])
+    l3.solve(100)
+    l3.optimize_step(10, 100)
+    l3.close()
 print("SOLVED", flush=True)
 lat.debug_damage_canary()
 try:
