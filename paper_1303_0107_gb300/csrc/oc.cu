@@ -126,14 +126,18 @@ __global__ void k_oc_emit(const LatticeView* __restrict__ views, const int* __re
   const WordMasks m = word_masks(L->mask, nx, L->ny, L->wpr, y, w, L->guard);
   int of = off_f[i], os = off_s[i];
   bool bad = false;
+  // a field value, its index checked in the bounds-checked build (0 when outside)
+  const long long plane = L->plane;
+  (void)plane;
+  auto fld = [&](const float* a, long long c) { return LBM_OK_IDX(c, plane) ? (double)a[c] : 0.0; };
   uint32_t fc = m.fluid_cand;
   while (fc) {
     const int b = __ffs(fc) - 1;
     fc &= fc - 1;
     const int x = w * 32 + b;
     const long long c = (long long)y * pitch + x;
-    const double ux = L->ux[c], uy = L->uy[c];
-    const double rho = __dadd_rn(rho0, (double)L->drho[c]);
+    const double ux = fld(L->ux, c), uy = fld(L->uy, c);
+    const double rho = __dadd_rn(rho0, fld(L->drho, c));
     const double s = __dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy));
     const double q = __dmul_rn(__dmul_rn(0.5, rho), s);
     bad |= isnan(q);
@@ -151,10 +155,10 @@ __global__ void k_oc_emit(const LatticeView* __restrict__ views, const int* __re
     const bool fe = !((m.e >> b) & 1u), fn = !((m.n >> b) & 1u), fw = !((m.w >> b) & 1u),
                fs = !((m.s >> b) & 1u);
     double sigma = 0.0;
-    if (fe) sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, fabs((double)L->uy[c + 1])), 0.5));
-    if (fn) sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, fabs((double)L->ux[c + pitch])), 0.5));
-    if (fw) sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, fabs((double)L->uy[c - 1])), 0.5));
-    if (fs) sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, fabs((double)L->ux[c - pitch])), 0.5));
+    if (fe) sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, fabs(fld(L->uy, c + 1))), 0.5));
+    if (fn) sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, fabs(fld(L->ux, c + pitch))), 0.5));
+    if (fw) sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, fabs(fld(L->uy, c - 1))), 0.5));
+    if (fs) sigma = __dadd_rn(sigma, __ddiv_rn(__dmul_rn(mu, fabs(fld(L->ux, c - pitch))), 0.5));
     bad |= isnan(sigma);
     key_s[os] = ~order_key(sigma);  // ascending key = descending sigma
     idx_s[os] = y * nx + x;
@@ -283,7 +287,11 @@ __global__ void k_oc_apply(const LatticeView* __restrict__ views, const int* __r
   T* F = static_cast<T*>(L->f);
   const int* sel_f = sel_f_all + L->sel_off;
   const int* sel_s = sel_s_all + L->sel_off;
+  const long long cells = (long long)nx * L->ny;
+  (void)cells;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    // the picks are cell indices of the lattice (checked in the bounds-checked build)
+    if (!LBM_OK_IDX(sel_f[k], cells) || !LBM_OK_IDX(sel_s[k], cells)) continue;
     {  // fluid -> solid
       const int id = sel_f[k];
       const int y = id / nx, x = id - y * nx;
@@ -299,7 +307,8 @@ __global__ void k_oc_apply(const LatticeView* __restrict__ views, const int* __r
       atomicAnd(mask + (long long)y * ms + (x >> 5), ~(1u << (x & 31)));
       const long long c = (long long)y * pitch + x;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) F[i * pl + c] = T(0.0f);
+      for (int i = 0; i < 9; ++i)
+        if (LBM_OK_IDX(i * pl + c, L->f_elems)) F[i * pl + c] = T(0.0f);
       L->drho[c] = 0.0f;
       L->ux[c] = 0.0f;
       L->uy[c] = 0.0f;
