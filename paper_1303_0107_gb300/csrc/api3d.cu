@@ -375,7 +375,7 @@ lbm_status create3(const lbm3d_params& p, const uint8_t* cells, void* stream, lb
   CU3(h->alloc(&nbs, sizeof(uint32_t) * 32 * (size_t)h->total_words));
   v.nbs = nbs;
   uint32_t* cidx = nullptr;
-  CU3(h->alloc(&cidx, sizeof(uint32_t) * packed3_capacity(h->total_words)));
+  CU3(h->alloc(&cidx, sizeof(uint32_t) * packed3_capacity(g.fluid)));  // the exchange keeps the fluid count
   v.cidx = cidx;
   CU3(h->alloc(&h->seg_scratch, sizeof(int) * seg3_scratch_ints(h->total_words)));
   CU3(h->alloc(&h->n_segs, 2 * sizeof(int)));

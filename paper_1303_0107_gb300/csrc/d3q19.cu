@@ -832,7 +832,7 @@ inline int feat3(const View3& v) {
 
 size_t seg3_scratch_ints(long long total) { return 4 * (size_t)total + 2 + scan_tmp_ints(total); }
 
-size_t packed3_capacity(long long total) { return 32 * (size_t)total + 32; }
+size_t packed3_capacity(long long fluid) { return (size_t)fluid + 32; }
 
 cudaError_t launch_build_segments3(const View3& v, int pack_below, int* scratch, Seg3* segs, int* counts,
                                    cudaStream_t stream) {

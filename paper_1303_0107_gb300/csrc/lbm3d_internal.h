@@ -80,10 +80,11 @@ static_assert(sizeof(Seg3) == 8, "Seg3 layout");
 // plane): their fluid cells follow as packed tasks of 32 cells, their indices in v.cidx (ascending, padded to whole tasks) and
 // their flags in v.nbs after the segment tasks' blocks.  counts = {segment
 // tasks, all tasks}.  scratch holds seg3_scratch_ints(total) ints, segs
-// total entries, v.nbs 32 total and v.cidx packed3_capacity(total),
-// total = seg3_words(v).
+// total entries, v.nbs 32 total and v.cidx packed3_capacity(fluid cells)
+// (packed cells are fluid cells, plus one task's padding), total =
+// seg3_words(v).
 size_t seg3_scratch_ints(long long total);
-size_t packed3_capacity(long long total);
+size_t packed3_capacity(long long fluid);
 cudaError_t launch_build_segments3(const View3& v, int pack_below, int* scratch, Seg3* segs, int* counts,
                                    cudaStream_t stream);
 
