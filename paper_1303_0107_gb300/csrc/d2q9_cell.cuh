@@ -133,6 +133,86 @@ __device__ __forceinline__ void bgk(float (&g)[9], float rho0, float omega, floa
   close_moments(g, drho, jx, jy);
 }
 
+// The same update for two cells at once (a lane's pair of a paired task), in
+// the packed FP32 instructions of sm_100-family parts (add/sub/mul/fma.rn
+// .f32x2).  Each step is the rounding the compiler gives bgk()'s expressions:
+// a product feeding a sum becomes one fused multiply-add (t0 + 3 rho cu,
+// then + 4.5 rho cu^2; g + omega (e - g); drho - 1.5 rho (ux ux + uy uy)), so
+// that the two forms give the same bits -- the paired kernel's GPU tests
+// require it against the row-segment kernel at every storage type.
+struct F2 {
+  unsigned long long v;  // two FP32 values: the lower cell, the upper cell
+};
+__device__ __forceinline__ F2 f2(float lo, float hi) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_split(F2 a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  F2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b) {
+  F2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+  F2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c) {
+  F2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ F2 f2_c(float c) { return f2(c, c); }
+
+__device__ __forceinline__ void relax_pair2(F2& gi, F2& go, F2 cu, F2 w, F2 r3, F2 r3n, F2 r45, F2 t0, F2 omega) {
+  const F2 b = f2_mul(r45, cu);
+  const F2 ei = f2_mul(w, f2_fma(b, cu, f2_fma(r3, cu, t0)));
+  const F2 eo = f2_mul(w, f2_fma(b, cu, f2_fma(r3n, cu, t0)));
+  gi = f2_fma(omega, f2_sub(ei, gi), gi);
+  go = f2_fma(omega, f2_sub(eo, go), go);
+}
+
+__device__ __forceinline__ void bgk2(float (&a)[9], float (&b)[9], float rho0_, float omega_, float& dra,
+                                     float& uxa, float& uya, float& drb, float& uxb, float& uyb) {
+  F2 g[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) g[i] = f2(a[i], b[i]);
+  const F2 drho = f2_add(f2_add(f2_add(f2_add(g[0], g[1]), f2_add(g[2], g[3])),
+                                f2_add(f2_add(g[4], g[5]), f2_add(g[6], g[7]))), g[8]);
+  const F2 rho = f2_add(f2_c(rho0_), drho);
+  const F2 jx = f2_add(f2_add(f2_sub(g[1], g[3]), f2_sub(g[5], g[7])), f2_sub(g[8], g[6]));
+  const F2 jy = f2_add(f2_add(f2_sub(g[2], g[4]), f2_sub(g[5], g[7])), f2_sub(g[6], g[8]));
+  float rl, rh;
+  f2_split(rho, rl, rh);
+  const F2 inv = f2(__frcp_rn(rl), __frcp_rn(rh));  // correctly rounded: the value of 1.0f / rho
+  const F2 ux = f2_mul(jx, inv), uy = f2_mul(jy, inv);
+  const F2 t0 = f2_fma(f2_mul(f2_c(-1.5f), rho), f2_fma(ux, ux, f2_mul(uy, uy)), drho);
+  const F2 r3 = f2_mul(f2_c(3.0f), rho), r3n = f2_mul(f2_c(-3.0f), rho), r45 = f2_mul(f2_c(4.5f), rho);
+  const F2 omega = f2_c(omega_);
+  relax_pair2(g[1], g[3], ux, f2_c(kW1), r3, r3n, r45, t0, omega);
+  relax_pair2(g[2], g[4], uy, f2_c(kW1), r3, r3n, r45, t0, omega);
+  relax_pair2(g[5], g[7], f2_add(ux, uy), f2_c(kW5), r3, r3n, r45, t0, omega);
+  relax_pair2(g[8], g[6], f2_sub(ux, uy), f2_c(kW5), r3, r3n, r45, t0, omega);
+  g[1] = f2_sub(f2_add(jx, g[3]), f2_add(f2_sub(g[5], g[7]), f2_sub(g[8], g[6])));
+  g[2] = f2_sub(f2_add(jy, g[4]), f2_add(f2_sub(g[5], g[7]), f2_sub(g[6], g[8])));
+  g[0] = f2_sub(drho, f2_add(f2_add(f2_add(g[1], g[2]), f2_add(g[3], g[4])),
+                             f2_add(f2_add(g[5], g[6]), f2_add(g[7], g[8]))));
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f2_split(g[i], a[i], b[i]);
+  f2_split(drho, dra, drb);
+  f2_split(ux, uxa, uxb);
+  f2_split(uy, uya, uyb);
+}
+
 // Shifted equilibria of all nine directions for (rho0 + drho, ux, uy).
 __device__ __forceinline__ void shifted_equilibria(float (&e)[9], float rho0, float drho, float ux,
                                                    float uy) {

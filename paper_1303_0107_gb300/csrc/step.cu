@@ -506,8 +506,7 @@ __device__ __forceinline__ void pair_finish(const LatticeView* __restrict__ L, T
   const bool first = lane == 0, last = lane == 31;
   const float rho0 = L->rho0, omega = L->omega;
   float dra, uxa, uya, drb, uxb, uyb;
-  bgk(a, rho0, omega, dra, uxa, uya);
-  bgk(b, rho0, omega, drb, uxb, uyb);
+  bgk2(a, b, rho0, omega, dra, uxa, uya, drb, uxb, uyb);
   if (PHASE == 0) {
     // pushes g_i to F[opp(i)] at x + c_i
     PST2(c, a[0], b[0]);
