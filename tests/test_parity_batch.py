@@ -155,3 +155,29 @@ def test_full_candidate_batch_in_groups_matches_alone_and_oracle(ora):
     assert np.abs(ux - s.ux).max() / np.abs(s.ux).max() <= 1e-5
     assert abs(rb[k]["dp"] - o["dp"]) <= 1e-5 * abs(o["dp"])
     b.close()
+
+
+def test_full_candidate_batch_in_16bit_groups_matches_alone():
+    """The 256 candidates with BF16 storage, in the groups of the 16-bit
+    budget (two thirds of a third of the L2 of populations: about 4/3 of the
+    FP32 groups' cells): at least as many groups as the population bytes
+    need, and sampled members equal their runs alone bit for bit."""
+    import math
+    import torch
+    cands = I.config_candidates(256)
+    members = [dict(cells=c["cells"], tau=c["tau"], u_max=c["u_max"]) for c in cands]
+    b = L.Batch(members, precision=L.BF16_SHIFTED, residual_every=0)
+    rb = b.solve(600)
+    fluid = sum(int((c["cells"] == 0).sum()) for c in cands)
+    l2 = getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 0)
+    assert b.step_groups() > 1
+    if l2:
+        assert b.step_groups() >= math.ceil(9 * 2 * fluid / (l2 / 3.0 * 2.0 / 3.0))
+    for i in (0, 101, 255):
+        c = cands[i]
+        h = L.Lattice(c["cells"], c["tau"], c["u_max"], precision=L.BF16_SHIFTED, residual_every=0)
+        r = h.solve(600)
+        assert r["dp"] == rb[i]["dp"] and np.array_equal(r["m_out"], rb[i]["m_out"]), i
+        assert np.array_equal(h.read(L.FIELD_POPS), b.read(i, L.FIELD_POPS)), i
+        h.close()
+    b.close()
